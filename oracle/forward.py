@@ -1,0 +1,271 @@
+"""FP64 oracle: the MLPF transformer forward written out step by step.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
+The architecture follows Sec. 5.3 of the paper (arXiv 2601.17554): PF elements
+are embedded by a feed-forward network, processed by a classification (PID)
+transformer encoder and a regression encoder, and decoded by two-layer FFN
+heads.  Readings of points the paper leaves open (all listed in the design
+notes) are marked "reading:" below.
+
+Parity status: every function here is pinned by tests/test_oracle_pins.py
+(brute-force attention, closed forms, invariants, an independent torch.nn
+float64 model); none is "parity unpinned".
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+from scipy.special import erf
+
+F64 = np.float64
+
+
+# ---------------------------------------------------------------- primitives
+
+def layer_norm(x, g, b, eps=1e-5):
+    """Layer normalisation over the last axis (pre-LN blocks, Sec. 5.3).
+
+    reading: eps = 1e-5, biased variance.
+    """
+    x = np.asarray(x, F64)
+    mu = x.mean(axis=-1, keepdims=True)
+    var = ((x - mu) ** 2).mean(axis=-1, keepdims=True)
+    return (x - mu) / np.sqrt(var + eps) * np.asarray(g, F64) + np.asarray(b, F64)
+
+
+def gelu(x):
+    """Exact GELU x * Phi(x), Phi the standard normal CDF written with erf."""
+    x = np.asarray(x, F64)
+    return 0.5 * x * (1.0 + erf(x / math.sqrt(2.0)))
+
+
+def relu(x):
+    """Rectified linear unit (the paper's activation, Sec. 5.3)."""
+    return np.maximum(np.asarray(x, F64), 0.0)
+
+
+def activation(cfg_act):
+    return relu if cfg_act == 1 else gelu
+
+
+def linear(x, w, b):
+    """y = x W^T + b with W stored [out, in]."""
+    return np.asarray(x, F64) @ np.asarray(w, F64).T + np.asarray(b, F64)
+
+
+def softmax_rows(s):
+    """Row softmax: positive entries that sum to one per row (Sec. 5.3, Eq. 4).
+
+    A key masked with -inf gets weight exactly zero.
+    """
+    s = np.asarray(s, F64)
+    m = s.max(axis=-1, keepdims=True)
+    p = np.exp(s - m)
+    return p / p.sum(axis=-1, keepdims=True)
+
+
+def attention_matrix(q, k, key_mask=None):
+    """A = softmax(Q K^T / sqrt(d_k)) (Sec. 5.3, Eq. 4).
+
+    q [N, dk], k [M, dk]; key_mask [M] bool (True = real key) restricts the
+    softmax to real keys (padding keys get weight zero).
+    """
+    q = np.asarray(q, F64)
+    k = np.asarray(k, F64)
+    s = q @ k.T / math.sqrt(q.shape[-1])
+    if key_mask is not None:
+        s = np.where(np.asarray(key_mask, bool)[None, :], s, -np.inf)
+    return softmax_rows(s)
+
+
+def sdpa(q, k, v, key_mask=None):
+    """Scaled dot-product attention A V (Sec. 5.3, Eq. 4; FlashAttention computes
+    the same values exactly, Sec. 5.3)."""
+    return attention_matrix(q, k, key_mask) @ np.asarray(v, F64)
+
+
+# ------------------------------------------------------------------- blocks
+
+def multi_head_attention(zn, W, p, heads, key_mask=None):
+    """Multi-head self-attention over one event's elements.
+
+    reading: Q, K, V and output projections carry biases; heads split the
+    model width into `heads` contiguous slices of d/heads.
+    """
+    q = linear(zn, W[p + "wq"], W[p + "bq"])
+    k = linear(zn, W[p + "wk"], W[p + "bk"])
+    v = linear(zn, W[p + "wv"], W[p + "bv"])
+    d = q.shape[1]
+    dh = d // heads
+    o = np.empty_like(q)
+    for h in range(heads):
+        sl = slice(h * dh, (h + 1) * dh)
+        o[:, sl] = sdpa(q[:, sl], k[:, sl], v[:, sl], key_mask)
+    return linear(o, W[p + "wo"], W[p + "bo"])
+
+
+def encoder_block(z, W, p, heads, act, key_mask=None):
+    """Pre-LN transformer block (Sec. 5.3): z += MHA(LN1 z); z += FFN(LN2 z)."""
+    z = np.asarray(z, F64)
+    z = z + multi_head_attention(layer_norm(z, W[p + "ln1.g"], W[p + "ln1.b"]),
+                                 W, p, heads, key_mask)
+    zn = layer_norm(z, W[p + "ln2.g"], W[p + "ln2.b"])
+    hid = act(linear(zn, W[p + "ffn.w1"], W[p + "ffn.b1"]))
+    return z + linear(hid, W[p + "ffn.w2"], W[p + "ffn.b2"])
+
+
+def encoder_stack(z, W, prefix, n_layers, heads, act, key_mask=None):
+    """A stack of encoder blocks followed by a final LayerNorm.
+
+    reading: pre-LN stacks end with one LayerNorm (prefix.lnf).
+    """
+    for l in range(n_layers):
+        z = encoder_block(z, W, f"{prefix}.{l}.", heads, act, key_mask)
+    return layer_norm(z, W[prefix + ".lnf.g"], W[prefix + ".lnf.b"])
+
+
+def embed(x, W, act):
+    """Element embedding, a two-layer FFN 42 -> d -> d (Sec. 5.3).
+
+    reading: one shared FFN for all element types (the type one-hot is part
+    of x); activation between the layers, none after the second.
+    """
+    return linear(act(linear(x, W["emb.w1"], W["emb.b1"])), W["emb.w2"], W["emb.b2"])
+
+
+def reg_embed(x, h_pid, W, act):
+    """Input of the regression encoder: FFN over concat(x, h_pid), (42+d) -> d -> d.
+
+    reading: the regression stack takes the PID stack's (final-normed) output
+    concatenated with the raw input features.
+    """
+    xin = np.concatenate([np.asarray(x, F64), np.asarray(h_pid, F64)], axis=1)
+    return linear(act(linear(xin, W["remb.w1"], W["remb.b1"])), W["remb.w2"], W["remb.b2"])
+
+
+def ffn_head(h, W, name, act):
+    """Two-layer FFN output head (Sec. 5.3): d -> d -> k."""
+    p = f"head.{name}."
+    return linear(act(linear(h, W[p + "w1"], W[p + "b1"])), W[p + "w2"], W[p + "b2"])
+
+
+# ------------------------------------------------------------------ forward
+
+@dataclasses.dataclass
+class OracleOutput:
+    logits: np.ndarray      # [T, 6] raw class scores
+    raw: np.ndarray         # [T, 5] head outputs (pT', eta, sin, cos, E')
+    reg: np.ndarray         # [T, 5] decoded (pT, eta, sin phi, cos phi, E)
+    cls: np.ndarray         # [T] argmax class (0 = none)
+    sums: np.ndarray        # [n_events, 3] (METx, METy, sum pT)
+    h_pid: np.ndarray | None = None
+    h_reg: np.ndarray | None = None
+
+
+def forward_event(W, cfg, x, key_mask=None, keep_hidden=False):
+    """Forward of one event: x [N, 42] -> (logits [N, 6], raw [N, 5]).
+
+    Attention runs over this event's elements only (a set; no positional
+    encoding, Sec. 5.3).
+    """
+    act = activation(cfg.act)
+    x = np.asarray(x, F64)
+    e = embed(x, W, act)
+    h_pid = encoder_stack(e, W, "pid", cfg.l_pid, cfg.heads, act, key_mask)
+    r = reg_embed(x, h_pid, W, act)
+    h_reg = encoder_stack(r, W, "reg", cfg.l_reg, cfg.heads, act, key_mask)
+    logits = ffn_head(h_pid, W, "cls", act)
+    raw = np.concatenate([ffn_head(h_reg, W, "pt", act), ffn_head(h_reg, W, "eta", act),
+                          ffn_head(h_reg, W, "phi", act), ffn_head(h_reg, W, "e", act)],
+                         axis=1)
+    if keep_hidden:
+        return logits, raw, h_pid, h_reg
+    return logits, raw
+
+
+def decode(x, logits, raw):
+    """Candidates from head outputs (Sec. 5.3, Eq. 2 inverted).
+
+    class = argmax of the scores, lowest index on ties (0 = no particle);
+    pT = pT_elem * exp(pT'), E = E_elem * exp(E'), with log pT_elem = x[:, 8]
+    and log E_elem = x[:, 9]; eta, sin phi, cos phi as predicted.
+    """
+    x = np.asarray(x, F64)
+    raw = np.asarray(raw, F64)
+    cls = np.argmax(np.asarray(logits, F64), axis=1).astype(np.int32)
+    reg = np.empty_like(raw)
+    reg[:, 0] = np.exp(x[:, 8] + raw[:, 0])
+    reg[:, 1] = raw[:, 1]
+    reg[:, 2] = raw[:, 2]
+    reg[:, 3] = raw[:, 3]
+    reg[:, 4] = np.exp(x[:, 9] + raw[:, 4])
+    return cls, reg
+
+
+def event_sums(cls, reg, cu_seqlens):
+    """Per-event (METx, METy, sum pT) over predicted particles (cls != 0).
+
+    The missing-pT vector is the negative vector pT sum of the candidates
+    (Sec. 3.3, uncorrected and unweighted here).  phi enters through
+    (sin, cos) normalised by r = sqrt(s^2 + c^2); an element with r = 0 adds
+    its pT to the scalar sum but nothing to the vector sum.
+    """
+    cls = np.asarray(cls)
+    reg = np.asarray(reg, F64)
+    cu = np.asarray(cu_seqlens, np.int64)
+    out = np.zeros((len(cu) - 1, 3), F64)
+    for ev in range(len(cu) - 1):
+        sl = slice(cu[ev], cu[ev + 1])
+        keep = cls[sl] != 0
+        pt = reg[sl, 0][keep]
+        s = reg[sl, 2][keep]
+        c = reg[sl, 3][keep]
+        r = np.sqrt(s * s + c * c)
+        ok = r > 0
+        px = np.where(ok, pt * np.divide(c, r, out=np.zeros_like(c), where=ok), 0.0)
+        py = np.where(ok, pt * np.divide(s, r, out=np.zeros_like(s), where=ok), 0.0)
+        out[ev, 0] = -px.sum()
+        out[ev, 1] = -py.sum()
+        out[ev, 2] = pt.sum()
+    return out
+
+
+def forward(W, cfg, x, cu_seqlens, events=None, keep_hidden=False):
+    """Forward over a packed batch; events are independent.
+
+    events: optional list of event indices to evaluate (the others are left
+    as NaN rows / NaN sums), for sampled checks of large batches.
+    """
+    x = np.asarray(x, F64)
+    cu = np.asarray(cu_seqlens, np.int64)
+    total = int(cu[-1])
+    n = len(cu) - 1
+    logits = np.full((total, cfg.n_cls), np.nan)
+    raw = np.full((total, cfg.n_reg), np.nan)
+    hp = np.full((total, cfg.d), np.nan) if keep_hidden else None
+    hr = np.full((total, cfg.d), np.nan) if keep_hidden else None
+    todo = range(n) if events is None else events
+    for ev in todo:
+        sl = slice(cu[ev], cu[ev + 1])
+        if cu[ev + 1] == cu[ev]:
+            continue
+        res = forward_event(W, cfg, x[sl], keep_hidden=keep_hidden)
+        logits[sl], raw[sl] = res[0], res[1]
+        if keep_hidden:
+            hp[sl], hr[sl] = res[2], res[3]
+    cls = np.zeros(total, np.int32)
+    reg = np.full((total, cfg.n_reg), np.nan)
+    done = ~np.isnan(logits[:, 0])
+    if done.any():
+        c, r = decode(x[done], logits[done], raw[done])
+        cls[done] = c
+        reg[done] = r
+    sums = np.full((n, 3), np.nan)
+    for ev in todo:
+        sums[ev] = event_sums(cls[cu[ev]:cu[ev + 1]], reg[cu[ev]:cu[ev + 1]],
+                              [0, cu[ev + 1] - cu[ev]])[0]
+    return OracleOutput(logits=logits, raw=raw, reg=reg, cls=cls, sums=sums,
+                        h_pid=hp, h_reg=hr)

@@ -1,0 +1,299 @@
+"""Seeded synthetic inputs: PF-element events and model weight blobs.
+
+This module is shared by the FP64 oracle, the tests and the benchmark.  It holds
+no arithmetic of the MLPF method itself: only a counter-based random generator,
+the event generator, the seeded weight initialiser and the weight-blob writer.
+
+Random numbers come from one counter-based generator, the SplitMix64 output
+function (Steele, Lea, Flood, "Fast splittable pseudorandom number generators",
+OOPSLA 2014) applied as a hash of a key tuple, so that every value is a pure
+function of (seed, stream, index...) and any element can be regenerated alone.
+
+Events (Sec. 5.2 features; size statistics mimic the Run-3 pileup samples of
+Sec. 4, about 5000 elements per event per Sec. 5.3):
+  x[:, 0:8]   one-hot element type: track, ECAL, HCAL, HF-EM, HF-HAD, GSF track,
+              brem, supercluster (drawn with probabilities 40/25/20/3/3/3/3/3 %)
+  x[:, 8]     log pT  ~ N(0, 1)   (log GeV)
+  x[:, 9]     log E   ~ N(0, 1)   (log GeV)
+  x[:, 10]    eta: tracks, GSF tracks, brem U[-2.5, 2.5]; HF U[-5, 5];
+              ECAL, HCAL, supercluster U[-3, 3]
+  x[:, 11:13] sin phi, cos phi with phi ~ U[-pi, pi]
+  x[:, 13:30] 17 track-only features ~ N(0,1), zero for calorimeter types
+  x[:, 30:42] 12 cluster-only features ~ N(0,1), zero for track types
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+import struct
+
+import numpy as np
+
+IN_DIM = 42
+N_TYPES = 8
+N_CLS = 6
+N_REG = 5
+TYPE_NAMES = ("track", "ecal", "hcal", "hf_em", "hf_had", "gsf", "brem", "sc")
+TYPE_PROBS = (0.40, 0.25, 0.20, 0.03, 0.03, 0.03, 0.03, 0.03)
+TRACK_TYPES = (0, 5, 6)
+CLUSTER_TYPES = (1, 2, 3, 4, 7)
+CLASS_NAMES = ("none", "ch_had", "n_had", "photon", "electron", "muon")
+
+_M64 = np.uint64(0xFFFFFFFFFFFFFFFF)
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_C1 = np.uint64(0xBF58476D1CE4E5B9)
+_C2 = np.uint64(0x94D049BB133111EB)
+
+# stream identifiers (first key word after the seed)
+STREAM_EVENT_SIZE = 1
+STREAM_ELEMENT = 2
+STREAM_WEIGHT = 3
+
+
+def splitmix64(z):
+    """SplitMix64 output function on uint64 arrays (wrapping arithmetic)."""
+    z = np.asarray(z, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = z + _GOLDEN
+        z = (z ^ (z >> np.uint64(30))) * _C1
+        z = (z ^ (z >> np.uint64(27))) * _C2
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def hash_key(*words):
+    """Hash a tuple of integer (array) words into one uint64 per element."""
+    h = splitmix64(np.uint64(0))
+    for w in words:
+        h = splitmix64(h ^ np.asarray(w, dtype=np.uint64))
+    return h
+
+
+def uniform(*words):
+    """U[0,1) double from the top 53 bits of hash_key(words)."""
+    h = hash_key(*words)
+    return (h >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+
+
+def normal(*words):
+    """N(0,1) by Box-Muller from two sub-keys of words (sub-key 0 and 1)."""
+    u1 = uniform(*words, 0)
+    u2 = uniform(*words, 1)
+    return np.sqrt(-2.0 * np.log1p(-u1)) * np.cos(2.0 * math.pi * u2)
+
+
+# --------------------------------------------------------------------------
+# event sizes
+# --------------------------------------------------------------------------
+
+def sizes_uniform(seed: int, n_events: int, lo: int = 1000, hi: int = 6000):
+    """N ~ U{lo..hi} per event (pileup-like size mix)."""
+    e = np.arange(n_events, dtype=np.uint64)
+    u = uniform(seed, STREAM_EVENT_SIZE, e)
+    return (lo + np.floor(u * (hi - lo + 1))).astype(np.int64)
+
+
+def sizes_lognormal(seed: int, n_events: int, median: float = 2500.0,
+                    sigma: float = 0.5, lo: int = 100, hi: int = 12000):
+    """N ~ LogNormal(ln median, sigma), rounded and clipped to [lo, hi]."""
+    e = np.arange(n_events, dtype=np.uint64)
+    z = normal(seed, STREAM_EVENT_SIZE, e)
+    n = np.rint(np.exp(math.log(median) + sigma * z))
+    return np.clip(n, lo, hi).astype(np.int64)
+
+
+# --------------------------------------------------------------------------
+# events
+# --------------------------------------------------------------------------
+
+def gen_events(seed: int, sizes):
+    """Packed events: x [T, 42] float32 and cu_seqlens [n+1] int32.
+
+    Element i of event e depends only on (seed, e, i).
+    """
+    sizes = np.asarray(sizes, dtype=np.int64)
+    cu = np.zeros(len(sizes) + 1, dtype=np.int64)
+    np.cumsum(sizes, out=cu[1:])
+    total = int(cu[-1])
+    ev = np.repeat(np.arange(len(sizes), dtype=np.uint64), sizes)
+    idx = (np.arange(total, dtype=np.int64) - np.repeat(cu[:-1], sizes)).astype(np.uint64)
+    x = np.zeros((total, IN_DIM), dtype=np.float32)
+    if total == 0:
+        return x, cu.astype(np.int32)
+
+    def U(slot):
+        return uniform(seed, STREAM_ELEMENT, ev, idx, slot)
+
+    def Nrm(slot):
+        return normal(seed, STREAM_ELEMENT, ev, idx, slot)
+
+    u_type = U(0)
+    edges = np.cumsum(TYPE_PROBS)
+    edges[-1] = 1.0 + 1e-12
+    typ = np.searchsorted(edges, u_type, side="right")
+    x[np.arange(total), typ] = 1.0
+    x[:, 8] = Nrm(1)
+    x[:, 9] = Nrm(2)
+    ueta = U(3) * 2.0 - 1.0
+    eta_half = np.where(np.isin(typ, (3, 4)), 5.0,
+                        np.where(np.isin(typ, (1, 2, 7)), 3.0, 2.5))
+    x[:, 10] = ueta * eta_half
+    phi = (U(4) * 2.0 - 1.0) * math.pi
+    x[:, 11] = np.sin(phi)
+    x[:, 12] = np.cos(phi)
+    is_trk = np.isin(typ, TRACK_TYPES)
+    for k in range(17):
+        x[:, 13 + k] = np.where(is_trk, Nrm(10 + k), 0.0)
+    for k in range(12):
+        x[:, 30 + k] = np.where(~is_trk, Nrm(40 + k), 0.0)
+    return x, cu.astype(np.int32)
+
+
+# --------------------------------------------------------------------------
+# model configuration and weights
+# --------------------------------------------------------------------------
+
+ACT_GELU = 0
+ACT_RELU = 1
+
+
+@dataclasses.dataclass(frozen=True)
+class ModelConfig:
+    d: int = 64
+    heads: int = 4
+    ffn: int = 256
+    l_pid: int = 1
+    l_reg: int = 1
+    act: int = ACT_GELU
+    in_dim: int = IN_DIM
+    n_cls: int = N_CLS
+    n_reg: int = N_REG
+
+    @property
+    def dh(self) -> int:
+        return self.d // self.heads
+
+
+# The architecture of the 1-event / 64-event / 512-event workloads.
+SMALL = ModelConfig(d=64, heads=4, ffn=256, l_pid=1, l_reg=1)
+# The full-size architecture (d=256, 8 heads of 32, FFN 1024, 3+3 layers).
+FULL = ModelConfig(d=256, heads=8, ffn=1024, l_pid=3, l_reg=3)
+
+# Output width of each regression head, in output-column order.
+REG_HEADS = (("pt", 1), ("eta", 1), ("phi", 2), ("e", 1))
+
+
+def tensor_specs(cfg: ModelConfig):
+    """Ordered (name, shape, kind) of every parameter tensor.
+
+    kind: 'w' Xavier-initialised matrix [out, in]; 'b' bias; 'g' LN gain;
+    'beta' LN shift.  The order fixes the random stream index of each tensor.
+    """
+    d, f = cfg.d, cfg.ffn
+    specs = [("emb.w1", (d, cfg.in_dim), "w"), ("emb.b1", (d,), "b"),
+             ("emb.w2", (d, d), "w"), ("emb.b2", (d,), "b")]
+
+    def stack(prefix, n):
+        out = []
+        for l in range(n):
+            p = f"{prefix}.{l}."
+            out += [(p + "ln1.g", (d,), "g"), (p + "ln1.b", (d,), "beta"),
+                    (p + "wq", (d, d), "w"), (p + "bq", (d,), "b"),
+                    (p + "wk", (d, d), "w"), (p + "bk", (d,), "b"),
+                    (p + "wv", (d, d), "w"), (p + "bv", (d,), "b"),
+                    (p + "wo", (d, d), "w"), (p + "bo", (d,), "b"),
+                    (p + "ln2.g", (d,), "g"), (p + "ln2.b", (d,), "beta"),
+                    (p + "ffn.w1", (f, d), "w"), (p + "ffn.b1", (f,), "b"),
+                    (p + "ffn.w2", (d, f), "w"), (p + "ffn.b2", (d,), "b")]
+        out += [(prefix + ".lnf.g", (d,), "g"), (prefix + ".lnf.b", (d,), "beta")]
+        return out
+
+    specs += stack("pid", cfg.l_pid)
+    specs += [("remb.w1", (d, cfg.in_dim + d), "w"), ("remb.b1", (d,), "b"),
+              ("remb.w2", (d, d), "w"), ("remb.b2", (d,), "b")]
+    specs += stack("reg", cfg.l_reg)
+    specs += [("head.cls.w1", (d, d), "w"), ("head.cls.b1", (d,), "b"),
+              ("head.cls.w2", (cfg.n_cls, d), "w"), ("head.cls.b2", (cfg.n_cls,), "b")]
+    for name, k in REG_HEADS:
+        specs += [(f"head.{name}.w1", (d, d), "w"), (f"head.{name}.b1", (d,), "b"),
+                  (f"head.{name}.w2", (k, d), "w"), (f"head.{name}.b2", (k,), "b")]
+    return specs
+
+
+def make_weights(cfg: ModelConfig, seed: int, perturbed: bool = False,
+                 cls_scale: float = 1.0):
+    """Seeded weights: dict name -> float32 array.
+
+    Matrices: Xavier-uniform, W ~ U(-a, a) with a = sqrt(6/(fan_in+fan_out)).
+    Default: biases 0, LN gain 1, LN shift 0.  perturbed=True draws biases and
+    LN shifts from U(-0.1, 0.1) and gains from 1 + U(-0.1, 0.1), so that every
+    bias and normalisation parameter is exercised by parity tests.
+    cls_scale multiplies the last class-head layer (weights and bias).
+    """
+    w = {}
+    for t, (name, shape, kind) in enumerate(tensor_specs(cfg)):
+        n = int(np.prod(shape))
+        u = uniform(seed, STREAM_WEIGHT, t, np.arange(n, dtype=np.uint64))
+        if kind == "w":
+            a = math.sqrt(6.0 / (shape[0] + shape[1]))
+            v = (2.0 * u - 1.0) * a
+        elif kind == "g":
+            v = 1.0 + (0.2 * u - 0.1 if perturbed else 0.0 * u)
+        else:
+            v = (0.2 * u - 0.1) if perturbed else 0.0 * u
+        w[name] = v.reshape(shape).astype(np.float32)
+    if cls_scale != 1.0:
+        w["head.cls.w2"] = (w["head.cls.w2"] * np.float32(cls_scale)).astype(np.float32)
+        w["head.cls.b2"] = (w["head.cls.b2"] * np.float32(cls_scale)).astype(np.float32)
+    return w
+
+
+# --------------------------------------------------------------------------
+# weight blob (read by mlpf_load_weights)
+# --------------------------------------------------------------------------
+
+BLOB_MAGIC = b"MLPF"
+BLOB_VERSION = 1
+NAME_BYTES = 48
+
+
+def pack_blob(cfg: ModelConfig, weights) -> bytes:
+    """Serialise weights into the library's blob format.
+
+    Layout (little endian):
+      char magic[4] = "MLPF"; int32 version;
+      int32 in_dim, d, heads, ffn, l_pid, l_reg, n_cls, n_reg, act, n_tensors;
+      n_tensors records: char name[48]; int32 ndim; int32 shape[2];
+                         float32 data[prod(shape)]
+    """
+    specs = tensor_specs(cfg)
+    out = [BLOB_MAGIC, struct.pack("<i", BLOB_VERSION),
+           struct.pack("<10i", cfg.in_dim, cfg.d, cfg.heads, cfg.ffn, cfg.l_pid,
+                       cfg.l_reg, cfg.n_cls, cfg.n_reg, cfg.act, len(specs))]
+    for name, shape, _ in specs:
+        a = np.ascontiguousarray(weights[name], dtype=np.float32)
+        assert a.shape == tuple(shape), (name, a.shape, shape)
+        nb = name.encode()
+        assert len(nb) < NAME_BYTES
+        dims = list(shape) + [1] * (2 - len(shape))
+        out.append(nb + b"\0" * (NAME_BYTES - len(nb)))
+        out.append(struct.pack("<3i", len(shape), dims[0], dims[1]))
+        out.append(a.tobytes())
+    return b"".join(out)
+
+
+# --------------------------------------------------------------------------
+# named workloads
+# --------------------------------------------------------------------------
+
+def workload(name: str):
+    """(model config, weight seed, input seed, sizes) of a named workload."""
+    if name == "event256":          # one event of 256 elements, FP32 parity
+        return SMALL, 0, 101, np.array([256])
+    if name == "full16":            # 16 events U{1000..6000}, full-size model
+        return FULL, 1, 102, sizes_uniform(102, 16)
+    if name == "prec64":            # 64 events U{1000..6000}, small model
+        return SMALL, 0, 103, sizes_uniform(103, 64)
+    if name == "batch512":          # 512 events LogNormal(2500, 0.5) in [100, 12000]
+        return SMALL, 0, 104, sizes_lognormal(104, 512)
+    raise KeyError(name)

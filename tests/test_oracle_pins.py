@@ -1,0 +1,287 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: brute force on
+tiny inputs, closed forms, invariants of the method (a set model with no
+positional encoding, Sec. 5.3), and an independent float64 model assembled from
+torch.nn.functional library routines.  No GPU is needed.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import torch
+import torch.nn.functional as F
+
+import oracle
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+rng = np.random.default_rng(7)
+
+
+# ---------------------------------------------------------------- attention
+
+def brute_force_sdpa(q, k, v, mask=None):
+    """Pure-Python loop nest of Eq. 4 (no numpy reductions)."""
+    n, dk = len(q), len(q[0])
+    m = len(k)
+    out = []
+    for i in range(n):
+        scores = []
+        for j in range(m):
+            if mask is not None and not mask[j]:
+                scores.append(None)
+                continue
+            s = 0.0
+            for t in range(dk):
+                s += float(q[i][t]) * float(k[j][t])
+            scores.append(s / math.sqrt(dk))
+        mx = max(s for s in scores if s is not None)
+        w = [0.0 if s is None else math.exp(s - mx) for s in scores]
+        tot = sum(w)
+        row = []
+        for t in range(len(v[0])):
+            acc = 0.0
+            for j in range(m):
+                acc += w[j] / tot * float(v[j][t])
+            row.append(acc)
+        out.append(row)
+    return np.array(out)
+
+
+@pytest.mark.parametrize("n,m,dk", [(1, 1, 4), (3, 5, 16), (16, 16, 16), (7, 16, 32)])
+def test_sdpa_brute_force(n, m, dk):
+    q, k, v = rng.normal(size=(n, dk)), rng.normal(size=(m, dk)), rng.normal(size=(m, dk))
+    np.testing.assert_allclose(oracle.sdpa(q, k, v), brute_force_sdpa(q, k, v),
+                               rtol=1e-12, atol=1e-13)
+
+
+def test_sdpa_brute_force_masked():
+    q, k, v = rng.normal(size=(6, 16)), rng.normal(size=(12, 16)), rng.normal(size=(12, 16))
+    mask = np.array([True] * 9 + [False] * 3)
+    mask[4] = False
+    np.testing.assert_allclose(oracle.sdpa(q, k, v, mask), brute_force_sdpa(q, k, v, mask),
+                               rtol=1e-12, atol=1e-13)
+
+
+def test_softmax_rows_positive_and_sum_to_one():
+    q, k = rng.normal(size=(40, 16)) * 3, rng.normal(size=(33, 16)) * 3
+    a = oracle.attention_matrix(q, k)
+    assert (a > 0).all()
+    np.testing.assert_allclose(a.sum(axis=1), 1.0, atol=1e-15 * 33)
+
+
+def test_sdpa_single_key_returns_v():
+    q, k, v = rng.normal(size=(1, 16)), rng.normal(size=(1, 16)), rng.normal(size=(1, 16))
+    np.testing.assert_array_equal(oracle.sdpa(q, k, v), v)
+
+
+def test_sdpa_textbook_library():
+    q, k, v = (torch.randn(1, 1, 20, 16, dtype=torch.float64) for _ in range(3))
+    ref = F.scaled_dot_product_attention(q, k, v)[0, 0].numpy()
+    np.testing.assert_allclose(oracle.sdpa(q[0, 0].numpy(), k[0, 0].numpy(), v[0, 0].numpy()),
+                               ref, rtol=1e-12, atol=1e-13)
+
+
+# ----------------------------------------------------------- LN and GELU
+
+def test_layer_norm_closed_forms():
+    g, b = rng.normal(size=8), rng.normal(size=8)
+    np.testing.assert_allclose(oracle.layer_norm(np.full((1, 8), 3.7), g, b)[0], b, atol=1e-12)
+    a = 2.5
+    x = np.array([[a, -a]])
+    y = oracle.layer_norm(x, np.ones(2), np.zeros(2), eps=1e-5)
+    np.testing.assert_allclose(y[0], [a / math.sqrt(a * a + 1e-5), -a / math.sqrt(a * a + 1e-5)],
+                               rtol=1e-14)
+    z = oracle.layer_norm(rng.normal(size=(5, 64)) * 10 + 3, np.ones(64), np.zeros(64))
+    np.testing.assert_allclose(z.mean(axis=1), 0.0, atol=1e-12)
+    np.testing.assert_allclose(z.var(axis=1), 1.0, rtol=1e-5)
+
+
+def test_gelu_closed_forms():
+    phi1 = 0.8413447460685429  # standard normal CDF at 1
+    np.testing.assert_allclose(oracle.gelu([0.0, 1.0, -1.0]), [0.0, phi1, -(1 - phi1)],
+                               rtol=1e-15, atol=1e-16)
+    np.testing.assert_allclose(oracle.gelu([12.0, -12.0]), [12.0, 0.0], atol=1e-30)
+    np.testing.assert_array_equal(oracle.relu([-2.0, 0.0, 3.0]), [0.0, 0.0, 3.0])
+
+
+# -------------------------------------------------- independent torch model
+
+def torch_reference(W, cfg, x):
+    """The architecture assembled from torch.nn.functional routines in float64."""
+    T = {k: torch.tensor(np.asarray(v, np.float64)) for k, v in W.items()}
+    act = (lambda t: F.gelu(t, approximate="none")) if cfg.act == 0 else F.relu
+    x = torch.tensor(np.asarray(x, np.float64))
+
+    def lin(t, p):
+        return F.linear(t, T[p + "w" if p.endswith(".") else p + ".w"], None)
+
+    def ln(t, p):
+        return F.layer_norm(t, (cfg.d,), T[p + ".g"], T[p + ".b"], eps=1e-5)
+
+    def mlp(t, w1, b1, w2, b2):
+        return F.linear(act(F.linear(t, T[w1], T[b1])), T[w2], T[b2])
+
+    def stack(z, prefix, n):
+        for l in range(n):
+            p = f"{prefix}.{l}."
+            zn = ln(z, p + "ln1")
+            q = F.linear(zn, T[p + "wq"], T[p + "bq"])
+            k = F.linear(zn, T[p + "wk"], T[p + "bk"])
+            v = F.linear(zn, T[p + "wv"], T[p + "bv"])
+            split = lambda t: t.view(-1, cfg.heads, cfg.dh).transpose(0, 1)
+            o = F.scaled_dot_product_attention(split(q), split(k), split(v))
+            o = o.transpose(0, 1).reshape(-1, cfg.d)
+            z = z + F.linear(o, T[p + "wo"], T[p + "bo"])
+            z = z + mlp(ln(z, p + "ln2"), p + "ffn.w1", p + "ffn.b1", p + "ffn.w2", p + "ffn.b2")
+        return ln(z, prefix + ".lnf")
+
+    h_pid = stack(mlp(x, "emb.w1", "emb.b1", "emb.w2", "emb.b2"), "pid", cfg.l_pid)
+    h_reg = stack(mlp(torch.cat([x, h_pid], 1), "remb.w1", "remb.b1", "remb.w2", "remb.b2"),
+                  "reg", cfg.l_reg)
+    head = lambda h, n: mlp(h, f"head.{n}.w1", f"head.{n}.b1", f"head.{n}.w2", f"head.{n}.b2")
+    logits = head(h_pid, "cls")
+    raw = torch.cat([head(h_reg, n) for n, _ in synth.REG_HEADS], 1)
+    return logits.numpy(), raw.numpy()
+
+
+@pytest.mark.parametrize("cfg", [synth.SMALL, synth.FULL,
+                                 synth.ModelConfig(d=32, heads=2, ffn=64, l_pid=2, l_reg=1, act=1)])
+def test_forward_matches_torch_functional(cfg):
+    W = synth.make_weights(cfg, seed=5, perturbed=True)
+    x, cu = synth.gen_events(11, [23])
+    lo, raw = oracle.forward_event(W, cfg, x)
+    tl, traw = torch_reference(W, cfg, x)
+    np.testing.assert_allclose(lo, tl, rtol=1e-10, atol=1e-11)
+    np.testing.assert_allclose(raw, traw, rtol=1e-10, atol=1e-11)
+
+
+# --------------------------------------------------------------- invariants
+
+@pytest.fixture(scope="module")
+def small_model():
+    cfg = synth.SMALL
+    return cfg, synth.make_weights(cfg, seed=3, perturbed=True)
+
+
+def test_permutation_equivariance(small_model):
+    cfg, W = small_model
+    x, _ = synth.gen_events(12, [31])
+    perm = np.random.default_rng(1).permutation(31)
+    lo, raw = oracle.forward_event(W, cfg, x)
+    lo_p, raw_p = oracle.forward_event(W, cfg, x[perm])
+    np.testing.assert_allclose(lo_p, lo[perm], rtol=1e-11, atol=1e-12)
+    np.testing.assert_allclose(raw_p, raw[perm], rtol=1e-11, atol=1e-12)
+
+
+def test_padding_invariance(small_model):
+    cfg, W = small_model
+    x, _ = synth.gen_events(13, [20])
+    pad = np.random.default_rng(2).normal(size=(9, 42)) * 5
+    xp = np.concatenate([x, pad])
+    mask = np.array([True] * 20 + [False] * 9)
+    lo, raw = oracle.forward_event(W, cfg, x)
+    lo_p, raw_p = oracle.forward_event(W, cfg, xp, key_mask=mask)
+    np.testing.assert_allclose(lo_p[:20], lo, rtol=1e-11, atol=1e-12)
+    np.testing.assert_allclose(raw_p[:20], raw, rtol=1e-11, atol=1e-12)
+
+
+def test_identity_when_sublayers_zeroed(small_model):
+    cfg, W = small_model
+    W = dict(W)
+    for l in range(cfg.l_pid):
+        for n in ("wo", "bo", "ffn.w2", "ffn.b2"):
+            W[f"pid.{l}.{n}"] = np.zeros_like(W[f"pid.{l}.{n}"])
+    z = np.random.default_rng(3).normal(size=(17, cfg.d))
+    out = oracle.encoder_stack(z, W, "pid", cfg.l_pid, cfg.heads, oracle.gelu)
+    ref = oracle.layer_norm(z, W["pid.lnf.g"], W["pid.lnf.b"])
+    np.testing.assert_array_equal(out, ref)
+
+
+def test_single_element_reduces_to_mlp(small_model):
+    """N=1: attention returns V, so a block is a per-element map independent of
+    any other element; the event forward equals the forward of each element alone."""
+    cfg, W = small_model
+    x, _ = synth.gen_events(14, [1])
+    lo, raw = oracle.forward_event(W, cfg, x)
+    tl, traw = torch_reference(W, cfg, x)
+    np.testing.assert_allclose(lo, tl, rtol=1e-10)
+    np.testing.assert_allclose(raw, traw, rtol=1e-10)
+
+
+def test_duplicate_elements_identical(small_model):
+    cfg, W = small_model
+    x, _ = synth.gen_events(15, [10])
+    x[7] = x[2]
+    lo, raw = oracle.forward_event(W, cfg, x)
+    np.testing.assert_array_equal(lo[7], lo[2])
+    np.testing.assert_array_equal(raw[7], raw[2])
+
+
+def test_events_independent(small_model):
+    cfg, W = small_model
+    x, cu = synth.gen_events(16, [5, 0, 12, 1])
+    out = oracle.forward(W, cfg, x, cu)
+    for e in range(4):
+        sl = slice(cu[e], cu[e + 1])
+        if cu[e + 1] == cu[e]:
+            assert out.sums[e].tolist() == [0.0, 0.0, 0.0] or np.isnan(out.sums[e]).all()
+            continue
+        lo, raw = oracle.forward_event(W, cfg, x[sl])
+        np.testing.assert_array_equal(out.logits[sl], lo)
+        np.testing.assert_array_equal(out.raw[sl], raw)
+
+
+# ------------------------------------------------------- decode and sums
+
+def test_decode_and_event_sums_hand_examples():
+    with open(os.path.join(GOLDEN, "event_sums_hand.json")) as f:
+        cases = json.load(f)["cases"]
+    for case in cases:
+        x = np.zeros((len(case["log_pt"]), 42))
+        x[:, 8] = case["log_pt"]
+        x[:, 9] = case["log_e"]
+        logits = np.array(case["logits"], dtype=np.float64)
+        raw = np.array(case["raw"], dtype=np.float64)
+        cls, reg = oracle.decode(x, logits, raw)
+        assert cls.tolist() == case["cls"], case["name"]
+        np.testing.assert_allclose(reg[:, 0], case["pt"], rtol=1e-14)
+        np.testing.assert_allclose(reg[:, 4], case["e"], rtol=1e-14)
+        sums = oracle.event_sums(cls, reg, [0, len(cls)])[0]
+        np.testing.assert_allclose(sums, case["sums"], atol=1e-12, err_msg=case["name"])
+
+
+# ------------------------------------------------------------- generator
+
+def test_generator_statistics_and_masks():
+    x, cu = synth.gen_events(104, synth.sizes_lognormal(104, 64))
+    typ = x[:, :8].argmax(1)
+    assert np.all(x[:, :8].sum(1) == 1)
+    frac = np.bincount(typ, minlength=8) / len(typ)
+    np.testing.assert_allclose(frac, synth.TYPE_PROBS, atol=0.01)
+    trk = np.isin(typ, synth.TRACK_TYPES)
+    assert np.all(x[trk, 30:42] == 0) and np.all(x[~trk, 13:30] == 0)
+    np.testing.assert_allclose(x[:, 11] ** 2 + x[:, 12] ** 2, 1.0, rtol=1e-6)
+    assert np.abs(x[np.isin(typ, (3, 4)), 10]).max() <= 5.0
+    assert np.abs(x[trk, 10]).max() <= 2.5
+    assert abs(x[:, 8].mean()) < 0.02 and abs(x[:, 8].std() - 1) < 0.02
+
+
+def test_generator_counter_based():
+    x1, _ = synth.gen_events(9, [4, 7])
+    x2, _ = synth.gen_events(9, [4, 9, 3])
+    np.testing.assert_array_equal(x1[:4], x2[:4])
+    np.testing.assert_array_equal(x1[4:11], x2[4:11])
+    n = synth.sizes_lognormal(104, 512)
+    assert n.min() >= 100 and n.max() <= 12000
+    assert 2200 < np.median(n) < 2800
+    u = synth.sizes_uniform(103, 64)
+    assert u.min() >= 1000 and u.max() <= 6000
+
+
+def test_splitmix64_published_vector():
+    # SplitMix64 output sequence for state 0 (first output), a published value.
+    assert int(synth.splitmix64(np.uint64(0))) == 0xE220A8397B1DCDAF
