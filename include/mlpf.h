@@ -1,0 +1,167 @@
+/*
+ * mlpf.h -- C ABI of the B300 (sm_103a) MLPF full-event transformer forward.
+ *
+ * The library maps each event's variable-length set of PF elements (tracks and
+ * calorimeter clusters, one 42-float feature vector each; Sec. 5.2) to a
+ * per-element particle class (none, charged hadron, neutral hadron, photon,
+ * electron, muon) and the regressed (pT, eta, sin phi, cos phi, E) of the MLPF
+ * transformer (Sec. 5.3), plus FP64 per-event missing-pT and scalar-pT sums
+ * (Sec. 3.3).  Many events are packed back to back and described by offsets.
+ *
+ * Conventions for every entry point:
+ *  - Every call returns an mlpf_status and never aborts the process.  On a
+ *    non-OK status, mlpf_last_error() returns a message (thread-local).
+ *  - "device" pointers are CUDA device memory on the model's device (for
+ *    instance torch tensors' data_ptr()); "host" pointers are CPU memory.
+ *  - The caller owns every input and output buffer.  The model owns its
+ *    weights and its workspace.
+ *  - A model may be used from one host thread and one stream at a time.
+ *    Different models are independent.
+ */
+#ifndef MLPF_H
+#define MLPF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mlpf_model mlpf_model; /* opaque */
+
+typedef enum {
+    MLPF_OK = 0,
+    MLPF_E_INVALID = 1,     /* bad argument (null pointer, size, precision) */
+    MLPF_E_FORMAT = 2,      /* malformed weight blob (magic, version, shapes) */
+    MLPF_E_CUDA = 3,        /* a CUDA runtime/driver call failed */
+    MLPF_E_OOM = 4,         /* device allocation failed */
+    MLPF_E_TIMEOUT = 5,     /* a bounded device-side wait ran out (see mlpf_sync) */
+    MLPF_E_NONFINITE = 6,   /* non-finite values reached the outputs (see mlpf_sync) */
+    MLPF_E_UNSUPPORTED = 7  /* precision/architecture combination not built */
+} mlpf_status;
+
+typedef enum {
+    MLPF_FP32 = 0, /* plain path: SIMT FP32 FFMA GEMMs and attention, no TF32 */
+    MLPF_BF16 = 1, /* tcgen05 tensor cores, BF16 operands, FP32 accumulation */
+    MLPF_FP8 = 2   /* E4M3 projection/FFN GEMMs with per-tensor scales (BF16 attention) */
+} mlpf_precision;
+
+/* Model configuration, as stored in the weight blob header. */
+typedef struct {
+    int32_t in_dim; /* 42 input features per element */
+    int32_t d;      /* model width */
+    int32_t heads;  /* attention heads; head width d/heads */
+    int32_t ffn;    /* FFN hidden width */
+    int32_t l_pid;  /* encoder blocks in the classification (PID) stack */
+    int32_t l_reg;  /* encoder blocks in the regression stack */
+    int32_t n_cls;  /* 6 classes: none, ch. hadron, n. hadron, photon, electron, muon */
+    int32_t n_reg;  /* 5 regression outputs: pT, eta, sin phi, cos phi, E */
+    int32_t act;    /* 0 = GELU (exact erf form), 1 = ReLU */
+} mlpf_config;
+
+/*
+ * Load a weight blob and create a model on CUDA device `device`.
+ *
+ * The blob plays the role of the paper's frozen inference graph (Sec. 8):
+ *   char magic[4] = "MLPF"; int32 version = 1;
+ *   int32 in_dim, d, heads, ffn, l_pid, l_reg, n_cls, n_reg, act, n_tensors;
+ *   n_tensors x { char name[48]; int32 ndim; int32 shape[2]; float data[] }
+ * (little endian; tensors as written by synth.pack_blob, matrices [out, in]).
+ * blob: host memory, read during the call only.  *out receives the model.
+ * Errors: MLPF_E_INVALID (null, nbytes too small, bad device),
+ *         MLPF_E_FORMAT (magic, version, missing/extra/mis-shaped tensor,
+ *         truncated data), MLPF_E_CUDA / MLPF_E_OOM.
+ */
+mlpf_status mlpf_load_weights(const void* blob, size_t nbytes, int device, mlpf_model** out);
+
+/* Release a model, its weights, workspace and cached graphs.  NULL is a no-op. */
+void mlpf_free(mlpf_model* m);
+
+/* Copy the model configuration into *cfg (host). */
+mlpf_status mlpf_get_config(const mlpf_model* m, mlpf_config* cfg);
+
+/*
+ * Batched forward over packed events (Sec. 5.3; inference decoding as in
+ * Sec. 5.3; missing-pT sums as in Sec. 3.3).  Asynchronous on `stream`.
+ *
+ * x          device, [total, 42] float32 row-major; event e occupies rows
+ *            cu_seqlens[e] .. cu_seqlens[e+1]-1.  Feature layout: x[:,0:8]
+ *            type one-hot, x[:,8] log pT, x[:,9] log E, x[:,10] eta,
+ *            x[:,11:13] sin/cos phi, x[:,13:42] other features.
+ * cu_seqlens device, [n_events+1] int32, cu[0] = 0, non-decreasing,
+ *            cu[n_events] = total.  Empty events (N = 0) are allowed.
+ * n_events, total   host scalars matching cu_seqlens.
+ * max_n      host scalar >= max_e N_e (sizes launch grids), <= 65536.
+ * logits     device out, [total, 6] float32 raw class scores.
+ * reg        device out, [total, 5] float32 decoded (pT GeV, eta, sin phi,
+ *            cos phi, E GeV) with pT = exp(x[:,8] + pT'), E = exp(x[:,9] + E').
+ * cls        device out or NULL, [total] int32 argmax class, lowest index on ties.
+ * event_sums device out or NULL, [n_events, 3] float64 (METx, METy, sum pT)
+ *            over elements with cls != 0; phi from (sin, cos) / |(sin, cos)|.
+ * stream     cudaStream_t (NULL = legacy default stream).
+ *
+ * total = 0 is a no-op.  Inputs are not validated on the device: offsets
+ * that break the contract give undefined results (but stay in bounds of
+ * the workspace sized from total/max_n/n_events).
+ * Errors: MLPF_E_INVALID (null pointers, negative sizes, max_n > 65536,
+ *         unknown precision), MLPF_E_UNSUPPORTED (precision not built for this
+ *         configuration), MLPF_E_OOM (workspace growth), MLPF_E_CUDA.
+ * Device-side timeouts and non-finite outputs are reported by mlpf_sync().
+ */
+mlpf_status mlpf_forward(mlpf_model* m, int32_t precision,
+                         const float* x, const int32_t* cu_seqlens,
+                         int32_t n_events, int32_t total, int32_t max_n,
+                         float* logits, float* reg, int32_t* cls,
+                         double* event_sums, void* stream);
+
+/*
+ * Same as mlpf_forward with HOST buffers: copies x and cu_seqlens to the
+ * device (through the model's pinned staging buffers), runs the forward and
+ * copies the outputs back; returns when the host outputs are written.
+ * x, cu_seqlens: host inputs; logits, reg: host outputs; cls, event_sums:
+ * host outputs or NULL.  Errors as mlpf_forward plus those of mlpf_sync.
+ */
+mlpf_status mlpf_forward_host(mlpf_model* m, int32_t precision,
+                              const float* x, const int32_t* cu_seqlens,
+                              int32_t n_events, int32_t total, int32_t max_n,
+                              float* logits, float* reg, int32_t* cls,
+                              double* event_sums, void* stream);
+
+/*
+ * Wait for the model's work on `stream` and report device-side status:
+ * MLPF_E_TIMEOUT if a bounded wait inside a kernel ran out since the last
+ * mlpf_sync (the kernel returned early; outputs are invalid), otherwise
+ * MLPF_OK.  Clears the device status word.
+ */
+mlpf_status mlpf_sync(mlpf_model* m, void* stream);
+
+/* Options (mlpf_set_option). */
+enum {
+    MLPF_OPT_USE_GRAPHS = 1,        /* 1 (default): replay CUDA graphs for repeated calls */
+    MLPF_OPT_WAIT_LIMIT_NS = 2,     /* bound of every device-side wait (default 2e9 ns) */
+    MLPF_OPT_DEBUG_STALL = 3,       /* 1: attention consumers wait on a barrier nothing
+                                       arms, to exercise the timeout path (tests only) */
+    MLPF_OPT_ATTN_CTAS_PER_SM = 4,  /* attention persistent grid size factor (autotuned) */
+    MLPF_OPT_ATTN_KV_STAGES = 5     /* read-only in this build: K/V pipeline depth */
+};
+mlpf_status mlpf_set_option(mlpf_model* m, int32_t option, int64_t value);
+mlpf_status mlpf_get_option(const mlpf_model* m, int32_t option, int64_t* value);
+
+/*
+ * Number of kernels launched by the most recent forward call (all precisions),
+ * counted on the host at launch (a graph replay counts its kernel nodes).
+ */
+int64_t mlpf_last_launch_count(const mlpf_model* m);
+
+/* Thread-local message describing the last non-OK status of this thread. */
+const char* mlpf_last_error(void);
+
+/* ABI version of this library (major * 100 + minor). */
+int32_t mlpf_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MLPF_H */

@@ -1,0 +1,112 @@
+"""B300 (sm_103a) MLPF full-event transformer forward behind a C ABI.
+
+This module is a thin binding: it passes torch tensors' device pointers, sizes
+and the current CUDA stream to the C entry points of libmlpf.so
+(include/mlpf.h).  Every step of the forward runs in the library's CUDA
+kernels; there is no CPU or PyTorch fallback: if the library cannot be loaded
+or the GPU path fails, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+
+from . import _lib
+from ._lib import (MLPF_FP32, MLPF_BF16, MLPF_FP8, MlpfError, check,  # noqa: F401
+                   OPT_USE_GRAPHS, OPT_WAIT_LIMIT_NS, OPT_DEBUG_STALL)
+
+PRECISIONS = {"fp32": MLPF_FP32, "bf16": MLPF_BF16, "fp8": MLPF_FP8}
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+class Model:
+    """A loaded MLPF model on one CUDA device (owns weights and workspace)."""
+
+    def __init__(self, blob: bytes, device: int = 0):
+        self.L = _lib.load()
+        h = ctypes.c_void_p()
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        check(self.L.mlpf_load_weights(buf, len(blob), device, ctypes.byref(h)))
+        self.h = h
+        self.device = device
+        cfg = _lib.MlpfConfig()
+        check(self.L.mlpf_get_config(self.h, ctypes.byref(cfg)))
+        self.config = {n: getattr(cfg, n) for n, _ in _lib.MlpfConfig._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.mlpf_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_option(self, option: int, value: int):
+        check(self.L.mlpf_set_option(self.h, option, int(value)))
+
+    def get_option(self, option: int) -> int:
+        v = ctypes.c_int64()
+        check(self.L.mlpf_get_option(self.h, option, ctypes.byref(v)))
+        return v.value
+
+    @property
+    def last_launch_count(self) -> int:
+        return int(self.L.mlpf_last_launch_count(self.h))
+
+    def forward(self, x, cu_seqlens, max_n: int, precision="bf16", logits=None, reg=None,
+                cls=None, event_sums=None, want_cls=True, want_sums=True, stream=None):
+        """Batched forward over packed events (device tensors).
+
+        x: float32 [total, 42] CUDA tensor; cu_seqlens: int32 [n_events+1] CUDA
+        tensor.  Returns (logits [total,6], reg [total,5], cls [total] | None,
+        event_sums [n_events,3] float64 | None), asynchronous on `stream`
+        (default: torch's current stream).
+        """
+        import torch
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        total = x.shape[0]
+        n_events = cu_seqlens.shape[0] - 1
+        dev = x.device
+        if logits is None:
+            logits = torch.empty((total, 6), dtype=torch.float32, device=dev)
+        if reg is None:
+            reg = torch.empty((total, 5), dtype=torch.float32, device=dev)
+        if cls is None and want_cls:
+            cls = torch.empty((total,), dtype=torch.int32, device=dev)
+        if event_sums is None and want_sums:
+            event_sums = torch.empty((n_events, 3), dtype=torch.float64, device=dev)
+        if stream is None:
+            stream = torch.cuda.current_stream(dev).cuda_stream
+        check(self.L.mlpf_forward(self.h, prec, _ptr(x), _ptr(cu_seqlens), n_events, total,
+                                  int(max_n), _ptr(logits), _ptr(reg), _ptr(cls),
+                                  _ptr(event_sums), ctypes.c_void_p(stream)))
+        return logits, reg, cls, event_sums
+
+    def forward_host(self, x, cu_seqlens, max_n: int, precision="bf16", logits=None, reg=None,
+                     cls=None, event_sums=None, stream=None):
+        """Forward with host (CPU) tensors; copies in and out inside the call."""
+        import torch
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        total = x.shape[0]
+        n_events = cu_seqlens.shape[0] - 1
+        if logits is None:
+            logits = torch.empty((total, 6), dtype=torch.float32)
+        if reg is None:
+            reg = torch.empty((total, 5), dtype=torch.float32)
+        s = ctypes.c_void_p(stream if stream is not None else
+                            torch.cuda.current_stream(self.device).cuda_stream)
+        check(self.L.mlpf_forward_host(self.h, prec, _ptr(x), _ptr(cu_seqlens), n_events, total,
+                                       int(max_n), _ptr(logits), _ptr(reg), _ptr(cls),
+                                       _ptr(event_sums), s))
+        return logits, reg, cls, event_sums
+
+    def sync(self, stream=None):
+        """Wait for the stream and raise on a device-side timeout / non-finite output."""
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream(self.device).cuda_stream
+        check(self.L.mlpf_sync(self.h, ctypes.c_void_p(s)))

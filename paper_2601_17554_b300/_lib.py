@@ -1,0 +1,76 @@
+"""ctypes declarations of the C ABI in include/mlpf.h (argument marshalling only)."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmlpf.so")
+
+MLPF_OK, MLPF_E_INVALID, MLPF_E_FORMAT, MLPF_E_CUDA, MLPF_E_OOM, MLPF_E_TIMEOUT, \
+    MLPF_E_NONFINITE, MLPF_E_UNSUPPORTED = range(8)
+MLPF_FP32, MLPF_BF16, MLPF_FP8 = 0, 1, 2
+OPT_USE_GRAPHS, OPT_WAIT_LIMIT_NS, OPT_DEBUG_STALL, OPT_ATTN_CTAS_PER_SM, OPT_ATTN_KV_STAGES = 1, 2, 3, 4, 5
+
+# every symbol include/mlpf.h declares
+EXPORTS = ("mlpf_load_weights", "mlpf_free", "mlpf_get_config", "mlpf_forward",
+           "mlpf_forward_host", "mlpf_sync", "mlpf_set_option", "mlpf_get_option",
+           "mlpf_last_launch_count", "mlpf_last_error", "mlpf_abi_version")
+
+
+class MlpfConfig(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in
+                ("in_dim", "d", "heads", "ffn", "l_pid", "l_reg", "n_cls", "n_reg", "act")]
+
+
+_handle = None
+
+
+def load(build_if_missing: bool = True):
+    """Load libmlpf.so (building it with nvcc first if it is missing)."""
+    global _handle
+    if _handle is not None:
+        return _handle
+    if not os.path.exists(LIB_PATH):
+        if not build_if_missing:
+            raise RuntimeError(f"{LIB_PATH} is missing; run python -m paper_2601_17554_b300.build")
+        from .build import build
+        build()
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+    L.mlpf_load_weights.argtypes = [vp, sz, ctypes.c_int, ctypes.POINTER(vp)]
+    L.mlpf_load_weights.restype = ctypes.c_int
+    L.mlpf_free.argtypes = [vp]
+    L.mlpf_free.restype = None
+    L.mlpf_get_config.argtypes = [vp, ctypes.POINTER(MlpfConfig)]
+    L.mlpf_get_config.restype = ctypes.c_int
+    fwd = [vp, i32, vp, vp, i32, i32, i32, vp, vp, vp, vp, vp]
+    L.mlpf_forward.argtypes = fwd
+    L.mlpf_forward.restype = ctypes.c_int
+    L.mlpf_forward_host.argtypes = fwd
+    L.mlpf_forward_host.restype = ctypes.c_int
+    L.mlpf_sync.argtypes = [vp, vp]
+    L.mlpf_sync.restype = ctypes.c_int
+    L.mlpf_set_option.argtypes = [vp, i32, i64]
+    L.mlpf_set_option.restype = ctypes.c_int
+    L.mlpf_get_option.argtypes = [vp, i32, ctypes.POINTER(i64)]
+    L.mlpf_get_option.restype = ctypes.c_int
+    L.mlpf_last_launch_count.argtypes = [vp]
+    L.mlpf_last_launch_count.restype = i64
+    L.mlpf_last_error.argtypes = []
+    L.mlpf_last_error.restype = ctypes.c_char_p
+    L.mlpf_abi_version.argtypes = []
+    L.mlpf_abi_version.restype = i32
+    _handle = L
+    return L
+
+
+class MlpfError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"mlpf status {status}: {msg}")
+        self.status = status
+
+
+def check(status: int):
+    if status != MLPF_OK:
+        raise MlpfError(status, load().mlpf_last_error().decode(errors="replace"))

@@ -1,0 +1,517 @@
+// C ABI of the MLPF forward: weight-blob parsing and upload, workspace
+// management, argument validation, dispatch to the FP32 / tensor-core paths,
+// the CUDA-graph cache and the host-buffer entry point.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <tuple>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace mlpf {
+
+static thread_local std::string g_last_error;
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+bool GraphKey::operator<(const GraphKey& o) const {
+    return std::tie(prec, x, cu, lo, rg, cl, su, n_events, total, max_n) <
+           std::tie(o.prec, o.x, o.cu, o.lo, o.rg, o.cl, o.su, o.n_events, o.total, o.max_n);
+}
+
+// ------------------------------------------------------------ blob parsing
+static const char* REG_HEAD_NAMES[4] = {"pt", "eta", "phi", "e"};
+static const int REG_HEAD_WIDTH[4] = {1, 1, 2, 1};
+
+static std::vector<std::pair<std::string, std::vector<int>>> expected_tensors(const mlpf_config& c) {
+    std::vector<std::pair<std::string, std::vector<int>>> v;
+    const int d = c.d, f = c.ffn;
+    v.push_back({"emb.w1", {d, c.in_dim}});
+    v.push_back({"emb.b1", {d}});
+    v.push_back({"emb.w2", {d, d}});
+    v.push_back({"emb.b2", {d}});
+    auto stack = [&](const std::string& p0, int n) {
+        for (int l = 0; l < n; ++l) {
+            const std::string p = p0 + "." + std::to_string(l) + ".";
+            v.push_back({p + "ln1.g", {d}});
+            v.push_back({p + "ln1.b", {d}});
+            for (const char* q : {"q", "k", "v", "o"}) {
+                v.push_back({p + "w" + q, {d, d}});
+                v.push_back({p + "b" + q, {d}});
+            }
+            v.push_back({p + "ln2.g", {d}});
+            v.push_back({p + "ln2.b", {d}});
+            v.push_back({p + "ffn.w1", {f, d}});
+            v.push_back({p + "ffn.b1", {f}});
+            v.push_back({p + "ffn.w2", {d, f}});
+            v.push_back({p + "ffn.b2", {d}});
+        }
+        v.push_back({p0 + ".lnf.g", {d}});
+        v.push_back({p0 + ".lnf.b", {d}});
+    };
+    stack("pid", c.l_pid);
+    v.push_back({"remb.w1", {d, c.in_dim + d}});
+    v.push_back({"remb.b1", {d}});
+    v.push_back({"remb.w2", {d, d}});
+    v.push_back({"remb.b2", {d}});
+    stack("reg", c.l_reg);
+    v.push_back({"head.cls.w1", {d, d}});
+    v.push_back({"head.cls.b1", {d}});
+    v.push_back({"head.cls.w2", {c.n_cls, d}});
+    v.push_back({"head.cls.b2", {c.n_cls}});
+    for (int h = 0; h < 4; ++h) {
+        const std::string p = std::string("head.") + REG_HEAD_NAMES[h] + ".";
+        v.push_back({p + "w1", {d, d}});
+        v.push_back({p + "b1", {d}});
+        v.push_back({p + "w2", {REG_HEAD_WIDTH[h], d}});
+        v.push_back({p + "b2", {REG_HEAD_WIDTH[h]}});
+    }
+    return v;
+}
+
+static mlpf_status parse_blob(const uint8_t* p, size_t nbytes, Model& m) {
+    size_t off = 0;
+    auto need = [&](size_t k) { return off + k <= nbytes; };
+    if (!need(8 + 40)) { set_error("blob truncated: header"); return MLPF_E_FORMAT; }
+    if (std::memcmp(p, "MLPF", 4) != 0) { set_error("blob magic is not MLPF"); return MLPF_E_FORMAT; }
+    int32_t version;
+    std::memcpy(&version, p + 4, 4);
+    if (version != 1) { set_error("unsupported blob version " + std::to_string(version)); return MLPF_E_FORMAT; }
+    int32_t h[10];
+    std::memcpy(h, p + 8, 40);
+    off = 48;
+    mlpf_config c{h[0], h[1], h[2], h[3], h[4], h[5], h[6], h[7], h[8]};
+    const int n_tensors = h[9];
+    if (c.in_dim != 42 || c.n_cls != 6 || c.n_reg != 5 || c.d <= 0 || c.d > 256 || c.heads <= 0 ||
+        c.d % c.heads != 0 || (c.d / c.heads != 16 && c.d / c.heads != 32 && c.d / c.heads != 64) ||
+        c.ffn <= 0 || c.ffn > 4096 || c.l_pid < 1 || c.l_reg < 1 || c.l_pid > 16 ||
+        c.l_reg > 16 || (c.act != 0 && c.act != 1)) {
+        set_error("unsupported model configuration in blob header");
+        return MLPF_E_FORMAT;
+    }
+    m.cfg = c;
+    auto exp = expected_tensors(c);
+    if (n_tensors != (int)exp.size()) {
+        set_error("blob has " + std::to_string(n_tensors) + " tensors, expected " +
+                  std::to_string(exp.size()));
+        return MLPF_E_FORMAT;
+    }
+    for (int t = 0; t < n_tensors; ++t) {
+        if (!need(48 + 12)) { set_error("blob truncated: tensor record"); return MLPF_E_FORMAT; }
+        char name[49];
+        std::memcpy(name, p + off, 48);
+        name[48] = 0;
+        off += 48;
+        int32_t nd, s0, s1;
+        std::memcpy(&nd, p + off, 4);
+        std::memcpy(&s0, p + off + 4, 4);
+        std::memcpy(&s1, p + off + 8, 4);
+        off += 12;
+        const auto& e = exp[t];
+        if (e.first != name) { set_error(std::string("unexpected tensor ") + name + ", expected " + e.first); return MLPF_E_FORMAT; }
+        if (nd != (int)e.second.size() || s0 != e.second[0] || (nd == 2 ? s1 != e.second[1] : s1 != 1)) {
+            set_error(std::string("bad shape for tensor ") + name);
+            return MLPF_E_FORMAT;
+        }
+        const size_t cnt = (size_t)s0 * (nd == 2 ? s1 : 1);
+        if (!need(cnt * 4)) { set_error(std::string("blob truncated: data of ") + name); return MLPF_E_FORMAT; }
+        HostTensor ht;
+        ht.shape = e.second;
+        ht.data.resize(cnt);
+        std::memcpy(ht.data.data(), p + off, cnt * 4);
+        off += cnt * 4;
+        m.host[name] = std::move(ht);
+    }
+    if (off != nbytes) { set_error("trailing bytes after the last tensor"); return MLPF_E_FORMAT; }
+    return MLPF_OK;
+}
+
+static mlpf_status cuda_fail(cudaError_t e, const char* what) {
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? MLPF_E_OOM : MLPF_E_CUDA;
+}
+
+#define CK(call)                                           \
+    do {                                                   \
+        cudaError_t _e = (call);                           \
+        if (_e != cudaSuccess) return cuda_fail(_e, #call); \
+    } while (0)
+
+static mlpf_status upload_f32(Model& m) {
+    const mlpf_config& c = m.cfg;
+    size_t count = 0;
+    for (auto& kv : m.host) count += (kv.second.data.size() + 63) / 64 * 64;
+    const int d = c.d;
+    count += (size_t)(c.l_pid + c.l_reg) * ((3 * d * d + 63) / 64 * 64 + (3 * d + 63) / 64 * 64);
+    CK(cudaMalloc(&m.w.f32_base, count * sizeof(float)));
+    std::vector<float> img(count, 0.f);
+    size_t off = 0;
+    for (auto& kv : m.host) {
+        std::copy(kv.second.data.begin(), kv.second.data.end(), img.begin() + off);
+        m.w.f32[kv.first] = m.w.f32_base + off;
+        off += (kv.second.data.size() + 63) / 64 * 64;
+    }
+    auto cat = [&](const std::string& p, std::vector<float*>& wv, std::vector<float*>& bv) {
+        size_t wo = off;
+        for (const char* q : {"wq", "wk", "wv"}) {
+            auto& t = m.host.at(p + q).data;
+            std::copy(t.begin(), t.end(), img.begin() + off);
+            off += t.size();
+        }
+        off = wo + (3 * d * d + 63) / 64 * 64;
+        size_t bo = off;
+        for (const char* q : {"bq", "bk", "bv"}) {
+            auto& t = m.host.at(p + q).data;
+            std::copy(t.begin(), t.end(), img.begin() + off);
+            off += t.size();
+        }
+        off = bo + (3 * d + 63) / 64 * 64;
+        wv.push_back(m.w.f32_base + wo);
+        bv.push_back(m.w.f32_base + bo);
+    };
+    for (int l = 0; l < c.l_pid; ++l) cat("pid." + std::to_string(l) + ".", m.w.wqkv_pid, m.w.bqkv_pid);
+    for (int l = 0; l < c.l_reg; ++l) cat("reg." + std::to_string(l) + ".", m.w.wqkv_reg, m.w.bqkv_reg);
+    CK(cudaMemcpy(m.w.f32_base, img.data(), count * sizeof(float), cudaMemcpyHostToDevice));
+    return MLPF_OK;
+}
+
+// ---------------------------------------------------------------- workspace
+static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+static mlpf_status ensure_workspace(Model& m, int total, int n_events, bool tc) {
+    Workspace& w = m.ws;
+    const bool fits = (size_t)total <= w.cap_total && (size_t)n_events <= w.cap_events &&
+                      (!tc || w.tz != nullptr) && w.base != nullptr;
+    if (fits) return MLPF_OK;
+    // grow geometrically; keep both paths' buffers in one allocation
+    const size_t cap_t = std::max<size_t>({(size_t)total, w.cap_total * 5 / 4, 1024});
+    const size_t cap_e = std::max<size_t>({(size_t)n_events, w.cap_events * 5 / 4, 16});
+    const bool want_tc = tc || w.tz != nullptr;
+    if (w.base) {
+        cudaFree(w.base);
+        w = Workspace{};
+    }
+    for (auto& g : m.graphs) cudaGraphExecDestroy(g.second.first);
+    m.graphs.clear();
+    const mlpf_config& c = m.cfg;
+    const size_t d = c.d, F = c.ffn;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 1024); return o; };
+    const size_t o_z = take(cap_t * d * 4), o_zn = take(cap_t * d * 4), o_qkv = take(cap_t * 3 * d * 4),
+                 o_o = take(cap_t * d * 4), o_hid = take(cap_t * std::max(F, d) * 4),
+                 o_hp = take(cap_t * d * 4), o_hr = take(cap_t * d * 4), o_raw = take(cap_t * 5 * 4);
+    const int64_t tpad = (int64_t)align_up(cap_t + 64 * cap_e, 128);
+    size_t o_tz = 0, o_tq = 0, o_tk = 0, o_to = 0, o_tvt = 0, o_thp = 0, o_blk = 0, o_items = 0;
+    if (want_tc) {
+        o_tz = take(tpad * 64 * 4);
+        o_tq = take(tpad * 64 * 2);
+        o_tk = take(tpad * 64 * 2);
+        o_to = take(tpad * 64 * 2);
+        o_tvt = take(tpad * 64 * 2);
+        o_thp = take(tpad * 64 * 2);
+        o_blk = take((tpad / 64) * sizeof(int4));
+        o_items = take((tpad / 128 + cap_e + 1) * sizeof(int4));
+    }
+    const size_t o_cnt = take(64 * sizeof(int));
+    const size_t o_hx = take(cap_t * 42 * 4), o_hcu = take((cap_e + 1) * 4),
+                 o_hlo = take(cap_t * 6 * 4), o_hrg = take(cap_t * 5 * 4), o_hcl = take(cap_t * 4),
+                 o_hsu = take(cap_e * 3 * 8);
+    void* base = nullptr;
+    cudaError_t e = cudaMalloc(&base, off);
+    if (e != cudaSuccess) return cuda_fail(e, "workspace allocation");
+    char* b = (char*)base;
+    w.base = base;
+    w.bytes = off;
+    w.cap_total = cap_t;
+    w.cap_events = cap_e;
+    w.z = (float*)(b + o_z); w.zn = (float*)(b + o_zn); w.qkv = (float*)(b + o_qkv);
+    w.o = (float*)(b + o_o); w.hid = (float*)(b + o_hid); w.hpid = (float*)(b + o_hp);
+    w.hreg = (float*)(b + o_hr); w.raw = (float*)(b + o_raw);
+    w.counters = (int*)(b + o_cnt);
+    w.hx = (float*)(b + o_hx); w.hcu = (int32_t*)(b + o_hcu); w.hlogits = (float*)(b + o_hlo);
+    w.hreg_out = (float*)(b + o_hrg); w.hcls = (int32_t*)(b + o_hcl); w.hsums = (double*)(b + o_hsu);
+    if (want_tc) {
+        w.cap_tpad = tpad;
+        w.tz = (float*)(b + o_tz);
+        w.tq = (__nv_bfloat16*)(b + o_tq);
+        w.tk = (__nv_bfloat16*)(b + o_tk);
+        w.to = (__nv_bfloat16*)(b + o_to);
+        w.tvt = (__nv_bfloat16*)(b + o_tvt);
+        w.thp = (__nv_bfloat16*)(b + o_thp);
+        w.blk = (int4*)(b + o_blk);
+        w.items = (int4*)(b + o_items);
+        CK(cudaMemset(w.tvt, 0, tpad * 64 * 2));
+        if (!tc_make_maps(m)) return MLPF_E_CUDA;
+    }
+    CK(cudaMemset(w.counters, 0, 64 * sizeof(int)));
+    return MLPF_OK;
+}
+
+static mlpf_status validate(const Model* m, int32_t prec, const void* x, const void* cu,
+                            int32_t n_events, int32_t total, int32_t max_n, const void* logits,
+                            const void* reg) {
+    if (!m) { set_error("model is NULL"); return MLPF_E_INVALID; }
+    if (prec < 0 || prec > 2) { set_error("unknown precision " + std::to_string(prec)); return MLPF_E_INVALID; }
+    if (n_events < 0 || total < 0 || max_n < 0) { set_error("negative size"); return MLPF_E_INVALID; }
+    if (max_n > 65536) { set_error("max_n above 65536"); return MLPF_E_INVALID; }
+    if (total > 0 && max_n == 0) { set_error("max_n = 0 with total > 0"); return MLPF_E_INVALID; }
+    if (total > 0 && n_events == 0) { set_error("total > 0 with no events"); return MLPF_E_INVALID; }
+    if (total > 0 && (!x || !cu || !logits || !reg)) { set_error("NULL input or output pointer"); return MLPF_E_INVALID; }
+    if (n_events > 0 && !cu) { set_error("cu_seqlens is NULL"); return MLPF_E_INVALID; }
+    if (prec != MLPF_FP32 && !m->tc_supported) {
+        set_error("tensor-core path is built for d=64, 4 heads, FFN 256 models only");
+        return MLPF_E_UNSUPPORTED;
+    }
+    return MLPF_OK;
+}
+
+static mlpf_status launch_sequence(Model& m, int32_t prec, const float* x, const int32_t* cu,
+                                   int32_t n_events, int32_t total, int32_t max_n, float* logits,
+                                   float* reg, int32_t* cls, double* sums, cudaStream_t st,
+                                   int64_t& launches) {
+    int64_t n = 0;
+    if (total > 0) {
+        n = (prec == MLPF_FP32)
+                ? run_forward_f32(m, x, cu, n_events, total, max_n, logits, reg, st)
+                : run_forward_tc(m, prec, x, cu, n_events, total, max_n, logits, reg, st);
+        if (n < 0) {
+            set_error(std::string("kernel launch failed: ") + cudaGetErrorString(cudaGetLastError()));
+            return MLPF_E_CUDA;
+        }
+    } else if (sums && n_events > 0) {
+        cudaMemsetAsync(sums, 0, (size_t)n_events * 3 * sizeof(double), st);
+    }
+    if (total > 0) {
+        int64_t k = run_event_sums(m, cu, n_events, logits, reg, cls, sums, m.cfg.n_cls, st);
+        if (k < 0) { set_error("event-sum launch failed"); return MLPF_E_CUDA; }
+        n += k;
+    }
+    launches = n;
+    return MLPF_OK;
+}
+
+static mlpf_status forward_impl(Model& m, int32_t prec, const float* x, const int32_t* cu,
+                                int32_t n_events, int32_t total, int32_t max_n, float* logits,
+                                float* reg, int32_t* cls, double* sums, cudaStream_t st) {
+    CK(cudaSetDevice(m.device));
+    mlpf_status s = ensure_workspace(m, total, n_events, prec != MLPF_FP32);
+    if (s != MLPF_OK) return s;
+    if (total == 0) {
+        if (sums && n_events > 0) CK(cudaMemsetAsync(sums, 0, (size_t)n_events * 3 * sizeof(double), st));
+        m.last_launches = 0;
+        return MLPF_OK;
+    }
+    if (!m.use_graphs) {
+        int64_t n = 0;
+        s = launch_sequence(m, prec, x, cu, n_events, total, max_n, logits, reg, cls, sums, st, n);
+        m.last_launches = n;
+        return s;
+    }
+    GraphKey key{prec, x, cu, logits, reg, cls, sums, n_events, total, max_n};
+    auto it = m.graphs.find(key);
+    if (it == m.graphs.end()) {
+        if (m.graphs.size() >= 16) {
+            cudaGraphExecDestroy(m.graphs.begin()->second.first);
+            m.graphs.erase(m.graphs.begin());
+        }
+        if (!m.cap_stream) CK(cudaStreamCreateWithFlags(&m.cap_stream, cudaStreamNonBlocking));
+        CK(cudaStreamBeginCapture(m.cap_stream, cudaStreamCaptureModeThreadLocal));
+        int64_t n = 0;
+        mlpf_status ls = launch_sequence(m, prec, x, cu, n_events, total, max_n, logits, reg, cls,
+                                         sums, m.cap_stream, n);
+        cudaGraph_t g = nullptr;
+        cudaError_t ce = cudaStreamEndCapture(m.cap_stream, &g);
+        if (ls != MLPF_OK) { if (g) cudaGraphDestroy(g); return ls; }
+        if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
+        cudaGraphExec_t ex = nullptr;
+        ce = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        if (ce != cudaSuccess) return cuda_fail(ce, "cudaGraphInstantiate");
+        it = m.graphs.emplace(key, std::make_pair(ex, n)).first;
+    }
+    CK(cudaGraphLaunch(it->second.first, st));
+    m.last_launches = it->second.second;
+    return MLPF_OK;
+}
+
+}  // namespace mlpf
+
+using namespace mlpf;
+
+struct mlpf_model {
+    Model impl;
+};
+
+extern "C" {
+
+int32_t mlpf_abi_version(void) { return 100; }
+
+const char* mlpf_last_error(void) { return g_last_error.c_str(); }
+
+mlpf_status mlpf_load_weights(const void* blob, size_t nbytes, int device, mlpf_model** out) {
+    if (!blob || !out) { set_error("NULL blob or out pointer"); return MLPF_E_INVALID; }
+    *out = nullptr;
+    if (nbytes < 48) { set_error("blob smaller than its header"); return MLPF_E_INVALID; }
+    auto* mm = new (std::nothrow) mlpf_model();
+    if (!mm) { set_error("host allocation failed"); return MLPF_E_OOM; }
+    Model& m = mm->impl;
+    m.device = device;
+    // the blob is parsed on the host first, so format errors need no GPU
+    mlpf_status s = parse_blob((const uint8_t*)blob, nbytes, m);
+    if (s == MLPF_OK) {
+        int ndev = 0;
+        if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+            cudaGetLastError();
+            set_error("no such CUDA device " + std::to_string(device));
+            delete mm;
+            return MLPF_E_INVALID;
+        }
+    }
+    if (s == MLPF_OK && cudaSetDevice(device) != cudaSuccess) { set_error("cudaSetDevice failed"); s = MLPF_E_CUDA; }
+    if (s == MLPF_OK) {
+        cudaDeviceProp prop;
+        cudaGetDeviceProperties(&prop, device);
+        m.sm_count = prop.multiProcessorCount;
+        s = upload_f32(m);
+    }
+    if (s == MLPF_OK) {
+        cudaError_t e = cudaMalloc(&m.status, 64);
+        if (e == cudaSuccess) e = cudaMemset(m.status, 0, 64);
+        if (e != cudaSuccess) s = cuda_fail(e, "status word");
+    }
+    if (s == MLPF_OK) {
+        const mlpf_config& c = m.cfg;
+        cudaDeviceProp prop;
+        cudaGetDeviceProperties(&prop, device);
+        const bool arch_ok = prop.major == 10 && prop.minor == 3;
+        m.tc_supported = arch_ok && c.d == 64 && c.heads == 4 && c.ffn == 256;
+        if (m.tc_supported && !tc_prepare_weights(m)) s = MLPF_E_CUDA;
+    }
+    if (s != MLPF_OK) {
+        if (m.w.f32_base || m.status) mlpf_free(mm);
+        else delete mm;
+        return s;
+    }
+    *out = mm;
+    return MLPF_OK;
+}
+
+void mlpf_free(mlpf_model* mm) {
+    if (!mm) return;
+    Model& m = mm->impl;
+    cudaSetDevice(m.device);
+    for (auto& g : m.graphs) cudaGraphExecDestroy(g.second.first);
+    if (m.cap_stream) cudaStreamDestroy(m.cap_stream);
+    if (m.ws.base) cudaFree(m.ws.base);
+    if (m.w.f32_base) cudaFree(m.w.f32_base);
+    if (m.w.img_base) cudaFree(m.w.img_base);
+    if (m.w.img8_base) cudaFree(m.w.img8_base);
+    if (m.w.tc_f32_base) cudaFree(m.w.tc_f32_base);
+    if (m.status) cudaFree(m.status);
+    delete mm;
+}
+
+mlpf_status mlpf_get_config(const mlpf_model* m, mlpf_config* cfg) {
+    if (!m || !cfg) { set_error("NULL argument"); return MLPF_E_INVALID; }
+    *cfg = m->impl.cfg;
+    return MLPF_OK;
+}
+
+mlpf_status mlpf_forward(mlpf_model* mm, int32_t precision, const float* x,
+                         const int32_t* cu_seqlens, int32_t n_events, int32_t total,
+                         int32_t max_n, float* logits, float* reg, int32_t* cls,
+                         double* event_sums, void* stream) {
+    mlpf_status s = validate(mm ? &mm->impl : nullptr, precision, x, cu_seqlens, n_events, total,
+                             max_n, logits, reg);
+    if (s != MLPF_OK) return s;
+    return forward_impl(mm->impl, precision, x, cu_seqlens, n_events, total, max_n, logits, reg,
+                        cls, event_sums, (cudaStream_t)stream);
+}
+
+mlpf_status mlpf_sync(mlpf_model* mm, void* stream) {
+    if (!mm) { set_error("model is NULL"); return MLPF_E_INVALID; }
+    Model& m = mm->impl;
+    CK(cudaSetDevice(m.device));
+    unsigned st = 0;
+    CK(cudaMemcpyAsync(&st, m.status, sizeof(unsigned), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    CK(cudaMemsetAsync(m.status, 0, sizeof(unsigned), (cudaStream_t)stream));
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    if (st & (ST_TIMEOUT_ATTN | ST_TIMEOUT_GEMM)) {
+        set_error("a bounded device-side wait ran out (status " + std::to_string(st) + ")");
+        return MLPF_E_TIMEOUT;
+    }
+    if (st & ST_NONFINITE) { set_error("non-finite values in the outputs"); return MLPF_E_NONFINITE; }
+    return MLPF_OK;
+}
+
+mlpf_status mlpf_forward_host(mlpf_model* mm, int32_t precision, const float* x,
+                              const int32_t* cu_seqlens, int32_t n_events, int32_t total,
+                              int32_t max_n, float* logits, float* reg, int32_t* cls,
+                              double* event_sums, void* stream) {
+    mlpf_status s = validate(mm ? &mm->impl : nullptr, precision, x, cu_seqlens, n_events, total,
+                             max_n, logits, reg);
+    if (s != MLPF_OK) return s;
+    Model& m = mm->impl;
+    CK(cudaSetDevice(m.device));
+    s = ensure_workspace(m, total, n_events, precision != MLPF_FP32);
+    if (s != MLPF_OK) return s;
+    Workspace& w = m.ws;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (total > 0) CK(cudaMemcpyAsync(w.hx, x, (size_t)total * 42 * 4, cudaMemcpyHostToDevice, st));
+    if (n_events > 0) CK(cudaMemcpyAsync(w.hcu, cu_seqlens, (size_t)(n_events + 1) * 4, cudaMemcpyHostToDevice, st));
+    s = forward_impl(m, precision, w.hx, w.hcu, n_events, total, max_n, w.hlogits, w.hreg_out,
+                     cls ? w.hcls : nullptr, event_sums ? w.hsums : nullptr, st);
+    if (s != MLPF_OK) return s;
+    if (total > 0) {
+        CK(cudaMemcpyAsync(logits, w.hlogits, (size_t)total * 6 * 4, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(reg, w.hreg_out, (size_t)total * 5 * 4, cudaMemcpyDeviceToHost, st));
+        if (cls) CK(cudaMemcpyAsync(cls, w.hcls, (size_t)total * 4, cudaMemcpyDeviceToHost, st));
+    }
+    if (event_sums && n_events > 0)
+        CK(cudaMemcpyAsync(event_sums, w.hsums, (size_t)n_events * 3 * 8, cudaMemcpyDeviceToHost, st));
+    return mlpf_sync(mm, stream);
+}
+
+mlpf_status mlpf_set_option(mlpf_model* mm, int32_t option, int64_t value) {
+    if (!mm) { set_error("model is NULL"); return MLPF_E_INVALID; }
+    Model& m = mm->impl;
+    switch (option) {
+        case MLPF_OPT_USE_GRAPHS: m.use_graphs = value != 0; return MLPF_OK;
+        case MLPF_OPT_WAIT_LIMIT_NS:
+            if (value < 1000000 || value > 60000000000LL) { set_error("wait limit out of range"); return MLPF_E_INVALID; }
+            m.wait_limit_ns = value;
+            break;
+        case MLPF_OPT_DEBUG_STALL: m.debug_stall = value != 0; break;
+        case MLPF_OPT_ATTN_CTAS_PER_SM:
+            if (value < 1 || value > 1) { set_error("attention runs one CTA per SM in this build"); return MLPF_E_INVALID; }
+            m.attn_ctas_per_sm = (int)value;
+            break;
+        default: set_error("unknown or read-only option " + std::to_string(option)); return MLPF_E_INVALID;
+    }
+    // options baked into captured graphs: drop them
+    cudaSetDevice(m.device);
+    for (auto& g : m.graphs) cudaGraphExecDestroy(g.second.first);
+    m.graphs.clear();
+    return MLPF_OK;
+}
+
+mlpf_status mlpf_get_option(const mlpf_model* mm, int32_t option, int64_t* value) {
+    if (!mm || !value) { set_error("NULL argument"); return MLPF_E_INVALID; }
+    const Model& m = mm->impl;
+    switch (option) {
+        case MLPF_OPT_USE_GRAPHS: *value = m.use_graphs; return MLPF_OK;
+        case MLPF_OPT_WAIT_LIMIT_NS: *value = m.wait_limit_ns; return MLPF_OK;
+        case MLPF_OPT_DEBUG_STALL: *value = m.debug_stall; return MLPF_OK;
+        case MLPF_OPT_ATTN_CTAS_PER_SM: *value = m.attn_ctas_per_sm; return MLPF_OK;
+        case MLPF_OPT_ATTN_KV_STAGES: *value = 4; return MLPF_OK;
+        default: set_error("unknown option " + std::to_string(option)); return MLPF_E_INVALID;
+    }
+}
+
+int64_t mlpf_last_launch_count(const mlpf_model* m) { return m ? m->impl.last_launches : -1; }
+
+}  // extern "C"

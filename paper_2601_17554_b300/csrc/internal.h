@@ -1,0 +1,111 @@
+// Host-side internals shared by the library's translation units.
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/mlpf.h"
+
+namespace mlpf {
+
+void set_error(const std::string& msg);
+
+// status bits written to the model's device status word
+enum : unsigned {
+    ST_TIMEOUT_ATTN = 1u,
+    ST_TIMEOUT_GEMM = 2u,
+    ST_NONFINITE = 4u,
+};
+
+
+// ---------------------------------------------------------------- weights
+struct HostTensor {
+    std::vector<int> shape;
+    std::vector<float> data;
+};
+
+// fp32 device copies of every tensor (plain path) and prepared tensor-core images.
+struct DeviceWeights {
+    std::map<std::string, float*> f32;   // name -> device pointer (shared allocation)
+    float* f32_base = nullptr;
+    // FP32 path: concatenated QKV per layer, [3d, d] and [3d]
+    std::vector<float*> wqkv_pid, bqkv_pid, wqkv_reg, bqkv_reg;
+    // tensor-core path (d = 64 model only): bf16 128B-swizzled weight images
+    uint8_t* img_base = nullptr;
+    std::map<std::string, uint8_t*> img;  // name -> device pointer of the image
+    std::map<std::string, uint32_t> img_bytes;
+    float* tc_f32_base = nullptr;         // fused bias vectors for the tensor-core kernels
+    std::map<std::string, float*> tcv;
+    // FP8 E4M3 images (same layout, one byte per element) and per-tensor scales
+    uint8_t* img8_base = nullptr;
+    std::map<std::string, uint8_t*> img8;
+    std::map<std::string, uint32_t> img8_bytes;
+    std::map<std::string, float> w_scale;  // per-tensor weight scale (amax / 448)
+};
+
+// ---------------------------------------------------------------- workspace
+struct Workspace {
+    size_t cap_total = 0, cap_events = 0;
+    int64_t cap_tpad = 0;   // padded-row capacity (multiple of 128)
+    void* base = nullptr;
+    size_t bytes = 0;
+    // plain FP32 path
+    float *z = nullptr, *zn = nullptr, *qkv = nullptr, *o = nullptr, *hid = nullptr;
+    float *hpid = nullptr, *hreg = nullptr, *raw = nullptr;
+    // tensor-core path (padded layout, rows of event e start at a multiple of 64)
+    float* tz = nullptr;                 // [tpad, 64] residual stream fp32
+    __nv_bfloat16 *tq = nullptr, *tk = nullptr, *to = nullptr, *tvt = nullptr, *thp = nullptr;
+    int4* blk = nullptr;                 // per 64-row block: event, packed row, n valid
+    int4* items = nullptr;               // attention work items
+    int* counters = nullptr;             // [0]=n_items [1]=tpad rows [2..3]=attn tickets
+    CUtensorMap map_q, map_k, map_o, map_vt, map_hp;
+    // host-buffer entry point: device staging
+    float *hx = nullptr, *hlogits = nullptr, *hreg_out = nullptr;
+    int32_t *hcu = nullptr, *hcls = nullptr;
+    double* hsums = nullptr;
+};
+
+struct GraphKey {
+    int prec;
+    const void *x, *cu, *lo, *rg, *cl, *su;
+    int32_t n_events, total, max_n;
+    bool operator<(const GraphKey& o) const;
+};
+
+struct Model {
+    int device = 0;
+    mlpf_config cfg{};
+    std::map<std::string, HostTensor> host;
+    DeviceWeights w;
+    Workspace ws;
+    unsigned* status = nullptr;  // device status word
+    int sm_count = 148;
+    bool tc_supported = false;   // tensor-core path built for this configuration
+    // options
+    bool use_graphs = true;
+    int64_t wait_limit_ns = 2000000000LL;
+    bool debug_stall = false;
+    int attn_ctas_per_sm = 1;
+    int64_t last_launches = 0;
+    cudaStream_t cap_stream = nullptr;
+    std::map<GraphKey, std::pair<cudaGraphExec_t, int64_t>> graphs;
+};
+
+// launch sequences (return number of kernels launched, or -1 on launch error)
+int64_t run_forward_f32(Model& m, const float* x, const int32_t* cu, int n_events, int total,
+                        int max_n, float* logits, float* reg, cudaStream_t st);
+int64_t run_forward_tc(Model& m, int prec, const float* x, const int32_t* cu, int n_events,
+                       int total, int max_n, float* logits, float* reg, cudaStream_t st);
+int64_t run_event_sums(Model& m, const int32_t* cu, int n_events, const float* logits,
+                       const float* reg, int32_t* cls, double* sums, int n_cls,
+                       cudaStream_t st);
+
+// tensor-core path preparation (weights images, tensor maps)
+bool tc_prepare_weights(Model& m);
+bool tc_make_maps(Model& m);
+
+}  // namespace mlpf

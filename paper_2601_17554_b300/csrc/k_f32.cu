@@ -1,0 +1,348 @@
+// Plain FP32 path: SIMT FFMA kernels over the packed layout (no tensor cores,
+// no TF32).  It is the precision reference on the GPU and the "plain" baseline
+// the tensor-core path is measured against.  Also holds the per-event missing-pT
+// sum kernel shared by every precision.
+#include <cuda_runtime.h>
+#include <cmath>
+#include <cstdint>
+
+#include "internal.h"
+#include "ptx.cuh"
+
+namespace mlpf {
+
+namespace {
+
+constexpr int LIN_BM = 64, LIN_BN = 64, LIN_BK = 16;
+
+__device__ __forceinline__ float act_fn(float v, int act) {
+    if (act == 1) return fmaxf(v, 0.0f);
+    if (act == 0) return 0.5f * v * (1.0f + erff(v * 0.70710678118654752f));
+    return v;
+}
+
+// Y[r, n] = act(sum_k X[r, k] W[n, k] + b[n]) (+ R[r, n]); X = [X1 | X2] by columns.
+// act: -1 none, 0 GELU, 1 ReLU.  R may alias Y (each element read then written
+// by the same thread).
+__global__ void __launch_bounds__(256) k_linear(const float* __restrict__ X1, int ld1, int K1,
+                                                const float* __restrict__ X2, int ld2, int K2,
+                                                const float* __restrict__ W,
+                                                const float* __restrict__ b, const float* R,
+                                                int ldr, float* Y, int ldy, int T, int N,
+                                                int act) {
+    __shared__ float As[LIN_BK][LIN_BM + 4];
+    __shared__ float Ws[LIN_BK][LIN_BN + 4];
+    const int K = K1 + K2;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int r0 = blockIdx.y * LIN_BM, n0 = blockIdx.x * LIN_BN;
+    float acc[4][4] = {};
+    for (int k0 = 0; k0 < K; k0 += LIN_BK) {
+        for (int i = threadIdx.x; i < LIN_BM * LIN_BK; i += 256) {
+            const int rr = i / LIN_BK, kk = i % LIN_BK;
+            const int r = r0 + rr, k = k0 + kk;
+            float v = 0.f;
+            if (r < T && k < K) v = (k < K1) ? X1[(size_t)r * ld1 + k] : X2[(size_t)r * ld2 + (k - K1)];
+            As[kk][rr] = v;
+            const int n = n0 + rr;
+            Ws[kk][rr] = (n < N && k < K) ? W[(size_t)n * K + k] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < LIN_BK; ++kk) {
+            float a[4], w[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) w[j] = Ws[kk][tx * 4 + j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], w[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int r = r0 + ty * 4 + i;
+        if (r >= T) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int n = n0 + tx * 4 + j;
+            if (n >= N) continue;
+            float v = act_fn(acc[i][j] + b[n], act);
+            if (R) v += R[(size_t)r * ldr + n];
+            Y[(size_t)r * ldy + n] = v;
+        }
+    }
+}
+
+// LayerNorm over d columns, one warp per row (two-pass moments in FP32).
+__global__ void k_layernorm(const float* __restrict__ X, const float* __restrict__ g,
+                            const float* __restrict__ b, float* __restrict__ Y, int T, int d) {
+    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (row >= T) return;
+    const float* x = X + (size_t)row * d;
+    float v[8];
+    float s = 0.f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int c = lane + 32 * i;
+        v[i] = (c < d) ? x[c] : 0.f;
+        s += v[i];
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    const float mu = s / d;
+    float q = 0.f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int c = lane + 32 * i;
+        const float t = (c < d) ? v[i] - mu : 0.f;
+        q += t * t;
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+    const float rs = rsqrtf(q / d + 1e-5f);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int c = lane + 32 * i;
+        if (c < d) Y[(size_t)row * d + c] = (v[i] - mu) * rs * g[c] + b[c];
+    }
+}
+
+// Self-attention within each event; one thread per query row, 64 keys per
+// shared-memory tile, FP32 online softmax (exact expf).  qkv rows are
+// [q | k | v] with head h in columns h*DH .. h*DH+DH-1 of each part.
+template <int DH>
+__global__ void __launch_bounds__(64) k_attention(const float* __restrict__ qkv,
+                                                  float* __restrict__ out,
+                                                  const int32_t* __restrict__ cu, int d,
+                                                  float scale) {
+    __shared__ float Ks[64][DH + 1];
+    __shared__ float Vs[64][DH + 1];
+    const int e = blockIdx.z, h = blockIdx.y;
+    const int start = cu[e], n = cu[e + 1] - start;
+    if (blockIdx.x * 64 >= n) return;
+    const int qi = blockIdx.x * 64 + threadIdx.x;
+    const bool active = qi < n;
+    const int ld = 3 * d;
+    float q[DH], acc[DH];
+    float m = -INFINITY, l = 0.f;
+#pragma unroll
+    for (int c = 0; c < DH; ++c) {
+        q[c] = active ? qkv[(size_t)(start + qi) * ld + h * DH + c] * scale : 0.f;
+        acc[c] = 0.f;
+    }
+    for (int kb = 0; kb < n; kb += 64) {
+        const int kj = kb + threadIdx.x;
+        if (kj < n) {
+            const float* kr = qkv + (size_t)(start + kj) * ld + d + h * DH;
+            const float* vr = qkv + (size_t)(start + kj) * ld + 2 * d + h * DH;
+#pragma unroll
+            for (int c = 0; c < DH; ++c) {
+                Ks[threadIdx.x][c] = kr[c];
+                Vs[threadIdx.x][c] = vr[c];
+            }
+        }
+        __syncthreads();
+        const int cnt = min(64, n - kb);
+        if (active) {
+            float s[64];
+            float mx = m;
+#pragma unroll
+            for (int j = 0; j < 64; ++j) {
+                if (j < cnt) {
+                    float t = 0.f;
+#pragma unroll
+                    for (int c = 0; c < DH; ++c) t = fmaf(q[c], Ks[j][c], t);
+                    s[j] = t;
+                    mx = fmaxf(mx, t);
+                }
+            }
+            const float alpha = expf(m - mx);
+            l *= alpha;
+#pragma unroll
+            for (int c = 0; c < DH; ++c) acc[c] *= alpha;
+#pragma unroll
+            for (int j = 0; j < 64; ++j) {
+                if (j < cnt) {
+                    const float p = expf(s[j] - mx);
+                    l += p;
+#pragma unroll
+                    for (int c = 0; c < DH; ++c) acc[c] = fmaf(p, Vs[j][c], acc[c]);
+                }
+            }
+            m = mx;
+        }
+        __syncthreads();
+    }
+    if (active) {
+        const float inv = 1.0f / l;
+#pragma unroll
+        for (int c = 0; c < DH; ++c) out[(size_t)(start + qi) * d + h * DH + c] = acc[c] * inv;
+    }
+}
+
+// reg[r] = (pT_elem*exp(pT'), eta, sin, cos, E_elem*exp(E')), log pT_elem = x[r,8].
+__global__ void k_decode(const float* __restrict__ x, const float* __restrict__ raw,
+                         float* __restrict__ reg, int T) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= T) return;
+    const float* a = raw + (size_t)r * 5;
+    float* o = reg + (size_t)r * 5;
+    o[0] = expf(x[(size_t)r * 42 + 8] + a[0]);
+    o[1] = a[1];
+    o[2] = a[2];
+    o[3] = a[3];
+    o[4] = expf(x[(size_t)r * 42 + 9] + a[4]);
+}
+
+// One warp per event: class = argmax (lowest index on ties); FP64 sums of
+// -px, -py and pT over elements with class != 0, lanes stride over the rows
+// and a fixed xor-butterfly combines them (deterministic).
+__global__ void k_event_sums(const int32_t* __restrict__ cu, int n_events,
+                             const float* __restrict__ logits, const float* __restrict__ reg,
+                             int32_t* __restrict__ cls_out, double* __restrict__ sums, int n_cls,
+                             unsigned* status) {
+    const int e = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (e >= n_events) return;
+    const int s = cu[e], t = cu[e + 1];
+    double px = 0.0, py = 0.0, pt = 0.0;
+    bool finite = true;
+    for (int r = s + lane; r < t; r += 32) {
+        const float* lo = logits + (size_t)r * n_cls;
+        int best = 0;
+        float bv = lo[0];
+        finite &= isfinite(bv);
+        for (int c = 1; c < n_cls; ++c) {
+            const float v = lo[c];
+            finite &= isfinite(v);
+            if (v > bv) { bv = v; best = c; }
+        }
+        const float* rg = reg + (size_t)r * 5;
+#pragma unroll
+        for (int c = 0; c < 5; ++c) finite &= isfinite(rg[c]);
+        if (cls_out) cls_out[r] = best;
+        if (best != 0) {
+            const double p = rg[0], sn = rg[2], cs = rg[3];
+            const double rr = sqrt(sn * sn + cs * cs);
+            if (rr > 0.0) {
+                px += p * (cs / rr);
+                py += p * (sn / rr);
+            }
+            pt += p;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        px += __shfl_xor_sync(0xffffffffu, px, o);
+        py += __shfl_xor_sync(0xffffffffu, py, o);
+        pt += __shfl_xor_sync(0xffffffffu, pt, o);
+    }
+    if (!__all_sync(0xffffffffu, finite) && lane == 0) atomicOr(status, ST_NONFINITE);
+    if (lane == 0 && sums) {
+        sums[(size_t)e * 3 + 0] = -px;
+        sums[(size_t)e * 3 + 1] = -py;
+        sums[(size_t)e * 3 + 2] = pt;
+    }
+}
+
+inline unsigned cdiv(long a, long b) { return (unsigned)((a + b - 1) / b); }
+
+}  // namespace
+
+static void linear(const float* X1, int ld1, int K1, const float* X2, int ld2, int K2,
+                   const float* W, const float* b, const float* R, int ldr, float* Y, int ldy,
+                   int T, int N, int act, cudaStream_t st, int64_t& n) {
+    dim3 grid(cdiv(N, LIN_BN), cdiv(T, LIN_BM));
+    k_linear<<<grid, 256, 0, st>>>(X1, ld1, K1, X2, ld2, K2, W, b, R, ldr, Y, ldy, T, N, act);
+    ++n;
+}
+
+static void layernorm(const float* X, const float* g, const float* b, float* Y, int T, int d,
+                      cudaStream_t st, int64_t& n) {
+    k_layernorm<<<cdiv(T, 8), 256, 0, st>>>(X, g, b, Y, T, d);
+    ++n;
+}
+
+int64_t run_forward_f32(Model& m, const float* x, const int32_t* cu, int n_events, int total,
+                        int max_n, float* logits, float* reg, cudaStream_t st) {
+    const mlpf_config& c = m.cfg;
+    const int T = total, d = c.d, F = c.ffn, dh = d / c.heads, act = c.act;
+    Workspace& w = m.ws;
+    auto W = [&](const std::string& s) { return m.w.f32.at(s); };
+    int64_t n = 0;
+    const float scale = 1.0f / sqrtf((float)dh);
+
+    auto stack = [&](const char* prefix, int layers, std::vector<float*>& wqkv,
+                     std::vector<float*>& bqkv, float* out) {
+        for (int l = 0; l < layers; ++l) {
+            const std::string p = std::string(prefix) + "." + std::to_string(l) + ".";
+            layernorm(w.z, W(p + "ln1.g"), W(p + "ln1.b"), w.zn, T, d, st, n);
+            linear(w.zn, d, d, nullptr, 0, 0, wqkv[l], bqkv[l], nullptr, 0, w.qkv, 3 * d, T, 3 * d,
+                   -1, st, n);
+            dim3 grid(cdiv(max_n, 64), c.heads, n_events);
+            if (dh == 16)
+                k_attention<16><<<grid, 64, 0, st>>>(w.qkv, w.o, cu, d, scale);
+            else if (dh == 32)
+                k_attention<32><<<grid, 64, 0, st>>>(w.qkv, w.o, cu, d, scale);
+            else
+                k_attention<64><<<grid, 64, 0, st>>>(w.qkv, w.o, cu, d, scale);
+            ++n;
+            linear(w.o, d, d, nullptr, 0, 0, W(p + "wo"), W(p + "bo"), w.z, d, w.z, d, T, d, -1, st,
+                   n);
+            layernorm(w.z, W(p + "ln2.g"), W(p + "ln2.b"), w.zn, T, d, st, n);
+            linear(w.zn, d, d, nullptr, 0, 0, W(p + "ffn.w1"), W(p + "ffn.b1"), nullptr, 0, w.hid, F,
+                   T, F, act, st, n);
+            linear(w.hid, F, F, nullptr, 0, 0, W(p + "ffn.w2"), W(p + "ffn.b2"), w.z, d, w.z, d, T,
+                   d, -1, st, n);
+        }
+        layernorm(w.z, W(std::string(prefix) + ".lnf.g"), W(std::string(prefix) + ".lnf.b"), out,
+                  T, d, st, n);
+    };
+
+    linear(x, 42, 42, nullptr, 0, 0, W("emb.w1"), W("emb.b1"), nullptr, 0, w.hid, d, T, d, act, st,
+           n);
+    linear(w.hid, d, d, nullptr, 0, 0, W("emb.w2"), W("emb.b2"), nullptr, 0, w.z, d, T, d, -1, st,
+           n);
+    stack("pid", c.l_pid, m.w.wqkv_pid, m.w.bqkv_pid, w.hpid);
+    linear(x, 42, 42, w.hpid, d, d, W("remb.w1"), W("remb.b1"), nullptr, 0, w.hid, d, T, d, act, st,
+           n);
+    linear(w.hid, d, d, nullptr, 0, 0, W("remb.w2"), W("remb.b2"), nullptr, 0, w.z, d, T, d, -1, st,
+           n);
+    stack("reg", c.l_reg, m.w.wqkv_reg, m.w.bqkv_reg, w.hreg);
+    // heads
+    linear(w.hpid, d, d, nullptr, 0, 0, W("head.cls.w1"), W("head.cls.b1"), nullptr, 0, w.hid, d,
+           T, d, act, st, n);
+    linear(w.hid, d, d, nullptr, 0, 0, W("head.cls.w2"), W("head.cls.b2"), nullptr, 0, logits,
+           c.n_cls, T, c.n_cls, -1, st, n);
+    const char* names[4] = {"pt", "eta", "phi", "e"};
+    const int widths[4] = {1, 1, 2, 1};
+    int off = 0;
+    for (int h = 0; h < 4; ++h) {
+        const std::string p = std::string("head.") + names[h] + ".";
+        linear(w.hreg, d, d, nullptr, 0, 0, W(p + "w1"), W(p + "b1"), nullptr, 0, w.hid, d, T, d,
+               act, st, n);
+        linear(w.hid, d, d, nullptr, 0, 0, W(p + "w2"), W(p + "b2"), nullptr, 0, w.raw + off, 5, T,
+               widths[h], -1, st, n);
+        off += widths[h];
+    }
+    k_decode<<<cdiv(T, 256), 256, 0, st>>>(x, w.raw, reg, T);
+    ++n;
+    if (cudaPeekAtLastError() != cudaSuccess) return -1;
+    return n;
+}
+
+int64_t run_event_sums(Model& m, const int32_t* cu, int n_events, const float* logits,
+                       const float* reg, int32_t* cls, double* sums, int n_cls,
+                       cudaStream_t st) {
+    if (n_events <= 0 || (!cls && !sums)) return 0;
+    k_event_sums<<<cdiv(n_events, 8), 256, 0, st>>>(cu, n_events, logits, reg, cls, sums, n_cls,
+                                                     m.status);
+    if (cudaPeekAtLastError() != cudaSuccess) return -1;
+    return 1;
+}
+
+}  // namespace mlpf

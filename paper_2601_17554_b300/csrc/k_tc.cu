@@ -1,0 +1,1190 @@
+// Tensor-core path of the MLPF forward (model width 64, 4 heads of 16, FFN 256):
+//
+//   k_schedule      one CTA: padded layout (each event starts at a multiple of 64
+//                   rows), per-64-row block table, attention work list sorted by
+//                   event size (longest first)
+//   k_embed_qkv     per 128-row tile: element embedding FFN (Sec. 5.3) [or the
+//                   regression-stack input FFN over concat(x, h_pid)], residual
+//                   stream out, pre-LN, fused Q/K/V projection
+//   k_attention     persistent varlen self-attention (Sec. 5.3, Eq. 4) with
+//                   tcgen05 QK^T and PV, FP32 online softmax, one warpgroup per head
+//   k_post          per 128-row tile: out-projection + residual, LN, FFN up, GELU,
+//                   FFN down + residual, then either the next block's LN+QKV, the
+//                   end of the PID stack (final LN, class head) or the end of the
+//                   regression stack (final LN, four regression heads, decode)
+//
+// GEMM operands are BF16 in 128-byte-swizzled shared-memory tiles (TMA or
+// per-thread swizzled stores), accumulators FP32 in TMEM; thread t of a CTA owns
+// row t of each 128-row tile, so LayerNorm moments and softmax statistics are
+// per-thread FP32 sums with no cross-thread reduction.
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "ptx.cuh"
+
+namespace mlpf {
+
+namespace {
+
+constexpr int D = 64;            // model width
+constexpr int NH = 4;            // heads
+constexpr int ROWS = 128;        // rows per tile (UMMA M)
+constexpr int ATOM = ROWS * 128; // bytes of a [128 x 64] bf16 swizzled atom column
+constexpr float LN_EPS = 1e-5f;
+
+MLPF_DEV uint8_t* align1024(uint8_t* p) {
+    return (uint8_t*)(((uintptr_t)p + 1023) & ~(uintptr_t)1023);
+}
+
+MLPF_DEV float gelu_f(float v) { return 0.5f * v * (1.0f + erff(v * 0.70710678118654752f)); }
+MLPF_DEV float act_f(float v, int act) { return act == 1 ? fmaxf(v, 0.f) : gelu_f(v); }
+
+// Issue a [128 x K] x [N x K]^T GEMM from swizzled smem tiles into TMEM columns.
+// a_ncols_atoms: K/64.  b tile: N rows per atom column.
+MLPF_DEV void issue_gemm(uint32_t d_tmem, const uint8_t* a, const uint8_t* b, int N, int katoms) {
+    const uint32_t idesc = idesc_f16(128, N, 1);
+    const uint32_t a0 = smem_u32(a), b0 = smem_u32(b);
+    for (int kc = 0; kc < katoms * 4; ++kc) {
+        const uint32_t ao = a0 + (kc >> 2) * ATOM + (kc & 3) * 32;
+        const uint32_t bo = b0 + (kc >> 2) * (N * 128) + (kc & 3) * 32;
+        mma_f16(d_tmem, sdesc_sw128(ao), sdesc_sw128(bo), idesc, kc > 0 ? 1u : 0u);
+    }
+}
+
+// 64 consecutive TMEM columns of this thread's row.
+MLPF_DEV void ld_row64(uint32_t taddr, float* v) {
+    tmem_ld32(taddr, v);
+    tmem_ld32(taddr + 32, v + 32);
+    tmem_wait_ld();
+}
+
+// Store 64 floats of row r as bf16 into atom column `tile` (swizzled).
+MLPF_DEV void st_row_bf16(uint8_t* tile, int r, const float* v) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        uint4 u;
+        u.x = pack_bf16x2(v[8 * c + 0], v[8 * c + 1]);
+        u.y = pack_bf16x2(v[8 * c + 2], v[8 * c + 3]);
+        u.z = pack_bf16x2(v[8 * c + 4], v[8 * c + 5]);
+        u.w = pack_bf16x2(v[8 * c + 6], v[8 * c + 7]);
+        *(uint4*)(tile + sw128_off(r, c)) = u;
+    }
+}
+
+MLPF_DEV void st_global_bf16_row64(__nv_bfloat16* dst, const float* v) {
+    uint4* d4 = (uint4*)dst;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        uint4 u;
+        u.x = pack_bf16x2(v[8 * c + 0], v[8 * c + 1]);
+        u.y = pack_bf16x2(v[8 * c + 2], v[8 * c + 3]);
+        u.z = pack_bf16x2(v[8 * c + 4], v[8 * c + 5]);
+        u.w = pack_bf16x2(v[8 * c + 6], v[8 * c + 7]);
+        d4[c] = u;
+    }
+}
+
+// In-place LayerNorm of a 64-vector (two-pass FP32 moments, biased variance).
+MLPF_DEV void layernorm64(const float* z, float* out, const float* g, const float* b) {
+    float s = 0.f;
+#pragma unroll
+    for (int i = 0; i < D; ++i) s += z[i];
+    const float mu = s * (1.0f / D);
+    float q = 0.f;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        const float t = z[i] - mu;
+        q = fmaf(t, t, q);
+    }
+    const float rs = rsqrtf(q * (1.0f / D) + LN_EPS);
+#pragma unroll
+    for (int i = 0; i < D; ++i) out[i] = (z[i] - mu) * rs * __ldg(g + i) + __ldg(b + i);
+}
+
+// Load this row's 42 input features, convert to bf16 and store them (zero
+// padded to 64 columns) into the swizzled atom column.
+MLPF_DEV void load_x_row(uint8_t* tile, int r, const float* x, bool valid, int prow) {
+    float v[64];
+#pragma unroll
+    for (int i = 0; i < 64; ++i) v[i] = 0.f;
+    if (valid) {
+        const float2* src = (const float2*)(x + (size_t)prow * 42);
+#pragma unroll
+        for (int i = 0; i < 21; ++i) {
+            const float2 t = __ldg(src + i);
+            v[2 * i] = t.x;
+            v[2 * i + 1] = t.y;
+        }
+    }
+    st_row_bf16(tile, r, v);
+}
+
+struct RowInfo {
+    bool valid;
+    int prow;
+};
+MLPF_DEV RowInfo row_info(const int4* blk, int nblk, int p) {
+    const int b = p >> 6;
+    RowInfo ri{false, 0};
+    if (b < nblk) {
+        const int4 e = blk[b];
+        ri.valid = (p & 63) < e.z;
+        ri.prow = e.y + (p & 63);
+    }
+    return ri;
+}
+
+// Q, K rows and transposed V (zero for padding rows) from the QKV accumulator.
+MLPF_DEV void store_qkv(uint32_t tacc, const float* bqkv, int p, bool valid, __nv_bfloat16* q,
+                        __nv_bfloat16* k, __nv_bfloat16* vt, long ldvt) {
+    float v[64];
+    ld_row64(tacc, v);
+#pragma unroll
+    for (int i = 0; i < 64; ++i) v[i] += __ldg(bqkv + i);
+    st_global_bf16_row64(q + (size_t)p * D, v);
+    ld_row64(tacc + 64, v);
+#pragma unroll
+    for (int i = 0; i < 64; ++i) v[i] += __ldg(bqkv + 64 + i);
+    st_global_bf16_row64(k + (size_t)p * D, v);
+    ld_row64(tacc + 128, v);
+#pragma unroll
+    for (int i = 0; i < 64; ++i) {
+        const float t = valid ? v[i] + __ldg(bqkv + 128 + i) : 0.f;
+        vt[(size_t)i * ldvt + p] = __float2bfloat16_rn(t);
+    }
+}
+
+// ------------------------------------------------------------------ scheduler
+// cu: [n_events+1].  blk[b] = {event, packed row of the block's first element,
+// valid rows in the block, 0}.  items[i] = {padded row of the event's first
+// element, query tile, N_e, event}, ordered by N_e descending.
+// counters: [0] items, [1] padded rows, [2..33] attention tickets.
+// Event sizes are clamped to [0, 65536] and every write is bounded by the
+// workspace capacities, so offsets that break the contract cannot write out of
+// bounds.
+__global__ void __launch_bounds__(1024) k_schedule(const int32_t* __restrict__ cu, int n_events,
+                                                   int4* __restrict__ blk,
+                                                   int4* __restrict__ items,
+                                                   int* __restrict__ counters, int cap_blocks,
+                                                   int cap_items) {
+    constexpr int NB = 1025;  // buckets by key-tile count (max_n <= 65536)
+    __shared__ int hist[NB];
+    __shared__ int wsum[32];
+    __shared__ int carry;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    for (int i = tid; i < NB; i += 1024) hist[i] = 0;
+    if (tid == 0) carry = 0;
+    __syncthreads();
+    for (int e = tid; e < n_events; e += 1024) {
+        const int n = min(max(cu[e + 1] - cu[e], 0), 65536);
+        if (n > 0) atomicAdd(&hist[(n + 63) >> 6], (n + 127) >> 7);
+    }
+    __syncthreads();
+    if (tid == 0) {  // exclusive offsets, larger events first
+        int acc = 0;
+        for (int b = NB - 1; b >= 0; --b) {
+            const int c = hist[b];
+            hist[b] = acc;
+            acc += c;
+        }
+        counters[0] = acc;
+    }
+    __syncthreads();
+    for (int base = 0; base < n_events; base += 1024) {
+        const int e = base + tid;
+        const int n = e < n_events ? min(max(cu[e + 1] - cu[e], 0), 65536) : 0;
+        const int nb = (n + 63) >> 6;
+        int incl = nb;  // block-wide inclusive scan
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) wsum[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            int w = wsum[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += t;
+            }
+            wsum[lane] = w;
+        }
+        __syncthreads();
+        const int start = carry + incl - nb + (wid > 0 ? wsum[wid - 1] : 0);
+        if (n > 0) {
+            const int c0 = cu[e];
+            for (int b = 0; b < nb && start + b < cap_blocks; ++b)
+                blk[start + b] = make_int4(e, c0 + 64 * b, min(64, n - 64 * b), 0);
+            const int nq = (n + 127) >> 7;
+            const int pos = atomicAdd(&hist[nb], nq);
+            // an event that does not fit the padded capacity gets no work
+            const bool fits = start + nb <= cap_blocks;
+            for (int qt = 0; qt < nq && pos + qt < cap_items; ++qt)
+                items[pos + qt] = fits ? make_int4(start * 64, qt, n, e) : make_int4(0, 0, 0, e);
+        }
+        __syncthreads();
+        if (tid == 1023) carry = start + nb;
+        __syncthreads();
+    }
+    if (tid == 0) {
+        counters[1] = min(carry, cap_blocks) * 64;
+        counters[0] = min(counters[0], cap_items);
+    }
+    if (tid >= 2 && tid < 34) counters[tid] = 0;
+}
+
+// ------------------------------------------------------------ embed + QKV
+struct EmbedParams {
+    const float* x;
+    const int4* blk;
+    const int* counters;
+    const uint8_t* w1;   // [64 x 64] or [64 x 128] image
+    const uint8_t* w2;   // [64 x 64]
+    const uint8_t* wqkv; // [192 x 64]
+    const float *b1, *b2, *lng, *lnb, *bqkv;
+    float* z;
+    __nv_bfloat16 *q, *k, *vt;
+    long ldvt;
+    unsigned* status;
+    uint64_t wait_ns;
+    int act;
+};
+
+template <int MODE>  // 0: input x (K = 42 -> 64); 1: concat(x, h_pid) (K = 128)
+__global__ void __launch_bounds__(128, 1) k_embed_qkv(const __grid_constant__ CUtensorMap map_hp,
+                                                      EmbedParams p) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* sm = align1024(smem_raw);
+    constexpr int KA = MODE == 0 ? 1 : 2;
+    constexpr uint32_t W1B = 64 * 128 * KA, W2B = 64 * 128, WQB = 192 * 128;
+    uint8_t* sW1 = sm;
+    uint8_t* sW2 = sW1 + W1B;
+    uint8_t* sWq = sW2 + W2B;
+    uint8_t* sA = sWq + WQB;          // KA atom columns
+    uint8_t* sH = sA + KA * ATOM;     // 1 atom column
+    uint64_t* bars = (uint64_t*)(sH + ATOM);  // 0 weights, 1 tma, 2 mma
+    uint32_t* tmem_hold = (uint32_t*)(bars + 4);
+    int* abort_flag = (int*)(tmem_hold + 1);
+    const int tid = threadIdx.x;
+
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        mbar_init(&bars[2], 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (tid < 32) {
+        tmem_alloc(tmem_hold, 256);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = *tmem_hold;
+    const uint32_t trow = tbase + ((uint32_t)(tid & 96) << 16);  // lane quarter of this warp
+    volatile int* ab = abort_flag;
+
+    if (tid == 0) {
+        mbar_arrive_expect_tx(&bars[0], W1B + W2B + WQB);
+        bulk_load(sW1, p.w1, W1B, &bars[0]);
+        bulk_load(sW2, p.w2, W2B, &bars[0]);
+        bulk_load(sWq, p.wqkv, WQB, &bars[0]);
+    }
+    bool fail = !mbar_wait(&bars[0], 0, ab, p.status, ST_TIMEOUT_GEMM, p.wait_ns);
+
+    const int tpad = p.counters[1];
+    const int nblk = tpad >> 6;
+    const int ntiles = (tpad + ROWS - 1) / ROWS;
+    uint32_t mph = 0, aph = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        if (__syncthreads_or(fail)) break;
+        const int p0 = tile * ROWS;
+        const int prow_pad = p0 + tid;
+        const RowInfo ri = row_info(p.blk, nblk, prow_pad);
+        if (MODE == 1 && tid == 0) {
+            mbar_arrive_expect_tx(&bars[1], ATOM);
+            tma_load_2d(sA + ATOM, &map_hp, 0, p0, &bars[1]);
+        }
+        load_x_row(sA, tid, p.x, ri.valid, ri.prow);
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            if (MODE == 1) {
+                fail |= !mbar_wait(&bars[1], aph, ab, p.status, ST_TIMEOUT_GEMM, p.wait_ns);
+            }
+            tc_fence_after();
+            if (!fail) issue_gemm(tbase, sA, sW1, 64, KA);
+            mma_commit(&bars[2]);
+        }
+        aph ^= 1;
+        fail |= !mbar_wait(&bars[2], mph, ab, p.status, ST_TIMEOUT_GEMM, p.wait_ns);
+        mph ^= 1;
+        if (__syncthreads_or(fail)) break;
+        tc_fence_after();
+        float v[64];
+        ld_row64(trow, v);
+#pragma unroll
+        for (int i = 0; i < 64; ++i) v[i] = act_f(v[i] + __ldg(p.b1 + i), p.act);
+        st_row_bf16(sH, tid, v);
+        tc_fence_before();
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            issue_gemm(tbase, sH, sW2, 64, 1);
+            mma_commit(&bars[2]);
+        }
+        fail |= !mbar_wait(&bars[2], mph, ab, p.status, ST_TIMEOUT_GEMM, p.wait_ns);
+        mph ^= 1;
+        if (__syncthreads_or(fail)) break;
+        tc_fence_after();
+        ld_row64(trow, v);
+#pragma unroll
+        for (int i = 0; i < 64; ++i) v[i] += __ldg(p.b2 + i);
+        {
+            float4* zd = (float4*)(p.z + (size_t)prow_pad * D);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) zd[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+        }
+        layernorm64(v, v, p.lng, p.lnb);
+        st_row_bf16(sH, tid, v);
+        tc_fence_before();
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            issue_gemm(tbase, sH, sWq, 192, 1);
+            mma_commit(&bars[2]);
+        }
+        fail |= !mbar_wait(&bars[2], mph, ab, p.status, ST_TIMEOUT_GEMM, p.wait_ns);
+        mph ^= 1;
+        if (__syncthreads_or(fail)) break;
+        tc_fence_after();
+        store_qkv(trow, p.bqkv, prow_pad, ri.valid, p.q, p.k, p.vt, p.ldvt);
+        tc_fence_before();
+    }
+    __syncthreads();
+    if (*ab && tid == 0) {
+        for (int i = 0; i < 1000; ++i) __nanosleep(1000);  // let in-flight copies land
+    }
+    __syncthreads();
+    if (tid < 32) {
+        tc_fence_after();
+        tmem_dealloc(tbase, 256);
+    }
+}
+
+// ------------------------------------------------------------ post-attention
+struct PostParams {
+    const float* x;
+    const int4* blk;
+    const int* counters;
+    const uint8_t *wo, *wup, *wdn;  // [64x64], [256x64], [64x256]
+    const uint8_t *wa, *wb;         // mode 0: wqkv [192x64]; 1: cls w1 [64x64], w2 [16x64];
+                                    // 2: heads w1 [256x64], w2 [16x256]
+    const float *bo, *ln2g, *ln2b, *bup, *bdn;
+    const float *lng, *lnb;         // next LN1 (mode 0) or final LN (modes 1, 2)
+    const float *ba, *bb;           // mode 0: bqkv; 1: cls b1, b2 (16); 2: heads b1 (256), b2 (16)
+    float* z;
+    __nv_bfloat16 *q, *k, *vt, *hp;
+    long ldvt;
+    float* logits;
+    float* reg;
+    unsigned* status;
+    uint64_t wait_ns;
+    int act;
+};
+
+template <int MODE>  // 0: next layer LN1 + QKV; 1: end of PID stack; 2: end of regression stack
+__global__ void __launch_bounds__(128, 1) k_post(const __grid_constant__ CUtensorMap map_o,
+                                                 PostParams p) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* sm = align1024(smem_raw);
+    constexpr uint32_t WOB = 64 * 128, WUB = 256 * 128, WDB = 4 * 64 * 128;
+    constexpr uint32_t WAB = MODE == 0 ? 192 * 128 : (MODE == 1 ? 64 * 128 : 256 * 128);
+    constexpr uint32_t WBB = MODE == 0 ? 0 : (MODE == 1 ? 16 * 128 : 4 * 16 * 128);
+    uint8_t* sWo = sm;
+    uint8_t* sWu = sWo + WOB;
+    uint8_t* sWd = sWu + WUB;
+    uint8_t* sWa = sWd + WDB;
+    uint8_t* sWb = sWa + WAB;
+    uint8_t* sA = sWb + ((WBB + 1023) & ~1023u);
+    uint8_t* sH = sA + ATOM;  // 4 atom columns
+    uint64_t* bars = (uint64_t*)(sH + 4 * ATOM);
+    uint32_t* tmem_hold = (uint32_t*)(bars + 4);
+    int* abort_flag = (int*)(tmem_hold + 1);
+    const int tid = threadIdx.x;
+
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        mbar_init(&bars[2], 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (tid < 32) {
+        tmem_alloc(tmem_hold, 256);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = *tmem_hold;
+    const uint32_t trow = tbase + ((uint32_t)(tid & 96) << 16);
+    volatile int* ab = abort_flag;
+    if (tid == 0) {
+        mbar_arrive_expect_tx(&bars[0], WOB + WUB + WDB + WAB + WBB);
+        bulk_load(sWo, p.wo, WOB, &bars[0]);
+        bulk_load(sWu, p.wup, WUB, &bars[0]);
+        bulk_load(sWd, p.wdn, WDB, &bars[0]);
+        bulk_load(sWa, p.wa, WAB, &bars[0]);
+        if (WBB) bulk_load(sWb, p.wb, WBB, &bars[0]);
+    }
+    bool fail = !mbar_wait(&bars[0], 0, ab, p.status, ST_TIMEOUT_GEMM, p.wait_ns);
+
+    const int tpad = p.counters[1];
+    const int nblk = tpad >> 6;
+    const int ntiles = (tpad + ROWS - 1) / ROWS;
+    uint32_t mph = 0, aph = 0;
+    auto gemm = [&](const uint8_t* a, const uint8_t* b, int N, int ka) -> bool {
+        tc_fence_before();
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            issue_gemm(tbase, a, b, N, ka);
+            mma_commit(&bars[2]);
+        }
+        fail |= !mbar_wait(&bars[2], mph, ab, p.status, ST_TIMEOUT_GEMM, p.wait_ns);
+        mph ^= 1;
+        const bool stop = __syncthreads_or(fail);
+        tc_fence_after();
+        return !stop;
+    };
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        if (__syncthreads_or(fail)) break;
+        const int p0 = tile * ROWS;
+        const int pp = p0 + tid;
+        const RowInfo ri = row_info(p.blk, nblk, pp);
+        if (tid == 0) {
+            mbar_arrive_expect_tx(&bars[1], ATOM);
+            tma_load_2d(sA, &map_o, 0, p0, &bars[1]);
+        }
+        float zr[64], v[64];
+        {
+            const float4* zs = (const float4*)(p.z + (size_t)pp * D);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const float4 t = zs[i];
+                zr[4 * i] = t.x; zr[4 * i + 1] = t.y; zr[4 * i + 2] = t.z; zr[4 * i + 3] = t.w;
+            }
+        }
+        fail |= !mbar_wait(&bars[1], aph, ab, p.status, ST_TIMEOUT_GEMM, p.wait_ns);
+        aph ^= 1;
+        if (!gemm(sA, sWo, 64, 1)) break;
+        ld_row64(trow, v);
+#pragma unroll
+        for (int i = 0; i < 64; ++i) zr[i] += v[i] + __ldg(p.bo + i);
+        layernorm64(zr, v, p.ln2g, p.ln2b);
+        st_row_bf16(sA, tid, v);
+        if (!gemm(sA, sWu, 256, 1)) break;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            ld_row64(trow + 64 * c, v);
+#pragma unroll
+            for (int i = 0; i < 64; ++i) v[i] = act_f(v[i] + __ldg(p.bup + 64 * c + i), p.act);
+            st_row_bf16(sH + c * ATOM, tid, v);
+        }
+        if (!gemm(sH, sWd, 64, 4)) break;
+        ld_row64(trow, v);
+#pragma unroll
+        for (int i = 0; i < 64; ++i) zr[i] += v[i] + __ldg(p.bdn + i);
+        if (MODE == 0) {
+            float4* zd = (float4*)(p.z + (size_t)pp * D);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) zd[i] = make_float4(zr[4 * i], zr[4 * i + 1], zr[4 * i + 2], zr[4 * i + 3]);
+            layernorm64(zr, v, p.lng, p.lnb);
+            st_row_bf16(sA, tid, v);
+            if (!gemm(sA, sWa, 192, 1)) break;
+            store_qkv(trow, p.ba, pp, ri.valid, p.q, p.k, p.vt, p.ldvt);
+        } else if (MODE == 1) {
+            layernorm64(zr, v, p.lng, p.lnb);  // h_pid
+            st_global_bf16_row64(p.hp + (size_t)pp * D, v);
+            st_row_bf16(sA, tid, v);
+            if (!gemm(sA, sWa, 64, 1)) break;
+            ld_row64(trow, v);
+#pragma unroll
+            for (int i = 0; i < 64; ++i) v[i] = act_f(v[i] + __ldg(p.ba + i), p.act);
+            st_row_bf16(sH, tid, v);
+            if (!gemm(sH, sWb, 16, 1)) break;
+            tmem_ld16(trow, v);
+            tmem_wait_ld();
+            if (ri.valid) {
+                float2* lo = (float2*)(p.logits + (size_t)ri.prow * 6);
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    lo[c] = make_float2(v[2 * c] + __ldg(p.bb + 2 * c), v[2 * c + 1] + __ldg(p.bb + 2 * c + 1));
+            }
+        } else {
+            layernorm64(zr, v, p.lng, p.lnb);  // h_reg
+            st_row_bf16(sA, tid, v);
+            if (!gemm(sA, sWa, 256, 1)) break;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                ld_row64(trow + 64 * c, v);
+#pragma unroll
+                for (int i = 0; i < 64; ++i) v[i] = act_f(v[i] + __ldg(p.ba + 64 * c + i), p.act);
+                st_row_bf16(sH + c * ATOM, tid, v);
+            }
+            if (!gemm(sH, sWb, 16, 4)) break;
+            tmem_ld16(trow, v);
+            tmem_wait_ld();
+            if (ri.valid) {
+                float o[5];
+#pragma unroll
+                for (int c = 0; c < 5; ++c) o[c] = v[c] + __ldg(p.bb + c);
+                const float* xr = p.x + (size_t)ri.prow * 42;
+                float* rg = p.reg + (size_t)ri.prow * 5;
+                rg[0] = expf(__ldg(xr + 8) + o[0]);
+                rg[1] = o[1];
+                rg[2] = o[2];
+                rg[3] = o[3];
+                rg[4] = expf(__ldg(xr + 9) + o[4]);
+            }
+        }
+        tc_fence_before();
+    }
+    __syncthreads();
+    if (*ab && tid == 0) {
+        for (int i = 0; i < 1000; ++i) __nanosleep(1000);
+    }
+    __syncthreads();
+    if (tid < 32) {
+        tc_fence_after();
+        tmem_dealloc(tbase, 256);
+    }
+}
+
+// ------------------------------------------------------------- attention
+constexpr int AT_STAGES = 4;
+constexpr int AT_THREADS = NH * 128 + 32;
+constexpr uint32_t AT_QB = 128 * 128;   // Q tile bytes (128 rows x 64 ch bf16)
+constexpr uint32_t AT_KB = 64 * 128;    // K tile bytes (64 keys x 64 ch)
+constexpr uint32_t AT_VB = 64 * 128;    // V^T tile bytes (64 ch x 64 keys)
+constexpr uint32_t AT_PB = 128 * 128;   // P tile bytes per head (128 rows x 64 keys)
+constexpr uint32_t AT_OFF_K = 2 * AT_QB;
+constexpr uint32_t AT_OFF_V = AT_OFF_K + AT_STAGES * AT_KB;
+constexpr uint32_t AT_OFF_P = AT_OFF_V + AT_STAGES * AT_VB;
+constexpr uint32_t AT_OFF_BAR = AT_OFF_P + NH * AT_PB;
+constexpr uint32_t AT_SMEM = AT_OFF_BAR + 512 + 1024;
+
+struct AttnParams {
+    const int4* items;
+    int* counters;
+    int layer;
+    __nv_bfloat16* out;
+    unsigned* status;
+    uint64_t wait_ns;
+    int debug_stall;
+};
+
+MLPF_DEV bool bar_or(int id, int n, bool pred) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, %2, %3, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)pred), "r"(id), "r"(n)
+        : "memory");
+    return r != 0;
+}
+
+__global__ void __launch_bounds__(AT_THREADS, 1)
+    k_attention(const __grid_constant__ CUtensorMap map_q, const __grid_constant__ CUtensorMap map_k,
+                const __grid_constant__ CUtensorMap map_vt, AttnParams p) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* sm = align1024(smem_raw);
+    uint8_t* sQ = sm;
+    uint8_t* sK = sm + AT_OFF_K;
+    uint8_t* sV = sm + AT_OFF_V;
+    uint8_t* sP = sm + AT_OFF_P;
+    uint64_t* bars = (uint64_t*)(sm + AT_OFF_BAR);
+    uint64_t* q_full = bars;                 // [2]
+    uint64_t* q_empty = bars + 2;            // [2]
+    uint64_t* kv_full = bars + 4;            // [4]
+    uint64_t* kv_empty = bars + 8;           // [4]
+    uint64_t* s_full = bars + 12;            // [4 heads][2 buffers]
+    uint64_t* pv_done = bars + 20;           // [4 heads]
+    uint64_t* never = bars + 24;             // armed by nobody (debug stall)
+    int4* info = (int4*)(bars + 26);         // [2]
+    uint32_t* tmem_hold = (uint32_t*)(info + 2);
+    int* abort_flag = (int*)(tmem_hold + 1);
+    volatile int* ab = abort_flag;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    if (tid == 0) {
+        for (int i = 0; i < 2; ++i) { mbar_init(&q_full[i], 1); mbar_init(&q_empty[i], NH); }
+        for (int i = 0; i < AT_STAGES; ++i) { mbar_init(&kv_full[i], 1); mbar_init(&kv_empty[i], NH); }
+        for (int i = 0; i < 2 * NH; ++i) mbar_init(&s_full[i], 1);
+        for (int i = 0; i < NH; ++i) mbar_init(&pv_done[i], 1);
+        mbar_init(never, 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 0) {
+        tmem_alloc(tmem_hold, 512);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = *tmem_hold;
+    const int n_items = p.counters[0];
+    int* ticket = p.counters + 2 + p.layer;
+
+    if (warp == NH * 4) {
+        // ------------------------------------------------ TMA producer
+        if (lane == 0) {
+            tma_prefetch_map(&map_q);
+            tma_prefetch_map(&map_k);
+            tma_prefetch_map(&map_vt);
+            int q_it = 0;
+            uint32_t g = 0;
+            bool ok = true;
+            while (ok) {
+                const int item = atomicAdd(ticket, 1);
+                const int qb = q_it & 1;
+                if (q_it >= 2 &&
+                    !mbar_wait(&q_empty[qb], ((q_it >> 1) - 1) & 1, ab, p.status, ST_TIMEOUT_ATTN, p.wait_ns))
+                    break;
+                if (item >= n_items) {
+                    info[qb] = make_int4(-1, 0, 0, 0);
+                    mbar_arrive(&q_full[qb]);
+                    break;
+                }
+                const int4 it = p.items[item];
+                info[qb] = it;
+                mbar_arrive_expect_tx(&q_full[qb], AT_QB);
+                tma_load_2d(sQ + qb * AT_QB, &map_q, 0, it.x + it.y * ROWS, &q_full[qb]);
+                const int nk = (it.z + 63) >> 6;
+                for (int j = 0; j < nk; ++j, ++g) {
+                    const int s = g & (AT_STAGES - 1);
+                    if (g >= AT_STAGES &&
+                        !mbar_wait(&kv_empty[s], ((g / AT_STAGES) - 1) & 1, ab, p.status, ST_TIMEOUT_ATTN,
+                                   p.wait_ns)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_expect_tx(&kv_full[s], AT_KB + AT_VB);
+                    tma_load_2d(sK + s * AT_KB, &map_k, 0, it.x + 64 * j, &kv_full[s]);
+                    tma_load_2d(sV + s * AT_VB, &map_vt, it.x + 64 * j, 0, &kv_full[s]);
+                }
+                ++q_it;
+            }
+        }
+    } else {
+        // ------------------------------------------------ one warpgroup per head
+        const int h = warp >> 2;
+        const int r = tid & 127;                 // query row within the tile
+        const bool leader = r == 0;
+        const int bar_id = 1 + h;
+        const uint32_t tl = tbase + ((uint32_t)((warp & 3) * 32) << 16);  // this warp's lanes
+        const uint32_t scol = h * 128;           // two 64-column S buffers per head
+        const uint32_t IQK = idesc_f16(128, 64, 1), IPV = idesc_f16(128, 16, 1);
+        const float c = 0.25f * 1.4426950408889634f;  // log2(e) / sqrt(16)
+        uint8_t* myP = sP + h * AT_PB;
+        int q_it = 0;
+        uint32_t g = 0;
+        while (true) {
+            const int qb = q_it & 1;
+            bool fail = !mbar_wait(&q_full[qb], (q_it >> 1) & 1, ab, p.status, ST_TIMEOUT_ATTN, p.wait_ns);
+            int4 it = fail ? make_int4(-1, 0, 0, 0) : info[qb];
+            if (!fail && p.debug_stall)
+                fail = !mbar_wait(never, 0, ab, p.status, ST_TIMEOUT_ATTN, p.wait_ns);
+            if (bar_or(bar_id, 128, fail || it.x < 0)) break;
+            const int nk = (it.z + 63) >> 6;
+            if (nk == 0) {  // an event the scheduler could not place: no keys loaded
+                if (leader) mbar_arrive(&q_empty[qb]);
+                ++q_it;
+                continue;
+            }
+            const int qrow0 = it.x + it.y * ROWS;
+            const int rows_valid = min(ROWS, it.z - it.y * ROWS);
+            float o[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) o[i] = 0.f;
+            float m = -INFINITY, l = 0.f, alpha_prev = 0.f;
+            if (leader) {
+                const uint32_t s = g & (AT_STAGES - 1);
+                if (mbar_wait(&kv_full[s], (g / AT_STAGES) & 1, ab, p.status, ST_TIMEOUT_ATTN, p.wait_ns)) {
+                    tc_fence_after();
+                    mma_f16(tbase + scol + (g & 1) * 64, sdesc_sw128(smem_u32(sQ + qb * AT_QB) + h * 32),
+                            sdesc_sw128(smem_u32(sK + s * AT_KB) + h * 32), IQK, 0);
+                    mma_commit(&s_full[h * 2 + (g & 1)]);
+                } else {
+                    fail = true;
+                }
+            }
+            bool stop = false;
+            for (int j = 0; j < nk; ++j) {
+                const uint32_t gj = g + j;
+                const uint32_t sb = gj & 1;
+                if (j > 0 && !fail) {
+                    // PV of tile j-1 landed in the other buffer's first 16 columns
+                    if (__all_sync(0xffffffffu, mbar_wait(&pv_done[h], (gj - 1) & 1, ab, p.status, ST_TIMEOUT_ATTN, p.wait_ns))) {
+                        tc_fence_after();
+                        float part[16];
+                        tmem_ld16(tl + scol + (sb ^ 1) * 64, part);
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) o[i] = fmaf(o[i], alpha_prev, part[i]);
+                    } else {
+                        fail = true;
+                    }
+                }
+                tc_fence_before();
+                if (bar_or(bar_id, 128, fail)) { stop = true; break; }
+                if (leader && j + 1 < nk) {
+                    const uint32_t g1 = gj + 1, s1 = g1 & (AT_STAGES - 1);
+                    if (mbar_wait(&kv_full[s1], (g1 / AT_STAGES) & 1, ab, p.status, ST_TIMEOUT_ATTN, p.wait_ns)) {
+                        tc_fence_after();
+                        mma_f16(tbase + scol + (g1 & 1) * 64, sdesc_sw128(smem_u32(sQ + qb * AT_QB) + h * 32),
+                                sdesc_sw128(smem_u32(sK + s1 * AT_KB) + h * 32), IQK, 0);
+                        mma_commit(&s_full[h * 2 + (g1 & 1)]);
+                    } else {
+                        fail = true;
+                    }
+                }
+                {   // warp-uniform: the TMEM loads below are .sync.aligned
+                    const bool got = fail ? false
+                                          : mbar_wait(&s_full[h * 2 + sb], (gj >> 1) & 1, ab, p.status,
+                                                      ST_TIMEOUT_ATTN, p.wait_ns);
+                    fail = !__all_sync(0xffffffffu, got);
+                }
+                if (!fail) {
+                    tc_fence_after();
+                    const uint32_t sa = tl + scol + sb * 64;
+                    const int kvalid = (j == nk - 1) ? it.z - 64 * j : 64;
+                    // pass 1: row max over the 64 scores (second half kept in registers)
+                    float s[32];
+                    tmem_ld32(sa, s);
+                    tmem_wait_ld();
+                    float mx = -INFINITY;
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) mx = fmaxf(mx, i < kvalid ? s[i] : -INFINITY);
+                    tmem_ld32(sa + 32, s);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) {
+                        if (i + 32 >= kvalid) s[i] = -INFINITY;
+                        mx = fmaxf(mx, s[i]);
+                    }
+                    const float m_new = fmaxf(m, mx * c);
+                    const float alpha = ex2_approx(m - m_new);
+                    float sum = 0.f;
+                    // pass 2: exponentials, row sum, bf16 P into the swizzled tile
+#pragma unroll
+                    for (int half = 1; half >= 0; --half) {
+                        if (half == 0) {
+                            tmem_ld32(sa, s);
+                            tmem_wait_ld();
+#pragma unroll
+                            for (int i = 0; i < 32; ++i)
+                                if (i >= kvalid) s[i] = -INFINITY;
+                        }
+#pragma unroll
+                        for (int cc = 0; cc < 4; ++cc) {
+                            uint32_t pk[4];
+#pragma unroll
+                            for (int t = 0; t < 4; ++t) {
+                                const float p0 = ex2_approx(fmaf(s[8 * cc + 2 * t], c, -m_new));
+                                const float p1 = ex2_approx(fmaf(s[8 * cc + 2 * t + 1], c, -m_new));
+                                sum += p0 + p1;
+                                pk[t] = pack_bf16x2(p0, p1);
+                            }
+                            *(uint4*)(myP + sw128_off(r, half * 4 + cc)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                        }
+                    }
+                    l = fmaf(l, alpha, sum);
+                    m = m_new;
+                    alpha_prev = alpha;
+                    fence_proxy_async_smem();
+                } else {
+                    fail = true;
+                }
+                tc_fence_before();
+                if (bar_or(bar_id, 128, fail)) { stop = true; break; }
+                if (leader) {
+                    tc_fence_after();
+                    const uint32_t s = gj & (AT_STAGES - 1);
+                    const uint32_t pa = smem_u32(myP), va = smem_u32(sV + s * AT_VB) + h * 16 * 128;
+#pragma unroll
+                    for (int kc = 0; kc < 4; ++kc)
+                        mma_f16(tbase + scol + sb * 64, sdesc_sw128(pa + kc * 32), sdesc_sw128(va + kc * 32),
+                                IPV, kc > 0 ? 1u : 0u);
+                    mma_commit(&pv_done[h]);
+                    mma_commit(&kv_empty[s]);
+                }
+            }
+            if (stop) break;
+            const uint32_t gl = g + nk - 1;
+            const bool got_last = fail ? false : mbar_wait(&pv_done[h], gl & 1, ab, p.status, ST_TIMEOUT_ATTN, p.wait_ns);
+            if (__all_sync(0xffffffffu, got_last)) {
+                tc_fence_after();
+                float part[16];
+                tmem_ld16(tl + scol + (gl & 1) * 64, part);
+                tmem_wait_ld();
+#pragma unroll
+                for (int i = 0; i < 16; ++i) o[i] = fmaf(o[i], alpha_prev, part[i]);
+            } else {
+                fail = true;
+            }
+            if (leader && !fail) mbar_arrive(&q_empty[qb]);
+            if (!fail && r < rows_valid) {
+                const float inv = 1.0f / l;
+                uint4 u0, u1;
+                u0.x = pack_bf16x2(o[0] * inv, o[1] * inv);
+                u0.y = pack_bf16x2(o[2] * inv, o[3] * inv);
+                u0.z = pack_bf16x2(o[4] * inv, o[5] * inv);
+                u0.w = pack_bf16x2(o[6] * inv, o[7] * inv);
+                u1.x = pack_bf16x2(o[8] * inv, o[9] * inv);
+                u1.y = pack_bf16x2(o[10] * inv, o[11] * inv);
+                u1.z = pack_bf16x2(o[12] * inv, o[13] * inv);
+                u1.w = pack_bf16x2(o[14] * inv, o[15] * inv);
+                uint4* dst = (uint4*)(p.out + (size_t)(qrow0 + r) * D + h * 16);
+                dst[0] = u0;
+                dst[1] = u1;
+            }
+            tc_fence_before();
+            if (bar_or(bar_id, 128, fail)) break;
+            g += nk;
+            ++q_it;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (*ab && tid == 0) {
+        for (int i = 0; i < 1000; ++i) __nanosleep(1000);
+    }
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tbase, 512);
+    }
+}
+
+// ---------------------------------------------------------------- host side
+uint32_t embed_smem(int mode) {
+    const int ka = mode == 0 ? 1 : 2;
+    const uint32_t need = 64 * 128 * ka + 64 * 128 + 192 * 128 + ka * ATOM + ATOM + 64 + 1024;
+    // at least 80 KB so that no more than two CTAs (2 x 256 TMEM columns) share an SM
+    return need < 80 * 1024 ? 80 * 1024 : need;
+}
+uint32_t post_smem(int mode) {
+    const uint32_t wab = mode == 0 ? 192 * 128 : (mode == 1 ? 64 * 128 : 256 * 128);
+    const uint32_t wbb = mode == 0 ? 0 : (mode == 1 ? 16 * 128 : 4 * 16 * 128);
+    return 64 * 128 + 256 * 128 + 4 * 64 * 128 + wab + ((wbb + 1023) & ~1023u) + 5 * ATOM + 64 + 1024;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    }
+    return fn;
+}
+
+bool make_map_bf16(CUtensorMap* map, void* base, uint64_t inner, uint64_t outer, uint32_t box_inner,
+                   uint32_t box_outer) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {inner, outer};
+    cuuint64_t strides[1] = {inner * 2};
+    cuuint32_t box[2] = {box_inner, box_outer};
+    cuuint32_t es[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// bf16 swizzled image of a weight matrix: out[n][k'] = W[n][colmap(k')], zero padded.
+void build_image(std::vector<uint8_t>& out, int Npad, int Kpad, const std::vector<float>& W,
+                 int N, int K, const std::vector<int>& colmap, const std::vector<int>& rowmap) {
+    out.assign((size_t)Npad * Kpad * 2, 0);
+    const int atoms = Kpad / 64;
+    for (int a = 0; a < atoms; ++a)
+        for (int n = 0; n < Npad; ++n)
+            for (int kk = 0; kk < 64; ++kk) {
+                const int kp = a * 64 + kk;
+                const int src_k = colmap.empty() ? (kp < K ? kp : -1) : colmap[kp];
+                const int src_n = rowmap.empty() ? (n < N ? n : -1) : rowmap[n];
+                float v = 0.f;
+                if (src_k >= 0 && src_n >= 0) v = W[(size_t)src_n * K + src_k];
+                const __nv_bfloat16 b = __float2bfloat16_rn(v);
+                const size_t off = (size_t)a * Npad * 128 + (size_t)n * 128 +
+                                   (size_t)((((kk >> 3) ^ (n & 7)) << 4)) + (kk & 7) * 2;
+                std::memcpy(&out[off], &b, 2);
+            }
+}
+
+}  // namespace
+
+bool tc_prepare_weights(Model& m) {
+    const mlpf_config& c = m.cfg;
+    auto H = [&](const std::string& s) -> const std::vector<float>& { return m.host.at(s).data; };
+    std::vector<std::pair<std::string, std::vector<uint8_t>>> imgs;
+    std::vector<std::pair<std::string, std::vector<float>>> vecs;
+    std::vector<uint8_t> img;
+    auto add = [&](const std::string& name, int Npad, int Kpad, const std::vector<float>& W, int N,
+                   int K, std::vector<int> colmap = {}, std::vector<int> rowmap = {}) {
+        build_image(img, Npad, Kpad, W, N, K, colmap, rowmap);
+        imgs.push_back({name, img});
+    };
+    auto cat = [&](std::initializer_list<std::string> names, int pad_to = 0) {
+        std::vector<float> v;
+        for (auto& n : names) v.insert(v.end(), H(n).begin(), H(n).end());
+        if ((int)v.size() < pad_to) v.resize(pad_to, 0.f);
+        return v;
+    };
+    add("emb.w1", 64, 64, H("emb.w1"), 64, 42);
+    add("emb.w2", 64, 64, H("emb.w2"), 64, 64);
+    vecs.push_back({"emb.b1", H("emb.b1")});
+    vecs.push_back({"emb.b2", H("emb.b2")});
+    for (const char* s : {"pid", "reg"}) {
+        const int L = std::string(s) == "pid" ? c.l_pid : c.l_reg;
+        for (int l = 0; l < L; ++l) {
+            const std::string p = std::string(s) + "." + std::to_string(l) + ".";
+            std::vector<float> wqkv = cat({p + "wq", p + "wk", p + "wv"});
+            add(p + "wqkv", 192, 64, wqkv, 192, 64);
+            add(p + "wo", 64, 64, H(p + "wo"), 64, 64);
+            add(p + "ffn.w1", 256, 64, H(p + "ffn.w1"), 256, 64);
+            add(p + "ffn.w2", 64, 256, H(p + "ffn.w2"), 64, 256);
+            vecs.push_back({p + "bqkv", cat({p + "bq", p + "bk", p + "bv"})});
+            for (const char* v : {"bo", "ln1.g", "ln1.b", "ln2.g", "ln2.b", "ffn.b1", "ffn.b2"})
+                vecs.push_back({p + v, H(p + v)});
+        }
+        vecs.push_back({std::string(s) + ".lnf.g", H(std::string(s) + ".lnf.g")});
+        vecs.push_back({std::string(s) + ".lnf.b", H(std::string(s) + ".lnf.b")});
+    }
+    {
+        std::vector<int> colmap(128, -1);
+        for (int k = 0; k < 42; ++k) colmap[k] = k;
+        for (int k = 0; k < 64; ++k) colmap[64 + k] = 42 + k;
+        add("remb.w1", 64, 128, H("remb.w1"), 64, 106, colmap);
+        add("remb.w2", 64, 64, H("remb.w2"), 64, 64);
+        vecs.push_back({"remb.b1", H("remb.b1")});
+        vecs.push_back({"remb.b2", H("remb.b2")});
+    }
+    add("head.cls.w1", 64, 64, H("head.cls.w1"), 64, 64);
+    add("head.cls.w2", 16, 64, H("head.cls.w2"), 6, 64);
+    vecs.push_back({"head.cls.b1", H("head.cls.b1")});
+    vecs.push_back({"head.cls.b2", cat({"head.cls.b2"}, 16)});
+    {
+        std::vector<float> w1 = cat({"head.pt.w1", "head.eta.w1", "head.phi.w1", "head.e.w1"});
+        add("head.reg.w1", 256, 64, w1, 256, 64);
+        // block-diagonal second layer: output o reads hidden block of its head
+        std::vector<float> w2(5 * 256, 0.f);
+        const char* names[4] = {"pt", "eta", "phi", "e"};
+        int o = 0;
+        for (int hh = 0; hh < 4; ++hh) {
+            const auto& src = H(std::string("head.") + names[hh] + ".w2");
+            const int k = (int)src.size() / 64;
+            for (int r = 0; r < k; ++r, ++o)
+                for (int i = 0; i < 64; ++i) w2[(size_t)o * 256 + hh * 64 + i] = src[(size_t)r * 64 + i];
+        }
+        add("head.reg.w2", 16, 256, w2, 5, 256);
+        vecs.push_back({"head.reg.b1", cat({"head.pt.b1", "head.eta.b1", "head.phi.b1", "head.e.b1"})});
+        vecs.push_back({"head.reg.b2", cat({"head.pt.b2", "head.eta.b2", "head.phi.b2", "head.e.b2"}, 16)});
+    }
+    size_t ib = 0, vb = 0;
+    for (auto& i : imgs) ib += (i.second.size() + 1023) / 1024 * 1024;
+    for (auto& v : vecs) vb += (v.second.size() + 63) / 64 * 64;
+    if (cudaMalloc(&m.w.img_base, ib) != cudaSuccess) { set_error("weight image allocation"); return false; }
+    if (cudaMalloc(&m.w.tc_f32_base, vb * 4) != cudaSuccess) { set_error("bias allocation"); return false; }
+    std::vector<uint8_t> hi(ib, 0);
+    std::vector<float> hv(vb, 0.f);
+    size_t o = 0;
+    for (auto& i : imgs) {
+        std::memcpy(&hi[o], i.second.data(), i.second.size());
+        m.w.img[i.first] = m.w.img_base + o;
+        m.w.img_bytes[i.first] = (uint32_t)i.second.size();
+        o += (i.second.size() + 1023) / 1024 * 1024;
+    }
+    o = 0;
+    for (auto& v : vecs) {
+        std::copy(v.second.begin(), v.second.end(), hv.begin() + o);
+        m.w.tcv[v.first] = m.w.tc_f32_base + o;
+        o += (v.second.size() + 63) / 64 * 64;
+    }
+    if (cudaMemcpy(m.w.img_base, hi.data(), ib, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(m.w.tc_f32_base, hv.data(), vb * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+        set_error("weight image upload");
+        return false;
+    }
+    static bool attrs = false;
+    if (!attrs) {
+        cudaFuncSetAttribute(k_embed_qkv<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, embed_smem(0));
+        cudaFuncSetAttribute(k_embed_qkv<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, embed_smem(1));
+        cudaFuncSetAttribute(k_post<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, post_smem(0));
+        cudaFuncSetAttribute(k_post<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, post_smem(1));
+        cudaFuncSetAttribute(k_post<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, post_smem(2));
+        cudaFuncSetAttribute(k_attention, cudaFuncAttributeMaxDynamicSharedMemorySize, AT_SMEM);
+        attrs = true;
+    }
+    if (cudaGetLastError() != cudaSuccess) { set_error("kernel attribute setup"); return false; }
+    return true;
+}
+
+bool tc_make_maps(Model& m) {
+    Workspace& w = m.ws;
+    const uint64_t T = (uint64_t)w.cap_tpad;
+    bool ok = make_map_bf16(&w.map_q, w.tq, 64, T, 64, 128) && make_map_bf16(&w.map_k, w.tk, 64, T, 64, 64) &&
+              make_map_bf16(&w.map_o, w.to, 64, T, 64, 128) && make_map_bf16(&w.map_vt, w.tvt, T, 64, 64, 64) &&
+              make_map_bf16(&w.map_hp, w.thp, 64, T, 64, 128);
+    if (!ok) set_error("cuTensorMapEncodeTiled failed");
+    return ok;
+}
+
+int64_t run_forward_tc(Model& m, int prec, const float* x, const int32_t* cu, int n_events, int total,
+                       int max_n, float* logits, float* reg, cudaStream_t st) {
+    (void)prec;
+    (void)total;
+    (void)max_n;
+    const mlpf_config& c = m.cfg;
+    Workspace& w = m.ws;
+    auto V = [&](const std::string& s) { return (const float*)m.w.tcv.at(s); };
+    auto I = [&](const std::string& s) { return (const uint8_t*)m.w.img.at(s); };
+    int64_t n = 0;
+    const int grid = m.sm_count;
+    k_schedule<<<1, 1024, 0, st>>>(cu, n_events, w.blk, w.items, w.counters, (int)(w.cap_tpad / 64),
+                                   (int)(w.cap_tpad / 128 + w.cap_events + 1));
+    ++n;
+    auto attention = [&](int layer) {
+        AttnParams ap{w.items, w.counters, layer, w.to, m.status, (uint64_t)m.wait_limit_ns, m.debug_stall ? 1 : 0};
+        k_attention<<<grid * m.attn_ctas_per_sm, AT_THREADS, AT_SMEM, st>>>(w.map_q, w.map_k, w.map_vt, ap);
+        ++n;
+    };
+    auto embed = [&](int mode, const std::string& lp) {
+        EmbedParams ep{};
+        ep.x = x;
+        ep.blk = w.blk;
+        ep.counters = w.counters;
+        const std::string e = mode == 0 ? "emb." : "remb.";
+        ep.w1 = I(e + "w1");
+        ep.w2 = I(e + "w2");
+        ep.wqkv = I(lp + "wqkv");
+        ep.b1 = V(e + "b1");
+        ep.b2 = V(e + "b2");
+        ep.lng = V(lp + "ln1.g");
+        ep.lnb = V(lp + "ln1.b");
+        ep.bqkv = V(lp + "bqkv");
+        ep.z = w.tz;
+        ep.q = w.tq;
+        ep.k = w.tk;
+        ep.vt = w.tvt;
+        ep.ldvt = w.cap_tpad;
+        ep.status = m.status;
+        ep.wait_ns = (uint64_t)m.wait_limit_ns;
+        ep.act = c.act;
+        if (mode == 0)
+            k_embed_qkv<0><<<grid * 2, 128, embed_smem(0), st>>>(w.map_hp, ep);
+        else
+            k_embed_qkv<1><<<grid * 2, 128, embed_smem(1), st>>>(w.map_hp, ep);
+        ++n;
+    };
+    auto post = [&](int mode, const std::string& lp, const std::string& next) {
+        PostParams pp{};
+        pp.x = x;
+        pp.blk = w.blk;
+        pp.counters = w.counters;
+        pp.wo = I(lp + "wo");
+        pp.wup = I(lp + "ffn.w1");
+        pp.wdn = I(lp + "ffn.w2");
+        pp.bo = V(lp + "bo");
+        pp.ln2g = V(lp + "ln2.g");
+        pp.ln2b = V(lp + "ln2.b");
+        pp.bup = V(lp + "ffn.b1");
+        pp.bdn = V(lp + "ffn.b2");
+        if (mode == 0) {
+            pp.wa = I(next + "wqkv");
+            pp.wb = nullptr;
+            pp.lng = V(next + "ln1.g");
+            pp.lnb = V(next + "ln1.b");
+            pp.ba = V(next + "bqkv");
+        } else if (mode == 1) {
+            pp.wa = I("head.cls.w1");
+            pp.wb = I("head.cls.w2");
+            pp.lng = V("pid.lnf.g");
+            pp.lnb = V("pid.lnf.b");
+            pp.ba = V("head.cls.b1");
+            pp.bb = V("head.cls.b2");
+        } else {
+            pp.wa = I("head.reg.w1");
+            pp.wb = I("head.reg.w2");
+            pp.lng = V("reg.lnf.g");
+            pp.lnb = V("reg.lnf.b");
+            pp.ba = V("head.reg.b1");
+            pp.bb = V("head.reg.b2");
+        }
+        pp.z = w.tz;
+        pp.q = w.tq;
+        pp.k = w.tk;
+        pp.vt = w.tvt;
+        pp.hp = w.thp;
+        pp.ldvt = w.cap_tpad;
+        pp.logits = logits;
+        pp.reg = reg;
+        pp.status = m.status;
+        pp.wait_ns = (uint64_t)m.wait_limit_ns;
+        pp.act = c.act;
+        if (mode == 0)
+            k_post<0><<<grid, 128, post_smem(0), st>>>(w.map_o, pp);
+        else if (mode == 1)
+            k_post<1><<<grid, 128, post_smem(1), st>>>(w.map_o, pp);
+        else
+            k_post<2><<<grid, 128, post_smem(2), st>>>(w.map_o, pp);
+        ++n;
+    };
+    int layer = 0;
+    embed(0, "pid.0.");
+    for (int l = 0; l < c.l_pid; ++l) {
+        attention(layer++);
+        const std::string lp = "pid." + std::to_string(l) + ".";
+        if (l + 1 < c.l_pid)
+            post(0, lp, "pid." + std::to_string(l + 1) + ".");
+        else
+            post(1, lp, "");
+    }
+    embed(1, "reg.0.");
+    for (int l = 0; l < c.l_reg; ++l) {
+        attention(layer++);
+        const std::string lp = "reg." + std::to_string(l) + ".";
+        if (l + 1 < c.l_reg)
+            post(0, lp, "reg." + std::to_string(l + 1) + ".");
+        else
+            post(2, lp, "");
+    }
+    if (cudaPeekAtLastError() != cudaSuccess) return -1;
+    return n;
+}
+
+}  // namespace mlpf
