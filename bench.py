@@ -1,0 +1,448 @@
+#!/usr/bin/env python
+"""Throughput of the MLPF forward on synthetic pileup-like events.
+
+One step = one batched forward (embedding, PID encoder, regression encoder,
+heads, decode, FP64 event sums) over the 512-event workload: N ~ LogNormal
+(median 2500, sigma 0.5) clipped to [100, 12000] elements per event, model
+width 64, 4 heads of 16, FFN 256, 1 + 1 encoder blocks, seeded weights.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+instead, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WORKLOAD = "batch512"
+WORKLOAD_DESC = ("512 events, N ~ LogNormal(median 2500, sigma 0.5) clipped to [100, 12000], "
+                 "42 features; model d=64, 4 heads x 16, FFN 256, 1 PID + 1 regression block")
+METRIC = "events/s & p50 ms/event, MLPF forward, BF16/FP8 vs FP32 plain at stated error"
+HEADS = 4
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp16", "fp32"])
+    ap.add_argument("--no-baselines", action="store_true",
+                    help="skip the FP32-plain, per-event-latency and CPU-oracle legs")
+    ap.add_argument("--events", type=int, default=512,
+                    help="use only the first N events of the batch (small profiling captures)")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0,
+                    help="approximate CPU time budget of the oracle sample")
+    return ap.parse_args()
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(ws, v):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def allreduce_sum(ws, v):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.device)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [ln.strip().split(", ") for ln in self.f if ln.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = max(mx, float(r[2]))
+                for n, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(n)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+def attention_traffic():
+    """Per-launch DRAM bytes of the attention kernel from the committed ncu summary."""
+    p = os.path.join(ROOT, "profiles", "attention_batch512_traffic.txt")
+    if not os.path.exists(p):
+        return None
+    vals = {}
+    for ln in open(p):
+        if ":" in ln and not ln.lstrip().startswith("#"):
+            k, v = ln.split(":", 1)
+            vals[k.strip()] = v.strip()
+    try:
+        return float(vals["bytes_per_launch_full_workload"])
+    except (KeyError, ValueError):
+        return None
+
+
+def workload_inputs(rank, n_events=512):
+    cfg, wseed, iseed, sizes = synth.workload(WORKLOAD)
+    if rank > 0:  # weak scaling: every rank its own batch of the same distribution
+        iseed = iseed + 1000 * rank
+        sizes = synth.sizes_lognormal(iseed, len(sizes))
+    sizes = sizes[:n_events]
+    x, cu = synth.gen_events(iseed, sizes)
+    return cfg, wseed, x, cu, sizes
+
+
+# --------------------------------------------------------------------- oracle
+def oracle_sample(cfg, W, x, cu, budget_s, max_events=None):
+    """Time the FP64 oracle on the first events of the batch (i.i.d. sizes)."""
+    import oracle
+    out, t0, done = [], time.perf_counter(), 0
+    n = len(cu) - 1
+    while done < n and (max_events is None or done < max_events):
+        e = done
+        xs = x[cu[e]:cu[e + 1]]
+        lo, raw = oracle.forward_event(W, cfg, xs)
+        cls, reg = oracle.decode(xs, lo, raw)
+        sums = oracle.event_sums(cls, reg, [0, len(xs)])[0]
+        out.append((e, lo, reg, cls, sums))
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    return out, time.perf_counter() - t0
+
+
+def blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        info = threadpool_info()
+        return max((i.get("num_threads", 1) for i in info), default=1)
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_reference(args):
+    ws, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
+    if rank != 0:
+        return
+    import oracle
+    cfg, wseed, x, cu, sizes = workload_inputs(0)
+    W = synth.make_weights(cfg, wseed)
+    n = len(sizes)
+    ev = 0
+    for _ in range(args.warmup):
+        oracle.forward_event(W, cfg, x[cu[ev % n]:cu[ev % n + 1]])
+        ev += 1
+    t0 = time.perf_counter()
+    n_done = 0
+    for _ in range(args.steps):
+        e = ev % n
+        xs = x[cu[e]:cu[e + 1]]
+        lo, raw = oracle.forward_event(W, cfg, xs)
+        cls, reg = oracle.decode(xs, lo, raw)
+        oracle.event_sums(cls, reg, [0, len(xs)])
+        ev += 1
+        n_done += 1
+    dt = time.perf_counter() - t0
+    v = n_done / dt
+    cores = blas_threads()
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "events/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{WORKLOAD}: {WORKLOAD_DESC}",
+                       "sample": "one event of the batch per step, in generation order"},
+            "cpu_baseline": {"value": v, "unit": "events/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{n_done} events of the 512-event batch, one per step"},
+            "e2e": {"value": v, "unit": "events/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------ ours
+def run_ours(args):
+    import torch
+    from paper_2601_17554_b300 import Model, _lib
+
+    ws, rank, local = dist_setup()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    cfg, wseed, x, cu, sizes = workload_inputs(rank, args.events)
+    W = synth.make_weights(cfg, wseed)
+    model = Model(synth.pack_blob(cfg, W), device=local)
+    T, n_ev, max_n = x.shape[0], len(sizes), int(sizes.max())
+    xd = torch.from_numpy(x).to(dev)
+    cud = torch.from_numpy(cu).to(dev)
+    lo = torch.empty((T, 6), dtype=torch.float32, device=dev)
+    rg = torch.empty((T, 5), dtype=torch.float32, device=dev)
+    cl = torch.empty((T,), dtype=torch.int32, device=dev)
+    su = torch.empty((n_ev, 3), dtype=torch.float64, device=dev)
+    prec = args.precision
+
+    def step():
+        model.forward(xd, cud, max_n, precision=prec, logits=lo, reg=rg, cls=cl, event_sums=su)
+
+    model.set_option(_lib.OPT_PROFILE, 1)
+    for _ in range(max(args.warmup, 3)):
+        step()
+    model.sync()
+    names_buf = ctypes_buf = None
+    import ctypes
+    cap = 64
+    names_buf = ctypes.create_string_buffer(32 * cap)
+    ms_buf = (ctypes.c_float * cap)()
+    kernel_ms = {}
+
+    def read_profile():
+        n = model.L.mlpf_profile_get(model.h, cap, names_buf, ms_buf)
+        for i in range(min(n, cap)):
+            nm = names_buf.raw[32 * i:32 * (i + 1)].split(b"\0")[0].decode()
+            kernel_ms.setdefault(nm, []).append(ms_buf[i])
+
+    stream = torch.cuda.current_stream(dev)
+    clocks = Clocks(local)
+    barrier(ws)
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for _ in range(args.steps):
+        step()
+        read_profile()  # waits for this step's last kernel (graph-internal events)
+    t_end.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(ws)
+    clk = clocks.stop()
+    ms_total = t_start.elapsed_time(t_end)
+    ms_step = allreduce_max(ws, ms_total / args.steps)
+    launches_per_step = model.last_launch_count
+    model.sync()
+    events_all = allreduce_sum(ws, n_ev)
+    value = events_all / (ms_step / 1000.0)
+
+    # ---- end-to-end through the host-buffer C entry point (pinned host memory)
+    xh = torch.from_numpy(x).pin_memory()
+    cuh = torch.from_numpy(cu).pin_memory()
+    loh = torch.empty((T, 6), dtype=torch.float32).pin_memory()
+    rgh = torch.empty((T, 5), dtype=torch.float32).pin_memory()
+    clh = torch.empty((T,), dtype=torch.int32).pin_memory()
+    suh = torch.empty((n_ev, 3), dtype=torch.float64).pin_memory()
+    e2e_steps = max(3, min(args.steps, 10))
+    for _ in range(2):
+        model.forward_host(xh, cuh, max_n, precision=prec, logits=loh, reg=rgh, cls=clh, event_sums=suh)
+    barrier(ws)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        model.forward_host(xh, cuh, max_n, precision=prec, logits=loh, reg=rgh, cls=clh, event_sums=suh)
+    e2e_ms = allreduce_max(ws, 1000 * (time.perf_counter() - t0) / e2e_steps)
+    h2d = x.nbytes + cu.nbytes
+    d2h = T * 6 * 4 + T * 5 * 4 + T * 4 + n_ev * 3 * 8
+
+    # ---- roofline of the dominant kernel (attention): exponentials per launch
+    att = kernel_ms.get("attention", [])
+    att_ms = sum(att) / len(att) if att else None
+    exps = float(np.sum(sizes.astype(np.float64) ** 2)) * HEADS
+    peaks, peak_src = measured_peaks()
+    # MUFU ex2: 16 lanes per SM per clock (4 per SM sub-partition) x 148 SMs x max SM clock
+    exp_peak = 148 * 16 * peaks.get("sm_max_mhz", 2032.0) * 1e6
+    roof = None
+    if att_ms:
+        ach = exps / (att_ms / 1000.0)
+        roof = {"kernel": "k_attention", "bound": "alu", "achieved": ach / 1e9,
+                "peak": exp_peak / 1e9, "unit": "Gexp/s", "frac": ach / exp_peak,
+                "traffic": attention_traffic(),
+                "peak_source": f"derived: 148 SMs x 16 ex2/clk x {peaks.get('sm_max_mhz', 2032.0):.0f} MHz "
+                               f"(clock from MEASURED_PEAKS.json, {peak_src})",
+                "launch_ms": att_ms,
+                "algorithmic_exps_per_launch": exps,
+                "mma_tflops": 4 * float(np.sum(sizes.astype(np.float64) ** 2)) * 64 / (att_ms / 1000.0) / 1e12}
+    kernel_avg = {k: sum(v) / len(v) for k, v in kernel_ms.items()}
+
+    line = {"metric": METRIC, "value": value, "unit": "events/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": prec, "data": "synthetic",
+            "config": {"workload": f"{WORKLOAD}: {WORKLOAD_DESC}" +
+                       ("" if n_ev == 512 else f" (first {n_ev} events only)"), "events_per_gpu": n_ev,
+                       "elements_per_gpu": T, "precision": prec,
+                       "l2": "inputs larger than L2 (x is %.0f MB > 126 MB)" % (x.nbytes / 1e6),
+                       "parallelism": f"replicas x{ws} (events shard, no collective)"},
+            "batch_ms_per_event": ms_step / n_ev,
+            "gpu_launches": int(launches_per_step * args.steps),
+            "kernel_ms": kernel_avg,
+            "roofline": roof,
+            "e2e": {"value": events_all / (e2e_ms / 1000.0), "unit": "events/s",
+                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                    "ms_per_step": e2e_ms},
+            "clocks": clk}
+
+    if not args.no_baselines and rank == 0:
+        # ---- per-event latency: each event alone, one launch sequence per event
+        model.set_option(_lib.OPT_USE_GRAPHS, 0)
+        model.set_option(_lib.OPT_PROFILE, 0)
+        lat = []
+        ev_s, ev_e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for e in range(n_ev):
+            xs = xd[cu[e]:cu[e + 1]]
+            cs = torch.tensor([0, int(sizes[e])], dtype=torch.int32, device=dev)
+            if e == 0:
+                model.forward(xs, cs, int(sizes[e]), precision=prec)
+            ev_s.record(stream)
+            model.forward(xs, cs, int(sizes[e]), precision=prec)
+            ev_e.record(stream)
+            ev_e.synchronize()
+            lat.append(ev_s.elapsed_time(ev_e))
+        line["p50_ms_per_event"] = float(np.percentile(lat, 50))
+        line["p99_ms_per_event"] = float(np.percentile(lat, 99))
+        line["latency_note"] = "each event run alone (no graph), CUDA events on the stream"
+        # ---- plain FP32 baseline: the same batch as 512 separate FP32 launch sequences
+        model.forward(xd[:int(sizes[0])], torch.tensor([0, int(sizes[0])], dtype=torch.int32,
+                                                         device=dev), int(sizes[0]), precision="fp32")
+        torch.cuda.synchronize(dev)
+        t_s = torch.cuda.Event(enable_timing=True)
+        t_e = torch.cuda.Event(enable_timing=True)
+        cs_all = [torch.tensor([0, int(sizes[e])], dtype=torch.int32, device=dev) for e in range(n_ev)]
+        t_s.record(stream)
+        for e in range(n_ev):
+            model.forward(xd[cu[e]:cu[e + 1]], cs_all[e], int(sizes[e]), precision="fp32",
+                          logits=lo[cu[e]:cu[e + 1]], reg=rg[cu[e]:cu[e + 1]],
+                          cls=cl[cu[e]:cu[e + 1]], event_sums=su[e:e + 1])
+        t_e.record(stream)
+        torch.cuda.synchronize(dev)
+        fp32_ms = t_s.elapsed_time(t_e)
+        model.sync()
+        line["fp32_plain"] = {"value": n_ev / (fp32_ms / 1000.0), "unit": "events/s",
+                              "ms_per_batch": fp32_ms,
+                              "how": "512 separate per-event FP32 SIMT launch sequences"}
+        line["speedup_vs_fp32_plain"] = (ms_step and fp32_ms / ms_step)
+        model.set_option(_lib.OPT_USE_GRAPHS, 1)
+        # ---- CPU oracle on a bounded sample, and the error of the GPU outputs on it
+        step()
+        model.sync()
+        glo, grg, gcl, gsu = lo.cpu().numpy(), rg.cpu().numpy(), cl.cpu().numpy(), su.cpu().numpy()
+        samp, cpu_s = oracle_sample(cfg, W, x, cu, args.cpu_seconds)
+        nsamp = len(samp)
+        line["cpu_baseline"] = {"value": nsamp / cpu_s, "unit": "events/s", "cores": blas_threads(),
+                                "kind": "oracle",
+                                "sample": f"first {nsamp} events of the batch (i.i.d. sizes), "
+                                          f"{cpu_s:.1f} s, numpy float64 with BLAS matmuls"}
+        import oracle
+        agree, num, den, raw_err, same_cls_err = [], 0.0, 0.0, [], []
+        for e, olo, oreg, ocls, osum in samp:
+            sl = slice(cu[e], cu[e + 1])
+            agree.append(gcl[sl] == ocls)
+            num = num + ((grg[sl] - oreg) ** 2).sum(0)
+            den = den + (oreg ** 2).sum(0)
+            scale = max(np.abs(osum).max(), 1e-12)
+            raw_err.append(np.abs(gsu[e] - osum).max() / scale)
+            # the oracle's regressions summed over the GPU's selected elements
+            osum_g = oracle.event_sums(gcl[sl], oreg, [0, len(ocls)])[0]
+            same_cls_err.append(np.abs(gsu[e] - osum_g).max() / scale)
+        ag = np.concatenate(agree)
+        line["error_vs_oracle"] = {
+            "events": nsamp, "elements": int(ag.size), "argmax_agreement": float(ag.mean()),
+            "reg_rel_err_per_column": [float(v) for v in np.sqrt(num / den)],
+            "event_sum_rel_err_max": float(max(raw_err)),
+            "event_sum_rel_err_max_same_classes": float(max(same_cls_err)),
+            "note": "event sums relative to max |component|; 'same_classes' sums the oracle's "
+                    "regressions over the GPU's selected elements"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    model.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -44,7 +44,8 @@ typedef enum {
 typedef enum {
     MLPF_FP32 = 0, /* plain path: SIMT FP32 FFMA GEMMs and attention, no TF32 */
     MLPF_BF16 = 1, /* tcgen05 tensor cores, BF16 operands, FP32 accumulation */
-    MLPF_FP8 = 2   /* E4M3 projection/FFN GEMMs with per-tensor scales (BF16 attention) */
+    MLPF_FP8 = 2,  /* E4M3 projection/FFN GEMMs with per-tensor scales (16-bit attention) */
+    MLPF_FP16 = 3  /* as MLPF_BF16 with FP16 operands (same tensor-core rate, 3 more mantissa bits) */
 } mlpf_precision;
 
 /* Model configuration, as stored in the weight blob header. */
@@ -143,7 +144,9 @@ enum {
     MLPF_OPT_DEBUG_STALL = 3,       /* 1: attention consumers wait on a barrier nothing
                                        arms, to exercise the timeout path (tests only) */
     MLPF_OPT_ATTN_CTAS_PER_SM = 4,  /* attention persistent grid size factor (autotuned) */
-    MLPF_OPT_ATTN_KV_STAGES = 5     /* read-only in this build: K/V pipeline depth */
+    MLPF_OPT_ATTN_KV_STAGES = 5,    /* read-only in this build: K/V pipeline depth */
+    MLPF_OPT_PROFILE = 6            /* 1: CUDA events around every kernel launch (also
+                                       inside captured graphs); see mlpf_profile_get */
 };
 mlpf_status mlpf_set_option(mlpf_model* m, int32_t option, int64_t value);
 mlpf_status mlpf_get_option(const mlpf_model* m, int32_t option, int64_t* value);
@@ -153,6 +156,16 @@ mlpf_status mlpf_get_option(const mlpf_model* m, int32_t option, int64_t* value)
  * counted on the host at launch (a graph replay counts its kernel nodes).
  */
 int64_t mlpf_last_launch_count(const mlpf_model* m);
+
+/*
+ * Per-kernel device times of the most recent forward made with MLPF_OPT_PROFILE
+ * on (for a graph replay: of that replay).  Waits for the last kernel.
+ * names: host out or NULL, cap x 32 bytes (NUL-terminated kernel names);
+ * ms: host out or NULL, cap floats (milliseconds, CUDA-event resolution).
+ * Returns the number of profiled launches (may exceed cap), 0 when profiling
+ * is off, -1 on error.
+ */
+int32_t mlpf_profile_get(mlpf_model* m, int32_t cap, char* names, float* ms);
 
 /* Thread-local message describing the last non-OK status of this thread. */
 const char* mlpf_last_error(void);

@@ -11,10 +11,10 @@ from __future__ import annotations
 import ctypes
 
 from . import _lib
-from ._lib import (MLPF_FP32, MLPF_BF16, MLPF_FP8, MlpfError, check,  # noqa: F401
+from ._lib import (MLPF_FP32, MLPF_BF16, MLPF_FP8, MLPF_FP16, MlpfError, check,  # noqa: F401
                    OPT_USE_GRAPHS, OPT_WAIT_LIMIT_NS, OPT_DEBUG_STALL)
 
-PRECISIONS = {"fp32": MLPF_FP32, "bf16": MLPF_BF16, "fp8": MLPF_FP8}
+PRECISIONS = {"fp32": MLPF_FP32, "bf16": MLPF_BF16, "fp8": MLPF_FP8, "fp16": MLPF_FP16}
 
 
 def _ptr(t):

@@ -9,13 +9,14 @@ LIB_PATH = os.path.join(HERE, "libmlpf.so")
 
 MLPF_OK, MLPF_E_INVALID, MLPF_E_FORMAT, MLPF_E_CUDA, MLPF_E_OOM, MLPF_E_TIMEOUT, \
     MLPF_E_NONFINITE, MLPF_E_UNSUPPORTED = range(8)
-MLPF_FP32, MLPF_BF16, MLPF_FP8 = 0, 1, 2
-OPT_USE_GRAPHS, OPT_WAIT_LIMIT_NS, OPT_DEBUG_STALL, OPT_ATTN_CTAS_PER_SM, OPT_ATTN_KV_STAGES = 1, 2, 3, 4, 5
+MLPF_FP32, MLPF_BF16, MLPF_FP8, MLPF_FP16 = 0, 1, 2, 3
+OPT_USE_GRAPHS, OPT_WAIT_LIMIT_NS, OPT_DEBUG_STALL, OPT_ATTN_CTAS_PER_SM, OPT_ATTN_KV_STAGES, \
+    OPT_PROFILE = 1, 2, 3, 4, 5, 6
 
 # every symbol include/mlpf.h declares
 EXPORTS = ("mlpf_load_weights", "mlpf_free", "mlpf_get_config", "mlpf_forward",
            "mlpf_forward_host", "mlpf_sync", "mlpf_set_option", "mlpf_get_option",
-           "mlpf_last_launch_count", "mlpf_last_error", "mlpf_abi_version")
+           "mlpf_last_launch_count", "mlpf_profile_get", "mlpf_last_error", "mlpf_abi_version")
 
 
 class MlpfConfig(ctypes.Structure):
@@ -57,6 +58,8 @@ def load(build_if_missing: bool = True):
     L.mlpf_get_option.restype = ctypes.c_int
     L.mlpf_last_launch_count.argtypes = [vp]
     L.mlpf_last_launch_count.restype = i64
+    L.mlpf_profile_get.argtypes = [vp, i32, ctypes.c_char_p, ctypes.POINTER(ctypes.c_float)]
+    L.mlpf_profile_get.restype = i32
     L.mlpf_last_error.argtypes = []
     L.mlpf_last_error.restype = ctypes.c_char_p
     L.mlpf_abi_version.argtypes = []

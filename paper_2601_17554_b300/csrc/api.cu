@@ -17,6 +17,35 @@ namespace mlpf {
 static thread_local std::string g_last_error;
 void set_error(const std::string& msg) { g_last_error = msg; }
 
+void prof_begin(Model& m, cudaStream_t st, const char* name) {
+    Profile* p = m.cur_prof;
+    if (!m.profile || !p) return;
+    if ((int)p->ev.size() < 2 * (p->n + 1)) {
+        cudaEvent_t a, b;
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        p->ev.push_back(a);
+        p->ev.push_back(b);
+    }
+    if ((int)p->names.size() <= p->n) p->names.resize(p->n + 1);
+    p->names[p->n] = name;
+    cudaEventRecordWithFlags(p->ev[2 * p->n], st, cudaEventRecordExternal);
+}
+
+void prof_end(Model& m, cudaStream_t st) {
+    Profile* p = m.cur_prof;
+    if (!m.profile || !p) return;
+    cudaEventRecordWithFlags(p->ev[2 * p->n + 1], st, cudaEventRecordExternal);
+    ++p->n;
+}
+
+static void prof_destroy(Profile& p) {
+    for (cudaEvent_t e : p.ev) cudaEventDestroy(e);
+    p.ev.clear();
+    p.names.clear();
+    p.n = 0;
+}
+
 bool GraphKey::operator<(const GraphKey& o) const {
     return std::tie(prec, x, cu, lo, rg, cl, su, n_events, total, max_n) <
            std::tie(o.prec, o.x, o.cu, o.lo, o.rg, o.cl, o.su, o.n_events, o.total, o.max_n);
@@ -194,8 +223,9 @@ static mlpf_status ensure_workspace(Model& m, int total, int n_events, bool tc) 
         cudaFree(w.base);
         w = Workspace{};
     }
-    for (auto& g : m.graphs) cudaGraphExecDestroy(g.second.first);
+    for (auto& g : m.graphs) { cudaGraphExecDestroy(g.second.exec); prof_destroy(g.second.prof); }
     m.graphs.clear();
+    m.last_prof = nullptr;
     const mlpf_config& c = m.cfg;
     const size_t d = c.d, F = c.ffn;
     size_t off = 0;
@@ -254,13 +284,17 @@ static mlpf_status validate(const Model* m, int32_t prec, const void* x, const v
                             int32_t n_events, int32_t total, int32_t max_n, const void* logits,
                             const void* reg) {
     if (!m) { set_error("model is NULL"); return MLPF_E_INVALID; }
-    if (prec < 0 || prec > 2) { set_error("unknown precision " + std::to_string(prec)); return MLPF_E_INVALID; }
+    if (prec < 0 || prec > 3) { set_error("unknown precision " + std::to_string(prec)); return MLPF_E_INVALID; }
     if (n_events < 0 || total < 0 || max_n < 0) { set_error("negative size"); return MLPF_E_INVALID; }
     if (max_n > 65536) { set_error("max_n above 65536"); return MLPF_E_INVALID; }
     if (total > 0 && max_n == 0) { set_error("max_n = 0 with total > 0"); return MLPF_E_INVALID; }
     if (total > 0 && n_events == 0) { set_error("total > 0 with no events"); return MLPF_E_INVALID; }
     if (total > 0 && (!x || !cu || !logits || !reg)) { set_error("NULL input or output pointer"); return MLPF_E_INVALID; }
     if (n_events > 0 && !cu) { set_error("cu_seqlens is NULL"); return MLPF_E_INVALID; }
+    if (prec == MLPF_FP8) {
+        set_error("the FP8 path is not built in this version");
+        return MLPF_E_UNSUPPORTED;
+    }
     if (prec != MLPF_FP32 && !m->tc_supported) {
         set_error("tensor-core path is built for d=64, 4 heads, FFN 256 models only");
         return MLPF_E_UNSUPPORTED;
@@ -306,7 +340,11 @@ static mlpf_status forward_impl(Model& m, int32_t prec, const float* x, const in
     }
     if (!m.use_graphs) {
         int64_t n = 0;
+        m.direct_prof.n = 0;
+        m.cur_prof = &m.direct_prof;
         s = launch_sequence(m, prec, x, cu, n_events, total, max_n, logits, reg, cls, sums, st, n);
+        m.cur_prof = nullptr;
+        m.last_prof = &m.direct_prof;
         m.last_launches = n;
         return s;
     }
@@ -314,26 +352,36 @@ static mlpf_status forward_impl(Model& m, int32_t prec, const float* x, const in
     auto it = m.graphs.find(key);
     if (it == m.graphs.end()) {
         if (m.graphs.size() >= 16) {
-            cudaGraphExecDestroy(m.graphs.begin()->second.first);
-            m.graphs.erase(m.graphs.begin());
+            auto victim = m.graphs.begin();
+            if (m.last_prof == &victim->second.prof) m.last_prof = nullptr;
+            cudaGraphExecDestroy(victim->second.exec);
+            prof_destroy(victim->second.prof);
+            m.graphs.erase(victim);
         }
         if (!m.cap_stream) CK(cudaStreamCreateWithFlags(&m.cap_stream, cudaStreamNonBlocking));
+        Profile prof;
+        m.cur_prof = &prof;
         CK(cudaStreamBeginCapture(m.cap_stream, cudaStreamCaptureModeThreadLocal));
         int64_t n = 0;
         mlpf_status ls = launch_sequence(m, prec, x, cu, n_events, total, max_n, logits, reg, cls,
                                          sums, m.cap_stream, n);
+        m.cur_prof = nullptr;
         cudaGraph_t g = nullptr;
         cudaError_t ce = cudaStreamEndCapture(m.cap_stream, &g);
-        if (ls != MLPF_OK) { if (g) cudaGraphDestroy(g); return ls; }
-        if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
+        if (ls != MLPF_OK || ce != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            prof_destroy(prof);
+            return ls != MLPF_OK ? ls : cuda_fail(ce, "cudaStreamEndCapture");
+        }
         cudaGraphExec_t ex = nullptr;
         ce = cudaGraphInstantiate(&ex, g, 0);
         cudaGraphDestroy(g);
-        if (ce != cudaSuccess) return cuda_fail(ce, "cudaGraphInstantiate");
-        it = m.graphs.emplace(key, std::make_pair(ex, n)).first;
+        if (ce != cudaSuccess) { prof_destroy(prof); return cuda_fail(ce, "cudaGraphInstantiate"); }
+        it = m.graphs.emplace(key, Model::GraphEntry{ex, n, prof}).first;
     }
-    CK(cudaGraphLaunch(it->second.first, st));
-    m.last_launches = it->second.second;
+    CK(cudaGraphLaunch(it->second.exec, st));
+    m.last_launches = it->second.launches;
+    m.last_prof = &it->second.prof;
     return MLPF_OK;
 }
 
@@ -403,7 +451,8 @@ void mlpf_free(mlpf_model* mm) {
     if (!mm) return;
     Model& m = mm->impl;
     cudaSetDevice(m.device);
-    for (auto& g : m.graphs) cudaGraphExecDestroy(g.second.first);
+    for (auto& g : m.graphs) { cudaGraphExecDestroy(g.second.exec); prof_destroy(g.second.prof); }
+    prof_destroy(m.direct_prof);
     if (m.cap_stream) cudaStreamDestroy(m.cap_stream);
     if (m.ws.base) cudaFree(m.ws.base);
     if (m.w.f32_base) cudaFree(m.w.f32_base);
@@ -486,6 +535,7 @@ mlpf_status mlpf_set_option(mlpf_model* mm, int32_t option, int64_t value) {
             m.wait_limit_ns = value;
             break;
         case MLPF_OPT_DEBUG_STALL: m.debug_stall = value != 0; break;
+        case MLPF_OPT_PROFILE: m.profile = value != 0; break;
         case MLPF_OPT_ATTN_CTAS_PER_SM:
             if (value < 1 || value > 1) { set_error("attention runs one CTA per SM in this build"); return MLPF_E_INVALID; }
             m.attn_ctas_per_sm = (int)value;
@@ -494,8 +544,9 @@ mlpf_status mlpf_set_option(mlpf_model* mm, int32_t option, int64_t value) {
     }
     // options baked into captured graphs: drop them
     cudaSetDevice(m.device);
-    for (auto& g : m.graphs) cudaGraphExecDestroy(g.second.first);
+    for (auto& g : m.graphs) { cudaGraphExecDestroy(g.second.exec); prof_destroy(g.second.prof); }
     m.graphs.clear();
+    m.last_prof = nullptr;
     return MLPF_OK;
 }
 
@@ -508,10 +559,33 @@ mlpf_status mlpf_get_option(const mlpf_model* mm, int32_t option, int64_t* value
         case MLPF_OPT_DEBUG_STALL: *value = m.debug_stall; return MLPF_OK;
         case MLPF_OPT_ATTN_CTAS_PER_SM: *value = m.attn_ctas_per_sm; return MLPF_OK;
         case MLPF_OPT_ATTN_KV_STAGES: *value = 4; return MLPF_OK;
+        case MLPF_OPT_PROFILE: *value = m.profile; return MLPF_OK;
         default: set_error("unknown option " + std::to_string(option)); return MLPF_E_INVALID;
     }
 }
 
 int64_t mlpf_last_launch_count(const mlpf_model* m) { return m ? m->impl.last_launches : -1; }
+
+int32_t mlpf_profile_get(mlpf_model* mm, int32_t cap, char* names, float* ms) {
+    if (!mm) { set_error("model is NULL"); return -1; }
+    Model& m = mm->impl;
+    const Profile* p = m.last_prof;
+    if (!p || !m.profile) return 0;
+    cudaSetDevice(m.device);
+    for (int i = 0; i < p->n && i < cap; ++i) {
+        if (cudaEventSynchronize(p->ev[2 * i + 1]) != cudaSuccess) { set_error("event sync failed"); return -1; }
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, p->ev[2 * i], p->ev[2 * i + 1]) != cudaSuccess) {
+            set_error("cudaEventElapsedTime failed");
+            return -1;
+        }
+        if (ms) ms[i] = t;
+        if (names) {
+            std::memset(names + 32 * i, 0, 32);
+            std::strncpy(names + 32 * i, p->names[i].c_str(), 31);
+        }
+    }
+    return p->n;
+}
 
 }  // extern "C"

@@ -36,7 +36,8 @@ struct DeviceWeights {
     std::vector<float*> wqkv_pid, bqkv_pid, wqkv_reg, bqkv_reg;
     // tensor-core path (d = 64 model only): bf16 128B-swizzled weight images
     uint8_t* img_base = nullptr;
-    std::map<std::string, uint8_t*> img;  // name -> device pointer of the image
+    std::map<std::string, uint8_t*> img;    // name -> device pointer of the BF16 image
+    std::map<std::string, uint8_t*> img_h;  // name -> device pointer of the FP16 image
     std::map<std::string, uint32_t> img_bytes;
     float* tc_f32_base = nullptr;         // fused bias vectors for the tensor-core kernels
     std::map<std::string, float*> tcv;
@@ -76,6 +77,14 @@ struct GraphKey {
     bool operator<(const GraphKey& o) const;
 };
 
+// CUDA events around each kernel launch (MLPF_OPT_PROFILE); captured into
+// graphs as external event-record nodes so replays re-record them.
+struct Profile {
+    std::vector<std::string> names;
+    std::vector<cudaEvent_t> ev;  // 2 per launch
+    int n = 0;
+};
+
 struct Model {
     int device = 0;
     mlpf_config cfg{};
@@ -90,10 +99,24 @@ struct Model {
     int64_t wait_limit_ns = 2000000000LL;
     bool debug_stall = false;
     int attn_ctas_per_sm = 1;
+    int embed_ctas_per_sm = 1;   // measured occupancy of the embedding kernels
     int64_t last_launches = 0;
     cudaStream_t cap_stream = nullptr;
-    std::map<GraphKey, std::pair<cudaGraphExec_t, int64_t>> graphs;
+    struct GraphEntry {
+        cudaGraphExec_t exec;
+        int64_t launches;
+        Profile prof;
+    };
+    std::map<GraphKey, GraphEntry> graphs;
+    bool profile = false;
+    Profile* cur_prof = nullptr;   // profile being recorded by the launch sequence
+    Profile direct_prof;           // profile of the last non-graph forward
+    const Profile* last_prof = nullptr;
 };
+
+// Record the start / end of one kernel launch when profiling is on.
+void prof_begin(Model& m, cudaStream_t st, const char* name);
+void prof_end(Model& m, cudaStream_t st);
 
 // launch sequences (return number of kernels launched, or -1 on launch error)
 int64_t run_forward_f32(Model& m, const float* x, const int32_t* cu, int n_events, int total,

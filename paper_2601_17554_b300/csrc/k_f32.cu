@@ -198,20 +198,26 @@ __global__ void k_decode(const float* __restrict__ x, const float* __restrict__ 
     o[4] = expf(x[(size_t)r * 42 + 9] + a[4]);
 }
 
-// One warp per event: class = argmax (lowest index on ties); FP64 sums of
-// -px, -py and pT over elements with class != 0, lanes stride over the rows
-// and a fixed xor-butterfly combines them (deterministic).
-__global__ void k_event_sums(const int32_t* __restrict__ cu, int n_events,
-                             const float* __restrict__ logits, const float* __restrict__ reg,
-                             int32_t* __restrict__ cls_out, double* __restrict__ sums, int n_cls,
-                             unsigned* status) {
-    const int e = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (e >= n_events) return;
+// One block of 256 threads per event: class = argmax (lowest index on ties);
+// FP64 sums of -px, -py and pT over elements with class != 0.  Threads stride
+// over the event's rows; the partial sums are combined by a fixed xor
+// butterfly per warp and then in warp order, so the result is deterministic.
+__global__ void __launch_bounds__(256) k_event_sums(const int32_t* __restrict__ cu, int n_events,
+                                                    const float* __restrict__ logits,
+                                                    const float* __restrict__ reg,
+                                                    int32_t* __restrict__ cls_out,
+                                                    double* __restrict__ sums, int n_cls,
+                                                    unsigned* status) {
+    __shared__ double part[3][8];
+    __shared__ int bad;
+    const int e = blockIdx.x;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x == 0) bad = 0;
+    __syncthreads();
     const int s = cu[e], t = cu[e + 1];
     double px = 0.0, py = 0.0, pt = 0.0;
     bool finite = true;
-    for (int r = s + lane; r < t; r += 32) {
+    for (int r = s + threadIdx.x; r < t; r += 256) {
         const float* lo = logits + (size_t)r * n_cls;
         int best = 0;
         float bv = lo[0];
@@ -241,11 +247,26 @@ __global__ void k_event_sums(const int32_t* __restrict__ cu, int n_events,
         py += __shfl_xor_sync(0xffffffffu, py, o);
         pt += __shfl_xor_sync(0xffffffffu, pt, o);
     }
-    if (!__all_sync(0xffffffffu, finite) && lane == 0) atomicOr(status, ST_NONFINITE);
-    if (lane == 0 && sums) {
-        sums[(size_t)e * 3 + 0] = -px;
-        sums[(size_t)e * 3 + 1] = -py;
-        sums[(size_t)e * 3 + 2] = pt;
+    if (!finite) bad = 1;
+    if (lane == 0) {
+        part[0][wid] = px;
+        part[1][wid] = py;
+        part[2][wid] = pt;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+        for (int w = 0; w < 8; ++w) {
+            a0 += part[0][w];
+            a1 += part[1][w];
+            a2 += part[2][w];
+        }
+        if (bad) atomicOr(status, ST_NONFINITE);
+        if (sums) {
+            sums[(size_t)e * 3 + 0] = -a0;
+            sums[(size_t)e * 3 + 1] = -a1;
+            sums[(size_t)e * 3 + 2] = a2;
+        }
     }
 }
 
@@ -253,17 +274,23 @@ inline unsigned cdiv(long a, long b) { return (unsigned)((a + b - 1) / b); }
 
 }  // namespace
 
+static Model* g_model = nullptr;  // model of the launch sequence being recorded
+
 static void linear(const float* X1, int ld1, int K1, const float* X2, int ld2, int K2,
                    const float* W, const float* b, const float* R, int ldr, float* Y, int ldy,
                    int T, int N, int act, cudaStream_t st, int64_t& n) {
     dim3 grid(cdiv(N, LIN_BN), cdiv(T, LIN_BM));
+    prof_begin(*g_model, st, "f32_linear");
     k_linear<<<grid, 256, 0, st>>>(X1, ld1, K1, X2, ld2, K2, W, b, R, ldr, Y, ldy, T, N, act);
+    prof_end(*g_model, st);
     ++n;
 }
 
 static void layernorm(const float* X, const float* g, const float* b, float* Y, int T, int d,
                       cudaStream_t st, int64_t& n) {
+    prof_begin(*g_model, st, "f32_layernorm");
     k_layernorm<<<cdiv(T, 8), 256, 0, st>>>(X, g, b, Y, T, d);
+    prof_end(*g_model, st);
     ++n;
 }
 
@@ -274,6 +301,7 @@ int64_t run_forward_f32(Model& m, const float* x, const int32_t* cu, int n_event
     Workspace& w = m.ws;
     auto W = [&](const std::string& s) { return m.w.f32.at(s); };
     int64_t n = 0;
+    g_model = &m;
     const float scale = 1.0f / sqrtf((float)dh);
 
     auto stack = [&](const char* prefix, int layers, std::vector<float*>& wqkv,
@@ -284,12 +312,14 @@ int64_t run_forward_f32(Model& m, const float* x, const int32_t* cu, int n_event
             linear(w.zn, d, d, nullptr, 0, 0, wqkv[l], bqkv[l], nullptr, 0, w.qkv, 3 * d, T, 3 * d,
                    -1, st, n);
             dim3 grid(cdiv(max_n, 64), c.heads, n_events);
+            prof_begin(m, st, "f32_attention");
             if (dh == 16)
                 k_attention<16><<<grid, 64, 0, st>>>(w.qkv, w.o, cu, d, scale);
             else if (dh == 32)
                 k_attention<32><<<grid, 64, 0, st>>>(w.qkv, w.o, cu, d, scale);
             else
                 k_attention<64><<<grid, 64, 0, st>>>(w.qkv, w.o, cu, d, scale);
+            prof_end(m, st);
             ++n;
             linear(w.o, d, d, nullptr, 0, 0, W(p + "wo"), W(p + "bo"), w.z, d, w.z, d, T, d, -1, st,
                    n);
@@ -329,7 +359,9 @@ int64_t run_forward_f32(Model& m, const float* x, const int32_t* cu, int n_event
                widths[h], -1, st, n);
         off += widths[h];
     }
+    prof_begin(m, st, "f32_decode");
     k_decode<<<cdiv(T, 256), 256, 0, st>>>(x, w.raw, reg, T);
+    prof_end(m, st);
     ++n;
     if (cudaPeekAtLastError() != cudaSuccess) return -1;
     return n;
@@ -339,8 +371,9 @@ int64_t run_event_sums(Model& m, const int32_t* cu, int n_events, const float* l
                        const float* reg, int32_t* cls, double* sums, int n_cls,
                        cudaStream_t st) {
     if (n_events <= 0 || (!cls && !sums)) return 0;
-    k_event_sums<<<cdiv(n_events, 8), 256, 0, st>>>(cu, n_events, logits, reg, cls, sums, n_cls,
-                                                     m.status);
+    prof_begin(m, st, "event_sums");
+    k_event_sums<<<n_events, 256, 0, st>>>(cu, n_events, logits, reg, cls, sums, n_cls, m.status);
+    prof_end(m, st);
     if (cudaPeekAtLastError() != cudaSuccess) return -1;
     return 1;
 }

@@ -19,6 +19,8 @@
 // per-thread FP32 sums with no cross-thread reduction.
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -47,13 +49,16 @@ MLPF_DEV float act_f(float v, int act) { return act == 1 ? fmaxf(v, 0.f) : gelu_
 
 // Issue a [128 x K] x [N x K]^T GEMM from swizzled smem tiles into TMEM columns.
 // a_ncols_atoms: K/64.  b tile: N rows per atom column.
-MLPF_DEV void issue_gemm(uint32_t d_tmem, const uint8_t* a, const uint8_t* b, int N, int katoms) {
-    const uint32_t idesc = idesc_f16(128, N, 1);
+// accumulate: add to the existing accumulator from the first k-step on.
+template <bool F16>
+MLPF_DEV void issue_gemm(uint32_t d_tmem, const uint8_t* a, const uint8_t* b, int N, int katoms,
+                         bool accumulate = false) {
+    const uint32_t idesc = idesc_f16(128, N, F16 ? 0u : 1u);
     const uint32_t a0 = smem_u32(a), b0 = smem_u32(b);
     for (int kc = 0; kc < katoms * 4; ++kc) {
         const uint32_t ao = a0 + (kc >> 2) * ATOM + (kc & 3) * 32;
         const uint32_t bo = b0 + (kc >> 2) * (N * 128) + (kc & 3) * 32;
-        mma_f16(d_tmem, sdesc_sw128(ao), sdesc_sw128(bo), idesc, kc > 0 ? 1u : 0u);
+        mma_f16(d_tmem, sdesc_sw128(ao), sdesc_sw128(bo), idesc, (kc > 0 || accumulate) ? 1u : 0u);
     }
 }
 
@@ -64,28 +69,30 @@ MLPF_DEV void ld_row64(uint32_t taddr, float* v) {
     tmem_wait_ld();
 }
 
-// Store 64 floats of row r as bf16 into atom column `tile` (swizzled).
-MLPF_DEV void st_row_bf16(uint8_t* tile, int r, const float* v) {
+// Store 64 floats of row r in the 16-bit operand format into atom column `tile` (swizzled).
+template <bool F16>
+MLPF_DEV void st_row16(uint8_t* tile, int r, const float* v) {
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
         uint4 u;
-        u.x = pack_bf16x2(v[8 * c + 0], v[8 * c + 1]);
-        u.y = pack_bf16x2(v[8 * c + 2], v[8 * c + 3]);
-        u.z = pack_bf16x2(v[8 * c + 4], v[8 * c + 5]);
-        u.w = pack_bf16x2(v[8 * c + 6], v[8 * c + 7]);
+        u.x = pack2<F16>(v[8 * c + 0], v[8 * c + 1]);
+        u.y = pack2<F16>(v[8 * c + 2], v[8 * c + 3]);
+        u.z = pack2<F16>(v[8 * c + 4], v[8 * c + 5]);
+        u.w = pack2<F16>(v[8 * c + 6], v[8 * c + 7]);
         *(uint4*)(tile + sw128_off(r, c)) = u;
     }
 }
 
-MLPF_DEV void st_global_bf16_row64(__nv_bfloat16* dst, const float* v) {
+template <bool F16>
+MLPF_DEV void st_global_row64(uint16_t* dst, const float* v) {
     uint4* d4 = (uint4*)dst;
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
         uint4 u;
-        u.x = pack_bf16x2(v[8 * c + 0], v[8 * c + 1]);
-        u.y = pack_bf16x2(v[8 * c + 2], v[8 * c + 3]);
-        u.z = pack_bf16x2(v[8 * c + 4], v[8 * c + 5]);
-        u.w = pack_bf16x2(v[8 * c + 6], v[8 * c + 7]);
+        u.x = pack2<F16>(v[8 * c + 0], v[8 * c + 1]);
+        u.y = pack2<F16>(v[8 * c + 2], v[8 * c + 3]);
+        u.z = pack2<F16>(v[8 * c + 4], v[8 * c + 5]);
+        u.w = pack2<F16>(v[8 * c + 6], v[8 * c + 7]);
         d4[c] = u;
     }
 }
@@ -109,6 +116,7 @@ MLPF_DEV void layernorm64(const float* z, float* out, const float* g, const floa
 
 // Load this row's 42 input features, convert to bf16 and store them (zero
 // padded to 64 columns) into the swizzled atom column.
+template <bool F16>
 MLPF_DEV void load_x_row(uint8_t* tile, int r, const float* x, bool valid, int prow) {
     float v[64];
 #pragma unroll
@@ -122,7 +130,7 @@ MLPF_DEV void load_x_row(uint8_t* tile, int r, const float* x, bool valid, int p
             v[2 * i + 1] = t.y;
         }
     }
-    st_row_bf16(tile, r, v);
+    st_row16<F16>(tile, r, v);
 }
 
 struct RowInfo {
@@ -141,22 +149,23 @@ MLPF_DEV RowInfo row_info(const int4* blk, int nblk, int p) {
 }
 
 // Q, K rows and transposed V (zero for padding rows) from the QKV accumulator.
-MLPF_DEV void store_qkv(uint32_t tacc, const float* bqkv, int p, bool valid, __nv_bfloat16* q,
-                        __nv_bfloat16* k, __nv_bfloat16* vt, long ldvt) {
+template <bool F16>
+MLPF_DEV void store_qkv(uint32_t tacc, const float* bqkv, int p, bool valid, uint16_t* q,
+                        uint16_t* k, uint16_t* vt, long ldvt) {
     float v[64];
     ld_row64(tacc, v);
 #pragma unroll
     for (int i = 0; i < 64; ++i) v[i] += __ldg(bqkv + i);
-    st_global_bf16_row64(q + (size_t)p * D, v);
+    st_global_row64<F16>(q + (size_t)p * D, v);
     ld_row64(tacc + 64, v);
 #pragma unroll
     for (int i = 0; i < 64; ++i) v[i] += __ldg(bqkv + 64 + i);
-    st_global_bf16_row64(k + (size_t)p * D, v);
+    st_global_row64<F16>(k + (size_t)p * D, v);
     ld_row64(tacc + 128, v);
 #pragma unroll
     for (int i = 0; i < 64; ++i) {
         const float t = valid ? v[i] + __ldg(bqkv + 128 + i) : 0.f;
-        vt[(size_t)i * ldvt + p] = __float2bfloat16_rn(t);
+        vt[(size_t)i * ldvt + p] = (uint16_t)(pack2<F16>(t, 0.f) & 0xffffu);
     }
 }
 
@@ -251,14 +260,15 @@ struct EmbedParams {
     const uint8_t* wqkv; // [192 x 64]
     const float *b1, *b2, *lng, *lnb, *bqkv;
     float* z;
-    __nv_bfloat16 *q, *k, *vt;
+    uint16_t *q, *k, *vt;
     long ldvt;
     unsigned* status;
     uint64_t wait_ns;
     int act;
 };
 
-template <int MODE>  // 0: input x (K = 42 -> 64); 1: concat(x, h_pid) (K = 128)
+// F16: operands in FP16 (else BF16), FP32 accumulation either way.
+template <int MODE, bool F16>  // MODE 0: input x (K = 42 -> 64); 1: concat(x, h_pid) (K = 128)
 __global__ void __launch_bounds__(128, 1) k_embed_qkv(const __grid_constant__ CUtensorMap map_hp,
                                                       EmbedParams p) {
     extern __shared__ uint8_t smem_raw[];
@@ -314,7 +324,7 @@ __global__ void __launch_bounds__(128, 1) k_embed_qkv(const __grid_constant__ CU
             mbar_arrive_expect_tx(&bars[1], ATOM);
             tma_load_2d(sA + ATOM, &map_hp, 0, p0, &bars[1]);
         }
-        load_x_row(sA, tid, p.x, ri.valid, ri.prow);
+        load_x_row<F16>(sA, tid, p.x, ri.valid, ri.prow);
         fence_proxy_async_smem();
         __syncthreads();
         if (tid == 0) {
@@ -322,7 +332,7 @@ __global__ void __launch_bounds__(128, 1) k_embed_qkv(const __grid_constant__ CU
                 fail |= !mbar_wait(&bars[1], aph, ab, p.status, ST_TIMEOUT_GEMM, p.wait_ns);
             }
             tc_fence_after();
-            if (!fail) issue_gemm(tbase, sA, sW1, 64, KA);
+            if (!fail) issue_gemm<F16>(tbase, sA, sW1, 64, KA);
             mma_commit(&bars[2]);
         }
         aph ^= 1;
@@ -334,13 +344,13 @@ __global__ void __launch_bounds__(128, 1) k_embed_qkv(const __grid_constant__ CU
         ld_row64(trow, v);
 #pragma unroll
         for (int i = 0; i < 64; ++i) v[i] = act_f(v[i] + __ldg(p.b1 + i), p.act);
-        st_row_bf16(sH, tid, v);
+        st_row16<F16>(sH, tid, v);
         tc_fence_before();
         fence_proxy_async_smem();
         __syncthreads();
         if (tid == 0) {
             tc_fence_after();
-            issue_gemm(tbase, sH, sW2, 64, 1);
+            issue_gemm<F16>(tbase, sH, sW2, 64, 1);
             mma_commit(&bars[2]);
         }
         fail |= !mbar_wait(&bars[2], mph, ab, p.status, ST_TIMEOUT_GEMM, p.wait_ns);
@@ -356,20 +366,20 @@ __global__ void __launch_bounds__(128, 1) k_embed_qkv(const __grid_constant__ CU
             for (int i = 0; i < 16; ++i) zd[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
         }
         layernorm64(v, v, p.lng, p.lnb);
-        st_row_bf16(sH, tid, v);
+        st_row16<F16>(sH, tid, v);
         tc_fence_before();
         fence_proxy_async_smem();
         __syncthreads();
         if (tid == 0) {
             tc_fence_after();
-            issue_gemm(tbase, sH, sWq, 192, 1);
+            issue_gemm<F16>(tbase, sH, sWq, 192, 1);
             mma_commit(&bars[2]);
         }
         fail |= !mbar_wait(&bars[2], mph, ab, p.status, ST_TIMEOUT_GEMM, p.wait_ns);
         mph ^= 1;
         if (__syncthreads_or(fail)) break;
         tc_fence_after();
-        store_qkv(trow, p.bqkv, prow_pad, ri.valid, p.q, p.k, p.vt, p.ldvt);
+        store_qkv<F16>(trow, p.bqkv, prow_pad, ri.valid, p.q, p.k, p.vt, p.ldvt);
         tc_fence_before();
     }
     __syncthreads();
@@ -393,9 +403,9 @@ struct PostParams {
                                     // 2: heads w1 [256x64], w2 [16x256]
     const float *bo, *ln2g, *ln2b, *bup, *bdn;
     const float *lng, *lnb;         // next LN1 (mode 0) or final LN (modes 1, 2)
-    const float *ba, *bb;           // mode 0: bqkv; 1: cls b1, b2 (16); 2: heads b1 (256), b2 (16)
+    const float *ba, *bb;           // mode 0: bqkv (192); 1: cls b1 (64), b2 (16); 2: heads b1 (256), b2 (16)
     float* z;
-    __nv_bfloat16 *q, *k, *vt, *hp;
+    uint16_t *q, *k, *vt, *hp;
     long ldvt;
     float* logits;
     float* reg;
@@ -404,9 +414,71 @@ struct PostParams {
     int act;
 };
 
-template <int MODE>  // 0: next layer LN1 + QKV; 1: end of PID stack; 2: end of regression stack
-__global__ void __launch_bounds__(128, 1) k_post(const __grid_constant__ CUtensorMap map_o,
-                                                 PostParams p) {
+// parameter vector offsets (floats) in shared memory
+constexpr int PV_BO = 0, PV_LN2G = 64, PV_LN2B = 128, PV_BUP = 192, PV_BDN = 448, PV_LNG = 512,
+              PV_LNB = 576, PV_BA = 640, PV_BB = 896, PV_N = 912;
+constexpr int PT_THREADS = 512;   // two teams x two warpgroups
+constexpr uint32_t PT_TEAM_BYTES = ATOM + 2 * ATOM;  // sA (64 cols) + sH (128 cols)
+constexpr int PT_RED_FLOATS = 2 * 2 * 128;            // per team: [pass][wg][row] LN partial sums
+
+MLPF_DEV bool team_sync_or(int team, bool pred) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, %2, 256, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)pred), "r"(1 + team)
+        : "memory");
+    return r != 0;
+}
+
+MLPF_DEV void team_bar(int team) {
+    asm volatile("bar.sync %0, 256;" ::"r"(1 + team) : "memory");
+}
+
+// LayerNorm of a 64-column row whose columns are split between the two
+// warpgroups of a team (32 each): two-pass FP32 moments, partial sums exchanged
+// through shared memory.  z32/out32: this warpgroup's 32 columns.
+MLPF_DEV void layernorm_split(const float* z32, float* out32, const float* g, const float* b, int wg,
+                              int r, int team, float* red) {
+    float s = 0.f;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) s += z32[i];
+    red[wg * 128 + r] = s;
+    team_bar(team);
+    s += red[(wg ^ 1) * 128 + r];
+    const float mu = s * (1.0f / D);
+    float q = 0.f;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        const float t = z32[i] - mu;
+        q = fmaf(t, t, q);
+    }
+    red[256 + wg * 128 + r] = q;
+    team_bar(team);
+    q += red[256 + (wg ^ 1) * 128 + r];
+    const float rs = rsqrtf(q * (1.0f / D) + LN_EPS);
+#pragma unroll
+    for (int i = 0; i < 32; ++i) out32[i] = (z32[i] - mu) * rs * g[32 * wg + i] + b[32 * wg + i];
+}
+
+// Store 32 of a row's 64 columns (half `wg`) as 16-bit into the swizzled atom column.
+template <bool F16>
+MLPF_DEV void st_row_half16(uint8_t* tile, int r, const float* v32, int wg) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        uint4 u;
+        u.x = pack2<F16>(v32[8 * c + 0], v32[8 * c + 1]);
+        u.y = pack2<F16>(v32[8 * c + 2], v32[8 * c + 3]);
+        u.z = pack2<F16>(v32[8 * c + 4], v32[8 * c + 5]);
+        u.w = pack2<F16>(v32[8 * c + 6], v32[8 * c + 7]);
+        *(uint4*)(tile + sw128_off(r, 4 * wg + c)) = u;
+    }
+}
+
+template <int MODE, bool F16>  // 0: next layer LN1 + QKV; 1: end of PID stack; 2: end of regression stack
+__global__ void __launch_bounds__(PT_THREADS, 1) k_post(const __grid_constant__ CUtensorMap map_o,
+                                                        PostParams p) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sm = align1024(smem_raw);
     constexpr uint32_t WOB = 64 * 128, WUB = 256 * 128, WDB = 4 * 64 * 128;
@@ -417,28 +489,50 @@ __global__ void __launch_bounds__(128, 1) k_post(const __grid_constant__ CUtenso
     uint8_t* sWd = sWu + WUB;
     uint8_t* sWa = sWd + WDB;
     uint8_t* sWb = sWa + WAB;
-    uint8_t* sA = sWb + ((WBB + 1023) & ~1023u);
-    uint8_t* sH = sA + ATOM;  // 4 atom columns
-    uint64_t* bars = (uint64_t*)(sH + 4 * ATOM);
-    uint32_t* tmem_hold = (uint32_t*)(bars + 4);
+    uint8_t* sTeam0 = sWb + ((WBB + 1023) & ~1023u);
+    float* pv = (float*)(sTeam0 + 2 * PT_TEAM_BYTES);
+    float* red_all = pv + PV_N;               // [team][PT_RED_FLOATS]
+    uint64_t* bars = (uint64_t*)(red_all + 2 * PT_RED_FLOATS);  // 0 weights; team t: 1+2t tma, 2+2t mma
+    uint32_t* tmem_hold = (uint32_t*)(bars + 6);
     int* abort_flag = (int*)(tmem_hold + 1);
     const int tid = threadIdx.x;
+    const int team = tid >> 8, wg = (tid >> 7) & 1, r = tid & 127;
+    const bool leader = (tid & 255) == 0;
+    uint8_t* sA = sTeam0 + team * PT_TEAM_BYTES;
+    uint8_t* sH = sA + ATOM;
+    uint64_t* tma_bar = &bars[1 + 2 * team];
+    uint64_t* mma_bar = &bars[2 + 2 * team];
+    float* red = red_all + team * PT_RED_FLOATS;
 
     if (tid == 0) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
-        mbar_init(&bars[2], 1);
+        for (int i = 0; i < 5; ++i) mbar_init(&bars[i], 1);
         *abort_flag = 0;
         fence_mbar_init();
     }
     if (tid < 32) {
-        tmem_alloc(tmem_hold, 256);
+        tmem_alloc(tmem_hold, 512);
         tmem_relinquish();
+    }
+    // bias / LayerNorm vectors into shared memory
+    for (int i = tid; i < PV_N; i += PT_THREADS) {
+        float v = 0.f;
+        if (i < PV_LN2G) v = p.bo[i - PV_BO];
+        else if (i < PV_LN2B) v = p.ln2g[i - PV_LN2G];
+        else if (i < PV_BUP) v = p.ln2b[i - PV_LN2B];
+        else if (i < PV_BDN) v = p.bup[i - PV_BUP];
+        else if (i < PV_LNG) v = p.bdn[i - PV_BDN];
+        else if (i < PV_LNB) v = p.lng[i - PV_LNG];
+        else if (i < PV_BA) v = p.lnb[i - PV_LNB];
+        else if (i < PV_BB) {
+            const int n = MODE == 0 ? 192 : (MODE == 1 ? 64 : 256);
+            v = (i - PV_BA) < n ? p.ba[i - PV_BA] : 0.f;
+        } else v = MODE == 0 ? 0.f : p.bb[i - PV_BB];
+        pv[i] = v;
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tbase = *tmem_hold;
+    const uint32_t tbase = *tmem_hold + 256 * team;
     const uint32_t trow = tbase + ((uint32_t)(tid & 96) << 16);
     volatile int* ab = abort_flag;
     if (tid == 0) {
@@ -455,110 +549,164 @@ __global__ void __launch_bounds__(128, 1) k_post(const __grid_constant__ CUtenso
     const int nblk = tpad >> 6;
     const int ntiles = (tpad + ROWS - 1) / ROWS;
     uint32_t mph = 0, aph = 0;
-    auto gemm = [&](const uint8_t* a, const uint8_t* b, int N, int ka) -> bool {
+    // sync the team, let its leader issue MMAs, wait for them; false on failure
+    auto run_mma = [&](auto issue) -> bool {
         tc_fence_before();
         fence_proxy_async_smem();
-        __syncthreads();
-        if (tid == 0) {
+        if (team_sync_or(team, fail)) return false;
+        if (leader) {
             tc_fence_after();
-            issue_gemm(tbase, a, b, N, ka);
-            mma_commit(&bars[2]);
+            issue();
+            mma_commit(mma_bar);
         }
-        fail |= !mbar_wait(&bars[2], mph, ab, p.status, ST_TIMEOUT_GEMM, p.wait_ns);
+        fail |= !mbar_wait(mma_bar, mph, ab, p.status, ST_TIMEOUT_GEMM, p.wait_ns);
         mph ^= 1;
-        const bool stop = __syncthreads_or(fail);
+        const bool stop = team_sync_or(team, fail);
         tc_fence_after();
         return !stop;
     };
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        if (__syncthreads_or(fail)) break;
-        const int p0 = tile * ROWS;
-        const int pp = p0 + tid;
+    for (int tile = blockIdx.x * 2 + team; tile < ntiles; tile += 2 * gridDim.x) {
+        if (team_sync_or(team, fail)) break;
+        const int pp = tile * ROWS + r;
         const RowInfo ri = row_info(p.blk, nblk, pp);
-        if (tid == 0) {
-            mbar_arrive_expect_tx(&bars[1], ATOM);
-            tma_load_2d(sA, &map_o, 0, p0, &bars[1]);
+        if (leader) {
+            mbar_arrive_expect_tx(tma_bar, ATOM);
+            tma_load_2d(sA, &map_o, 0, tile * ROWS, tma_bar);
         }
-        float zr[64], v[64];
+        float zr[32], v[32];   // this warpgroup's 32 columns of the residual row
         {
-            const float4* zs = (const float4*)(p.z + (size_t)pp * D);
+            const float4* zs = (const float4*)(p.z + (size_t)pp * D + 32 * wg);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
+            for (int i = 0; i < 8; ++i) {
                 const float4 t = zs[i];
                 zr[4 * i] = t.x; zr[4 * i + 1] = t.y; zr[4 * i + 2] = t.z; zr[4 * i + 3] = t.w;
             }
         }
-        fail |= !mbar_wait(&bars[1], aph, ab, p.status, ST_TIMEOUT_GEMM, p.wait_ns);
+        fail |= !mbar_wait(tma_bar, aph, ab, p.status, ST_TIMEOUT_GEMM, p.wait_ns);
         aph ^= 1;
-        if (!gemm(sA, sWo, 64, 1)) break;
-        ld_row64(trow, v);
+        // out-projection + residual, LN2
+        if (!run_mma([&] { issue_gemm<F16>(tbase, sA, sWo, 64, 1); })) break;
+        tmem_ld32(trow + 32 * wg, v);
+        tmem_wait_ld();
 #pragma unroll
-        for (int i = 0; i < 64; ++i) zr[i] += v[i] + __ldg(p.bo + i);
-        layernorm64(zr, v, p.ln2g, p.ln2b);
-        st_row_bf16(sA, tid, v);
-        if (!gemm(sA, sWu, 256, 1)) break;
+        for (int i = 0; i < 32; ++i) zr[i] += v[i] + pv[PV_BO + 32 * wg + i];
+        layernorm_split(zr, v, pv + PV_LN2G, pv + PV_LN2B, wg, r, team, red);
+        st_row_half16<F16>(sA, r, v, wg);
+        // FFN: two halves of 128 hidden columns, GELU, down-projection accumulated
+        bool stop = false;
+#pragma unroll 1
+        for (int half = 0; half < 2 && !stop; ++half) {
+            if (!run_mma([&] { issue_gemm<F16>(tbase, sA, sWu + half * 128 * 128, 128, 1); })) { stop = true; break; }
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            ld_row64(trow + 64 * c, v);
+            for (int q2 = 0; q2 < 2; ++q2) {
+                tmem_ld32(trow + 64 * wg + 32 * q2, v);
+                tmem_wait_ld();
 #pragma unroll
-            for (int i = 0; i < 64; ++i) v[i] = act_f(v[i] + __ldg(p.bup + 64 * c + i), p.act);
-            st_row_bf16(sH + c * ATOM, tid, v);
+                for (int i = 0; i < 32; ++i)
+                    v[i] = act_f(v[i] + pv[PV_BUP + 128 * half + 64 * wg + 32 * q2 + i], p.act);
+                st_row_half16<F16>(sH + wg * ATOM, r, v, q2);
+            }
+            if (!run_mma([&] { issue_gemm<F16>(tbase + 128, sH, sWd + half * 2 * 64 * 128, 64, 2, half > 0); })) {
+                stop = true;
+                break;
+            }
         }
-        if (!gemm(sH, sWd, 64, 4)) break;
-        ld_row64(trow, v);
+        if (stop) break;
+        tmem_ld32(trow + 128 + 32 * wg, v);
+        tmem_wait_ld();
 #pragma unroll
-        for (int i = 0; i < 64; ++i) zr[i] += v[i] + __ldg(p.bdn + i);
+        for (int i = 0; i < 32; ++i) zr[i] += v[i] + pv[PV_BDN + 32 * wg + i];
         if (MODE == 0) {
-            float4* zd = (float4*)(p.z + (size_t)pp * D);
+            float4* zd = (float4*)(p.z + (size_t)pp * D + 32 * wg);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) zd[i] = make_float4(zr[4 * i], zr[4 * i + 1], zr[4 * i + 2], zr[4 * i + 3]);
-            layernorm64(zr, v, p.lng, p.lnb);
-            st_row_bf16(sA, tid, v);
-            if (!gemm(sA, sWa, 192, 1)) break;
-            store_qkv(trow, p.ba, pp, ri.valid, p.q, p.k, p.vt, p.ldvt);
-        } else if (MODE == 1) {
-            layernorm64(zr, v, p.lng, p.lnb);  // h_pid
-            st_global_bf16_row64(p.hp + (size_t)pp * D, v);
-            st_row_bf16(sA, tid, v);
-            if (!gemm(sA, sWa, 64, 1)) break;
-            ld_row64(trow, v);
+            for (int i = 0; i < 8; ++i) zd[i] = make_float4(zr[4 * i], zr[4 * i + 1], zr[4 * i + 2], zr[4 * i + 3]);
+            layernorm_split(zr, v, pv + PV_LNG, pv + PV_LNB, wg, r, team, red);
+            st_row_half16<F16>(sA, r, v, wg);
+            if (!run_mma([&] { issue_gemm<F16>(tbase, sA, sWa, 192, 1); })) break;
+            // wg 0: Q and V channels 0..31; wg 1: K and V channels 32..63
+            uint16_t* qk = (wg == 0 ? p.q : p.k) + (size_t)pp * D;
 #pragma unroll
-            for (int i = 0; i < 64; ++i) v[i] = act_f(v[i] + __ldg(p.ba + i), p.act);
-            st_row_bf16(sH, tid, v);
-            if (!gemm(sH, sWb, 16, 1)) break;
-            tmem_ld16(trow, v);
+            for (int q2 = 0; q2 < 2; ++q2) {
+                tmem_ld32(trow + 64 * wg + 32 * q2, v);
+                tmem_wait_ld();
+#pragma unroll
+                for (int i = 0; i < 32; ++i) v[i] += pv[PV_BA + 64 * wg + 32 * q2 + i];
+                uint4* d4 = (uint4*)(qk + 32 * q2);
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    d4[c] = make_uint4(pack2<F16>(v[8 * c], v[8 * c + 1]), pack2<F16>(v[8 * c + 2], v[8 * c + 3]),
+                                       pack2<F16>(v[8 * c + 4], v[8 * c + 5]), pack2<F16>(v[8 * c + 6], v[8 * c + 7]));
+            }
+            tmem_ld32(trow + 128 + 32 * wg, v);
             tmem_wait_ld();
-            if (ri.valid) {
-                float2* lo = (float2*)(p.logits + (size_t)ri.prow * 6);
 #pragma unroll
-                for (int c = 0; c < 3; ++c)
-                    lo[c] = make_float2(v[2 * c] + __ldg(p.bb + 2 * c), v[2 * c + 1] + __ldg(p.bb + 2 * c + 1));
+            for (int i = 0; i < 32; ++i) {
+                const float t = ri.valid ? v[i] + pv[PV_BA + 128 + 32 * wg + i] : 0.f;
+                p.vt[(size_t)(32 * wg + i) * p.ldvt + pp] = (uint16_t)(pack2<F16>(t, 0.f) & 0xffffu);
+            }
+        } else if (MODE == 1) {
+            layernorm_split(zr, v, pv + PV_LNG, pv + PV_LNB, wg, r, team, red);  // h_pid
+            {
+                uint4* d4 = (uint4*)(p.hp + (size_t)pp * D + 32 * wg);
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    d4[c] = make_uint4(pack2<F16>(v[8 * c], v[8 * c + 1]), pack2<F16>(v[8 * c + 2], v[8 * c + 3]),
+                                       pack2<F16>(v[8 * c + 4], v[8 * c + 5]), pack2<F16>(v[8 * c + 6], v[8 * c + 7]));
+            }
+            st_row_half16<F16>(sA, r, v, wg);
+            if (!run_mma([&] { issue_gemm<F16>(tbase, sA, sWa, 64, 1); })) break;
+            tmem_ld32(trow + 32 * wg, v);
+            tmem_wait_ld();
+#pragma unroll
+            for (int i = 0; i < 32; ++i) v[i] = act_f(v[i] + pv[PV_BA + 32 * wg + i], p.act);
+            st_row_half16<F16>(sH, r, v, wg);
+            if (!run_mma([&] { issue_gemm<F16>(tbase + 64, sH, sWb, 16, 1); })) break;
+            if (wg == 0) {
+                tmem_ld16(trow + 64, v);
+                tmem_wait_ld();
+                if (ri.valid) {
+                    float2* lo = (float2*)(p.logits + (size_t)ri.prow * 6);
+#pragma unroll
+                    for (int c2 = 0; c2 < 3; ++c2)
+                        lo[c2] = make_float2(v[2 * c2] + pv[PV_BB + 2 * c2], v[2 * c2 + 1] + pv[PV_BB + 2 * c2 + 1]);
+                }
             }
         } else {
-            layernorm64(zr, v, p.lng, p.lnb);  // h_reg
-            st_row_bf16(sA, tid, v);
-            if (!gemm(sA, sWa, 256, 1)) break;
+            layernorm_split(zr, v, pv + PV_LNG, pv + PV_LNB, wg, r, team, red);  // h_reg
+            st_row_half16<F16>(sA, r, v, wg);
+#pragma unroll 1
+            for (int half = 0; half < 2 && !stop; ++half) {
+                if (!run_mma([&] { issue_gemm<F16>(tbase, sA, sWa + half * 128 * 128, 128, 1); })) { stop = true; break; }
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                ld_row64(trow + 64 * c, v);
+                for (int q2 = 0; q2 < 2; ++q2) {
+                    tmem_ld32(trow + 64 * wg + 32 * q2, v);
+                    tmem_wait_ld();
 #pragma unroll
-                for (int i = 0; i < 64; ++i) v[i] = act_f(v[i] + __ldg(p.ba + 64 * c + i), p.act);
-                st_row_bf16(sH + c * ATOM, tid, v);
+                    for (int i = 0; i < 32; ++i)
+                        v[i] = act_f(v[i] + pv[PV_BA + 128 * half + 64 * wg + 32 * q2 + i], p.act);
+                    st_row_half16<F16>(sH + wg * ATOM, r, v, q2);
+                }
+                if (!run_mma([&] { issue_gemm<F16>(tbase + 128, sH, sWb + half * 2 * 16 * 128, 16, 2, half > 0); })) {
+                    stop = true;
+                    break;
+                }
             }
-            if (!gemm(sH, sWb, 16, 4)) break;
-            tmem_ld16(trow, v);
-            tmem_wait_ld();
-            if (ri.valid) {
-                float o[5];
+            if (stop) break;
+            if (wg == 0) {
+                tmem_ld16(trow + 128, v);
+                tmem_wait_ld();
+                if (ri.valid) {
+                    float o[5];
 #pragma unroll
-                for (int c = 0; c < 5; ++c) o[c] = v[c] + __ldg(p.bb + c);
-                const float* xr = p.x + (size_t)ri.prow * 42;
-                float* rg = p.reg + (size_t)ri.prow * 5;
-                rg[0] = expf(__ldg(xr + 8) + o[0]);
-                rg[1] = o[1];
-                rg[2] = o[2];
-                rg[3] = o[3];
-                rg[4] = expf(__ldg(xr + 9) + o[4]);
+                    for (int c2 = 0; c2 < 5; ++c2) o[c2] = v[c2] + pv[PV_BB + c2];
+                    const float* xr = p.x + (size_t)ri.prow * 42;
+                    float* rg = p.reg + (size_t)ri.prow * 5;
+                    rg[0] = expf(__ldg(xr + 8) + o[0]);
+                    rg[1] = o[1];
+                    rg[2] = o[2];
+                    rg[3] = o[3];
+                    rg[4] = expf(__ldg(xr + 9) + o[4]);
+                }
             }
         }
         tc_fence_before();
@@ -570,44 +718,100 @@ __global__ void __launch_bounds__(128, 1) k_post(const __grid_constant__ CUtenso
     __syncthreads();
     if (tid < 32) {
         tc_fence_after();
-        tmem_dealloc(tbase, 256);
+        tmem_dealloc(*tmem_hold, 512);
     }
 }
 
 // ------------------------------------------------------------- attention
+// Persistent varlen self-attention (Sec. 5.3, Eq. 4): one CTA per SM, a TMA
+// producer warp and one warpgroup per head.  Work items are (event, 128-query
+// tile); keys come in 64-row tiles of the same event (events start at 64-row
+// boundaries of the padded layout, so a key tile never mixes events).  Per key
+// tile and head: S = Q_h K_h^T on tcgen05 into a TMEM buffer (two per head),
+// FP32 online softmax by the thread owning each query row, P (16-bit) into a
+// swizzled shared-memory tile, then P V_h and P 1 (the row sum of the rounded
+// P) on tcgen05 into the same TMEM buffer, accumulated into registers with the
+// running rescale.  Warps signal through mbarriers only, and every wait is
+// bounded.
 constexpr int AT_STAGES = 4;
 constexpr int AT_THREADS = NH * 128 + 32;
-constexpr uint32_t AT_QB = 128 * 128;   // Q tile bytes (128 rows x 64 ch bf16)
+constexpr uint32_t AT_QB = 128 * 128;   // Q tile bytes (128 rows x 64 ch, 16-bit)
 constexpr uint32_t AT_KB = 64 * 128;    // K tile bytes (64 keys x 64 ch)
 constexpr uint32_t AT_VB = 64 * 128;    // V^T tile bytes (64 ch x 64 keys)
 constexpr uint32_t AT_PB = 128 * 128;   // P tile bytes per head (128 rows x 64 keys)
 constexpr uint32_t AT_OFF_K = 2 * AT_QB;
 constexpr uint32_t AT_OFF_V = AT_OFF_K + AT_STAGES * AT_KB;
 constexpr uint32_t AT_OFF_P = AT_OFF_V + AT_STAGES * AT_VB;
-constexpr uint32_t AT_OFF_BAR = AT_OFF_P + NH * AT_PB;
+constexpr uint32_t AT_OFF_ONE = AT_OFF_P + NH * AT_PB;   // 16 x 64 block of ones
+constexpr uint32_t AT_OFF_BAR = AT_OFF_ONE + 16 * 128;
 constexpr uint32_t AT_SMEM = AT_OFF_BAR + 512 + 1024;
 
 struct AttnParams {
     const int4* items;
     int* counters;
     int layer;
-    __nv_bfloat16* out;
+    uint16_t* out;
     unsigned* status;
     uint64_t wait_ns;
     int debug_stall;
 };
 
-MLPF_DEV bool bar_or(int id, int n, bool pred) {
-    uint32_t r;
-    asm volatile(
-        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
-        "bar.red.or.pred q, %2, %3, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
-        : "=r"(r)
-        : "r"((uint32_t)pred), "r"(id), "r"(n)
-        : "memory");
-    return r != 0;
+MLPF_DEV float max3f(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
 }
 
+// (d0, d1) = (a0, a1) * s + (t, t), one packed FP32x2 FMA
+MLPF_DEV void ffma2_bcast(float& d0, float& d1, float a0, float a1, float s, float t) {
+    uint64_t a, b, c, d;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(a) : "f"(a0), "f"(a1));
+    asm("mov.b64 %0, {%1, %1};" : "=l"(b) : "f"(s));
+    asm("mov.b64 %0, {%1, %1};" : "=l"(c) : "f"(t));
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(d0), "=f"(d1) : "l"(d));
+}
+
+// 2^x0, 2^x1 packed in the 16-bit operand format.  FP16: one packed MUFU op on
+// the FP16-rounded arguments; BF16: two FP32 MUFU ops, rounded to BF16.
+template <bool F16>
+MLPF_DEV uint32_t exp2_pair(float x0, float x1) {
+    if constexpr (F16) {
+        const uint32_t h = pack_f16x2(x0, x1);
+        uint32_t p;
+        asm("ex2.approx.f16x2 %0, %1;" : "=r"(p) : "r"(h));
+        return p;
+    } else {
+        return pack_bf16x2(ex2_approx(x0), ex2_approx(x1));
+    }
+}
+
+// Softmax numerator of 32 scores (already masked) into 4 swizzled 16-byte chunks.
+template <bool F16>
+MLPF_DEV void softmax_chunk32(const float* s, float c, float neg_m, uint8_t* prow_base, int r,
+                              int chunk0) {
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) {
+        uint32_t pk[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            float x0, x1;
+            ffma2_bcast(x0, x1, s[8 * cc + 2 * t], s[8 * cc + 2 * t + 1], c, neg_m);
+            pk[t] = exp2_pair<F16>(x0, x1);
+        }
+        *(uint4*)(prow_base + sw128_off(r, chunk0 + cc)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    }
+}
+
+MLPF_DEV bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* ab, unsigned* status,
+                        uint64_t wait_ns) {
+    const bool ok = mbar_wait(bar, parity, ab, status, ST_TIMEOUT_ATTN, wait_ns);
+    return __all_sync(0xffffffffu, ok);
+}
+
+// 17 warps: one SM sub-partition holds five of them, which caps the kernel at
+// 96 registers per thread (5 x 32 x 96 <= 16384).
+template <bool F16>
 __global__ void __launch_bounds__(AT_THREADS, 1)
     k_attention(const __grid_constant__ CUtensorMap map_q, const __grid_constant__ CUtensorMap map_k,
                 const __grid_constant__ CUtensorMap map_vt, AttnParams p) {
@@ -617,6 +821,7 @@ __global__ void __launch_bounds__(AT_THREADS, 1)
     uint8_t* sK = sm + AT_OFF_K;
     uint8_t* sV = sm + AT_OFF_V;
     uint8_t* sP = sm + AT_OFF_P;
+    uint8_t* sOne = sm + AT_OFF_ONE;
     uint64_t* bars = (uint64_t*)(sm + AT_OFF_BAR);
     uint64_t* q_full = bars;                 // [2]
     uint64_t* q_empty = bars + 2;            // [2]
@@ -624,8 +829,10 @@ __global__ void __launch_bounds__(AT_THREADS, 1)
     uint64_t* kv_empty = bars + 8;           // [4]
     uint64_t* s_full = bars + 12;            // [4 heads][2 buffers]
     uint64_t* pv_done = bars + 20;           // [4 heads]
-    uint64_t* never = bars + 24;             // armed by nobody (debug stall)
-    int4* info = (int4*)(bars + 26);         // [2]
+    uint64_t* p_ready = bars + 24;           // [4 heads], one arrival per warp
+    uint64_t* s_free = bars + 28;            // [4 heads][2 buffers], one arrival per warp
+    uint64_t* never = bars + 36;             // armed by nobody (debug stall)
+    int4* info = (int4*)(bars + 38);         // [2]
     uint32_t* tmem_hold = (uint32_t*)(info + 2);
     int* abort_flag = (int*)(tmem_hold + 1);
     volatile int* ab = abort_flag;
@@ -635,10 +842,19 @@ __global__ void __launch_bounds__(AT_THREADS, 1)
         for (int i = 0; i < 2; ++i) { mbar_init(&q_full[i], 1); mbar_init(&q_empty[i], NH); }
         for (int i = 0; i < AT_STAGES; ++i) { mbar_init(&kv_full[i], 1); mbar_init(&kv_empty[i], NH); }
         for (int i = 0; i < 2 * NH; ++i) mbar_init(&s_full[i], 1);
-        for (int i = 0; i < NH; ++i) mbar_init(&pv_done[i], 1);
+        for (int i = 0; i < NH; ++i) {
+            mbar_init(&pv_done[i], 1);
+            mbar_init(&p_ready[i], 4);
+        }
+        for (int i = 0; i < 2 * NH; ++i) mbar_init(&s_free[i], 4);
         mbar_init(never, 1);
         *abort_flag = 0;
         fence_mbar_init();
+    }
+    {   // 16 rows x 64 keys of 1.0 (B operand of the row-sum MMA)
+        const uint32_t one2 = F16 ? 0x3C003C00u : 0x3F803F80u;
+        for (int i = tid; i < 16 * 128 / 4; i += AT_THREADS) ((uint32_t*)sOne)[i] = one2;
+        fence_proxy_async_smem();
     }
     if (warp == 0) {
         tmem_alloc(tmem_hold, 512);
@@ -695,22 +911,48 @@ __global__ void __launch_bounds__(AT_THREADS, 1)
         // ------------------------------------------------ one warpgroup per head
         const int h = warp >> 2;
         const int r = tid & 127;                 // query row within the tile
-        const bool leader = r == 0;
-        const int bar_id = 1 + h;
+        const bool leader = r == 0;              // issues this head's MMAs
         const uint32_t tl = tbase + ((uint32_t)((warp & 3) * 32) << 16);  // this warp's lanes
         const uint32_t scol = h * 128;           // two 64-column S buffers per head
-        const uint32_t IQK = idesc_f16(128, 64, 1), IPV = idesc_f16(128, 16, 1);
+        const uint32_t fmt = F16 ? 0u : 1u;
+        const uint32_t IQK = idesc_f16(128, 64, fmt), IPV = idesc_f16(128, 16, fmt);
         const float c = 0.25f * 1.4426950408889634f;  // log2(e) / sqrt(16)
         uint8_t* myP = sP + h * AT_PB;
+        const uint32_t one_addr = smem_u32(sOne);
         int q_it = 0;
-        uint32_t g = 0;
-        while (true) {
+        uint32_t g = 0;   // global key-tile counter (same sequence as the producer)
+        bool ok = true;
+        // Barrier phases.  Every barrier below is waited on with a parity bit, which
+        // is only sound while the waiter is at most one completion behind:
+        //  s_full[h][b]: tiles b, b+2, ...; the next QK^T into buffer b needs
+        //                s_free of this tile, i.e. every warp past its s_full wait.
+        //  s_free[h][b]: one completion per tile in buffer b (all four warps read
+        //                its PV partial); the next completion needs PV of the
+        //                next tile in b, issued only after the leader's wait.
+        //  p_ready[h]:   one completion per tile; a warp stores P(t+1) only after
+        //                PV(t), which the leader issues after its wait.
+        //  pv_done[h]:   one completion per tile; PV(t+1) needs every warp's P(t+1),
+        //                stored after that warp's wait for PV(t).
+        // QK^T(t) overwrites TMEM buffer t&1, last used by tile t-2.
+        auto issue_qk = [&](uint32_t gg, int qb) -> bool {
+            if (gg >= 2 && !mbar_wait(&s_free[h * 2 + (gg & 1)], ((gg - 2) >> 1) & 1, ab, p.status,
+                                      ST_TIMEOUT_ATTN, p.wait_ns))
+                return false;
+            const uint32_t s = gg & (AT_STAGES - 1);
+            if (!mbar_wait(&kv_full[s], (gg / AT_STAGES) & 1, ab, p.status, ST_TIMEOUT_ATTN, p.wait_ns))
+                return false;
+            tc_fence_after();
+            mma_f16(tbase + scol + (gg & 1) * 64, sdesc_sw128(smem_u32(sQ + qb * AT_QB) + h * 32),
+                    sdesc_sw128(smem_u32(sK + s * AT_KB) + h * 32), IQK, 0);
+            mma_commit(&s_full[h * 2 + (gg & 1)]);
+            return true;
+        };
+        while (ok) {
             const int qb = q_it & 1;
-            bool fail = !mbar_wait(&q_full[qb], (q_it >> 1) & 1, ab, p.status, ST_TIMEOUT_ATTN, p.wait_ns);
-            int4 it = fail ? make_int4(-1, 0, 0, 0) : info[qb];
-            if (!fail && p.debug_stall)
-                fail = !mbar_wait(never, 0, ab, p.status, ST_TIMEOUT_ATTN, p.wait_ns);
-            if (bar_or(bar_id, 128, fail || it.x < 0)) break;
+            if (!warp_wait(&q_full[qb], (q_it >> 1) & 1, ab, p.status, p.wait_ns)) break;
+            const int4 it = info[qb];
+            if (it.x < 0) break;
+            if (p.debug_stall && !warp_wait(never, 0, ab, p.status, p.wait_ns)) break;
             const int nk = (it.z + 63) >> 6;
             if (nk == 0) {  // an event the scheduler could not place: no keys loaded
                 if (leader) mbar_arrive(&q_empty[qb]);
@@ -723,149 +965,119 @@ __global__ void __launch_bounds__(AT_THREADS, 1)
 #pragma unroll
             for (int i = 0; i < 16; ++i) o[i] = 0.f;
             float m = -INFINITY, l = 0.f, alpha_prev = 0.f;
-            if (leader) {
-                const uint32_t s = g & (AT_STAGES - 1);
-                if (mbar_wait(&kv_full[s], (g / AT_STAGES) & 1, ab, p.status, ST_TIMEOUT_ATTN, p.wait_ns)) {
-                    tc_fence_after();
-                    mma_f16(tbase + scol + (g & 1) * 64, sdesc_sw128(smem_u32(sQ + qb * AT_QB) + h * 32),
-                            sdesc_sw128(smem_u32(sK + s * AT_KB) + h * 32), IQK, 0);
-                    mma_commit(&s_full[h * 2 + (g & 1)]);
-                } else {
-                    fail = true;
-                }
-            }
-            bool stop = false;
-            for (int j = 0; j < nk; ++j) {
+            if (leader) ok = issue_qk(g, qb);
+            ok = __all_sync(0xffffffffu, ok);   // keep every lane of the warp on one path
+            for (int j = 0; j < nk && ok; ++j) {
                 const uint32_t gj = g + j;
                 const uint32_t sb = gj & 1;
-                if (j > 0 && !fail) {
-                    // PV of tile j-1 landed in the other buffer's first 16 columns
-                    if (__all_sync(0xffffffffu, mbar_wait(&pv_done[h], (gj - 1) & 1, ab, p.status, ST_TIMEOUT_ATTN, p.wait_ns))) {
-                        tc_fence_after();
-                        float part[16];
-                        tmem_ld16(tl + scol + (sb ^ 1) * 64, part);
-                        tmem_wait_ld();
-#pragma unroll
-                        for (int i = 0; i < 16; ++i) o[i] = fmaf(o[i], alpha_prev, part[i]);
-                    } else {
-                        fail = true;
-                    }
-                }
-                tc_fence_before();
-                if (bar_or(bar_id, 128, fail)) { stop = true; break; }
-                if (leader && j + 1 < nk) {
-                    const uint32_t g1 = gj + 1, s1 = g1 & (AT_STAGES - 1);
-                    if (mbar_wait(&kv_full[s1], (g1 / AT_STAGES) & 1, ab, p.status, ST_TIMEOUT_ATTN, p.wait_ns)) {
-                        tc_fence_after();
-                        mma_f16(tbase + scol + (g1 & 1) * 64, sdesc_sw128(smem_u32(sQ + qb * AT_QB) + h * 32),
-                                sdesc_sw128(smem_u32(sK + s1 * AT_KB) + h * 32), IQK, 0);
-                        mma_commit(&s_full[h * 2 + (g1 & 1)]);
-                    } else {
-                        fail = true;
-                    }
-                }
-                {   // warp-uniform: the TMEM loads below are .sync.aligned
-                    const bool got = fail ? false
-                                          : mbar_wait(&s_full[h * 2 + sb], (gj >> 1) & 1, ab, p.status,
-                                                      ST_TIMEOUT_ATTN, p.wait_ns);
-                    fail = !__all_sync(0xffffffffu, got);
-                }
-                if (!fail) {
+                if (j > 0) {
+                    // PV and P.1 of tile j-1 landed in the other buffer's columns 0..31
+                    if (!warp_wait(&pv_done[h], (gj - 1) & 1, ab, p.status, p.wait_ns)) { ok = false; break; }
                     tc_fence_after();
-                    const uint32_t sa = tl + scol + sb * 64;
-                    const int kvalid = (j == nk - 1) ? it.z - 64 * j : 64;
-                    // pass 1: row max over the 64 scores (second half kept in registers)
-                    float s[32];
-                    tmem_ld32(sa, s);
-                    tmem_wait_ld();
-                    float mx = -INFINITY;
-#pragma unroll
-                    for (int i = 0; i < 32; ++i) mx = fmaxf(mx, i < kvalid ? s[i] : -INFINITY);
-                    tmem_ld32(sa + 32, s);
+                    float part[32];
+                    tmem_ld32(tl + scol + (sb ^ 1) * 64, part);
                     tmem_wait_ld();
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) {
-                        if (i + 32 >= kvalid) s[i] = -INFINITY;
-                        mx = fmaxf(mx, s[i]);
-                    }
-                    const float m_new = fmaxf(m, mx * c);
-                    const float alpha = ex2_approx(m - m_new);
-                    float sum = 0.f;
-                    // pass 2: exponentials, row sum, bf16 P into the swizzled tile
-#pragma unroll
-                    for (int half = 1; half >= 0; --half) {
-                        if (half == 0) {
-                            tmem_ld32(sa, s);
-                            tmem_wait_ld();
-#pragma unroll
-                            for (int i = 0; i < 32; ++i)
-                                if (i >= kvalid) s[i] = -INFINITY;
-                        }
-#pragma unroll
-                        for (int cc = 0; cc < 4; ++cc) {
-                            uint32_t pk[4];
-#pragma unroll
-                            for (int t = 0; t < 4; ++t) {
-                                const float p0 = ex2_approx(fmaf(s[8 * cc + 2 * t], c, -m_new));
-                                const float p1 = ex2_approx(fmaf(s[8 * cc + 2 * t + 1], c, -m_new));
-                                sum += p0 + p1;
-                                pk[t] = pack_bf16x2(p0, p1);
-                            }
-                            *(uint4*)(myP + sw128_off(r, half * 4 + cc)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-                        }
-                    }
-                    l = fmaf(l, alpha, sum);
-                    m = m_new;
-                    alpha_prev = alpha;
-                    fence_proxy_async_smem();
-                } else {
-                    fail = true;
+                    for (int i = 0; i < 16; ++i) o[i] = fmaf(o[i], alpha_prev, part[i]);
+                    l = fmaf(l, alpha_prev, part[16]);
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&s_free[h * 2 + (sb ^ 1)]);
                 }
-                tc_fence_before();
-                if (bar_or(bar_id, 128, fail)) { stop = true; break; }
-                if (leader) {
-                    tc_fence_after();
-                    const uint32_t s = gj & (AT_STAGES - 1);
-                    const uint32_t pa = smem_u32(myP), va = smem_u32(sV + s * AT_VB) + h * 16 * 128;
-#pragma unroll
-                    for (int kc = 0; kc < 4; ++kc)
-                        mma_f16(tbase + scol + sb * 64, sdesc_sw128(pa + kc * 32), sdesc_sw128(va + kc * 32),
-                                IPV, kc > 0 ? 1u : 0u);
-                    mma_commit(&pv_done[h]);
-                    mma_commit(&kv_empty[s]);
-                }
-            }
-            if (stop) break;
-            const uint32_t gl = g + nk - 1;
-            const bool got_last = fail ? false : mbar_wait(&pv_done[h], gl & 1, ab, p.status, ST_TIMEOUT_ATTN, p.wait_ns);
-            if (__all_sync(0xffffffffu, got_last)) {
+                if (leader && j + 1 < nk) ok = issue_qk(gj + 1, qb);
+                ok = __all_sync(0xffffffffu, ok);
+                if (!ok) break;
+                if (!warp_wait(&s_full[h * 2 + sb], (gj >> 1) & 1, ab, p.status, p.wait_ns)) { ok = false; break; }
                 tc_fence_after();
-                float part[16];
-                tmem_ld16(tl + scol + (gl & 1) * 64, part);
+                const uint32_t sa = tl + scol + sb * 64;
+                const bool last = (j == nk - 1);
+                const int kvalid = it.z - 64 * j;
+                float s[32];
+                // pass 1: row max over the two 32-column halves (re-read below, to
+                // stay within the register budget)
+                float mx = -INFINITY;
+#pragma unroll
+                for (int hf = 0; hf < 2; ++hf) {
+                    tmem_ld32(sa + 32 * hf, s);
+                    tmem_wait_ld();
+                    if (last) {
+#pragma unroll
+                        for (int i = 0; i < 32; ++i)
+                            if (i + 32 * hf >= kvalid) s[i] = -INFINITY;
+                    }
+#pragma unroll
+                    for (int i = 0; i < 32; i += 2) mx = max3f(mx, s[i], s[i + 1]);
+                }
+                const float m_new = fmaxf(m, mx * c);
+                alpha_prev = ex2_approx(m - m_new);
+                m = m_new;
+                // pass 2: exponentials into the P tile
+#pragma unroll
+                for (int hf = 0; hf < 2; ++hf) {
+                    tmem_ld32(sa + 32 * hf, s);
+                    tmem_wait_ld();
+                    if (last) {
+#pragma unroll
+                        for (int i = 0; i < 32; ++i)
+                            if (i + 32 * hf >= kvalid) s[i] = -INFINITY;
+                    }
+                    softmax_chunk32<F16>(s, c, -m_new, myP, r, 4 * hf);
+                }
+                fence_proxy_async_smem();
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&p_ready[h]);
+                if (leader) {
+                    if (!mbar_wait(&p_ready[h], gj & 1, ab, p.status, ST_TIMEOUT_ATTN, p.wait_ns)) {
+                        ok = false;
+                    } else {
+                        tc_fence_after();
+                        const uint32_t st = gj & (AT_STAGES - 1);
+                        const uint32_t pa = smem_u32(myP), va = smem_u32(sV + st * AT_VB) + h * 16 * 128;
+                        const uint32_t dst = tbase + scol + sb * 64;
+#pragma unroll
+                        for (int kc = 0; kc < 4; ++kc) {
+                            mma_f16(dst, sdesc_sw128(pa + kc * 32), sdesc_sw128(va + kc * 32), IPV, kc > 0 ? 1u : 0u);
+                            mma_f16(dst + 16, sdesc_sw128(pa + kc * 32), sdesc_sw128(one_addr + kc * 32), IPV,
+                                    kc > 0 ? 1u : 0u);
+                        }
+                        mma_commit(&pv_done[h]);
+                        mma_commit(&kv_empty[st]);
+                    }
+                }
+                ok = __all_sync(0xffffffffu, ok);
+            }
+            if (!ok) break;
+            const uint32_t gl = g + nk - 1;
+            if (!warp_wait(&pv_done[h], gl & 1, ab, p.status, p.wait_ns)) break;
+            tc_fence_after();
+            {
+                float part[32];
+                tmem_ld32(tl + scol + (gl & 1) * 64, part);
                 tmem_wait_ld();
 #pragma unroll
                 for (int i = 0; i < 16; ++i) o[i] = fmaf(o[i], alpha_prev, part[i]);
-            } else {
-                fail = true;
+                l = fmaf(l, alpha_prev, part[16]);
             }
-            if (leader && !fail) mbar_arrive(&q_empty[qb]);
-            if (!fail && r < rows_valid) {
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&s_free[h * 2 + (gl & 1)]);
+            if (leader) mbar_arrive(&q_empty[qb]);  // every QK^T of this item has completed
+            if (r < rows_valid) {
                 const float inv = 1.0f / l;
                 uint4 u0, u1;
-                u0.x = pack_bf16x2(o[0] * inv, o[1] * inv);
-                u0.y = pack_bf16x2(o[2] * inv, o[3] * inv);
-                u0.z = pack_bf16x2(o[4] * inv, o[5] * inv);
-                u0.w = pack_bf16x2(o[6] * inv, o[7] * inv);
-                u1.x = pack_bf16x2(o[8] * inv, o[9] * inv);
-                u1.y = pack_bf16x2(o[10] * inv, o[11] * inv);
-                u1.z = pack_bf16x2(o[12] * inv, o[13] * inv);
-                u1.w = pack_bf16x2(o[14] * inv, o[15] * inv);
+                u0.x = pack2<F16>(o[0] * inv, o[1] * inv);
+                u0.y = pack2<F16>(o[2] * inv, o[3] * inv);
+                u0.z = pack2<F16>(o[4] * inv, o[5] * inv);
+                u0.w = pack2<F16>(o[6] * inv, o[7] * inv);
+                u1.x = pack2<F16>(o[8] * inv, o[9] * inv);
+                u1.y = pack2<F16>(o[10] * inv, o[11] * inv);
+                u1.z = pack2<F16>(o[12] * inv, o[13] * inv);
+                u1.w = pack2<F16>(o[14] * inv, o[15] * inv);
                 uint4* dst = (uint4*)(p.out + (size_t)(qrow0 + r) * D + h * 16);
                 dst[0] = u0;
                 dst[1] = u1;
             }
-            tc_fence_before();
-            if (bar_or(bar_id, 128, fail)) break;
             g += nk;
             ++q_it;
         }
@@ -892,7 +1104,8 @@ uint32_t embed_smem(int mode) {
 uint32_t post_smem(int mode) {
     const uint32_t wab = mode == 0 ? 192 * 128 : (mode == 1 ? 64 * 128 : 256 * 128);
     const uint32_t wbb = mode == 0 ? 0 : (mode == 1 ? 16 * 128 : 4 * 16 * 128);
-    return 64 * 128 + 256 * 128 + 4 * 64 * 128 + wab + ((wbb + 1023) & ~1023u) + 5 * ATOM + 64 + 1024;
+    return 64 * 128 + 256 * 128 + 4 * 64 * 128 + wab + ((wbb + 1023) & ~1023u) + 2 * PT_TEAM_BYTES +
+           PV_N * 4 + 2 * PT_RED_FLOATS * 4 + 64 + 1024;
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
@@ -926,9 +1139,11 @@ bool make_map_bf16(CUtensorMap* map, void* base, uint64_t inner, uint64_t outer,
               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// bf16 swizzled image of a weight matrix: out[n][k'] = W[n][colmap(k')], zero padded.
+// 16-bit (BF16 or FP16) swizzled image of a weight matrix:
+// out[n][k'] = W[n][colmap(k')], zero padded.
 void build_image(std::vector<uint8_t>& out, int Npad, int Kpad, const std::vector<float>& W,
-                 int N, int K, const std::vector<int>& colmap, const std::vector<int>& rowmap) {
+                 int N, int K, const std::vector<int>& colmap, const std::vector<int>& rowmap,
+                 bool f16) {
     out.assign((size_t)Npad * Kpad * 2, 0);
     const int atoms = Kpad / 64;
     for (int a = 0; a < atoms; ++a)
@@ -939,11 +1154,63 @@ void build_image(std::vector<uint8_t>& out, int Npad, int Kpad, const std::vecto
                 const int src_n = rowmap.empty() ? (n < N ? n : -1) : rowmap[n];
                 float v = 0.f;
                 if (src_k >= 0 && src_n >= 0) v = W[(size_t)src_n * K + src_k];
-                const __nv_bfloat16 b = __float2bfloat16_rn(v);
+                uint16_t b;
+                if (f16) {
+                    const __half hv = __float2half_rn(v);
+                    std::memcpy(&b, &hv, 2);
+                } else {
+                    const __nv_bfloat16 bv = __float2bfloat16_rn(v);
+                    std::memcpy(&b, &bv, 2);
+                }
                 const size_t off = (size_t)a * Npad * 128 + (size_t)n * 128 +
                                    (size_t)((((kk >> 3) ^ (n & 7)) << 4)) + (kk & 7) * 2;
                 std::memcpy(&out[off], &b, 2);
             }
+}
+
+// Resident CTAs per SM of a kernel at its launch configuration (0 = cannot launch).
+template <typename K>
+int occupancy(K kernel, int threads, uint32_t smem) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) != cudaSuccess) return 0;
+    return n;
+}
+
+// Every kernel must fit one CTA per SM; the embedding kernels (256 TMEM columns
+// each) must not exceed two co-resident CTAs.  Returns an
+// empty string or a description of the kernels that do not fit.
+template <bool F16>
+std::string check_occupancy() {
+    const int o[6] = {occupancy(k_attention<F16>, AT_THREADS, AT_SMEM),
+                      occupancy(k_post<0, F16>, PT_THREADS, post_smem(0)),
+                      occupancy(k_post<1, F16>, PT_THREADS, post_smem(1)),
+                      occupancy(k_post<2, F16>, PT_THREADS, post_smem(2)),
+                      occupancy(k_embed_qkv<0, F16>, 128, embed_smem(0)),
+                      occupancy(k_embed_qkv<1, F16>, 128, embed_smem(1))};
+    if (o[0] >= 1 && o[1] >= 1 && o[2] >= 1 && o[3] >= 1 && o[4] >= 1 && o[4] <= 2 && o[5] >= 1 &&
+        o[5] <= 2)
+        return "";
+    std::string msg = std::string(F16 ? "fp16" : "bf16") + " CTAs/SM: attention " +
+                      std::to_string(o[0]) + ", post " + std::to_string(o[1]) + "/" + std::to_string(o[2]) +
+                      "/" + std::to_string(o[3]) + ", embed " + std::to_string(o[4]) + "/" +
+                      std::to_string(o[5]);
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, k_post<2, F16>) == cudaSuccess)
+        msg += "; post regs " + std::to_string(fa.numRegs) + " max threads " + std::to_string(fa.maxThreadsPerBlock);
+    if (cudaFuncGetAttributes(&fa, k_attention<F16>) == cudaSuccess)
+        msg += "; attention regs " + std::to_string(fa.numRegs) + " max threads " +
+               std::to_string(fa.maxThreadsPerBlock);
+    return msg;
+}
+
+template <bool F16>
+void set_attrs() {
+    cudaFuncSetAttribute(k_embed_qkv<0, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, embed_smem(0));
+    cudaFuncSetAttribute(k_embed_qkv<1, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, embed_smem(1));
+    cudaFuncSetAttribute(k_post<0, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, post_smem(0));
+    cudaFuncSetAttribute(k_post<1, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, post_smem(1));
+    cudaFuncSetAttribute(k_post<2, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, post_smem(2));
+    cudaFuncSetAttribute(k_attention<F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, AT_SMEM);
 }
 
 }  // namespace
@@ -951,13 +1218,15 @@ void build_image(std::vector<uint8_t>& out, int Npad, int Kpad, const std::vecto
 bool tc_prepare_weights(Model& m) {
     const mlpf_config& c = m.cfg;
     auto H = [&](const std::string& s) -> const std::vector<float>& { return m.host.at(s).data; };
-    std::vector<std::pair<std::string, std::vector<uint8_t>>> imgs;
+    std::vector<std::pair<std::string, std::vector<uint8_t>>> imgs, imgs_h;
     std::vector<std::pair<std::string, std::vector<float>>> vecs;
     std::vector<uint8_t> img;
     auto add = [&](const std::string& name, int Npad, int Kpad, const std::vector<float>& W, int N,
                    int K, std::vector<int> colmap = {}, std::vector<int> rowmap = {}) {
-        build_image(img, Npad, Kpad, W, N, K, colmap, rowmap);
+        build_image(img, Npad, Kpad, W, N, K, colmap, rowmap, false);
         imgs.push_back({name, img});
+        build_image(img, Npad, Kpad, W, N, K, colmap, rowmap, true);
+        imgs_h.push_back({name, img});
     };
     auto cat = [&](std::initializer_list<std::string> names, int pad_to = 0) {
         std::vector<float> v;
@@ -1018,9 +1287,9 @@ bool tc_prepare_weights(Model& m) {
     size_t ib = 0, vb = 0;
     for (auto& i : imgs) ib += (i.second.size() + 1023) / 1024 * 1024;
     for (auto& v : vecs) vb += (v.second.size() + 63) / 64 * 64;
-    if (cudaMalloc(&m.w.img_base, ib) != cudaSuccess) { set_error("weight image allocation"); return false; }
+    if (cudaMalloc(&m.w.img_base, 2 * ib) != cudaSuccess) { set_error("weight image allocation"); return false; }
     if (cudaMalloc(&m.w.tc_f32_base, vb * 4) != cudaSuccess) { set_error("bias allocation"); return false; }
-    std::vector<uint8_t> hi(ib, 0);
+    std::vector<uint8_t> hi(2 * ib, 0);
     std::vector<float> hv(vb, 0.f);
     size_t o = 0;
     for (auto& i : imgs) {
@@ -1029,28 +1298,37 @@ bool tc_prepare_weights(Model& m) {
         m.w.img_bytes[i.first] = (uint32_t)i.second.size();
         o += (i.second.size() + 1023) / 1024 * 1024;
     }
+    for (auto& i : imgs_h) {
+        std::memcpy(&hi[o], i.second.data(), i.second.size());
+        m.w.img_h[i.first] = m.w.img_base + o;
+        o += (i.second.size() + 1023) / 1024 * 1024;
+    }
     o = 0;
     for (auto& v : vecs) {
         std::copy(v.second.begin(), v.second.end(), hv.begin() + o);
         m.w.tcv[v.first] = m.w.tc_f32_base + o;
         o += (v.second.size() + 63) / 64 * 64;
     }
-    if (cudaMemcpy(m.w.img_base, hi.data(), ib, cudaMemcpyHostToDevice) != cudaSuccess ||
+    if (cudaMemcpy(m.w.img_base, hi.data(), 2 * ib, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(m.w.tc_f32_base, hv.data(), vb * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
         set_error("weight image upload");
         return false;
     }
     static bool attrs = false;
     if (!attrs) {
-        cudaFuncSetAttribute(k_embed_qkv<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, embed_smem(0));
-        cudaFuncSetAttribute(k_embed_qkv<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, embed_smem(1));
-        cudaFuncSetAttribute(k_post<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, post_smem(0));
-        cudaFuncSetAttribute(k_post<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, post_smem(1));
-        cudaFuncSetAttribute(k_post<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, post_smem(2));
-        cudaFuncSetAttribute(k_attention, cudaFuncAttributeMaxDynamicSharedMemorySize, AT_SMEM);
+        set_attrs<false>();
+        set_attrs<true>();
         attrs = true;
     }
     if (cudaGetLastError() != cudaSuccess) { set_error("kernel attribute setup"); return false; }
+    m.embed_ctas_per_sm = std::max(1, std::min(occupancy(k_embed_qkv<1, false>, 128, embed_smem(1)),
+                                               occupancy(k_embed_qkv<1, true>, 128, embed_smem(1))));
+    const std::string occ = check_occupancy<false>() + check_occupancy<true>();
+    if (!occ.empty()) {
+        cudaGetLastError();
+        set_error("a tensor-core kernel does not fit its launch configuration: " + occ);
+        return false;
+    }
     return true;
 }
 
@@ -1064,23 +1342,25 @@ bool tc_make_maps(Model& m) {
     return ok;
 }
 
-int64_t run_forward_tc(Model& m, int prec, const float* x, const int32_t* cu, int n_events, int total,
-                       int max_n, float* logits, float* reg, cudaStream_t st) {
-    (void)prec;
-    (void)total;
-    (void)max_n;
+template <bool F16>
+static int64_t run_tc(Model& m, const float* x, const int32_t* cu, int n_events, float* logits,
+                      float* reg, cudaStream_t st) {
     const mlpf_config& c = m.cfg;
     Workspace& w = m.ws;
     auto V = [&](const std::string& s) { return (const float*)m.w.tcv.at(s); };
-    auto I = [&](const std::string& s) { return (const uint8_t*)m.w.img.at(s); };
+    auto I = [&](const std::string& s) { return (const uint8_t*)(F16 ? m.w.img_h : m.w.img).at(s); };
     int64_t n = 0;
     const int grid = m.sm_count;
+    prof_begin(m, st, "schedule");
     k_schedule<<<1, 1024, 0, st>>>(cu, n_events, w.blk, w.items, w.counters, (int)(w.cap_tpad / 64),
                                    (int)(w.cap_tpad / 128 + w.cap_events + 1));
+    prof_end(m, st);
     ++n;
     auto attention = [&](int layer) {
-        AttnParams ap{w.items, w.counters, layer, w.to, m.status, (uint64_t)m.wait_limit_ns, m.debug_stall ? 1 : 0};
-        k_attention<<<grid * m.attn_ctas_per_sm, AT_THREADS, AT_SMEM, st>>>(w.map_q, w.map_k, w.map_vt, ap);
+        AttnParams ap{w.items, w.counters, layer, (uint16_t*)w.to, m.status, (uint64_t)m.wait_limit_ns, m.debug_stall ? 1 : 0};
+        prof_begin(m, st, "attention");
+        k_attention<F16><<<grid * m.attn_ctas_per_sm, AT_THREADS, AT_SMEM, st>>>(w.map_q, w.map_k, w.map_vt, ap);
+        prof_end(m, st);
         ++n;
     };
     auto embed = [&](int mode, const std::string& lp) {
@@ -1098,17 +1378,19 @@ int64_t run_forward_tc(Model& m, int prec, const float* x, const int32_t* cu, in
         ep.lnb = V(lp + "ln1.b");
         ep.bqkv = V(lp + "bqkv");
         ep.z = w.tz;
-        ep.q = w.tq;
-        ep.k = w.tk;
-        ep.vt = w.tvt;
+        ep.q = (uint16_t*)w.tq;
+        ep.k = (uint16_t*)w.tk;
+        ep.vt = (uint16_t*)w.tvt;
         ep.ldvt = w.cap_tpad;
         ep.status = m.status;
         ep.wait_ns = (uint64_t)m.wait_limit_ns;
         ep.act = c.act;
+        prof_begin(m, st, mode == 0 ? "embed_qkv" : "reg_embed_qkv");
         if (mode == 0)
-            k_embed_qkv<0><<<grid * 2, 128, embed_smem(0), st>>>(w.map_hp, ep);
+            k_embed_qkv<0, F16><<<grid * m.embed_ctas_per_sm, 128, embed_smem(0), st>>>(w.map_hp, ep);
         else
-            k_embed_qkv<1><<<grid * 2, 128, embed_smem(1), st>>>(w.map_hp, ep);
+            k_embed_qkv<1, F16><<<grid * m.embed_ctas_per_sm, 128, embed_smem(1), st>>>(w.map_hp, ep);
+        prof_end(m, st);
         ++n;
     };
     auto post = [&](int mode, const std::string& lp, const std::string& next) {
@@ -1146,22 +1428,24 @@ int64_t run_forward_tc(Model& m, int prec, const float* x, const int32_t* cu, in
             pp.bb = V("head.reg.b2");
         }
         pp.z = w.tz;
-        pp.q = w.tq;
-        pp.k = w.tk;
-        pp.vt = w.tvt;
-        pp.hp = w.thp;
+        pp.q = (uint16_t*)w.tq;
+        pp.k = (uint16_t*)w.tk;
+        pp.vt = (uint16_t*)w.tvt;
+        pp.hp = (uint16_t*)w.thp;
         pp.ldvt = w.cap_tpad;
         pp.logits = logits;
         pp.reg = reg;
         pp.status = m.status;
         pp.wait_ns = (uint64_t)m.wait_limit_ns;
         pp.act = c.act;
+        prof_begin(m, st, mode == 0 ? "post_qkv" : (mode == 1 ? "post_cls_head" : "post_reg_heads"));
         if (mode == 0)
-            k_post<0><<<grid, 128, post_smem(0), st>>>(w.map_o, pp);
+            k_post<0, F16><<<grid, PT_THREADS, post_smem(0), st>>>(w.map_o, pp);
         else if (mode == 1)
-            k_post<1><<<grid, 128, post_smem(1), st>>>(w.map_o, pp);
+            k_post<1, F16><<<grid, PT_THREADS, post_smem(1), st>>>(w.map_o, pp);
         else
-            k_post<2><<<grid, 128, post_smem(2), st>>>(w.map_o, pp);
+            k_post<2, F16><<<grid, PT_THREADS, post_smem(2), st>>>(w.map_o, pp);
+        prof_end(m, st);
         ++n;
     };
     int layer = 0;
@@ -1185,6 +1469,14 @@ int64_t run_forward_tc(Model& m, int prec, const float* x, const int32_t* cu, in
     }
     if (cudaPeekAtLastError() != cudaSuccess) return -1;
     return n;
+}
+
+int64_t run_forward_tc(Model& m, int prec, const float* x, const int32_t* cu, int n_events, int total,
+                       int max_n, float* logits, float* reg, cudaStream_t st) {
+    (void)total;
+    (void)max_n;
+    return prec == MLPF_FP16 ? run_tc<true>(m, x, cu, n_events, logits, reg, st)
+                             : run_tc<false>(m, x, cu, n_events, logits, reg, st);
 }
 
 }  // namespace mlpf

@@ -215,6 +215,20 @@ MLPF_DEV uint32_t pack_bf16x2(float lo, float hi) {
     return r;
 }
 
+MLPF_DEV uint32_t pack_f16x2(float lo, float hi) {
+    uint32_t r;
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+// Two floats -> packed 16-bit pair in the operand format (F16 or BF16).
+template <bool F16>
+MLPF_DEV uint32_t pack2(float lo, float hi) {
+    if constexpr (F16)
+        return pack_f16x2(lo, hi);
+    else
+        return pack_bf16x2(lo, hi);
+}
+
 // Byte offset of 16-byte chunk `c` (0..7) of row `r` inside one 128-byte-swizzled
 // atom column (rows of 128 bytes; chunk index XORed with row mod 8).
 MLPF_DEV uint32_t sw128_off(int r, int c) {
