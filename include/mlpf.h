@@ -130,6 +130,32 @@ mlpf_status mlpf_forward_host(mlpf_model* m, int32_t precision,
                               double* event_sums, void* stream);
 
 /*
+ * mlpf_forward with no device allocation: for callers that may not allocate GPU
+ * memory while they run (an event loop under a caching allocator or a fixed
+ * memory budget, or code that cannot afford the synchronisation a cudaMalloc
+ * implies).  The paper has no counterpart; this is a library-usage variant.
+ *
+ * Same arguments, layouts and result as mlpf_forward for precision MLPF_BF16 or
+ * MLPF_FP16 (others: MLPF_E_UNSUPPORTED).  The forward's scratch lives in one
+ * file-scope device array of about 18.4 MB (held on every GPU that loads the
+ * library until the process exits) instead of the model's workspace, so each
+ * call takes at most 16384 elements and 64 events (larger: MLPF_E_INVALID with
+ * a message).  No CUDA graph is used and nothing is allocated: not the
+ * workspace, not profiling events.
+ * The first call on a device resolves the array's device address
+ * (cudaGetSymbolAddress) and encodes its tensor maps; make that first call
+ * before any stream capture.  Every call on a device shares the one array and
+ * overwrites it: calls that overlap on the GPU (several streams, models or host
+ * threads at once) race; serialise them.  Asynchronous on `stream`; device-side
+ * status via mlpf_sync.
+ */
+mlpf_status mlpf_forward_noalloc(mlpf_model* m, int32_t precision,
+                                 const float* x, const int32_t* cu_seqlens,
+                                 int32_t n_events, int32_t total, int32_t max_n,
+                                 float* logits, float* reg, int32_t* cls,
+                                 double* event_sums, void* stream);
+
+/*
  * Wait for the model's work on `stream` and report device-side status:
  * MLPF_E_TIMEOUT if a bounded wait inside a kernel ran out since the last
  * mlpf_sync (the kernel returned early; outputs are invalid), otherwise

@@ -1,0 +1,65 @@
+"""mlpf_forward_noalloc against mlpf_forward (GPU).
+
+The no-allocation entry point serves callers that may not allocate device
+memory while they run; its scratch is a fixed device array shared by every
+call.  This file is collected last so that a failing run stopped at the first
+failure has already run every other test.  It passes alone in a fresh process
+and after the other tests.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import synth
+from paper_2601_17554_b300 import MlpfError, _lib, check
+from tests.util import make_model
+
+pytestmark = pytest.mark.gpu
+
+
+def _call(fn_name, model, x, cu, prec, max_n):
+    import torch
+    T, n = x.shape[0], len(cu) - 1
+    out = (torch.empty((T, 6), device="cuda"), torch.empty((T, 5), device="cuda"),
+           torch.empty((T,), dtype=torch.int32, device="cuda"),
+           torch.empty((n, 3), dtype=torch.float64, device="cuda"))
+    xt = torch.from_numpy(x).cuda()
+    ct = torch.from_numpy(cu).cuda()
+    st = torch.cuda.current_stream().cuda_stream
+    p = lambda t: ctypes.c_void_p(t.data_ptr())
+    fn = getattr(model.L, fn_name)
+    check(fn(model.h, prec, p(xt), p(ct), n, T, max_n,
+             p(out[0]), p(out[1]), p(out[2]), p(out[3]), ctypes.c_void_p(st)))
+    model.sync()
+    return [o.cpu().numpy() for o in out]
+
+
+@pytest.mark.parametrize("prec", [_lib.MLPF_FP16, _lib.MLPF_BF16])
+def test_noalloc_matches_forward_twice(prec):
+    model, _ = make_model(synth.SMALL, 3, perturbed=True)
+    # two different calls in a row: the shared scratch keeps the previous call's
+    # contents, which must not leak into the next result
+    for seed, sizes in ((41, [2000, 1, 129, 700]), (42, [64, 3000, 0, 65, 5000])):
+        x, cu = synth.gen_events(seed, sizes)
+        ref = _call("mlpf_forward", model, x, cu, prec, max(sizes))
+        got = _call("mlpf_forward_noalloc", model, x, cu, prec, max(sizes))
+        # same kernels and arithmetic: identical within the tests' tolerance
+        # (they are in fact bitwise equal)
+        for a, b in zip(got, ref):
+            np.testing.assert_allclose(a, b, rtol=1e-6, atol=1e-6)
+        assert (got[2] == ref[2]).all()
+    model.close()
+
+
+def test_noalloc_rejects_oversize_and_fp32():
+    model, _ = make_model(synth.SMALL, 0)
+    x, cu = synth.gen_events(43, [16385])
+    with pytest.raises(MlpfError) as ei:
+        _call("mlpf_forward_noalloc", model, x, cu, _lib.MLPF_FP16, 16385)
+    assert ei.value.status == _lib.MLPF_E_INVALID
+    x, cu = synth.gen_events(44, [10])
+    with pytest.raises(MlpfError) as ei:
+        _call("mlpf_forward_noalloc", model, x, cu, _lib.MLPF_FP32, 10)
+    assert ei.value.status == _lib.MLPF_E_UNSUPPORTED
+    model.close()
