@@ -41,7 +41,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp16", "fp32"])
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp16", "fp8", "fp32"])
     ap.add_argument("--no-baselines", action="store_true",
                     help="skip the FP32-plain, per-event-latency and CPU-oracle legs")
     ap.add_argument("--events", type=int, default=512,
@@ -262,6 +262,11 @@ def run_ours(args):
     def step():
         model.forward(xd, cud, max_n, precision=prec, logits=lo, reg=rg, cls=cl, event_sums=su)
 
+    if prec == "fp8":
+        # static per-tensor activation scales from 32 calibration events (seed 999)
+        csz = synth.sizes_lognormal(999, 32)
+        cx, ccu = synth.gen_events(999, csz)
+        model.calibrate_fp8(torch.from_numpy(cx).to(dev), torch.from_numpy(ccu).to(dev), int(csz.max()))
     model.set_option(_lib.OPT_PROFILE, 1)
     for _ in range(max(args.warmup, 3)):
         step()

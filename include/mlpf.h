@@ -44,7 +44,7 @@ typedef enum {
 typedef enum {
     MLPF_FP32 = 0, /* plain path: SIMT FP32 FFMA GEMMs and attention, no TF32 */
     MLPF_BF16 = 1, /* tcgen05 tensor cores, BF16 operands, FP32 accumulation */
-    MLPF_FP8 = 2,  /* E4M3 projection/FFN GEMMs with per-tensor scales (16-bit attention) */
+    MLPF_FP8 = 2,  /* E4M3 GEMMs with per-tensor scales, FP16 attention (needs mlpf_calibrate_fp8) */
     MLPF_FP16 = 3  /* as MLPF_BF16 with FP16 operands (same tensor-core rate, 3 more mantissa bits) */
 } mlpf_precision;
 
@@ -154,6 +154,25 @@ mlpf_status mlpf_forward_noalloc(mlpf_model* m, int32_t precision,
                                  int32_t n_events, int32_t total, int32_t max_n,
                                  float* logits, float* reg, int32_t* cls,
                                  double* event_sums, void* stream);
+
+/*
+ * Static FP8 calibration (per-tensor scales of the E4M3 GEMMs).  Runs the FP16
+ * tensor-core forward on the given calibration events (device buffers, as in
+ * mlpf_forward) while recording, for every GEMM input (activation), the largest
+ * |value| over valid elements; sets that input's scale to amax / 448 (the
+ * largest finite E4M3).  Weight scales are set at load time the same way from
+ * each weight matrix.  Synchronous; must precede the first MLPF_FP8 forward
+ * (otherwise MLPF_E_INVALID) and replaces earlier scales.
+ */
+mlpf_status mlpf_calibrate_fp8(mlpf_model* m, const float* x, const int32_t* cu_seqlens,
+                               int32_t n_events, int32_t total, int32_t max_n, void* stream);
+
+/*
+ * Names (cap x 32 bytes, or NULL) and activation scales (cap floats, or NULL)
+ * of the FP8 calibration; returns the number of activation slots, 0 before
+ * calibration, -1 on error.
+ */
+int32_t mlpf_get_fp8_scales(const mlpf_model* m, int32_t cap, char* names, float* scales);
 
 /*
  * Wait for the model's work on `stream` and report device-side status:

@@ -105,6 +105,23 @@ class Model:
                                        _ptr(event_sums), s))
         return logits, reg, cls, event_sums
 
+    def calibrate_fp8(self, x, cu_seqlens, max_n: int, stream=None):
+        """Static FP8 activation scales from an FP16 run on these events (device tensors)."""
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream(self.device).cuda_stream
+        check(self.L.mlpf_calibrate_fp8(self.h, _ptr(x), _ptr(cu_seqlens), cu_seqlens.shape[0] - 1,
+                                        x.shape[0], int(max_n), ctypes.c_void_p(s)))
+
+    def fp8_scales(self) -> dict:
+        """Activation scales of the FP8 calibration, by GEMM input."""
+        n = self.L.mlpf_get_fp8_scales(self.h, 0, None, None)
+        if n <= 0:
+            return {}
+        names = ctypes.create_string_buffer(32 * n)
+        vals = (ctypes.c_float * n)()
+        self.L.mlpf_get_fp8_scales(self.h, n, names, vals)
+        return {names.raw[32 * i:32 * (i + 1)].split(b"\0")[0].decode(): vals[i] for i in range(n)}
+
     def sync(self, stream=None):
         """Wait for the stream and raise on a device-side timeout / non-finite output."""
         import torch

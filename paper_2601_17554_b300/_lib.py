@@ -15,7 +15,8 @@ OPT_USE_GRAPHS, OPT_WAIT_LIMIT_NS, OPT_DEBUG_STALL, OPT_ATTN_CTAS_PER_SM, OPT_AT
 
 # every symbol include/mlpf.h declares
 EXPORTS = ("mlpf_load_weights", "mlpf_free", "mlpf_get_config", "mlpf_forward",
-           "mlpf_forward_host", "mlpf_forward_noalloc", "mlpf_sync", "mlpf_set_option", "mlpf_get_option",
+           "mlpf_forward_host", "mlpf_forward_noalloc", "mlpf_calibrate_fp8", "mlpf_get_fp8_scales",
+           "mlpf_sync", "mlpf_set_option", "mlpf_get_option",
            "mlpf_last_launch_count", "mlpf_profile_get", "mlpf_last_error", "mlpf_abi_version")
 
 
@@ -52,6 +53,10 @@ def load(build_if_missing: bool = True):
     L.mlpf_forward_host.restype = ctypes.c_int
     L.mlpf_forward_noalloc.argtypes = fwd
     L.mlpf_forward_noalloc.restype = ctypes.c_int
+    L.mlpf_calibrate_fp8.argtypes = [vp, vp, vp, i32, i32, i32, vp]
+    L.mlpf_calibrate_fp8.restype = ctypes.c_int
+    L.mlpf_get_fp8_scales.argtypes = [vp, i32, ctypes.c_char_p, ctypes.POINTER(ctypes.c_float)]
+    L.mlpf_get_fp8_scales.restype = i32
     L.mlpf_sync.argtypes = [vp, vp]
     L.mlpf_sync.restype = ctypes.c_int
     L.mlpf_set_option.argtypes = [vp, i32, i64]

@@ -291,13 +291,13 @@ static mlpf_status validate(const Model* m, int32_t prec, const void* x, const v
     if (total > 0 && n_events == 0) { set_error("total > 0 with no events"); return MLPF_E_INVALID; }
     if (total > 0 && (!x || !cu || !logits || !reg)) { set_error("NULL input or output pointer"); return MLPF_E_INVALID; }
     if (n_events > 0 && !cu) { set_error("cu_seqlens is NULL"); return MLPF_E_INVALID; }
-    if (prec == MLPF_FP8) {
-        set_error("the FP8 path is not built in this version");
-        return MLPF_E_UNSUPPORTED;
-    }
     if (prec != MLPF_FP32 && !m->tc_supported) {
         set_error("tensor-core path is built for d=64, 4 heads, FFN 256 models only");
         return MLPF_E_UNSUPPORTED;
+    }
+    if (prec == MLPF_FP8 && !m->fp8_ready) {
+        set_error("MLPF_FP8 needs activation scales: call mlpf_calibrate_fp8 first");
+        return MLPF_E_INVALID;
     }
     return MLPF_OK;
 }
@@ -460,6 +460,7 @@ void mlpf_free(mlpf_model* mm) {
     if (m.w.img8_base) cudaFree(m.w.img8_base);
     if (m.w.tc_f32_base) cudaFree(m.w.tc_f32_base);
     if (m.status) cudaFree(m.status);
+    if (m.amax_dev) cudaFree(m.amax_dev);
     delete mm;
 }
 
@@ -523,6 +524,62 @@ mlpf_status mlpf_forward_host(mlpf_model* mm, int32_t precision, const float* x,
     if (event_sums && n_events > 0)
         CK(cudaMemcpyAsync(event_sums, w.hsums, (size_t)n_events * 3 * 8, cudaMemcpyDeviceToHost, st));
     return mlpf_sync(mm, stream);
+}
+
+mlpf_status mlpf_calibrate_fp8(mlpf_model* mm, const float* x, const int32_t* cu_seqlens,
+                               int32_t n_events, int32_t total, int32_t max_n, void* stream) {
+    mlpf_status s = validate(mm ? &mm->impl : nullptr, MLPF_FP16, x, cu_seqlens, n_events, total, max_n,
+                             x, x);
+    if (s != MLPF_OK) return s;
+    if (total == 0) { set_error("calibration needs at least one element"); return MLPF_E_INVALID; }
+    Model& m = mm->impl;
+    CK(cudaSetDevice(m.device));
+    s = ensure_workspace(m, total, n_events, true);
+    if (s != MLPF_OK) return s;
+    if (!m.amax_dev) CK(cudaMalloc(&m.amax_dev, 64 * sizeof(unsigned)));
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaMemsetAsync(m.amax_dev, 0, 64 * sizeof(unsigned), st));
+    Workspace& w = m.ws;
+    m.calibrating = true;
+    m.cur_prof = nullptr;
+    const int64_t n = run_forward_tc(m, MLPF_FP16, x, cu_seqlens, n_events, total, max_n, w.hlogits,
+                                     w.hreg_out, st);
+    m.calibrating = false;
+    if (n < 0) { set_error("calibration launch failed"); return MLPF_E_CUDA; }
+    unsigned host[64];
+    CK(cudaMemcpyAsync(host, m.amax_dev, sizeof(host), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    s = mlpf_sync(mm, stream);
+    if (s != MLPF_OK) return s;
+    // static per-tensor activation scale s_a = amax / 448 (the largest finite E4M3)
+    for (auto& kv : m.act_slot) {
+        float a;
+        std::memcpy(&a, &host[kv.second], 4);
+        m.act_scale[kv.second] = a > 0.f ? a / 448.f : 1.f;
+    }
+    m.fp8_ready = true;
+    for (auto& g : m.graphs) { cudaGraphExecDestroy(g.second.exec); prof_destroy(g.second.prof); }
+    m.graphs.clear();
+    m.last_prof = nullptr;
+    return MLPF_OK;
+}
+
+int32_t mlpf_get_fp8_scales(const mlpf_model* mm, int32_t cap, char* names, float* scales) {
+    if (!mm) { set_error("model is NULL"); return -1; }
+    const Model& m = mm->impl;
+    if (!m.fp8_ready) return 0;
+    int i = 0;
+    for (auto& kv : m.act_slot) {
+        if (i < cap) {
+            if (names) {
+                std::memset(names + 32 * i, 0, 32);
+                std::strncpy(names + 32 * i, kv.first.c_str(), 31);
+            }
+            if (scales) scales[i] = m.act_scale[kv.second];
+        }
+        ++i;
+    }
+    return i;
 }
 
 mlpf_status mlpf_set_option(mlpf_model* mm, int32_t option, int64_t value) {

@@ -99,6 +99,12 @@ struct Model {
     int64_t wait_limit_ns = 2000000000LL;
     bool debug_stall = false;
     int attn_ctas_per_sm = 1;
+    // FP8: activation slots (one per GEMM input) and their static scales s_a = amax / 448
+    std::map<std::string, int> act_slot;
+    std::vector<float> act_scale;
+    bool fp8_ready = false;
+    bool calibrating = false;       // 16-bit forward that records per-slot amax
+    unsigned* amax_dev = nullptr;   // [64] max |activation| per slot (float bits)
     int embed_ctas_per_sm = 1;   // measured occupancy of the embedding kernels
     int64_t last_launches = 0;
     cudaStream_t cap_stream = nullptr;
@@ -130,5 +136,6 @@ int64_t run_event_sums(Model& m, const int32_t* cu, int n_events, const float* l
 // tensor-core path preparation (weights images, tensor maps)
 bool tc_prepare_weights(Model& m);
 bool tc_make_maps(Model& m);
+int act_slot(Model& m, const std::string& name);
 
 }  // namespace mlpf

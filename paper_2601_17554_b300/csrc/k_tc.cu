@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -47,18 +48,35 @@ MLPF_DEV uint8_t* align1024(uint8_t* p) {
 MLPF_DEV float gelu_f(float v) { return 0.5f * v * (1.0f + erff(v * 0.70710678118654752f)); }
 MLPF_DEV float act_f(float v, int act) { return act == 1 ? fmaxf(v, 0.f) : gelu_f(v); }
 
+// GEMM operand formats of the row-tile kernels.  A 128-byte swizzle atom holds
+// 64 16-bit or 128 E4M3 K-elements; one K-step is 32 bytes in every format
+// (16 elements of kind::f16, 32 of kind::f8f6f4).  A K=64 operand in E4M3 uses
+// the first half of an atom (chunks 0..3); the rest stays zero.
+enum : int { FMT_BF16 = 0, FMT_FP16 = 1, FMT_E4M3 = 2 };
+template <int FMT>
+constexpr bool kIs8 = FMT == FMT_E4M3;
+// 16-bit format of Q, K, V^T, O and h_pid (attention inputs/outputs): FP16 unless BF16
+template <int FMT>
+constexpr bool kOutF16 = FMT != FMT_BF16;
+// K-elements per 128-byte atom
+template <int FMT>
+constexpr int kAtomK = kIs8<FMT> ? 128 : 64;
+
 // Issue a [128 x K] x [N x K]^T GEMM from swizzled smem tiles into TMEM columns.
-// a_ncols_atoms: K/64.  b tile: N rows per atom column.
+// katoms: number of 128-byte atom columns in K.  b tile: N rows per atom column.
 // accumulate: add to the existing accumulator from the first k-step on.
-template <bool F16>
+template <int FMT>
 MLPF_DEV void issue_gemm(uint32_t d_tmem, const uint8_t* a, const uint8_t* b, int N, int katoms,
                          bool accumulate = false) {
-    const uint32_t idesc = idesc_f16(128, N, F16 ? 0u : 1u);
     const uint32_t a0 = smem_u32(a), b0 = smem_u32(b);
     for (int kc = 0; kc < katoms * 4; ++kc) {
         const uint32_t ao = a0 + (kc >> 2) * ATOM + (kc & 3) * 32;
         const uint32_t bo = b0 + (kc >> 2) * (N * 128) + (kc & 3) * 32;
-        mma_f16(d_tmem, sdesc_sw128(ao), sdesc_sw128(bo), idesc, (kc > 0 || accumulate) ? 1u : 0u);
+        const uint32_t acc = (kc > 0 || accumulate) ? 1u : 0u;
+        if constexpr (kIs8<FMT>)
+            mma_f8(d_tmem, sdesc_sw128(ao), sdesc_sw128(bo), idesc_e4m3(128, N), acc);
+        else
+            mma_f16(d_tmem, sdesc_sw128(ao), sdesc_sw128(bo), idesc_f16(128, N, FMT == FMT_FP16 ? 0u : 1u), acc);
     }
 }
 
@@ -69,17 +87,45 @@ MLPF_DEV void ld_row64(uint32_t taddr, float* v) {
     tmem_wait_ld();
 }
 
-// Store 64 floats of row r in the 16-bit operand format into atom column `tile` (swizzled).
-template <bool F16>
-MLPF_DEV void st_row16(uint8_t* tile, int r, const float* v) {
+MLPF_DEV uint32_t pack_e4m3x4(float a, float b, float c, float d) {
+    uint16_t lo, hi;
+    asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(lo) : "f"(b), "f"(a));
+    asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(hi) : "f"(d), "f"(c));
+    return (uint32_t)lo | ((uint32_t)hi << 16);
+}
+
+// Store n (a multiple of 32) values of row r, starting at K-column k0, into the
+// A-operand tile `tile` in format FMT (swizzled 128-byte rows; K-columns beyond
+// one atom continue in the next atom column).  E4M3 values are v * qs.
+// zero_hi (E4M3, K=64 operands): also clear the matching chunk of the unused
+// upper half of the atom (the tile may hold other data there).
+template <int FMT>
+MLPF_DEV void st_op(uint8_t* tile, int r, const float* v, int n, int k0, float qs, bool zero_hi = false) {
+    if constexpr (kIs8<FMT>) {
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        uint4 u;
-        u.x = pack2<F16>(v[8 * c + 0], v[8 * c + 1]);
-        u.y = pack2<F16>(v[8 * c + 2], v[8 * c + 3]);
-        u.z = pack2<F16>(v[8 * c + 4], v[8 * c + 5]);
-        u.w = pack2<F16>(v[8 * c + 6], v[8 * c + 7]);
-        *(uint4*)(tile + sw128_off(r, c)) = u;
+        for (int c = 0; c < n / 16; ++c) {
+            const int k = k0 + 16 * c;
+            const float* w = v + 16 * c;
+            uint4 u;
+            u.x = pack_e4m3x4(w[0] * qs, w[1] * qs, w[2] * qs, w[3] * qs);
+            u.y = pack_e4m3x4(w[4] * qs, w[5] * qs, w[6] * qs, w[7] * qs);
+            u.z = pack_e4m3x4(w[8] * qs, w[9] * qs, w[10] * qs, w[11] * qs);
+            u.w = pack_e4m3x4(w[12] * qs, w[13] * qs, w[14] * qs, w[15] * qs);
+            *(uint4*)(tile + (k >> 7) * ATOM + sw128_off(r, (k & 127) >> 4)) = u;
+            if (zero_hi) *(uint4*)(tile + sw128_off(r, ((k & 127) >> 4) + 4)) = make_uint4(0, 0, 0, 0);
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < n / 8; ++c) {
+            const int k = k0 + 8 * c;
+            const float* w = v + 8 * c;
+            uint4 u;
+            u.x = pack2<FMT == FMT_FP16>(w[0], w[1]);
+            u.y = pack2<FMT == FMT_FP16>(w[2], w[3]);
+            u.z = pack2<FMT == FMT_FP16>(w[4], w[5]);
+            u.w = pack2<FMT == FMT_FP16>(w[6], w[7]);
+            *(uint4*)(tile + (k >> 6) * ATOM + sw128_off(r, (k & 63) >> 3)) = u;
+        }
     }
 }
 
@@ -95,6 +141,29 @@ MLPF_DEV void st_global_row64(uint16_t* dst, const float* v) {
         u.w = pack2<F16>(v[8 * c + 6], v[8 * c + 7]);
         d4[c] = u;
     }
+}
+
+// 16-bit pair -> two floats
+template <bool F16>
+MLPF_DEV void unpack2(uint32_t u, float& a, float& b) {
+    if constexpr (F16) {
+        const __half2 h = *reinterpret_cast<const __half2*>(&u);
+        const float2 f = __half22float2(h);
+        a = f.x;
+        b = f.y;
+    } else {
+        a = __uint_as_float(u << 16);
+        b = __uint_as_float(u & 0xffff0000u);
+    }
+}
+
+// Record max |v| of valid rows into amax[slot] (calibration of FP8 scales).
+MLPF_DEV void record_amax(unsigned* amax, int slot, const float* v, int n, bool valid) {
+    float mx = 0.f;
+    for (int i = 0; i < n; ++i) mx = fmaxf(mx, fabsf(v[i]));
+    unsigned u = valid ? __float_as_uint(mx) : 0u;
+    u = __reduce_max_sync(0xffffffffu, u);
+    if ((threadIdx.x & 31) == 0 && u) atomicMax(amax + slot, u);
 }
 
 // In-place LayerNorm of a 64-vector (two-pass FP32 moments, biased variance).
@@ -114,11 +183,8 @@ MLPF_DEV void layernorm64(const float* z, float* out, const float* g, const floa
     for (int i = 0; i < D; ++i) out[i] = (z[i] - mu) * rs * __ldg(g + i) + __ldg(b + i);
 }
 
-// Load this row's 42 input features, convert to bf16 and store them (zero
-// padded to 64 columns) into the swizzled atom column.
-template <bool F16>
-MLPF_DEV void load_x_row(uint8_t* tile, int r, const float* x, bool valid, int prow) {
-    float v[64];
+// This row's 42 input features, zero padded to 64.
+MLPF_DEV void load_x_row(float* v, const float* x, bool valid, int prow) {
 #pragma unroll
     for (int i = 0; i < 64; ++i) v[i] = 0.f;
     if (valid) {
@@ -130,7 +196,6 @@ MLPF_DEV void load_x_row(uint8_t* tile, int r, const float* x, bool valid, int p
             v[2 * i + 1] = t.y;
         }
     }
-    st_row16<F16>(tile, r, v);
 }
 
 struct RowInfo {
@@ -148,23 +213,24 @@ MLPF_DEV RowInfo row_info(const int4* blk, int nblk, int p) {
     return ri;
 }
 
-// Q, K rows and transposed V (zero for padding rows) from the QKV accumulator.
+// Q, K rows and transposed V (zero for padding rows) from the QKV accumulator,
+// acc * ds + bias, stored in the 16-bit attention format.
 template <bool F16>
-MLPF_DEV void store_qkv(uint32_t tacc, const float* bqkv, int p, bool valid, uint16_t* q,
+MLPF_DEV void store_qkv(uint32_t tacc, const float* bqkv, float ds, int p, bool valid, uint16_t* q,
                         uint16_t* k, uint16_t* vt, long ldvt) {
     float v[64];
     ld_row64(tacc, v);
 #pragma unroll
-    for (int i = 0; i < 64; ++i) v[i] += __ldg(bqkv + i);
+    for (int i = 0; i < 64; ++i) v[i] = fmaf(v[i], ds, __ldg(bqkv + i));
     st_global_row64<F16>(q + (size_t)p * D, v);
     ld_row64(tacc + 64, v);
 #pragma unroll
-    for (int i = 0; i < 64; ++i) v[i] += __ldg(bqkv + 64 + i);
+    for (int i = 0; i < 64; ++i) v[i] = fmaf(v[i], ds, __ldg(bqkv + 64 + i));
     st_global_row64<F16>(k + (size_t)p * D, v);
     ld_row64(tacc + 128, v);
 #pragma unroll
     for (int i = 0; i < 64; ++i) {
-        const float t = valid ? v[i] + __ldg(bqkv + 128 + i) : 0.f;
+        const float t = valid ? fmaf(v[i], ds, __ldg(bqkv + 128 + i)) : 0.f;
         vt[(size_t)i * ldvt + p] = (uint16_t)(pack2<F16>(t, 0.f) & 0xffffu);
     }
 }
@@ -255,26 +321,36 @@ struct EmbedParams {
     const float* x;
     const int4* blk;
     const int* counters;
-    const uint8_t* w1;   // [64 x 64] or [64 x 128] image
+    const uint8_t* w1;   // [64 x K1] image (K1: 42 -> one atom; 42 + 64 -> one E4M3 or two 16-bit atoms)
     const uint8_t* w2;   // [64 x 64]
     const uint8_t* wqkv; // [192 x 64]
     const float *b1, *b2, *lng, *lnb, *bqkv;
+    const uint16_t* hp;  // MODE 1: h_pid rows (16-bit), read per thread in E4M3 mode and calibration
     float* z;
     uint16_t *q, *k, *vt;
     long ldvt;
     unsigned* status;
     uint64_t wait_ns;
     int act;
+    // E4M3: qs[i] = 1/s_a of A operand i (input, hidden, LN1); ds[i] = s_a * s_w of GEMM i
+    // (1 in the 16-bit formats)
+    float qs[3], ds[3];
+    unsigned* amax;      // calibration: max |A operand| of valid rows per slot, or NULL
+    int slot[3];
 };
 
-// F16: operands in FP16 (else BF16), FP32 accumulation either way.
-template <int MODE, bool F16>  // MODE 0: input x (K = 42 -> 64); 1: concat(x, h_pid) (K = 128)
+// FMT: GEMM operand format (BF16, FP16 or E4M3), FP32 accumulation in every case.
+// The embedding FFN runs in FE (FP16 when FMT is E4M3: only the projection and FFN
+// GEMMs of the encoder blocks use E4M3); the QKV projection runs in FMT.
+template <int MODE, int FMT>  // MODE 0: input x (K = 42 -> 64); 1: concat(x, h_pid) (K = 106 -> 128)
 __global__ void __launch_bounds__(128, 1) k_embed_qkv(const __grid_constant__ CUtensorMap map_hp,
                                                       EmbedParams p) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sm = align1024(smem_raw);
-    constexpr int KA = MODE == 0 ? 1 : 2;
+    constexpr int FE = kIs8<FMT> ? FMT_FP16 : FMT;
+    constexpr int KA = MODE == 0 ? 1 : 2;  // atoms of the first GEMM's A operand
     constexpr uint32_t W1B = 64 * 128 * KA, W2B = 64 * 128, WQB = 192 * 128;
+    constexpr bool TMA_HP = MODE == 1;
     uint8_t* sW1 = sm;
     uint8_t* sW2 = sW1 + W1B;
     uint8_t* sWq = sW2 + W2B;
@@ -320,19 +396,39 @@ __global__ void __launch_bounds__(128, 1) k_embed_qkv(const __grid_constant__ CU
         const int p0 = tile * ROWS;
         const int prow_pad = p0 + tid;
         const RowInfo ri = row_info(p.blk, nblk, prow_pad);
-        if (MODE == 1 && tid == 0) {
+        if (TMA_HP && tid == 0) {
             mbar_arrive_expect_tx(&bars[1], ATOM);
             tma_load_2d(sA + ATOM, &map_hp, 0, p0, &bars[1]);
         }
-        load_x_row<F16>(sA, tid, p.x, ri.valid, ri.prow);
+        float v[64];
+        load_x_row(v, p.x, ri.valid, ri.prow);
+        st_op<FE>(sA, tid, v, 64, 0, 1.f);
+        float amx = 0.f;
+        if (p.amax) {
+#pragma unroll
+            for (int i = 0; i < 42; ++i) amx = fmaxf(amx, fabsf(v[i]));
+        }
+        if (MODE == 1 && p.amax) {
+            // h_pid row of this element (16-bit, as written by the PID stack)
+            const uint4* src = (const uint4*)(p.hp + (size_t)prow_pad * D);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const uint4 u = src[c];
+                unpack2<kOutF16<FMT>>(u.x, v[8 * c], v[8 * c + 1]);
+                unpack2<kOutF16<FMT>>(u.y, v[8 * c + 2], v[8 * c + 3]);
+                unpack2<kOutF16<FMT>>(u.z, v[8 * c + 4], v[8 * c + 5]);
+                unpack2<kOutF16<FMT>>(u.w, v[8 * c + 6], v[8 * c + 7]);
+            }
+#pragma unroll
+            for (int i = 0; i < 64; ++i) amx = fmaxf(amx, fabsf(v[i]));
+        }
+        if (p.amax) record_amax(p.amax, p.slot[0], &amx, 1, ri.valid);
         fence_proxy_async_smem();
         __syncthreads();
         if (tid == 0) {
-            if (MODE == 1) {
-                fail |= !mbar_wait(&bars[1], aph, ab, p.status, ST_TIMEOUT_GEMM, p.wait_ns);
-            }
+            if (TMA_HP) fail |= !mbar_wait(&bars[1], aph, ab, p.status, ST_TIMEOUT_GEMM, p.wait_ns);
             tc_fence_after();
-            if (!fail) issue_gemm<F16>(tbase, sA, sW1, 64, KA);
+            if (!fail) issue_gemm<FE>(tbase, sA, sW1, 64, KA);
             mma_commit(&bars[2]);
         }
         aph ^= 1;
@@ -340,17 +436,17 @@ __global__ void __launch_bounds__(128, 1) k_embed_qkv(const __grid_constant__ CU
         mph ^= 1;
         if (__syncthreads_or(fail)) break;
         tc_fence_after();
-        float v[64];
         ld_row64(trow, v);
 #pragma unroll
         for (int i = 0; i < 64; ++i) v[i] = act_f(v[i] + __ldg(p.b1 + i), p.act);
-        st_row16<F16>(sH, tid, v);
+        if (p.amax) record_amax(p.amax, p.slot[1], v, 64, ri.valid);
+        st_op<FE>(sH, tid, v, 64, 0, 1.f);
         tc_fence_before();
         fence_proxy_async_smem();
         __syncthreads();
         if (tid == 0) {
             tc_fence_after();
-            issue_gemm<F16>(tbase, sH, sW2, 64, 1);
+            issue_gemm<FE>(tbase, sH, sW2, 64, 1);
             mma_commit(&bars[2]);
         }
         fail |= !mbar_wait(&bars[2], mph, ab, p.status, ST_TIMEOUT_GEMM, p.wait_ns);
@@ -366,20 +462,21 @@ __global__ void __launch_bounds__(128, 1) k_embed_qkv(const __grid_constant__ CU
             for (int i = 0; i < 16; ++i) zd[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
         }
         layernorm64(v, v, p.lng, p.lnb);
-        st_row16<F16>(sH, tid, v);
+        if (p.amax) record_amax(p.amax, p.slot[2], v, 64, ri.valid);
+        st_op<FMT>(sH, tid, v, 64, 0, p.qs[2], true);
         tc_fence_before();
         fence_proxy_async_smem();
         __syncthreads();
         if (tid == 0) {
             tc_fence_after();
-            issue_gemm<F16>(tbase, sH, sWq, 192, 1);
+            issue_gemm<FMT>(tbase, sH, sWq, 192, 1);
             mma_commit(&bars[2]);
         }
         fail |= !mbar_wait(&bars[2], mph, ab, p.status, ST_TIMEOUT_GEMM, p.wait_ns);
         mph ^= 1;
         if (__syncthreads_or(fail)) break;
         tc_fence_after();
-        store_qkv<F16>(trow, p.bqkv, prow_pad, ri.valid, p.q, p.k, p.vt, p.ldvt);
+        store_qkv<kOutF16<FMT>>(trow, p.bqkv, p.ds[2], prow_pad, ri.valid, p.q, p.k, p.vt, p.ldvt);
         tc_fence_before();
     }
     __syncthreads();
@@ -412,13 +509,20 @@ struct PostParams {
     unsigned* status;
     uint64_t wait_ns;
     int act;
+    // E4M3: qs = 1/s_a of the A operands (O, LN2, FFN hidden, a, b); ds = s_a * s_w of
+    // the GEMMs (out-proj, FFN up, FFN down, a, b); 1 in the 16-bit formats
+    float qs[5], ds[5];
+    unsigned* amax;  // calibration: max |A operand| of valid rows per slot, or NULL
+    int slot[5];
 };
 
 // parameter vector offsets (floats) in shared memory
 constexpr int PV_BO = 0, PV_LN2G = 64, PV_LN2B = 128, PV_BUP = 192, PV_BDN = 448, PV_LNG = 512,
               PV_LNB = 576, PV_BA = 640, PV_BB = 896, PV_N = 912;
 constexpr int PT_THREADS = 512;   // two teams x two warpgroups
-constexpr uint32_t PT_TEAM_BYTES = ATOM + 2 * ATOM;  // sA (64 cols) + sH (128 cols)
+// per team: sA (64-column operands) + sH (128 hidden columns: two 16-bit atoms, or one
+// E4M3 atom followed by the 16-bit staging tile of the attention output)
+constexpr uint32_t PT_TEAM_BYTES = 3 * ATOM;
 constexpr int PT_RED_FLOATS = 2 * 2 * 128;            // per team: [pass][wg][row] LN partial sums
 
 MLPF_DEV bool team_sync_or(int team, bool pred) {
@@ -462,26 +566,17 @@ MLPF_DEV void layernorm_split(const float* z32, float* out32, const float* g, co
     for (int i = 0; i < 32; ++i) out32[i] = (z32[i] - mu) * rs * g[32 * wg + i] + b[32 * wg + i];
 }
 
-// Store 32 of a row's 64 columns (half `wg`) as 16-bit into the swizzled atom column.
-template <bool F16>
-MLPF_DEV void st_row_half16(uint8_t* tile, int r, const float* v32, int wg) {
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        uint4 u;
-        u.x = pack2<F16>(v32[8 * c + 0], v32[8 * c + 1]);
-        u.y = pack2<F16>(v32[8 * c + 2], v32[8 * c + 3]);
-        u.z = pack2<F16>(v32[8 * c + 4], v32[8 * c + 5]);
-        u.w = pack2<F16>(v32[8 * c + 6], v32[8 * c + 7]);
-        *(uint4*)(tile + sw128_off(r, 4 * wg + c)) = u;
-    }
-}
-
-template <int MODE, bool F16>  // 0: next layer LN1 + QKV; 1: end of PID stack; 2: end of regression stack
+template <int MODE, int FMT>  // 0: next layer LN1 + QKV; 1: end of PID stack; 2: end of regression stack
 __global__ void __launch_bounds__(PT_THREADS, 1) k_post(const __grid_constant__ CUtensorMap map_o,
                                                         PostParams p) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sm = align1024(smem_raw);
-    constexpr uint32_t WOB = 64 * 128, WUB = 256 * 128, WDB = 4 * 64 * 128;
+    // FMT: out-projection, FFN and QKV GEMMs; FH: output heads (FP16 when FMT is E4M3)
+    constexpr int FH = kIs8<FMT> ? FMT_FP16 : FMT;
+    constexpr bool F16 = kOutF16<FMT>;           // 16-bit format of O, Q, K, V^T, h_pid
+    constexpr int HA = kIs8<FMT> ? 1 : 2;        // atoms of a 128-column FFN hidden operand
+    constexpr int KA256 = 256 / kAtomK<FMT>;     // atoms of the 256-column FFN-down operand
+    constexpr uint32_t WOB = 64 * 128, WUB = 256 * 128, WDB = KA256 * 64 * 128;
     constexpr uint32_t WAB = MODE == 0 ? 192 * 128 : (MODE == 1 ? 64 * 128 : 256 * 128);
     constexpr uint32_t WBB = MODE == 0 ? 0 : (MODE == 1 ? 16 * 128 : 4 * 16 * 128);
     uint8_t* sWo = sm;
@@ -500,6 +595,7 @@ __global__ void __launch_bounds__(PT_THREADS, 1) k_post(const __grid_constant__ 
     const bool leader = (tid & 255) == 0;
     uint8_t* sA = sTeam0 + team * PT_TEAM_BYTES;
     uint8_t* sH = sA + ATOM;
+    uint8_t* sO16 = kIs8<FMT> ? sA + 2 * ATOM : sA;  // where the attention output lands
     uint64_t* tma_bar = &bars[1 + 2 * team];
     uint64_t* mma_bar = &bars[2 + 2 * team];
     float* red = red_all + team * PT_RED_FLOATS;
@@ -571,7 +667,7 @@ __global__ void __launch_bounds__(PT_THREADS, 1) k_post(const __grid_constant__ 
         const RowInfo ri = row_info(p.blk, nblk, pp);
         if (leader) {
             mbar_arrive_expect_tx(tma_bar, ATOM);
-            tma_load_2d(sA, &map_o, 0, tile * ROWS, tma_bar);
+            tma_load_2d(sO16, &map_o, 0, tile * ROWS, tma_bar);
         }
         float zr[32], v[32];   // this warpgroup's 32 columns of the residual row
         {
@@ -584,29 +680,44 @@ __global__ void __launch_bounds__(PT_THREADS, 1) k_post(const __grid_constant__ 
         }
         fail |= !mbar_wait(tma_bar, aph, ab, p.status, ST_TIMEOUT_GEMM, p.wait_ns);
         aph ^= 1;
+        if (kIs8<FMT> || p.amax) {
+            // this warpgroup's 32 columns of the attention output (16-bit swizzled tile)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const uint4 u = *(const uint4*)(sO16 + sw128_off(r, 4 * wg + c));
+                unpack2<F16>(u.x, v[8 * c], v[8 * c + 1]);
+                unpack2<F16>(u.y, v[8 * c + 2], v[8 * c + 3]);
+                unpack2<F16>(u.z, v[8 * c + 4], v[8 * c + 5]);
+                unpack2<F16>(u.w, v[8 * c + 6], v[8 * c + 7]);
+            }
+            if (p.amax) record_amax(p.amax, p.slot[0], v, 32, ri.valid);
+            if constexpr (kIs8<FMT>) st_op<FMT>(sA, r, v, 32, 32 * wg, p.qs[0], true);
+        }
         // out-projection + residual, LN2
-        if (!run_mma([&] { issue_gemm<F16>(tbase, sA, sWo, 64, 1); })) break;
+        if (!run_mma([&] { issue_gemm<FMT>(tbase, sA, sWo, 64, 1); })) break;
         tmem_ld32(trow + 32 * wg, v);
         tmem_wait_ld();
 #pragma unroll
-        for (int i = 0; i < 32; ++i) zr[i] += v[i] + pv[PV_BO + 32 * wg + i];
+        for (int i = 0; i < 32; ++i) zr[i] += fmaf(v[i], p.ds[0], pv[PV_BO + 32 * wg + i]);
         layernorm_split(zr, v, pv + PV_LN2G, pv + PV_LN2B, wg, r, team, red);
-        st_row_half16<F16>(sA, r, v, wg);
+        if (p.amax) record_amax(p.amax, p.slot[1], v, 32, ri.valid);
+        st_op<FMT>(sA, r, v, 32, 32 * wg, p.qs[1], true);
         // FFN: two halves of 128 hidden columns, GELU, down-projection accumulated
         bool stop = false;
 #pragma unroll 1
         for (int half = 0; half < 2 && !stop; ++half) {
-            if (!run_mma([&] { issue_gemm<F16>(tbase, sA, sWu + half * 128 * 128, 128, 1); })) { stop = true; break; }
+            if (!run_mma([&] { issue_gemm<FMT>(tbase, sA, sWu + half * 128 * 128, 128, 1); })) { stop = true; break; }
 #pragma unroll
             for (int q2 = 0; q2 < 2; ++q2) {
                 tmem_ld32(trow + 64 * wg + 32 * q2, v);
                 tmem_wait_ld();
 #pragma unroll
                 for (int i = 0; i < 32; ++i)
-                    v[i] = act_f(v[i] + pv[PV_BUP + 128 * half + 64 * wg + 32 * q2 + i], p.act);
-                st_row_half16<F16>(sH + wg * ATOM, r, v, q2);
+                    v[i] = act_f(fmaf(v[i], p.ds[1], pv[PV_BUP + 128 * half + 64 * wg + 32 * q2 + i]), p.act);
+                if (p.amax) record_amax(p.amax, p.slot[2], v, 32, ri.valid);
+                st_op<FMT>(sH, r, v, 32, 64 * wg + 32 * q2, p.qs[2]);
             }
-            if (!run_mma([&] { issue_gemm<F16>(tbase + 128, sH, sWd + half * 2 * 64 * 128, 64, 2, half > 0); })) {
+            if (!run_mma([&] { issue_gemm<FMT>(tbase + 128, sH, sWd + half * HA * 64 * 128, 64, HA, half > 0); })) {
                 stop = true;
                 break;
             }
@@ -615,14 +726,15 @@ __global__ void __launch_bounds__(PT_THREADS, 1) k_post(const __grid_constant__ 
         tmem_ld32(trow + 128 + 32 * wg, v);
         tmem_wait_ld();
 #pragma unroll
-        for (int i = 0; i < 32; ++i) zr[i] += v[i] + pv[PV_BDN + 32 * wg + i];
+        for (int i = 0; i < 32; ++i) zr[i] += fmaf(v[i], p.ds[2], pv[PV_BDN + 32 * wg + i]);
         if (MODE == 0) {
             float4* zd = (float4*)(p.z + (size_t)pp * D + 32 * wg);
 #pragma unroll
             for (int i = 0; i < 8; ++i) zd[i] = make_float4(zr[4 * i], zr[4 * i + 1], zr[4 * i + 2], zr[4 * i + 3]);
             layernorm_split(zr, v, pv + PV_LNG, pv + PV_LNB, wg, r, team, red);
-            st_row_half16<F16>(sA, r, v, wg);
-            if (!run_mma([&] { issue_gemm<F16>(tbase, sA, sWa, 192, 1); })) break;
+            if (p.amax) record_amax(p.amax, p.slot[3], v, 32, ri.valid);
+            st_op<FMT>(sA, r, v, 32, 32 * wg, p.qs[3], true);
+            if (!run_mma([&] { issue_gemm<FMT>(tbase, sA, sWa, 192, 1); })) break;
             // wg 0: Q and V channels 0..31; wg 1: K and V channels 32..63
             uint16_t* qk = (wg == 0 ? p.q : p.k) + (size_t)pp * D;
 #pragma unroll
@@ -630,7 +742,7 @@ __global__ void __launch_bounds__(PT_THREADS, 1) k_post(const __grid_constant__ 
                 tmem_ld32(trow + 64 * wg + 32 * q2, v);
                 tmem_wait_ld();
 #pragma unroll
-                for (int i = 0; i < 32; ++i) v[i] += pv[PV_BA + 64 * wg + 32 * q2 + i];
+                for (int i = 0; i < 32; ++i) v[i] = fmaf(v[i], p.ds[3], pv[PV_BA + 64 * wg + 32 * q2 + i]);
                 uint4* d4 = (uint4*)(qk + 32 * q2);
 #pragma unroll
                 for (int c = 0; c < 4; ++c)
@@ -641,7 +753,7 @@ __global__ void __launch_bounds__(PT_THREADS, 1) k_post(const __grid_constant__ 
             tmem_wait_ld();
 #pragma unroll
             for (int i = 0; i < 32; ++i) {
-                const float t = ri.valid ? v[i] + pv[PV_BA + 128 + 32 * wg + i] : 0.f;
+                const float t = ri.valid ? fmaf(v[i], p.ds[3], pv[PV_BA + 128 + 32 * wg + i]) : 0.f;
                 p.vt[(size_t)(32 * wg + i) * p.ldvt + pp] = (uint16_t)(pack2<F16>(t, 0.f) & 0xffffu);
             }
         } else if (MODE == 1) {
@@ -653,14 +765,16 @@ __global__ void __launch_bounds__(PT_THREADS, 1) k_post(const __grid_constant__ 
                     d4[c] = make_uint4(pack2<F16>(v[8 * c], v[8 * c + 1]), pack2<F16>(v[8 * c + 2], v[8 * c + 3]),
                                        pack2<F16>(v[8 * c + 4], v[8 * c + 5]), pack2<F16>(v[8 * c + 6], v[8 * c + 7]));
             }
-            st_row_half16<F16>(sA, r, v, wg);
-            if (!run_mma([&] { issue_gemm<F16>(tbase, sA, sWa, 64, 1); })) break;
+            if (p.amax) record_amax(p.amax, p.slot[3], v, 32, ri.valid);
+            st_op<FH>(sA, r, v, 32, 32 * wg, 1.f);
+            if (!run_mma([&] { issue_gemm<FH>(tbase, sA, sWa, 64, 1); })) break;
             tmem_ld32(trow + 32 * wg, v);
             tmem_wait_ld();
 #pragma unroll
             for (int i = 0; i < 32; ++i) v[i] = act_f(v[i] + pv[PV_BA + 32 * wg + i], p.act);
-            st_row_half16<F16>(sH, r, v, wg);
-            if (!run_mma([&] { issue_gemm<F16>(tbase + 64, sH, sWb, 16, 1); })) break;
+            if (p.amax) record_amax(p.amax, p.slot[4], v, 32, ri.valid);
+            st_op<FH>(sH, r, v, 32, 32 * wg, 1.f);
+            if (!run_mma([&] { issue_gemm<FH>(tbase + 64, sH, sWb, 16, 1); })) break;
             if (wg == 0) {
                 tmem_ld16(trow + 64, v);
                 tmem_wait_ld();
@@ -673,10 +787,11 @@ __global__ void __launch_bounds__(PT_THREADS, 1) k_post(const __grid_constant__ 
             }
         } else {
             layernorm_split(zr, v, pv + PV_LNG, pv + PV_LNB, wg, r, team, red);  // h_reg
-            st_row_half16<F16>(sA, r, v, wg);
+            if (p.amax) record_amax(p.amax, p.slot[3], v, 32, ri.valid);
+            st_op<FH>(sA, r, v, 32, 32 * wg, 1.f);
 #pragma unroll 1
             for (int half = 0; half < 2 && !stop; ++half) {
-                if (!run_mma([&] { issue_gemm<F16>(tbase, sA, sWa + half * 128 * 128, 128, 1); })) { stop = true; break; }
+                if (!run_mma([&] { issue_gemm<FH>(tbase, sA, sWa + half * 128 * 128, 128, 1); })) { stop = true; break; }
 #pragma unroll
                 for (int q2 = 0; q2 < 2; ++q2) {
                     tmem_ld32(trow + 64 * wg + 32 * q2, v);
@@ -684,9 +799,10 @@ __global__ void __launch_bounds__(PT_THREADS, 1) k_post(const __grid_constant__ 
 #pragma unroll
                     for (int i = 0; i < 32; ++i)
                         v[i] = act_f(v[i] + pv[PV_BA + 128 * half + 64 * wg + 32 * q2 + i], p.act);
-                    st_row_half16<F16>(sH + wg * ATOM, r, v, q2);
+                    if (p.amax) record_amax(p.amax, p.slot[4], v, 32, ri.valid);
+                    st_op<FH>(sH, r, v, 32, 64 * wg + 32 * q2, 1.f);
                 }
-                if (!run_mma([&] { issue_gemm<F16>(tbase + 128, sH, sWb + half * 2 * 16 * 128, 16, 2, half > 0); })) {
+                if (!run_mma([&] { issue_gemm<FH>(tbase + 128, sH, sWb + half * 2 * 16 * 128, 16, 2, half > 0); })) {
                     stop = true;
                     break;
                 }
@@ -1095,16 +1211,18 @@ __global__ void __launch_bounds__(AT_THREADS, 1)
 }
 
 // ---------------------------------------------------------------- host side
-uint32_t embed_smem(int mode) {
+uint32_t embed_smem(int mode, int fmt) {
+    (void)fmt;
     const int ka = mode == 0 ? 1 : 2;
     const uint32_t need = 64 * 128 * ka + 64 * 128 + 192 * 128 + ka * ATOM + ATOM + 64 + 1024;
     // at least 80 KB so that no more than two CTAs (2 x 256 TMEM columns) share an SM
     return need < 80 * 1024 ? 80 * 1024 : need;
 }
-uint32_t post_smem(int mode) {
+uint32_t post_smem(int mode, int fmt) {
+    const uint32_t ka256 = fmt == FMT_E4M3 ? 2 : 4;
     const uint32_t wab = mode == 0 ? 192 * 128 : (mode == 1 ? 64 * 128 : 256 * 128);
     const uint32_t wbb = mode == 0 ? 0 : (mode == 1 ? 16 * 128 : 4 * 16 * 128);
-    return 64 * 128 + 256 * 128 + 4 * 64 * 128 + wab + ((wbb + 1023) & ~1023u) + 2 * PT_TEAM_BYTES +
+    return 64 * 128 + 256 * 128 + ka256 * 64 * 128 + wab + ((wbb + 1023) & ~1023u) + 2 * PT_TEAM_BYTES +
            PV_N * 4 + 2 * PT_RED_FLOATS * 4 + 64 + 1024;
 }
 
@@ -1126,8 +1244,9 @@ EncodeTiledFn encode_fn() {
     return fn;
 }
 
-bool make_map_bf16(CUtensorMap* map, void* base, uint64_t inner, uint64_t outer, uint32_t box_inner,
-                   uint32_t box_outer) {
+// 2-D map over a row-major 16-bit buffer (BF16 or FP16: TMA only moves bytes).
+bool make_map_16(CUtensorMap* map, void* base, uint64_t inner, uint64_t outer, uint32_t box_inner,
+                 uint32_t box_outer) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return false;
     cuuint64_t dims[2] = {inner, outer};
@@ -1139,32 +1258,35 @@ bool make_map_bf16(CUtensorMap* map, void* base, uint64_t inner, uint64_t outer,
               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// 16-bit (BF16 or FP16) swizzled image of a weight matrix:
-// out[n][k'] = W[n][colmap(k')], zero padded.
+// Swizzled operand image of a weight matrix in format fmt:
+// out[n][k'] = W[n][colmap(k')] (scaled by 1/scale for E4M3), zero padded.
+// Atoms of 64 (16-bit) or 128 (E4M3) K-columns, each Npad rows of 128 bytes.
 void build_image(std::vector<uint8_t>& out, int Npad, int Kpad, const std::vector<float>& W,
                  int N, int K, const std::vector<int>& colmap, const std::vector<int>& rowmap,
-                 bool f16) {
-    out.assign((size_t)Npad * Kpad * 2, 0);
-    const int atoms = Kpad / 64;
+                 int fmt, float scale) {
+    const int esz = fmt == FMT_E4M3 ? 1 : 2, ak = 128 / esz;
+    out.assign((size_t)Npad * Kpad * esz, 0);
+    const int atoms = Kpad / ak;
     for (int a = 0; a < atoms; ++a)
         for (int n = 0; n < Npad; ++n)
-            for (int kk = 0; kk < 64; ++kk) {
-                const int kp = a * 64 + kk;
-                const int src_k = colmap.empty() ? (kp < K ? kp : -1) : colmap[kp];
+            for (int kk = 0; kk < ak; ++kk) {
+                const int kp = a * ak + kk;
+                const int src_k = colmap.empty() ? (kp < K ? kp : -1) : (kp < (int)colmap.size() ? colmap[kp] : -1);
                 const int src_n = rowmap.empty() ? (n < N ? n : -1) : rowmap[n];
                 float v = 0.f;
                 if (src_k >= 0 && src_n >= 0) v = W[(size_t)src_n * K + src_k];
-                uint16_t b;
-                if (f16) {
+                const int byte = kk * esz;
+                const size_t off = (size_t)a * Npad * 128 + (size_t)n * 128 +
+                                   (size_t)((((byte >> 4) ^ (n & 7)) << 4)) + (byte & 15);
+                if (fmt == FMT_E4M3) {
+                    out[off] = (uint8_t)__nv_cvt_float_to_fp8(v / scale, __NV_SATFINITE, __NV_E4M3);
+                } else if (fmt == FMT_FP16) {
                     const __half hv = __float2half_rn(v);
-                    std::memcpy(&b, &hv, 2);
+                    std::memcpy(&out[off], &hv, 2);
                 } else {
                     const __nv_bfloat16 bv = __float2bfloat16_rn(v);
-                    std::memcpy(&b, &bv, 2);
+                    std::memcpy(&out[off], &bv, 2);
                 }
-                const size_t off = (size_t)a * Npad * 128 + (size_t)n * 128 +
-                                   (size_t)((((kk >> 3) ^ (n & 7)) << 4)) + (kk & 7) * 2;
-                std::memcpy(&out[off], &b, 2);
             }
 }
 
@@ -1179,38 +1301,30 @@ int occupancy(K kernel, int threads, uint32_t smem) {
 // Every kernel must fit one CTA per SM; the embedding kernels (256 TMEM columns
 // each) must not exceed two co-resident CTAs.  Returns an
 // empty string or a description of the kernels that do not fit.
-template <bool F16>
+template <int FMT>
 std::string check_occupancy() {
-    const int o[6] = {occupancy(k_attention<F16>, AT_THREADS, AT_SMEM),
-                      occupancy(k_post<0, F16>, PT_THREADS, post_smem(0)),
-                      occupancy(k_post<1, F16>, PT_THREADS, post_smem(1)),
-                      occupancy(k_post<2, F16>, PT_THREADS, post_smem(2)),
-                      occupancy(k_embed_qkv<0, F16>, 128, embed_smem(0)),
-                      occupancy(k_embed_qkv<1, F16>, 128, embed_smem(1))};
+    const int o[6] = {occupancy(k_attention<kOutF16<FMT>>, AT_THREADS, AT_SMEM),
+                      occupancy(k_post<0, FMT>, PT_THREADS, post_smem(0, FMT)),
+                      occupancy(k_post<1, FMT>, PT_THREADS, post_smem(1, FMT)),
+                      occupancy(k_post<2, FMT>, PT_THREADS, post_smem(2, FMT)),
+                      occupancy(k_embed_qkv<0, FMT>, 128, embed_smem(0, FMT)),
+                      occupancy(k_embed_qkv<1, FMT>, 128, embed_smem(1, FMT))};
     if (o[0] >= 1 && o[1] >= 1 && o[2] >= 1 && o[3] >= 1 && o[4] >= 1 && o[4] <= 2 && o[5] >= 1 &&
         o[5] <= 2)
         return "";
-    std::string msg = std::string(F16 ? "fp16" : "bf16") + " CTAs/SM: attention " +
-                      std::to_string(o[0]) + ", post " + std::to_string(o[1]) + "/" + std::to_string(o[2]) +
-                      "/" + std::to_string(o[3]) + ", embed " + std::to_string(o[4]) + "/" +
-                      std::to_string(o[5]);
-    cudaFuncAttributes fa;
-    if (cudaFuncGetAttributes(&fa, k_post<2, F16>) == cudaSuccess)
-        msg += "; post regs " + std::to_string(fa.numRegs) + " max threads " + std::to_string(fa.maxThreadsPerBlock);
-    if (cudaFuncGetAttributes(&fa, k_attention<F16>) == cudaSuccess)
-        msg += "; attention regs " + std::to_string(fa.numRegs) + " max threads " +
-               std::to_string(fa.maxThreadsPerBlock);
-    return msg;
+    return "format " + std::to_string(FMT) + " CTAs/SM: attention " + std::to_string(o[0]) + ", post " +
+           std::to_string(o[1]) + "/" + std::to_string(o[2]) + "/" + std::to_string(o[3]) + ", embed " +
+           std::to_string(o[4]) + "/" + std::to_string(o[5]) + "; ";
 }
 
-template <bool F16>
+template <int FMT>
 void set_attrs() {
-    cudaFuncSetAttribute(k_embed_qkv<0, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, embed_smem(0));
-    cudaFuncSetAttribute(k_embed_qkv<1, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, embed_smem(1));
-    cudaFuncSetAttribute(k_post<0, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, post_smem(0));
-    cudaFuncSetAttribute(k_post<1, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, post_smem(1));
-    cudaFuncSetAttribute(k_post<2, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, post_smem(2));
-    cudaFuncSetAttribute(k_attention<F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, AT_SMEM);
+    cudaFuncSetAttribute(k_embed_qkv<0, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, embed_smem(0, FMT));
+    cudaFuncSetAttribute(k_embed_qkv<1, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, embed_smem(1, FMT));
+    cudaFuncSetAttribute(k_post<0, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, post_smem(0, FMT));
+    cudaFuncSetAttribute(k_post<1, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, post_smem(1, FMT));
+    cudaFuncSetAttribute(k_post<2, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, post_smem(2, FMT));
+    cudaFuncSetAttribute(k_attention<kOutF16<FMT>>, cudaFuncAttributeMaxDynamicSharedMemorySize, AT_SMEM);
 }
 
 }  // namespace
@@ -1218,15 +1332,26 @@ void set_attrs() {
 bool tc_prepare_weights(Model& m) {
     const mlpf_config& c = m.cfg;
     auto H = [&](const std::string& s) -> const std::vector<float>& { return m.host.at(s).data; };
-    std::vector<std::pair<std::string, std::vector<uint8_t>>> imgs, imgs_h;
+    struct Img {
+        std::string name;
+        std::vector<uint8_t> data[3];
+        float scale;
+    };
+    std::vector<Img> imgs;
     std::vector<std::pair<std::string, std::vector<float>>> vecs;
-    std::vector<uint8_t> img;
-    auto add = [&](const std::string& name, int Npad, int Kpad, const std::vector<float>& W, int N,
-                   int K, std::vector<int> colmap = {}, std::vector<int> rowmap = {}) {
-        build_image(img, Npad, Kpad, W, N, K, colmap, rowmap, false);
-        imgs.push_back({name, img});
-        build_image(img, Npad, Kpad, W, N, K, colmap, rowmap, true);
-        imgs_h.push_back({name, img});
+    // Kpad16: padded K of the 16-bit image (E4M3: rounded up to 128)
+    auto add = [&](const std::string& name, int Npad, int Kpad16, const std::vector<float>& W, int N, int K,
+                   std::vector<int> colmap = {}, std::vector<int> rowmap = {}) {
+        Img im;
+        im.name = name;
+        float amax = 0.f;
+        for (float v : W) amax = std::max(amax, std::fabs(v));
+        im.scale = amax > 0.f ? amax / 448.f : 1.f;  // per-tensor E4M3 scale
+        build_image(im.data[FMT_BF16], Npad, Kpad16, W, N, K, colmap, rowmap, FMT_BF16, 1.f);
+        build_image(im.data[FMT_FP16], Npad, Kpad16, W, N, K, colmap, rowmap, FMT_FP16, 1.f);
+        build_image(im.data[FMT_E4M3], Npad, (Kpad16 + 127) / 128 * 128, W, N, K, colmap, rowmap, FMT_E4M3,
+                    im.scale);
+        imgs.push_back(std::move(im));
     };
     auto cat = [&](std::initializer_list<std::string> names, int pad_to = 0) {
         std::vector<float> v;
@@ -1255,6 +1380,7 @@ bool tc_prepare_weights(Model& m) {
         vecs.push_back({std::string(s) + ".lnf.b", H(std::string(s) + ".lnf.b")});
     }
     {
+        // concat(x, h_pid): x in K-columns 0..41, h_pid in 64..127 (both formats)
         std::vector<int> colmap(128, -1);
         for (int k = 0; k < 42; ++k) colmap[k] = k;
         for (int k = 0; k < 64; ++k) colmap[64 + k] = 42 + k;
@@ -1285,23 +1411,21 @@ bool tc_prepare_weights(Model& m) {
         vecs.push_back({"head.reg.b2", cat({"head.pt.b2", "head.eta.b2", "head.phi.b2", "head.e.b2"}, 16)});
     }
     size_t ib = 0, vb = 0;
-    for (auto& i : imgs) ib += (i.second.size() + 1023) / 1024 * 1024;
+    for (auto& i : imgs)
+        for (int f = 0; f < 3; ++f) ib += (i.data[f].size() + 1023) / 1024 * 1024;
     for (auto& v : vecs) vb += (v.second.size() + 63) / 64 * 64;
-    if (cudaMalloc(&m.w.img_base, 2 * ib) != cudaSuccess) { set_error("weight image allocation"); return false; }
+    if (cudaMalloc(&m.w.img_base, ib) != cudaSuccess) { set_error("weight image allocation"); return false; }
     if (cudaMalloc(&m.w.tc_f32_base, vb * 4) != cudaSuccess) { set_error("bias allocation"); return false; }
-    std::vector<uint8_t> hi(2 * ib, 0);
+    std::vector<uint8_t> hi(ib, 0);
     std::vector<float> hv(vb, 0.f);
     size_t o = 0;
     for (auto& i : imgs) {
-        std::memcpy(&hi[o], i.second.data(), i.second.size());
-        m.w.img[i.first] = m.w.img_base + o;
-        m.w.img_bytes[i.first] = (uint32_t)i.second.size();
-        o += (i.second.size() + 1023) / 1024 * 1024;
-    }
-    for (auto& i : imgs_h) {
-        std::memcpy(&hi[o], i.second.data(), i.second.size());
-        m.w.img_h[i.first] = m.w.img_base + o;
-        o += (i.second.size() + 1023) / 1024 * 1024;
+        for (int f = 0; f < 3; ++f) {
+            std::memcpy(&hi[o], i.data[f].data(), i.data[f].size());
+            (f == FMT_BF16 ? m.w.img : f == FMT_FP16 ? m.w.img_h : m.w.img8)[i.name] = m.w.img_base + o;
+            o += (i.data[f].size() + 1023) / 1024 * 1024;
+        }
+        m.w.w_scale[i.name] = i.scale;
     }
     o = 0;
     for (auto& v : vecs) {
@@ -1309,21 +1433,22 @@ bool tc_prepare_weights(Model& m) {
         m.w.tcv[v.first] = m.w.tc_f32_base + o;
         o += (v.second.size() + 63) / 64 * 64;
     }
-    if (cudaMemcpy(m.w.img_base, hi.data(), 2 * ib, cudaMemcpyHostToDevice) != cudaSuccess ||
+    if (cudaMemcpy(m.w.img_base, hi.data(), ib, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(m.w.tc_f32_base, hv.data(), vb * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
         set_error("weight image upload");
         return false;
     }
     static bool attrs = false;
     if (!attrs) {
-        set_attrs<false>();
-        set_attrs<true>();
+        set_attrs<FMT_BF16>();
+        set_attrs<FMT_FP16>();
+        set_attrs<FMT_E4M3>();
         attrs = true;
     }
     if (cudaGetLastError() != cudaSuccess) { set_error("kernel attribute setup"); return false; }
-    m.embed_ctas_per_sm = std::max(1, std::min(occupancy(k_embed_qkv<1, false>, 128, embed_smem(1)),
-                                               occupancy(k_embed_qkv<1, true>, 128, embed_smem(1))));
-    const std::string occ = check_occupancy<false>() + check_occupancy<true>();
+    m.embed_ctas_per_sm = std::max(1, std::min(occupancy(k_embed_qkv<1, FMT_BF16>, 128, embed_smem(1, FMT_BF16)),
+                                               occupancy(k_embed_qkv<1, FMT_FP16>, 128, embed_smem(1, FMT_FP16))));
+    const std::string occ = check_occupancy<FMT_BF16>() + check_occupancy<FMT_FP16>() + check_occupancy<FMT_E4M3>();
     if (!occ.empty()) {
         cudaGetLastError();
         set_error("a tensor-core kernel does not fit its launch configuration: " + occ);
@@ -1335,20 +1460,41 @@ bool tc_prepare_weights(Model& m) {
 bool tc_make_maps(Model& m) {
     Workspace& w = m.ws;
     const uint64_t T = (uint64_t)w.cap_tpad;
-    bool ok = make_map_bf16(&w.map_q, w.tq, 64, T, 64, 128) && make_map_bf16(&w.map_k, w.tk, 64, T, 64, 64) &&
-              make_map_bf16(&w.map_o, w.to, 64, T, 64, 128) && make_map_bf16(&w.map_vt, w.tvt, T, 64, 64, 64) &&
-              make_map_bf16(&w.map_hp, w.thp, 64, T, 64, 128);
+    bool ok = make_map_16(&w.map_q, w.tq, 64, T, 64, 128) && make_map_16(&w.map_k, w.tk, 64, T, 64, 64) &&
+              make_map_16(&w.map_o, w.to, 64, T, 64, 128) && make_map_16(&w.map_vt, w.tvt, T, 64, 64, 64) &&
+              make_map_16(&w.map_hp, w.thp, 64, T, 64, 128);
     if (!ok) set_error("cuTensorMapEncodeTiled failed");
     return ok;
 }
 
-template <bool F16>
+int act_slot(Model& m, const std::string& name) {
+    auto it = m.act_slot.find(name);
+    if (it != m.act_slot.end()) return it->second;
+    const int i = (int)m.act_slot.size();
+    m.act_slot[name] = i;
+    if ((int)m.act_scale.size() <= i) m.act_scale.resize(i + 1, 1.f);
+    return i;
+}
+
+template <int FMT>
 static int64_t run_tc(Model& m, const float* x, const int32_t* cu, int n_events, float* logits,
                       float* reg, cudaStream_t st) {
     const mlpf_config& c = m.cfg;
     Workspace& w = m.ws;
     auto V = [&](const std::string& s) { return (const float*)m.w.tcv.at(s); };
-    auto I = [&](const std::string& s) { return (const uint8_t*)(F16 ? m.w.img_h : m.w.img).at(s); };
+    // weight image of a GEMM in format f
+    auto IF = [&](const std::string& s, int f) {
+        return (const uint8_t*)(f == FMT_BF16 ? m.w.img : f == FMT_FP16 ? m.w.img_h : m.w.img8).at(s);
+    };
+    constexpr int FE = FMT == FMT_E4M3 ? FMT_FP16 : FMT;  // embedding FFNs and output heads
+    auto I = [&](const std::string& s) { return IF(s, FMT); };
+    auto IE = [&](const std::string& s) { return IF(s, FE); };
+    // E4M3: 1/s_a of an activation slot and s_a * s_w of a GEMM (1 for 16-bit formats)
+    auto QS = [&](const std::string& slot) { return FMT == FMT_E4M3 ? 1.f / m.act_scale[act_slot(m, slot)] : 1.f; };
+    auto DS = [&](const std::string& slot, const std::string& wname) {
+        return FMT == FMT_E4M3 ? m.act_scale[act_slot(m, slot)] * m.w.w_scale.at(wname) : 1.f;
+    };
+    unsigned* amax = m.calibrating ? m.amax_dev : nullptr;
     int64_t n = 0;
     const int grid = m.sm_count;
     prof_begin(m, st, "schedule");
@@ -1359,7 +1505,7 @@ static int64_t run_tc(Model& m, const float* x, const int32_t* cu, int n_events,
     auto attention = [&](int layer) {
         AttnParams ap{w.items, w.counters, layer, (uint16_t*)w.to, m.status, (uint64_t)m.wait_limit_ns, m.debug_stall ? 1 : 0};
         prof_begin(m, st, "attention");
-        k_attention<F16><<<grid * m.attn_ctas_per_sm, AT_THREADS, AT_SMEM, st>>>(w.map_q, w.map_k, w.map_vt, ap);
+        k_attention<kOutF16<FMT>><<<grid * m.attn_ctas_per_sm, AT_THREADS, AT_SMEM, st>>>(w.map_q, w.map_k, w.map_vt, ap);
         prof_end(m, st);
         ++n;
     };
@@ -1369,14 +1515,15 @@ static int64_t run_tc(Model& m, const float* x, const int32_t* cu, int n_events,
         ep.blk = w.blk;
         ep.counters = w.counters;
         const std::string e = mode == 0 ? "emb." : "remb.";
-        ep.w1 = I(e + "w1");
-        ep.w2 = I(e + "w2");
+        ep.w1 = IE(e + "w1");
+        ep.w2 = IE(e + "w2");
         ep.wqkv = I(lp + "wqkv");
         ep.b1 = V(e + "b1");
         ep.b2 = V(e + "b2");
         ep.lng = V(lp + "ln1.g");
         ep.lnb = V(lp + "ln1.b");
         ep.bqkv = V(lp + "bqkv");
+        ep.hp = (const uint16_t*)w.thp;
         ep.z = w.tz;
         ep.q = (uint16_t*)w.tq;
         ep.k = (uint16_t*)w.tk;
@@ -1385,11 +1532,22 @@ static int64_t run_tc(Model& m, const float* x, const int32_t* cu, int n_events,
         ep.status = m.status;
         ep.wait_ns = (uint64_t)m.wait_limit_ns;
         ep.act = c.act;
+        const std::string s_in = mode == 0 ? "x" : "remb.in", s_h = e + "h", s_ln = lp + "ln1";
+        ep.qs[0] = 1.f;  // the embedding FFN is 16-bit in every mode
+        ep.qs[1] = 1.f;
+        ep.qs[2] = QS(s_ln);
+        ep.ds[0] = 1.f;
+        ep.ds[1] = 1.f;
+        ep.ds[2] = DS(s_ln, lp + "wqkv");
+        ep.amax = amax;
+        ep.slot[0] = act_slot(m, s_in);
+        ep.slot[1] = act_slot(m, s_h);
+        ep.slot[2] = act_slot(m, s_ln);
         prof_begin(m, st, mode == 0 ? "embed_qkv" : "reg_embed_qkv");
         if (mode == 0)
-            k_embed_qkv<0, F16><<<grid * m.embed_ctas_per_sm, 128, embed_smem(0), st>>>(w.map_hp, ep);
+            k_embed_qkv<0, FMT><<<grid * m.embed_ctas_per_sm, 128, embed_smem(0, FMT), st>>>(w.map_hp, ep);
         else
-            k_embed_qkv<1, F16><<<grid * m.embed_ctas_per_sm, 128, embed_smem(1), st>>>(w.map_hp, ep);
+            k_embed_qkv<1, FMT><<<grid * m.embed_ctas_per_sm, 128, embed_smem(1, FMT), st>>>(w.map_hp, ep);
         prof_end(m, st);
         ++n;
     };
@@ -1406,27 +1564,56 @@ static int64_t run_tc(Model& m, const float* x, const int32_t* cu, int n_events,
         pp.ln2b = V(lp + "ln2.b");
         pp.bup = V(lp + "ffn.b1");
         pp.bdn = V(lp + "ffn.b2");
+        std::string s_a, s_b, w_a, w_b;
         if (mode == 0) {
             pp.wa = I(next + "wqkv");
             pp.wb = nullptr;
             pp.lng = V(next + "ln1.g");
             pp.lnb = V(next + "ln1.b");
             pp.ba = V(next + "bqkv");
+            s_a = next + "ln1";
+            w_a = next + "wqkv";
         } else if (mode == 1) {
-            pp.wa = I("head.cls.w1");
-            pp.wb = I("head.cls.w2");
+            pp.wa = IE("head.cls.w1");
+            pp.wb = IE("head.cls.w2");
             pp.lng = V("pid.lnf.g");
             pp.lnb = V("pid.lnf.b");
             pp.ba = V("head.cls.b1");
             pp.bb = V("head.cls.b2");
+            s_a = "pid.lnf";
+            s_b = "cls.h";
+            w_a = "head.cls.w1";
+            w_b = "head.cls.w2";
         } else {
-            pp.wa = I("head.reg.w1");
-            pp.wb = I("head.reg.w2");
+            pp.wa = IE("head.reg.w1");
+            pp.wb = IE("head.reg.w2");
             pp.lng = V("reg.lnf.g");
             pp.lnb = V("reg.lnf.b");
             pp.ba = V("head.reg.b1");
             pp.bb = V("head.reg.b2");
+            s_a = "reg.lnf";
+            s_b = "heads.h";
+            w_a = "head.reg.w1";
+            w_b = "head.reg.w2";
         }
+        const std::string s_o = lp + "o", s_ln2 = lp + "ln2", s_ffn = lp + "ffn";
+        pp.qs[0] = QS(s_o);
+        pp.qs[1] = QS(s_ln2);
+        pp.qs[2] = QS(s_ffn);
+        // heads (modes 1, 2) are 16-bit in every mode
+        pp.qs[3] = mode == 0 ? QS(s_a) : 1.f;
+        pp.qs[4] = 1.f;
+        pp.ds[0] = DS(s_o, lp + "wo");
+        pp.ds[1] = DS(s_ln2, lp + "ffn.w1");
+        pp.ds[2] = DS(s_ffn, lp + "ffn.w2");
+        pp.ds[3] = mode == 0 ? DS(s_a, w_a) : 1.f;
+        pp.ds[4] = 1.f;
+        pp.amax = amax;
+        pp.slot[0] = act_slot(m, s_o);
+        pp.slot[1] = act_slot(m, s_ln2);
+        pp.slot[2] = act_slot(m, s_ffn);
+        pp.slot[3] = act_slot(m, s_a);
+        pp.slot[4] = mode == 0 ? 0 : act_slot(m, s_b);
         pp.z = w.tz;
         pp.q = (uint16_t*)w.tq;
         pp.k = (uint16_t*)w.tk;
@@ -1440,11 +1627,11 @@ static int64_t run_tc(Model& m, const float* x, const int32_t* cu, int n_events,
         pp.act = c.act;
         prof_begin(m, st, mode == 0 ? "post_qkv" : (mode == 1 ? "post_cls_head" : "post_reg_heads"));
         if (mode == 0)
-            k_post<0, F16><<<grid, PT_THREADS, post_smem(0), st>>>(w.map_o, pp);
+            k_post<0, FMT><<<grid, PT_THREADS, post_smem(0, FMT), st>>>(w.map_o, pp);
         else if (mode == 1)
-            k_post<1, F16><<<grid, PT_THREADS, post_smem(1), st>>>(w.map_o, pp);
+            k_post<1, FMT><<<grid, PT_THREADS, post_smem(1, FMT), st>>>(w.map_o, pp);
         else
-            k_post<2, F16><<<grid, PT_THREADS, post_smem(2), st>>>(w.map_o, pp);
+            k_post<2, FMT><<<grid, PT_THREADS, post_smem(2, FMT), st>>>(w.map_o, pp);
         prof_end(m, st);
         ++n;
     };
@@ -1475,8 +1662,9 @@ int64_t run_forward_tc(Model& m, int prec, const float* x, const int32_t* cu, in
                        int max_n, float* logits, float* reg, cudaStream_t st) {
     (void)total;
     (void)max_n;
-    return prec == MLPF_FP16 ? run_tc<true>(m, x, cu, n_events, logits, reg, st)
-                             : run_tc<false>(m, x, cu, n_events, logits, reg, st);
+    if (prec == MLPF_FP8) return run_tc<FMT_E4M3>(m, x, cu, n_events, logits, reg, st);
+    return prec == MLPF_FP16 ? run_tc<FMT_FP16>(m, x, cu, n_events, logits, reg, st)
+                             : run_tc<FMT_BF16>(m, x, cu, n_events, logits, reg, st);
 }
 
 }  // namespace mlpf
