@@ -175,6 +175,57 @@ mlpf_status mlpf_calibrate_fp8(mlpf_model* m, const float* x, const int32_t* cu_
 int32_t mlpf_get_fp8_scales(const mlpf_model* m, int32_t cap, char* names, float* scales);
 
 /*
+ * Student inference with per-event fallback to the full model.  `student` runs
+ * on every event (precision student_precision); an event whose mean, over its
+ * elements, of the student's largest class probability (max softmax of the
+ * logits) is below `threshold` is rerun by `teacher` (teacher_precision) and its
+ * rows of logits/reg are replaced.  Arguments as mlpf_forward, plus:
+ * used_teacher  device out or NULL, [n_events] int32, 1 where the teacher ran;
+ * n_fallback    host out or NULL, number of such events.
+ * Synchronises `stream` once (to size the teacher's batch).  Both models must
+ * live on the same device.  The paper runs the full model only; this is the
+ * distilled-student extension.
+ */
+mlpf_status mlpf_forward_gated(mlpf_model* student, mlpf_model* teacher, float threshold,
+                               int32_t student_precision, int32_t teacher_precision,
+                               const float* x, const int32_t* cu_seqlens,
+                               int32_t n_events, int32_t total, int32_t max_n,
+                               float* logits, float* reg, int32_t* cls, double* event_sums,
+                               int32_t* used_teacher, int32_t* n_fallback, void* stream);
+
+/*
+ * Training of a (student) model on per-element outputs of a full model, with
+ * hand-written FP32 forward and backward kernels and the LAMB optimizer.
+ *
+ * Loss, averaged over the batch's elements: KL(p_teacher || p_student) of the
+ * class probabilities plus the sum of squared differences of the 5 raw
+ * regression outputs (pT', eta, sin phi, cos phi, E'), the teacher's raw values
+ * recovered from its decoded ones (pT' = log(pT / pT_elem), E' likewise; Eq. 2).
+ */
+typedef struct mlpf_trainer mlpf_trainer;
+
+/* Create a trainer from a weight blob (initial weights); blob read during the call. */
+mlpf_status mlpf_trainer_create(const void* blob, size_t nbytes, int device, mlpf_trainer** out);
+void mlpf_trainer_free(mlpf_trainer* t);
+/* Number of trainable parameters (the gradient vector's length), -1 on NULL. */
+int64_t mlpf_trainer_num_params(const mlpf_trainer* t);
+
+/*
+ * One step on a packed batch (device buffers as in mlpf_forward).
+ * t_logits, t_reg: device, the teacher's mlpf_forward outputs for this batch.
+ * lr: learning rate of this step.  update: 0 = loss and gradients only.
+ * grads_out: device or NULL, [num_params] float, the gradient in blob tensor order.
+ * loss_out: host or NULL (then the call is asynchronous), the batch loss.
+ */
+mlpf_status mlpf_trainer_step(mlpf_trainer* t, const float* x, const int32_t* cu_seqlens,
+                              int32_t n_events, int32_t total, int32_t max_n,
+                              const float* t_logits, const float* t_reg, float lr,
+                              int32_t update, float* grads_out, double* loss_out, void* stream);
+
+/* Current weights as a blob (host buffer of cap bytes, or NULL to query *nbytes). */
+mlpf_status mlpf_trainer_export(const mlpf_trainer* t, void* blob, size_t cap, size_t* nbytes);
+
+/*
  * Wait for the model's work on `stream` and report device-side status:
  * MLPF_E_TIMEOUT if a bounded wait inside a kernel ran out since the last
  * mlpf_sync (the kernel returned early; outputs are invalid), otherwise

@@ -13,4 +13,5 @@ from .forward import (  # noqa: F401
     layer_norm, gelu, relu, linear, softmax_rows, sdpa, attention_matrix,
     multi_head_attention, encoder_block, encoder_stack, embed, reg_embed,
     ffn_head, forward_event, decode, event_sums, forward, OracleOutput,
+    raw_from_decoded, log_softmax_rows, distill_loss,
 )

@@ -269,3 +269,38 @@ def forward(W, cfg, x, cu_seqlens, events=None, keep_hidden=False):
                               [0, cu[ev + 1] - cu[ev]])[0]
     return OracleOutput(logits=logits, raw=raw, reg=reg, cls=cls, sums=sums,
                         h_pid=hp, h_reg=hr)
+
+
+# ---------------------------------------------------------- distillation loss
+
+def raw_from_decoded(x, reg):
+    """Raw head outputs (pT', eta, sin, cos, E') from decoded ones: the log-ratio
+    targets of Eq. 2 with the element's pT and E (x[:, 8], x[:, 9] in log GeV)."""
+    x = np.asarray(x, F64)
+    reg = np.asarray(reg, F64)
+    raw = reg.copy()
+    raw[:, 0] = np.log(reg[:, 0]) - x[:, 8]
+    raw[:, 4] = np.log(reg[:, 4]) - x[:, 9]
+    return raw
+
+
+def log_softmax_rows(s):
+    s = np.asarray(s, F64)
+    m = s.max(axis=-1, keepdims=True)
+    return s - m - np.log(np.exp(s - m).sum(axis=-1, keepdims=True))
+
+
+def distill_loss(W, cfg, x, cu_seqlens, t_logits, t_reg):
+    """Distillation loss of a student with weights W on a teacher's outputs.
+
+    reading: mean over elements of KL(p_teacher || p_student) over the classes
+    plus the squared error of the five raw regression outputs (the regression
+    part of the paper's loss, Eq. 3, with unit weights), the teacher's raw
+    outputs recovered from its decoded ones (Eq. 2).
+    """
+    out = forward(W, cfg, x, cu_seqlens)
+    lt = log_softmax_rows(t_logits)
+    ls = log_softmax_rows(out.logits)
+    kl = (np.exp(lt) * (lt - ls)).sum(axis=1)
+    mse = ((out.raw - raw_from_decoded(x, t_reg)) ** 2).sum(axis=1)
+    return float((kl + mse).mean())

@@ -127,3 +127,71 @@ class Model:
         import torch
         s = stream if stream is not None else torch.cuda.current_stream(self.device).cuda_stream
         check(self.L.mlpf_sync(self.h, ctypes.c_void_p(s)))
+
+
+class Trainer:
+    """Distillation trainer of a model (hand-written FP32 forward/backward kernels, LAMB)."""
+
+    def __init__(self, blob: bytes, device: int = 0):
+        self.L = _lib.load()
+        h = ctypes.c_void_p()
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        check(self.L.mlpf_trainer_create(buf, len(blob), device, ctypes.byref(h)))
+        self.h = h
+        self.device = device
+        self.num_params = int(self.L.mlpf_trainer_num_params(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.mlpf_trainer_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, x, cu_seqlens, max_n: int, t_logits, t_reg, lr: float, update: bool = True,
+             grads=None, want_loss: bool = True, stream=None):
+        """One step on device tensors; returns the batch loss (or None if not wanted)."""
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream(self.device).cuda_stream
+        loss = ctypes.c_double(0.0)
+        check(self.L.mlpf_trainer_step(self.h, _ptr(x), _ptr(cu_seqlens), cu_seqlens.shape[0] - 1,
+                                       x.shape[0], int(max_n), _ptr(t_logits), _ptr(t_reg),
+                                       float(lr), int(bool(update)), _ptr(grads),
+                                       ctypes.byref(loss) if want_loss else None, ctypes.c_void_p(s)))
+        return loss.value if want_loss else None
+
+    def export(self) -> bytes:
+        """Current weights as a weight blob (loadable with Model)."""
+        n = ctypes.c_size_t(0)
+        check(self.L.mlpf_trainer_export(self.h, None, 0, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        check(self.L.mlpf_trainer_export(self.h, buf, n.value, ctypes.byref(n)))
+        return buf.raw
+
+
+def forward_gated(student: Model, teacher: Model, threshold: float, x, cu_seqlens, max_n: int,
+                  student_precision="bf16", teacher_precision="fp32", stream=None):
+    """Student forward with per-event fallback to the teacher (device tensors).
+
+    Returns (logits, reg, cls, event_sums, used_teacher [n_events] int32, n_fallback).
+    """
+    import torch
+    sp = PRECISIONS[student_precision] if isinstance(student_precision, str) else int(student_precision)
+    tp = PRECISIONS[teacher_precision] if isinstance(teacher_precision, str) else int(teacher_precision)
+    total, n_events, dev = x.shape[0], cu_seqlens.shape[0] - 1, x.device
+    logits = torch.empty((total, 6), dtype=torch.float32, device=dev)
+    reg = torch.empty((total, 5), dtype=torch.float32, device=dev)
+    cls = torch.empty((total,), dtype=torch.int32, device=dev)
+    sums = torch.empty((n_events, 3), dtype=torch.float64, device=dev)
+    used = torch.empty((n_events,), dtype=torch.int32, device=dev)
+    nfb = ctypes.c_int32(0)
+    s = stream if stream is not None else torch.cuda.current_stream(dev).cuda_stream
+    check(student.L.mlpf_forward_gated(student.h, teacher.h, float(threshold), sp, tp, _ptr(x),
+                                       _ptr(cu_seqlens), n_events, total, int(max_n), _ptr(logits),
+                                       _ptr(reg), _ptr(cls), _ptr(sums), _ptr(used),
+                                       ctypes.byref(nfb), ctypes.c_void_p(s)))
+    return logits, reg, cls, sums, used, nfb.value

@@ -16,7 +16,8 @@ OPT_USE_GRAPHS, OPT_WAIT_LIMIT_NS, OPT_DEBUG_STALL, OPT_ATTN_CTAS_PER_SM, OPT_AT
 # every symbol include/mlpf.h declares
 EXPORTS = ("mlpf_load_weights", "mlpf_free", "mlpf_get_config", "mlpf_forward",
            "mlpf_forward_host", "mlpf_forward_noalloc", "mlpf_calibrate_fp8", "mlpf_get_fp8_scales",
-           "mlpf_sync", "mlpf_set_option", "mlpf_get_option",
+           "mlpf_forward_gated", "mlpf_trainer_create", "mlpf_trainer_free", "mlpf_trainer_num_params",
+           "mlpf_trainer_step", "mlpf_trainer_export", "mlpf_sync", "mlpf_set_option", "mlpf_get_option",
            "mlpf_last_launch_count", "mlpf_profile_get", "mlpf_last_error", "mlpf_abi_version")
 
 
@@ -57,6 +58,20 @@ def load(build_if_missing: bool = True):
     L.mlpf_calibrate_fp8.restype = ctypes.c_int
     L.mlpf_get_fp8_scales.argtypes = [vp, i32, ctypes.c_char_p, ctypes.POINTER(ctypes.c_float)]
     L.mlpf_get_fp8_scales.restype = i32
+    L.mlpf_forward_gated.argtypes = [vp, vp, ctypes.c_float, i32, i32, vp, vp, i32, i32, i32, vp, vp, vp,
+                                     vp, vp, ctypes.POINTER(i32), vp]
+    L.mlpf_forward_gated.restype = ctypes.c_int
+    L.mlpf_trainer_create.argtypes = [vp, sz, ctypes.c_int, ctypes.POINTER(vp)]
+    L.mlpf_trainer_create.restype = ctypes.c_int
+    L.mlpf_trainer_free.argtypes = [vp]
+    L.mlpf_trainer_free.restype = None
+    L.mlpf_trainer_num_params.argtypes = [vp]
+    L.mlpf_trainer_num_params.restype = i64
+    L.mlpf_trainer_step.argtypes = [vp, vp, vp, i32, i32, i32, vp, vp, ctypes.c_float, i32, vp,
+                                    ctypes.POINTER(ctypes.c_double), vp]
+    L.mlpf_trainer_step.restype = ctypes.c_int
+    L.mlpf_trainer_export.argtypes = [vp, vp, sz, ctypes.POINTER(sz)]
+    L.mlpf_trainer_export.restype = ctypes.c_int
     L.mlpf_sync.argtypes = [vp, vp]
     L.mlpf_sync.restype = ctypes.c_int
     L.mlpf_set_option.argtypes = [vp, i32, i64]

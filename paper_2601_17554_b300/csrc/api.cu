@@ -158,6 +158,8 @@ static mlpf_status parse_blob(const uint8_t* p, size_t nbytes, Model& m) {
     return MLPF_OK;
 }
 
+mlpf_status parse_blob_into(const uint8_t* p, size_t nbytes, Model& m) { return parse_blob(p, nbytes, m); }
+
 static mlpf_status cuda_fail(cudaError_t e, const char* what) {
     set_error(std::string(what) + ": " + cudaGetErrorString(e));
     return e == cudaErrorMemoryAllocation ? MLPF_E_OOM : MLPF_E_CUDA;
@@ -461,6 +463,7 @@ void mlpf_free(mlpf_model* mm) {
     if (m.w.tc_f32_base) cudaFree(m.w.tc_f32_base);
     if (m.status) cudaFree(m.status);
     if (m.amax_dev) cudaFree(m.amax_dev);
+    if (m.gate.base) cudaFree(m.gate.base);
     delete mm;
 }
 

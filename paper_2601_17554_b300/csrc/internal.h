@@ -114,6 +114,13 @@ struct Model {
         Profile prof;
     };
     std::map<GraphKey, GraphEntry> graphs;
+    // buffers of the gated (student + fallback) forward
+    struct Gate {
+        size_t cap_total = 0, cap_events = 0;
+        void* base = nullptr;
+        float *sub_x = nullptr, *sub_lo = nullptr, *sub_rg = nullptr, *conf = nullptr;
+        int32_t *flag = nullptr, *sub_cu = nullptr, *src = nullptr, *meta = nullptr;
+    } gate;
     bool profile = false;
     Profile* cur_prof = nullptr;   // profile being recorded by the launch sequence
     Profile direct_prof;           // profile of the last non-graph forward
@@ -132,6 +139,15 @@ int64_t run_forward_tc(Model& m, int prec, const float* x, const int32_t* cu, in
 int64_t run_event_sums(Model& m, const int32_t* cu, int n_events, const float* logits,
                        const float* reg, int32_t* cls, double* sums, int n_cls,
                        cudaStream_t st);
+
+// plain FP32 kernels shared with the training code (act: -1 none, 0 GELU, 1 ReLU)
+void f32_linear(const float* X1, int ld1, int K1, const float* X2, int ld2, int K2, const float* W,
+                const float* b, const float* R, int ldr, float* Y, int ldy, int T, int N, int act,
+                cudaStream_t st);
+void f32_layernorm(const float* X, const float* g, const float* b, float* Y, int T, int d, cudaStream_t st);
+void f32_attention(const float* qkv, float* out, const int32_t* cu, int n_events, int max_n, int d,
+                   int heads, float* lse, cudaStream_t st);
+mlpf_status parse_blob_into(const uint8_t* p, size_t nbytes, Model& m);
 
 // tensor-core path preparation (weights images, tensor maps)
 bool tc_prepare_weights(Model& m);

@@ -114,11 +114,13 @@ __global__ void k_layernorm(const float* __restrict__ X, const float* __restrict
 // Self-attention within each event; one thread per query row, 64 keys per
 // shared-memory tile, FP32 online softmax (exact expf).  qkv rows are
 // [q | k | v] with head h in columns h*DH .. h*DH+DH-1 of each part.
+// lse (optional, [T, heads]): log-sum-exp of each row's scaled scores, for the
+// backward pass.
 template <int DH>
 __global__ void __launch_bounds__(64) k_attention(const float* __restrict__ qkv,
                                                   float* __restrict__ out,
                                                   const int32_t* __restrict__ cu, int d,
-                                                  float scale) {
+                                                  float scale, float* __restrict__ lse) {
     __shared__ float Ks[64][DH + 1];
     __shared__ float Vs[64][DH + 1];
     const int e = blockIdx.z, h = blockIdx.y;
@@ -181,6 +183,7 @@ __global__ void __launch_bounds__(64) k_attention(const float* __restrict__ qkv,
         const float inv = 1.0f / l;
 #pragma unroll
         for (int c = 0; c < DH; ++c) out[(size_t)(start + qi) * d + h * DH + c] = acc[c] * inv;
+        if (lse) lse[(size_t)(start + qi) * gridDim.y + h] = m + logf(l);
     }
 }
 
@@ -314,11 +317,11 @@ int64_t run_forward_f32(Model& m, const float* x, const int32_t* cu, int n_event
             dim3 grid(cdiv(max_n, 64), c.heads, n_events);
             prof_begin(m, st, "f32_attention");
             if (dh == 16)
-                k_attention<16><<<grid, 64, 0, st>>>(w.qkv, w.o, cu, d, scale);
+                k_attention<16><<<grid, 64, 0, st>>>(w.qkv, w.o, cu, d, scale, nullptr);
             else if (dh == 32)
-                k_attention<32><<<grid, 64, 0, st>>>(w.qkv, w.o, cu, d, scale);
+                k_attention<32><<<grid, 64, 0, st>>>(w.qkv, w.o, cu, d, scale, nullptr);
             else
-                k_attention<64><<<grid, 64, 0, st>>>(w.qkv, w.o, cu, d, scale);
+                k_attention<64><<<grid, 64, 0, st>>>(w.qkv, w.o, cu, d, scale, nullptr);
             prof_end(m, st);
             ++n;
             linear(w.o, d, d, nullptr, 0, 0, W(p + "wo"), W(p + "bo"), w.z, d, w.z, d, T, d, -1, st,
@@ -365,6 +368,33 @@ int64_t run_forward_f32(Model& m, const float* x, const int32_t* cu, int n_event
     ++n;
     if (cudaPeekAtLastError() != cudaSuccess) return -1;
     return n;
+}
+
+void f32_linear(const float* X1, int ld1, int K1, const float* X2, int ld2, int K2, const float* W,
+                const float* b, const float* R, int ldr, float* Y, int ldy, int T, int N, int act,
+                cudaStream_t st) {
+    if (T <= 0) return;
+    dim3 grid(cdiv(N, LIN_BN), cdiv(T, LIN_BM));
+    k_linear<<<grid, 256, 0, st>>>(X1, ld1, K1, X2, ld2, K2, W, b, R, ldr, Y, ldy, T, N, act);
+}
+
+void f32_layernorm(const float* X, const float* g, const float* b, float* Y, int T, int d, cudaStream_t st) {
+    if (T <= 0) return;
+    k_layernorm<<<cdiv(T, 8), 256, 0, st>>>(X, g, b, Y, T, d);
+}
+
+void f32_attention(const float* qkv, float* out, const int32_t* cu, int n_events, int max_n, int d,
+                   int heads, float* lse, cudaStream_t st) {
+    if (n_events <= 0 || max_n <= 0) return;
+    const int dh = d / heads;
+    const float scale = 1.0f / sqrtf((float)dh);
+    dim3 grid(cdiv(max_n, 64), heads, n_events);
+    if (dh == 16)
+        k_attention<16><<<grid, 64, 0, st>>>(qkv, out, cu, d, scale, lse);
+    else if (dh == 32)
+        k_attention<32><<<grid, 64, 0, st>>>(qkv, out, cu, d, scale, lse);
+    else
+        k_attention<64><<<grid, 64, 0, st>>>(qkv, out, cu, d, scale, lse);
 }
 
 int64_t run_event_sums(Model& m, const int32_t* cu, int n_events, const float* logits,

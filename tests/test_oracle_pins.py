@@ -285,3 +285,37 @@ def test_generator_counter_based():
 def test_splitmix64_published_vector():
     # SplitMix64 output sequence for state 0 (first output), a published value.
     assert int(synth.splitmix64(np.uint64(0))) == 0xE220A8397B1DCDAF
+
+
+# ------------------------------------------------------- distillation loss
+
+def test_distill_loss_zero_on_own_outputs():
+    """KL(p || p) = 0 and the raw targets recovered from the decoded outputs equal
+    the raw outputs, so a model distilled on its own outputs has zero loss."""
+    cfg = synth.ModelConfig(d=32, heads=2, ffn=64, l_pid=1, l_reg=1)
+    W = synth.make_weights(cfg, 8, perturbed=True)
+    x, cu = synth.gen_events(31, [9, 4])
+    out = oracle.forward(W, cfg, x, cu)
+    assert abs(oracle.distill_loss(W, cfg, x, cu, out.logits, out.reg)) < 1e-12
+
+
+def test_distill_loss_hand_example():
+    """One element: teacher probabilities (1/2, 1/2, 0...) vs a uniform student over
+    two classes is KL = 0 (same distribution); a regression offset of 0.5 in eta
+    adds 0.25."""
+    cfg = synth.ModelConfig(d=32, heads=2, ffn=64, l_pid=1, l_reg=1)
+    W = synth.make_weights(cfg, 9)
+    x, cu = synth.gen_events(32, [1])
+    out = oracle.forward(W, cfg, x, cu)
+    t_reg = out.reg.copy()
+    t_reg[:, 1] += 0.5
+    np.testing.assert_allclose(oracle.distill_loss(W, cfg, x, cu, out.logits, t_reg), 0.25, rtol=1e-12)
+    lt = oracle.log_softmax_rows(np.array([[0.0, 0.0, -1e300, -1e300, -1e300, -1e300]]))
+    np.testing.assert_allclose(np.exp(lt[0, :2]), [0.5, 0.5], rtol=1e-15)
+
+
+def test_raw_from_decoded_inverts_decode():
+    x, _ = synth.gen_events(33, [6])
+    raw = np.random.default_rng(4).normal(size=(6, 5))
+    _, reg = oracle.decode(x, np.zeros((6, 6)), raw)
+    np.testing.assert_allclose(oracle.raw_from_decoded(x, reg), raw, rtol=1e-12, atol=1e-12)
