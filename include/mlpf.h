@@ -168,6 +168,20 @@ mlpf_status mlpf_calibrate_fp8(mlpf_model* m, const float* x, const int32_t* cu_
                                int32_t n_events, int32_t total, int32_t max_n, void* stream);
 
 /*
+ * Autotuner (no counterpart in the paper): times every attention variant (heads
+ * per warpgroup x K/V pipeline depth) of `precision` on the given batch (device
+ * buffers, laid out as in mlpf_forward; outputs go to the model's scratch) and
+ * keeps the fastest for this model.  cache_path (host string, or NULL for no
+ * cache): a text file of "key variant ms" lines keyed by GPU arch, SM count, model
+ * width, precision and element count rounded up to a power of two; a cached key is
+ * applied without timing, a new one is appended.  Synchronous on `stream`.
+ * MLPF_FP32 has nothing to tune and returns MLPF_OK.  Errors as mlpf_forward.
+ */
+mlpf_status mlpf_autotune(mlpf_model* m, int32_t precision, const float* x, const int32_t* cu_seqlens,
+                          int32_t n_events, int32_t total, int32_t max_n, const char* cache_path,
+                          void* stream);
+
+/*
  * Names (cap x 32 bytes, or NULL) and activation scales (cap floats, or NULL)
  * of the FP8 calibration; returns the number of activation slots, 0 before
  * calibration, -1 on error.
@@ -240,9 +254,15 @@ enum {
     MLPF_OPT_DEBUG_STALL = 3,       /* 1: attention consumers wait on a barrier nothing
                                        arms, to exercise the timeout path (tests only) */
     MLPF_OPT_ATTN_CTAS_PER_SM = 4,  /* attention persistent grid size factor (autotuned) */
-    MLPF_OPT_ATTN_KV_STAGES = 5,    /* read-only in this build: K/V pipeline depth */
-    MLPF_OPT_PROFILE = 6            /* 1: CUDA events around every kernel launch (also
+    MLPF_OPT_ATTN_KV_STAGES = 5,    /* read-only: K/V pipeline depth of the BF16 variant */
+    MLPF_OPT_PROFILE = 6,           /* 1: CUDA events around every kernel launch (also
                                        inside captured graphs); see mlpf_profile_get */
+    MLPF_OPT_ATTN_VARIANT_BF16 = 7, /* attention kernel variant of a precision, 0..3:
+                                       0 = one head per warpgroup, 4 K/V stages (default);
+                                       1 = one head, 2 stages; 2 = two heads, 4 stages;
+                                       3 = two heads, 2 stages.  Set by mlpf_autotune. */
+    MLPF_OPT_ATTN_VARIANT_FP16 = 8,
+    MLPF_OPT_ATTN_VARIANT_FP8 = 9
 };
 mlpf_status mlpf_set_option(mlpf_model* m, int32_t option, int64_t value);
 mlpf_status mlpf_get_option(const mlpf_model* m, int32_t option, int64_t* value);

@@ -12,7 +12,8 @@ import ctypes
 
 from . import _lib
 from ._lib import (MLPF_FP32, MLPF_BF16, MLPF_FP8, MLPF_FP16, MlpfError, check,  # noqa: F401
-                   OPT_USE_GRAPHS, OPT_WAIT_LIMIT_NS, OPT_DEBUG_STALL)
+                   OPT_USE_GRAPHS, OPT_WAIT_LIMIT_NS, OPT_DEBUG_STALL, OPT_ATTN_VARIANT_BF16,
+                   OPT_ATTN_VARIANT_FP16, OPT_ATTN_VARIANT_FP8)
 
 PRECISIONS = {"fp32": MLPF_FP32, "bf16": MLPF_BF16, "fp8": MLPF_FP8, "fp16": MLPF_FP16}
 
@@ -104,6 +105,19 @@ class Model:
                                        int(max_n), _ptr(logits), _ptr(reg), _ptr(cls),
                                        _ptr(event_sums), s))
         return logits, reg, cls, event_sums
+
+    def autotune(self, x, cu_seqlens, max_n: int, precision="bf16", cache_path=None, stream=None):
+        """Keep the fastest attention variant of `precision` on this batch (device
+        tensors); returns the chosen variant index (None for fp32)."""
+        import torch
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        s = stream if stream is not None else torch.cuda.current_stream(self.device).cuda_stream
+        check(self.L.mlpf_autotune(self.h, prec, _ptr(x), _ptr(cu_seqlens), cu_seqlens.shape[0] - 1,
+                                   x.shape[0], int(max_n),
+                                   cache_path.encode() if cache_path else None, ctypes.c_void_p(s)))
+        opt = {MLPF_BF16: OPT_ATTN_VARIANT_BF16, MLPF_FP16: OPT_ATTN_VARIANT_FP16,
+               MLPF_FP8: OPT_ATTN_VARIANT_FP8}.get(prec)
+        return self.get_option(opt) if opt else None
 
     def calibrate_fp8(self, x, cu_seqlens, max_n: int, stream=None):
         """Static FP8 activation scales from an FP16 run on these events (device tensors)."""

@@ -11,12 +11,13 @@ MLPF_OK, MLPF_E_INVALID, MLPF_E_FORMAT, MLPF_E_CUDA, MLPF_E_OOM, MLPF_E_TIMEOUT,
     MLPF_E_NONFINITE, MLPF_E_UNSUPPORTED = range(8)
 MLPF_FP32, MLPF_BF16, MLPF_FP8, MLPF_FP16 = 0, 1, 2, 3
 OPT_USE_GRAPHS, OPT_WAIT_LIMIT_NS, OPT_DEBUG_STALL, OPT_ATTN_CTAS_PER_SM, OPT_ATTN_KV_STAGES, \
-    OPT_PROFILE = 1, 2, 3, 4, 5, 6
+    OPT_PROFILE, OPT_ATTN_VARIANT_BF16, OPT_ATTN_VARIANT_FP16, OPT_ATTN_VARIANT_FP8 = range(1, 10)
 
 # every symbol include/mlpf.h declares
 EXPORTS = ("mlpf_load_weights", "mlpf_free", "mlpf_get_config", "mlpf_forward",
            "mlpf_forward_host", "mlpf_forward_noalloc", "mlpf_calibrate_fp8", "mlpf_get_fp8_scales",
-           "mlpf_forward_gated", "mlpf_trainer_create", "mlpf_trainer_free", "mlpf_trainer_num_params",
+           "mlpf_autotune", "mlpf_forward_gated", "mlpf_trainer_create", "mlpf_trainer_free",
+           "mlpf_trainer_num_params",
            "mlpf_trainer_step", "mlpf_trainer_export", "mlpf_sync", "mlpf_set_option", "mlpf_get_option",
            "mlpf_last_launch_count", "mlpf_profile_get", "mlpf_last_error", "mlpf_abi_version")
 
@@ -56,6 +57,8 @@ def load(build_if_missing: bool = True):
     L.mlpf_forward_noalloc.restype = ctypes.c_int
     L.mlpf_calibrate_fp8.argtypes = [vp, vp, vp, i32, i32, i32, vp]
     L.mlpf_calibrate_fp8.restype = ctypes.c_int
+    L.mlpf_autotune.argtypes = [vp, i32, vp, vp, i32, i32, i32, ctypes.c_char_p, vp]
+    L.mlpf_autotune.restype = ctypes.c_int
     L.mlpf_get_fp8_scales.argtypes = [vp, i32, ctypes.c_char_p, ctypes.POINTER(ctypes.c_float)]
     L.mlpf_get_fp8_scales.restype = i32
     L.mlpf_forward_gated.argtypes = [vp, vp, ctypes.c_float, i32, i32, vp, vp, i32, i32, i32, vp, vp, vp,

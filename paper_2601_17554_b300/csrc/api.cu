@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdio>
 #include <tuple>
 #include <cmath>
 #include <cstring>
@@ -567,6 +568,94 @@ mlpf_status mlpf_calibrate_fp8(mlpf_model* mm, const float* x, const int32_t* cu
     return MLPF_OK;
 }
 
+static void drop_graphs(Model& m) {
+    for (auto& g : m.graphs) { cudaGraphExecDestroy(g.second.exec); prof_destroy(g.second.prof); }
+    m.graphs.clear();
+    m.last_prof = nullptr;
+}
+
+static int fmt_of(int32_t prec) { return prec == MLPF_FP16 ? 1 : prec == MLPF_FP8 ? 2 : 0; }
+
+mlpf_status mlpf_autotune(mlpf_model* mm, int32_t precision, const float* x, const int32_t* cu_seqlens,
+                          int32_t n_events, int32_t total, int32_t max_n, const char* cache_path,
+                          void* stream) {
+    mlpf_status s = validate(mm ? &mm->impl : nullptr, precision, x, cu_seqlens, n_events, total, max_n, x, x);
+    if (s != MLPF_OK) return s;
+    if (precision == MLPF_FP32) return MLPF_OK;  // nothing to choose on the plain path
+    if (total == 0) { set_error("autotuning needs at least one element"); return MLPF_E_INVALID; }
+    Model& m = mm->impl;
+    CK(cudaSetDevice(m.device));
+    cudaDeviceProp prop;
+    CK(cudaGetDeviceProperties(&prop, m.device));
+    int bucket = 1;
+    while (bucket < total) bucket <<= 1;
+    const std::string key = "sm" + std::to_string(prop.major) + std::to_string(prop.minor) + "_" +
+                            std::to_string(prop.multiProcessorCount) + "_d" + std::to_string(m.cfg.d) + "_prec" +
+                            std::to_string(precision) + "_T" + std::to_string(bucket);
+    const int f = fmt_of(precision);
+    // cache: one "key variant ms" line per tuned case
+    if (cache_path) {
+        FILE* fp = std::fopen(cache_path, "r");
+        if (fp) {
+            char k[256];
+            int v;
+            float ms;
+            bool hit = false;
+            while (!hit && std::fscanf(fp, "%255s %d %f", k, &v, &ms) == 3)
+                if (key == k && v >= 0 && v < 4) hit = true;
+            std::fclose(fp);
+            if (hit) {
+                m.attn_variant[f] = v;
+                drop_graphs(m);
+                return MLPF_OK;
+            }
+        }
+    }
+    s = ensure_workspace(m, total, n_events, true);
+    if (s != MLPF_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    Workspace& w = m.ws;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best_ms = 1e30f;
+    int best = 0;
+    m.cur_prof = nullptr;
+    for (int v = 0; v < 4; ++v) {
+        m.attn_variant[f] = v;
+        float ms_sum = 0.f;
+        for (int rep = 0; rep < 3; ++rep) {
+            cudaEventRecord(e0, st);
+            if (run_forward_tc(m, precision, x, cu_seqlens, n_events, total, max_n, w.hlogits, w.hreg_out, st) < 0) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                set_error("autotune launch failed");
+                return MLPF_E_CUDA;
+            }
+            cudaEventRecord(e1, st);
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) ms_sum += ms;  // the first run warms up
+        }
+        if (ms_sum / 2 < best_ms) { best_ms = ms_sum / 2; best = v; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    s = mlpf_sync(mm, stream);
+    if (s != MLPF_OK) return s;
+    m.attn_variant[f] = best;
+    drop_graphs(m);
+    if (cache_path) {
+        FILE* fp = std::fopen(cache_path, "a");
+        if (fp) {
+            std::fprintf(fp, "%s %d %.4f\n", key.c_str(), best, best_ms);
+            std::fclose(fp);
+        }
+    }
+    return MLPF_OK;
+}
+
 int32_t mlpf_get_fp8_scales(const mlpf_model* mm, int32_t cap, char* names, float* scales) {
     if (!mm) { set_error("model is NULL"); return -1; }
     const Model& m = mm->impl;
@@ -596,6 +685,12 @@ mlpf_status mlpf_set_option(mlpf_model* mm, int32_t option, int64_t value) {
             break;
         case MLPF_OPT_DEBUG_STALL: m.debug_stall = value != 0; break;
         case MLPF_OPT_PROFILE: m.profile = value != 0; break;
+        case MLPF_OPT_ATTN_VARIANT_BF16:
+        case MLPF_OPT_ATTN_VARIANT_FP16:
+        case MLPF_OPT_ATTN_VARIANT_FP8:
+            if (value < 0 || value > 3) { set_error("attention variant must be 0..3"); return MLPF_E_INVALID; }
+            m.attn_variant[option - MLPF_OPT_ATTN_VARIANT_BF16] = (int)value;
+            break;
         case MLPF_OPT_ATTN_CTAS_PER_SM:
             if (value < 1 || value > 1) { set_error("attention runs one CTA per SM in this build"); return MLPF_E_INVALID; }
             m.attn_ctas_per_sm = (int)value;
@@ -618,8 +713,11 @@ mlpf_status mlpf_get_option(const mlpf_model* mm, int32_t option, int64_t* value
         case MLPF_OPT_WAIT_LIMIT_NS: *value = m.wait_limit_ns; return MLPF_OK;
         case MLPF_OPT_DEBUG_STALL: *value = m.debug_stall; return MLPF_OK;
         case MLPF_OPT_ATTN_CTAS_PER_SM: *value = m.attn_ctas_per_sm; return MLPF_OK;
-        case MLPF_OPT_ATTN_KV_STAGES: *value = 4; return MLPF_OK;
+        case MLPF_OPT_ATTN_KV_STAGES: *value = (m.attn_variant[0] & 1) ? 2 : 4; return MLPF_OK;
         case MLPF_OPT_PROFILE: *value = m.profile; return MLPF_OK;
+        case MLPF_OPT_ATTN_VARIANT_BF16:
+        case MLPF_OPT_ATTN_VARIANT_FP16:
+        case MLPF_OPT_ATTN_VARIANT_FP8: *value = m.attn_variant[option - MLPF_OPT_ATTN_VARIANT_BF16]; return MLPF_OK;
         default: set_error("unknown option " + std::to_string(option)); return MLPF_E_INVALID;
     }
 }

@@ -849,18 +849,25 @@ __global__ void __launch_bounds__(PT_THREADS, 1) k_post(const __grid_constant__ 
 // P) on tcgen05 into the same TMEM buffer, accumulated into registers with the
 // running rescale.  Warps signal through mbarriers only, and every wait is
 // bounded.
-constexpr int AT_STAGES = 4;
-constexpr int AT_THREADS = NH * 128 + 32;
+// Attention variants (chosen by the autotuner): HPW heads per consumer warpgroup
+// (NH / HPW warpgroups) and a K/V pipeline of ST stages.
 constexpr uint32_t AT_QB = 128 * 128;   // Q tile bytes (128 rows x 64 ch, 16-bit)
 constexpr uint32_t AT_KB = 64 * 128;    // K tile bytes (64 keys x 64 ch)
 constexpr uint32_t AT_VB = 64 * 128;    // V^T tile bytes (64 ch x 64 keys)
 constexpr uint32_t AT_PB = 128 * 128;   // P tile bytes per head (128 rows x 64 keys)
-constexpr uint32_t AT_OFF_K = 2 * AT_QB;
-constexpr uint32_t AT_OFF_V = AT_OFF_K + AT_STAGES * AT_KB;
-constexpr uint32_t AT_OFF_P = AT_OFF_V + AT_STAGES * AT_VB;
-constexpr uint32_t AT_OFF_ONE = AT_OFF_P + NH * AT_PB;   // 16 x 64 block of ones
-constexpr uint32_t AT_OFF_BAR = AT_OFF_ONE + 16 * 128;
-constexpr uint32_t AT_SMEM = AT_OFF_BAR + 512 + 1024;
+template <int HPW>
+constexpr int at_wg() { return NH / HPW; }
+template <int HPW>
+constexpr int at_threads() { return at_wg<HPW>() * 128 + 32; }
+template <int ST>
+struct AtLayout {
+    static constexpr uint32_t OFF_K = 2 * AT_QB;
+    static constexpr uint32_t OFF_V = OFF_K + ST * AT_KB;
+    static constexpr uint32_t OFF_P = OFF_V + ST * AT_VB;
+    static constexpr uint32_t OFF_ONE = OFF_P + NH * AT_PB;   // 16 x 64 block of ones
+    static constexpr uint32_t OFF_BAR = OFF_ONE + 16 * 128;
+    static constexpr uint32_t SMEM = OFF_BAR + 512 + 1024;
+};
 
 struct AttnParams {
     const int4* items;
@@ -925,44 +932,50 @@ MLPF_DEV bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* ab, unsign
     return __all_sync(0xffffffffu, ok);
 }
 
-// 17 warps: one SM sub-partition holds five of them, which caps the kernel at
-// 96 registers per thread (5 x 32 x 96 <= 16384).
-template <bool F16>
-__global__ void __launch_bounds__(AT_THREADS, 1)
+// NH/HPW consumer warpgroups (heads HPW*w .. HPW*w+HPW-1 each) and a TMA producer
+// warp.  The register budget follows from the warp count: with HPW = 1, 17 warps,
+// five share an SM sub-partition (96 registers a thread); with HPW = 2, nine
+// warps, three share one (up to 168).
+template <bool F16, int HPW, int ST>
+__global__ void __launch_bounds__(at_threads<HPW>(), 1)
     k_attention(const __grid_constant__ CUtensorMap map_q, const __grid_constant__ CUtensorMap map_k,
                 const __grid_constant__ CUtensorMap map_vt, AttnParams p) {
+    constexpr int AT_WG = at_wg<HPW>(), AT_THREADS = at_threads<HPW>(), AT_STAGES = ST;
+    using LY = AtLayout<ST>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sm = align1024(smem_raw);
     uint8_t* sQ = sm;
-    uint8_t* sK = sm + AT_OFF_K;
-    uint8_t* sV = sm + AT_OFF_V;
-    uint8_t* sP = sm + AT_OFF_P;
-    uint8_t* sOne = sm + AT_OFF_ONE;
-    uint64_t* bars = (uint64_t*)(sm + AT_OFF_BAR);
+    uint8_t* sK = sm + LY::OFF_K;
+    uint8_t* sV = sm + LY::OFF_V;
+    uint8_t* sP = sm + LY::OFF_P;
+    uint8_t* sOne = sm + LY::OFF_ONE;
+    uint64_t* bars = (uint64_t*)(sm + LY::OFF_BAR);
     uint64_t* q_full = bars;                 // [2]
     uint64_t* q_empty = bars + 2;            // [2]
-    uint64_t* kv_full = bars + 4;            // [4]
-    uint64_t* kv_empty = bars + 8;           // [4]
-    uint64_t* s_full = bars + 12;            // [4 heads][2 buffers]
-    uint64_t* pv_done = bars + 20;           // [4 heads]
-    uint64_t* p_ready = bars + 24;           // [4 heads], one arrival per warp
-    uint64_t* s_free = bars + 28;            // [4 heads][2 buffers], one arrival per warp
-    uint64_t* never = bars + 36;             // armed by nobody (debug stall)
-    int4* info = (int4*)(bars + 38);         // [2]
+    uint64_t* kv_full = bars + 4;             // [stages]
+    uint64_t* kv_empty = kv_full + AT_STAGES; // [stages]
+    uint64_t* s_full = kv_empty + AT_STAGES;  // [warpgroups][2 buffers]
+    uint64_t* pv_done = s_full + 2 * AT_WG;   // [warpgroups]
+    uint64_t* p_ready = pv_done + AT_WG;      // [warpgroups], one arrival per warp
+    uint64_t* s_free = p_ready + AT_WG;       // [warpgroups][2 buffers], one arrival per warp
+    uint64_t* never = s_free + 2 * AT_WG;     // armed by nobody (debug stall)
+    int4* info = (int4*)(never + 2);          // [2]
     uint32_t* tmem_hold = (uint32_t*)(info + 2);
     int* abort_flag = (int*)(tmem_hold + 1);
     volatile int* ab = abort_flag;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     if (tid == 0) {
-        for (int i = 0; i < 2; ++i) { mbar_init(&q_full[i], 1); mbar_init(&q_empty[i], NH); }
-        for (int i = 0; i < AT_STAGES; ++i) { mbar_init(&kv_full[i], 1); mbar_init(&kv_empty[i], NH); }
-        for (int i = 0; i < 2 * NH; ++i) mbar_init(&s_full[i], 1);
-        for (int i = 0; i < NH; ++i) {
+        for (int i = 0; i < 2; ++i) { mbar_init(&q_full[i], 1); mbar_init(&q_empty[i], AT_WG); }
+        for (int i = 0; i < AT_STAGES; ++i) { mbar_init(&kv_full[i], 1); mbar_init(&kv_empty[i], AT_WG); }
+        for (int i = 0; i < 2 * AT_WG; ++i) {
+            mbar_init(&s_full[i], 1);
+            mbar_init(&s_free[i], 4);
+        }
+        for (int i = 0; i < AT_WG; ++i) {
             mbar_init(&pv_done[i], 1);
             mbar_init(&p_ready[i], 4);
         }
-        for (int i = 0; i < 2 * NH; ++i) mbar_init(&s_free[i], 4);
         mbar_init(never, 1);
         *abort_flag = 0;
         fence_mbar_init();
@@ -983,7 +996,7 @@ __global__ void __launch_bounds__(AT_THREADS, 1)
     const int n_items = p.counters[0];
     int* ticket = p.counters + 2 + p.layer;
 
-    if (warp == NH * 4) {
+    if (warp == AT_WG * 4) {
         // ------------------------------------------------ TMA producer
         if (lane == 0) {
             tma_prefetch_map(&map_q);
@@ -1024,43 +1037,45 @@ __global__ void __launch_bounds__(AT_THREADS, 1)
             }
         }
     } else {
-        // ------------------------------------------------ one warpgroup per head
-        const int h = warp >> 2;
+        // ------------------------------------------------ one warpgroup per HPW heads
+        // Barrier phases (parity waits stay at most one completion behind):
+        //  s_full[w][b]: tiles b, b+2, ...; QK^T(t+2) needs s_free of tile t, i.e.
+        //                every warp past its wait for S(t).
+        //  s_free[w][b]: one completion per tile in buffer b (four warps read its
+        //                PV partials); the next needs PV of tile t+2, issued only
+        //                after the leader's wait.
+        //  p_ready[w]:   one per tile; a warp stores P(t+1) only after PV(t), which
+        //                the leader issues after its wait.
+        //  pv_done[w]:   one per tile; PV(t+1) needs every warp's P(t+1), stored
+        //                after that warp's wait for PV(t).
+        const int wgi = warp >> 2;
+        const int h0 = HPW * wgi;                // this warpgroup's heads: h0 .. h0 + HPW - 1
         const int r = tid & 127;                 // query row within the tile
-        const bool leader = r == 0;              // issues this head's MMAs
+        const bool leader = r == 0;              // issues this warpgroup's MMAs
         const uint32_t tl = tbase + ((uint32_t)((warp & 3) * 32) << 16);  // this warp's lanes
-        const uint32_t scol = h * 128;           // two 64-column S buffers per head
         const uint32_t fmt = F16 ? 0u : 1u;
         const uint32_t IQK = idesc_f16(128, 64, fmt), IPV = idesc_f16(128, 16, fmt);
         const float c = 0.25f * 1.4426950408889634f;  // log2(e) / sqrt(16)
-        uint8_t* myP = sP + h * AT_PB;
         const uint32_t one_addr = smem_u32(sOne);
         int q_it = 0;
         uint32_t g = 0;   // global key-tile counter (same sequence as the producer)
         bool ok = true;
-        // Barrier phases.  Every barrier below is waited on with a parity bit, which
-        // is only sound while the waiter is at most one completion behind:
-        //  s_full[h][b]: tiles b, b+2, ...; the next QK^T into buffer b needs
-        //                s_free of this tile, i.e. every warp past its s_full wait.
-        //  s_free[h][b]: one completion per tile in buffer b (all four warps read
-        //                its PV partial); the next completion needs PV of the
-        //                next tile in b, issued only after the leader's wait.
-        //  p_ready[h]:   one completion per tile; a warp stores P(t+1) only after
-        //                PV(t), which the leader issues after its wait.
-        //  pv_done[h]:   one completion per tile; PV(t+1) needs every warp's P(t+1),
-        //                stored after that warp's wait for PV(t).
-        // QK^T(t) overwrites TMEM buffer t&1, last used by tile t-2.
-        auto issue_qk = [&](uint32_t gg, int qb) -> bool {
-            if (gg >= 2 && !mbar_wait(&s_free[h * 2 + (gg & 1)], ((gg - 2) >> 1) & 1, ab, p.status,
-                                      ST_TIMEOUT_ATTN, p.wait_ns))
+        // S columns of head h, buffer b: h*128 + b*64
+        auto issue_qk = [&](uint32_t t, int qb) -> bool {
+            if (t >= 2 && !mbar_wait(&s_free[wgi * 2 + (t & 1)], ((t - 2) >> 1) & 1, ab, p.status,
+                                     ST_TIMEOUT_ATTN, p.wait_ns))
                 return false;
-            const uint32_t s = gg & (AT_STAGES - 1);
-            if (!mbar_wait(&kv_full[s], (gg / AT_STAGES) & 1, ab, p.status, ST_TIMEOUT_ATTN, p.wait_ns))
+            const uint32_t s = t & (AT_STAGES - 1);
+            if (!mbar_wait(&kv_full[s], (t / AT_STAGES) & 1, ab, p.status, ST_TIMEOUT_ATTN, p.wait_ns))
                 return false;
             tc_fence_after();
-            mma_f16(tbase + scol + (gg & 1) * 64, sdesc_sw128(smem_u32(sQ + qb * AT_QB) + h * 32),
-                    sdesc_sw128(smem_u32(sK + s * AT_KB) + h * 32), IQK, 0);
-            mma_commit(&s_full[h * 2 + (gg & 1)]);
+#pragma unroll
+            for (int hh = 0; hh < HPW; ++hh) {
+                const int h = h0 + hh;
+                mma_f16(tbase + h * 128 + (t & 1) * 64, sdesc_sw128(smem_u32(sQ + qb * AT_QB) + h * 32),
+                        sdesc_sw128(smem_u32(sK + s * AT_KB) + h * 32), IQK, 0);
+            }
+            mma_commit(&s_full[wgi * 2 + (t & 1)]);
             return true;
         };
         while (ok) {
@@ -1075,89 +1090,116 @@ __global__ void __launch_bounds__(AT_THREADS, 1)
                 ++q_it;
                 continue;
             }
-            const int qrow0 = it.x + it.y * ROWS;
-            const int rows_valid = min(ROWS, it.z - it.y * ROWS);
-            float o[16];
+            float o[HPW][16];
 #pragma unroll
-            for (int i = 0; i < 16; ++i) o[i] = 0.f;
-            float m = -INFINITY, l = 0.f, alpha_prev = 0.f;
+            for (int hh = 0; hh < HPW; ++hh)
+#pragma unroll
+                for (int i = 0; i < 16; ++i) o[hh][i] = 0.f;
+            float m[HPW], l[HPW], alpha_prev[HPW];
+#pragma unroll
+            for (int hh = 0; hh < HPW; ++hh) {
+                m[hh] = -INFINITY;
+                l[hh] = 0.f;
+                alpha_prev[hh] = 0.f;
+            }
             if (leader) ok = issue_qk(g, qb);
             ok = __all_sync(0xffffffffu, ok);   // keep every lane of the warp on one path
             for (int j = 0; j < nk && ok; ++j) {
-                const uint32_t gj = g + j;
-                const uint32_t sb = gj & 1;
+                const uint32_t t = g + j;
+                const uint32_t sb = t & 1;
                 if (j > 0) {
-                    // PV and P.1 of tile j-1 landed in the other buffer's columns 0..31
-                    if (!warp_wait(&pv_done[h], (gj - 1) & 1, ab, p.status, p.wait_ns)) { ok = false; break; }
+                    // PV and P.1 of tile t-1 (each head) landed in buffer sb^1, columns 0..31
+                    if (!warp_wait(&pv_done[wgi], (t - 1) & 1, ab, p.status, p.wait_ns)) { ok = false; break; }
                     tc_fence_after();
-                    float part[32];
-                    tmem_ld32(tl + scol + (sb ^ 1) * 64, part);
+                    float part[HPW][32];
+#pragma unroll
+                    for (int hh = 0; hh < HPW; ++hh) tmem_ld32(tl + (h0 + hh) * 128 + (sb ^ 1) * 64, part[hh]);
                     tmem_wait_ld();
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) o[i] = fmaf(o[i], alpha_prev, part[i]);
-                    l = fmaf(l, alpha_prev, part[16]);
+                    for (int hh = 0; hh < HPW; ++hh) {
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) o[hh][i] = fmaf(o[hh][i], alpha_prev[hh], part[hh][i]);
+                        l[hh] = fmaf(l[hh], alpha_prev[hh], part[hh][16]);
+                    }
                     tc_fence_before();
                     __syncwarp();
-                    if (lane == 0) mbar_arrive(&s_free[h * 2 + (sb ^ 1)]);
+                    if (lane == 0) mbar_arrive(&s_free[wgi * 2 + (sb ^ 1)]);
                 }
-                if (leader && j + 1 < nk) ok = issue_qk(gj + 1, qb);
+                if (leader && j + 1 < nk) ok = issue_qk(t + 1, qb);
                 ok = __all_sync(0xffffffffu, ok);
                 if (!ok) break;
-                if (!warp_wait(&s_full[h * 2 + sb], (gj >> 1) & 1, ab, p.status, p.wait_ns)) { ok = false; break; }
+                if (!warp_wait(&s_full[wgi * 2 + sb], (t >> 1) & 1, ab, p.status, p.wait_ns)) { ok = false; break; }
                 tc_fence_after();
-                const uint32_t sa = tl + scol + sb * 64;
                 const bool last = (j == nk - 1);
                 const int kvalid = it.z - 64 * j;
-                float s[32];
-                // pass 1: row max over the two 32-column halves (re-read below, to
-                // stay within the register budget)
-                float mx = -INFINITY;
+                float s[HPW][32];
+                // pass 1: row max of each head over the two 32-column halves
+                float mx[HPW];
+#pragma unroll
+                for (int hh = 0; hh < HPW; ++hh) mx[hh] = -INFINITY;
 #pragma unroll
                 for (int hf = 0; hf < 2; ++hf) {
-                    tmem_ld32(sa + 32 * hf, s);
+#pragma unroll
+                    for (int hh = 0; hh < HPW; ++hh) tmem_ld32(tl + (h0 + hh) * 128 + sb * 64 + 32 * hf, s[hh]);
                     tmem_wait_ld();
-                    if (last) {
 #pragma unroll
-                        for (int i = 0; i < 32; ++i)
-                            if (i + 32 * hf >= kvalid) s[i] = -INFINITY;
+                    for (int hh = 0; hh < HPW; ++hh) {
+                        if (last) {
+#pragma unroll
+                            for (int i = 0; i < 32; ++i)
+                                if (i + 32 * hf >= kvalid) s[hh][i] = -INFINITY;
+                        }
+#pragma unroll
+                        for (int i = 0; i < 32; i += 2) mx[hh] = max3f(mx[hh], s[hh][i], s[hh][i + 1]);
                     }
-#pragma unroll
-                    for (int i = 0; i < 32; i += 2) mx = max3f(mx, s[i], s[i + 1]);
                 }
-                const float m_new = fmaxf(m, mx * c);
-                alpha_prev = ex2_approx(m - m_new);
-                m = m_new;
-                // pass 2: exponentials into the P tile
+                float m_new[HPW];
+#pragma unroll
+                for (int hh = 0; hh < HPW; ++hh) {
+                    m_new[hh] = fmaxf(m[hh], mx[hh] * c);
+                    alpha_prev[hh] = ex2_approx(m[hh] - m_new[hh]);
+                    m[hh] = m_new[hh];
+                }
+                // pass 2: exponentials into the P tiles
 #pragma unroll
                 for (int hf = 0; hf < 2; ++hf) {
-                    tmem_ld32(sa + 32 * hf, s);
-                    tmem_wait_ld();
-                    if (last) {
 #pragma unroll
-                        for (int i = 0; i < 32; ++i)
-                            if (i + 32 * hf >= kvalid) s[i] = -INFINITY;
+                    for (int hh = 0; hh < HPW; ++hh) tmem_ld32(tl + (h0 + hh) * 128 + sb * 64 + 32 * hf, s[hh]);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int hh = 0; hh < HPW; ++hh) {
+                        if (last) {
+#pragma unroll
+                            for (int i = 0; i < 32; ++i)
+                                if (i + 32 * hf >= kvalid) s[hh][i] = -INFINITY;
+                        }
+                        softmax_chunk32<F16>(s[hh], c, -m_new[hh], sP + (h0 + hh) * AT_PB, r, 4 * hf);
                     }
-                    softmax_chunk32<F16>(s, c, -m_new, myP, r, 4 * hf);
                 }
                 fence_proxy_async_smem();
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&p_ready[h]);
+                if (lane == 0) mbar_arrive(&p_ready[wgi]);
                 if (leader) {
-                    if (!mbar_wait(&p_ready[h], gj & 1, ab, p.status, ST_TIMEOUT_ATTN, p.wait_ns)) {
+                    if (!mbar_wait(&p_ready[wgi], t & 1, ab, p.status, ST_TIMEOUT_ATTN, p.wait_ns)) {
                         ok = false;
                     } else {
                         tc_fence_after();
-                        const uint32_t st = gj & (AT_STAGES - 1);
-                        const uint32_t pa = smem_u32(myP), va = smem_u32(sV + st * AT_VB) + h * 16 * 128;
-                        const uint32_t dst = tbase + scol + sb * 64;
+                        const uint32_t st = t & (AT_STAGES - 1);
 #pragma unroll
-                        for (int kc = 0; kc < 4; ++kc) {
-                            mma_f16(dst, sdesc_sw128(pa + kc * 32), sdesc_sw128(va + kc * 32), IPV, kc > 0 ? 1u : 0u);
-                            mma_f16(dst + 16, sdesc_sw128(pa + kc * 32), sdesc_sw128(one_addr + kc * 32), IPV,
-                                    kc > 0 ? 1u : 0u);
+                        for (int hh = 0; hh < HPW; ++hh) {
+                            const int h = h0 + hh;
+                            const uint32_t pa = smem_u32(sP + h * AT_PB), va = smem_u32(sV + st * AT_VB) + h * 16 * 128;
+                            const uint32_t dst = tbase + h * 128 + sb * 64;
+#pragma unroll
+                            for (int kc = 0; kc < 4; ++kc) {
+                                mma_f16(dst, sdesc_sw128(pa + kc * 32), sdesc_sw128(va + kc * 32), IPV,
+                                        kc > 0 ? 1u : 0u);
+                                mma_f16(dst + 16, sdesc_sw128(pa + kc * 32), sdesc_sw128(one_addr + kc * 32), IPV,
+                                        kc > 0 ? 1u : 0u);
+                            }
                         }
-                        mma_commit(&pv_done[h]);
+                        mma_commit(&pv_done[wgi]);
                         mma_commit(&kv_empty[st]);
                     }
                 }
@@ -1165,34 +1207,42 @@ __global__ void __launch_bounds__(AT_THREADS, 1)
             }
             if (!ok) break;
             const uint32_t gl = g + nk - 1;
-            if (!warp_wait(&pv_done[h], gl & 1, ab, p.status, p.wait_ns)) break;
+            if (!warp_wait(&pv_done[wgi], gl & 1, ab, p.status, p.wait_ns)) break;
             tc_fence_after();
             {
-                float part[32];
-                tmem_ld32(tl + scol + (gl & 1) * 64, part);
+                float part[HPW][32];
+#pragma unroll
+                for (int hh = 0; hh < HPW; ++hh) tmem_ld32(tl + (h0 + hh) * 128 + (gl & 1) * 64, part[hh]);
                 tmem_wait_ld();
 #pragma unroll
-                for (int i = 0; i < 16; ++i) o[i] = fmaf(o[i], alpha_prev, part[i]);
-                l = fmaf(l, alpha_prev, part[16]);
+                for (int hh = 0; hh < HPW; ++hh) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) o[hh][i] = fmaf(o[hh][i], alpha_prev[hh], part[hh][i]);
+                    l[hh] = fmaf(l[hh], alpha_prev[hh], part[hh][16]);
+                }
             }
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&s_free[h * 2 + (gl & 1)]);
+            if (lane == 0) mbar_arrive(&s_free[wgi * 2 + (gl & 1)]);
             if (leader) mbar_arrive(&q_empty[qb]);  // every QK^T of this item has completed
-            if (r < rows_valid) {
-                const float inv = 1.0f / l;
-                uint4 u0, u1;
-                u0.x = pack2<F16>(o[0] * inv, o[1] * inv);
-                u0.y = pack2<F16>(o[2] * inv, o[3] * inv);
-                u0.z = pack2<F16>(o[4] * inv, o[5] * inv);
-                u0.w = pack2<F16>(o[6] * inv, o[7] * inv);
-                u1.x = pack2<F16>(o[8] * inv, o[9] * inv);
-                u1.y = pack2<F16>(o[10] * inv, o[11] * inv);
-                u1.z = pack2<F16>(o[12] * inv, o[13] * inv);
-                u1.w = pack2<F16>(o[14] * inv, o[15] * inv);
-                uint4* dst = (uint4*)(p.out + (size_t)(qrow0 + r) * D + h * 16);
-                dst[0] = u0;
-                dst[1] = u1;
+            const int qrow0 = it.x + it.y * ROWS;
+            if (r < min(ROWS, it.z - it.y * ROWS)) {
+#pragma unroll
+                for (int hh = 0; hh < HPW; ++hh) {
+                    const float inv = 1.0f / l[hh];
+                    uint4 u0, u1;
+                    u0.x = pack2<F16>(o[hh][0] * inv, o[hh][1] * inv);
+                    u0.y = pack2<F16>(o[hh][2] * inv, o[hh][3] * inv);
+                    u0.z = pack2<F16>(o[hh][4] * inv, o[hh][5] * inv);
+                    u0.w = pack2<F16>(o[hh][6] * inv, o[hh][7] * inv);
+                    u1.x = pack2<F16>(o[hh][8] * inv, o[hh][9] * inv);
+                    u1.y = pack2<F16>(o[hh][10] * inv, o[hh][11] * inv);
+                    u1.z = pack2<F16>(o[hh][12] * inv, o[hh][13] * inv);
+                    u1.w = pack2<F16>(o[hh][14] * inv, o[hh][15] * inv);
+                    uint4* dst = (uint4*)(p.out + (size_t)(qrow0 + r) * D + (h0 + hh) * 16);
+                    dst[0] = u0;
+                    dst[1] = u1;
+                }
             }
             g += nk;
             ++q_it;
@@ -1303,7 +1353,10 @@ int occupancy(K kernel, int threads, uint32_t smem) {
 // empty string or a description of the kernels that do not fit.
 template <int FMT>
 std::string check_occupancy() {
-    const int o[6] = {occupancy(k_attention<kOutF16<FMT>>, AT_THREADS, AT_SMEM),
+    const int o[6] = {std::min(std::min(occupancy(k_attention<kOutF16<FMT>, 1, 4>, at_threads<1>(), AtLayout<4>::SMEM),
+                                        occupancy(k_attention<kOutF16<FMT>, 1, 2>, at_threads<1>(), AtLayout<2>::SMEM)),
+                               std::min(occupancy(k_attention<kOutF16<FMT>, 2, 4>, at_threads<2>(), AtLayout<4>::SMEM),
+                                        occupancy(k_attention<kOutF16<FMT>, 2, 2>, at_threads<2>(), AtLayout<2>::SMEM))),
                       occupancy(k_post<0, FMT>, PT_THREADS, post_smem(0, FMT)),
                       occupancy(k_post<1, FMT>, PT_THREADS, post_smem(1, FMT)),
                       occupancy(k_post<2, FMT>, PT_THREADS, post_smem(2, FMT)),
@@ -1324,7 +1377,10 @@ void set_attrs() {
     cudaFuncSetAttribute(k_post<0, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, post_smem(0, FMT));
     cudaFuncSetAttribute(k_post<1, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, post_smem(1, FMT));
     cudaFuncSetAttribute(k_post<2, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, post_smem(2, FMT));
-    cudaFuncSetAttribute(k_attention<kOutF16<FMT>>, cudaFuncAttributeMaxDynamicSharedMemorySize, AT_SMEM);
+    cudaFuncSetAttribute(k_attention<kOutF16<FMT>, 1, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, AtLayout<4>::SMEM);
+    cudaFuncSetAttribute(k_attention<kOutF16<FMT>, 1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, AtLayout<2>::SMEM);
+    cudaFuncSetAttribute(k_attention<kOutF16<FMT>, 2, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, AtLayout<4>::SMEM);
+    cudaFuncSetAttribute(k_attention<kOutF16<FMT>, 2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, AtLayout<2>::SMEM);
 }
 
 }  // namespace
@@ -1505,7 +1561,14 @@ static int64_t run_tc(Model& m, const float* x, const int32_t* cu, int n_events,
     auto attention = [&](int layer) {
         AttnParams ap{w.items, w.counters, layer, (uint16_t*)w.to, m.status, (uint64_t)m.wait_limit_ns, m.debug_stall ? 1 : 0};
         prof_begin(m, st, "attention");
-        k_attention<kOutF16<FMT>><<<grid * m.attn_ctas_per_sm, AT_THREADS, AT_SMEM, st>>>(w.map_q, w.map_k, w.map_vt, ap);
+        constexpr bool AF = kOutF16<FMT>;
+        const dim3 g(grid * m.attn_ctas_per_sm);
+        switch (m.attn_variant[FMT]) {
+            case 1: k_attention<AF, 1, 2><<<g, at_threads<1>(), AtLayout<2>::SMEM, st>>>(w.map_q, w.map_k, w.map_vt, ap); break;
+            case 2: k_attention<AF, 2, 4><<<g, at_threads<2>(), AtLayout<4>::SMEM, st>>>(w.map_q, w.map_k, w.map_vt, ap); break;
+            case 3: k_attention<AF, 2, 2><<<g, at_threads<2>(), AtLayout<2>::SMEM, st>>>(w.map_q, w.map_k, w.map_vt, ap); break;
+            default: k_attention<AF, 1, 4><<<g, at_threads<1>(), AtLayout<4>::SMEM, st>>>(w.map_q, w.map_k, w.map_vt, ap); break;
+        }
         prof_end(m, st);
         ++n;
     };

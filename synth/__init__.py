@@ -106,16 +106,17 @@ def sizes_lognormal(seed: int, n_events: int, median: float = 2500.0,
 # events
 # --------------------------------------------------------------------------
 
-def gen_events(seed: int, sizes):
+def gen_events(seed: int, sizes, first_event: int = 0):
     """Packed events: x [T, 42] float32 and cu_seqlens [n+1] int32.
 
-    Element i of event e depends only on (seed, e, i).
+    Element i of event e depends only on (seed, first_event + e, i), so a large
+    set can be generated in independent chunks.
     """
     sizes = np.asarray(sizes, dtype=np.int64)
     cu = np.zeros(len(sizes) + 1, dtype=np.int64)
     np.cumsum(sizes, out=cu[1:])
     total = int(cu[-1])
-    ev = np.repeat(np.arange(len(sizes), dtype=np.uint64), sizes)
+    ev = np.repeat(np.arange(len(sizes), dtype=np.uint64) + np.uint64(first_event), sizes)
     idx = (np.arange(total, dtype=np.int64) - np.repeat(cu[:-1], sizes)).astype(np.uint64)
     x = np.zeros((total, IN_DIM), dtype=np.float32)
     if total == 0:
