@@ -257,13 +257,21 @@ enum {
     MLPF_OPT_ATTN_KV_STAGES = 5,    /* read-only: K/V pipeline depth of the BF16 variant */
     MLPF_OPT_PROFILE = 6,           /* 1: CUDA events around every kernel launch (also
                                        inside captured graphs); see mlpf_profile_get */
-    MLPF_OPT_ATTN_VARIANT_BF16 = 7, /* attention kernel variant of a precision, 0..3:
-                                       0 = one head per warpgroup, 4 K/V stages (default);
-                                       1 = one head, 2 stages; 2 = two heads, 4 stages;
-                                       3 = two heads, 2 stages.  Set by mlpf_autotune. */
+    MLPF_OPT_ATTN_VARIANT_BF16 = 7, /* attention kernel variant of a precision,
+                                       0..MLPF_ATTN_VARIANTS-1 (set by mlpf_autotune):
+                                       tcgen05, 64-key score tiles, one head per warpgroup:
+                                         0 = 4 K/V stages, 1 = 2, 5 = 6;
+                                       tcgen05, 64-key tiles, two heads per warpgroup:
+                                         2 = 4 stages, 3 = 2 stages;
+                                       tcgen05, 32-key score tiles, four TMEM buffers per
+                                       head, PV partial folded one tile late:
+                                         4 = 4 stages, 6 = 6 stages;
+                                       warp-level MMAs, each warp 32 rows of one head:
+                                         7 = 4 stages, 8 = 8 stages (default) */
     MLPF_OPT_ATTN_VARIANT_FP16 = 8,
     MLPF_OPT_ATTN_VARIANT_FP8 = 9
 };
+#define MLPF_ATTN_VARIANTS 9
 mlpf_status mlpf_set_option(mlpf_model* m, int32_t option, int64_t value);
 mlpf_status mlpf_get_option(const mlpf_model* m, int32_t option, int64_t* value);
 

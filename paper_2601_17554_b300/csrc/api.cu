@@ -602,7 +602,7 @@ mlpf_status mlpf_autotune(mlpf_model* mm, int32_t precision, const float* x, con
             float ms;
             bool hit = false;
             while (!hit && std::fscanf(fp, "%255s %d %f", k, &v, &ms) == 3)
-                if (key == k && v >= 0 && v < 4) hit = true;
+                if (key == k && v >= 0 && v < MLPF_ATTN_VARIANTS) hit = true;
             std::fclose(fp);
             if (hit) {
                 m.attn_variant[f] = v;
@@ -621,7 +621,7 @@ mlpf_status mlpf_autotune(mlpf_model* mm, int32_t precision, const float* x, con
     float best_ms = 1e30f;
     int best = 0;
     m.cur_prof = nullptr;
-    for (int v = 0; v < 4; ++v) {
+    for (int v = 0; v < MLPF_ATTN_VARIANTS; ++v) {
         m.attn_variant[f] = v;
         float ms_sum = 0.f;
         for (int rep = 0; rep < 3; ++rep) {
@@ -688,7 +688,10 @@ mlpf_status mlpf_set_option(mlpf_model* mm, int32_t option, int64_t value) {
         case MLPF_OPT_ATTN_VARIANT_BF16:
         case MLPF_OPT_ATTN_VARIANT_FP16:
         case MLPF_OPT_ATTN_VARIANT_FP8:
-            if (value < 0 || value > 3) { set_error("attention variant must be 0..3"); return MLPF_E_INVALID; }
+            if (value < 0 || value >= MLPF_ATTN_VARIANTS) {
+                set_error("attention variant must be 0.." + std::to_string(MLPF_ATTN_VARIANTS - 1));
+                return MLPF_E_INVALID;
+            }
             m.attn_variant[option - MLPF_OPT_ATTN_VARIANT_BF16] = (int)value;
             break;
         case MLPF_OPT_ATTN_CTAS_PER_SM:
@@ -713,7 +716,11 @@ mlpf_status mlpf_get_option(const mlpf_model* mm, int32_t option, int64_t* value
         case MLPF_OPT_WAIT_LIMIT_NS: *value = m.wait_limit_ns; return MLPF_OK;
         case MLPF_OPT_DEBUG_STALL: *value = m.debug_stall; return MLPF_OK;
         case MLPF_OPT_ATTN_CTAS_PER_SM: *value = m.attn_ctas_per_sm; return MLPF_OK;
-        case MLPF_OPT_ATTN_KV_STAGES: *value = (m.attn_variant[0] & 1) ? 2 : 4; return MLPF_OK;
+        case MLPF_OPT_ATTN_KV_STAGES: {
+            static const int stages[MLPF_ATTN_VARIANTS] = {4, 2, 4, 2, 4, 6, 6, 4, 8};
+            *value = stages[m.attn_variant[0]];
+            return MLPF_OK;
+        }
         case MLPF_OPT_PROFILE: *value = m.profile; return MLPF_OK;
         case MLPF_OPT_ATTN_VARIANT_BF16:
         case MLPF_OPT_ATTN_VARIANT_FP16:

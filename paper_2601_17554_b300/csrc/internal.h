@@ -99,9 +99,9 @@ struct Model {
     int64_t wait_limit_ns = 2000000000LL;
     bool debug_stall = false;
     int attn_ctas_per_sm = 1;
-    // attention variant per operand format (BF16, FP16, E4M3): 0 = 1 head per
-    // warpgroup / 4 K-V stages, 1 = 1 / 2, 2 = 2 / 4, 3 = 2 / 2 (set by the autotuner)
-    int attn_variant[3] = {0, 0, 0};
+    // attention kernel variant per operand format (BF16, FP16, E4M3), numbered as
+    // MLPF_OPT_ATTN_VARIANT_* in mlpf.h; default: warp-level MMAs, 8 K/V stages
+    int attn_variant[3] = {8, 8, 8};
     // FP8: activation slots (one per GEMM input) and their static scales s_a = amax / 448
     std::map<std::string, int> act_slot;
     std::vector<float> act_scale;

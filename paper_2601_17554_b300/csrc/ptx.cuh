@@ -235,4 +235,27 @@ MLPF_DEV uint32_t sw128_off(int r, int c) {
     return (uint32_t)r * 128u + ((uint32_t)(c ^ (r & 7)) << 4);
 }
 
+// ---------------------------------------------------- warp-level MMA (m16n8k16)
+// Four 8x8 16-bit matrices from shared memory; lanes 8i..8i+7 give the row
+// addresses of matrix i, which lands in register i.
+MLPF_DEV void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+// d[16x8] += a[16x16] * b[16x8], FP32 accumulate; 16-bit operands FP16 or BF16
+template <bool F16>
+MLPF_DEV void mma16816(float* d, const uint32_t* a, uint32_t b0, uint32_t b1) {
+    if constexpr (F16)
+        asm("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+            "{%0, %1, %2, %3};"
+            : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+    else
+        asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+            "{%0, %1, %2, %3};"
+            : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
 }  // namespace mlpf
