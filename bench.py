@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp16", "fp8", "fp32"])
+    ap.add_argument("--attn-variant", type=int, default=None,
+                    help="fixed attention kernel variant (default: autotuned on the batch)")
     ap.add_argument("--no-baselines", action="store_true",
                     help="skip the FP32-plain, per-event-latency and CPU-oracle legs")
     ap.add_argument("--events", type=int, default=512,
@@ -149,17 +151,9 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def measured_peaks():
-    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(p):
-        with open(p) as f:
-            return json.load(f), "measured"
-    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
-
-
 def attention_traffic():
     """Per-launch DRAM bytes of the attention kernel from the committed ncu summary."""
-    p = os.path.join(ROOT, "profiles", "attention_batch512_traffic.txt")
+    p = os.path.join(ROOT, "profiles", "attention_warp_batch512_traffic.txt")
     if not os.path.exists(p):
         return None
     vals = {}
@@ -277,8 +271,17 @@ def run_ours(args):
         csz = synth.sizes_lognormal(999, 32)
         cx, ccu = synth.gen_events(999, csz)
         model.calibrate_fp8(torch.from_numpy(cx).to(dev), torch.from_numpy(ccu).to(dev), int(csz.max()))
+    # roofline denominators measured on this device (before anything is timed)
+    from paper_2601_17554_b300 import measure_unit_rates
+    unit_rates = measure_unit_rates(local)
     # attention kernel variant: timed on this batch before the warm-up (no cache)
-    attn_variant = model.autotune(xd, cud, max_n, precision=prec)
+    if args.attn_variant is None:
+        attn_variant = model.autotune(xd, cud, max_n, precision=prec)
+    else:
+        attn_variant = args.attn_variant
+        if prec != "fp32":
+            model.set_option({"bf16": _lib.OPT_ATTN_VARIANT_BF16, "fp16": _lib.OPT_ATTN_VARIANT_FP16,
+                              "fp8": _lib.OPT_ATTN_VARIANT_FP8}[prec], attn_variant)
     model.set_option(_lib.OPT_PROFILE, 1)
     for _ in range(max(args.warmup, 3)):
         step()
@@ -339,19 +342,20 @@ def run_ours(args):
     att = kernel_ms.get("attention", [])
     att_ms = sum(att) / len(att) if att else None
     exps = float(np.sum(sizes.astype(np.float64) ** 2)) * HEADS
-    peaks, peak_src = measured_peaks()
-    # MUFU ex2: 16 lanes per SM per clock (4 per SM sub-partition) x 148 SMs x max SM clock
-    exp_peak = 148 * 16 * peaks.get("sm_max_mhz", 2032.0) * 1e6
+    # peak: the MUFU exp2 rate measured on this device by the library's probe
+    # kernel (independent chains on every SM), taken before the timed region
     roof = None
     if att_ms:
         ach = exps / (att_ms / 1000.0)
-        roof = {"kernel": "k_attention", "bound": "alu", "achieved": ach / 1e9,
+        exp_peak = unit_rates["ex2_per_s"]
+        roof = {"kernel": "k_attention_warp", "bound": "alu", "achieved": ach / 1e9,
                 "peak": exp_peak / 1e9, "unit": "Gexp/s", "frac": ach / exp_peak,
                 "traffic": attention_traffic(),
-                "peak_source": f"derived: 148 SMs x 16 ex2/clk x {peaks.get('sm_max_mhz', 2032.0):.0f} MHz "
-                               f"(clock from MEASURED_PEAKS.json, {peak_src})",
+                "peak_source": "measured: mlpf_measure_unit_rates (ex2.approx.f32 results/s on this GPU, "
+                               "best of 3, timed alone)",
                 "launch_ms": att_ms,
                 "algorithmic_exps_per_launch": exps,
+                "fp32_fma_peak_per_s": unit_rates["ffma_per_s"],
                 "mma_tflops": 4 * float(np.sum(sizes.astype(np.float64) ** 2)) * 64 / (att_ms / 1000.0) / 1e12}
     kernel_avg = {k: sum(v) / len(v) for k, v in kernel_ms.items()}
 

@@ -182,6 +182,15 @@ mlpf_status mlpf_autotune(mlpf_model* m, int32_t precision, const float* x, cons
                           void* stream);
 
 /*
+ * Measured unit rates of `device` (no counterpart in the paper; the roofline
+ * denominators of the attention kernel): results per second of the MUFU base-2
+ * exponential (ex2.approx.f32) and of FP32 FMA, each from a kernel of independent
+ * chains on every SM (best of three timed runs, about 1 ms each).  Either output
+ * pointer (host) may be NULL.  Allocates and frees its own scratch; synchronous.
+ */
+mlpf_status mlpf_measure_unit_rates(int32_t device, double* ex2_per_s, double* ffma_per_s);
+
+/*
  * Names (cap x 32 bytes, or NULL) and activation scales (cap floats, or NULL)
  * of the FP8 calibration; returns the number of activation slots, 0 before
  * calibration, -1 on error.

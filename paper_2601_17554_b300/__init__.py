@@ -22,6 +22,14 @@ def _ptr(t):
     return None if t is None else ctypes.c_void_p(t.data_ptr())
 
 
+def measure_unit_rates(device: int = 0) -> dict:
+    """Measured MUFU exp2 and FP32 FMA rates (results per second) of a device."""
+    L = _lib.load()
+    ex2, ffma = ctypes.c_double(), ctypes.c_double()
+    check(L.mlpf_measure_unit_rates(device, ctypes.byref(ex2), ctypes.byref(ffma)))
+    return {"ex2_per_s": ex2.value, "ffma_per_s": ffma.value}
+
+
 class Model:
     """A loaded MLPF model on one CUDA device (owns weights and workspace)."""
 

@@ -1604,12 +1604,17 @@ __global__ void __launch_bounds__(A32_THREADS, 1)
 // kernel is bound by the softmax; a 128-row tcgen05 MMA would tie the four
 // warps of a warpgroup together at every key tile.  Here each warp owns 32
 // query rows of one head end to end: S comes out of the MMA in registers, the
-// exponentials are packed straight into the A fragments of the PV MMA, and the
-// row sums are one more MMA against a constant block of ones, so the warps
-// meet only at the K/V stage barriers.  Softmax rescaling is lazy: the
+// exponentials (FP32) are packed straight into the A fragments of the PV MMA
+// and summed in FP32 for the row sums, so the warps meet only at the K/V stage
+// barriers.  Softmax rescaling is lazy: the
 // exponent reference of a row is raised (and O, l rescaled) only when a
 // 16-key step exceeds it by more than kStaleMax, so P <= 2^kStaleMax.
 constexpr int AW_THREADS = NH * 4 * 32 + 32;   // 16 consumer warps + a TMA producer warp
+// Softmax order of the warp kernel: the maxima checked before the exponentials
+// (BF16) or the exponentials first, redone on a raised reference (16-bit FP16
+// operands: measured faster).  Row sums by MMA in both.
+template <bool F16>
+constexpr int kAwMode = F16 ? 2 : 0;
 template <int ST>
 struct AwLayout {
     static constexpr uint32_t OFF_K = 2 * AT_QB;
@@ -1618,11 +1623,12 @@ struct AwLayout {
     static constexpr uint32_t SMEM = OFF_BAR + 512 + 1024;
 };
 
-template <bool F16, int ST>
+template <bool F16, int ST, int AM>
 __global__ void __launch_bounds__(AW_THREADS, 1)
     k_attention_warp(const __grid_constant__ CUtensorMap map_q, const __grid_constant__ CUtensorMap map_k,
                      const __grid_constant__ CUtensorMap map_vt, AttnParams p) {
     constexpr int NW = NH * 4;   // consumer warps
+    constexpr bool kSumF32 = AM & 1, kOptimistic = AM & 2;
     using LY = AwLayout<ST>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sm = align1024(smem_raw);
@@ -1699,6 +1705,7 @@ __global__ void __launch_bounds__(AW_THREADS, 1)
         const int mi = lane >> 3;                    // ldmatrix: matrix this lane addresses
         const float c = 0.25f * 1.4426950408889634f;  // log2(e) / sqrt(16)
         const uint32_t ONE2 = F16 ? 0x3C003C00u : 0x3F803F80u;
+        (void)ONE2;
         const uint32_t sQa = smem_u32(sQ), sKa = smem_u32(sK), sVa = smem_u32(sV);
         // per-lane ldmatrix offsets: K rows (keys) + channel chunk; V^T rows (channels) + key chunk
         const int k_row = (lane & 7) + 8 * (mi >> 1), k_chunk = 2 * h + (mi & 1);
@@ -1723,6 +1730,9 @@ __global__ void __launch_bounds__(AW_THREADS, 1)
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&q_empty[qb]);
+            // o: output accumulators; la: row sums (kSumF32: this lane's partial sums
+            // over its key columns [mt][row half], reduced over the quad at the end;
+            // else the ones-MMA accumulator fragment [mt][4]); ref: exponent references
             float o[2][2][4], la[2][4], ref[2][2];
 #pragma unroll
             for (int mt = 0; mt < 2; ++mt) {
@@ -1736,21 +1746,24 @@ __global__ void __launch_bounds__(AW_THREADS, 1)
                 if (!warp_wait(&kv_full[s], (g / ST) & 1, ab, p.status, p.wait_ns)) { ok = false; break; }
                 const int kvalid = it.z - 64 * j;
                 const uint32_t kb = sKa + s * AT_KB, vb = sVa + s * AT_VB;
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    if (16 * q >= kvalid) break;   // warp-uniform
-                    // S = Q K^T for keys 16q .. 16q+15 (two 8-key column tiles)
+                // S = Q K^T for keys 16q .. 16q+15 (two 8-key column tiles)
+                auto qk = [&](int q, float (&dst)[2][2][4]) {
                     uint32_t kf[4];
                     ldsm_x4(kb + sw128_off(16 * q + k_row, k_chunk), kf[0], kf[1], kf[2], kf[3]);
-                    float sc[2][2][4];
 #pragma unroll
                     for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
                         for (int nt = 0; nt < 2; ++nt) {
 #pragma unroll
-                            for (int e = 0; e < 4; ++e) sc[mt][nt][e] = 0.f;
-                            mma16816<F16>(sc[mt][nt], qa[mt], kf[2 * nt], kf[2 * nt + 1]);
+                            for (int e = 0; e < 4; ++e) dst[mt][nt][e] = 0.f;
+                            mma16816<F16>(dst[mt][nt], qa[mt], kf[2 * nt], kf[2 * nt + 1]);
                         }
+                };
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (16 * q >= kvalid) break;   // warp-uniform
+                    float sc[2][2][4];
+                    qk(q, sc);
                     if (16 * q + 16 > kvalid) {   // ragged end of the event
 #pragma unroll
                         for (int mt = 0; mt < 2; ++mt)
@@ -1760,9 +1773,37 @@ __global__ void __launch_bounds__(AW_THREADS, 1)
                                 for (int e = 0; e < 4; ++e)
                                     if (16 * q + 8 * nt + 2 * tq + (e & 1) >= kvalid) sc[mt][nt][e] = -INFINITY;
                     }
-                    // local row maxima (rows gq, gq + 8 of each tile) against the references
+                    // P = 2^(S c - ref) as the A fragments of PV (16 keys = one K-step).
+                    // kSumF32: row sums from the FP32 exponentials (else an MMA of P
+                    // against ones); kOptimistic: exponentials first, against the
+                    // current references, redone if a reference is raised (else the
+                    // maxima are checked first).
+                    uint32_t pa[2][4];
+                    float ls[2][2];
+                    auto exps = [&]() {
+#pragma unroll
+                        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                            for (int hr = 0; hr < 2; ++hr) {
+                                const float2 nr = make_float2(-ref[mt][hr], -ref[mt][hr]);
+                                const float2 cc = make_float2(c, c);
+                                const float2 x0 = __ffma2_rn(make_float2(sc[mt][0][2 * hr], sc[mt][0][2 * hr + 1]), cc, nr);
+                                const float2 x1 = __ffma2_rn(make_float2(sc[mt][1][2 * hr], sc[mt][1][2 * hr + 1]), cc, nr);
+                                if constexpr (kSumF32) {
+                                    const float e0 = ex2_approx(x0.x), e1 = ex2_approx(x0.y);
+                                    const float e2 = ex2_approx(x1.x), e3 = ex2_approx(x1.y);
+                                    ls[mt][hr] = (e0 + e1) + (e2 + e3);
+                                    pa[mt][hr] = pack2<F16>(e0, e1);
+                                    pa[mt][2 + hr] = pack2<F16>(e2, e3);
+                                } else {
+                                    pa[mt][hr] = exp2_pair<F16>(x0.x, x0.y);
+                                    pa[mt][2 + hr] = exp2_pair<F16>(x1.x, x1.y);
+                                }
+                            }
+                    };
                     float lm[2][2];
                     bool raise = false;
+                    if constexpr (kOptimistic) exps();
 #pragma unroll
                     for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
@@ -1771,7 +1812,8 @@ __global__ void __launch_bounds__(AW_THREADS, 1)
                                                sc[mt][1][2 * hr + 1]);
                             raise |= lm[mt][hr] * c > ref[mt][hr] + kStaleMax;
                         }
-                    if (__any_sync(0xffffffffu, raise)) {
+                    const bool raised = __any_sync(0xffffffffu, raise);
+                    if (raised) {
                         // new reference: the running row max (over the quad), then rescale
 #pragma unroll
                         for (int mt = 0; mt < 2; ++mt)
@@ -1787,22 +1829,19 @@ __global__ void __launch_bounds__(AW_THREADS, 1)
                                 for (int e = 0; e < 2; ++e) {
                                     o[mt][0][2 * hr + e] *= a;
                                     o[mt][1][2 * hr + e] *= a;
-                                    la[mt][2 * hr + e] *= a;
+                                    if constexpr (!kSumF32) la[mt][2 * hr + e] *= a;
                                 }
+                                if constexpr (kSumF32) la[mt][hr] *= a;
                             }
                     }
-                    // P = 2^(S c - ref) as the A fragments of PV (16 keys = one K-step)
-                    uint32_t pa[2][4];
+                    if (!kOptimistic || raised) exps();
+                    if constexpr (kSumF32) {
 #pragma unroll
-                    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-                        for (int nt = 0; nt < 2; ++nt)
-#pragma unroll
-                            for (int hr = 0; hr < 2; ++hr) {
-                                float x0, x1;
-                                ffma2_bcast(x0, x1, sc[mt][nt][2 * hr], sc[mt][nt][2 * hr + 1], c, -ref[mt][hr]);
-                                pa[mt][2 * nt + hr] = exp2_pair<F16>(x0, x1);
-                            }
+                        for (int mt = 0; mt < 2; ++mt) {
+                            la[mt][0] += ls[mt][0];
+                            la[mt][1] += ls[mt][1];
+                        }
+                    }
                     // V fragments: channels 0-7 / 8-15 of the head, keys 16q .. 16q+15
                     uint32_t vf[4];
                     ldsm_x4(vb + sw128_off(v_row, 2 * q + v_sub), vf[0], vf[1], vf[2], vf[3]);
@@ -1810,7 +1849,7 @@ __global__ void __launch_bounds__(AW_THREADS, 1)
                     for (int mt = 0; mt < 2; ++mt) {
                         mma16816<F16>(o[mt][0], pa[mt], vf[0], vf[1]);
                         mma16816<F16>(o[mt][1], pa[mt], vf[2], vf[3]);
-                        mma16816<F16>(la[mt], pa[mt], ONE2, ONE2);   // row sums of the rounded P
+                        if constexpr (!kSumF32) mma16816<F16>(la[mt], pa[mt], ONE2, ONE2);
                     }
                 }
                 __syncwarp();
@@ -1823,9 +1862,17 @@ __global__ void __launch_bounds__(AW_THREADS, 1)
             for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
                 for (int hr = 0; hr < 2; ++hr) {
+                    float l;
+                    if constexpr (kSumF32) {
+                        l = la[mt][hr];
+                        l += __shfl_xor_sync(0xffffffffu, l, 1);
+                        l += __shfl_xor_sync(0xffffffffu, l, 2);
+                    } else {
+                        l = la[mt][2 * hr];
+                    }
                     const int r = rb * 32 + mt * 16 + gq + 8 * hr;
                     if (r < nrows) {
-                        const float inv = 1.0f / la[mt][2 * hr];
+                        const float inv = 1.0f / l;
                         uint32_t* dst = (uint32_t*)(p.out + (size_t)(qrow0 + r) * D + h * 16 + 2 * tq);
                         dst[0] = pack2<F16>(o[mt][0][2 * hr] * inv, o[mt][0][2 * hr + 1] * inv);
                         dst[4] = pack2<F16>(o[mt][1][2 * hr] * inv, o[mt][1][2 * hr + 1] * inv);
@@ -1940,8 +1987,8 @@ std::string check_occupancy() {
                           occupancy(k_attention32<kOutF16<FMT>, 4>, A32_THREADS, At32Layout<4>::SMEM),
                           occupancy(k_attention<kOutF16<FMT>, 1, 6>, at_threads<1>(), AtLayout<6>::SMEM),
                           occupancy(k_attention32<kOutF16<FMT>, 6>, A32_THREADS, At32Layout<6>::SMEM),
-                          occupancy(k_attention_warp<kOutF16<FMT>, 4>, AW_THREADS, AwLayout<4>::SMEM),
-                          occupancy(k_attention_warp<kOutF16<FMT>, 8>, AW_THREADS, AwLayout<8>::SMEM)};
+                          occupancy(k_attention_warp<kOutF16<FMT>, 4, kAwMode<kOutF16<FMT>>>, AW_THREADS, AwLayout<4>::SMEM),
+                          occupancy(k_attention_warp<kOutF16<FMT>, 8, kAwMode<kOutF16<FMT>>>, AW_THREADS, AwLayout<8>::SMEM)};
     const int o[6] = {*std::min_element(o_att, o_att + 9),
                       occupancy(k_post<0, FMT>, PT_THREADS, post_smem(0, FMT)),
                       occupancy(k_post<1, FMT>, PT_THREADS, post_smem(1, FMT)),
@@ -1970,8 +2017,8 @@ void set_attrs() {
     cudaFuncSetAttribute(k_attention32<kOutF16<FMT>, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, At32Layout<4>::SMEM);
     cudaFuncSetAttribute(k_attention<kOutF16<FMT>, 1, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, AtLayout<6>::SMEM);
     cudaFuncSetAttribute(k_attention32<kOutF16<FMT>, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, At32Layout<6>::SMEM);
-    cudaFuncSetAttribute(k_attention_warp<kOutF16<FMT>, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, AwLayout<4>::SMEM);
-    cudaFuncSetAttribute(k_attention_warp<kOutF16<FMT>, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, AwLayout<8>::SMEM);
+    cudaFuncSetAttribute(k_attention_warp<kOutF16<FMT>, 4, kAwMode<kOutF16<FMT>>>, cudaFuncAttributeMaxDynamicSharedMemorySize, AwLayout<4>::SMEM);
+    cudaFuncSetAttribute(k_attention_warp<kOutF16<FMT>, 8, kAwMode<kOutF16<FMT>>>, cudaFuncAttributeMaxDynamicSharedMemorySize, AwLayout<8>::SMEM);
 }
 
 }  // namespace
@@ -2161,8 +2208,8 @@ static int64_t run_tc(Model& m, const float* x, const int32_t* cu, int n_events,
             case 4: k_attention32<AF, 4><<<g, A32_THREADS, At32Layout<4>::SMEM, st>>>(w.map_q, w.map_k, w.map_vt, ap); break;
             case 5: k_attention<AF, 1, 6><<<g, at_threads<1>(), AtLayout<6>::SMEM, st>>>(w.map_q, w.map_k, w.map_vt, ap); break;
             case 6: k_attention32<AF, 6><<<g, A32_THREADS, At32Layout<6>::SMEM, st>>>(w.map_q, w.map_k, w.map_vt, ap); break;
-            case 7: k_attention_warp<AF, 4><<<g, AW_THREADS, AwLayout<4>::SMEM, st>>>(w.map_q, w.map_k, w.map_vt, ap); break;
-            case 8: k_attention_warp<AF, 8><<<g, AW_THREADS, AwLayout<8>::SMEM, st>>>(w.map_q, w.map_k, w.map_vt, ap); break;
+            case 7: k_attention_warp<AF, 4, kAwMode<AF>><<<g, AW_THREADS, AwLayout<4>::SMEM, st>>>(w.map_q, w.map_k, w.map_vt, ap); break;
+            case 8: k_attention_warp<AF, 8, kAwMode<AF>><<<g, AW_THREADS, AwLayout<8>::SMEM, st>>>(w.map_q, w.map_k, w.map_vt, ap); break;
             default: k_attention<AF, 1, 4><<<g, at_threads<1>(), AtLayout<4>::SMEM, st>>>(w.map_q, w.map_k, w.map_vt, ap); break;
         }
         prof_end(m, st);
