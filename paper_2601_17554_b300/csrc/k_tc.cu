@@ -1610,11 +1610,14 @@ __global__ void __launch_bounds__(A32_THREADS, 1)
 // exponent reference of a row is raised (and O, l rescaled) only when a
 // 16-key step exceeds it by more than kStaleMax, so P <= 2^kStaleMax.
 constexpr int AW_THREADS = NH * 4 * 32 + 32;   // 16 consumer warps + a TMA producer warp
-// Softmax order of the warp kernel: the maxima checked before the exponentials
-// (BF16) or the exponentials first, redone on a raised reference (16-bit FP16
-// operands: measured faster).  Row sums by MMA in both.
+// Mode bits of the warp kernel (each measured on the 512-event batch):
+//   1 row sums from FP32 adds instead of the ones-MMA (slower: off)
+//   2 exponentials before the maxima check, redone on a raised reference
+//     (faster with FP16 operands only)
+//   4 V fragments loaded at the start of a step, maxima checked against
+//     raw-score thresholds (5-7 % faster: on)
 template <bool F16>
-constexpr int kAwMode = F16 ? 2 : 0;
+constexpr int kAwMode = F16 ? 6 : 4;
 template <int ST>
 struct AwLayout {
     static constexpr uint32_t OFF_K = 2 * AT_QB;
@@ -1628,7 +1631,7 @@ __global__ void __launch_bounds__(AW_THREADS, 1)
     k_attention_warp(const __grid_constant__ CUtensorMap map_q, const __grid_constant__ CUtensorMap map_k,
                      const __grid_constant__ CUtensorMap map_vt, AttnParams p) {
     constexpr int NW = NH * 4;   // consumer warps
-    constexpr bool kSumF32 = AM & 1, kOptimistic = AM & 2;
+    constexpr bool kSumF32 = AM & 1, kOptimistic = AM & 2, kHoist = AM & 4;
     using LY = AwLayout<ST>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sm = align1024(smem_raw);
@@ -1710,6 +1713,11 @@ __global__ void __launch_bounds__(AW_THREADS, 1)
         // per-lane ldmatrix offsets: K rows (keys) + channel chunk; V^T rows (channels) + key chunk
         const int k_row = (lane & 7) + 8 * (mi >> 1), k_chunk = 2 * h + (mi & 1);
         const int v_row = h * 16 + (lane & 7) + 8 * (mi >> 1), v_sub = mi & 1;
+        const uint32_t koff = sw128_off(k_row, k_chunk);   // K fragment offset of step 0
+        int voff[4];   // this lane's V^T fragment offsets of the four 16-key steps
+#pragma unroll
+        for (int q = 0; q < 4; ++q) voff[q] = (int)sw128_off(v_row, 2 * q + v_sub);
+        (void)voff;
         int q_it = 0;
         uint32_t g = 0;
         bool ok = true;
@@ -1733,23 +1741,26 @@ __global__ void __launch_bounds__(AW_THREADS, 1)
             // o: output accumulators; la: row sums (kSumF32: this lane's partial sums
             // over its key columns [mt][row half], reduced over the quad at the end;
             // else the ones-MMA accumulator fragment [mt][4]); ref: exponent references
-            float o[2][2][4], la[2][4], ref[2][2];
+            // thr (kHoist): raw-score level above which a row's reference is raised,
+            // (ref + kStaleMax) / c, so the check needs no multiply
+            float o[2][2][4], la[2][4], ref[2][2], thr[2][2];
 #pragma unroll
             for (int mt = 0; mt < 2; ++mt) {
 #pragma unroll
                 for (int e = 0; e < 4; ++e) { o[mt][0][e] = 0.f; o[mt][1][e] = 0.f; la[mt][e] = 0.f; }
-                ref[mt][0] = -INFINITY;
-                ref[mt][1] = -INFINITY;
+                ref[mt][0] = ref[mt][1] = -INFINITY;
+                thr[mt][0] = thr[mt][1] = -INFINITY;
             }
             for (int j = 0; j < nk; ++j, ++g) {
                 const uint32_t s = g % ST;
                 if (!warp_wait(&kv_full[s], (g / ST) & 1, ab, p.status, p.wait_ns)) { ok = false; break; }
                 const int kvalid = it.z - 64 * j;
                 const uint32_t kb = sKa + s * AT_KB, vb = sVa + s * AT_VB;
-                // S = Q K^T for keys 16q .. 16q+15 (two 8-key column tiles)
+                // S = Q K^T for keys 16q .. 16q+15 (two 8-key column tiles); the swizzle
+                // of rows 16q + k_row does not depend on q (16q is a multiple of 8)
                 auto qk = [&](int q, float (&dst)[2][2][4]) {
                     uint32_t kf[4];
-                    ldsm_x4(kb + sw128_off(16 * q + k_row, k_chunk), kf[0], kf[1], kf[2], kf[3]);
+                    ldsm_x4(kb + koff + 2048u * q, kf[0], kf[1], kf[2], kf[3]);
 #pragma unroll
                     for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
@@ -1763,6 +1774,9 @@ __global__ void __launch_bounds__(AW_THREADS, 1)
                 for (int q = 0; q < 4; ++q) {
                     if (16 * q >= kvalid) break;   // warp-uniform
                     float sc[2][2][4];
+                    uint32_t vf[4];
+                    if constexpr (kHoist)   // V fragments first: off the softmax's critical path
+                        ldsm_x4(vb + (uint32_t)voff[q], vf[0], vf[1], vf[2], vf[3]);
                     qk(q, sc);
                     if (16 * q + 16 > kvalid) {   // ragged end of the event
 #pragma unroll
@@ -1810,7 +1824,8 @@ __global__ void __launch_bounds__(AW_THREADS, 1)
                         for (int hr = 0; hr < 2; ++hr) {
                             lm[mt][hr] = max3f(fmaxf(sc[mt][0][2 * hr], sc[mt][0][2 * hr + 1]), sc[mt][1][2 * hr],
                                                sc[mt][1][2 * hr + 1]);
-                            raise |= lm[mt][hr] * c > ref[mt][hr] + kStaleMax;
+                            if constexpr (kHoist) raise |= lm[mt][hr] > thr[mt][hr];
+                            else raise |= lm[mt][hr] * c > ref[mt][hr] + kStaleMax;
                         }
                     const bool raised = __any_sync(0xffffffffu, raise);
                     if (raised) {
@@ -1825,6 +1840,7 @@ __global__ void __launch_bounds__(AW_THREADS, 1)
                                 const float rn = fmaxf(ref[mt][hr], mx * c);
                                 const float a = ex2_approx(ref[mt][hr] - rn);
                                 ref[mt][hr] = rn;
+                                thr[mt][hr] = (rn + kStaleMax) * (1.f / c);   // raw-score threshold
 #pragma unroll
                                 for (int e = 0; e < 2; ++e) {
                                     o[mt][0][2 * hr + e] *= a;
@@ -1843,8 +1859,7 @@ __global__ void __launch_bounds__(AW_THREADS, 1)
                         }
                     }
                     // V fragments: channels 0-7 / 8-15 of the head, keys 16q .. 16q+15
-                    uint32_t vf[4];
-                    ldsm_x4(vb + sw128_off(v_row, 2 * q + v_sub), vf[0], vf[1], vf[2], vf[3]);
+                    if constexpr (!kHoist) ldsm_x4(vb + sw128_off(v_row, 2 * q + v_sub), vf[0], vf[1], vf[2], vf[3]);
 #pragma unroll
                     for (int mt = 0; mt < 2; ++mt) {
                         mma16816<F16>(o[mt][0], pa[mt], vf[0], vf[1]);
