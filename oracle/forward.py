@@ -136,6 +136,27 @@ def embed(x, W, act):
     return linear(act(linear(x, W["emb.w1"], W["emb.b1"])), W["emb.w2"], W["emb.b2"])
 
 
+def is_track(x):
+    """Element types embedded by the track FFN: track, GSF track, brem (x[:, 0:8]
+    is the type one-hot: track, ECAL, HCAL, HF-EM, HF-HAD, GSF track, brem,
+    supercluster).
+
+    reading: "tracks and clusters are each embedded" (Sec. 5.3) = one FFN for the
+    three track-like types and one for the five calorimeter-cluster types.
+    """
+    x = np.asarray(x, F64)
+    return (x[:, 0] + x[:, 5] + x[:, 6]) > 0.5
+
+
+def embed_per_type(x, W, act):
+    """Per-type embedding (Sec. 5.3 as printed): a two-layer FFN 42 -> d -> d for
+    track-like elements (emb.trk) and another for clusters (emb.clu)."""
+    x = np.asarray(x, F64)
+    e_trk = linear(act(linear(x, W["emb.trk.w1"], W["emb.trk.b1"])), W["emb.trk.w2"], W["emb.trk.b2"])
+    e_clu = linear(act(linear(x, W["emb.clu.w1"], W["emb.clu.b1"])), W["emb.clu.w2"], W["emb.clu.b2"])
+    return np.where(is_track(x)[:, None], e_trk, e_clu)
+
+
 def reg_embed(x, h_pid, W, act):
     """Input of the regression encoder: FFN over concat(x, h_pid), (42+d) -> d -> d.
 
@@ -173,11 +194,20 @@ def forward_event(W, cfg, x, key_mask=None, keep_hidden=False):
     """
     act = activation(cfg.act)
     x = np.asarray(x, F64)
-    e = embed(x, W, act)
-    h_pid = encoder_stack(e, W, "pid", cfg.l_pid, cfg.heads, act, key_mask)
-    r = reg_embed(x, h_pid, W, act)
-    h_reg = encoder_stack(r, W, "reg", cfg.l_reg, cfg.heads, act, key_mask)
-    logits = ffn_head(h_pid, W, "cls", act)
+    if getattr(cfg, "arch", 0) == 1:
+        # Sec. 5.3 as printed: per-type embedding; two parallel encoders on it;
+        # binary and multi-class PID heads on the classification encoder
+        e = embed_per_type(x, W, act)
+        h_pid = encoder_stack(e, W, "pid", cfg.l_pid, cfg.heads, act, key_mask)
+        h_reg = encoder_stack(e, W, "reg", cfg.l_reg, cfg.heads, act, key_mask)
+        logits = np.concatenate([ffn_head(h_pid, W, "bin", act), ffn_head(h_pid, W, "pid", act)],
+                                axis=1)
+    else:
+        e = embed(x, W, act)
+        h_pid = encoder_stack(e, W, "pid", cfg.l_pid, cfg.heads, act, key_mask)
+        r = reg_embed(x, h_pid, W, act)
+        h_reg = encoder_stack(r, W, "reg", cfg.l_reg, cfg.heads, act, key_mask)
+        logits = ffn_head(h_pid, W, "cls", act)
     raw = np.concatenate([ffn_head(h_reg, W, "pt", act), ffn_head(h_reg, W, "eta", act),
                           ffn_head(h_reg, W, "phi", act), ffn_head(h_reg, W, "e", act)],
                          axis=1)
@@ -186,16 +216,23 @@ def forward_event(W, cfg, x, key_mask=None, keep_hidden=False):
     return logits, raw
 
 
-def decode(x, logits, raw):
+def decode(x, logits, raw, arch=0):
     """Candidates from head outputs (Sec. 5.3, Eq. 2 inverted).
 
-    class = argmax of the scores, lowest index on ties (0 = no particle);
+    arch 0: class = argmax of the 6 scores, lowest index on ties (0 = no
+    particle).  arch 1 (Sec. 5.3 as printed): a particle where the binary score
+    is above 0.5, i.e. its logit (column 0) > 0, with PID = 1 + argmax of the 5
+    PID scores (columns 1-5, lowest index on ties); otherwise class 0.
     pT = pT_elem * exp(pT'), E = E_elem * exp(E'), with log pT_elem = x[:, 8]
     and log E_elem = x[:, 9]; eta, sin phi, cos phi as predicted.
     """
     x = np.asarray(x, F64)
     raw = np.asarray(raw, F64)
-    cls = np.argmax(np.asarray(logits, F64), axis=1).astype(np.int32)
+    lg = np.asarray(logits, F64)
+    if arch == 1:
+        cls = np.where(lg[:, 0] > 0, 1 + np.argmax(lg[:, 1:], axis=1), 0).astype(np.int32)
+    else:
+        cls = np.argmax(lg, axis=1).astype(np.int32)
     reg = np.empty_like(raw)
     reg[:, 0] = np.exp(x[:, 8] + raw[:, 0])
     reg[:, 1] = raw[:, 1]
@@ -260,7 +297,7 @@ def forward(W, cfg, x, cu_seqlens, events=None, keep_hidden=False):
     reg = np.full((total, cfg.n_reg), np.nan)
     done = ~np.isnan(logits[:, 0])
     if done.any():
-        c, r = decode(x[done], logits[done], raw[done])
+        c, r = decode(x[done], logits[done], raw[done], getattr(cfg, "arch", 0))
         cls[done] = c
         reg[done] = r
     sums = np.full((n, 3), np.nan)

@@ -169,16 +169,27 @@ class ModelConfig:
     in_dim: int = IN_DIM
     n_cls: int = N_CLS
     n_reg: int = N_REG
+    # ARCH_SEQ: one shared embedding, the regression stack reads concat(x, h_pid),
+    # one 6-class head.  ARCH_PAPER (Sec. 5.3 as printed): track and cluster
+    # embeddings, two parallel stacks on the same embedding, binary + 5-class PID
+    # heads (class-score columns: [binary logit, 5 PID logits]).
+    arch: int = 0
 
     @property
     def dh(self) -> int:
         return self.d // self.heads
 
 
+ARCH_SEQ, ARCH_PAPER = 0, 1
+
 # The architecture of the 1-event / 64-event / 512-event workloads.
 SMALL = ModelConfig(d=64, heads=4, ffn=256, l_pid=1, l_reg=1)
 # The full-size architecture (d=256, 8 heads of 32, FFN 1024, 3+3 layers).
 FULL = ModelConfig(d=256, heads=8, ffn=1024, l_pid=3, l_reg=3)
+
+# The architecture as Sec. 5.3 prints it: d=256, 16 heads of 16, ReLU, 3+3 blocks
+# (FFN width unstated: 4 d), per-type embedding, parallel encoders, binary + PID heads.
+PAPER = ModelConfig(d=256, heads=16, ffn=1024, l_pid=3, l_reg=3, act=ACT_RELU, arch=ARCH_PAPER)
 
 # Output width of each regression head, in output-column order.
 REG_HEADS = (("pt", 1), ("eta", 1), ("phi", 2), ("e", 1))
@@ -191,8 +202,16 @@ def tensor_specs(cfg: ModelConfig):
     'beta' LN shift.  The order fixes the random stream index of each tensor.
     """
     d, f = cfg.d, cfg.ffn
-    specs = [("emb.w1", (d, cfg.in_dim), "w"), ("emb.b1", (d,), "b"),
-             ("emb.w2", (d, d), "w"), ("emb.b2", (d,), "b")]
+    paper = cfg.arch == ARCH_PAPER
+
+    def mlp(prefix, n_in, n_out):
+        return [(prefix + ".w1", (d, n_in), "w"), (prefix + ".b1", (d,), "b"),
+                (prefix + ".w2", (n_out, d), "w"), (prefix + ".b2", (n_out,), "b")]
+
+    if paper:
+        specs = mlp("emb.trk", cfg.in_dim, d) + mlp("emb.clu", cfg.in_dim, d)
+    else:
+        specs = mlp("emb", cfg.in_dim, d)
 
     def stack(prefix, n):
         out = []
@@ -210,14 +229,15 @@ def tensor_specs(cfg: ModelConfig):
         return out
 
     specs += stack("pid", cfg.l_pid)
-    specs += [("remb.w1", (d, cfg.in_dim + d), "w"), ("remb.b1", (d,), "b"),
-              ("remb.w2", (d, d), "w"), ("remb.b2", (d,), "b")]
+    if not paper:
+        specs += mlp("remb", cfg.in_dim + d, d)
     specs += stack("reg", cfg.l_reg)
-    specs += [("head.cls.w1", (d, d), "w"), ("head.cls.b1", (d,), "b"),
-              ("head.cls.w2", (cfg.n_cls, d), "w"), ("head.cls.b2", (cfg.n_cls,), "b")]
+    if paper:
+        specs += mlp("head.bin", d, 1) + mlp("head.pid", d, cfg.n_cls - 1)
+    else:
+        specs += mlp("head.cls", d, cfg.n_cls)
     for name, k in REG_HEADS:
-        specs += [(f"head.{name}.w1", (d, d), "w"), (f"head.{name}.b1", (d,), "b"),
-                  (f"head.{name}.w2", (k, d), "w"), (f"head.{name}.b2", (k,), "b")]
+        specs += mlp(f"head.{name}", d, k)
     return specs
 
 
@@ -244,8 +264,10 @@ def make_weights(cfg: ModelConfig, seed: int, perturbed: bool = False,
             v = (0.2 * u - 0.1) if perturbed else 0.0 * u
         w[name] = v.reshape(shape).astype(np.float32)
     if cls_scale != 1.0:
-        w["head.cls.w2"] = (w["head.cls.w2"] * np.float32(cls_scale)).astype(np.float32)
-        w["head.cls.b2"] = (w["head.cls.b2"] * np.float32(cls_scale)).astype(np.float32)
+        last = ("head.pid",) if cfg.arch == ARCH_PAPER else ("head.cls",)
+        for h in last:
+            w[h + ".w2"] = (w[h + ".w2"] * np.float32(cls_scale)).astype(np.float32)
+            w[h + ".b2"] = (w[h + ".b2"] * np.float32(cls_scale)).astype(np.float32)
     return w
 
 
@@ -263,14 +285,20 @@ def pack_blob(cfg: ModelConfig, weights) -> bytes:
 
     Layout (little endian):
       char magic[4] = "MLPF"; int32 version;
-      int32 in_dim, d, heads, ffn, l_pid, l_reg, n_cls, n_reg, act, n_tensors;
+      int32 in_dim, d, heads, ffn, l_pid, l_reg, n_cls, n_reg, act,
+            [version 2 only: arch,] n_tensors;
       n_tensors records: char name[48]; int32 ndim; int32 shape[2];
                          float32 data[prod(shape)]
+    Version 1 (arch 0 implied) is written for ARCH_SEQ, version 2 otherwise.
     """
     specs = tensor_specs(cfg)
-    out = [BLOB_MAGIC, struct.pack("<i", BLOB_VERSION),
-           struct.pack("<10i", cfg.in_dim, cfg.d, cfg.heads, cfg.ffn, cfg.l_pid,
-                       cfg.l_reg, cfg.n_cls, cfg.n_reg, cfg.act, len(specs))]
+    hdr = [cfg.in_dim, cfg.d, cfg.heads, cfg.ffn, cfg.l_pid, cfg.l_reg, cfg.n_cls, cfg.n_reg,
+           cfg.act]
+    version = BLOB_VERSION if cfg.arch == ARCH_SEQ else 2
+    if version == 2:
+        hdr.append(cfg.arch)
+    hdr.append(len(specs))
+    out = [BLOB_MAGIC, struct.pack("<i", version), struct.pack(f"<{len(hdr)}i", *hdr)]
     for name, shape, _ in specs:
         a = np.ascontiguousarray(weights[name], dtype=np.float32)
         assert a.shape == tuple(shape), (name, a.shape, shape)
@@ -297,4 +325,6 @@ def workload(name: str):
         return SMALL, 0, 103, sizes_uniform(103, 64)
     if name == "batch512":          # 512 events LogNormal(2500, 0.5) in [100, 12000]
         return SMALL, 0, 104, sizes_lognormal(104, 512)
+    if name == "paper8":            # 8 events U{1000..6000}, the architecture as printed
+        return PAPER, 2, 105, sizes_uniform(105, 8)
     raise KeyError(name)

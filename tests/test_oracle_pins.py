@@ -139,17 +139,29 @@ def torch_reference(W, cfg, x):
             z = z + mlp(ln(z, p + "ln2"), p + "ffn.w1", p + "ffn.b1", p + "ffn.w2", p + "ffn.b2")
         return ln(z, prefix + ".lnf")
 
-    h_pid = stack(mlp(x, "emb.w1", "emb.b1", "emb.w2", "emb.b2"), "pid", cfg.l_pid)
-    h_reg = stack(mlp(torch.cat([x, h_pid], 1), "remb.w1", "remb.b1", "remb.w2", "remb.b2"),
-                  "reg", cfg.l_reg)
     head = lambda h, n: mlp(h, f"head.{n}.w1", f"head.{n}.b1", f"head.{n}.w2", f"head.{n}.b2")
-    logits = head(h_pid, "cls")
+    if cfg.arch == synth.ARCH_PAPER:
+        # track-like types (track, GSF track, brem) take the track embedding
+        trk = (x[:, synth.TRACK_TYPES].sum(1) > 0.5)[:, None]
+        e = torch.where(trk, mlp(x, "emb.trk.w1", "emb.trk.b1", "emb.trk.w2", "emb.trk.b2"),
+                        mlp(x, "emb.clu.w1", "emb.clu.b1", "emb.clu.w2", "emb.clu.b2"))
+        h_pid, h_reg = stack(e, "pid", cfg.l_pid), stack(e, "reg", cfg.l_reg)
+        logits = torch.cat([head(h_pid, "bin"), head(h_pid, "pid")], 1)
+    else:
+        h_pid = stack(mlp(x, "emb.w1", "emb.b1", "emb.w2", "emb.b2"), "pid", cfg.l_pid)
+        h_reg = stack(mlp(torch.cat([x, h_pid], 1), "remb.w1", "remb.b1", "remb.w2", "remb.b2"),
+                      "reg", cfg.l_reg)
+        logits = head(h_pid, "cls")
     raw = torch.cat([head(h_reg, n) for n, _ in synth.REG_HEADS], 1)
     return logits.numpy(), raw.numpy()
 
 
+PAPER_SMALL = synth.ModelConfig(d=32, heads=2, ffn=64, l_pid=2, l_reg=1, act=1, arch=synth.ARCH_PAPER)
+
+
 @pytest.mark.parametrize("cfg", [synth.SMALL, synth.FULL,
-                                 synth.ModelConfig(d=32, heads=2, ffn=64, l_pid=2, l_reg=1, act=1)])
+                                 synth.ModelConfig(d=32, heads=2, ffn=64, l_pid=2, l_reg=1, act=1),
+                                 PAPER_SMALL, synth.PAPER])
 def test_forward_matches_torch_functional(cfg):
     W = synth.make_weights(cfg, seed=5, perturbed=True)
     x, cu = synth.gen_events(11, [23])
@@ -319,3 +331,71 @@ def test_raw_from_decoded_inverts_decode():
     raw = np.random.default_rng(4).normal(size=(6, 5))
     _, reg = oracle.decode(x, np.zeros((6, 6)), raw)
     np.testing.assert_allclose(oracle.raw_from_decoded(x, reg), raw, rtol=1e-12, atol=1e-12)
+
+
+# ------------------------------------------ the architecture as printed (Sec. 5.3)
+
+def test_paper_arch_parallel_encoders_are_independent():
+    """Two parallel encoders on one embedding: the regression outputs do not
+    depend on the classification encoder or its heads, and the class scores do
+    not depend on the regression encoder (the sequential reading couples them)."""
+    cfg = PAPER_SMALL
+    W = synth.make_weights(cfg, seed=7, perturbed=True)
+    x, _ = synth.gen_events(14, [29])
+    lo, raw = oracle.forward_event(W, cfg, x)
+    rng = np.random.default_rng(3)
+    Wc = {k: (v + rng.normal(size=v.shape).astype(np.float32) if k.startswith(("pid.", "head.bin", "head.pid"))
+              else v) for k, v in W.items()}
+    lo_c, raw_c = oracle.forward_event(Wc, cfg, x)
+    np.testing.assert_array_equal(raw_c, raw)
+    assert np.abs(lo_c - lo).max() > 1e-3
+    Wr = {k: (v + rng.normal(size=v.shape).astype(np.float32) if k.startswith("reg.") else v)
+          for k, v in W.items()}
+    lo_r, raw_r = oracle.forward_event(Wr, cfg, x)
+    np.testing.assert_array_equal(lo_r, lo)
+    assert np.abs(raw_r - raw).max() > 1e-3
+
+
+def test_paper_arch_per_type_embedding():
+    """Track-like elements (track, GSF track, brem) use emb.trk, clusters emb.clu:
+    an event of tracks only ignores the cluster embedding's weights."""
+    cfg = PAPER_SMALL
+    W = synth.make_weights(cfg, seed=8, perturbed=True)
+    x, _ = synth.gen_events(15, [200])
+    assert oracle.is_track(x).any() and (~oracle.is_track(x)).any()
+    trk = x[oracle.is_track(x)][:12]
+    assert set(np.argmax(trk[:, :8], 1).tolist()) <= {0, 5, 6}
+    lo, raw = oracle.forward_event(W, cfg, trk)
+    W2 = dict(W)
+    for k in ("emb.clu.w1", "emb.clu.b1", "emb.clu.w2", "emb.clu.b2"):
+        W2[k] = W[k] * 3 + 1
+    lo2, raw2 = oracle.forward_event(W2, cfg, trk)
+    np.testing.assert_array_equal(lo2, lo)
+    np.testing.assert_array_equal(raw2, raw)
+    # and the per-element embedding is the selected FFN's output
+    act = oracle.relu
+    e = oracle.embed_per_type(x, W, act)
+    i_t, i_c = np.flatnonzero(oracle.is_track(x))[0], np.flatnonzero(~oracle.is_track(x))[0]
+    ft = oracle.linear(act(oracle.linear(x[i_t:i_t + 1], W["emb.trk.w1"], W["emb.trk.b1"])),
+                       W["emb.trk.w2"], W["emb.trk.b2"])
+    fc = oracle.linear(act(oracle.linear(x[i_c:i_c + 1], W["emb.clu.w1"], W["emb.clu.b1"])),
+                       W["emb.clu.w2"], W["emb.clu.b2"])
+    np.testing.assert_array_equal(e[i_t], ft[0])
+    np.testing.assert_array_equal(e[i_c], fc[0])
+
+
+def test_paper_arch_decode_hand_values():
+    """Binary score above 0.5 (logit > 0) selects a particle with PID = 1 + argmax
+    of the five PID scores (Sec. 5.3); logit <= 0 gives class 0 whatever the PID
+    scores; equal PID scores take the lowest index."""
+    x = np.zeros((5, 42))
+    raw = np.zeros((5, 5))
+    logits = np.array([[0.3, 0.0, 2.0, 1.0, 0.0, 0.0],     # particle, PID 2 -> class 2
+                       [-0.1, 9.0, 0.0, 0.0, 0.0, 0.0],    # no particle
+                       [0.0, 0.0, 0.0, 0.0, 0.0, 5.0],     # logit 0 = score 0.5: not above
+                       [1e-9, 1.0, 1.0, 0.5, 0.5, 0.5],    # tie -> lowest PID index -> class 1
+                       [4.0, -3.0, -2.0, -1.0, -4.0, -0.5]])  # PID 5 -> class 5
+    cls, _ = oracle.decode(x, logits, raw, arch=1)
+    assert cls.tolist() == [2, 0, 0, 1, 5]
+    cls0, _ = oracle.decode(x, logits, raw, arch=0)
+    assert cls0.tolist() == [2, 0, 5, 1, 0]
