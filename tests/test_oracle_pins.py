@@ -380,8 +380,8 @@ def test_paper_arch_per_type_embedding():
                        W["emb.trk.w2"], W["emb.trk.b2"])
     fc = oracle.linear(act(oracle.linear(x[i_c:i_c + 1], W["emb.clu.w1"], W["emb.clu.b1"])),
                        W["emb.clu.w2"], W["emb.clu.b2"])
-    np.testing.assert_array_equal(e[i_t], ft[0])
-    np.testing.assert_array_equal(e[i_c], fc[0])
+    np.testing.assert_allclose(e[i_t], ft[0], rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(e[i_c], fc[0], rtol=1e-12, atol=1e-14)
 
 
 def test_paper_arch_decode_hand_values():
