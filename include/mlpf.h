@@ -59,6 +59,13 @@ typedef struct {
     int32_t n_cls;  /* 6 classes: none, ch. hadron, n. hadron, photon, electron, muon */
     int32_t n_reg;  /* 5 regression outputs: pT, eta, sin phi, cos phi, E */
     int32_t act;    /* 0 = GELU (exact erf form), 1 = ReLU */
+    int32_t arch;   /* 0 = one shared embedding, the regression stack reads
+                       concat(x, h_pid), one 6-class head (argmax);
+                       1 = the architecture as Sec. 5.3 prints it: track and cluster
+                       embeddings, two parallel stacks on the same embedding, a
+                       binary head (logit column 0; a particle where it is > 0, i.e.
+                       score > 0.5) and a 5-class PID head (columns 1-5; class =
+                       1 + argmax).  arch 1 runs on MLPF_FP32 only. */
 } mlpf_config;
 
 /*

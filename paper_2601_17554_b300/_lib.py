@@ -24,7 +24,7 @@ EXPORTS = ("mlpf_load_weights", "mlpf_free", "mlpf_get_config", "mlpf_forward",
 
 class MlpfConfig(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in
-                ("in_dim", "d", "heads", "ffn", "l_pid", "l_reg", "n_cls", "n_reg", "act")]
+                ("in_dim", "d", "heads", "ffn", "l_pid", "l_reg", "n_cls", "n_reg", "act", "arch")]
 
 
 _handle = None

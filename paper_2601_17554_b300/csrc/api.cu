@@ -59,10 +59,18 @@ static const int REG_HEAD_WIDTH[4] = {1, 1, 2, 1};
 static std::vector<std::pair<std::string, std::vector<int>>> expected_tensors(const mlpf_config& c) {
     std::vector<std::pair<std::string, std::vector<int>>> v;
     const int d = c.d, f = c.ffn;
-    v.push_back({"emb.w1", {d, c.in_dim}});
-    v.push_back({"emb.b1", {d}});
-    v.push_back({"emb.w2", {d, d}});
-    v.push_back({"emb.b2", {d}});
+    auto mlp = [&](const std::string& p, int n_in, int n_out) {
+        v.push_back({p + ".w1", {d, n_in}});
+        v.push_back({p + ".b1", {d}});
+        v.push_back({p + ".w2", {n_out, d}});
+        v.push_back({p + ".b2", {n_out}});
+    };
+    if (c.arch == 1) {
+        mlp("emb.trk", c.in_dim, d);
+        mlp("emb.clu", c.in_dim, d);
+    } else {
+        mlp("emb", c.in_dim, d);
+    }
     auto stack = [&](const std::string& p0, int n) {
         for (int l = 0; l < n; ++l) {
             const std::string p = p0 + "." + std::to_string(l) + ".";
@@ -83,22 +91,15 @@ static std::vector<std::pair<std::string, std::vector<int>>> expected_tensors(co
         v.push_back({p0 + ".lnf.b", {d}});
     };
     stack("pid", c.l_pid);
-    v.push_back({"remb.w1", {d, c.in_dim + d}});
-    v.push_back({"remb.b1", {d}});
-    v.push_back({"remb.w2", {d, d}});
-    v.push_back({"remb.b2", {d}});
+    if (c.arch != 1) mlp("remb", c.in_dim + d, d);
     stack("reg", c.l_reg);
-    v.push_back({"head.cls.w1", {d, d}});
-    v.push_back({"head.cls.b1", {d}});
-    v.push_back({"head.cls.w2", {c.n_cls, d}});
-    v.push_back({"head.cls.b2", {c.n_cls}});
-    for (int h = 0; h < 4; ++h) {
-        const std::string p = std::string("head.") + REG_HEAD_NAMES[h] + ".";
-        v.push_back({p + "w1", {d, d}});
-        v.push_back({p + "b1", {d}});
-        v.push_back({p + "w2", {REG_HEAD_WIDTH[h], d}});
-        v.push_back({p + "b2", {REG_HEAD_WIDTH[h]}});
+    if (c.arch == 1) {
+        mlp("head.bin", d, 1);
+        mlp("head.pid", d, c.n_cls - 1);
+    } else {
+        mlp("head.cls", d, c.n_cls);
     }
+    for (int h = 0; h < 4; ++h) mlp(std::string("head.") + REG_HEAD_NAMES[h], d, REG_HEAD_WIDTH[h]);
     return v;
 }
 
@@ -109,12 +110,16 @@ static mlpf_status parse_blob(const uint8_t* p, size_t nbytes, Model& m) {
     if (std::memcmp(p, "MLPF", 4) != 0) { set_error("blob magic is not MLPF"); return MLPF_E_FORMAT; }
     int32_t version;
     std::memcpy(&version, p + 4, 4);
-    if (version != 1) { set_error("unsupported blob version " + std::to_string(version)); return MLPF_E_FORMAT; }
-    int32_t h[10];
-    std::memcpy(h, p + 8, 40);
-    off = 48;
-    mlpf_config c{h[0], h[1], h[2], h[3], h[4], h[5], h[6], h[7], h[8]};
-    const int n_tensors = h[9];
+    if (version != 1 && version != 2) { set_error("unsupported blob version " + std::to_string(version)); return MLPF_E_FORMAT; }
+    // version 1: 10 header words (arch 0); version 2: an arch word before n_tensors
+    const int nh = version == 1 ? 10 : 11;
+    if (!need(8 + 4 * (size_t)nh)) { set_error("blob truncated: header"); return MLPF_E_FORMAT; }
+    int32_t h[11];
+    std::memcpy(h, p + 8, 4 * (size_t)nh);
+    off = 8 + 4 * (size_t)nh;
+    mlpf_config c{h[0], h[1], h[2], h[3], h[4], h[5], h[6], h[7], h[8], version == 1 ? 0 : h[9]};
+    const int n_tensors = h[nh - 1];
+    if (c.arch != 0 && c.arch != 1) { set_error("unknown architecture in blob header"); return MLPF_E_FORMAT; }
     if (c.in_dim != 42 || c.n_cls != 6 || c.n_reg != 5 || c.d <= 0 || c.d > 256 || c.heads <= 0 ||
         c.d % c.heads != 0 || (c.d / c.heads != 16 && c.d / c.heads != 32 && c.d / c.heads != 64) ||
         c.ffn <= 0 || c.ffn > 4096 || c.l_pid < 1 || c.l_reg < 1 || c.l_pid > 16 ||
@@ -295,7 +300,7 @@ static mlpf_status validate(const Model* m, int32_t prec, const void* x, const v
     if (total > 0 && (!x || !cu || !logits || !reg)) { set_error("NULL input or output pointer"); return MLPF_E_INVALID; }
     if (n_events > 0 && !cu) { set_error("cu_seqlens is NULL"); return MLPF_E_INVALID; }
     if (prec != MLPF_FP32 && !m->tc_supported) {
-        set_error("tensor-core path is built for d=64, 4 heads, FFN 256 models only");
+        set_error("tensor-core path is built for d=64, 4 heads, FFN 256, arch 0 models only");
         return MLPF_E_UNSUPPORTED;
     }
     if (prec == MLPF_FP8 && !m->fp8_ready) {
@@ -398,7 +403,7 @@ struct mlpf_model {
 
 extern "C" {
 
-int32_t mlpf_abi_version(void) { return 100; }
+int32_t mlpf_abi_version(void) { return 101; }
 
 const char* mlpf_last_error(void) { return g_last_error.c_str(); }
 
@@ -438,7 +443,7 @@ mlpf_status mlpf_load_weights(const void* blob, size_t nbytes, int device, mlpf_
         cudaDeviceProp prop;
         cudaGetDeviceProperties(&prop, device);
         const bool arch_ok = prop.major == 10 && prop.minor == 3;
-        m.tc_supported = arch_ok && c.d == 64 && c.heads == 4 && c.ffn == 256;
+        m.tc_supported = arch_ok && c.d == 64 && c.heads == 4 && c.ffn == 256 && c.arch == 0;
         if (m.tc_supported && !tc_prepare_weights(m)) s = MLPF_E_CUDA;
     }
     if (s != MLPF_OK) {

@@ -128,6 +128,10 @@ extern "C" mlpf_status mlpf_forward_gated(mlpf_model* student, mlpf_model* teach
     if (!student || !teacher) { set_error("NULL model"); return MLPF_E_INVALID; }
     Model& sm = student->impl;
     if (sm.device != teacher->impl.device) { set_error("student and teacher on different devices"); return MLPF_E_INVALID; }
+    if (sm.cfg.arch != teacher->impl.cfg.arch) {
+        set_error("student and teacher must share the class-score layout (arch)");
+        return MLPF_E_INVALID;
+    }
     cudaStream_t st = (cudaStream_t)stream;
     mlpf_status s = mlpf_forward(student, student_precision, x, cu_seqlens, n_events, total, max_n, logits, reg,
                                  nullptr, nullptr, stream);

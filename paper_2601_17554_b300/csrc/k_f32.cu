@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(256) k_event_sums(const int32_t* __restrict__ 
                                                     const float* __restrict__ reg,
                                                     int32_t* __restrict__ cls_out,
                                                     double* __restrict__ sums, int n_cls,
-                                                    unsigned* status) {
+                                                    int arch, unsigned* status) {
     __shared__ double part[3][8];
     __shared__ int bad;
     const int e = blockIdx.x;
@@ -222,14 +222,18 @@ __global__ void __launch_bounds__(256) k_event_sums(const int32_t* __restrict__ 
     bool finite = true;
     for (int r = s + threadIdx.x; r < t; r += 256) {
         const float* lo = logits + (size_t)r * n_cls;
-        int best = 0;
-        float bv = lo[0];
-        finite &= isfinite(bv);
-        for (int c = 1; c < n_cls; ++c) {
+        // arch 0: argmax of all scores (lowest index on ties); arch 1: a particle
+        // where the binary logit (column 0) is > 0, PID = 1 + argmax of columns 1..
+        const int c0 = arch == 1 ? 1 : 0;
+        int best = c0;
+        float bv = lo[c0];
+        finite &= isfinite(lo[0]) && isfinite(bv);
+        for (int c = c0 + 1; c < n_cls; ++c) {
             const float v = lo[c];
             finite &= isfinite(v);
             if (v > bv) { bv = v; best = c; }
         }
+        if (arch == 1 && !(lo[0] > 0.f)) best = 0;
         const float* rg = reg + (size_t)r * 5;
 #pragma unroll
         for (int c = 0; c < 5; ++c) finite &= isfinite(rg[c]);
@@ -297,6 +301,17 @@ static void layernorm(const float* X, const float* g, const float* b, float* Y, 
     ++n;
 }
 
+// Per-type embedding (arch 1): rows of cluster-type elements take the cluster
+// FFN's output.  Track-like types: track, GSF track, brem (one-hot x[0], x[5], x[6]).
+__global__ void k_type_select(const float* __restrict__ x, const float* __restrict__ e_clu,
+                              float* __restrict__ z, int T, int d) {
+    const int r = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    if (r >= T) return;
+    const float* xr = x + (size_t)r * 42;
+    if (xr[0] + xr[5] + xr[6] > 0.5f) return;
+    for (int c = threadIdx.x & 31; c < d; c += 32) z[(size_t)r * d + c] = e_clu[(size_t)r * d + c];
+}
+
 int64_t run_forward_f32(Model& m, const float* x, const int32_t* cu, int n_events, int total,
                         int max_n, float* logits, float* reg, cudaStream_t st) {
     const mlpf_config& c = m.cfg;
@@ -336,30 +351,47 @@ int64_t run_forward_f32(Model& m, const float* x, const int32_t* cu, int n_event
                   T, d, st, n);
     };
 
-    linear(x, 42, 42, nullptr, 0, 0, W("emb.w1"), W("emb.b1"), nullptr, 0, w.hid, d, T, d, act, st,
-           n);
-    linear(w.hid, d, d, nullptr, 0, 0, W("emb.w2"), W("emb.b2"), nullptr, 0, w.z, d, T, d, -1, st,
-           n);
-    stack("pid", c.l_pid, m.w.wqkv_pid, m.w.bqkv_pid, w.hpid);
-    linear(x, 42, 42, w.hpid, d, d, W("remb.w1"), W("remb.b1"), nullptr, 0, w.hid, d, T, d, act, st,
-           n);
-    linear(w.hid, d, d, nullptr, 0, 0, W("remb.w2"), W("remb.b2"), nullptr, 0, w.z, d, T, d, -1, st,
-           n);
-    stack("reg", c.l_reg, m.w.wqkv_reg, m.w.bqkv_reg, w.hreg);
-    // heads
-    linear(w.hpid, d, d, nullptr, 0, 0, W("head.cls.w1"), W("head.cls.b1"), nullptr, 0, w.hid, d,
-           T, d, act, st, n);
-    linear(w.hid, d, d, nullptr, 0, 0, W("head.cls.w2"), W("head.cls.b2"), nullptr, 0, logits,
-           c.n_cls, T, c.n_cls, -1, st, n);
+    auto mlp = [&](const float* in, int k_in, const char* p, float* out, int ldo, int n_out) {
+        const std::string s(p);
+        linear(in, k_in, k_in, nullptr, 0, 0, W(s + ".w1"), W(s + ".b1"), nullptr, 0, w.hid, d, T, d,
+               act, st, n);
+        linear(w.hid, d, d, nullptr, 0, 0, W(s + ".w2"), W(s + ".b2"), nullptr, 0, out, ldo, T, n_out,
+               -1, st, n);
+    };
+    if (c.arch == 1) {
+        // Sec. 5.3 as printed: track and cluster embeddings; two parallel stacks on
+        // the embedding (kept in hreg while the classification stack runs)
+        mlp(x, 42, "emb.trk", w.hreg, d, d);
+        mlp(x, 42, "emb.clu", w.zn, d, d);
+        prof_begin(m, st, "f32_type_select");
+        k_type_select<<<cdiv(T, 8), 256, 0, st>>>(x, w.zn, w.hreg, T, d);
+        prof_end(m, st);
+        ++n;
+        if (cudaMemcpyAsync(w.z, w.hreg, (size_t)T * d * sizeof(float), cudaMemcpyDeviceToDevice, st) !=
+            cudaSuccess)
+            return -1;
+        stack("pid", c.l_pid, m.w.wqkv_pid, m.w.bqkv_pid, w.hpid);
+        if (cudaMemcpyAsync(w.z, w.hreg, (size_t)T * d * sizeof(float), cudaMemcpyDeviceToDevice, st) !=
+            cudaSuccess)
+            return -1;
+        stack("reg", c.l_reg, m.w.wqkv_reg, m.w.bqkv_reg, w.hreg);
+        mlp(w.hpid, d, "head.bin", logits, c.n_cls, 1);
+        mlp(w.hpid, d, "head.pid", logits + 1, c.n_cls, c.n_cls - 1);
+    } else {
+        mlp(x, 42, "emb", w.z, d, d);
+        stack("pid", c.l_pid, m.w.wqkv_pid, m.w.bqkv_pid, w.hpid);
+        linear(x, 42, 42, w.hpid, d, d, W("remb.w1"), W("remb.b1"), nullptr, 0, w.hid, d, T, d, act, st,
+               n);
+        linear(w.hid, d, d, nullptr, 0, 0, W("remb.w2"), W("remb.b2"), nullptr, 0, w.z, d, T, d, -1, st,
+               n);
+        stack("reg", c.l_reg, m.w.wqkv_reg, m.w.bqkv_reg, w.hreg);
+        mlp(w.hpid, d, "head.cls", logits, c.n_cls, c.n_cls);
+    }
     const char* names[4] = {"pt", "eta", "phi", "e"};
     const int widths[4] = {1, 1, 2, 1};
     int off = 0;
     for (int h = 0; h < 4; ++h) {
-        const std::string p = std::string("head.") + names[h] + ".";
-        linear(w.hreg, d, d, nullptr, 0, 0, W(p + "w1"), W(p + "b1"), nullptr, 0, w.hid, d, T, d,
-               act, st, n);
-        linear(w.hid, d, d, nullptr, 0, 0, W(p + "w2"), W(p + "b2"), nullptr, 0, w.raw + off, 5, T,
-               widths[h], -1, st, n);
+        mlp(w.hreg, d, (std::string("head.") + names[h]).c_str(), w.raw + off, 5, widths[h]);
         off += widths[h];
     }
     prof_begin(m, st, "f32_decode");
@@ -402,7 +434,7 @@ int64_t run_event_sums(Model& m, const int32_t* cu, int n_events, const float* l
                        cudaStream_t st) {
     if (n_events <= 0 || (!cls && !sums)) return 0;
     prof_begin(m, st, "event_sums");
-    k_event_sums<<<n_events, 256, 0, st>>>(cu, n_events, logits, reg, cls, sums, n_cls, m.status);
+    k_event_sums<<<n_events, 256, 0, st>>>(cu, n_events, logits, reg, cls, sums, n_cls, m.cfg.arch, m.status);
     prof_end(m, st);
     if (cudaPeekAtLastError() != cudaSuccess) return -1;
     return 1;

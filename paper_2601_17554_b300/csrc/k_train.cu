@@ -743,7 +743,7 @@ mlpf_status mlpf_trainer_create(const void* blob, size_t nbytes, int device, mlp
     mlpf_status s = parse_blob_into((const uint8_t*)blob, nbytes, t.m);
     if (s != MLPF_OK) { delete tt; return s; }
     const mlpf_config& c = t.m.cfg;
-    if (c.d > 256 || c.ffn > 4096) { delete tt; set_error("unsupported trainer configuration"); return MLPF_E_UNSUPPORTED; }
+    if (c.d > 256 || c.ffn > 4096 || c.arch != 0) { delete tt; set_error("unsupported trainer configuration"); return MLPF_E_UNSUPPORTED; }
     // parameter vector in blob order (names re-read from the blob)
     {
         const uint8_t* p = (const uint8_t*)blob;

@@ -326,5 +326,5 @@ def workload(name: str):
     if name == "batch512":          # 512 events LogNormal(2500, 0.5) in [100, 12000]
         return SMALL, 0, 104, sizes_lognormal(104, 512)
     if name == "paper8":            # 8 events U{1000..6000}, the architecture as printed
-        return PAPER, 2, 105, sizes_uniform(105, 8)
+        return PAPER, 4, 105, sizes_uniform(105, 8)
     raise KeyError(name)
