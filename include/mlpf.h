@@ -310,6 +310,16 @@ int32_t mlpf_profile_get(mlpf_model* m, int32_t cap, char* names, float* ms);
 /* Thread-local message describing the last non-OK status of this thread. */
 const char* mlpf_last_error(void);
 
+/*
+ * Evaluate an activation as a path computes it, on device arrays (a check of the
+ * kernels' arithmetic; no counterpart in the paper): impl 0 = the FP32 path
+ * (GELU from CUDA erff), impl 1 = the tensor-core epilogues (GELU from the
+ * Abramowitz & Stegun 7.1.26 erf with MUFU reciprocal and exponential);
+ * act 0 = GELU, 1 = ReLU.  y[i] = act(x[i]) for i < n, asynchronous on `stream`.
+ */
+mlpf_status mlpf_eval_activation(int32_t impl, int32_t act, const float* x, float* y, int32_t n,
+                                 void* stream);
+
 /* ABI version of this library (major * 100 + minor). */
 int32_t mlpf_abi_version(void);
 

@@ -15,10 +15,11 @@ OPT_USE_GRAPHS, OPT_WAIT_LIMIT_NS, OPT_DEBUG_STALL, OPT_ATTN_CTAS_PER_SM, OPT_AT
 
 # every symbol include/mlpf.h declares
 EXPORTS = ("mlpf_load_weights", "mlpf_free", "mlpf_get_config", "mlpf_forward",
-           "mlpf_forward_host", "mlpf_forward_noalloc", "mlpf_calibrate_fp8", "mlpf_get_fp8_scales",
-           "mlpf_autotune", "mlpf_measure_unit_rates", "mlpf_forward_gated", "mlpf_trainer_create", "mlpf_trainer_free",
-           "mlpf_trainer_num_params",
-           "mlpf_trainer_step", "mlpf_trainer_export", "mlpf_sync", "mlpf_set_option", "mlpf_get_option",
+           "mlpf_forward_host", "mlpf_forward_noalloc", "mlpf_calibrate_fp8",
+           "mlpf_get_fp8_scales", "mlpf_autotune", "mlpf_measure_unit_rates",
+           "mlpf_eval_activation", "mlpf_forward_gated", "mlpf_trainer_create",
+           "mlpf_trainer_free", "mlpf_trainer_num_params", "mlpf_trainer_step",
+           "mlpf_trainer_export", "mlpf_sync", "mlpf_set_option", "mlpf_get_option",
            "mlpf_last_launch_count", "mlpf_profile_get", "mlpf_last_error", "mlpf_abi_version")
 
 
@@ -60,6 +61,8 @@ def load(build_if_missing: bool = True):
     L.mlpf_measure_unit_rates.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_double)]
     L.mlpf_measure_unit_rates.restype = ctypes.c_int
+    L.mlpf_eval_activation.argtypes = [i32, i32, vp, vp, i32, vp]
+    L.mlpf_eval_activation.restype = ctypes.c_int
     L.mlpf_autotune.argtypes = [vp, i32, vp, vp, i32, i32, i32, ctypes.c_char_p, vp]
     L.mlpf_autotune.restype = ctypes.c_int
     L.mlpf_get_fp8_scales.argtypes = [vp, i32, ctypes.c_char_p, ctypes.POINTER(ctypes.c_float)]

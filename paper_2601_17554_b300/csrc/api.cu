@@ -403,6 +403,18 @@ struct mlpf_model {
 
 extern "C" {
 
+mlpf_status mlpf_eval_activation(int32_t impl, int32_t act, const float* x, float* y, int32_t n, void* stream) {
+    if (impl < 0 || impl > 1 || act < 0 || act > 1 || n < 0 || (n > 0 && (!x || !y))) {
+        set_error("bad argument to mlpf_eval_activation");
+        return MLPF_E_INVALID;
+    }
+    if (impl == 0) f32_eval_activation(x, y, n, act, (cudaStream_t)stream);
+    else tc_eval_activation(x, y, n, act, (cudaStream_t)stream);
+    const cudaError_t e = cudaPeekAtLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "activation kernel");
+    return MLPF_OK;
+}
+
 int32_t mlpf_abi_version(void) { return 101; }
 
 const char* mlpf_last_error(void) { return g_last_error.c_str(); }

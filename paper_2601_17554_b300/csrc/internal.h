@@ -139,6 +139,8 @@ int64_t run_forward_f32(Model& m, const float* x, const int32_t* cu, int n_event
                         int max_n, float* logits, float* reg, cudaStream_t st);
 int64_t run_forward_tc(Model& m, int prec, const float* x, const int32_t* cu, int n_events,
                        int total, int max_n, float* logits, float* reg, cudaStream_t st);
+void f32_eval_activation(const float* x, float* y, int n, int act, cudaStream_t st);
+void tc_eval_activation(const float* x, float* y, int n, int act, cudaStream_t st);
 int64_t run_event_sums(Model& m, const int32_t* cu, int n_events, const float* logits,
                        const float* reg, int32_t* cls, double* sums, int n_cls,
                        cudaStream_t st);

@@ -429,6 +429,15 @@ void f32_attention(const float* qkv, float* out, const int32_t* cu, int n_events
         k_attention<64><<<grid, 64, 0, st>>>(qkv, out, cu, d, scale, lse);
 }
 
+__global__ void k_eval_act_f32(const float* __restrict__ x, float* __restrict__ y, int n, int act) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = act_fn(x[i], act);
+}
+
+void f32_eval_activation(const float* x, float* y, int n, int act, cudaStream_t st) {
+    if (n > 0) k_eval_act_f32<<<(n + 255) / 256, 256, 0, st>>>(x, y, n, act);
+}
+
 int64_t run_event_sums(Model& m, const int32_t* cu, int n_events, const float* logits,
                        const float* reg, int32_t* cls, double* sums, int n_cls,
                        cudaStream_t st) {

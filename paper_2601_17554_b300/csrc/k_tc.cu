@@ -45,7 +45,25 @@ MLPF_DEV uint8_t* align1024(uint8_t* p) {
     return (uint8_t*)(((uintptr_t)p + 1023) & ~(uintptr_t)1023);
 }
 
-MLPF_DEV float gelu_f(float v) { return 0.5f * v * (1.0f + erff(v * 0.70710678118654752f)); }
+// GELU(v) = v Phi(v) = v (1 + erf(v / sqrt 2)) / 2 with erf from the rational
+// approximation of Abramowitz & Stegun, Handbook of Mathematical Functions,
+// formula 7.1.26 (Hastings): for z >= 0, erf(z) = 1 - t (a1 + t (a2 + t (a3 + t (a4
+// + t a5)))) e^(-z^2), t = 1 / (1 + p z), |error| <= 1.5e-7; erf(-z) = -erf(z).
+// The reciprocal and the exponential run on the MUFU (approximate, ~1 ulp), which
+// is idle in the GEMM epilogues; the result is far below the 16-bit rounding of
+// the operands it feeds.  Checked against the FP32 path's erff-based GELU by
+// mlpf_eval_activation.
+MLPF_DEV float gelu_f(float v) {
+    constexpr float kP = 0.3275911f, kA1 = 0.254829592f, kA2 = -0.284496736f, kA3 = 1.421413741f,
+                    kA4 = -1.453152027f, kA5 = 1.061405429f;
+    const float z = fabsf(v) * 0.70710678118654752f;
+    float t, e;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(t) : "f"(fmaf(kP, z, 1.f)));
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(-z * z * 1.4426950408889634f));
+    const float poly = t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, kA5, kA4), kA3), kA2), kA1);
+    const float erf_abs = fmaf(-poly, e, 1.f);
+    return 0.5f * v * (1.f + copysignf(erf_abs, v));
+}
 MLPF_DEV float act_f(float v, int act) { return act == 1 ? fmaxf(v, 0.f) : gelu_f(v); }
 
 // GEMM operand formats of the row-tile kernels.  A 128-byte swizzle atom holds
@@ -1902,6 +1920,11 @@ __global__ void __launch_bounds__(AW_THREADS, 1)
     }
 }
 
+__global__ void k_eval_act_tc(const float* __restrict__ x, float* __restrict__ y, int n, int act) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = act_f(x[i], act);
+}
+
 // ---------------------------------------------------------------- host side
 uint32_t embed_smem(int mode, int fmt) {
     (void)fmt;
@@ -2037,6 +2060,10 @@ void set_attrs() {
 }
 
 }  // namespace
+
+void tc_eval_activation(const float* x, float* y, int n, int act, cudaStream_t st) {
+    if (n > 0) k_eval_act_tc<<<(n + 255) / 256, 256, 0, st>>>(x, y, n, act);
+}
 
 bool tc_prepare_weights(Model& m) {
     const mlpf_config& c = m.cfg;
