@@ -357,156 +357,6 @@ struct EmbedParams {
     int slot[3];
 };
 
-// FMT: GEMM operand format (BF16, FP16 or E4M3), FP32 accumulation in every case.
-// The embedding FFN runs in FE (FP16 when FMT is E4M3: only the projection and FFN
-// GEMMs of the encoder blocks use E4M3); the QKV projection runs in FMT.
-template <int MODE, int FMT>  // MODE 0: input x (K = 42 -> 64); 1: concat(x, h_pid) (K = 106 -> 128)
-__global__ void __launch_bounds__(128, 1) k_embed_qkv(const __grid_constant__ CUtensorMap map_hp,
-                                                      EmbedParams p) {
-    extern __shared__ uint8_t smem_raw[];
-    uint8_t* sm = align1024(smem_raw);
-    constexpr int FE = kIs8<FMT> ? FMT_FP16 : FMT;
-    constexpr int KA = MODE == 0 ? 1 : 2;  // atoms of the first GEMM's A operand
-    constexpr uint32_t W1B = 64 * 128 * KA, W2B = 64 * 128, WQB = 192 * 128;
-    constexpr bool TMA_HP = MODE == 1;
-    uint8_t* sW1 = sm;
-    uint8_t* sW2 = sW1 + W1B;
-    uint8_t* sWq = sW2 + W2B;
-    uint8_t* sA = sWq + WQB;          // KA atom columns
-    uint8_t* sH = sA + KA * ATOM;     // 1 atom column
-    uint64_t* bars = (uint64_t*)(sH + ATOM);  // 0 weights, 1 tma, 2 mma
-    uint32_t* tmem_hold = (uint32_t*)(bars + 4);
-    int* abort_flag = (int*)(tmem_hold + 1);
-    const int tid = threadIdx.x;
-
-    if (tid == 0) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
-        mbar_init(&bars[2], 1);
-        *abort_flag = 0;
-        fence_mbar_init();
-    }
-    if (tid < 32) {
-        tmem_alloc(tmem_hold, 256);
-        tmem_relinquish();
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tbase = *tmem_hold;
-    const uint32_t trow = tbase + ((uint32_t)(tid & 96) << 16);  // lane quarter of this warp
-    volatile int* ab = abort_flag;
-
-    if (tid == 0) {
-        mbar_arrive_expect_tx(&bars[0], W1B + W2B + WQB);
-        bulk_load(sW1, p.w1, W1B, &bars[0]);
-        bulk_load(sW2, p.w2, W2B, &bars[0]);
-        bulk_load(sWq, p.wqkv, WQB, &bars[0]);
-    }
-    bool fail = !mbar_wait(&bars[0], 0, ab, p.status, ST_TIMEOUT_GEMM, p.wait_ns);
-
-    const int tpad = p.counters[1];
-    const int nblk = tpad >> 6;
-    const int ntiles = (tpad + ROWS - 1) / ROWS;
-    uint32_t mph = 0, aph = 0;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        if (__syncthreads_or(fail)) break;
-        const int p0 = tile * ROWS;
-        const int prow_pad = p0 + tid;
-        const RowInfo ri = row_info(p.blk, nblk, prow_pad);
-        if (TMA_HP && tid == 0) {
-            mbar_arrive_expect_tx(&bars[1], ATOM);
-            tma_load_2d(sA + ATOM, &map_hp, 0, p0, &bars[1]);
-        }
-        float v[64];
-        load_x_row(v, p.x, ri.valid, ri.prow);
-        st_op<FE>(sA, tid, v, 64, 0, 1.f);
-        float amx = 0.f;
-        if (p.amax) {
-#pragma unroll
-            for (int i = 0; i < 42; ++i) amx = fmaxf(amx, fabsf(v[i]));
-        }
-        if (MODE == 1 && p.amax) {
-            // h_pid row of this element (16-bit, as written by the PID stack)
-            const uint4* src = (const uint4*)(p.hp + (size_t)prow_pad * D);
-#pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                const uint4 u = src[c];
-                unpack2<kOutF16<FMT>>(u.x, v[8 * c], v[8 * c + 1]);
-                unpack2<kOutF16<FMT>>(u.y, v[8 * c + 2], v[8 * c + 3]);
-                unpack2<kOutF16<FMT>>(u.z, v[8 * c + 4], v[8 * c + 5]);
-                unpack2<kOutF16<FMT>>(u.w, v[8 * c + 6], v[8 * c + 7]);
-            }
-#pragma unroll
-            for (int i = 0; i < 64; ++i) amx = fmaxf(amx, fabsf(v[i]));
-        }
-        if (p.amax) record_amax(p.amax, p.slot[0], &amx, 1, ri.valid);
-        fence_proxy_async_smem();
-        __syncthreads();
-        if (tid == 0) {
-            if (TMA_HP) fail |= !mbar_wait(&bars[1], aph, ab, p.status, ST_TIMEOUT_GEMM, p.wait_ns);
-            tc_fence_after();
-            if (!fail) issue_gemm<FE>(tbase, sA, sW1, 64, KA);
-            mma_commit(&bars[2]);
-        }
-        aph ^= 1;
-        fail |= !mbar_wait(&bars[2], mph, ab, p.status, ST_TIMEOUT_GEMM, p.wait_ns);
-        mph ^= 1;
-        if (__syncthreads_or(fail)) break;
-        tc_fence_after();
-        ld_row64(trow, v);
-#pragma unroll
-        for (int i = 0; i < 64; ++i) v[i] = act_f(v[i] + __ldg(p.b1 + i), p.act);
-        if (p.amax) record_amax(p.amax, p.slot[1], v, 64, ri.valid);
-        st_op<FE>(sH, tid, v, 64, 0, 1.f);
-        tc_fence_before();
-        fence_proxy_async_smem();
-        __syncthreads();
-        if (tid == 0) {
-            tc_fence_after();
-            issue_gemm<FE>(tbase, sH, sW2, 64, 1);
-            mma_commit(&bars[2]);
-        }
-        fail |= !mbar_wait(&bars[2], mph, ab, p.status, ST_TIMEOUT_GEMM, p.wait_ns);
-        mph ^= 1;
-        if (__syncthreads_or(fail)) break;
-        tc_fence_after();
-        ld_row64(trow, v);
-#pragma unroll
-        for (int i = 0; i < 64; ++i) v[i] += __ldg(p.b2 + i);
-        {
-            float4* zd = (float4*)(p.z + (size_t)prow_pad * D);
-#pragma unroll
-            for (int i = 0; i < 16; ++i) zd[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
-        }
-        layernorm64(v, v, p.lng, p.lnb);
-        if (p.amax) record_amax(p.amax, p.slot[2], v, 64, ri.valid);
-        st_op<FMT>(sH, tid, v, 64, 0, p.qs[2], true);
-        tc_fence_before();
-        fence_proxy_async_smem();
-        __syncthreads();
-        if (tid == 0) {
-            tc_fence_after();
-            issue_gemm<FMT>(tbase, sH, sWq, 192, 1);
-            mma_commit(&bars[2]);
-        }
-        fail |= !mbar_wait(&bars[2], mph, ab, p.status, ST_TIMEOUT_GEMM, p.wait_ns);
-        mph ^= 1;
-        if (__syncthreads_or(fail)) break;
-        tc_fence_after();
-        store_qkv<kOutF16<FMT>>(trow, p.bqkv, p.ds[2], prow_pad, ri.valid, p.q, p.k, p.vt, p.ldvt);
-        tc_fence_before();
-    }
-    __syncthreads();
-    if (*ab && tid == 0) {
-        for (int i = 0; i < 1000; ++i) __nanosleep(1000);  // let in-flight copies land
-    }
-    __syncthreads();
-    if (tid < 32) {
-        tc_fence_after();
-        tmem_dealloc(tbase, 256);
-    }
-}
 
 // ------------------------------------------------------------ post-attention
 struct PostParams {
@@ -582,6 +432,194 @@ MLPF_DEV void layernorm_split(const float* z32, float* out32, const float* g, co
     const float rs = rsqrtf(q * (1.0f / D) + LN_EPS);
 #pragma unroll
     for (int i = 0; i < 32; ++i) out32[i] = (z32[i] - mu) * rs * g[32 * wg + i] + b[32 * wg + i];
+}
+
+// FMT: GEMM operand format (BF16, FP16 or E4M3), FP32 accumulation in every case.
+// The embedding FFN runs in FE (FP16 when FMT is E4M3: only the projection and FFN
+// GEMMs of the encoder blocks use E4M3); the QKV projection runs in FMT.
+// 256 threads: thread (wg, r) owns row r of the 128-row tile and, in every
+// epilogue, the warpgroup's half of the columns; LayerNorm moments are combined
+// through shared memory.
+constexpr int EM_THREADS = 256;
+template <int MODE, int FMT>  // MODE 0: input x (K = 42 -> 64); 1: concat(x, h_pid) (K = 106 -> 128)
+__global__ void __launch_bounds__(EM_THREADS, 2) k_embed_qkv(const __grid_constant__ CUtensorMap map_hp,
+                                                             EmbedParams p) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* sm = align1024(smem_raw);
+    constexpr int FE = kIs8<FMT> ? FMT_FP16 : FMT;
+    constexpr int KA = MODE == 0 ? 1 : 2;  // atoms of the first GEMM's A operand
+    constexpr uint32_t W1B = 64 * 128 * KA, W2B = 64 * 128, WQB = 192 * 128;
+    constexpr bool TMA_HP = MODE == 1;
+    constexpr bool F16 = kOutF16<FMT>;
+    uint8_t* sW1 = sm;
+    uint8_t* sW2 = sW1 + W1B;
+    uint8_t* sWq = sW2 + W2B;
+    uint8_t* sA = sWq + WQB;          // KA atom columns
+    uint8_t* sH = sA + KA * ATOM;     // 1 atom column
+    float* red = (float*)(sH + ATOM); // [pass][wg][row] LayerNorm partial sums
+    uint64_t* bars = (uint64_t*)(red + 2 * 2 * 128);  // 0 weights, 1 tma, 2 mma
+    uint32_t* tmem_hold = (uint32_t*)(bars + 4);
+    int* abort_flag = (int*)(tmem_hold + 1);
+    const int tid = threadIdx.x;
+    const int wg = tid >> 7, r = tid & 127;
+
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        mbar_init(&bars[2], 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (tid < 32) {
+        tmem_alloc(tmem_hold, 256);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = *tmem_hold;
+    const uint32_t trow = tbase + ((uint32_t)(tid & 96) << 16);  // lane quarter of this warp
+    volatile int* ab = abort_flag;
+
+    if (tid == 0) {
+        mbar_arrive_expect_tx(&bars[0], W1B + W2B + WQB);
+        bulk_load(sW1, p.w1, W1B, &bars[0]);
+        bulk_load(sW2, p.w2, W2B, &bars[0]);
+        bulk_load(sWq, p.wqkv, WQB, &bars[0]);
+    }
+    bool fail = !mbar_wait(&bars[0], 0, ab, p.status, ST_TIMEOUT_GEMM, p.wait_ns);
+
+    const int tpad = p.counters[1];
+    const int nblk = tpad >> 6;
+    const int ntiles = (tpad + ROWS - 1) / ROWS;
+    uint32_t mph = 0, aph = 0;
+    // every thread: sync, thread 0 issues, wait for the MMA; false on failure
+    auto run_mma = [&](auto issue) -> bool {
+        tc_fence_before();
+        fence_proxy_async_smem();
+        if (__syncthreads_or(fail)) return false;
+        if (tid == 0) {
+            tc_fence_after();
+            issue();
+            mma_commit(&bars[2]);
+        }
+        fail |= !mbar_wait(&bars[2], mph, ab, p.status, ST_TIMEOUT_GEMM, p.wait_ns);
+        mph ^= 1;
+        const bool stop = __syncthreads_or(fail);
+        tc_fence_after();
+        return !stop;
+    };
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        if (__syncthreads_or(fail)) break;
+        const int p0 = tile * ROWS;
+        const int prow_pad = p0 + r;
+        const RowInfo ri = row_info(p.blk, nblk, prow_pad);
+        if (TMA_HP && tid == 0) {
+            mbar_arrive_expect_tx(&bars[1], ATOM);
+            tma_load_2d(sA + ATOM, &map_hp, 0, p0, &bars[1]);
+        }
+        float v[32];
+        // this warpgroup's 32 of the row's 42 features (zero padded to 64)
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = 0.f;
+        if (ri.valid) {
+            const float2* src = (const float2*)(p.x + (size_t)ri.prow * 42 + 32 * wg);
+            if (wg == 0) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) { const float2 t = __ldg(src + i); v[2 * i] = t.x; v[2 * i + 1] = t.y; }
+            } else {
+#pragma unroll
+                for (int i = 0; i < 5; ++i) { const float2 t = __ldg(src + i); v[2 * i] = t.x; v[2 * i + 1] = t.y; }
+            }
+        }
+        st_op<FE>(sA, r, v, 32, 32 * wg, 1.f);
+        if (p.amax) {
+            float amx = 0.f;
+#pragma unroll
+            for (int i = 0; i < 32; ++i) amx = fmaxf(amx, fabsf(v[i]));
+            if (MODE == 1) {
+                // this warpgroup's half of the h_pid row (16-bit, as the PID stack wrote it)
+                const uint4* src = (const uint4*)(p.hp + (size_t)prow_pad * D + 32 * wg);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const uint4 u = src[c];
+                    float a, b;
+                    unpack2<F16>(u.x, a, b); amx = fmaxf(amx, fmaxf(fabsf(a), fabsf(b)));
+                    unpack2<F16>(u.y, a, b); amx = fmaxf(amx, fmaxf(fabsf(a), fabsf(b)));
+                    unpack2<F16>(u.z, a, b); amx = fmaxf(amx, fmaxf(fabsf(a), fabsf(b)));
+                    unpack2<F16>(u.w, a, b); amx = fmaxf(amx, fmaxf(fabsf(a), fabsf(b)));
+                }
+            }
+            record_amax(p.amax, p.slot[0], &amx, 1, ri.valid);
+        }
+        if (TMA_HP && tid == 0) fail |= !mbar_wait(&bars[1], aph, ab, p.status, ST_TIMEOUT_GEMM, p.wait_ns);
+        aph ^= 1;
+        // embedding FFN, first layer
+        if (!run_mma([&] { issue_gemm<FE>(tbase, sA, sW1, 64, KA); })) break;
+        tmem_ld32(trow + 32 * wg, v);
+        tmem_wait_ld();
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = act_f(v[i] + __ldg(p.b1 + 32 * wg + i), p.act);
+        if (p.amax) record_amax(p.amax, p.slot[1], v, 32, ri.valid);
+        st_op<FE>(sH, r, v, 32, 32 * wg, 1.f);
+        // second layer: the residual stream, then LN1
+        if (!run_mma([&] { issue_gemm<FE>(tbase, sH, sW2, 64, 1); })) break;
+        tmem_ld32(trow + 32 * wg, v);
+        tmem_wait_ld();
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] += __ldg(p.b2 + 32 * wg + i);
+        {
+            float4* zd = (float4*)(p.z + (size_t)prow_pad * D + 32 * wg);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) zd[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+        }
+        layernorm_split(v, v, p.lng, p.lnb, wg, r, 0, red);
+        if (p.amax) record_amax(p.amax, p.slot[2], v, 32, ri.valid);
+        st_op<FMT>(sH, r, v, 32, 32 * wg, p.qs[2], true);
+        // fused Q/K/V projection: warpgroup 0 stores Q and V^T columns 0-31,
+        // warpgroup 1 stores K and V^T columns 32-63
+        if (!run_mma([&] { issue_gemm<FMT>(tbase, sH, sWq, 192, 1); })) break;
+        {
+            const float ds = p.ds[2];
+            float u[32];
+            uint16_t* dst = (wg == 0 ? p.q : p.k) + (size_t)prow_pad * D;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                tmem_ld32(trow + 64 * wg + 32 * h, u);
+                tmem_wait_ld();
+#pragma unroll
+                for (int i = 0; i < 32; ++i) u[i] = fmaf(u[i], ds, __ldg(p.bqkv + 64 * wg + 32 * h + i));
+                uint4* d4 = (uint4*)(dst + 32 * h);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    uint4 w4;
+                    w4.x = pack2<F16>(u[8 * c + 0], u[8 * c + 1]);
+                    w4.y = pack2<F16>(u[8 * c + 2], u[8 * c + 3]);
+                    w4.z = pack2<F16>(u[8 * c + 4], u[8 * c + 5]);
+                    w4.w = pack2<F16>(u[8 * c + 6], u[8 * c + 7]);
+                    d4[c] = w4;
+                }
+            }
+            tmem_ld32(trow + 128 + 32 * wg, u);
+            tmem_wait_ld();
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+                const int ch = 32 * wg + i;
+                const float t = ri.valid ? fmaf(u[i], ds, __ldg(p.bqkv + 128 + ch)) : 0.f;
+                p.vt[(size_t)ch * p.ldvt + prow_pad] = (uint16_t)(pack2<F16>(t, 0.f) & 0xffffu);
+            }
+        }
+        tc_fence_before();
+    }
+    __syncthreads();
+    if (*ab && tid == 0) {
+        for (int i = 0; i < 1000; ++i) __nanosleep(1000);  // let in-flight copies land
+    }
+    __syncthreads();
+    if (tid < 32) {
+        tc_fence_after();
+        tmem_dealloc(tbase, 256);
+    }
 }
 
 template <int MODE, int FMT>  // 0: next layer LN1 + QKV; 1: end of PID stack; 2: end of regression stack
@@ -1929,7 +1967,7 @@ __global__ void k_eval_act_tc(const float* __restrict__ x, float* __restrict__ y
 uint32_t embed_smem(int mode, int fmt) {
     (void)fmt;
     const int ka = mode == 0 ? 1 : 2;
-    const uint32_t need = 64 * 128 * ka + 64 * 128 + 192 * 128 + ka * ATOM + ATOM + 64 + 1024;
+    const uint32_t need = 64 * 128 * ka + 64 * 128 + 192 * 128 + ka * ATOM + ATOM + 2 * 2 * 128 * 4 + 64 + 1024;
     // at least 80 KB so that no more than two CTAs (2 x 256 TMEM columns) share an SM
     return need < 80 * 1024 ? 80 * 1024 : need;
 }
@@ -2031,8 +2069,8 @@ std::string check_occupancy() {
                       occupancy(k_post<0, FMT>, PT_THREADS, post_smem(0, FMT)),
                       occupancy(k_post<1, FMT>, PT_THREADS, post_smem(1, FMT)),
                       occupancy(k_post<2, FMT>, PT_THREADS, post_smem(2, FMT)),
-                      occupancy(k_embed_qkv<0, FMT>, 128, embed_smem(0, FMT)),
-                      occupancy(k_embed_qkv<1, FMT>, 128, embed_smem(1, FMT))};
+                      occupancy(k_embed_qkv<0, FMT>, EM_THREADS, embed_smem(0, FMT)),
+                      occupancy(k_embed_qkv<1, FMT>, EM_THREADS, embed_smem(1, FMT))};
     if (o[0] >= 1 && o[1] >= 1 && o[2] >= 1 && o[3] >= 1 && o[4] >= 1 && o[4] <= 2 && o[5] >= 1 &&
         o[5] <= 2)
         return "";
@@ -2182,8 +2220,8 @@ bool tc_prepare_weights(Model& m) {
         attrs = true;
     }
     if (cudaGetLastError() != cudaSuccess) { set_error("kernel attribute setup"); return false; }
-    m.embed_ctas_per_sm = std::max(1, std::min(occupancy(k_embed_qkv<1, FMT_BF16>, 128, embed_smem(1, FMT_BF16)),
-                                               occupancy(k_embed_qkv<1, FMT_FP16>, 128, embed_smem(1, FMT_FP16))));
+    m.embed_ctas_per_sm = std::max(1, std::min(occupancy(k_embed_qkv<1, FMT_BF16>, EM_THREADS, embed_smem(1, FMT_BF16)),
+                                               occupancy(k_embed_qkv<1, FMT_FP16>, EM_THREADS, embed_smem(1, FMT_FP16))));
     const std::string occ = check_occupancy<FMT_BF16>() + check_occupancy<FMT_FP16>() + check_occupancy<FMT_E4M3>();
     if (!occ.empty()) {
         cudaGetLastError();
@@ -2293,9 +2331,9 @@ static int64_t run_tc(Model& m, const float* x, const int32_t* cu, int n_events,
         ep.slot[2] = act_slot(m, s_ln);
         prof_begin(m, st, mode == 0 ? "embed_qkv" : "reg_embed_qkv");
         if (mode == 0)
-            k_embed_qkv<0, FMT><<<grid * m.embed_ctas_per_sm, 128, embed_smem(0, FMT), st>>>(w.map_hp, ep);
+            k_embed_qkv<0, FMT><<<grid * m.embed_ctas_per_sm, EM_THREADS, embed_smem(0, FMT), st>>>(w.map_hp, ep);
         else
-            k_embed_qkv<1, FMT><<<grid * m.embed_ctas_per_sm, 128, embed_smem(1, FMT), st>>>(w.map_hp, ep);
+            k_embed_qkv<1, FMT><<<grid * m.embed_ctas_per_sm, EM_THREADS, embed_smem(1, FMT), st>>>(w.map_hp, ep);
         prof_end(m, st);
         ++n;
     };
