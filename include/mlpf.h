@@ -283,11 +283,13 @@ enum {
                                        head, PV partial folded one tile late:
                                          4 = 4 stages, 6 = 6 stages;
                                        warp-level MMAs, each warp 32 rows of one head:
-                                         7 = 4 stages, 8 = 8 stages (default) */
+                                         7 = 4 stages, 8 = 8 stages (default);
+                                       the same on 64-row half items, two CTAs per SM,
+                                       4 stages: 9 */
     MLPF_OPT_ATTN_VARIANT_FP16 = 8,
     MLPF_OPT_ATTN_VARIANT_FP8 = 9
 };
-#define MLPF_ATTN_VARIANTS 9
+#define MLPF_ATTN_VARIANTS 10
 mlpf_status mlpf_set_option(mlpf_model* m, int32_t option, int64_t value);
 mlpf_status mlpf_get_option(const mlpf_model* m, int32_t option, int64_t* value);
 

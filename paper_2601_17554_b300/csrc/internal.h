@@ -63,7 +63,7 @@ struct Workspace {
     int4* blk = nullptr;                 // per 64-row block: event, packed row, n valid
     int4* items = nullptr;               // attention work items
     int* counters = nullptr;             // [0]=n_items [1]=tpad rows [2..3]=attn tickets
-    CUtensorMap map_q, map_k, map_o, map_vt, map_hp;
+    CUtensorMap map_q, map_q64, map_k, map_o, map_vt, map_hp;
     // host-buffer entry point: device staging
     float *hx = nullptr, *hlogits = nullptr, *hreg_out = nullptr;
     int32_t *hcu = nullptr, *hcls = nullptr;

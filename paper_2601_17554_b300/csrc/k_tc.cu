@@ -1001,6 +1001,8 @@ __global__ void __launch_bounds__(at_threads<HPW>(), 1)
     k_attention(const __grid_constant__ CUtensorMap map_q, const __grid_constant__ CUtensorMap map_k,
                 const __grid_constant__ CUtensorMap map_vt, AttnParams p) {
     constexpr int AT_WG = at_wg<HPW>(), AT_THREADS = at_threads<HPW>(), AT_STAGES = ST;
+    constexpr int QR = ROWS;          // query rows per work item
+    constexpr uint32_t QB = AT_QB;    // Q tile bytes
     using LY = AtLayout<ST>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sm = align1024(smem_raw);
@@ -1066,20 +1068,28 @@ __global__ void __launch_bounds__(at_threads<HPW>(), 1)
             uint32_t g = 0;
             bool ok = true;
             while (ok) {
-                const int item = atomicAdd(ticket, 1);
+                // a ticket is an item (QR = 128) or half of one (QR = 64; halves
+                // without query rows are skipped)
+                const int t = atomicAdd(ticket, 1);
+                const int item = QR == 128 ? t : t >> 1, half = QR == 128 ? 0 : t & 1;
+                int4 it = make_int4(-1, 0, 0, 0);
+                if (item < n_items) {
+                    it = p.items[item];
+                    it.w = half;
+                    if (it.z - it.y * ROWS - QR * half <= 0) continue;
+                }
                 const int qb = q_it & 1;
                 if (q_it >= 2 &&
                     !mbar_wait(&q_empty[qb], ((q_it >> 1) - 1) & 1, ab, p.status, ST_TIMEOUT_ATTN, p.wait_ns))
                     break;
                 if (item >= n_items) {
-                    info[qb] = make_int4(-1, 0, 0, 0);
+                    info[qb] = it;
                     mbar_arrive(&q_full[qb]);
                     break;
                 }
-                const int4 it = p.items[item];
                 info[qb] = it;
-                mbar_arrive_expect_tx(&q_full[qb], AT_QB);
-                tma_load_2d(sQ + qb * AT_QB, &map_q, 0, it.x + it.y * ROWS, &q_full[qb]);
+                mbar_arrive_expect_tx(&q_full[qb], QB);
+                tma_load_2d(sQ + qb * QB, &map_q, 0, it.x + it.y * ROWS + QR * half, &q_full[qb]);
                 const int nk = (it.z + 63) >> 6;
                 for (int j = 0; j < nk; ++j, ++g) {
                     const int s = (int)(g % AT_STAGES);
@@ -1391,6 +1401,8 @@ __global__ void __launch_bounds__(A32_THREADS, 1)
     k_attention32(const __grid_constant__ CUtensorMap map_q, const __grid_constant__ CUtensorMap map_k,
                   const __grid_constant__ CUtensorMap map_vt, AttnParams p) {
     // ST: 64-key K/V stages
+    constexpr int QR = ROWS;          // query rows per work item
+    constexpr uint32_t QB = AT_QB;    // Q tile bytes
     using LY = At32Layout<ST>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sm = align1024(smem_raw);
@@ -1454,20 +1466,28 @@ __global__ void __launch_bounds__(A32_THREADS, 1)
             uint32_t g = 0;
             bool ok = true;
             while (ok) {
-                const int item = atomicAdd(ticket, 1);
+                // a ticket is an item (QR = 128) or half of one (QR = 64; halves
+                // without query rows are skipped)
+                const int t = atomicAdd(ticket, 1);
+                const int item = QR == 128 ? t : t >> 1, half = QR == 128 ? 0 : t & 1;
+                int4 it = make_int4(-1, 0, 0, 0);
+                if (item < n_items) {
+                    it = p.items[item];
+                    it.w = half;
+                    if (it.z - it.y * ROWS - QR * half <= 0) continue;
+                }
                 const int qb = q_it & 1;
                 if (q_it >= 2 &&
                     !mbar_wait(&q_empty[qb], ((q_it >> 1) - 1) & 1, ab, p.status, ST_TIMEOUT_ATTN, p.wait_ns))
                     break;
                 if (item >= n_items) {
-                    info[qb] = make_int4(-1, 0, 0, 0);
+                    info[qb] = it;
                     mbar_arrive(&q_full[qb]);
                     break;
                 }
-                const int4 it = p.items[item];
                 info[qb] = it;
-                mbar_arrive_expect_tx(&q_full[qb], AT_QB);
-                tma_load_2d(sQ + qb * AT_QB, &map_q, 0, it.x + it.y * ROWS, &q_full[qb]);
+                mbar_arrive_expect_tx(&q_full[qb], QB);
+                tma_load_2d(sQ + qb * QB, &map_q, 0, it.x + it.y * ROWS + QR * half, &q_full[qb]);
                 const int nk = (it.z + 63) >> 6;
                 for (int j = 0; j < nk; ++j, ++g) {
                     const int s = (int)(g % ST);
@@ -1660,12 +1680,15 @@ __global__ void __launch_bounds__(A32_THREADS, 1)
 // kernel is bound by the softmax; a 128-row tcgen05 MMA would tie the four
 // warps of a warpgroup together at every key tile.  Here each warp owns 32
 // query rows of one head end to end: S comes out of the MMA in registers, the
-// exponentials (FP32) are packed straight into the A fragments of the PV MMA
-// and summed in FP32 for the row sums, so the warps meet only at the K/V stage
-// barriers.  Softmax rescaling is lazy: the
-// exponent reference of a row is raised (and O, l rescaled) only when a
-// 16-key step exceeds it by more than kStaleMax, so P <= 2^kStaleMax.
-constexpr int AW_THREADS = NH * 4 * 32 + 32;   // 16 consumer warps + a TMA producer warp
+// exponentials are packed straight into the A fragments of the PV MMA, and the
+// row sums are one more MMA against a constant block of ones, so the warps
+// meet only at the K/V stage barriers.  Softmax rescaling is lazy: the exponent
+// reference of a row is raised (and O, l rescaled) only when a 16-key step
+// exceeds it by more than kStaleMax, so P <= 2^kStaleMax.
+// QR: query rows per work item, 128 (one CTA per SM, 16 consumer warps) or 64
+// (half items, two CTAs per SM of 8 consumer warps).
+template <int QR>
+constexpr int aw_threads() { return NH * (QR / 32) * 32 + 32; }   // consumer warps + a TMA producer warp
 // Mode bits of the warp kernel (each measured on the 512-event batch):
 //   1 row sums from FP32 adds instead of the ones-MMA (slower: off)
 //   2 exponentials before the maxima check, redone on a raised reference
@@ -1674,21 +1697,24 @@ constexpr int AW_THREADS = NH * 4 * 32 + 32;   // 16 consumer warps + a TMA prod
 //     raw-score thresholds (5-7 % faster: on)
 template <bool F16>
 constexpr int kAwMode = F16 ? 6 : 4;
-template <int ST>
+template <int ST, int QR = 128>
 struct AwLayout {
-    static constexpr uint32_t OFF_K = 2 * AT_QB;
+    static constexpr uint32_t QB = QR * 128;   // Q tile bytes
+    static constexpr uint32_t OFF_K = 2 * QB;
     static constexpr uint32_t OFF_V = OFF_K + ST * AT_KB;
     static constexpr uint32_t OFF_BAR = OFF_V + ST * AT_VB;
     static constexpr uint32_t SMEM = OFF_BAR + 512 + 1024;
 };
 
-template <bool F16, int ST, int AM>
-__global__ void __launch_bounds__(AW_THREADS, 1)
+template <bool F16, int ST, int AM, int QR = 128>
+__global__ void __launch_bounds__(aw_threads<QR>(), QR == 128 ? 1 : 2)
     k_attention_warp(const __grid_constant__ CUtensorMap map_q, const __grid_constant__ CUtensorMap map_k,
                      const __grid_constant__ CUtensorMap map_vt, AttnParams p) {
-    constexpr int NW = NH * 4;   // consumer warps
+    constexpr int RB = QR / 32;   // 32-row blocks (one per warp) per item
+    constexpr int NW = NH * RB;   // consumer warps
     constexpr bool kSumF32 = AM & 1, kOptimistic = AM & 2, kHoist = AM & 4;
-    using LY = AwLayout<ST>;
+    constexpr uint32_t QB = AwLayout<ST, QR>::QB;
+    using LY = AwLayout<ST, QR>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sm = align1024(smem_raw);
     uint8_t* sQ = sm;
@@ -1726,20 +1752,28 @@ __global__ void __launch_bounds__(AW_THREADS, 1)
             uint32_t g = 0;
             bool ok = true;
             while (ok) {
-                const int item = atomicAdd(ticket, 1);
+                // a ticket is an item (QR = 128) or half of one (QR = 64; halves
+                // without query rows are skipped)
+                const int t = atomicAdd(ticket, 1);
+                const int item = QR == 128 ? t : t >> 1, half = QR == 128 ? 0 : t & 1;
+                int4 it = make_int4(-1, 0, 0, 0);
+                if (item < n_items) {
+                    it = p.items[item];
+                    it.w = half;
+                    if (it.z - it.y * ROWS - QR * half <= 0) continue;
+                }
                 const int qb = q_it & 1;
                 if (q_it >= 2 &&
                     !mbar_wait(&q_empty[qb], ((q_it >> 1) - 1) & 1, ab, p.status, ST_TIMEOUT_ATTN, p.wait_ns))
                     break;
                 if (item >= n_items) {
-                    info[qb] = make_int4(-1, 0, 0, 0);
+                    info[qb] = it;
                     mbar_arrive(&q_full[qb]);
                     break;
                 }
-                const int4 it = p.items[item];
                 info[qb] = it;
-                mbar_arrive_expect_tx(&q_full[qb], AT_QB);
-                tma_load_2d(sQ + qb * AT_QB, &map_q, 0, it.x + it.y * ROWS, &q_full[qb]);
+                mbar_arrive_expect_tx(&q_full[qb], QB);
+                tma_load_2d(sQ + qb * QB, &map_q, 0, it.x + it.y * ROWS + QR * half, &q_full[qb]);
                 const int nk = (it.z + 63) >> 6;
                 for (int j = 0; j < nk; ++j, ++g) {
                     const int s = (int)(g % ST);
@@ -1759,7 +1793,7 @@ __global__ void __launch_bounds__(AW_THREADS, 1)
         // ------------------------------------------------ warp: head h, query rows 32 rb .. 32 rb + 31
         // Fragments (m16n8k16): lane = 4 gq + tq; an accumulator holds rows gq
         // and gq + 8 of its 16-row tile at columns 2 tq, 2 tq + 1.
-        const int h = warp >> 2, rb = warp & 3;
+        const int h = warp / RB, rb = warp % RB;
         const int gq = lane >> 2, tq = lane & 3;
         const int mi = lane >> 3;                    // ldmatrix: matrix this lane addresses
         const float c = 0.25f * 1.4426950408889634f;  // log2(e) / sqrt(16)
@@ -1789,7 +1823,7 @@ __global__ void __launch_bounds__(AW_THREADS, 1)
 #pragma unroll
             for (int mt = 0; mt < 2; ++mt) {
                 const int row = rb * 32 + mt * 16 + (lane & 15);
-                ldsm_x4(sQa + qb * AT_QB + sw128_off(row, 2 * h + (lane >> 4)), qa[mt][0], qa[mt][1], qa[mt][2],
+                ldsm_x4(sQa + qb * QB + sw128_off(row, 2 * h + (lane >> 4)), qa[mt][0], qa[mt][1], qa[mt][2],
                         qa[mt][3]);
             }
             __syncwarp();
@@ -1927,8 +1961,8 @@ __global__ void __launch_bounds__(AW_THREADS, 1)
                 if (lane == 0) mbar_arrive(&kv_empty[s]);
             }
             if (!ok) break;
-            const int qrow0 = it.x + it.y * ROWS;
-            const int nrows = min(ROWS, it.z - it.y * ROWS);
+            const int qrow0 = it.x + it.y * ROWS + QR * it.w;   // it.w: half of the item (QR = 64)
+            const int nrows = min(QR, it.z - it.y * ROWS - QR * it.w);
 #pragma unroll
             for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
@@ -2056,16 +2090,17 @@ int occupancy(K kernel, int threads, uint32_t smem) {
 // empty string or a description of the kernels that do not fit.
 template <int FMT>
 std::string check_occupancy() {
-    const int o_att[9] = {occupancy(k_attention<kOutF16<FMT>, 1, 4>, at_threads<1>(), AtLayout<4>::SMEM),
+    const int o_att[10] = {occupancy(k_attention<kOutF16<FMT>, 1, 4>, at_threads<1>(), AtLayout<4>::SMEM),
                           occupancy(k_attention<kOutF16<FMT>, 1, 2>, at_threads<1>(), AtLayout<2>::SMEM),
                           occupancy(k_attention<kOutF16<FMT>, 2, 4>, at_threads<2>(), AtLayout<4>::SMEM),
                           occupancy(k_attention<kOutF16<FMT>, 2, 2>, at_threads<2>(), AtLayout<2>::SMEM),
                           occupancy(k_attention32<kOutF16<FMT>, 4>, A32_THREADS, At32Layout<4>::SMEM),
                           occupancy(k_attention<kOutF16<FMT>, 1, 6>, at_threads<1>(), AtLayout<6>::SMEM),
                           occupancy(k_attention32<kOutF16<FMT>, 6>, A32_THREADS, At32Layout<6>::SMEM),
-                          occupancy(k_attention_warp<kOutF16<FMT>, 4, kAwMode<kOutF16<FMT>>>, AW_THREADS, AwLayout<4>::SMEM),
-                          occupancy(k_attention_warp<kOutF16<FMT>, 8, kAwMode<kOutF16<FMT>>>, AW_THREADS, AwLayout<8>::SMEM)};
-    const int o[6] = {*std::min_element(o_att, o_att + 9),
+                          occupancy(k_attention_warp<kOutF16<FMT>, 4, kAwMode<kOutF16<FMT>>>, aw_threads<128>(), AwLayout<4>::SMEM),
+                          occupancy(k_attention_warp<kOutF16<FMT>, 8, kAwMode<kOutF16<FMT>>>, aw_threads<128>(), AwLayout<8>::SMEM),
+                          occupancy(k_attention_warp<kOutF16<FMT>, 4, kAwMode<kOutF16<FMT>>, 64>, aw_threads<64>(), AwLayout<4, 64>::SMEM) / 2};
+    const int o[6] = {*std::min_element(o_att, o_att + 10),
                       occupancy(k_post<0, FMT>, PT_THREADS, post_smem(0, FMT)),
                       occupancy(k_post<1, FMT>, PT_THREADS, post_smem(1, FMT)),
                       occupancy(k_post<2, FMT>, PT_THREADS, post_smem(2, FMT)),
@@ -2095,6 +2130,7 @@ void set_attrs() {
     cudaFuncSetAttribute(k_attention32<kOutF16<FMT>, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, At32Layout<6>::SMEM);
     cudaFuncSetAttribute(k_attention_warp<kOutF16<FMT>, 4, kAwMode<kOutF16<FMT>>>, cudaFuncAttributeMaxDynamicSharedMemorySize, AwLayout<4>::SMEM);
     cudaFuncSetAttribute(k_attention_warp<kOutF16<FMT>, 8, kAwMode<kOutF16<FMT>>>, cudaFuncAttributeMaxDynamicSharedMemorySize, AwLayout<8>::SMEM);
+    cudaFuncSetAttribute(k_attention_warp<kOutF16<FMT>, 4, kAwMode<kOutF16<FMT>>, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, AwLayout<4, 64>::SMEM);
 }
 
 }  // namespace
@@ -2234,7 +2270,8 @@ bool tc_prepare_weights(Model& m) {
 bool tc_make_maps(Model& m) {
     Workspace& w = m.ws;
     const uint64_t T = (uint64_t)w.cap_tpad;
-    bool ok = make_map_16(&w.map_q, w.tq, 64, T, 64, 128) && make_map_16(&w.map_k, w.tk, 64, T, 64, 64) &&
+    bool ok = make_map_16(&w.map_q, w.tq, 64, T, 64, 128) && make_map_16(&w.map_q64, w.tq, 64, T, 64, 64) &&
+              make_map_16(&w.map_k, w.tk, 64, T, 64, 64) &&
               make_map_16(&w.map_o, w.to, 64, T, 64, 128) && make_map_16(&w.map_vt, w.tvt, T, 64, 64, 64) &&
               make_map_16(&w.map_hp, w.thp, 64, T, 64, 128);
     if (!ok) set_error("cuTensorMapEncodeTiled failed");
@@ -2288,8 +2325,9 @@ static int64_t run_tc(Model& m, const float* x, const int32_t* cu, int n_events,
             case 4: k_attention32<AF, 4><<<g, A32_THREADS, At32Layout<4>::SMEM, st>>>(w.map_q, w.map_k, w.map_vt, ap); break;
             case 5: k_attention<AF, 1, 6><<<g, at_threads<1>(), AtLayout<6>::SMEM, st>>>(w.map_q, w.map_k, w.map_vt, ap); break;
             case 6: k_attention32<AF, 6><<<g, A32_THREADS, At32Layout<6>::SMEM, st>>>(w.map_q, w.map_k, w.map_vt, ap); break;
-            case 7: k_attention_warp<AF, 4, kAwMode<AF>><<<g, AW_THREADS, AwLayout<4>::SMEM, st>>>(w.map_q, w.map_k, w.map_vt, ap); break;
-            case 8: k_attention_warp<AF, 8, kAwMode<AF>><<<g, AW_THREADS, AwLayout<8>::SMEM, st>>>(w.map_q, w.map_k, w.map_vt, ap); break;
+            case 7: k_attention_warp<AF, 4, kAwMode<AF>><<<g, aw_threads<128>(), AwLayout<4>::SMEM, st>>>(w.map_q, w.map_k, w.map_vt, ap); break;
+            case 8: k_attention_warp<AF, 8, kAwMode<AF>><<<g, aw_threads<128>(), AwLayout<8>::SMEM, st>>>(w.map_q, w.map_k, w.map_vt, ap); break;
+            case 9: k_attention_warp<AF, 4, kAwMode<AF>, 64><<<2 * g.x, aw_threads<64>(), AwLayout<4, 64>::SMEM, st>>>(w.map_q64, w.map_k, w.map_vt, ap); break;
             default: k_attention<AF, 1, 4><<<g, at_threads<1>(), AtLayout<4>::SMEM, st>>>(w.map_q, w.map_k, w.map_vt, ap); break;
         }
         prof_end(m, st);

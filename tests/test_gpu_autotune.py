@@ -3,7 +3,8 @@
 Variants in one group run the same per-head arithmetic in the same order and
 must be bit-identical: the tcgen05 kernels with 64-key score tiles (one or two
 heads per warpgroup, two to six K/V stages), the tcgen05 kernels with 32-key
-tiles, and the warp-level-MMA kernels (four or eight stages).  Groups differ in
+tiles, and the warp-level-MMA kernels (four or eight stages, 128- or 64-row
+items).  Groups differ in
 summation order and exponent references: each must meet the oracle bounds of
 the precision and stay close to variant 0.  The autotuner must pick a valid
 variant, write its cache line and reuse it.
@@ -18,8 +19,8 @@ from tests.util import make_model, rel_err_cols, run_gpu
 pytestmark = pytest.mark.gpu
 
 SIZES = [1, 17, 64, 65, 129, 300, 0, 511, 1024, 2]
-N_VARIANTS = 9
-GROUPS = ((0, 1, 2, 3, 5), (4, 6), (7, 8))
+N_VARIANTS = 10
+GROUPS = ((0, 1, 2, 3, 5), (4, 6), (7, 8, 9))
 
 
 @pytest.fixture(scope="module")
