@@ -151,8 +151,9 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def attention_traffic():
-    """Per-launch DRAM bytes of the attention kernel from the committed ncu summary."""
+def attention_traffic(variant, precision):
+    """Per-launch DRAM bytes of the attention kernel variant from the committed ncu
+    summary (keys bytes_per_launch_<precision>_variant_<n>), else None."""
     p = os.path.join(ROOT, "profiles", "attention_warp_batch512_traffic.txt")
     if not os.path.exists(p):
         return None
@@ -162,7 +163,7 @@ def attention_traffic():
             k, v = ln.split(":", 1)
             vals[k.strip()] = v.strip()
     try:
-        return float(vals["bytes_per_launch_full_workload"])
+        return float(vals[f"bytes_per_launch_{precision}_variant_{variant}"])
     except (KeyError, ValueError):
         return None
 
@@ -348,9 +349,11 @@ def run_ours(args):
     if att_ms:
         ach = exps / (att_ms / 1000.0)
         exp_peak = unit_rates["ex2_per_s"]
-        roof = {"kernel": "k_attention_warp", "bound": "alu", "achieved": ach / 1e9,
+        kname = {7: "k_attention_warp", 8: "k_attention_warp", 9: "k_attention_warp (64-row items)",
+                 4: "k_attention32", 6: "k_attention32"}.get(attn_variant, "k_attention")
+        roof = {"kernel": kname, "attn_variant": attn_variant, "bound": "alu", "achieved": ach / 1e9,
                 "peak": exp_peak / 1e9, "unit": "Gexp/s", "frac": ach / exp_peak,
-                "traffic": attention_traffic(),
+                "traffic": attention_traffic(attn_variant, prec),
                 "peak_source": "measured: mlpf_measure_unit_rates (ex2.approx.f32 results/s on this GPU, "
                                "best of 3, timed alone)",
                 "launch_ms": att_ms,
