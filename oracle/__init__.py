@@ -13,5 +13,6 @@ from .forward import (  # noqa: F401
     layer_norm, gelu, relu, linear, softmax_rows, sdpa, attention_matrix,
     multi_head_attention, encoder_block, encoder_stack, embed, reg_embed,
     ffn_head, forward_event, decode, event_sums, forward, OracleOutput, is_track, embed_per_type,
-    raw_from_decoded, log_softmax_rows, distill_loss,
+    raw_from_decoded, log_softmax_rows, distill_loss, supervised_loss, softplus,
+    SUP_BETA, SUP_FOCAL, SUP_DELTA,
 )

@@ -341,3 +341,56 @@ def distill_loss(W, cfg, x, cu_seqlens, t_logits, t_reg):
     kl = (np.exp(lt) * (lt - ls)).sum(axis=1)
     mse = ((out.raw - raw_from_decoded(x, t_reg)) ** 2).sum(axis=1)
     return float((kl + mse).mean())
+
+
+# ------------------------------------------------------- supervised loss (Eq. 1)
+
+# readings of the points the paper leaves open:
+SUP_BETA = 0.01      # weight of the binary term: the later, more specific value (Sec. 5.3)
+SUP_FOCAL = 2.0      # focusing parameter of the focal loss (unstated; the value of Lin et al.)
+SUP_DELTA = 1.0      # weight of the angular regression terms (unstated)
+
+
+def softplus(z):
+    z = np.asarray(z, F64)
+    return np.maximum(z, 0.0) + np.log1p(np.exp(-np.abs(z)))
+
+
+def supervised_loss(x, logits, raw, cls_target, reg_target, beta=SUP_BETA, focal=SUP_FOCAL,
+                    delta=SUP_DELTA):
+    """Per-element loss of Eq. 1 for the printed architecture, averaged over elements.
+
+    logits [T, 6]: binary logit, then the 5 PID logits; raw [T, 5]: (pT', eta, sin phi,
+    cos phi, E'); cls_target [T]: 0 = no target particle, k = 1..5 = particle of PID
+    class k; reg_target [T, 5]: the target particle's (pT, eta, sin phi, cos phi, E).
+
+      L_i = beta BCE(b_i, sigmoid(z_i))
+            + b_i [ FL(k_i) + g_i (dpT'^2 + dE'^2) + delta (deta^2 + dsin^2 + dcos^2) ]
+    b_i = [cls_target > 0]; BCE = softplus(z) - b z; the focal loss (Lin et al. 2017)
+    FL = -(1 - p_t)^focal log p_t with p_t the PID softmax probability of the target
+    class; pT' and E' targets from Eq. 2 (log of the target over the element's value);
+    g_i = sqrt(pT target) (Sec. 5.3).
+
+    reading: the PID and regression terms apply to elements that have a target
+    particle only; the sum over elements is divided by their number.
+    """
+    x = np.asarray(x, F64)
+    lg = np.asarray(logits, F64)
+    raw = np.asarray(raw, F64)
+    k = np.asarray(cls_target, np.int64)
+    b = (k > 0).astype(F64)
+    z = lg[:, 0]
+    bce = softplus(z) - b * z
+    lp = log_softmax_rows(lg[:, 1:])
+    kk = np.clip(k - 1, 0, 4)
+    logpt = lp[np.arange(len(k)), kk]
+    fl = -((1.0 - np.exp(logpt)) ** focal) * logpt
+    reg_target = np.asarray(reg_target, F64)
+    ok = k > 0
+    rt = np.zeros_like(raw)
+    rt[ok] = raw_from_decoded(x[ok], reg_target[ok])
+    g = np.sqrt(np.where(ok, reg_target[:, 0], 1.0))
+    d2 = (raw - rt) ** 2
+    lreg = g * (d2[:, 0] + d2[:, 4]) + delta * (d2[:, 1] + d2[:, 2] + d2[:, 3])
+    per = beta * bce + b * (fl + lreg)
+    return float(per.mean())

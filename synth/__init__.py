@@ -312,6 +312,57 @@ def pack_blob(cfg: ModelConfig, weights) -> bytes:
 
 
 # --------------------------------------------------------------------------
+# synthetic targets (supervised training without the CMS samples)
+# --------------------------------------------------------------------------
+
+STREAM_TARGET = 4
+# P(target class | element type): rows = types (track, ECAL, HCAL, HF-EM, HF-HAD,
+# GSF track, brem, supercluster), columns = classes (none, ch. hadron, n. hadron,
+# photon, electron, muon).  Chosen so that the class is learnable from the type.
+TARGET_CLASS_PROBS = np.array([
+    [0.15, 0.70, 0.00, 0.00, 0.10, 0.05],
+    [0.40, 0.00, 0.00, 0.60, 0.00, 0.00],
+    [0.40, 0.00, 0.60, 0.00, 0.00, 0.00],
+    [0.50, 0.00, 0.00, 0.50, 0.00, 0.00],
+    [0.50, 0.00, 0.50, 0.00, 0.00, 0.00],
+    [0.30, 0.00, 0.00, 0.00, 0.70, 0.00],
+    [0.50, 0.00, 0.00, 0.50, 0.00, 0.00],
+    [0.40, 0.00, 0.00, 0.60, 0.00, 0.00]])
+
+
+def gen_targets(seed: int, x, cu_seqlens, first_event: int = 0):
+    """Synthetic per-element targets for the supervised loss: cls [T] int32 (0 = no
+    target particle, 1..5 PID class) drawn from TARGET_CLASS_PROBS by element type,
+    and reg [T, 5] float32 (pT, eta, sin phi, cos phi, E): the element's own values
+    perturbed by N(0, 0.3) in log pT and log E and N(0, 0.05) in eta and phi.
+    Element i of event e depends only on (seed, first_event + e, i)."""
+    x = np.asarray(x, np.float32)
+    cu = np.asarray(cu_seqlens, np.int64)
+    sizes = np.diff(cu)
+    total = int(cu[-1])
+    ev = np.repeat(np.arange(len(sizes), dtype=np.uint64) + np.uint64(first_event), sizes)
+    idx = (np.arange(total, dtype=np.int64) - np.repeat(cu[:-1], sizes)).astype(np.uint64)
+    def u(slot):
+        return uniform(seed, STREAM_TARGET, ev, idx, np.uint64(slot))
+    def n(slot):
+        return normal(seed, STREAM_TARGET, ev, idx, np.uint64(slot))
+    cls = np.zeros(total, np.int32)
+    reg = np.zeros((total, 5), np.float32)
+    if total == 0:
+        return cls, reg
+    typ = np.argmax(x[:, :N_TYPES], axis=1)
+    cdf = np.cumsum(TARGET_CLASS_PROBS[typ], axis=1)
+    cls[:] = np.minimum((u(0)[:, None] > cdf).sum(axis=1), N_CLS - 1)
+    phi = np.arctan2(x[:, 11], x[:, 12]) + 0.05 * n(3)
+    reg[:, 0] = np.exp(x[:, 8] + 0.3 * n(1))
+    reg[:, 1] = x[:, 10] + 0.05 * n(2)
+    reg[:, 2] = np.sin(phi)
+    reg[:, 3] = np.cos(phi)
+    reg[:, 4] = np.exp(x[:, 9] + 0.3 * n(4))
+    return cls, reg
+
+
+# --------------------------------------------------------------------------
 # named workloads
 # --------------------------------------------------------------------------
 

@@ -399,3 +399,73 @@ def test_paper_arch_decode_hand_values():
     assert cls.tolist() == [2, 0, 0, 1, 5]
     cls0, _ = oracle.decode(x, logits, raw, arch=0)
     assert cls0.tolist() == [2, 1, 5, 1, 0]   # plain argmax over all six columns
+
+
+# ---------------------------------------------------- supervised loss (Eq. 1)
+
+def test_supervised_loss_hand_value():
+    """Two elements: no target particle with z = 0 (beta log 2 only); a class-2
+    particle with equal PID scores (p_t = 1/5: focal (4/5)^2 log 5), z = 0, and a
+    pT' prediction off by 1 with pT target 4 (sqrt(4) * 1^2 = 2)."""
+    x = np.zeros((2, 42))
+    x[:, 8] = np.log(2.0)   # element pT 2 GeV
+    x[:, 9] = np.log(3.0)   # element E 3 GeV
+    reg_t = np.array([[1.0, 0.0, 0.0, 1.0, 1.0], [4.0, 0.3, 0.6, 0.8, 6.0]])
+    raw = np.zeros((2, 5))
+    raw[1] = [np.log(4.0 / 2.0) + 1.0, 0.3, 0.6, 0.8, np.log(6.0 / 3.0)]
+    logits = np.zeros((2, 6))
+    cls_t = np.array([0, 2])
+    L = oracle.supervised_loss(x, logits, raw, cls_t, reg_t)
+    b = oracle.SUP_BETA
+    expect = (b * np.log(2) + b * np.log(2) + 0.64 * np.log(5) + 2.0) / 2
+    assert abs(L - expect) < 1e-12
+
+
+def test_supervised_loss_special_cases():
+    rng = np.random.default_rng(4)
+    T = 50
+    x = rng.normal(size=(T, 42))
+    logits = rng.normal(size=(T, 6)) * 3
+    raw = rng.normal(size=(T, 5))
+    cls_t = rng.integers(0, 6, size=T)
+    reg_t = np.abs(rng.normal(size=(T, 5))) + 0.1
+    # focusing parameter 0: the PID term is the cross entropy of the 5-way softmax
+    no_reg = dict(delta=0.0)
+    part = raw.copy()
+    ok = cls_t > 0
+    # remove the pT/E regression terms by predicting their targets exactly
+    part[ok, 0] = np.log(reg_t[ok, 0]) - x[ok, 8]
+    part[ok, 4] = np.log(reg_t[ok, 4]) - x[ok, 9]
+    L0 = oracle.supervised_loss(x, logits, part, cls_t, reg_t, beta=0.0, focal=0.0, **no_reg)
+    u = logits[:, 1:]
+    ce = -(u[np.arange(T), np.clip(cls_t - 1, 0, 4)] - np.log(np.exp(u).sum(1)))
+    assert abs(L0 - (ce * ok).mean()) < 1e-12
+    # the binary term alone: -(b log sigmoid + (1 - b) log(1 - sigmoid)), stable at |z| = 50
+    Lb = oracle.supervised_loss(x, logits, part, cls_t, reg_t, beta=1.0, focal=0.0, **no_reg) - L0
+    sg = 1 / (1 + np.exp(-logits[:, 0]))
+    bce = -(ok * np.log(sg) + (~ok) * np.log(1 - sg))
+    assert abs(Lb - bce.mean()) < 1e-12
+    big = logits.copy()
+    big[:, 0] = np.where(ok, -50.0, 50.0)
+    Lbig = oracle.supervised_loss(x, big, part, cls_t, reg_t, beta=1.0, focal=0.0, **no_reg) - L0
+    assert abs(Lbig - 50.0) < 1e-9
+
+
+def test_synthetic_targets():
+    sizes = [3000, 2000, 0, 17]
+    x, cu = synth.gen_events(41, sizes)
+    c1, r1 = synth.gen_targets(7, x, cu)
+    c2, r2 = synth.gen_targets(7, x, cu)
+    np.testing.assert_array_equal(c1, c2)
+    np.testing.assert_array_equal(r1, r2)
+    # the last event regenerated alone gives the same targets
+    c3, r3 = synth.gen_targets(7, x[cu[3]:], [0, 17], first_event=3)
+    np.testing.assert_array_equal(c3, c1[cu[3]:])
+    typ = np.argmax(x[:, :8], 1)
+    for t in (0, 1, 2):
+        f = np.bincount(c1[typ == t], minlength=6) / (typ == t).sum()
+        np.testing.assert_allclose(f, synth.TARGET_CLASS_PROBS[t], atol=0.04)
+    np.testing.assert_allclose(r1[:, 2] ** 2 + r1[:, 3] ** 2, 1.0, atol=1e-6)
+    assert (r1[:, 0] > 0).all() and (r1[:, 4] > 0).all()
+    d = np.log(r1[:, 0]) - x[:, 8]
+    assert abs(d.std() - 0.3) < 0.02
