@@ -224,8 +224,10 @@ mlpf_status mlpf_forward_gated(mlpf_model* student, mlpf_model* teacher, float t
                                int32_t* used_teacher, int32_t* n_fallback, void* stream);
 
 /*
- * Training of a (student) model on per-element outputs of a full model, with
- * hand-written FP32 forward and backward kernels and the LAMB optimizer.
+ * Training of a model with hand-written FP32 forward and backward kernels and the
+ * LAMB optimizer: distillation of a (student) arch-0 model on per-element outputs
+ * of a full model (mlpf_trainer_step), or supervised training of an arch-1 model
+ * on per-element targets (mlpf_trainer_step_supervised).
  *
  * Loss, averaged over the batch's elements: KL(p_teacher || p_student) of the
  * class probabilities plus the sum of squared differences of the 5 raw
@@ -251,6 +253,27 @@ mlpf_status mlpf_trainer_step(mlpf_trainer* t, const float* x, const int32_t* cu
                               int32_t n_events, int32_t total, int32_t max_n,
                               const float* t_logits, const float* t_reg, float lr,
                               int32_t update, float* grads_out, double* loss_out, void* stream);
+
+/*
+ * One supervised training step of a model of the printed architecture (arch 1:
+ * binary + PID heads) on the loss of Eq. 1, averaged over the batch's elements:
+ *   beta BCE(b, sigmoid(z)) + b [ -(1 - p_t)^focal_gamma log p_t
+ *                                 + sqrt(pT_t) (dpT'^2 + dE'^2)
+ *                                 + delta (deta^2 + dsin^2 + dcos^2) ]
+ * with b = [cls_target > 0], p_t the PID softmax probability of class cls_target
+ * (1..5), pT' and E' targets log(target / element value) (Eq. 2).  The paper sets
+ * beta = 0.01 and weights the pT and E terms by sqrt(pT target); focal_gamma and
+ * delta are unstated (2 and 1 are the readings used by the oracle).
+ * cls_target: device [total] int32 in 0..5; reg_target: device [total, 5] fp32
+ * (pT, eta, sin phi, cos phi, E) of the target particle (read where cls > 0).
+ * Other arguments and the update as mlpf_trainer_step.  MLPF_E_UNSUPPORTED for an
+ * arch-0 model.
+ */
+mlpf_status mlpf_trainer_step_supervised(mlpf_trainer* t, const float* x, const int32_t* cu_seqlens,
+                                         int32_t n_events, int32_t total, int32_t max_n,
+                                         const int32_t* cls_target, const float* reg_target, float beta,
+                                         float focal_gamma, float delta, float lr, int32_t update,
+                                         float* grads_out, double* loss_out, void* stream);
 
 /* Current weights as a blob (host buffer of cap bytes, or NULL to query *nbytes). */
 mlpf_status mlpf_trainer_export(const mlpf_trainer* t, void* blob, size_t cap, size_t* nbytes);

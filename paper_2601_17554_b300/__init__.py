@@ -152,7 +152,8 @@ class Model:
 
 
 class Trainer:
-    """Distillation trainer of a model (hand-written FP32 forward/backward kernels, LAMB)."""
+    """Trainer of a model (hand-written FP32 forward/backward kernels, LAMB): distillation
+    (arch 0, step) or the supervised loss of Eq. 1 (arch 1, step_supervised)."""
 
     def __init__(self, blob: bytes, device: int = 0):
         self.L = _lib.load()
@@ -184,6 +185,19 @@ class Trainer:
                                        x.shape[0], int(max_n), _ptr(t_logits), _ptr(t_reg),
                                        float(lr), int(bool(update)), _ptr(grads),
                                        ctypes.byref(loss) if want_loss else None, ctypes.c_void_p(s)))
+        return loss.value if want_loss else None
+
+    def step_supervised(self, x, cu_seqlens, max_n: int, cls_target, reg_target, lr: float,
+                        update: bool = True, grads=None, want_loss: bool = True, beta: float = 0.01,
+                        focal_gamma: float = 2.0, delta: float = 1.0, stream=None):
+        """One step on the loss of Eq. 1 (arch-1 model; device tensors); returns the loss."""
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream(self.device).cuda_stream
+        loss = ctypes.c_double(0.0)
+        check(self.L.mlpf_trainer_step_supervised(
+            self.h, _ptr(x), _ptr(cu_seqlens), cu_seqlens.shape[0] - 1, x.shape[0], int(max_n),
+            _ptr(cls_target), _ptr(reg_target), float(beta), float(focal_gamma), float(delta), float(lr),
+            int(bool(update)), _ptr(grads), ctypes.byref(loss) if want_loss else None, ctypes.c_void_p(s)))
         return loss.value if want_loss else None
 
     def export(self) -> bytes:

@@ -19,7 +19,7 @@ EXPORTS = ("mlpf_load_weights", "mlpf_free", "mlpf_get_config", "mlpf_forward",
            "mlpf_get_fp8_scales", "mlpf_autotune", "mlpf_measure_unit_rates",
            "mlpf_eval_activation", "mlpf_forward_gated", "mlpf_trainer_create",
            "mlpf_trainer_free", "mlpf_trainer_num_params", "mlpf_trainer_step",
-           "mlpf_trainer_export", "mlpf_sync", "mlpf_set_option", "mlpf_get_option",
+           "mlpf_trainer_step_supervised", "mlpf_trainer_export", "mlpf_sync", "mlpf_set_option", "mlpf_get_option",
            "mlpf_last_launch_count", "mlpf_profile_get", "mlpf_last_error", "mlpf_abi_version")
 
 
@@ -79,6 +79,10 @@ def load(build_if_missing: bool = True):
     L.mlpf_trainer_step.argtypes = [vp, vp, vp, i32, i32, i32, vp, vp, ctypes.c_float, i32, vp,
                                     ctypes.POINTER(ctypes.c_double), vp]
     L.mlpf_trainer_step.restype = ctypes.c_int
+    L.mlpf_trainer_step_supervised.argtypes = [vp, vp, vp, i32, i32, i32, vp, vp, ctypes.c_float,
+                                               ctypes.c_float, ctypes.c_float, ctypes.c_float, i32, vp,
+                                               ctypes.POINTER(ctypes.c_double), vp]
+    L.mlpf_trainer_step_supervised.restype = ctypes.c_int
     L.mlpf_trainer_export.argtypes = [vp, vp, sz, ctypes.POINTER(sz)]
     L.mlpf_trainer_export.restype = ctypes.c_int
     L.mlpf_sync.argtypes = [vp, vp]

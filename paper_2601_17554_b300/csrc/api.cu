@@ -415,7 +415,7 @@ mlpf_status mlpf_eval_activation(int32_t impl, int32_t act, const float* x, floa
     return MLPF_OK;
 }
 
-int32_t mlpf_abi_version(void) { return 101; }
+int32_t mlpf_abi_version(void) { return 102; }
 
 const char* mlpf_last_error(void) { return g_last_error.c_str(); }
 

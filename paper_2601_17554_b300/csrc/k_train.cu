@@ -394,6 +394,102 @@ __global__ void __launch_bounds__(256) k_distill_loss(const float* __restrict__ 
     }
 }
 
+// Supervised loss of Eq. 1 (printed architecture: logits = [binary, 5 PID]) and
+// its gradient w.r.t. the logits and raw outputs, per element, mean over T:
+//   beta BCE(b, sigmoid(z)) + b [ -(1 - p_t)^fg log p_t
+//                                 + g (dpT'^2 + dE'^2) + delta (deta^2 + dsin^2 + dcos^2) ]
+// b = [cls > 0], p_t = softmax(PID)[cls - 1], g = sqrt(pT target), pT' and E' targets
+// by Eq. 2.  d/du_j of the focal term = c (delta_jk - p_j) with
+// c = fg (1 - p_t)^(fg - 1) p_t log p_t - (1 - p_t)^fg.
+__global__ void __launch_bounds__(256) k_supervised_loss(const float* __restrict__ lg, const float* __restrict__ raw,
+                                                         const float* __restrict__ x, const int32_t* __restrict__ cls,
+                                                         const float* __restrict__ regt, int T, float invT,
+                                                         float beta, float fg, float delta,
+                                                         float* __restrict__ dl, float* __restrict__ dr,
+                                                         double* loss) {
+    __shared__ double part[8];
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    double li = 0.0;
+    if (t < T) {
+        const float* l = lg + (long)t * 6;
+        const int k = cls[t];
+        const bool b = k > 0;
+        const float z = l[0];
+        const float bce = fmaxf(z, 0.f) + log1pf(expf(-fabsf(z))) - (b ? z : 0.f);
+        const float sig = 1.f / (1.f + expf(-z));
+        dl[(long)t * 6] = beta * (sig - (b ? 1.f : 0.f)) * invT;
+        float lt = beta * bce;
+        if (b) {
+            float m = l[1];
+            for (int c = 2; c < 6; ++c) m = fmaxf(m, l[c]);
+            float zs = 0.f;
+            for (int c = 1; c < 6; ++c) zs += expf(l[c] - m);
+            const float lzs = logf(zs);
+            const float logpt = l[k] - m - lzs, pt = expf(logpt), omp = 1.f - pt;
+            const float ompg = powf(omp, fg);
+            lt += -ompg * logpt;
+            const float coef = fg * (fg == 0.f ? 0.f : powf(omp, fg - 1.f)) * pt * logpt - ompg;
+            for (int c = 1; c < 6; ++c) {
+                const float pj = expf(l[c] - m - lzs);
+                dl[(long)t * 6 + c] = coef * ((c == k ? 1.f : 0.f) - pj) * invT;
+            }
+            const float* rt = regt + (long)t * 5;
+            const float* rs = raw + (long)t * 5;
+            const float g = sqrtf(rt[0]);
+            float tgt[5], w[5] = {g, delta, delta, delta, g};
+            tgt[0] = logf(rt[0]) - x[(long)t * 42 + 8];
+            tgt[1] = rt[1];
+            tgt[2] = rt[2];
+            tgt[3] = rt[3];
+            tgt[4] = logf(rt[4]) - x[(long)t * 42 + 9];
+            for (int c = 0; c < 5; ++c) {
+                const float df = rs[c] - tgt[c];
+                lt += w[c] * df * df;
+                dr[(long)t * 5 + c] = 2.f * w[c] * df * invT;
+            }
+        } else {
+            for (int c = 1; c < 6; ++c) dl[(long)t * 6 + c] = 0.f;
+            for (int c = 0; c < 5; ++c) dr[(long)t * 5 + c] = 0.f;
+        }
+        li = (double)lt * invT;
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) li += __shfl_xor_sync(0xffffffffu, li, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = li;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < 8; ++i) s += part[i];
+        atomicAdd(loss, s);
+    }
+}
+
+// Printed architecture: track-like elements (track, GSF track, brem; one-hot x[0],
+// x[5], x[6]) take the track embedding.  merge: z = is_track ? et : ec.  split:
+// dt = is_track ? d : 0, dc = is_track ? 0 : d (dt may alias d).
+__device__ __forceinline__ bool is_track_row(const float* x, long r) {
+    const float* xr = x + r * 42;
+    return xr[0] + xr[5] + xr[6] > 0.5f;
+}
+__global__ void k_type_merge(const float* __restrict__ x, const float* __restrict__ et, const float* __restrict__ ec,
+                             float* __restrict__ z, int T, int d) {
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long)T * d) return;
+    z[i] = is_track_row(x, i / d) ? et[i] : ec[i];
+}
+__global__ void k_type_split(const float* __restrict__ x, float* dt, float* __restrict__ dc, int T, int d) {
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long)T * d) return;
+    const float v = dt[i];
+    const bool trk = is_track_row(x, i / d);
+    dt[i] = trk ? v : 0.f;
+    dc[i] = trk ? 0.f : v;
+}
+__global__ void k_add(float* __restrict__ a, const float* __restrict__ b, long n) {
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] += b[i];
+}
+
 // LAMB: per chunk (tensor id, start, length) of the parameter vector.
 __global__ void __launch_bounds__(256) k_lamb_moments(const float* __restrict__ w, float* __restrict__ g,
                                                       float* __restrict__ m, float* __restrict__ v,
@@ -477,8 +573,11 @@ struct Acts {
     std::vector<float*> ln1r, qkvr, orr, lser, zmr, ln2r, afr, hfr; // per reg layer
     float *hp, *hreg, *ar, *hr, *ac, *hc, *logits, *raw;
     float *ah[4], *hh[4];
+    // printed architecture: cluster embedding hidden/output, track embedding output,
+    // PID head hidden (the binary head uses ac/hc)
+    float *a1c, *h1c, *et, *ec, *ac2, *hc2;
     // backward
-    float *dz, *dx1, *dx2, *dhp, *dhreg, *dlog, *draw, *D;
+    float *dz, *dx1, *dx2, *dhp, *dhreg, *dlog, *draw, *D, *demb, *dsel;
 };
 
 size_t acts_layout(const mlpf_config& c, size_t T, Acts* A, float* base) {
@@ -520,6 +619,15 @@ size_t acts_layout(const mlpf_config& c, size_t T, Acts* A, float* base) {
         a.ah[k] = take(d);
         a.hh[k] = take(d);
     }
+    const bool paper = c.arch == 1;
+    a.a1c = paper ? take(d) : nullptr;
+    a.h1c = paper ? take(d) : nullptr;
+    a.et = paper ? take(d) : nullptr;
+    a.ec = paper ? take(d) : nullptr;
+    a.ac2 = paper ? take(d) : nullptr;
+    a.hc2 = paper ? take(d) : nullptr;
+    a.demb = paper ? take(d) : nullptr;
+    a.dsel = paper ? take(d) : nullptr;
     a.dz = take(d);
     a.dx1 = take(W3);
     a.dx2 = take(W3);
@@ -582,9 +690,21 @@ static void train_forward(Trainer& t, const Acts& a, const float* x, const int32
                           int max_n, cudaStream_t st) {
     const mlpf_config& c = t.m.cfg;
     const int d = c.d, F = c.ffn, act = c.act;
-    f32_linear(x, 42, 42, nullptr, 0, 0, P(t, "emb.w1"), P(t, "emb.b1"), nullptr, 0, a.a1, d, T, d, -1, st);
-    act_fwd(a.a1, a.h1, (long)T * d, act, st);
-    f32_linear(a.h1, d, d, nullptr, 0, 0, P(t, "emb.w2"), P(t, "emb.b2"), nullptr, 0, a.zp[0], d, T, d, -1, st);
+    const bool paper = c.arch == 1;
+    if (paper) {   // track and cluster embeddings, selected per element type
+        f32_linear(x, 42, 42, nullptr, 0, 0, P(t, "emb.trk.w1"), P(t, "emb.trk.b1"), nullptr, 0, a.a1, d, T, d, -1, st);
+        act_fwd(a.a1, a.h1, (long)T * d, act, st);
+        f32_linear(a.h1, d, d, nullptr, 0, 0, P(t, "emb.trk.w2"), P(t, "emb.trk.b2"), nullptr, 0, a.et, d, T, d, -1, st);
+        f32_linear(x, 42, 42, nullptr, 0, 0, P(t, "emb.clu.w1"), P(t, "emb.clu.b1"), nullptr, 0, a.a1c, d, T, d, -1, st);
+        act_fwd(a.a1c, a.h1c, (long)T * d, act, st);
+        f32_linear(a.h1c, d, d, nullptr, 0, 0, P(t, "emb.clu.w2"), P(t, "emb.clu.b2"), nullptr, 0, a.ec, d, T, d, -1, st);
+        k_type_merge<<<cdivu((long)T * d, 256), 256, 0, st>>>(x, a.et, a.ec, a.zp[0], T, d);
+        cudaMemcpyAsync(a.zr[0], a.zp[0], (size_t)T * d * sizeof(float), cudaMemcpyDeviceToDevice, st);
+    } else {
+        f32_linear(x, 42, 42, nullptr, 0, 0, P(t, "emb.w1"), P(t, "emb.b1"), nullptr, 0, a.a1, d, T, d, -1, st);
+        act_fwd(a.a1, a.h1, (long)T * d, act, st);
+        f32_linear(a.h1, d, d, nullptr, 0, 0, P(t, "emb.w2"), P(t, "emb.b2"), nullptr, 0, a.zp[0], d, T, d, -1, st);
+    }
     auto stack = [&](const char* pre, int L, const std::vector<float*>& z, const std::vector<float*>& ln1,
                      const std::vector<float*>& qkv, const std::vector<float*>& o, const std::vector<float*>& lse,
                      const std::vector<float*>& zm, const std::vector<float*>& ln2, const std::vector<float*>& af,
@@ -608,14 +728,28 @@ static void train_forward(Trainer& t, const Acts& a, const float* x, const int32
         f32_layernorm(z[L], P(t, std::string(pre) + ".lnf.g"), P(t, std::string(pre) + ".lnf.b"), out, T, d, st);
     };
     stack("pid", c.l_pid, a.zp, a.ln1p, a.qkvp, a.op, a.lsep, a.zmp, a.ln2p, a.afp, a.hfp, a.hp);
-    f32_linear(x, 42, 42, a.hp, d, d, P(t, "remb.w1"), P(t, "remb.b1"), nullptr, 0, a.ar, d, T, d, -1, st);
-    act_fwd(a.ar, a.hr, (long)T * d, act, st);
-    f32_linear(a.hr, d, d, nullptr, 0, 0, P(t, "remb.w2"), P(t, "remb.b2"), nullptr, 0, a.zr[0], d, T, d, -1, st);
+    if (!paper) {
+        f32_linear(x, 42, 42, a.hp, d, d, P(t, "remb.w1"), P(t, "remb.b1"), nullptr, 0, a.ar, d, T, d, -1, st);
+        act_fwd(a.ar, a.hr, (long)T * d, act, st);
+        f32_linear(a.hr, d, d, nullptr, 0, 0, P(t, "remb.w2"), P(t, "remb.b2"), nullptr, 0, a.zr[0], d, T, d, -1, st);
+    }
     stack("reg", c.l_reg, a.zr, a.ln1r, a.qkvr, a.orr, a.lser, a.zmr, a.ln2r, a.afr, a.hfr, a.hreg);
-    f32_linear(a.hp, d, d, nullptr, 0, 0, P(t, "head.cls.w1"), P(t, "head.cls.b1"), nullptr, 0, a.ac, d, T, d, -1, st);
-    act_fwd(a.ac, a.hc, (long)T * d, act, st);
-    f32_linear(a.hc, d, d, nullptr, 0, 0, P(t, "head.cls.w2"), P(t, "head.cls.b2"), nullptr, 0, a.logits, 6, T, 6, -1,
-               st);
+    if (paper) {   // binary head -> logit column 0, PID head -> columns 1..5
+        f32_linear(a.hp, d, d, nullptr, 0, 0, P(t, "head.bin.w1"), P(t, "head.bin.b1"), nullptr, 0, a.ac, d, T, d, -1, st);
+        act_fwd(a.ac, a.hc, (long)T * d, act, st);
+        f32_linear(a.hc, d, d, nullptr, 0, 0, P(t, "head.bin.w2"), P(t, "head.bin.b2"), nullptr, 0, a.logits, 6, T, 1,
+                   -1, st);
+        f32_linear(a.hp, d, d, nullptr, 0, 0, P(t, "head.pid.w1"), P(t, "head.pid.b1"), nullptr, 0, a.ac2, d, T, d, -1,
+                   st);
+        act_fwd(a.ac2, a.hc2, (long)T * d, act, st);
+        f32_linear(a.hc2, d, d, nullptr, 0, 0, P(t, "head.pid.w2"), P(t, "head.pid.b2"), nullptr, 0, a.logits + 1, 6, T,
+                   5, -1, st);
+    } else {
+        f32_linear(a.hp, d, d, nullptr, 0, 0, P(t, "head.cls.w1"), P(t, "head.cls.b1"), nullptr, 0, a.ac, d, T, d, -1, st);
+        act_fwd(a.ac, a.hc, (long)T * d, act, st);
+        f32_linear(a.hc, d, d, nullptr, 0, 0, P(t, "head.cls.w2"), P(t, "head.cls.b2"), nullptr, 0, a.logits, 6, T, 6,
+                   -1, st);
+    }
     int off = 0;
     for (int k = 0; k < 4; ++k) {
         const std::string p = std::string("head.") + RH[k] + ".";
@@ -640,10 +774,19 @@ static void train_backward(Trainer& t, const Acts& a, const float* x, const int3
         colsum(dY, ldy, T, N, G(t, bn), st);
         if (dX) gemm_dx(dY, ldy, P(t, wn), K, dX, ldxo, T, N, K, acc, st);
     };
-    // class head
-    lin_bwd(a.dlog, 6, a.hc, d, "head.cls.w2", "head.cls.b2", 6, d, a.dx1, d, 0);
-    act_bwd(a.ac, a.dx1, a.dx2, (long)T * d, act, st);
-    lin_bwd(a.dx2, d, a.hp, d, "head.cls.w1", "head.cls.b1", d, d, a.dhp, d, 0);
+    const bool paper = c.arch == 1;
+    if (paper) {   // binary head (logit column 0) and PID head (columns 1..5)
+        lin_bwd(a.dlog, 6, a.hc, d, "head.bin.w2", "head.bin.b2", 1, d, a.dx1, d, 0);
+        act_bwd(a.ac, a.dx1, a.dx2, (long)T * d, act, st);
+        lin_bwd(a.dx2, d, a.hp, d, "head.bin.w1", "head.bin.b1", d, d, a.dhp, d, 0);
+        lin_bwd(a.dlog + 1, 6, a.hc2, d, "head.pid.w2", "head.pid.b2", 5, d, a.dx1, d, 0);
+        act_bwd(a.ac2, a.dx1, a.dx2, (long)T * d, act, st);
+        lin_bwd(a.dx2, d, a.hp, d, "head.pid.w1", "head.pid.b1", d, d, a.dhp, d, 1);
+    } else {   // class head
+        lin_bwd(a.dlog, 6, a.hc, d, "head.cls.w2", "head.cls.b2", 6, d, a.dx1, d, 0);
+        act_bwd(a.ac, a.dx1, a.dx2, (long)T * d, act, st);
+        lin_bwd(a.dx2, d, a.hp, d, "head.cls.w1", "head.cls.b1", d, d, a.dhp, d, 0);
+    }
     // regression heads
     int off = 0;
     for (int k = 0; k < 4; ++k) {
@@ -687,6 +830,20 @@ static void train_backward(Trainer& t, const Acts& a, const float* x, const int3
         }
     };
     stack_bwd("reg", c.l_reg, a.zr, a.ln1r, a.qkvr, a.orr, a.lser, a.zmr, a.ln2r, a.afr, a.hfr, a.dhreg);
+    if (paper) {
+        // both stacks read the embedding: its gradient is the sum of theirs
+        cudaMemcpyAsync(a.demb, a.dz, (size_t)T * d * sizeof(float), cudaMemcpyDeviceToDevice, st);
+        stack_bwd("pid", c.l_pid, a.zp, a.ln1p, a.qkvp, a.op, a.lsep, a.zmp, a.ln2p, a.afp, a.hfp, a.dhp);
+        k_add<<<cdivu((long)T * d, 256), 256, 0, st>>>(a.demb, a.dz, (long)T * d);
+        k_type_split<<<cdivu((long)T * d, 256), 256, 0, st>>>(x, a.demb, a.dsel, T, d);
+        lin_bwd(a.demb, d, a.h1, d, "emb.trk.w2", "emb.trk.b2", d, d, a.dx1, d, 0);
+        act_bwd(a.a1, a.dx1, a.dx2, (long)T * d, act, st);
+        lin_bwd(a.dx2, d, x, 42, "emb.trk.w1", "emb.trk.b1", d, 42, nullptr, 0, 0);
+        lin_bwd(a.dsel, d, a.h1c, d, "emb.clu.w2", "emb.clu.b2", d, d, a.dx1, d, 0);
+        act_bwd(a.a1c, a.dx1, a.dx2, (long)T * d, act, st);
+        lin_bwd(a.dx2, d, x, 42, "emb.clu.w1", "emb.clu.b1", d, 42, nullptr, 0, 0);
+        return;
+    }
     // regression-stack input FFN over concat(x, h_pid)
     lin_bwd(a.dz, d, a.hr, d, "remb.w2", "remb.b2", d, d, a.dx1, d, 0);
     act_bwd(a.ar, a.dx1, a.dx2, (long)T * d, act, st);
@@ -721,6 +878,50 @@ struct mlpf_trainer {
         }                                                                           \
     } while (0)
 
+// One step: forward, `loss` (fills a.dlog, a.draw and the loss accumulator), backward,
+// optional LAMB update.
+template <typename LossFn>
+static mlpf_status trainer_step_impl(mlpf_trainer* tt, const float* x, const int32_t* cu, int32_t n_events,
+                                     int32_t total, int32_t max_n, LossFn loss, float lr, int32_t update,
+                                     float* grads_out, double* loss_out, void* stream) {
+    Trainer& t = tt->t;
+    cudaStream_t st = (cudaStream_t)stream;
+    TCK(cudaSetDevice(t.m.device));
+    if ((size_t)total > t.cap_rows) {
+        if (t.act) cudaFree(t.act);
+        t.act = nullptr;
+        const size_t rows = std::max<size_t>(total, t.cap_rows * 5 / 4);
+        const size_t n = acts_layout(t.m.cfg, rows, nullptr, nullptr);
+        TCK(cudaMalloc(&t.act, n * sizeof(float)));
+        t.cap_rows = rows;
+        t.act_floats = n;
+    }
+    Acts a;
+    acts_layout(t.m.cfg, t.cap_rows, &a, t.act);
+    TCK(cudaMemsetAsync(t.g, 0, t.n_params * 4, st));
+    TCK(cudaMemsetAsync(t.scratch, 0, (1 + 2 * t.names.size()) * sizeof(double), st));
+    train_forward(t, a, x, cu, n_events, total, max_n, st);
+    loss(a, st);
+    train_backward(t, a, x, cu, n_events, total, max_n, st);
+    if (grads_out) TCK(cudaMemcpyAsync(grads_out, t.g, t.n_params * 4, cudaMemcpyDeviceToDevice, st));
+    if (update) {
+        ++t.step;
+        const float b1 = 0.9f, b2 = 0.999f;
+        const float bc1 = 1.f - powf(b1, (float)t.step), bc2 = 1.f - powf(b2, (float)t.step);
+        const size_t nt = t.names.size();
+        k_lamb_moments<<<t.n_chunks, 256, 0, st>>>(t.w, t.g, t.mom, t.var, t.chunks, t.scratch + 1,
+                                                   t.scratch + 1 + nt, b1, b2, 1e-6f, bc1, bc2, 0.f);
+        k_lamb_apply<<<t.n_chunks, 256, 0, st>>>(t.w, t.g, t.chunks, t.scratch + 1, t.scratch + 1 + nt, lr);
+    }
+    TCK(cudaGetLastError());
+    if (loss_out) {
+        TCK(cudaMemcpyAsync(loss_out, t.scratch, sizeof(double), cudaMemcpyDeviceToHost, st));
+        TCK(cudaStreamSynchronize(st));
+    }
+    return MLPF_OK;
+}
+
+
 extern "C" {
 
 void mlpf_trainer_free(mlpf_trainer* tt) {
@@ -743,14 +944,17 @@ mlpf_status mlpf_trainer_create(const void* blob, size_t nbytes, int device, mlp
     mlpf_status s = parse_blob_into((const uint8_t*)blob, nbytes, t.m);
     if (s != MLPF_OK) { delete tt; return s; }
     const mlpf_config& c = t.m.cfg;
-    if (c.d > 256 || c.ffn > 4096 || c.arch != 0) { delete tt; set_error("unsupported trainer configuration"); return MLPF_E_UNSUPPORTED; }
-    // parameter vector in blob order (names re-read from the blob)
+    if (c.d > 256 || c.ffn > 4096) { delete tt; set_error("unsupported trainer configuration"); return MLPF_E_UNSUPPORTED; }
+    // parameter vector in blob order (names re-read from the blob; version 2 has an
+    // arch word before the tensor count)
     {
         const uint8_t* p = (const uint8_t*)blob;
-        int32_t h[10];
-        std::memcpy(h, p + 8, 40);
-        size_t off = 48;
-        for (int i = 0; i < h[9]; ++i) {
+        int32_t version, h[11];
+        std::memcpy(&version, p + 4, 4);
+        const int nh = version == 1 ? 10 : 11;
+        std::memcpy(h, p + 8, 4 * (size_t)nh);
+        size_t off = 8 + 4 * (size_t)nh;
+        for (int i = 0; i < h[nh - 1]; ++i) {
             char name[49];
             std::memcpy(name, p + off, 48);
             name[48] = 0;
@@ -805,48 +1009,46 @@ mlpf_status mlpf_trainer_step(mlpf_trainer* tt, const float* x, const int32_t* c
         set_error("bad trainer step arguments");
         return MLPF_E_INVALID;
     }
-    Trainer& t = tt->t;
-    cudaStream_t st = (cudaStream_t)stream;
-    TCK(cudaSetDevice(t.m.device));
-    if ((size_t)total > t.cap_rows) {
-        if (t.act) cudaFree(t.act);
-        t.act = nullptr;
-        const size_t rows = std::max<size_t>(total, t.cap_rows * 5 / 4);
-        const size_t n = acts_layout(t.m.cfg, rows, nullptr, nullptr);
-        TCK(cudaMalloc(&t.act, n * sizeof(float)));
-        t.cap_rows = rows;
-        t.act_floats = n;
+    if (tt->t.m.cfg.arch != 0) {
+        set_error("the distillation loss is defined for the 6-class head (arch 0)");
+        return MLPF_E_UNSUPPORTED;
     }
-    Acts a;
-    acts_layout(t.m.cfg, t.cap_rows, &a, t.act);
-    TCK(cudaMemsetAsync(t.g, 0, t.n_params * 4, st));
-    TCK(cudaMemsetAsync(t.scratch, 0, (1 + 2 * t.names.size()) * sizeof(double), st));
-    train_forward(t, a, x, cu, n_events, total, max_n, st);
-    k_distill_loss<<<cdivu(total, 256), 256, 0, st>>>(a.logits, a.raw, t_logits, t_reg, x, total, 1.0f / total,
-                                                      a.dlog, a.draw, t.scratch);
-    train_backward(t, a, x, cu, n_events, total, max_n, st);
-    if (grads_out) TCK(cudaMemcpyAsync(grads_out, t.g, t.n_params * 4, cudaMemcpyDeviceToDevice, st));
-    if (update) {
-        ++t.step;
-        const float b1 = 0.9f, b2 = 0.999f;
-        const float bc1 = 1.f - powf(b1, (float)t.step), bc2 = 1.f - powf(b2, (float)t.step);
-        const size_t nt = t.names.size();
-        k_lamb_moments<<<t.n_chunks, 256, 0, st>>>(t.w, t.g, t.mom, t.var, t.chunks, t.scratch + 1,
-                                                   t.scratch + 1 + nt, b1, b2, 1e-6f, bc1, bc2, 0.f);
-        k_lamb_apply<<<t.n_chunks, 256, 0, st>>>(t.w, t.g, t.chunks, t.scratch + 1, t.scratch + 1 + nt, lr);
+    double* acc = tt->t.scratch;
+    auto loss = [&](const Acts& a, cudaStream_t st) {
+        k_distill_loss<<<cdivu(total, 256), 256, 0, st>>>(a.logits, a.raw, t_logits, t_reg, x, total, 1.0f / total,
+                                                          a.dlog, a.draw, acc);
+    };
+    return trainer_step_impl(tt, x, cu, n_events, total, max_n, loss, lr, update, grads_out, loss_out, stream);
+}
+
+mlpf_status mlpf_trainer_step_supervised(mlpf_trainer* tt, const float* x, const int32_t* cu, int32_t n_events,
+                                         int32_t total, int32_t max_n, const int32_t* cls_target,
+                                         const float* reg_target, float beta, float focal_gamma, float delta,
+                                         float lr, int32_t update, float* grads_out, double* loss_out,
+                                         void* stream) {
+    if (!tt || !x || !cu || !cls_target || !reg_target || total <= 0 || n_events <= 0 || max_n <= 0 ||
+        max_n > 65536 || !(beta >= 0.f) || !(focal_gamma >= 0.f) || !(delta >= 0.f)) {
+        set_error("bad trainer step arguments");
+        return MLPF_E_INVALID;
     }
-    TCK(cudaGetLastError());
-    if (loss_out) {
-        TCK(cudaMemcpyAsync(loss_out, t.scratch, sizeof(double), cudaMemcpyDeviceToHost, st));
-        TCK(cudaStreamSynchronize(st));
+    if (tt->t.m.cfg.arch != 1) {
+        set_error("the supervised loss needs the binary + PID heads (arch 1)");
+        return MLPF_E_UNSUPPORTED;
     }
-    return MLPF_OK;
+    double* acc = tt->t.scratch;
+    auto loss = [&](const Acts& a, cudaStream_t st) {
+        k_supervised_loss<<<cdivu(total, 256), 256, 0, st>>>(a.logits, a.raw, x, cls_target, reg_target, total,
+                                                             1.0f / total, beta, focal_gamma, delta, a.dlog, a.draw,
+                                                             acc);
+    };
+    return trainer_step_impl(tt, x, cu, n_events, total, max_n, loss, lr, update, grads_out, loss_out, stream);
 }
 
 mlpf_status mlpf_trainer_export(const mlpf_trainer* tt, void* blob, size_t cap, size_t* nbytes) {
     if (!tt || !nbytes) { set_error("NULL argument"); return MLPF_E_INVALID; }
     const Trainer& t = tt->t;
-    const size_t need = 48 + t.names.size() * 60 + t.n_params * 4;
+    const bool v2 = t.m.cfg.arch != 0;   // version 2 blobs carry the arch word
+    const size_t need = (v2 ? 52 : 48) + t.names.size() * 60 + t.n_params * 4;
     *nbytes = need;
     if (!blob) return MLPF_OK;
     if (cap < need) { set_error("export buffer too small"); return MLPF_E_INVALID; }
@@ -859,10 +1061,18 @@ mlpf_status mlpf_trainer_export(const mlpf_trainer* tt, void* blob, size_t cap, 
     uint8_t* p = (uint8_t*)blob;
     const mlpf_config& c = t.m.cfg;
     std::memcpy(p, "MLPF", 4);
-    const int32_t hdr[11] = {1, c.in_dim, c.d, c.heads, c.ffn, c.l_pid, c.l_reg, c.n_cls, c.n_reg, c.act,
-                             (int32_t)t.names.size()};
-    std::memcpy(p + 4, hdr, 44);
-    size_t off = 48;
+    size_t off;
+    if (v2) {
+        const int32_t hdr[12] = {2, c.in_dim, c.d, c.heads, c.ffn, c.l_pid, c.l_reg, c.n_cls, c.n_reg, c.act,
+                                 c.arch, (int32_t)t.names.size()};
+        std::memcpy(p + 4, hdr, 48);
+        off = 52;
+    } else {
+        const int32_t hdr[11] = {1, c.in_dim, c.d, c.heads, c.ffn, c.l_pid, c.l_reg, c.n_cls, c.n_reg, c.act,
+                                 (int32_t)t.names.size()};
+        std::memcpy(p + 4, hdr, 44);
+        off = 48;
+    }
     for (size_t i = 0; i < t.names.size(); ++i) {
         char name[48] = {0};
         std::strncpy(name, t.names[i].c_str(), 47);
