@@ -14,5 +14,5 @@ from .forward import (  # noqa: F401
     multi_head_attention, encoder_block, encoder_stack, embed, reg_embed,
     ffn_head, forward_event, decode, event_sums, forward, OracleOutput, is_track, embed_per_type,
     raw_from_decoded, log_softmax_rows, distill_loss, supervised_loss, softplus,
-    SUP_BETA, SUP_FOCAL, SUP_DELTA,
+    SUP_BETA, SUP_FOCAL, SUP_DELTA, WINDOW_BLOCK, eta_order, window_mask,
 )

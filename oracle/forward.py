@@ -71,13 +71,15 @@ def attention_matrix(q, k, key_mask=None):
     """A = softmax(Q K^T / sqrt(d_k)) (Sec. 5.3, Eq. 4).
 
     q [N, dk], k [M, dk]; key_mask [M] bool (True = real key) restricts the
-    softmax to real keys (padding keys get weight zero).
+    softmax to real keys (padding keys get weight zero); a [N, M] key_mask
+    restricts each query row to its own keys (windowed attention).
     """
     q = np.asarray(q, F64)
     k = np.asarray(k, F64)
     s = q @ k.T / math.sqrt(q.shape[-1])
     if key_mask is not None:
-        s = np.where(np.asarray(key_mask, bool)[None, :], s, -np.inf)
+        km = np.asarray(key_mask, bool)
+        s = np.where(km if km.ndim == 2 else km[None, :], s, -np.inf)
     return softmax_rows(s)
 
 
@@ -270,11 +272,34 @@ def event_sums(cls, reg, cu_seqlens):
     return out
 
 
-def forward(W, cfg, x, cu_seqlens, events=None, keep_hidden=False):
+# ------------------------------------------------------ windowed attention
+# The paper names sparse or block attention as a way to cut the inference cost
+# (Sec. 9) and suggests partitioning the event before the correlation layers
+# (Sec. 5.3).  This variant (not the paper's model) orders each event's elements
+# by eta and lets query block b (of WINDOW_BLOCK elements) attend to the keys of
+# blocks b - window .. b + window only; window 0 in forward() = full attention.
+
+WINDOW_BLOCK = 128
+
+
+def eta_order(x):
+    """Order of an event's elements by eta (x[:, 10]); ties keep their input order."""
+    return np.argsort(np.asarray(x, F64)[:, 10], kind="stable")
+
+
+def window_mask(n, window, block=WINDOW_BLOCK):
+    """[n, n] allowed (query, key) pairs in eta order: |i // block - j // block| <= window."""
+    b = np.arange(n) // block
+    return np.abs(b[:, None] - b[None, :]) <= window
+
+
+def forward(W, cfg, x, cu_seqlens, events=None, keep_hidden=False, window=0):
     """Forward over a packed batch; events are independent.
 
     events: optional list of event indices to evaluate (the others are left
     as NaN rows / NaN sums), for sampled checks of large batches.
+    window > 0: windowed attention in eta order (see window_mask); outputs are
+    returned in the input order.
     """
     x = np.asarray(x, F64)
     cu = np.asarray(cu_seqlens, np.int64)
@@ -289,7 +314,16 @@ def forward(W, cfg, x, cu_seqlens, events=None, keep_hidden=False):
         sl = slice(cu[ev], cu[ev + 1])
         if cu[ev + 1] == cu[ev]:
             continue
-        res = forward_event(W, cfg, x[sl], keep_hidden=keep_hidden)
+        if window > 0:
+            xe = x[sl]
+            order = eta_order(xe)
+            res = forward_event(W, cfg, xe[order], key_mask=window_mask(len(order), window),
+                                keep_hidden=keep_hidden)
+            inv = np.empty_like(order)
+            inv[order] = np.arange(len(order))
+            res = tuple(r[inv] for r in res)
+        else:
+            res = forward_event(W, cfg, x[sl], keep_hidden=keep_hidden)
         logits[sl], raw[sl] = res[0], res[1]
         if keep_hidden:
             hp[sl], hr[sl] = res[2], res[3]

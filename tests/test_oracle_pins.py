@@ -469,3 +469,49 @@ def test_synthetic_targets():
     assert (r1[:, 0] > 0).all() and (r1[:, 4] > 0).all()
     d = np.log(r1[:, 0]) - x[:, 8]
     assert abs(d.std() - 0.3) < 0.02
+
+
+# ------------------------------------------------------------ windowed attention
+
+def test_window_mask_brute_force():
+    n, w, B = 300, 1, 128
+    m = oracle.window_mask(n, w, B)
+    for i in range(0, n, 7):
+        for j in range(0, n, 5):
+            assert m[i, j] == (abs(i // B - j // B) <= w)
+
+
+def test_windowed_attention_loop_nest():
+    """One head of windowed attention against a loop over each query's allowed keys."""
+    rng = np.random.default_rng(9)
+    n, dk = 300, 16
+    q, k, v = rng.normal(size=(3, n, dk))
+    out = oracle.sdpa(q, k, v, oracle.window_mask(n, 0))
+    for i in (0, 127, 128, 299):
+        lo, hi = (i // 128) * 128, min(n, (i // 128 + 1) * 128)
+        s = [sum(q[i, c] * k[j, c] for c in range(dk)) / 4.0 for j in range(lo, hi)]
+        m = max(s)
+        e = [math.exp(t - m) for t in s]
+        z = sum(e)
+        for c in range(dk):
+            ref = sum(e[j - lo] * v[j, c] for j in range(lo, hi)) / z
+            assert abs(out[i, c] - ref) < 1e-12
+
+
+def test_windowed_forward_reduces_to_full_and_is_order_invariant():
+    cfg = synth.SMALL
+    W = synth.make_weights(cfg, 12, perturbed=True)
+    x, cu = synth.gen_events(71, [300, 45])
+    full = oracle.forward(W, cfg, x, cu)
+    wide = oracle.forward(W, cfg, x, cu, window=3)    # 300 elements: 3 blocks, all in reach
+    np.testing.assert_allclose(wide.logits, full.logits, rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(wide.reg, full.reg, rtol=1e-10, atol=1e-12)
+    narrow = oracle.forward(W, cfg, x, cu, window=1)  # blocks 0 and 2 do not see each other
+    assert np.abs(narrow.logits[:300] - full.logits[:300]).max() > 1e-6
+    np.testing.assert_allclose(narrow.logits[300:], full.logits[300:], rtol=1e-10, atol=1e-12)
+    # canonical eta order: permuting the input permutes the outputs
+    perm = np.random.default_rng(3).permutation(300)
+    xp = x.copy()
+    xp[:300] = x[:300][perm]
+    narrow_p = oracle.forward(W, cfg, xp, cu, window=1)
+    np.testing.assert_allclose(narrow_p.logits[:300], narrow.logits[:300][perm], rtol=1e-10, atol=1e-12)
