@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp16", "fp8", "fp32"])
     ap.add_argument("--attn-variant", type=int, default=None,
                     help="fixed attention kernel variant (default: autotuned on the batch)")
+    ap.add_argument("--attn-window", type=int, default=0,
+                    help="windowed attention in eta order: query block b of 128 elements attends "
+                         "to blocks b-W..b+W (0 = full attention, the paper's model)")
     ap.add_argument("--no-baselines", action="store_true",
                     help="skip the FP32-plain, per-event-latency and CPU-oracle legs")
     ap.add_argument("--events", type=int, default=512,
@@ -151,6 +154,21 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def attention_pairs(sizes, window, block=128):
+    """(query, key) pairs of the attention over a batch: sum N^2, or with a window
+    of W blocks the pairs of each 128-row query block with blocks b-W..b+W."""
+    n = np.asarray(sizes, np.int64)
+    if window <= 0:
+        return float(np.sum(n.astype(np.float64) ** 2))
+    tot = 0.0
+    for ne in n:
+        for y in range((int(ne) + block - 1) // block):
+            rows = min(block, int(ne) - block * y)
+            keys = min(int(ne), (y + window + 1) * block) - max(0, (y - window) * block)
+            tot += rows * keys
+    return tot
+
+
 def attention_traffic(variant, precision):
     """Per-launch DRAM bytes of the attention kernel variant from the committed ncu
     summary (keys bytes_per_launch_<precision>_variant_<n>), else None."""
@@ -179,7 +197,7 @@ def workload_inputs(rank, n_events=512):
 
 
 # --------------------------------------------------------------------- oracle
-def oracle_sample(cfg, W, x, cu, budget_s, max_events=None):
+def oracle_sample(cfg, W, x, cu, budget_s, max_events=None, window=0):
     """Time the FP64 oracle on the first events of the batch (i.i.d. sizes)."""
     import oracle
     out, t0, done = [], time.perf_counter(), 0
@@ -187,9 +205,13 @@ def oracle_sample(cfg, W, x, cu, budget_s, max_events=None):
     while done < n and (max_events is None or done < max_events):
         e = done
         xs = x[cu[e]:cu[e + 1]]
-        lo, raw = oracle.forward_event(W, cfg, xs)
-        cls, reg = oracle.decode(xs, lo, raw)
-        sums = oracle.event_sums(cls, reg, [0, len(xs)])[0]
+        if window > 0:
+            r = oracle.forward(W, cfg, xs, [0, len(xs)], window=window)
+            lo, reg, cls, sums = r.logits, r.reg, r.cls, r.sums[0]
+        else:
+            lo, raw = oracle.forward_event(W, cfg, xs)
+            cls, reg = oracle.decode(xs, lo, raw)
+            sums = oracle.event_sums(cls, reg, [0, len(xs)])[0]
         out.append((e, lo, reg, cls, sums))
         done += 1
         if time.perf_counter() - t0 > budget_s:
@@ -272,6 +294,8 @@ def run_ours(args):
         csz = synth.sizes_lognormal(999, 32)
         cx, ccu = synth.gen_events(999, csz)
         model.calibrate_fp8(torch.from_numpy(cx).to(dev), torch.from_numpy(ccu).to(dev), int(csz.max()))
+    if args.attn_window > 0:
+        model.set_option(_lib.OPT_ATTN_WINDOW, args.attn_window)
     # roofline denominators measured on this device (before anything is timed)
     from paper_2601_17554_b300 import measure_unit_rates
     unit_rates = measure_unit_rates(local)
@@ -342,7 +366,7 @@ def run_ours(args):
     # ---- roofline of the dominant kernel (attention): exponentials per launch
     att = kernel_ms.get("attention", [])
     att_ms = sum(att) / len(att) if att else None
-    exps = float(np.sum(sizes.astype(np.float64) ** 2)) * HEADS
+    exps = attention_pairs(sizes, args.attn_window) * HEADS
     # peak: the MUFU exp2 rate measured on this device by the library's probe
     # kernel (independent chains on every SM), taken before the timed region
     roof = None
@@ -359,7 +383,7 @@ def run_ours(args):
                 "launch_ms": att_ms,
                 "algorithmic_exps_per_launch": exps,
                 "fp32_fma_peak_per_s": unit_rates["ffma_per_s"],
-                "mma_tflops": 4 * float(np.sum(sizes.astype(np.float64) ** 2)) * 64 / (att_ms / 1000.0) / 1e12}
+                "mma_tflops": 4 * attention_pairs(sizes, args.attn_window) * 64 / (att_ms / 1000.0) / 1e12}
     kernel_avg = {k: sum(v) / len(v) for k, v in kernel_ms.items()}
 
     line = {"metric": METRIC, "value": value, "unit": "events/s", "n_gpus": ws,
@@ -379,6 +403,33 @@ def run_ours(args):
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                     "ms_per_step": e2e_ms},
             "clocks": clk}
+    if args.attn_window > 0:
+        # agreement with full attention on the same batch, and the full-attention time
+        lw, rw, cw = lo.clone(), rg.clone(), cl.clone()
+        model.set_option(_lib.OPT_ATTN_WINDOW, 0)
+        model.set_option(_lib.OPT_PROFILE, 0)
+        step()
+        torch.cuda.synchronize(dev)
+        f_s, f_e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f_s.record(stream)
+        for _ in range(5):
+            step()
+        f_e.record(stream)
+        torch.cuda.synchronize(dev)
+        ms_full = f_s.elapsed_time(f_e) / 5
+        model.sync()
+        rwn, rgn = rw.double().cpu().numpy(), rg.double().cpu().numpy()
+        rel = np.sqrt(((rwn - rgn) ** 2).sum(0)) / np.maximum(np.sqrt((rgn ** 2).sum(0)), 1e-300)
+        line["config"]["attn_window"] = args.attn_window
+        line["window"] = {
+            "window_blocks": args.attn_window, "block": 128,
+            "note": "not the paper's model: eta-ordered block-banded attention (an option of the "
+                    "block/sparse attention the paper names as future work)",
+            "pairs_fraction_of_full": attention_pairs(sizes, args.attn_window) / attention_pairs(sizes, 0),
+            "argmax_agreement_vs_full": float((cw == cl).float().mean()),
+            "reg_rel_err_vs_full_per_column": [float(v) for v in rel],
+            "ms_full_attention": ms_full, "speedup_vs_full_attention": ms_full / ms_step}
+        model.set_option(_lib.OPT_ATTN_WINDOW, args.attn_window)
 
     if not args.no_baselines and rank == 0:
         # ---- per-event latency: each event alone, one launch sequence per event
@@ -424,7 +475,7 @@ def run_ours(args):
         step()
         model.sync()
         glo, grg, gcl, gsu = lo.cpu().numpy(), rg.cpu().numpy(), cl.cpu().numpy(), su.cpu().numpy()
-        samp, cpu_s = oracle_sample(cfg, W, x, cu, args.cpu_seconds)
+        samp, cpu_s = oracle_sample(cfg, W, x, cu, args.cpu_seconds, window=args.attn_window)
         nsamp = len(samp)
         line["cpu_baseline"] = {"value": nsamp / cpu_s, "unit": "events/s", "cores": blas_threads(),
                                 "kind": "oracle",

@@ -310,7 +310,18 @@ enum {
                                        the same on 64-row half items, two CTAs per SM,
                                        4 stages: 9 */
     MLPF_OPT_ATTN_VARIANT_FP16 = 8,
-    MLPF_OPT_ATTN_VARIANT_FP8 = 9
+    MLPF_OPT_ATTN_VARIANT_FP8 = 9,
+    MLPF_OPT_ATTN_WINDOW = 10       /* 0 (default): full attention within each event.
+                                       w > 0 (not the paper's model; an option of Sec. 9's
+                                       block/sparse attention): each event's elements are
+                                       ordered by eta (x[:, 10], ties by position), and
+                                       query block b of 128 elements attends to key blocks
+                                       b - w .. b + w only; outputs are returned in the
+                                       input order.  Runs on MLPF_FP32 and on the
+                                       warp-level attention kernels (variants 7-9; a
+                                       tcgen05 variant falls back to 8).  Events of at
+                                       most 16384 elements (else MLPF_E_UNSUPPORTED);
+                                       not available in mlpf_forward_noalloc. */
 };
 #define MLPF_ATTN_VARIANTS 10
 mlpf_status mlpf_set_option(mlpf_model* m, int32_t option, int64_t value);

@@ -257,6 +257,8 @@ static mlpf_status ensure_workspace(Model& m, int total, int n_events, bool tc) 
     const size_t o_hx = take(cap_t * 42 * 4), o_hcu = take((cap_e + 1) * 4),
                  o_hlo = take(cap_t * 6 * 4), o_hrg = take(cap_t * 5 * 4), o_hcl = take(cap_t * 4),
                  o_hsu = take(cap_e * 3 * 8);
+    const size_t o_perm = take(cap_t * 4), o_xs = take(cap_t * 42 * 4), o_los = take(cap_t * 6 * 4),
+                 o_rgs = take(cap_t * 5 * 4);
     void* base = nullptr;
     cudaError_t e = cudaMalloc(&base, off);
     if (e != cudaSuccess) return cuda_fail(e, "workspace allocation");
@@ -271,6 +273,8 @@ static mlpf_status ensure_workspace(Model& m, int total, int n_events, bool tc) 
     w.counters = (int*)(b + o_cnt);
     w.hx = (float*)(b + o_hx); w.hcu = (int32_t*)(b + o_hcu); w.hlogits = (float*)(b + o_hlo);
     w.hreg_out = (float*)(b + o_hrg); w.hcls = (int32_t*)(b + o_hcl); w.hsums = (double*)(b + o_hsu);
+    w.perm = (int32_t*)(b + o_perm); w.xs = (float*)(b + o_xs); w.los = (float*)(b + o_los);
+    w.rgs = (float*)(b + o_rgs);
     if (want_tc) {
         w.cap_tpad = tpad;
         w.tz = (float*)(b + o_tz);
@@ -303,6 +307,10 @@ static mlpf_status validate(const Model* m, int32_t prec, const void* x, const v
         set_error("tensor-core path is built for d=64, 4 heads, FFN 256, arch 0 models only");
         return MLPF_E_UNSUPPORTED;
     }
+    if (m->attn_window > 0 && max_n > 16384) {
+        set_error("windowed attention sorts events of at most 16384 elements");
+        return MLPF_E_UNSUPPORTED;
+    }
     if (prec == MLPF_FP8 && !m->fp8_ready) {
         set_error("MLPF_FP8 needs activation scales: call mlpf_calibrate_fp8 first");
         return MLPF_E_INVALID;
@@ -316,12 +324,29 @@ static mlpf_status launch_sequence(Model& m, int32_t prec, const float* x, const
                                    int64_t& launches) {
     int64_t n = 0;
     if (total > 0) {
-        n = (prec == MLPF_FP32)
-                ? run_forward_f32(m, x, cu, n_events, total, max_n, logits, reg, st)
-                : run_forward_tc(m, prec, x, cu, n_events, total, max_n, logits, reg, st);
-        if (n < 0) {
+        // windowed attention: run the forward on each event's elements in eta order
+        // and scatter the outputs back to the input order
+        const bool win = m.attn_window > 0;
+        const float* xin = x;
+        float *lo = logits, *rg = reg;
+        if (win) {
+            n = run_eta_order(m, x, cu, n_events, total, st);
+            xin = m.ws.xs;
+            lo = m.ws.los;
+            rg = m.ws.rgs;
+        }
+        const int64_t k = n < 0 ? -1
+                          : (prec == MLPF_FP32)
+                                ? run_forward_f32(m, xin, cu, n_events, total, max_n, lo, rg, st)
+                                : run_forward_tc(m, prec, xin, cu, n_events, total, max_n, lo, rg, st);
+        if (k < 0) {
             set_error(std::string("kernel launch failed: ") + cudaGetErrorString(cudaGetLastError()));
             return MLPF_E_CUDA;
+        }
+        n += k;
+        if (win) {
+            scatter_outputs(m.ws.perm, m.ws.los, m.ws.rgs, logits, reg, total, st);
+            ++n;
         }
     } else if (sums && n_events > 0) {
         cudaMemsetAsync(sums, 0, (size_t)n_events * 3 * sizeof(double), st);
@@ -702,6 +727,10 @@ mlpf_status mlpf_set_option(mlpf_model* mm, int32_t option, int64_t value) {
             break;
         case MLPF_OPT_DEBUG_STALL: m.debug_stall = value != 0; break;
         case MLPF_OPT_PROFILE: m.profile = value != 0; break;
+        case MLPF_OPT_ATTN_WINDOW:
+            if (value < 0 || value > 1024) { set_error("attention window must be 0..1024"); return MLPF_E_INVALID; }
+            m.attn_window = (int)value;
+            break;
         case MLPF_OPT_ATTN_VARIANT_BF16:
         case MLPF_OPT_ATTN_VARIANT_FP16:
         case MLPF_OPT_ATTN_VARIANT_FP8:
@@ -742,6 +771,7 @@ mlpf_status mlpf_get_option(const mlpf_model* mm, int32_t option, int64_t* value
         case MLPF_OPT_ATTN_VARIANT_BF16:
         case MLPF_OPT_ATTN_VARIANT_FP16:
         case MLPF_OPT_ATTN_VARIANT_FP8: *value = m.attn_variant[option - MLPF_OPT_ATTN_VARIANT_BF16]; return MLPF_OK;
+        case MLPF_OPT_ATTN_WINDOW: *value = m.attn_window; return MLPF_OK;
         default: set_error("unknown option " + std::to_string(option)); return MLPF_E_INVALID;
     }
 }

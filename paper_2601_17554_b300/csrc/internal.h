@@ -64,6 +64,10 @@ struct Workspace {
     int4* items = nullptr;               // attention work items
     int* counters = nullptr;             // [0]=n_items [1]=tpad rows [2..3]=attn tickets
     CUtensorMap map_q, map_q64, map_k, map_o, map_vt, map_hp;
+    // windowed attention: eta order of each event's elements (perm[r] = packed
+    // row of the r-th element in that order), inputs and outputs in that order
+    int32_t* perm = nullptr;
+    float *xs = nullptr, *los = nullptr, *rgs = nullptr;
     // host-buffer entry point: device staging
     float *hx = nullptr, *hlogits = nullptr, *hreg_out = nullptr;
     int32_t *hcu = nullptr, *hcls = nullptr;
@@ -102,6 +106,9 @@ struct Model {
     // attention kernel variant per operand format (BF16, FP16, E4M3), numbered as
     // MLPF_OPT_ATTN_VARIANT_* in mlpf.h; default: warp-level MMAs, 8 K/V stages
     int attn_variant[3] = {8, 8, 8};
+    // windowed attention (0 = full): in eta order, query block b of 128 elements
+    // attends to blocks b - attn_window .. b + attn_window
+    int attn_window = 0;
     // FP8: activation slots (one per GEMM input) and their static scales s_a = amax / 448
     std::map<std::string, int> act_slot;
     std::vector<float> act_scale;
@@ -141,6 +148,10 @@ int64_t run_forward_tc(Model& m, int prec, const float* x, const int32_t* cu, in
                        int total, int max_n, float* logits, float* reg, cudaStream_t st);
 void f32_eval_activation(const float* x, float* y, int n, int act, cudaStream_t st);
 void tc_eval_activation(const float* x, float* y, int n, int act, cudaStream_t st);
+// eta order / gather / scatter of the windowed-attention path (k_f32.cu)
+int64_t run_eta_order(Model& m, const float* x, const int32_t* cu, int n_events, int total, cudaStream_t st);
+void scatter_outputs(const int32_t* perm, const float* los, const float* rgs, float* logits, float* reg,
+                     int total, cudaStream_t st);
 int64_t run_event_sums(Model& m, const int32_t* cu, int n_events, const float* logits,
                        const float* reg, int32_t* cls, double* sums, int n_cls,
                        cudaStream_t st);

@@ -116,11 +116,13 @@ __global__ void k_layernorm(const float* __restrict__ X, const float* __restrict
 // [q | k | v] with head h in columns h*DH .. h*DH+DH-1 of each part.
 // lse (optional, [T, heads]): log-sum-exp of each row's scaled scores, for the
 // backward pass.
+// window > 0: the query rows of 128-row block y (in the event's current order)
+// attend to keys of blocks y - window .. y + window only.
 template <int DH>
 __global__ void __launch_bounds__(64) k_attention(const float* __restrict__ qkv,
                                                   float* __restrict__ out,
                                                   const int32_t* __restrict__ cu, int d,
-                                                  float scale, float* __restrict__ lse) {
+                                                  float scale, float* __restrict__ lse, int window) {
     __shared__ float Ks[64][DH + 1];
     __shared__ float Vs[64][DH + 1];
     const int e = blockIdx.z, h = blockIdx.y;
@@ -136,9 +138,15 @@ __global__ void __launch_bounds__(64) k_attention(const float* __restrict__ qkv,
         q[c] = active ? qkv[(size_t)(start + qi) * ld + h * DH + c] * scale : 0.f;
         acc[c] = 0.f;
     }
-    for (int kb = 0; kb < n; kb += 64) {
+    int k_begin = 0, k_end = n;
+    if (window > 0) {
+        const int y = (blockIdx.x * 64) / 128;
+        k_begin = max(0, (y - window) * 128);
+        k_end = min(n, (y + window + 1) * 128);
+    }
+    for (int kb = k_begin; kb < k_end; kb += 64) {
         const int kj = kb + threadIdx.x;
-        if (kj < n) {
+        if (kj < k_end) {
             const float* kr = qkv + (size_t)(start + kj) * ld + d + h * DH;
             const float* vr = qkv + (size_t)(start + kj) * ld + 2 * d + h * DH;
 #pragma unroll
@@ -148,7 +156,7 @@ __global__ void __launch_bounds__(64) k_attention(const float* __restrict__ qkv,
             }
         }
         __syncthreads();
-        const int cnt = min(64, n - kb);
+        const int cnt = min(64, k_end - kb);
         if (active) {
             float s[64];
             float mx = m;
@@ -332,11 +340,11 @@ int64_t run_forward_f32(Model& m, const float* x, const int32_t* cu, int n_event
             dim3 grid(cdiv(max_n, 64), c.heads, n_events);
             prof_begin(m, st, "f32_attention");
             if (dh == 16)
-                k_attention<16><<<grid, 64, 0, st>>>(w.qkv, w.o, cu, d, scale, nullptr);
+                k_attention<16><<<grid, 64, 0, st>>>(w.qkv, w.o, cu, d, scale, nullptr, m.attn_window);
             else if (dh == 32)
-                k_attention<32><<<grid, 64, 0, st>>>(w.qkv, w.o, cu, d, scale, nullptr);
+                k_attention<32><<<grid, 64, 0, st>>>(w.qkv, w.o, cu, d, scale, nullptr, m.attn_window);
             else
-                k_attention<64><<<grid, 64, 0, st>>>(w.qkv, w.o, cu, d, scale, nullptr);
+                k_attention<64><<<grid, 64, 0, st>>>(w.qkv, w.o, cu, d, scale, nullptr, m.attn_window);
             prof_end(m, st);
             ++n;
             linear(w.o, d, d, nullptr, 0, 0, W(p + "wo"), W(p + "bo"), w.z, d, w.z, d, T, d, -1, st,
@@ -422,11 +430,11 @@ void f32_attention(const float* qkv, float* out, const int32_t* cu, int n_events
     const float scale = 1.0f / sqrtf((float)dh);
     dim3 grid(cdiv(max_n, 64), heads, n_events);
     if (dh == 16)
-        k_attention<16><<<grid, 64, 0, st>>>(qkv, out, cu, d, scale, lse);
+        k_attention<16><<<grid, 64, 0, st>>>(qkv, out, cu, d, scale, lse, 0);
     else if (dh == 32)
-        k_attention<32><<<grid, 64, 0, st>>>(qkv, out, cu, d, scale, lse);
+        k_attention<32><<<grid, 64, 0, st>>>(qkv, out, cu, d, scale, lse, 0);
     else
-        k_attention<64><<<grid, 64, 0, st>>>(qkv, out, cu, d, scale, lse);
+        k_attention<64><<<grid, 64, 0, st>>>(qkv, out, cu, d, scale, lse, 0);
 }
 
 __global__ void k_eval_act_f32(const float* __restrict__ x, float* __restrict__ y, int n, int act) {
@@ -436,6 +444,84 @@ __global__ void k_eval_act_f32(const float* __restrict__ x, float* __restrict__ 
 
 void f32_eval_activation(const float* x, float* y, int n, int act, cudaStream_t st) {
     if (n > 0) k_eval_act_f32<<<(n + 255) / 256, 256, 0, st>>>(x, y, n, act);
+}
+
+// Eta order of each event's elements for windowed attention: one CTA per event
+// sorts the 64-bit keys (sortable eta bits << 32 | position) with a bitonic
+// network in shared memory (ties keep their input order), then writes perm and
+// gathers the input rows in that order.  Events of up to kSortMax elements.
+constexpr int kSortMax = 16384;
+__global__ void __launch_bounds__(1024) k_eta_order(const float* __restrict__ x, const int32_t* __restrict__ cu,
+                                                    int32_t* __restrict__ perm, float* __restrict__ xs) {
+    extern __shared__ unsigned long long keys[];
+    const int e = blockIdx.x;
+    const int start = cu[e], n = min(cu[e + 1] - start, kSortMax);
+    if (n <= 0) return;
+    int np2 = 1;
+    while (np2 < n) np2 <<= 1;
+    for (int i = threadIdx.x; i < np2; i += blockDim.x) {
+        unsigned long long k = ~0ull;
+        if (i < n) {
+            unsigned u = __float_as_uint(x[(size_t)(start + i) * 42 + 10]);
+            u ^= (u & 0x80000000u) ? 0xffffffffu : 0x80000000u;   // order-preserving bits
+            k = ((unsigned long long)u << 32) | (unsigned)i;
+        }
+        keys[i] = k;
+    }
+    __syncthreads();
+    for (int size = 2; size <= np2; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = threadIdx.x; i < np2; i += blockDim.x) {
+                const int j = i ^ stride;
+                if (j > i) {
+                    const unsigned long long a = keys[i], b = keys[j];
+                    const bool up = (i & size) == 0;
+                    if ((a > b) == up) {
+                        keys[i] = b;
+                        keys[j] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int r = threadIdx.x; r < n; r += blockDim.x) perm[start + r] = start + (int)(keys[r] & 0xffffffffu);
+    __syncthreads();
+    for (int t = threadIdx.x; t < n * 42; t += blockDim.x) {
+        const int r = t / 42, c = t - r * 42;
+        xs[(size_t)(start + r) * 42 + c] = x[(size_t)(start + (int)(keys[r] & 0xffffffffu)) * 42 + c];
+    }
+}
+
+__global__ void k_scatter_outputs(const int32_t* __restrict__ perm, const float* __restrict__ los,
+                                  const float* __restrict__ rgs, float* __restrict__ logits,
+                                  float* __restrict__ reg, int T) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= T) return;
+    const int o = perm[r];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) logits[(size_t)o * 6 + c] = los[(size_t)r * 6 + c];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) reg[(size_t)o * 5 + c] = rgs[(size_t)r * 5 + c];
+}
+
+int64_t run_eta_order(Model& m, const float* x, const int32_t* cu, int n_events, int total, cudaStream_t st) {
+    if (n_events <= 0 || total <= 0) return 0;
+    static bool attr[64] = {};
+    if (m.device >= 0 && m.device < 64 && !attr[m.device]) {
+        cudaFuncSetAttribute(k_eta_order, cudaFuncAttributeMaxDynamicSharedMemorySize, kSortMax * 8);
+        attr[m.device] = true;
+    }
+    prof_begin(m, st, "eta_order");
+    k_eta_order<<<n_events, 1024, kSortMax * 8, st>>>(x, cu, m.ws.perm, m.ws.xs);
+    prof_end(m, st);
+    if (cudaPeekAtLastError() != cudaSuccess) return -1;
+    return 1;
+}
+
+void scatter_outputs(const int32_t* perm, const float* los, const float* rgs, float* logits, float* reg, int total,
+                     cudaStream_t st) {
+    if (total > 0) k_scatter_outputs<<<cdiv(total, 256), 256, 0, st>>>(perm, los, rgs, logits, reg, total);
 }
 
 int64_t run_event_sums(Model& m, const int32_t* cu, int n_events, const float* logits,

@@ -933,7 +933,18 @@ struct AttnParams {
     unsigned* status;
     uint64_t wait_ns;
     int debug_stall;
+    int window;   // > 0: the query tile y attends to keys of 128-row blocks y - window .. y + window
 };
+
+// Keys [kb, ke) of the event that query tile y (128 rows) attends to.
+MLPF_DEV void key_range(int y, int n, int window, int& kb, int& ke) {
+    kb = 0;
+    ke = n;
+    if (window > 0) {
+        kb = max(0, (y - window) * ROWS);
+        ke = min(n, (y + window + 1) * ROWS);
+    }
+}
 
 // Largest excess (log2 units) of a tile's row max over the exponent reference
 // before the tile is redone: P <= 16, far inside the FP16 and BF16 ranges.
@@ -1774,7 +1785,9 @@ __global__ void __launch_bounds__(aw_threads<QR>(), QR == 128 ? 1 : 2)
                 info[qb] = it;
                 mbar_arrive_expect_tx(&q_full[qb], QB);
                 tma_load_2d(sQ + qb * QB, &map_q, 0, it.x + it.y * ROWS + QR * half, &q_full[qb]);
-                const int nk = (it.z + 63) >> 6;
+                int kb, ke;
+                key_range(it.y, it.z, p.window, kb, ke);
+                const int nk = (ke - kb + 63) >> 6;
                 for (int j = 0; j < nk; ++j, ++g) {
                     const int s = (int)(g % ST);
                     if (g >= ST &&
@@ -1783,8 +1796,8 @@ __global__ void __launch_bounds__(aw_threads<QR>(), QR == 128 ? 1 : 2)
                         break;
                     }
                     mbar_arrive_expect_tx(&kv_full[s], AT_KB + AT_VB);
-                    tma_load_2d(sK + s * AT_KB, &map_k, 0, it.x + 64 * j, &kv_full[s]);
-                    tma_load_2d(sV + s * AT_VB, &map_vt, it.x + 64 * j, 0, &kv_full[s]);
+                    tma_load_2d(sK + s * AT_KB, &map_k, 0, it.x + kb + 64 * j, &kv_full[s]);
+                    tma_load_2d(sV + s * AT_VB, &map_vt, it.x + kb + 64 * j, 0, &kv_full[s]);
                 }
                 ++q_it;
             }
@@ -1817,7 +1830,9 @@ __global__ void __launch_bounds__(aw_threads<QR>(), QR == 128 ? 1 : 2)
             const int4 it = info[qb];
             if (it.x < 0) break;
             if (p.debug_stall && !warp_wait(never, 0, ab, p.status, p.wait_ns)) break;
-            const int nk = (it.z + 63) >> 6;
+            int kb, ke;
+            key_range(it.y, it.z, p.window, kb, ke);
+            const int nk = (ke - kb + 63) >> 6;
             // Q fragments of the two 16-row tiles (one K-step: the head's 16 channels)
             uint32_t qa[2][4];
 #pragma unroll
@@ -1844,7 +1859,7 @@ __global__ void __launch_bounds__(aw_threads<QR>(), QR == 128 ? 1 : 2)
             for (int j = 0; j < nk; ++j, ++g) {
                 const uint32_t s = g % ST;
                 if (!warp_wait(&kv_full[s], (g / ST) & 1, ab, p.status, p.wait_ns)) { ok = false; break; }
-                const int kvalid = it.z - 64 * j;
+                const int kvalid = ke - kb - 64 * j;
                 const uint32_t kb = sKa + s * AT_KB, vb = sVa + s * AT_VB;
                 // S = Q K^T for keys 16q .. 16q+15 (two 8-key column tiles); the swizzle
                 // of rows 16q + k_row does not depend on q (16q is a multiple of 8)
@@ -2314,11 +2329,14 @@ static int64_t run_tc(Model& m, const float* x, const int32_t* cu, int n_events,
     prof_end(m, st);
     ++n;
     auto attention = [&](int layer) {
-        AttnParams ap{w.items, w.counters, layer, (uint16_t*)w.to, m.status, (uint64_t)m.wait_limit_ns, m.debug_stall ? 1 : 0};
+        AttnParams ap{w.items, w.counters, layer, (uint16_t*)w.to, m.status, (uint64_t)m.wait_limit_ns,
+                      m.debug_stall ? 1 : 0, m.attn_window};
         prof_begin(m, st, "attention");
         constexpr bool AF = kOutF16<FMT>;
         const dim3 g(grid * m.attn_ctas_per_sm);
-        switch (m.attn_variant[FMT]) {
+        // windowed attention runs on the warp-level kernels only
+        const int variant = m.attn_window > 0 && m.attn_variant[FMT] < 7 ? 8 : m.attn_variant[FMT];
+        switch (variant) {
             case 1: k_attention<AF, 1, 2><<<g, at_threads<1>(), AtLayout<2>::SMEM, st>>>(w.map_q, w.map_k, w.map_vt, ap); break;
             case 2: k_attention<AF, 2, 4><<<g, at_threads<2>(), AtLayout<4>::SMEM, st>>>(w.map_q, w.map_k, w.map_vt, ap); break;
             case 3: k_attention<AF, 2, 2><<<g, at_threads<2>(), AtLayout<2>::SMEM, st>>>(w.map_q, w.map_k, w.map_vt, ap); break;

@@ -97,6 +97,10 @@ extern "C" mlpf_status mlpf_forward_noalloc(mlpf_model* mm, int32_t precision, c
         set_error("mlpf_forward_noalloc runs the BF16 and FP16 tensor-core precisions only");
         return MLPF_E_UNSUPPORTED;
     }
+    if (m.attn_window > 0) {
+        set_error("mlpf_forward_noalloc has no scratch for windowed attention");
+        return MLPF_E_UNSUPPORTED;
+    }
     if (!m.tc_supported) {
         set_error("tensor-core path is built for d=64, 4 heads, FFN 256 models only");
         return MLPF_E_UNSUPPORTED;
