@@ -440,44 +440,46 @@ MLPF_DEV void layernorm_split(const float* z32, float* out32, const float* g, co
 // 256 threads: thread (wg, r) owns row r of the 128-row tile and, in every
 // epilogue, the warpgroup's half of the columns; LayerNorm moments are combined
 // through shared memory.
-constexpr int EM_THREADS = 256;
+constexpr int EM_THREADS = 512;   // two teams (tiles in flight) x two warpgroups
 template <int MODE, int FMT>  // MODE 0: input x (K = 42 -> 64); 1: concat(x, h_pid) (K = 106 -> 128)
-__global__ void __launch_bounds__(EM_THREADS, 2) k_embed_qkv(const __grid_constant__ CUtensorMap map_hp,
+__global__ void __launch_bounds__(EM_THREADS, 1) k_embed_qkv(const __grid_constant__ CUtensorMap map_hp,
                                                              EmbedParams p) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sm = align1024(smem_raw);
     constexpr int FE = kIs8<FMT> ? FMT_FP16 : FMT;
     constexpr int KA = MODE == 0 ? 1 : 2;  // atoms of the first GEMM's A operand
     constexpr uint32_t W1B = 64 * 128 * KA, W2B = 64 * 128, WQB = 192 * 128;
+    constexpr uint32_t TEAM_B = KA * ATOM + ATOM + 2 * 2 * 128 * 4;   // per team: sA, sH, LN sums
     constexpr bool TMA_HP = MODE == 1;
     constexpr bool F16 = kOutF16<FMT>;
+    const int tid = threadIdx.x;
+    const int team = tid >> 8, wg = (tid >> 7) & 1, r = tid & 127;
+    const bool leader = (tid & 255) == 0;
     uint8_t* sW1 = sm;
     uint8_t* sW2 = sW1 + W1B;
     uint8_t* sWq = sW2 + W2B;
-    uint8_t* sA = sWq + WQB;          // KA atom columns
-    uint8_t* sH = sA + KA * ATOM;     // 1 atom column
-    float* red = (float*)(sH + ATOM); // [pass][wg][row] LayerNorm partial sums
-    uint64_t* bars = (uint64_t*)(red + 2 * 2 * 128);  // 0 weights, 1 tma, 2 mma
-    uint32_t* tmem_hold = (uint32_t*)(bars + 4);
+    uint8_t* sA = sWq + WQB + team * TEAM_B;   // KA atom columns
+    uint8_t* sH = sA + KA * ATOM;              // 1 atom column
+    float* red = (float*)(sH + ATOM);          // [pass][wg][row] LayerNorm partial sums
+    uint64_t* bars = (uint64_t*)(sWq + WQB + 2 * TEAM_B);   // 0 weights; team t: 1 + 2t tma, 2 + 2t mma
+    uint64_t* tma_bar = &bars[1 + 2 * team];
+    uint64_t* mma_bar = &bars[2 + 2 * team];
+    uint32_t* tmem_hold = (uint32_t*)(bars + 6);
     int* abort_flag = (int*)(tmem_hold + 1);
-    const int tid = threadIdx.x;
-    const int wg = tid >> 7, r = tid & 127;
 
     if (tid == 0) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
-        mbar_init(&bars[2], 1);
+        for (int i = 0; i < 5; ++i) mbar_init(&bars[i], 1);
         *abort_flag = 0;
         fence_mbar_init();
     }
     if (tid < 32) {
-        tmem_alloc(tmem_hold, 256);
+        tmem_alloc(tmem_hold, 512);
         tmem_relinquish();
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tbase = *tmem_hold;
+    const uint32_t tbase = *tmem_hold + 256 * team;
     const uint32_t trow = tbase + ((uint32_t)(tid & 96) << 16);  // lane quarter of this warp
     volatile int* ab = abort_flag;
 
@@ -493,30 +495,30 @@ __global__ void __launch_bounds__(EM_THREADS, 2) k_embed_qkv(const __grid_consta
     const int nblk = tpad >> 6;
     const int ntiles = (tpad + ROWS - 1) / ROWS;
     uint32_t mph = 0, aph = 0;
-    // every thread: sync, thread 0 issues, wait for the MMA; false on failure
+    // the team syncs, its leader issues, everyone waits for the MMA; false on failure
     auto run_mma = [&](auto issue) -> bool {
         tc_fence_before();
         fence_proxy_async_smem();
-        if (__syncthreads_or(fail)) return false;
-        if (tid == 0) {
+        if (team_sync_or(team, fail)) return false;
+        if (leader) {
             tc_fence_after();
             issue();
-            mma_commit(&bars[2]);
+            mma_commit(mma_bar);
         }
-        fail |= !mbar_wait(&bars[2], mph, ab, p.status, ST_TIMEOUT_GEMM, p.wait_ns);
+        fail |= !mbar_wait(mma_bar, mph, ab, p.status, ST_TIMEOUT_GEMM, p.wait_ns);
         mph ^= 1;
-        const bool stop = __syncthreads_or(fail);
+        const bool stop = team_sync_or(team, fail);
         tc_fence_after();
         return !stop;
     };
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        if (__syncthreads_or(fail)) break;
+    for (int tile = blockIdx.x * 2 + team; tile < ntiles; tile += 2 * gridDim.x) {
+        if (team_sync_or(team, fail)) break;
         const int p0 = tile * ROWS;
         const int prow_pad = p0 + r;
         const RowInfo ri = row_info(p.blk, nblk, prow_pad);
-        if (TMA_HP && tid == 0) {
-            mbar_arrive_expect_tx(&bars[1], ATOM);
-            tma_load_2d(sA + ATOM, &map_hp, 0, p0, &bars[1]);
+        if (TMA_HP && leader) {
+            mbar_arrive_expect_tx(tma_bar, ATOM);
+            tma_load_2d(sA + ATOM, &map_hp, 0, p0, tma_bar);
         }
         float v[32];
         // this warpgroup's 32 of the row's 42 features (zero padded to 64)
@@ -552,7 +554,7 @@ __global__ void __launch_bounds__(EM_THREADS, 2) k_embed_qkv(const __grid_consta
             }
             record_amax(p.amax, p.slot[0], &amx, 1, ri.valid);
         }
-        if (TMA_HP && tid == 0) fail |= !mbar_wait(&bars[1], aph, ab, p.status, ST_TIMEOUT_GEMM, p.wait_ns);
+        if (TMA_HP && leader) fail |= !mbar_wait(tma_bar, aph, ab, p.status, ST_TIMEOUT_GEMM, p.wait_ns);
         aph ^= 1;
         // embedding FFN, first layer
         if (!run_mma([&] { issue_gemm<FE>(tbase, sA, sW1, 64, KA); })) break;
@@ -573,7 +575,7 @@ __global__ void __launch_bounds__(EM_THREADS, 2) k_embed_qkv(const __grid_consta
 #pragma unroll
             for (int i = 0; i < 8; ++i) zd[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
         }
-        layernorm_split(v, v, p.lng, p.lnb, wg, r, 0, red);
+        layernorm_split(v, v, p.lng, p.lnb, wg, r, team, red);
         if (p.amax) record_amax(p.amax, p.slot[2], v, 32, ri.valid);
         st_op<FMT>(sH, r, v, 32, 32 * wg, p.qs[2], true);
         // fused Q/K/V projection: warpgroup 0 stores Q and V^T columns 0-31,
@@ -618,7 +620,7 @@ __global__ void __launch_bounds__(EM_THREADS, 2) k_embed_qkv(const __grid_consta
     __syncthreads();
     if (tid < 32) {
         tc_fence_after();
-        tmem_dealloc(tbase, 256);
+        tmem_dealloc(*tmem_hold, 512);
     }
 }
 
@@ -2016,9 +2018,10 @@ __global__ void k_eval_act_tc(const float* __restrict__ x, float* __restrict__ y
 uint32_t embed_smem(int mode, int fmt) {
     (void)fmt;
     const int ka = mode == 0 ? 1 : 2;
-    const uint32_t need = 64 * 128 * ka + 64 * 128 + 192 * 128 + ka * ATOM + ATOM + 2 * 2 * 128 * 4 + 64 + 1024;
-    // at least 80 KB so that no more than two CTAs (2 x 256 TMEM columns) share an SM
-    return need < 80 * 1024 ? 80 * 1024 : need;
+    // weights + two teams x (A operand, hidden tile, LayerNorm sums) + barriers + alignment;
+    // at least 116 KB so that no two CTAs (512 TMEM columns each) share an SM
+    const uint32_t need = 64 * 128 * ka + 64 * 128 + 192 * 128 + 2 * (ka * ATOM + ATOM + 2 * 2 * 128 * 4) + 64 + 1024;
+    return need < 116 * 1024 ? 116 * 1024 : need;
 }
 uint32_t post_smem(int mode, int fmt) {
     const uint32_t ka256 = fmt == FMT_E4M3 ? 2 : 4;
@@ -2100,8 +2103,8 @@ int occupancy(K kernel, int threads, uint32_t smem) {
     return n;
 }
 
-// Every kernel must fit one CTA per SM; the embedding kernels (256 TMEM columns
-// each) must not exceed two co-resident CTAs.  Returns an
+// Every kernel must fit one CTA per SM; the embedding and post kernels (512 TMEM
+// columns each) must not share an SM with a second CTA.  Returns an
 // empty string or a description of the kernels that do not fit.
 template <int FMT>
 std::string check_occupancy() {
@@ -2121,8 +2124,7 @@ std::string check_occupancy() {
                       occupancy(k_post<2, FMT>, PT_THREADS, post_smem(2, FMT)),
                       occupancy(k_embed_qkv<0, FMT>, EM_THREADS, embed_smem(0, FMT)),
                       occupancy(k_embed_qkv<1, FMT>, EM_THREADS, embed_smem(1, FMT))};
-    if (o[0] >= 1 && o[1] >= 1 && o[2] >= 1 && o[3] >= 1 && o[4] >= 1 && o[4] <= 2 && o[5] >= 1 &&
-        o[5] <= 2)
+    if (o[0] >= 1 && o[1] >= 1 && o[2] >= 1 && o[3] >= 1 && o[4] == 1 && o[5] == 1)
         return "";
     return "format " + std::to_string(FMT) + " CTAs/SM: attention " + std::to_string(o[0]) + ", post " +
            std::to_string(o[1]) + "/" + std::to_string(o[2]) + "/" + std::to_string(o[3]) + ", embed " +
