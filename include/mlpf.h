@@ -206,10 +206,12 @@ int32_t mlpf_get_fp8_scales(const mlpf_model* m, int32_t cap, char* names, float
 
 /*
  * Student inference with per-event fallback to the full model.  `student` runs
- * on every event (precision student_precision); an event whose mean, over its
- * elements, of the student's largest class probability (max softmax of the
- * logits) is below `threshold` is rerun by `teacher` (teacher_precision) and its
- * rows of logits/reg are replaced.  Arguments as mlpf_forward, plus:
+ * on every event (precision student_precision); an event whose mean (or, with
+ * MLPF_OPT_GATE_CONFIDENCE = 1 on the student, minimum), over its elements, of
+ * the student's largest class probability (max softmax of the logits) is below
+ * `threshold` is rerun by `teacher` (teacher_precision) and its rows of
+ * logits/reg are replaced.  Both models must use the same class-score layout
+ * (arch).  Arguments as mlpf_forward, plus:
  * used_teacher  device out or NULL, [n_events] int32, 1 where the teacher ran;
  * n_fallback    host out or NULL, number of such events.
  * Synchronises `stream` once (to size the teacher's batch).  Both models must
@@ -311,7 +313,7 @@ enum {
                                        4 stages: 9 */
     MLPF_OPT_ATTN_VARIANT_FP16 = 8,
     MLPF_OPT_ATTN_VARIANT_FP8 = 9,
-    MLPF_OPT_ATTN_WINDOW = 10       /* 0 (default): full attention within each event.
+    MLPF_OPT_ATTN_WINDOW = 10,      /* 0 (default): full attention within each event.
                                        w > 0 (not the paper's model; an option of Sec. 9's
                                        block/sparse attention): each event's elements are
                                        ordered by eta (x[:, 10], ties by position), and
@@ -322,6 +324,9 @@ enum {
                                        tcgen05 variant falls back to 8).  Events of at
                                        most 16384 elements (else MLPF_E_UNSUPPORTED);
                                        not available in mlpf_forward_noalloc. */
+    MLPF_OPT_GATE_CONFIDENCE = 11   /* student models in mlpf_forward_gated: event
+                                       confidence = mean (0, default) or minimum (1) over
+                                       the event's elements of the max softmax */
 };
 #define MLPF_ATTN_VARIANTS 10
 mlpf_status mlpf_set_option(mlpf_model* m, int32_t option, int64_t value);

@@ -731,6 +731,10 @@ mlpf_status mlpf_set_option(mlpf_model* mm, int32_t option, int64_t value) {
             if (value < 0 || value > 1024) { set_error("attention window must be 0..1024"); return MLPF_E_INVALID; }
             m.attn_window = (int)value;
             break;
+        case MLPF_OPT_GATE_CONFIDENCE:
+            if (value < 0 || value > 1) { set_error("gate confidence mode must be 0 or 1"); return MLPF_E_INVALID; }
+            m.gate_confidence = (int)value;
+            return MLPF_OK;   // host-side choice: no captured graph depends on it
         case MLPF_OPT_ATTN_VARIANT_BF16:
         case MLPF_OPT_ATTN_VARIANT_FP16:
         case MLPF_OPT_ATTN_VARIANT_FP8:
@@ -772,6 +776,7 @@ mlpf_status mlpf_get_option(const mlpf_model* mm, int32_t option, int64_t* value
         case MLPF_OPT_ATTN_VARIANT_FP16:
         case MLPF_OPT_ATTN_VARIANT_FP8: *value = m.attn_variant[option - MLPF_OPT_ATTN_VARIANT_BF16]; return MLPF_OK;
         case MLPF_OPT_ATTN_WINDOW: *value = m.attn_window; return MLPF_OK;
+        case MLPF_OPT_GATE_CONFIDENCE: *value = m.gate_confidence; return MLPF_OK;
         default: set_error("unknown option " + std::to_string(option)); return MLPF_E_INVALID;
     }
 }

@@ -1,7 +1,8 @@
 // Student inference with per-event fallback to the full model: the student
-// runs on every event; events whose mean per-element class confidence (max
-// softmax) is below a threshold are compacted into a new packed batch, run
-// through the full (teacher) model and scattered back.
+// runs on every event; events whose per-element class confidence (max softmax),
+// averaged or minimised over the event (MLPF_OPT_GATE_CONFIDENCE), is below a
+// threshold are compacted into a new packed batch, run through the full
+// (teacher) model and scattered back.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -12,30 +13,36 @@
 namespace mlpf {
 namespace {
 
-// conf[e] = mean over the event's elements of max softmax(logits); flag[e] = conf < thr
+// conf[e] = mean (mode 0) or minimum (mode 1) over the event's elements of the
+// max softmax of the class scores; flag[e] = conf < thr
 __global__ void __launch_bounds__(256) k_event_confidence(const int32_t* __restrict__ cu,
                                                           const float* __restrict__ logits, float thr,
-                                                          int32_t* __restrict__ flag, float* __restrict__ conf) {
+                                                          int mode, int32_t* __restrict__ flag,
+                                                          float* __restrict__ conf) {
     __shared__ float part[8];
     const int e = blockIdx.x;
     const int s = cu[e], t = cu[e + 1];
-    float acc = 0.f;
+    float acc = mode == 1 ? 1.f : 0.f;
     for (int r = s + threadIdx.x; r < t; r += 256) {
         const float* l = logits + (size_t)r * 6;
         float m = l[0];
         for (int c = 1; c < 6; ++c) m = fmaxf(m, l[c]);
         float z = 0.f;
         for (int c = 0; c < 6; ++c) z += expf(l[c] - m);
-        acc += 1.f / z;  // max softmax = exp(m - m) / z
+        const float pmax = 1.f / z;   // max softmax = exp(m - m) / z
+        acc = mode == 1 ? fminf(acc, pmax) : acc + pmax;
     }
 #pragma unroll
-    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    for (int o = 16; o; o >>= 1) {
+        const float v = __shfl_xor_sync(0xffffffffu, acc, o);
+        acc = mode == 1 ? fminf(acc, v) : acc + v;
+    }
     if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
     __syncthreads();
     if (threadIdx.x == 0) {
-        float a = 0.f;
-        for (int i = 0; i < 8; ++i) a += part[i];
-        const float cf = t > s ? a / (float)(t - s) : 1.f;
+        float a = mode == 1 ? 1.f : 0.f;
+        for (int i = 0; i < 8; ++i) a = mode == 1 ? fminf(a, part[i]) : a + part[i];
+        const float cf = t <= s ? 1.f : (mode == 1 ? a : a / (float)(t - s));
         conf[e] = cf;
         flag[e] = cf < thr ? 1 : 0;
     }
@@ -165,7 +172,8 @@ extern "C" mlpf_status mlpf_forward_gated(mlpf_model* student, mlpf_model* teach
         gb.meta = gb.src + gb.cap_events + 1;
         gb.conf = (float*)(gb.meta + 16);
     }
-    k_event_confidence<<<n_events, 256, 0, st>>>(cu_seqlens, logits, threshold, gb.flag, gb.conf);
+    k_event_confidence<<<n_events, 256, 0, st>>>(cu_seqlens, logits, threshold, sm.gate_confidence, gb.flag,
+                                                  gb.conf);
     k_compact_events<<<1, 1024, 0, st>>>(cu_seqlens, gb.flag, n_events, gb.sub_cu, gb.src, gb.meta);
     int32_t meta[3];
     if (cudaMemcpyAsync(meta, gb.meta, sizeof(meta), cudaMemcpyDeviceToHost, st) != cudaSuccess ||

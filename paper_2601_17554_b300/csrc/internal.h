@@ -109,6 +109,9 @@ struct Model {
     // windowed attention (0 = full): in eta order, query block b of 128 elements
     // attends to blocks b - attn_window .. b + attn_window
     int attn_window = 0;
+    // gated inference (student models): event confidence = mean (0) or minimum (1)
+    // of the per-element max softmax
+    int gate_confidence = 0;
     // FP8: activation slots (one per GEMM input) and their static scales s_a = amax / 448
     std::map<std::string, int> act_slot;
     std::vector<float> act_scale;

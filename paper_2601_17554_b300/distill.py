@@ -78,7 +78,11 @@ def main(argv=None):
     ap.add_argument("--workers", type=int, default=min(16, os.cpu_count() or 1))
     ap.add_argument("--out", default="")
     ap.add_argument("--json", default="")
+    ap.add_argument("--student-blob", default="",
+                    help="evaluate this trained student (skip the training)")
     args = ap.parse_args(argv)
+    if args.student_blob:
+        args.train_events = args.batch_events   # only the teacher's confidence scale is needed
 
     # generate the training set before any CUDA call (spawned workers)
     t0 = time.time()
@@ -87,7 +91,7 @@ def main(argv=None):
     gen_s = time.time() - t0
 
     import torch
-    from paper_2601_17554_b300 import Model, Trainer, forward_gated
+    from paper_2601_17554_b300 import Model, Trainer, _lib, forward_gated
 
     dev = torch.device("cuda", 0)
     res = {"train_events": args.train_events, "train_elements": int(train_sizes.sum()),
@@ -119,6 +123,9 @@ def main(argv=None):
 
     # training
     init_blob = synth.pack_blob(synth.SMALL, synth.make_weights(synth.SMALL, STUDENT_SEED))
+    if args.student_blob:
+        batches = []
+        args.epochs = 0
     trainer = Trainer(init_blob)
     total_steps = args.epochs * len(batches)
     rng = np.random.default_rng(0)
@@ -140,6 +147,9 @@ def main(argv=None):
     res["loss_curve"] = losses
     blob = trainer.export()
     trainer.close()
+    if args.student_blob:
+        with open(args.student_blob, "rb") as f:
+            blob = f.read()
     if args.out:
         with open(args.out, "wb") as f:
             f.write(blob)
@@ -174,15 +184,18 @@ def main(argv=None):
              "student_reg_rel_err_vs_teacher": [
                  float(v) for v in np.sqrt(((s_reg - t_reg) ** 2).sum(0) / (t_reg ** 2).sum(0))],
              "student_ms": s_ms, "gated": {}}
-        for thr in sorted({args.threshold, 0.95, 0.99, 0.995, 0.999}):
-            gout, g_ms = timed(lambda: forward_gated(student, teacher, thr, X, CU, mn), reps=1)
-            g_cls = gout[2].cpu().numpy()
-            g_reg = gout[1].cpu().numpy()
-            rel = np.sqrt(((g_reg - t_reg) ** 2).sum(0) / (t_reg ** 2).sum(0))
-            r["gated"][str(thr)] = {"agreement": float((g_cls == t_cls).mean()),
-                                    "fallback_events": int(gout[5]), "fallback_rate": gout[5] / len(sizes),
-                                    "ms": g_ms, "speedup_vs_teacher": t_ms / g_ms,
-                                    "reg_rel_err_vs_teacher": [float(v) for v in rel]}
+        # event confidence: mean (mode 0) or minimum (mode 1) of the per-element max softmax
+        for mode, mname in ((0, "mean"), (1, "min")):
+            student.set_option(_lib.OPT_GATE_CONFIDENCE, mode)
+            for thr in sorted({args.threshold, 0.5, 0.7, 0.95, 0.99, 0.995, 0.999}):
+                gout, g_ms = timed(lambda: forward_gated(student, teacher, thr, X, CU, mn), reps=1)
+                g_cls = gout[2].cpu().numpy()
+                g_reg = gout[1].cpu().numpy()
+                rel = np.sqrt(((g_reg - t_reg) ** 2).sum(0) / (t_reg ** 2).sum(0))
+                r["gated"][f"{mname}@{thr}"] = {
+                    "agreement": float((g_cls == t_cls).mean()), "fallback_events": int(gout[5]),
+                    "fallback_rate": gout[5] / len(sizes), "ms": g_ms, "speedup_vs_teacher": t_ms / g_ms,
+                    "reg_rel_err_vs_teacher": [float(v) for v in rel]}
         res[name] = r
         student.close()
 

@@ -181,3 +181,14 @@ def test_gated_forward_extremes_and_flags():
     for e in range(5):
         src = t_out if flags[e] else s_out
         np.testing.assert_array_equal(lo[cu[e]:cu[e + 1]], src[0][cu[e]:cu[e + 1]])
+    # event confidence = minimum over the event's elements (MLPF_OPT_GATE_CONFIDENCE = 1)
+    cmin = np.array([(1.0 / p[cu[e]:cu[e + 1]].sum(1)).min() for e in range(5)])
+    c = np.sort(cmin)
+    thr = float((c[2] + c[3]) / 2)
+    student.set_option(11, 1)
+    try:
+        lo, rg, cl, su, used, nfb = forward_gated(student, teacher, thr, X, CU, 1200)
+    finally:
+        student.set_option(11, 0)
+    assert used.cpu().numpy().tolist() == (cmin < thr).astype(int).tolist()
+    assert nfb == int((cmin < thr).sum())
