@@ -247,13 +247,16 @@ __global__ void __launch_bounds__(256) k_event_sums(const int32_t* __restrict__ 
         for (int c = 0; c < 5; ++c) finite &= isfinite(rg[c]);
         if (cls_out) cls_out[r] = best;
         if (best != 0) {
-            const double p = rg[0], sn = rg[2], cs = rg[3];
-            const double rr = sqrt(sn * sn + cs * cs);
-            if (rr > 0.0) {
-                px += p * (cs / rr);
-                py += p * (sn / rr);
+            // per-element terms in FP32 (this GPU's FP64 divide and square root are
+            // slow), accumulated in FP64 in a fixed order
+            const float p = rg[0], sn = rg[2], cs = rg[3];
+            const float r2 = fmaf(sn, sn, cs * cs);
+            if (r2 > 0.f) {
+                const float inv = 1.0f / sqrtf(r2);
+                px += (double)(p * (cs * inv));
+                py += (double)(p * (sn * inv));
             }
-            pt += p;
+            pt += (double)p;
         }
     }
 #pragma unroll
