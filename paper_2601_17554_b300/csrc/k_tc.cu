@@ -441,6 +441,7 @@ MLPF_DEV void layernorm_split(const float* z32, float* out32, const float* g, co
 // epilogue, the warpgroup's half of the columns; LayerNorm moments are combined
 // through shared memory.
 constexpr int EM_THREADS = 512;   // two teams (tiles in flight) x two warpgroups
+constexpr int EV_N = 64 * 4 + 192;  // bias / LayerNorm floats of the embedding kernel
 template <int MODE, int FMT>  // MODE 0: input x (K = 42 -> 64); 1: concat(x, h_pid) (K = 106 -> 128)
 __global__ void __launch_bounds__(EM_THREADS, 1) k_embed_qkv(const __grid_constant__ CUtensorMap map_hp,
                                                              EmbedParams p) {
@@ -461,7 +462,9 @@ __global__ void __launch_bounds__(EM_THREADS, 1) k_embed_qkv(const __grid_consta
     uint8_t* sA = sWq + WQB + team * TEAM_B;   // KA atom columns
     uint8_t* sH = sA + KA * ATOM;              // 1 atom column
     float* red = (float*)(sH + ATOM);          // [pass][wg][row] LayerNorm partial sums
-    uint64_t* bars = (uint64_t*)(sWq + WQB + 2 * TEAM_B);   // 0 weights; team t: 1 + 2t tma, 2 + 2t mma
+    // bias and LayerNorm vectors: b1 [64], b2 [64], ln gain [64], ln shift [64], bqkv [192]
+    float* pv = (float*)(sWq + WQB + 2 * TEAM_B);
+    uint64_t* bars = (uint64_t*)(pv + EV_N);   // 0 weights; team t: 1 + 2t tma, 2 + 2t mma
     uint64_t* tma_bar = &bars[1 + 2 * team];
     uint64_t* mma_bar = &bars[2 + 2 * team];
     uint32_t* tmem_hold = (uint32_t*)(bars + 6);
@@ -476,6 +479,9 @@ __global__ void __launch_bounds__(EM_THREADS, 1) k_embed_qkv(const __grid_consta
         tmem_alloc(tmem_hold, 512);
         tmem_relinquish();
     }
+    for (int i = tid; i < EV_N; i += EM_THREADS)
+        pv[i] = i < 64 ? p.b1[i] : i < 128 ? p.b2[i - 64] : i < 192 ? p.lng[i - 128] : i < 256 ? p.lnb[i - 192]
+                                                                                       : p.bqkv[i - 256];
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -561,7 +567,7 @@ __global__ void __launch_bounds__(EM_THREADS, 1) k_embed_qkv(const __grid_consta
         tmem_ld32(trow + 32 * wg, v);
         tmem_wait_ld();
 #pragma unroll
-        for (int i = 0; i < 32; ++i) v[i] = act_f(v[i] + __ldg(p.b1 + 32 * wg + i), p.act);
+        for (int i = 0; i < 32; ++i) v[i] = act_f(v[i] + pv[32 * wg + i], p.act);
         if (p.amax) record_amax(p.amax, p.slot[1], v, 32, ri.valid);
         st_op<FE>(sH, r, v, 32, 32 * wg, 1.f);
         // second layer: the residual stream, then LN1
@@ -569,13 +575,13 @@ __global__ void __launch_bounds__(EM_THREADS, 1) k_embed_qkv(const __grid_consta
         tmem_ld32(trow + 32 * wg, v);
         tmem_wait_ld();
 #pragma unroll
-        for (int i = 0; i < 32; ++i) v[i] += __ldg(p.b2 + 32 * wg + i);
+        for (int i = 0; i < 32; ++i) v[i] += pv[64 + 32 * wg + i];
         {
             float4* zd = (float4*)(p.z + (size_t)prow_pad * D + 32 * wg);
 #pragma unroll
             for (int i = 0; i < 8; ++i) zd[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
         }
-        layernorm_split(v, v, p.lng, p.lnb, wg, r, team, red);
+        layernorm_split(v, v, pv + 128, pv + 192, wg, r, team, red);
         if (p.amax) record_amax(p.amax, p.slot[2], v, 32, ri.valid);
         st_op<FMT>(sH, r, v, 32, 32 * wg, p.qs[2], true);
         // fused Q/K/V projection: warpgroup 0 stores Q and V^T columns 0-31,
@@ -590,7 +596,7 @@ __global__ void __launch_bounds__(EM_THREADS, 1) k_embed_qkv(const __grid_consta
                 tmem_ld32(trow + 64 * wg + 32 * h, u);
                 tmem_wait_ld();
 #pragma unroll
-                for (int i = 0; i < 32; ++i) u[i] = fmaf(u[i], ds, __ldg(p.bqkv + 64 * wg + 32 * h + i));
+                for (int i = 0; i < 32; ++i) u[i] = fmaf(u[i], ds, pv[256 + 64 * wg + 32 * h + i]);
                 uint4* d4 = (uint4*)(dst + 32 * h);
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
@@ -607,7 +613,7 @@ __global__ void __launch_bounds__(EM_THREADS, 1) k_embed_qkv(const __grid_consta
 #pragma unroll
             for (int i = 0; i < 32; ++i) {
                 const int ch = 32 * wg + i;
-                const float t = ri.valid ? fmaf(u[i], ds, __ldg(p.bqkv + 128 + ch)) : 0.f;
+                const float t = ri.valid ? fmaf(u[i], ds, pv[256 + 128 + ch]) : 0.f;
                 p.vt[(size_t)ch * p.ldvt + prow_pad] = (uint16_t)(pack2<F16>(t, 0.f) & 0xffffu);
             }
         }
@@ -2020,7 +2026,8 @@ uint32_t embed_smem(int mode, int fmt) {
     const int ka = mode == 0 ? 1 : 2;
     // weights + two teams x (A operand, hidden tile, LayerNorm sums) + barriers + alignment;
     // at least 116 KB so that no two CTAs (512 TMEM columns each) share an SM
-    const uint32_t need = 64 * 128 * ka + 64 * 128 + 192 * 128 + 2 * (ka * ATOM + ATOM + 2 * 2 * 128 * 4) + 64 + 1024;
+    const uint32_t need =
+        64 * 128 * ka + 64 * 128 + 192 * 128 + 2 * (ka * ATOM + ATOM + 2 * 2 * 128 * 4) + EV_N * 4 + 64 + 1024;
     return need < 116 * 1024 ? 116 * 1024 : need;
 }
 uint32_t post_smem(int mode, int fmt) {
