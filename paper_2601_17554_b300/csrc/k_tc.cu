@@ -733,6 +733,9 @@ __global__ void __launch_bounds__(PT_THREADS, 1) k_post(const __grid_constant__ 
             mbar_arrive_expect_tx(tma_bar, ATOM);
             tma_load_2d(sO16, &map_o, 0, tile * ROWS, tma_bar);
         }
+        // the team's next attention-output tile into L2 (its TMA load is on the
+        // critical path of the next tile)
+        if (leader && tile + 2 * (int)gridDim.x < ntiles) tma_prefetch_2d(&map_o, 0, (tile + 2 * gridDim.x) * ROWS);
         float zr[32], v[32];   // this warpgroup's 32 columns of the residual row
         {
             const float4* zs = (const float4*)(p.z + (size_t)pp * D + 32 * wg);

@@ -91,6 +91,13 @@ MLPF_DEV void tma_load_2d(void* dst, const CUtensorMap* map, int c0, int c1, uin
         "l"(map), "r"(c0), "r"(c1), "r"(smem_u32(bar))
         : "memory");
 }
+// Prefetch a 2-D tensor tile into L2 (no shared memory, no completion to wait for)
+MLPF_DEV void tma_prefetch_2d(const CUtensorMap* map, int c0, int c1) {
+    asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(map), "r"(c0), "r"(c1)
+                 : "memory");
+}
+// Prefetch the 128-byte line holding addr into L2
+MLPF_DEV void prefetch_l2(const void* addr) { asm volatile("prefetch.global.L2 [%0];" ::"l"(addr)); }
 // 1-D bulk copy global -> shared (16-byte aligned, size multiple of 16)
 MLPF_DEV void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
     asm volatile(
