@@ -40,6 +40,9 @@ constexpr int NH = 4;            // heads
 constexpr int ROWS = 128;        // rows per tile (UMMA M)
 constexpr int ATOM = ROWS * 128; // bytes of a [128 x 64] bf16 swizzled atom column
 constexpr float LN_EPS = 1e-5f;
+// Q is stored multiplied by log2(e) / sqrt(16) (head width 16): the attention
+// kernels take the base-2 softmax exponent straight from Q K^T.
+constexpr float kQScale = 0.25f * 1.4426950408889634f;
 
 MLPF_DEV uint8_t* align1024(uint8_t* p) {
     return (uint8_t*)(((uintptr_t)p + 1023) & ~(uintptr_t)1023);
@@ -481,7 +484,7 @@ __global__ void __launch_bounds__(EM_THREADS, 1) k_embed_qkv(const __grid_consta
     }
     for (int i = tid; i < EV_N; i += EM_THREADS)
         pv[i] = i < 64 ? p.b1[i] : i < 128 ? p.b2[i - 64] : i < 192 ? p.lng[i - 128] : i < 256 ? p.lnb[i - 192]
-                                                                                       : p.bqkv[i - 256];
+                                                                                       : p.bqkv[i - 256] * (i < 320 ? kQScale : 1.f);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -588,7 +591,7 @@ __global__ void __launch_bounds__(EM_THREADS, 1) k_embed_qkv(const __grid_consta
         // warpgroup 1 stores K and V^T columns 32-63
         if (!run_mma([&] { issue_gemm<FMT>(tbase, sH, sWq, 192, 1); })) break;
         {
-            const float ds = p.ds[2];
+            const float ds = p.ds[2], dsqk = wg == 0 ? ds * kQScale : ds;
             float u[32];
             uint16_t* dst = (wg == 0 ? p.q : p.k) + (size_t)prow_pad * D;
 #pragma unroll
@@ -596,7 +599,7 @@ __global__ void __launch_bounds__(EM_THREADS, 1) k_embed_qkv(const __grid_consta
                 tmem_ld32(trow + 64 * wg + 32 * h, u);
                 tmem_wait_ld();
 #pragma unroll
-                for (int i = 0; i < 32; ++i) u[i] = fmaf(u[i], ds, pv[256 + 64 * wg + 32 * h + i]);
+                for (int i = 0; i < 32; ++i) u[i] = fmaf(u[i], dsqk, pv[256 + 64 * wg + 32 * h + i]);
                 uint4* d4 = (uint4*)(dst + 32 * h);
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
@@ -686,6 +689,7 @@ __global__ void __launch_bounds__(PT_THREADS, 1) k_post(const __grid_constant__ 
         else if (i < PV_BB) {
             const int n = MODE == 0 ? 192 : (MODE == 1 ? 64 : 256);
             v = (i - PV_BA) < n ? p.ba[i - PV_BA] : 0.f;
+            if (MODE == 0 && i - PV_BA < 64) v *= kQScale;   // Q bias
         } else v = MODE == 0 ? 0.f : p.bb[i - PV_BB];
         pv[i] = v;
     }
@@ -804,12 +808,13 @@ __global__ void __launch_bounds__(PT_THREADS, 1) k_post(const __grid_constant__ 
             if (!run_mma([&] { issue_gemm<FMT>(tbase, sA, sWa, 192, 1); })) break;
             // wg 0: Q and V channels 0..31; wg 1: K and V channels 32..63
             uint16_t* qk = (wg == 0 ? p.q : p.k) + (size_t)pp * D;
+            const float dsqk = wg == 0 ? p.ds[3] * kQScale : p.ds[3];
 #pragma unroll
             for (int q2 = 0; q2 < 2; ++q2) {
                 tmem_ld32(trow + 64 * wg + 32 * q2, v);
                 tmem_wait_ld();
 #pragma unroll
-                for (int i = 0; i < 32; ++i) v[i] = fmaf(v[i], p.ds[3], pv[PV_BA + 64 * wg + 32 * q2 + i]);
+                for (int i = 0; i < 32; ++i) v[i] = fmaf(v[i], dsqk, pv[PV_BA + 64 * wg + 32 * q2 + i]);
                 uint4* d4 = (uint4*)(qk + 32 * q2);
 #pragma unroll
                 for (int c = 0; c < 4; ++c)
@@ -1147,7 +1152,7 @@ __global__ void __launch_bounds__(at_threads<HPW>(), 1)
         const uint32_t tl = tbase + ((uint32_t)((warp & 3) * 32) << 16);  // this warp's lanes
         const uint32_t fmt = F16 ? 0u : 1u;
         const uint32_t IQK = idesc_f16(128, 64, fmt), IPV = idesc_f16(128, 16, fmt);
-        const float c = 0.25f * 1.4426950408889634f;  // log2(e) / sqrt(16)
+        const float c = 1.f;   // Q is pre-scaled (kQScale)
         const uint32_t one_addr = smem_u32(sOne);
         int q_it = 0;
         uint32_t g = 0;   // global key-tile counter (same sequence as the producer)
@@ -1544,7 +1549,7 @@ __global__ void __launch_bounds__(A32_THREADS, 1)
         const uint32_t colh = (uint32_t)h * 128;  // this head's four 32-column buffers
         const uint32_t fmt = F16 ? 0u : 1u;
         const uint32_t IQK = idesc_f16(128, 32, fmt), IPV = idesc_f16(128, 16, fmt);
-        const float c = 0.25f * 1.4426950408889634f;  // log2(e) / sqrt(16)
+        const float c = 1.f;   // Q is pre-scaled (kQScale)
         const uint32_t one_addr = smem_u32(sOne);
         uint8_t* sPh = sP + h * AT_PB;
         int q_it = 0;
@@ -1706,7 +1711,9 @@ __global__ void __launch_bounds__(A32_THREADS, 1)
 // row sums are one more MMA against a constant block of ones, so the warps
 // meet only at the K/V stage barriers.  Softmax rescaling is lazy: the exponent
 // reference of a row is raised (and O, l rescaled) only when a 16-key step
-// exceeds it by more than kStaleMax, so P <= 2^kStaleMax.
+// exceeds it by more than kStaleMax, so P <= 2^kStaleMax.  Q arrives scaled by
+// kQScale and the QK^T MMA starts from the negated references, so its output is
+// the exponent itself (no per-score multiply-add).
 // QR: query rows per work item, 128 (one CTA per SM, 16 consumer warps) or 64
 // (half items, two CTAs per SM of 8 consumer warps).
 template <int QR>
@@ -1715,8 +1722,7 @@ constexpr int aw_threads() { return NH * (QR / 32) * 32 + 32; }   // consumer wa
 //   1 row sums from FP32 adds instead of the ones-MMA (slower: off)
 //   2 exponentials before the maxima check, redone on a raised reference
 //     (faster with FP16 operands only)
-//   4 V fragments loaded at the start of a step, maxima checked against
-//     raw-score thresholds (5-7 % faster: on)
+//   4 V fragments loaded at the start of a step (5-7 % faster: on)
 template <bool F16>
 constexpr int kAwMode = F16 ? 6 : 4;
 template <int ST, int QR = 128>
@@ -1820,7 +1826,6 @@ __global__ void __launch_bounds__(aw_threads<QR>(), QR == 128 ? 1 : 2)
         const int h = warp / RB, rb = warp % RB;
         const int gq = lane >> 2, tq = lane & 3;
         const int mi = lane >> 3;                    // ldmatrix: matrix this lane addresses
-        const float c = 0.25f * 1.4426950408889634f;  // log2(e) / sqrt(16)
         const uint32_t ONE2 = F16 ? 0x3C003C00u : 0x3F803F80u;
         (void)ONE2;
         const uint32_t sQa = smem_u32(sQ), sKa = smem_u32(sK), sVa = smem_u32(sV);
@@ -1856,35 +1861,37 @@ __global__ void __launch_bounds__(aw_threads<QR>(), QR == 128 ? 1 : 2)
             if (lane == 0) mbar_arrive(&q_empty[qb]);
             // o: output accumulators; la: row sums (kSumF32: this lane's partial sums
             // over its key columns [mt][row half], reduced over the quad at the end;
-            // else the ones-MMA accumulator fragment [mt][4]); ref: exponent references
-            // thr (kHoist): raw-score level above which a row's reference is raised,
-            // (ref + kStaleMax) / c, so the check needs no multiply
-            float o[2][2][4], la[2][4], ref[2][2], thr[2][2];
+            // else the ones-MMA accumulator fragment [mt][4]); nr: the negated exponent
+            // references of the fragment's rows as an accumulator input, so that the
+            // QK^T MMA (Q pre-scaled) yields the exponent S - ref itself.  The first
+            // 16-key step always sets the references.
+            float o[2][2][4], la[2][4], nr[2][4];
 #pragma unroll
             for (int mt = 0; mt < 2; ++mt) {
 #pragma unroll
-                for (int e = 0; e < 4; ++e) { o[mt][0][e] = 0.f; o[mt][1][e] = 0.f; la[mt][e] = 0.f; }
-                ref[mt][0] = ref[mt][1] = -INFINITY;
-                thr[mt][0] = thr[mt][1] = -INFINITY;
+                for (int e = 0; e < 4; ++e) {
+                    o[mt][0][e] = 0.f;
+                    o[mt][1][e] = 0.f;
+                    la[mt][e] = 0.f;
+                    nr[mt][e] = 0.f;
+                }
             }
             for (int j = 0; j < nk; ++j, ++g) {
                 const uint32_t s = g % ST;
                 if (!warp_wait(&kv_full[s], (g / ST) & 1, ab, p.status, p.wait_ns)) { ok = false; break; }
                 const int kvalid = ke - kb - 64 * j;
                 const uint32_t kb = sKa + s * AT_KB, vb = sVa + s * AT_VB;
-                // S = Q K^T for keys 16q .. 16q+15 (two 8-key column tiles); the swizzle
-                // of rows 16q + k_row does not depend on q (16q is a multiple of 8)
+                // S - ref = Q K^T - ref for keys 16q .. 16q+15 (two 8-key column tiles);
+                // the swizzle of rows 16q + k_row does not depend on q (16q is a
+                // multiple of 8)
                 auto qk = [&](int q, float (&dst)[2][2][4]) {
                     uint32_t kf[4];
                     ldsm_x4(kb + koff + 2048u * q, kf[0], kf[1], kf[2], kf[3]);
 #pragma unroll
                     for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-                        for (int nt = 0; nt < 2; ++nt) {
-#pragma unroll
-                            for (int e = 0; e < 4; ++e) dst[mt][nt][e] = 0.f;
-                            mma16816<F16>(dst[mt][nt], qa[mt], kf[2 * nt], kf[2 * nt + 1]);
-                        }
+                        for (int nt = 0; nt < 2; ++nt)
+                            mma16816_c<F16>(dst[mt][nt], qa[mt], kf[2 * nt], kf[2 * nt + 1], nr[mt]);
                 };
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
@@ -1903,7 +1910,7 @@ __global__ void __launch_bounds__(aw_threads<QR>(), QR == 128 ? 1 : 2)
                                 for (int e = 0; e < 4; ++e)
                                     if (16 * q + 8 * nt + 2 * tq + (e & 1) >= kvalid) sc[mt][nt][e] = -INFINITY;
                     }
-                    // P = 2^(S c - ref) as the A fragments of PV (16 keys = one K-step).
+                    // P = 2^(S - ref) as the A fragments of PV (16 keys = one K-step).
                     // kSumF32: row sums from the FP32 exponentials (else an MMA of P
                     // against ones); kOptimistic: exponentials first, against the
                     // current references, redone if a reference is raised (else the
@@ -1915,37 +1922,39 @@ __global__ void __launch_bounds__(aw_threads<QR>(), QR == 128 ? 1 : 2)
                         for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
                             for (int hr = 0; hr < 2; ++hr) {
-                                const float2 nr = make_float2(-ref[mt][hr], -ref[mt][hr]);
-                                const float2 cc = make_float2(c, c);
-                                const float2 x0 = __ffma2_rn(make_float2(sc[mt][0][2 * hr], sc[mt][0][2 * hr + 1]), cc, nr);
-                                const float2 x1 = __ffma2_rn(make_float2(sc[mt][1][2 * hr], sc[mt][1][2 * hr + 1]), cc, nr);
+                                const float x0 = sc[mt][0][2 * hr], x1 = sc[mt][0][2 * hr + 1];
+                                const float x2 = sc[mt][1][2 * hr], x3 = sc[mt][1][2 * hr + 1];
                                 if constexpr (kSumF32) {
-                                    const float e0 = ex2_approx(x0.x), e1 = ex2_approx(x0.y);
-                                    const float e2 = ex2_approx(x1.x), e3 = ex2_approx(x1.y);
+                                    const float e0 = ex2_approx(x0), e1 = ex2_approx(x1);
+                                    const float e2 = ex2_approx(x2), e3 = ex2_approx(x3);
                                     ls[mt][hr] = (e0 + e1) + (e2 + e3);
                                     pa[mt][hr] = pack2<F16>(e0, e1);
                                     pa[mt][2 + hr] = pack2<F16>(e2, e3);
                                 } else {
-                                    pa[mt][hr] = exp2_pair<F16>(x0.x, x0.y);
-                                    pa[mt][2 + hr] = exp2_pair<F16>(x1.x, x1.y);
+                                    pa[mt][hr] = exp2_pair<F16>(x0, x1);
+                                    pa[mt][2 + hr] = exp2_pair<F16>(x2, x3);
                                 }
                             }
                     };
+                    const bool first = j == 0 && q == 0;
                     float lm[2][2];
-                    bool raise = false;
-                    if constexpr (kOptimistic) exps();
+                    bool raise = first;
+                    if constexpr (kOptimistic) {
+                        if (!first) exps();
+                    }
 #pragma unroll
                     for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
                         for (int hr = 0; hr < 2; ++hr) {
                             lm[mt][hr] = max3f(fmaxf(sc[mt][0][2 * hr], sc[mt][0][2 * hr + 1]), sc[mt][1][2 * hr],
                                                sc[mt][1][2 * hr + 1]);
-                            if constexpr (kHoist) raise |= lm[mt][hr] > thr[mt][hr];
-                            else raise |= lm[mt][hr] * c > ref[mt][hr] + kStaleMax;
+                            raise |= lm[mt][hr] > kStaleMax;
                         }
                     const bool raised = __any_sync(0xffffffffu, raise);
                     if (raised) {
-                        // new reference: the running row max (over the quad), then rescale
+                        // raise each row's reference by dr = (row max over the quad) - ref
+                        // (never lowered after the first step), rescale O and l by 2^-dr
+                        // and shift this step's exponents by -dr
 #pragma unroll
                         for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
@@ -1953,15 +1962,17 @@ __global__ void __launch_bounds__(aw_threads<QR>(), QR == 128 ? 1 : 2)
                                 float mx = lm[mt][hr];
                                 mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
                                 mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
-                                const float rn = fmaxf(ref[mt][hr], mx * c);
-                                const float a = ex2_approx(ref[mt][hr] - rn);
-                                ref[mt][hr] = rn;
-                                thr[mt][hr] = (rn + kStaleMax) * (1.f / c);   // raw-score threshold
+                                const float dr = first ? mx : fmaxf(mx, 0.f);
+                                const float a = first ? 0.f : ex2_approx(-dr);
+                                nr[mt][2 * hr] -= dr;
+                                nr[mt][2 * hr + 1] -= dr;
 #pragma unroll
                                 for (int e = 0; e < 2; ++e) {
                                     o[mt][0][2 * hr + e] *= a;
                                     o[mt][1][2 * hr + e] *= a;
                                     if constexpr (!kSumF32) la[mt][2 * hr + e] *= a;
+                                    sc[mt][0][2 * hr + e] -= dr;
+                                    sc[mt][1][2 * hr + e] -= dr;
                                 }
                                 if constexpr (kSumF32) la[mt][hr] *= a;
                             }

@@ -250,6 +250,23 @@ MLPF_DEV void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, u
                  : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
                  : "r"(addr));
 }
+// d[16x8] = a[16x16] * b[16x8] + c[16x8] with c in separate registers (kept
+// across calls), FP32 accumulate; 16-bit operands FP16 or BF16
+template <bool F16>
+MLPF_DEV void mma16816_c(float* d, const uint32_t* a, uint32_t b0, uint32_t b1, const float* c) {
+    if constexpr (F16)
+        asm("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+            "{%10, %11, %12, %13};"
+            : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1), "f"(c[0]), "f"(c[1]), "f"(c[2]),
+              "f"(c[3]));
+    else
+        asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+            "{%10, %11, %12, %13};"
+            : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1), "f"(c[0]), "f"(c[1]), "f"(c[2]),
+              "f"(c[3]));
+}
 // d[16x8] += a[16x16] * b[16x8], FP32 accumulate; 16-bit operands FP16 or BF16
 template <bool F16>
 MLPF_DEV void mma16816(float* d, const uint32_t* a, uint32_t b0, uint32_t b1) {
