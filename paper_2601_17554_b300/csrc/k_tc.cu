@@ -52,22 +52,52 @@ MLPF_DEV uint8_t* align1024(uint8_t* p) {
 // approximation of Abramowitz & Stegun, Handbook of Mathematical Functions,
 // formula 7.1.26 (Hastings): for z >= 0, erf(z) = 1 - t (a1 + t (a2 + t (a3 + t (a4
 // + t a5)))) e^(-z^2), t = 1 / (1 + p z), |error| <= 1.5e-7; erf(-z) = -erf(z).
-// The reciprocal and the exponential run on the MUFU (approximate, ~1 ulp), which
-// is idle in the GEMM epilogues; the result is far below the 16-bit rounding of
-// the operands it feeds.  Checked against the FP32 path's erff-based GELU by
-// mlpf_eval_activation.
-MLPF_DEV float gelu_f(float v) {
-    constexpr float kP = 0.3275911f, kA1 = 0.254829592f, kA2 = -0.284496736f, kA3 = 1.421413741f,
-                    kA4 = -1.453152027f, kA5 = 1.061405429f;
-    const float z = fabsf(v) * 0.70710678118654752f;
-    float t, e;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(t) : "f"(fmaf(kP, z, 1.f)));
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(-z * z * 1.4426950408889634f));
-    const float poly = t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, kA5, kA4), kA3), kA2), kA1);
-    const float erf_abs = fmaf(-poly, e, 1.f);
-    return 0.5f * v * (1.f + copysignf(erf_abs, v));
+// Two values at a time: the multiplies and multiply-adds are packed FP32x2 ops
+// (one issue for both values), the reciprocal and the exponential run on the
+// MUFU (approximate, ~1 ulp), which is idle in the GEMM epilogues.  The result is
+// far below the 16-bit rounding of the operands it feeds.  Checked against the
+// FP32 path's erff-based GELU by mlpf_eval_activation.
+MLPF_DEV float2 gelu2_f(float va, float vb) {
+    // Horner coefficients negated, so that the last step gives 1 - poly e directly
+    const float2 kP = make_float2(0.3275911f, 0.3275911f), kNA1 = make_float2(-0.254829592f, -0.254829592f),
+                 kNA2 = make_float2(0.284496736f, 0.284496736f), kNA3 = make_float2(-1.421413741f, -1.421413741f),
+                 kNA4 = make_float2(1.453152027f, 1.453152027f), kNA5 = make_float2(-1.061405429f, -1.061405429f);
+    const float2 one = make_float2(1.f, 1.f);
+    const float2 v = make_float2(va, vb);
+    // z = |v| / sqrt 2; -z^2 log2(e) = v^2 (-log2(e) / 2)
+    const float2 z = __fmul2_rn(make_float2(fabsf(va), fabsf(vb)), make_float2(0.70710678118654752f, 0.70710678118654752f));
+    const float2 den = __ffma2_rn(kP, z, one);
+    const float2 w = __fmul2_rn(__fmul2_rn(v, v), make_float2(-0.72134752044448170f, -0.72134752044448170f));
+    float2 t, e;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(t.x) : "f"(den.x));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(t.y) : "f"(den.y));
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e.x) : "f"(w.x));
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e.y) : "f"(w.y));
+    float2 q = __ffma2_rn(t, kNA5, kNA4);
+    q = __ffma2_rn(t, q, kNA3);
+    q = __ffma2_rn(t, q, kNA2);
+    q = __ffma2_rn(t, q, kNA1);
+    q = __fmul2_rn(t, q);                       // -poly
+    const float2 ea = __ffma2_rn(q, e, one);    // erf(|v| / sqrt 2)
+    const float2 es = make_float2(copysignf(ea.x, va), copysignf(ea.y, vb));
+    const float2 h = __fmul2_rn(v, make_float2(0.5f, 0.5f));
+    return __ffma2_rn(h, es, h);                // v (1 + erf) / 2
 }
-MLPF_DEV float act_f(float v, int act) { return act == 1 ? fmaxf(v, 0.f) : gelu_f(v); }
+// activation (0 GELU, 1 ReLU) of N (even) values in place
+template <int N>
+MLPF_DEV void act_n(float* v, int act) {
+    if (act == 1) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) v[i] = fmaxf(v[i], 0.f);
+    } else {
+#pragma unroll
+        for (int i = 0; i < N; i += 2) {
+            const float2 g = gelu2_f(v[i], v[i + 1]);
+            v[i] = g.x;
+            v[i + 1] = g.y;
+        }
+    }
+}
 
 // GEMM operand formats of the row-tile kernels.  A 128-byte swizzle atom holds
 // 64 16-bit or 128 E4M3 K-elements; one K-step is 32 bytes in every format
@@ -570,7 +600,8 @@ __global__ void __launch_bounds__(EM_THREADS, 1) k_embed_qkv(const __grid_consta
         tmem_ld32(trow + 32 * wg, v);
         tmem_wait_ld();
 #pragma unroll
-        for (int i = 0; i < 32; ++i) v[i] = act_f(v[i] + pv[32 * wg + i], p.act);
+        for (int i = 0; i < 32; ++i) v[i] += pv[32 * wg + i];
+        act_n<32>(v, p.act);
         if (p.amax) record_amax(p.amax, p.slot[1], v, 32, ri.valid);
         st_op<FE>(sH, r, v, 32, 32 * wg, 1.f);
         // second layer: the residual stream, then LN1
@@ -784,7 +815,8 @@ __global__ void __launch_bounds__(PT_THREADS, 1) k_post(const __grid_constant__ 
                 tmem_wait_ld();
 #pragma unroll
                 for (int i = 0; i < 32; ++i)
-                    v[i] = act_f(fmaf(v[i], p.ds[1], pv[PV_BUP + 128 * half + 64 * wg + 32 * q2 + i]), p.act);
+                    v[i] = fmaf(v[i], p.ds[1], pv[PV_BUP + 128 * half + 64 * wg + 32 * q2 + i]);
+                act_n<32>(v, p.act);
                 if (p.amax) record_amax(p.amax, p.slot[2], v, 32, ri.valid);
                 st_op<FMT>(sH, r, v, 32, 64 * wg + 32 * q2, p.qs[2]);
             }
@@ -843,7 +875,8 @@ __global__ void __launch_bounds__(PT_THREADS, 1) k_post(const __grid_constant__ 
             tmem_ld32(trow + 32 * wg, v);
             tmem_wait_ld();
 #pragma unroll
-            for (int i = 0; i < 32; ++i) v[i] = act_f(v[i] + pv[PV_BA + 32 * wg + i], p.act);
+            for (int i = 0; i < 32; ++i) v[i] += pv[PV_BA + 32 * wg + i];
+            act_n<32>(v, p.act);
             if (p.amax) record_amax(p.amax, p.slot[4], v, 32, ri.valid);
             st_op<FH>(sH, r, v, 32, 32 * wg, 1.f);
             if (!run_mma([&] { issue_gemm<FH>(tbase + 64, sH, sWb, 16, 1); })) break;
@@ -870,7 +903,8 @@ __global__ void __launch_bounds__(PT_THREADS, 1) k_post(const __grid_constant__ 
                     tmem_wait_ld();
 #pragma unroll
                     for (int i = 0; i < 32; ++i)
-                        v[i] = act_f(v[i] + pv[PV_BA + 128 * half + 64 * wg + 32 * q2 + i], p.act);
+                        v[i] += pv[PV_BA + 128 * half + 64 * wg + 32 * q2 + i];
+                    act_n<32>(v, p.act);
                     if (p.amax) record_amax(p.amax, p.slot[4], v, 32, ri.valid);
                     st_op<FH>(sH, r, v, 32, 64 * wg + 32 * q2, 1.f);
                 }
@@ -1719,7 +1753,8 @@ __global__ void __launch_bounds__(A32_THREADS, 1)
 template <int QR>
 constexpr int aw_threads() { return NH * (QR / 32) * 32 + 32; }   // consumer warps + a TMA producer warp
 // Mode bits of the warp kernel (each measured on the 512-event batch):
-//   1 row sums from FP32 adds instead of the ones-MMA (slower: off)
+//   1 row sums from packed FP32 adds instead of the ones-MMA (no measurable
+//     change with BF16; not for FP16, whose exponentials come packed from the MUFU)
 //   2 exponentials before the maxima check, redone on a raised reference
 //     (faster with FP16 operands only)
 //   4 V fragments loaded at the start of a step (5-7 % faster: on)
@@ -1859,9 +1894,9 @@ __global__ void __launch_bounds__(aw_threads<QR>(), QR == 128 ? 1 : 2)
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&q_empty[qb]);
-            // o: output accumulators; la: row sums (kSumF32: this lane's partial sums
-            // over its key columns [mt][row half], reduced over the quad at the end;
-            // else the ones-MMA accumulator fragment [mt][4]); nr: the negated exponent
+            // o: output accumulators; la: row sums in the accumulator fragment layout
+            // (kSumF32: this lane's partial sums over its key columns, reduced over the
+            // pair and the quad at the end; else the ones-MMA accumulator); nr: the negated exponent
             // references of the fragment's rows as an accumulator input, so that the
             // QK^T MMA (Q pre-scaled) yields the exponent S - ref itself.  The first
             // 16-key step always sets the references.
@@ -1916,7 +1951,7 @@ __global__ void __launch_bounds__(aw_threads<QR>(), QR == 128 ? 1 : 2)
                     // current references, redone if a reference is raised (else the
                     // maxima are checked first).
                     uint32_t pa[2][4];
-                    float ls[2][2];
+                    float2 ls[2][2];
                     auto exps = [&]() {
 #pragma unroll
                         for (int mt = 0; mt < 2; ++mt)
@@ -1927,7 +1962,7 @@ __global__ void __launch_bounds__(aw_threads<QR>(), QR == 128 ? 1 : 2)
                                 if constexpr (kSumF32) {
                                     const float e0 = ex2_approx(x0), e1 = ex2_approx(x1);
                                     const float e2 = ex2_approx(x2), e3 = ex2_approx(x3);
-                                    ls[mt][hr] = (e0 + e1) + (e2 + e3);
+                                    ls[mt][hr] = __fadd2_rn(make_float2(e0, e1), make_float2(e2, e3));
                                     pa[mt][hr] = pack2<F16>(e0, e1);
                                     pa[mt][2 + hr] = pack2<F16>(e2, e3);
                                 } else {
@@ -1970,20 +2005,23 @@ __global__ void __launch_bounds__(aw_threads<QR>(), QR == 128 ? 1 : 2)
                                 for (int e = 0; e < 2; ++e) {
                                     o[mt][0][2 * hr + e] *= a;
                                     o[mt][1][2 * hr + e] *= a;
-                                    if constexpr (!kSumF32) la[mt][2 * hr + e] *= a;
+                                    la[mt][2 * hr + e] *= a;
                                     sc[mt][0][2 * hr + e] -= dr;
                                     sc[mt][1][2 * hr + e] -= dr;
                                 }
-                                if constexpr (kSumF32) la[mt][hr] *= a;
                             }
                     }
                     if (!kOptimistic || raised) exps();
                     if constexpr (kSumF32) {
 #pragma unroll
-                        for (int mt = 0; mt < 2; ++mt) {
-                            la[mt][0] += ls[mt][0];
-                            la[mt][1] += ls[mt][1];
-                        }
+                        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                            for (int hr = 0; hr < 2; ++hr) {
+                                const float2 t =
+                                    __fadd2_rn(make_float2(la[mt][2 * hr], la[mt][2 * hr + 1]), ls[mt][hr]);
+                                la[mt][2 * hr] = t.x;
+                                la[mt][2 * hr + 1] = t.y;
+                            }
                     }
                     // V fragments: channels 0-7 / 8-15 of the head, keys 16q .. 16q+15
                     if constexpr (!kHoist) ldsm_x4(vb + sw128_off(v_row, 2 * q + v_sub), vf[0], vf[1], vf[2], vf[3]);
@@ -2006,7 +2044,7 @@ __global__ void __launch_bounds__(aw_threads<QR>(), QR == 128 ? 1 : 2)
                 for (int hr = 0; hr < 2; ++hr) {
                     float l;
                     if constexpr (kSumF32) {
-                        l = la[mt][hr];
+                        l = la[mt][2 * hr] + la[mt][2 * hr + 1];
                         l += __shfl_xor_sync(0xffffffffu, l, 1);
                         l += __shfl_xor_sync(0xffffffffu, l, 2);
                     } else {
@@ -2029,9 +2067,14 @@ __global__ void __launch_bounds__(aw_threads<QR>(), QR == 128 ? 1 : 2)
     }
 }
 
+// the epilogues' activation on an array: thread i takes elements 2i and 2i + 1
 __global__ void k_eval_act_tc(const float* __restrict__ x, float* __restrict__ y, int n, int act) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) y[i] = act_f(x[i], act);
+    const int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (i >= n) return;
+    float v[2] = {x[i], i + 1 < n ? x[i + 1] : 0.f};
+    act_n<2>(v, act);
+    y[i] = v[0];
+    if (i + 1 < n) y[i + 1] = v[1];
 }
 
 // ---------------------------------------------------------------- host side
@@ -2174,7 +2217,7 @@ void set_attrs() {
 }  // namespace
 
 void tc_eval_activation(const float* x, float* y, int n, int act, cudaStream_t st) {
-    if (n > 0) k_eval_act_tc<<<(n + 255) / 256, 256, 0, st>>>(x, y, n, act);
+    if (n > 0) k_eval_act_tc<<<((n + 1) / 2 + 255) / 256, 256, 0, st>>>(x, y, n, act);
 }
 
 bool tc_prepare_weights(Model& m) {

@@ -1,6 +1,7 @@
 """The tensor-core epilogues' GELU (erf of Abramowitz & Stegun 7.1.26, |error| <=
-1.5e-7, with MUFU reciprocal and exponential) against the FP32 path's GELU from
-CUDA erff, on device arrays through mlpf_eval_activation.
+1.5e-7, evaluated two values at a time with packed FP32x2 arithmetic and MUFU
+reciprocal and exponential) against the FP32 path's GELU from CUDA erff, on device
+arrays through mlpf_eval_activation (odd lengths exercise the unpaired last value).
 
 Bound: the erf error 1.5e-7 plus about 2 ulp from the approximate reciprocal and
 exponential gives |GELU_tc - GELU_f32| <= 4e-7 |x| (Phi errs by half the erf
@@ -44,6 +45,15 @@ def test_gelu_tensor_core_form_matches_erff():
     xs = x[:2_000_001].astype(np.float64)
     exact = 0.5 * xs * (1 + erf(xs / np.sqrt(2)))
     assert np.max(np.abs(y_tc[:2_000_001] - exact) - 4e-7 * np.abs(xs)) <= 1e-7
+
+
+def test_odd_length_tail():
+    x = np.linspace(-3, 3, 1001, dtype=np.float32)
+    y = _eval(1, 0, x).astype(np.float64)
+    from scipy.special import erf
+    xs = x.astype(np.float64)
+    exact = 0.5 * xs * (1 + erf(xs / np.sqrt(2)))
+    assert np.max(np.abs(y - exact) - 4e-7 * np.abs(xs)) <= 1e-7
 
 
 def test_relu_identical():
