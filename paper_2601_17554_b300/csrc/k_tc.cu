@@ -555,9 +555,18 @@ __global__ void __launch_bounds__(EM_THREADS, 1) k_embed_qkv(const __grid_consta
         const int p0 = tile * ROWS;
         const int prow_pad = p0 + r;
         const RowInfo ri = row_info(p.blk, nblk, prow_pad);
+        // the team's next tile: its row's block entry now, its feature row into L2
+        // after the first GEMM (a tile otherwise starts with two dependent HBM reads)
+        const int pn = prow_pad + 2 * (int)gridDim.x * ROWS;
+        int2 nb = make_int2(0, 0);   // packed row of the block's first row, valid rows
+        if (tile + 2 * (int)gridDim.x < ntiles && (pn >> 6) < nblk) {
+            const int4 e = p.blk[pn >> 6];
+            nb = make_int2(e.y, e.z);
+        }
         if (TMA_HP && leader) {
             mbar_arrive_expect_tx(tma_bar, ATOM);
             tma_load_2d(sA + ATOM, &map_hp, 0, p0, tma_bar);
+            if (tile + 2 * (int)gridDim.x < ntiles) tma_prefetch_2d(&map_hp, 0, p0 + 2 * gridDim.x * ROWS);
         }
         float v[32];
         // this warpgroup's 32 of the row's 42 features (zero padded to 64)
@@ -597,6 +606,11 @@ __global__ void __launch_bounds__(EM_THREADS, 1) k_embed_qkv(const __grid_consta
         aph ^= 1;
         // embedding FFN, first layer
         if (!run_mma([&] { issue_gemm<FE>(tbase, sA, sW1, 64, KA); })) break;
+        if ((pn & 63) < nb.y) {
+            const float* xn = p.x + (size_t)(nb.x + (pn & 63)) * 42 + 32 * wg;   // this warpgroup's features
+            prefetch_l2(xn);
+            prefetch_l2(xn + (wg == 0 ? 31 : 9));
+        }
         tmem_ld32(trow + 32 * wg, v);
         tmem_wait_ld();
 #pragma unroll
@@ -801,6 +815,8 @@ __global__ void __launch_bounds__(PT_THREADS, 1) k_post(const __grid_constant__ 
         tmem_wait_ld();
 #pragma unroll
         for (int i = 0; i < 32; ++i) zr[i] += fmaf(v[i], p.ds[0], pv[PV_BO + 32 * wg + i]);
+        // the element's log pT and log E for the decode at the end of the tile
+        if (MODE == 2 && wg == 0 && ri.valid) prefetch_l2(p.x + (size_t)ri.prow * 42 + 8);
         layernorm_split(zr, v, pv + PV_LN2G, pv + PV_LN2B, wg, r, team, red);
         if (p.amax) record_amax(p.amax, p.slot[1], v, 32, ri.valid);
         st_op<FMT>(sA, r, v, 32, 32 * wg, p.qs[1], true);
