@@ -242,7 +242,7 @@ static mlpf_status ensure_workspace(Model& m, int total, int n_events, bool tc) 
                  o_o = take(cap_t * d * 4), o_hid = take(cap_t * std::max(F, d) * 4),
                  o_hp = take(cap_t * d * 4), o_hr = take(cap_t * d * 4), o_raw = take(cap_t * 5 * 4);
     const int64_t tpad = (int64_t)align_up(cap_t + 64 * cap_e, 128);
-    size_t o_tz = 0, o_tq = 0, o_tk = 0, o_to = 0, o_tvt = 0, o_thp = 0, o_blk = 0, o_items = 0;
+    size_t o_tz = 0, o_tq = 0, o_tk = 0, o_to = 0, o_tvt = 0, o_thp = 0, o_blk = 0, o_kmax = 0, o_items = 0;
     if (want_tc) {
         o_tz = take(tpad * 64 * 4);
         o_tq = take(tpad * 64 * 2);
@@ -251,6 +251,7 @@ static mlpf_status ensure_workspace(Model& m, int total, int n_events, bool tc) 
         o_tvt = take(tpad * 64 * 2);
         o_thp = take(tpad * 64 * 2);
         o_blk = take((tpad / 64) * sizeof(int4));
+        o_kmax = take((tpad / 64) * 4 * sizeof(float));
         o_items = take((tpad / 128 + cap_e + 1) * sizeof(int4));
     }
     const size_t o_cnt = take(64 * sizeof(int));
@@ -284,6 +285,7 @@ static mlpf_status ensure_workspace(Model& m, int total, int n_events, bool tc) 
         w.tvt = (__nv_bfloat16*)(b + o_tvt);
         w.thp = (__nv_bfloat16*)(b + o_thp);
         w.blk = (int4*)(b + o_blk);
+        w.kmax = (float*)(b + o_kmax);
         w.items = (int4*)(b + o_items);
         CK(cudaMemset(w.tvt, 0, tpad * 64 * 2));
         if (!tc_make_maps(m)) return MLPF_E_CUDA;

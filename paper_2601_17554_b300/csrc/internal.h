@@ -61,6 +61,7 @@ struct Workspace {
     float* tz = nullptr;                 // [tpad, 64] residual stream fp32
     __nv_bfloat16 *tq = nullptr, *tk = nullptr, *to = nullptr, *tvt = nullptr, *thp = nullptr;
     int4* blk = nullptr;                 // per 64-row block: event, packed row, n valid
+    float* kmax = nullptr;               // per 64-row block and head: largest K-row norm
     int4* items = nullptr;               // attention work items
     int* counters = nullptr;             // [0]=n_items [1]=tpad rows [2..3]=attn tickets
     CUtensorMap map_q, map_q64, map_k, map_o, map_vt, map_hp;

@@ -379,6 +379,7 @@ struct EmbedParams {
     const uint16_t* hp;  // MODE 1: h_pid rows (16-bit), read per thread in E4M3 mode and calibration
     float* z;
     uint16_t *q, *k, *vt;
+    float* kmax;         // [64-row block][head] largest K-row norm (store_kmax)
     long ldvt;
     unsigned* status;
     uint64_t wait_ns;
@@ -404,6 +405,7 @@ struct PostParams {
     const float *ba, *bb;           // mode 0: bqkv (192); 1: cls b1 (64), b2 (16); 2: heads b1 (256), b2 (16)
     float* z;
     uint16_t *q, *k, *vt, *hp;
+    float* kmax;                    // mode 0: [64-row block][head] largest K-row norm
     long ldvt;
     float* logits;
     float* reg;
@@ -439,6 +441,38 @@ MLPF_DEV bool team_sync_or(int team, bool pred) {
 
 MLPF_DEV void team_bar(int team) {
     asm volatile("bar.sync %0, 256;" ::"r"(1 + team) : "memory");
+}
+
+// Largest K-row norm per head over each 64-row block of a 128-row tile: the
+// attention kernel's bound on the scores of a key tile, |q . k| <= |q| max |k|
+// (Cauchy-Schwarz), with 1 % added for the 16-bit rounding of the stored K.  Run
+// by the 128 threads of warpgroup 1 (the K half) of a team, each with the squared
+// per-head norms ss of its row (0 for padding rows); scratch: 16 floats of the
+// team's shared memory that are free at this point.
+MLPF_DEV void store_kmax(float (&ss)[4], float* scratch, int r, int team, float* kmax, int tile) {
+#pragma unroll
+    for (int hh = 0; hh < 4; ++hh)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) ss[hh] = fmaxf(ss[hh], __shfl_xor_sync(0xffffffffu, ss[hh], off));
+    if ((r & 31) == 0) {
+#pragma unroll
+        for (int hh = 0; hh < 4; ++hh) scratch[(r >> 5) * 4 + hh] = ss[hh];
+    }
+    asm volatile("bar.sync %0, 128;" ::"r"(3 + team) : "memory");
+    if (r < 8) {
+        const int b = r >> 2, hh = r & 3;   // 64-row block b of the tile: warps 2b, 2b + 1
+        kmax[(size_t)(2 * tile + b) * 4 + hh] = sqrtf(fmaxf(scratch[8 * b + hh], scratch[8 * b + 4 + hh])) * 1.01f;
+    }
+}
+// squared norms of the two 16-channel heads in 32 values
+MLPF_DEV void head_sq2(const float* u, float& s0, float& s1) {
+    s0 = 0.f;
+    s1 = 0.f;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        s0 = fmaf(u[i], u[i], s0);
+        s1 = fmaf(u[16 + i], u[16 + i], s1);
+    }
 }
 
 // LayerNorm of a 64-column row whose columns are split between the two
@@ -637,7 +671,7 @@ __global__ void __launch_bounds__(EM_THREADS, 1) k_embed_qkv(const __grid_consta
         if (!run_mma([&] { issue_gemm<FMT>(tbase, sH, sWq, 192, 1); })) break;
         {
             const float ds = p.ds[2], dsqk = wg == 0 ? ds * kQScale : ds;
-            float u[32];
+            float u[32], ss[4];
             uint16_t* dst = (wg == 0 ? p.q : p.k) + (size_t)prow_pad * D;
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
@@ -645,6 +679,7 @@ __global__ void __launch_bounds__(EM_THREADS, 1) k_embed_qkv(const __grid_consta
                 tmem_wait_ld();
 #pragma unroll
                 for (int i = 0; i < 32; ++i) u[i] = fmaf(u[i], dsqk, pv[256 + 64 * wg + 32 * h + i]);
+                if (wg == 1) head_sq2(u, ss[2 * h], ss[2 * h + 1]);
                 uint4* d4 = (uint4*)(dst + 32 * h);
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
@@ -655,6 +690,11 @@ __global__ void __launch_bounds__(EM_THREADS, 1) k_embed_qkv(const __grid_consta
                     w4.w = pack2<F16>(u[8 * c + 6], u[8 * c + 7]);
                     d4[c] = w4;
                 }
+            }
+            if (wg == 1) {
+#pragma unroll
+                for (int hh = 0; hh < 4; ++hh) ss[hh] = ri.valid ? ss[hh] : 0.f;
+                store_kmax(ss, red, r, team, p.kmax, tile);
             }
             tmem_ld32(trow + 128 + 32 * wg, u);
             tmem_wait_ld();
@@ -857,17 +897,24 @@ __global__ void __launch_bounds__(PT_THREADS, 1) k_post(const __grid_constant__ 
             // wg 0: Q and V channels 0..31; wg 1: K and V channels 32..63
             uint16_t* qk = (wg == 0 ? p.q : p.k) + (size_t)pp * D;
             const float dsqk = wg == 0 ? p.ds[3] * kQScale : p.ds[3];
+            float ss[4];
 #pragma unroll
             for (int q2 = 0; q2 < 2; ++q2) {
                 tmem_ld32(trow + 64 * wg + 32 * q2, v);
                 tmem_wait_ld();
 #pragma unroll
                 for (int i = 0; i < 32; ++i) v[i] = fmaf(v[i], dsqk, pv[PV_BA + 64 * wg + 32 * q2 + i]);
+                if (wg == 1) head_sq2(v, ss[2 * q2], ss[2 * q2 + 1]);
                 uint4* d4 = (uint4*)(qk + 32 * q2);
 #pragma unroll
                 for (int c = 0; c < 4; ++c)
                     d4[c] = make_uint4(pack2<F16>(v[8 * c], v[8 * c + 1]), pack2<F16>(v[8 * c + 2], v[8 * c + 3]),
                                        pack2<F16>(v[8 * c + 4], v[8 * c + 5]), pack2<F16>(v[8 * c + 6], v[8 * c + 7]));
+            }
+            if (wg == 1) {
+#pragma unroll
+                for (int hh = 0; hh < 4; ++hh) ss[hh] = ri.valid ? ss[hh] : 0.f;
+                store_kmax(ss, red, r, team, p.kmax, tile);
             }
             tmem_ld32(trow + 128 + 32 * wg, v);
             tmem_wait_ld();
@@ -1000,6 +1047,7 @@ struct AttnParams {
     uint64_t wait_ns;
     int debug_stall;
     int window;   // > 0: the query tile y attends to keys of 128-row blocks y - window .. y + window
+    const float* kmax;   // [64-row block][head] largest K-row norm (warp-MMA kernel)
 };
 
 // Keys [kb, ke) of the event that query tile y (128 rows) attends to.
@@ -1015,6 +1063,9 @@ MLPF_DEV void key_range(int y, int n, int window, int& kb, int& ke) {
 // Largest excess (log2 units) of a tile's row max over the exponent reference
 // before the tile is redone: P <= 16, far inside the FP16 and BF16 ranges.
 constexpr float kStaleMax = 4.f;
+// Largest exponent a key tile may reach without the maxima check (the warp
+// kernel's bound path): P <= 2^15, inside the FP16 range (65504).
+constexpr float kLimit = 15.f;
 
 MLPF_DEV float max3f(float a, float b, float c) {
     float r;
@@ -1768,22 +1819,25 @@ __global__ void __launch_bounds__(A32_THREADS, 1)
 // (half items, two CTAs per SM of 8 consumer warps).
 template <int QR>
 constexpr int aw_threads() { return NH * (QR / 32) * 32 + 32; }   // consumer warps + a TMA producer warp
-// Mode bits of the warp kernel (each measured on the 512-event batch):
-//   1 row sums from packed FP32 adds instead of the ones-MMA (no measurable
-//     change with BF16; not for FP16, whose exponentials come packed from the MUFU)
+// Mode bits of the warp kernel's checked path (each measured on the 512-event
+// batch; the default uses none: with the key-tile bound, most tiles skip the
+// checked path and its register-lean form is fastest in both formats):
 //   2 exponentials before the maxima check, redone on a raised reference
-//     (faster with FP16 operands only)
-//   4 V fragments loaded at the start of a step (5-7 % faster: on)
+//   8 maxima checked once per two 16-key steps (fewer votes, more registers)
+//  16 Q fragments re-read from shared memory for every block of steps instead of
+//     held in registers (the Q tile then stays until the item's last key tile)
 template <bool F16>
-constexpr int kAwMode = F16 ? 6 : 4;
+constexpr int kAwMode = 0;
 template <int ST, int QR = 128>
 struct AwLayout {
     static constexpr uint32_t QB = QR * 128;   // Q tile bytes
     static constexpr uint32_t OFF_K = 2 * QB;
     static constexpr uint32_t OFF_V = OFF_K + ST * AT_KB;
-    static constexpr uint32_t OFF_BAR = OFF_V + ST * AT_VB;
+    static constexpr uint32_t OFF_BAR = OFF_V + ST * AT_VB;   // barriers, item info, abort flag (< 256 B)
+    static constexpr uint32_t OFF_KN = OFF_BAR + 256;         // [ST][4] key-tile norm bounds
     static constexpr uint32_t SMEM = OFF_BAR + 512 + 1024;
 };
+static_assert((6 + 2 * 8) * 8 + 2 * 16 + 4 <= 256, "warp attention barrier area");
 
 template <bool F16, int ST, int AM, int QR = 128>
 __global__ void __launch_bounds__(aw_threads<QR>(), QR == 128 ? 1 : 2)
@@ -1791,7 +1845,9 @@ __global__ void __launch_bounds__(aw_threads<QR>(), QR == 128 ? 1 : 2)
                      const __grid_constant__ CUtensorMap map_vt, AttnParams p) {
     constexpr int RB = QR / 32;   // 32-row blocks (one per warp) per item
     constexpr int NW = NH * RB;   // consumer warps
-    constexpr bool kSumF32 = AM & 1, kOptimistic = AM & 2, kHoist = AM & 4;
+    constexpr bool kOptimistic = AM & 2;
+    constexpr int SB = (AM & 8) ? 2 : 1;   // 16-key steps per maxima check
+    constexpr bool kQReload = AM & 16;
     constexpr uint32_t QB = AwLayout<ST, QR>::QB;
     using LY = AwLayout<ST, QR>;
     extern __shared__ uint8_t smem_raw[];
@@ -1807,6 +1863,7 @@ __global__ void __launch_bounds__(aw_threads<QR>(), QR == 128 ? 1 : 2)
     uint64_t* never = kv_empty + ST;    // armed by nobody (debug stall)
     int4* info = (int4*)(never + 2);    // [2]
     int* abort_flag = (int*)(info + 2);
+    float* kn = (float*)(sm + LY::OFF_KN);   // per stage and head: largest K-row norm of the tile
     volatile int* ab = abort_flag;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
@@ -1863,9 +1920,12 @@ __global__ void __launch_bounds__(aw_threads<QR>(), QR == 128 ? 1 : 2)
                         ok = false;
                         break;
                     }
-                    mbar_arrive_expect_tx(&kv_full[s], AT_KB + AT_VB);
+                    // the tile's K and V^T and its per-head K-norm bounds (a 64-row block:
+                    // events start at 64-row boundaries, kb is a multiple of 128)
+                    mbar_arrive_expect_tx(&kv_full[s], AT_KB + AT_VB + 16);
                     tma_load_2d(sK + s * AT_KB, &map_k, 0, it.x + kb + 64 * j, &kv_full[s]);
                     tma_load_2d(sV + s * AT_VB, &map_vt, it.x + kb + 64 * j, 0, &kv_full[s]);
+                    bulk_load(kn + 4 * s, p.kmax + (size_t)(((it.x + kb) >> 6) + j) * 4, 16, &kv_full[s]);
                 }
                 ++q_it;
             }
@@ -1900,22 +1960,39 @@ __global__ void __launch_bounds__(aw_threads<QR>(), QR == 128 ? 1 : 2)
             int kb, ke;
             key_range(it.y, it.z, p.window, kb, ke);
             const int nk = (ke - kb + 63) >> 6;
-            // Q fragments of the two 16-row tiles (one K-step: the head's 16 channels)
+            // Q fragments of the two 16-row tiles (one K-step: the head's 16 channels);
+            // the second tile's rows are 16 further (same swizzle phase)
+            const uint32_t qfa = sQa + qb * QB + sw128_off(rb * 32 + (lane & 15), 2 * h + (lane >> 4));
             uint32_t qa[2][4];
+            auto load_q = [&]() {
 #pragma unroll
-            for (int mt = 0; mt < 2; ++mt) {
-                const int row = rb * 32 + mt * 16 + (lane & 15);
-                ldsm_x4(sQa + qb * QB + sw128_off(row, 2 * h + (lane >> 4)), qa[mt][0], qa[mt][1], qa[mt][2],
-                        qa[mt][3]);
+                for (int mt = 0; mt < 2; ++mt) ldsm_x4(qfa + 2048u * mt, qa[mt][0], qa[mt][1], qa[mt][2], qa[mt][3]);
+            };
+            // |q| of the fragment's rows (quad sums over the head's 16 channels), for
+            // the key tiles' score bounds |q| max |k|; 1 % for the FP32 sums
+            float qn[2][2];
+            load_q();
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                for (int hr = 0; hr < 2; ++hr) {
+                    float a0, a1, a2, a3;
+                    unpack2<F16>(qa[mt][hr], a0, a1);
+                    unpack2<F16>(qa[mt][2 + hr], a2, a3);
+                    float t = fmaf(a0, a0, fmaf(a1, a1, fmaf(a2, a2, a3 * a3)));
+                    t += __shfl_xor_sync(0xffffffffu, t, 1);
+                    t += __shfl_xor_sync(0xffffffffu, t, 2);
+                    qn[mt][hr] = sqrtf(t) * 1.01f;
+                }
+            if constexpr (!kQReload) {
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&q_empty[qb]);
             }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&q_empty[qb]);
-            // o: output accumulators; la: row sums in the accumulator fragment layout
-            // (kSumF32: this lane's partial sums over its key columns, reduced over the
-            // pair and the quad at the end; else the ones-MMA accumulator); nr: the negated exponent
-            // references of the fragment's rows as an accumulator input, so that the
-            // QK^T MMA (Q pre-scaled) yields the exponent S - ref itself.  The first
-            // 16-key step always sets the references.
+            // o: output accumulators; la: row sums (the ones-MMA accumulator, every
+            // column holds its row's sum); nr: the negated exponent references of the
+            // fragment's rows as an accumulator input, so that the QK^T MMA (Q
+            // pre-scaled) yields the exponent S - ref itself.  The first block of
+            // steps always sets the references.
             float o[2][2][4], la[2][4], nr[2][4];
 #pragma unroll
             for (int mt = 0; mt < 2; ++mt) {
@@ -1944,128 +2021,159 @@ __global__ void __launch_bounds__(aw_threads<QR>(), QR == 128 ? 1 : 2)
                         for (int nt = 0; nt < 2; ++nt)
                             mma16816_c<F16>(dst[mt][nt], qa[mt], kf[2 * nt], kf[2 * nt + 1], nr[mt]);
                 };
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    if (16 * q >= kvalid) break;   // warp-uniform
-                    float sc[2][2][4];
-                    uint32_t vf[4];
-                    if constexpr (kHoist)   // V fragments first: off the softmax's critical path
-                        ldsm_x4(vb + (uint32_t)voff[q], vf[0], vf[1], vf[2], vf[3]);
-                    qk(q, sc);
-                    if (16 * q + 16 > kvalid) {   // ragged end of the event
-#pragma unroll
-                        for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-                            for (int nt = 0; nt < 2; ++nt)
-#pragma unroll
-                                for (int e = 0; e < 4; ++e)
-                                    if (16 * q + 8 * nt + 2 * tq + (e & 1) >= kvalid) sc[mt][nt][e] = -INFINITY;
-                    }
-                    // P = 2^(S - ref) as the A fragments of PV (16 keys = one K-step).
-                    // kSumF32: row sums from the FP32 exponentials (else an MMA of P
-                    // against ones); kOptimistic: exponentials first, against the
-                    // current references, redone if a reference is raised (else the
-                    // maxima are checked first).
-                    uint32_t pa[2][4];
-                    float2 ls[2][2];
-                    auto exps = [&]() {
-#pragma unroll
-                        for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-                            for (int hr = 0; hr < 2; ++hr) {
-                                const float x0 = sc[mt][0][2 * hr], x1 = sc[mt][0][2 * hr + 1];
-                                const float x2 = sc[mt][1][2 * hr], x3 = sc[mt][1][2 * hr + 1];
-                                if constexpr (kSumF32) {
-                                    const float e0 = ex2_approx(x0), e1 = ex2_approx(x1);
-                                    const float e2 = ex2_approx(x2), e3 = ex2_approx(x3);
-                                    ls[mt][hr] = __fadd2_rn(make_float2(e0, e1), make_float2(e2, e3));
-                                    pa[mt][hr] = pack2<F16>(e0, e1);
-                                    pa[mt][2 + hr] = pack2<F16>(e2, e3);
-                                } else {
-                                    pa[mt][hr] = exp2_pair<F16>(x0, x1);
-                                    pa[mt][2 + hr] = exp2_pair<F16>(x2, x3);
-                                }
-                            }
-                    };
-                    const bool first = j == 0 && q == 0;
-                    float lm[2][2];
-                    bool raise = first;
-                    if constexpr (kOptimistic) {
-                        if (!first) exps();
-                    }
+                // Bound on the tile's scores, row by row: |q| max |k| <= ref + kLimit
+                // for every row of the warp means P <= 2^kLimit without looking at
+                // the maxima: the four 16-key steps then run without a vote or branch.
+                // The first tile (it sets the references) and a ragged last tile take
+                // the checked path.
+                bool fast = false;
+                if (j > 0 && kvalid >= 64) {
+                    const float km = kn[s * 4 + h];
+                    bool over = false;
 #pragma unroll
                     for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-                        for (int hr = 0; hr < 2; ++hr) {
-                            lm[mt][hr] = max3f(fmaxf(sc[mt][0][2 * hr], sc[mt][0][2 * hr + 1]), sc[mt][1][2 * hr],
-                                               sc[mt][1][2 * hr + 1]);
-                            raise |= lm[mt][hr] > kStaleMax;
+                        for (int hr = 0; hr < 2; ++hr) over |= fmaf(qn[mt][hr], km, nr[mt][2 * hr]) > kLimit;
+                    fast = !__any_sync(0xffffffffu, over);
+                }
+                if (fast) {
+                    if constexpr (kQReload) load_q();
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        float sc[2][2][4];
+                        uint32_t vf[4], pa[2][4];
+                        ldsm_x4(vb + (uint32_t)voff[q], vf[0], vf[1], vf[2], vf[3]);
+                        qk(q, sc);
+#pragma unroll
+                        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                            for (int hr = 0; hr < 2; ++hr) {
+                                pa[mt][hr] = exp2_pair<F16>(sc[mt][0][2 * hr], sc[mt][0][2 * hr + 1]);
+                                pa[mt][2 + hr] = exp2_pair<F16>(sc[mt][1][2 * hr], sc[mt][1][2 * hr + 1]);
+                            }
+#pragma unroll
+                        for (int mt = 0; mt < 2; ++mt) {
+                            mma16816<F16>(o[mt][0], pa[mt], vf[0], vf[1]);
+                            mma16816<F16>(o[mt][1], pa[mt], vf[2], vf[3]);
+                            mma16816<F16>(la[mt], pa[mt], ONE2, ONE2);   // row sums
                         }
-                    const bool raised = __any_sync(0xffffffffu, raise);
-                    if (raised) {
-                        // raise each row's reference by dr = (row max over the quad) - ref
-                        // (never lowered after the first step), rescale O and l by 2^-dr
-                        // and shift this step's exponents by -dr
-#pragma unroll
+                    }
+                } else {
+                    // SB 16-key steps per maxima check: S of all of them first, one vote,
+                    // then exponentials and PV (no branch between the steps of a block)
+    #pragma unroll
+                    for (int q0 = 0; q0 < 4; q0 += SB) {
+                        if (16 * q0 >= kvalid) break;   // warp-uniform
+                        float sc[SB][2][2][4];
+                        uint32_t vf[SB][4];
+                        if constexpr (kQReload) load_q();
+    #pragma unroll
+                        for (int b = 0; b < SB; ++b) {
+                            // V fragments (channels 0-7 / 8-15 of the head, keys 16q .. 16q+15)
+                            // first: off the softmax's critical path
+                            ldsm_x4(vb + (uint32_t)voff[q0 + b], vf[b][0], vf[b][1], vf[b][2], vf[b][3]);
+                            qk(q0 + b, sc[b]);
+                        }
+                        if (16 * (q0 + SB) > kvalid) {   // ragged end of the event
+    #pragma unroll
+                            for (int b = 0; b < SB; ++b)
+    #pragma unroll
+                                for (int mt = 0; mt < 2; ++mt)
+    #pragma unroll
+                                    for (int nt = 0; nt < 2; ++nt)
+    #pragma unroll
+                                        for (int e = 0; e < 4; ++e)
+                                            if (16 * (q0 + b) + 8 * nt + 2 * tq + (e & 1) >= kvalid)
+                                                sc[b][mt][nt][e] = -INFINITY;
+                        }
+                        // P = 2^(S - ref) as the A fragments of PV (16 keys = one K-step).
+                        // kOptimistic: exponentials first, against the current references,
+                        // redone if a reference is raised (else the maxima are checked first).
+                        uint32_t pa[SB][2][4];
+                        auto exps = [&]() {
+    #pragma unroll
+                            for (int b = 0; b < SB; ++b)
+    #pragma unroll
+                                for (int mt = 0; mt < 2; ++mt)
+    #pragma unroll
+                                    for (int hr = 0; hr < 2; ++hr) {
+                                        pa[b][mt][hr] = exp2_pair<F16>(sc[b][mt][0][2 * hr], sc[b][mt][0][2 * hr + 1]);
+                                        pa[b][mt][2 + hr] = exp2_pair<F16>(sc[b][mt][1][2 * hr], sc[b][mt][1][2 * hr + 1]);
+                                    }
+                        };
+                        const bool first = j == 0 && q0 == 0;
+                        float lm[2][2];
+                        bool raise = first;
+                        if constexpr (kOptimistic) {
+                            if (!first) exps();
+                        }
+    #pragma unroll
                         for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
+    #pragma unroll
                             for (int hr = 0; hr < 2; ++hr) {
-                                float mx = lm[mt][hr];
-                                mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
-                                mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
-                                const float dr = first ? mx : fmaxf(mx, 0.f);
-                                const float a = first ? 0.f : ex2_approx(-dr);
-                                nr[mt][2 * hr] -= dr;
-                                nr[mt][2 * hr + 1] -= dr;
-#pragma unroll
-                                for (int e = 0; e < 2; ++e) {
-                                    o[mt][0][2 * hr + e] *= a;
-                                    o[mt][1][2 * hr + e] *= a;
-                                    la[mt][2 * hr + e] *= a;
-                                    sc[mt][0][2 * hr + e] -= dr;
-                                    sc[mt][1][2 * hr + e] -= dr;
+                                float m = -INFINITY;
+    #pragma unroll
+                                for (int b = 0; b < SB; ++b)
+                                    m = fmaxf(m, max3f(fmaxf(sc[b][mt][0][2 * hr], sc[b][mt][0][2 * hr + 1]),
+                                                       sc[b][mt][1][2 * hr], sc[b][mt][1][2 * hr + 1]));
+                                lm[mt][hr] = m;
+                                raise |= m > kStaleMax;
+                            }
+                        const bool raised = __any_sync(0xffffffffu, raise);
+                        if (raised) {
+                            // raise each row's reference by dr = (row max over the quad) - ref
+                            // (never lowered after the first step), rescale O and l by 2^-dr
+                            // and shift this block's exponents by -dr
+    #pragma unroll
+                            for (int mt = 0; mt < 2; ++mt)
+    #pragma unroll
+                                for (int hr = 0; hr < 2; ++hr) {
+                                    float mx = lm[mt][hr];
+                                    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+                                    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+                                    const float dr = first ? mx : fmaxf(mx, 0.f);
+                                    const float a = first ? 0.f : ex2_approx(-dr);
+                                    nr[mt][2 * hr] -= dr;
+                                    nr[mt][2 * hr + 1] -= dr;
+    #pragma unroll
+                                    for (int e = 0; e < 2; ++e) {
+                                        o[mt][0][2 * hr + e] *= a;
+                                        o[mt][1][2 * hr + e] *= a;
+                                        la[mt][2 * hr + e] *= a;
+    #pragma unroll
+                                        for (int b = 0; b < SB; ++b) {
+                                            sc[b][mt][0][2 * hr + e] -= dr;
+                                            sc[b][mt][1][2 * hr + e] -= dr;
+                                        }
+                                    }
                                 }
+                        }
+                        if (!kOptimistic || raised) exps();
+    #pragma unroll
+                        for (int b = 0; b < SB; ++b)
+    #pragma unroll
+                            for (int mt = 0; mt < 2; ++mt) {
+                                mma16816<F16>(o[mt][0], pa[b][mt], vf[b][0], vf[b][1]);
+                                mma16816<F16>(o[mt][1], pa[b][mt], vf[b][2], vf[b][3]);
+                                mma16816<F16>(la[mt], pa[b][mt], ONE2, ONE2);   // row sums
                             }
-                    }
-                    if (!kOptimistic || raised) exps();
-                    if constexpr (kSumF32) {
-#pragma unroll
-                        for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-                            for (int hr = 0; hr < 2; ++hr) {
-                                const float2 t =
-                                    __fadd2_rn(make_float2(la[mt][2 * hr], la[mt][2 * hr + 1]), ls[mt][hr]);
-                                la[mt][2 * hr] = t.x;
-                                la[mt][2 * hr + 1] = t.y;
-                            }
-                    }
-                    // V fragments: channels 0-7 / 8-15 of the head, keys 16q .. 16q+15
-                    if constexpr (!kHoist) ldsm_x4(vb + sw128_off(v_row, 2 * q + v_sub), vf[0], vf[1], vf[2], vf[3]);
-#pragma unroll
-                    for (int mt = 0; mt < 2; ++mt) {
-                        mma16816<F16>(o[mt][0], pa[mt], vf[0], vf[1]);
-                        mma16816<F16>(o[mt][1], pa[mt], vf[2], vf[3]);
-                        if constexpr (!kSumF32) mma16816<F16>(la[mt], pa[mt], ONE2, ONE2);
                     }
                 }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&kv_empty[s]);
             }
             if (!ok) break;
+            if constexpr (kQReload) {   // the Q tile was read up to the last key tile
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&q_empty[qb]);
+            }
             const int qrow0 = it.x + it.y * ROWS + QR * it.w;   // it.w: half of the item (QR = 64)
             const int nrows = min(QR, it.z - it.y * ROWS - QR * it.w);
 #pragma unroll
             for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
                 for (int hr = 0; hr < 2; ++hr) {
-                    float l;
-                    if constexpr (kSumF32) {
-                        l = la[mt][2 * hr] + la[mt][2 * hr + 1];
-                        l += __shfl_xor_sync(0xffffffffu, l, 1);
-                        l += __shfl_xor_sync(0xffffffffu, l, 2);
-                    } else {
-                        l = la[mt][2 * hr];
-                    }
+                    const float l = la[mt][2 * hr];
                     const int r = rb * 32 + mt * 16 + gq + 8 * hr;
                     if (r < nrows) {
                         const float inv = 1.0f / l;
@@ -2412,7 +2520,7 @@ static int64_t run_tc(Model& m, const float* x, const int32_t* cu, int n_events,
     ++n;
     auto attention = [&](int layer) {
         AttnParams ap{w.items, w.counters, layer, (uint16_t*)w.to, m.status, (uint64_t)m.wait_limit_ns,
-                      m.debug_stall ? 1 : 0, m.attn_window};
+                      m.debug_stall ? 1 : 0, m.attn_window, w.kmax};
         prof_begin(m, st, "attention");
         constexpr bool AF = kOutF16<FMT>;
         const dim3 g(grid * m.attn_ctas_per_sm);
@@ -2452,6 +2560,7 @@ static int64_t run_tc(Model& m, const float* x, const int32_t* cu, int n_events,
         ep.q = (uint16_t*)w.tq;
         ep.k = (uint16_t*)w.tk;
         ep.vt = (uint16_t*)w.tvt;
+        ep.kmax = w.kmax;
         ep.ldvt = w.cap_tpad;
         ep.status = m.status;
         ep.wait_ns = (uint64_t)m.wait_limit_ns;
@@ -2543,6 +2652,7 @@ static int64_t run_tc(Model& m, const float* x, const int32_t* cu, int n_events,
         pp.k = (uint16_t*)w.tk;
         pp.vt = (uint16_t*)w.tvt;
         pp.hp = (uint16_t*)w.thp;
+        pp.kmax = w.kmax;
         pp.ldvt = w.cap_tpad;
         pp.logits = logits;
         pp.reg = reg;

@@ -30,7 +30,8 @@ constexpr size_t NA_OFF_TO = NA_OFF_TK + al(NA_TPAD * 64 * 2);
 constexpr size_t NA_OFF_TVT = NA_OFF_TO + al(NA_TPAD * 64 * 2);
 constexpr size_t NA_OFF_THP = NA_OFF_TVT + al(NA_TPAD * 64 * 2);
 constexpr size_t NA_OFF_BLK = NA_OFF_THP + al(NA_TPAD * 64 * 2);
-constexpr size_t NA_OFF_ITEMS = NA_OFF_BLK + al((NA_TPAD / 64) * sizeof(int4));
+constexpr size_t NA_OFF_KMAX = NA_OFF_BLK + al((NA_TPAD / 64) * sizeof(int4));
+constexpr size_t NA_OFF_ITEMS = NA_OFF_KMAX + al((NA_TPAD / 64) * 4 * sizeof(float));
 constexpr size_t NA_OFF_CNT = NA_OFF_ITEMS + al((NA_TPAD / 128 + NA_MAX_EVENTS + 1) * sizeof(int4));
 constexpr size_t NA_BYTES = NA_OFF_CNT + al(64 * sizeof(int));  // about 18.4 MB
 
@@ -66,6 +67,7 @@ Workspace na_workspace(unsigned char* b) {
     w.tvt = (__nv_bfloat16*)(b + NA_OFF_TVT);
     w.thp = (__nv_bfloat16*)(b + NA_OFF_THP);
     w.blk = (int4*)(b + NA_OFF_BLK);
+    w.kmax = (float*)(b + NA_OFF_KMAX);
     w.items = (int4*)(b + NA_OFF_ITEMS);
     w.counters = (int*)(b + NA_OFF_CNT);
     return w;
