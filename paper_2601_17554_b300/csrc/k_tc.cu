@@ -2061,13 +2061,13 @@ __global__ void __launch_bounds__(aw_threads<QR>(), QR == 128 ? 1 : 2)
                 } else {
                     // SB 16-key steps per maxima check: S of all of them first, one vote,
                     // then exponentials and PV (no branch between the steps of a block)
-    #pragma unroll
+#pragma unroll
                     for (int q0 = 0; q0 < 4; q0 += SB) {
                         if (16 * q0 >= kvalid) break;   // warp-uniform
                         float sc[SB][2][2][4];
                         uint32_t vf[SB][4];
                         if constexpr (kQReload) load_q();
-    #pragma unroll
+#pragma unroll
                         for (int b = 0; b < SB; ++b) {
                             // V fragments (channels 0-7 / 8-15 of the head, keys 16q .. 16q+15)
                             // first: off the softmax's critical path
@@ -2075,13 +2075,13 @@ __global__ void __launch_bounds__(aw_threads<QR>(), QR == 128 ? 1 : 2)
                             qk(q0 + b, sc[b]);
                         }
                         if (16 * (q0 + SB) > kvalid) {   // ragged end of the event
-    #pragma unroll
+#pragma unroll
                             for (int b = 0; b < SB; ++b)
-    #pragma unroll
+#pragma unroll
                                 for (int mt = 0; mt < 2; ++mt)
-    #pragma unroll
+#pragma unroll
                                     for (int nt = 0; nt < 2; ++nt)
-    #pragma unroll
+#pragma unroll
                                         for (int e = 0; e < 4; ++e)
                                             if (16 * (q0 + b) + 8 * nt + 2 * tq + (e & 1) >= kvalid)
                                                 sc[b][mt][nt][e] = -INFINITY;
@@ -2091,11 +2091,11 @@ __global__ void __launch_bounds__(aw_threads<QR>(), QR == 128 ? 1 : 2)
                         // redone if a reference is raised (else the maxima are checked first).
                         uint32_t pa[SB][2][4];
                         auto exps = [&]() {
-    #pragma unroll
+#pragma unroll
                             for (int b = 0; b < SB; ++b)
-    #pragma unroll
+#pragma unroll
                                 for (int mt = 0; mt < 2; ++mt)
-    #pragma unroll
+#pragma unroll
                                     for (int hr = 0; hr < 2; ++hr) {
                                         pa[b][mt][hr] = exp2_pair<F16>(sc[b][mt][0][2 * hr], sc[b][mt][0][2 * hr + 1]);
                                         pa[b][mt][2 + hr] = exp2_pair<F16>(sc[b][mt][1][2 * hr], sc[b][mt][1][2 * hr + 1]);
@@ -2107,12 +2107,12 @@ __global__ void __launch_bounds__(aw_threads<QR>(), QR == 128 ? 1 : 2)
                         if constexpr (kOptimistic) {
                             if (!first) exps();
                         }
-    #pragma unroll
+#pragma unroll
                         for (int mt = 0; mt < 2; ++mt)
-    #pragma unroll
+#pragma unroll
                             for (int hr = 0; hr < 2; ++hr) {
                                 float m = -INFINITY;
-    #pragma unroll
+#pragma unroll
                                 for (int b = 0; b < SB; ++b)
                                     m = fmaxf(m, max3f(fmaxf(sc[b][mt][0][2 * hr], sc[b][mt][0][2 * hr + 1]),
                                                        sc[b][mt][1][2 * hr], sc[b][mt][1][2 * hr + 1]));
@@ -2124,9 +2124,9 @@ __global__ void __launch_bounds__(aw_threads<QR>(), QR == 128 ? 1 : 2)
                             // raise each row's reference by dr = (row max over the quad) - ref
                             // (never lowered after the first step), rescale O and l by 2^-dr
                             // and shift this block's exponents by -dr
-    #pragma unroll
+#pragma unroll
                             for (int mt = 0; mt < 2; ++mt)
-    #pragma unroll
+#pragma unroll
                                 for (int hr = 0; hr < 2; ++hr) {
                                     float mx = lm[mt][hr];
                                     mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
@@ -2135,12 +2135,12 @@ __global__ void __launch_bounds__(aw_threads<QR>(), QR == 128 ? 1 : 2)
                                     const float a = first ? 0.f : ex2_approx(-dr);
                                     nr[mt][2 * hr] -= dr;
                                     nr[mt][2 * hr + 1] -= dr;
-    #pragma unroll
+#pragma unroll
                                     for (int e = 0; e < 2; ++e) {
                                         o[mt][0][2 * hr + e] *= a;
                                         o[mt][1][2 * hr + e] *= a;
                                         la[mt][2 * hr + e] *= a;
-    #pragma unroll
+#pragma unroll
                                         for (int b = 0; b < SB; ++b) {
                                             sc[b][mt][0][2 * hr + e] -= dr;
                                             sc[b][mt][1][2 * hr + e] -= dr;
@@ -2149,9 +2149,9 @@ __global__ void __launch_bounds__(aw_threads<QR>(), QR == 128 ? 1 : 2)
                                 }
                         }
                         if (!kOptimistic || raised) exps();
-    #pragma unroll
+#pragma unroll
                         for (int b = 0; b < SB; ++b)
-    #pragma unroll
+#pragma unroll
                             for (int mt = 0; mt < 2; ++mt) {
                                 mma16816<F16>(o[mt][0], pa[b][mt], vf[b][0], vf[b][1]);
                                 mma16816<F16>(o[mt][1], pa[b][mt], vf[b][2], vf[b][3]);
