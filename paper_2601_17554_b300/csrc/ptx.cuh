@@ -236,6 +236,17 @@ MLPF_DEV uint32_t pack2(float lo, float hi) {
         return pack_bf16x2(lo, hi);
 }
 
+// Packed 16-bit add of two pairs in the operand format (round to nearest).
+template <bool F16>
+MLPF_DEV uint32_t add2(uint32_t a, uint32_t b) {
+    uint32_t r;
+    if constexpr (F16)
+        asm("add.rn.f16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+    else
+        asm("add.rn.bf16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+    return r;
+}
+
 // Byte offset of 16-byte chunk `c` (0..7) of row `r` inside one 128-byte-swizzled
 // atom column (rows of 128 bytes; chunk index XORed with row mod 8).
 MLPF_DEV uint32_t sw128_off(int r, int c) {
