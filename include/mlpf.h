@@ -125,10 +125,14 @@ mlpf_status mlpf_forward(mlpf_model* m, int32_t precision,
 
 /*
  * Same as mlpf_forward with HOST buffers: copies x and cu_seqlens to the
- * device (through the model's pinned staging buffers), runs the forward and
- * copies the outputs back; returns when the host outputs are written.
- * x, cu_seqlens: host inputs; logits, reg: host outputs; cls, event_sums:
- * host outputs or NULL.  Errors as mlpf_forward plus those of mlpf_sync.
+ * device workspace, runs the forward and copies the outputs back; returns when
+ * the host outputs are written.  Large batches are processed in chunks of
+ * consecutive events (MLPF_OPT_HOST_CHUNKS) whose host-to-device copies,
+ * forwards and device-to-host copies are pipelined on the caller's stream and
+ * two copy streams of the model; the results are those of a single-chunk call
+ * (an event's outputs do not depend on the other events).  x, cu_seqlens: host inputs (pinned memory lets the copies run
+ * asynchronously); logits, reg: host outputs; cls, event_sums: host outputs or
+ * NULL.  Errors as mlpf_forward plus those of mlpf_sync.
  */
 mlpf_status mlpf_forward_host(mlpf_model* m, int32_t precision,
                               const float* x, const int32_t* cu_seqlens,
@@ -324,9 +328,15 @@ enum {
                                        tcgen05 variant falls back to 8).  Events of at
                                        most 16384 elements (else MLPF_E_UNSUPPORTED);
                                        not available in mlpf_forward_noalloc. */
-    MLPF_OPT_GATE_CONFIDENCE = 11   /* student models in mlpf_forward_gated: event
+    MLPF_OPT_GATE_CONFIDENCE = 11,  /* student models in mlpf_forward_gated: event
                                        confidence = mean (0, default) or minimum (1) over
                                        the event's elements of the max softmax */
+    MLPF_OPT_HOST_CHUNKS = 12       /* mlpf_forward_host: the batch is split into this many
+                                       chunks of consecutive events (about equal element
+                                       counts; 1..16, default 8); chunk c's input copy,
+                                       forward and output copy run on three streams, so
+                                       copies overlap the neighbouring chunks' compute.
+                                       Batches under 65536 elements run as one chunk. */
 };
 #define MLPF_ATTN_VARIANTS 10
 mlpf_status mlpf_set_option(mlpf_model* m, int32_t option, int64_t value);

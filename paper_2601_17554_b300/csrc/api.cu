@@ -255,7 +255,7 @@ static mlpf_status ensure_workspace(Model& m, int total, int n_events, bool tc) 
         o_items = take((tpad / 128 + cap_e + 1) * sizeof(int4));
     }
     const size_t o_cnt = take(64 * sizeof(int));
-    const size_t o_hx = take(cap_t * 42 * 4), o_hcu = take((cap_e + 1) * 4),
+    const size_t o_hx = take(cap_t * 42 * 4), o_hcu = take((cap_e + 1) * 4), o_hcc = take((cap_e + 17) * 4),
                  o_hlo = take(cap_t * 6 * 4), o_hrg = take(cap_t * 5 * 4), o_hcl = take(cap_t * 4),
                  o_hsu = take(cap_e * 3 * 8);
     const size_t o_perm = take(cap_t * 4), o_xs = take(cap_t * 42 * 4), o_los = take(cap_t * 6 * 4),
@@ -273,6 +273,7 @@ static mlpf_status ensure_workspace(Model& m, int total, int n_events, bool tc) 
     w.hreg = (float*)(b + o_hr); w.raw = (float*)(b + o_raw);
     w.counters = (int*)(b + o_cnt);
     w.hx = (float*)(b + o_hx); w.hcu = (int32_t*)(b + o_hcu); w.hlogits = (float*)(b + o_hlo);
+    w.hcu_chunks = (int32_t*)(b + o_hcc);
     w.hreg_out = (float*)(b + o_hrg); w.hcls = (int32_t*)(b + o_hcl); w.hsums = (double*)(b + o_hsu);
     w.perm = (int32_t*)(b + o_perm); w.xs = (float*)(b + o_xs); w.los = (float*)(b + o_los);
     w.rgs = (float*)(b + o_rgs);
@@ -442,7 +443,7 @@ mlpf_status mlpf_eval_activation(int32_t impl, int32_t act, const float* x, floa
     return MLPF_OK;
 }
 
-int32_t mlpf_abi_version(void) { return 102; }
+int32_t mlpf_abi_version(void) { return 103; }
 
 const char* mlpf_last_error(void) { return g_last_error.c_str(); }
 
@@ -501,6 +502,10 @@ void mlpf_free(mlpf_model* mm) {
     for (auto& g : m.graphs) { cudaGraphExecDestroy(g.second.exec); prof_destroy(g.second.prof); }
     prof_destroy(m.direct_prof);
     if (m.cap_stream) cudaStreamDestroy(m.cap_stream);
+    if (m.copy_in) cudaStreamDestroy(m.copy_in);
+    if (m.copy_out) cudaStreamDestroy(m.copy_out);
+    for (cudaEvent_t e : m.chunk_ev) cudaEventDestroy(e);
+    if (m.cu_pinned) cudaFreeHost(m.cu_pinned);
     if (m.ws.base) cudaFree(m.ws.base);
     if (m.w.f32_base) cudaFree(m.w.f32_base);
     if (m.w.img_base) cudaFree(m.w.img_base);
@@ -559,18 +564,88 @@ mlpf_status mlpf_forward_host(mlpf_model* mm, int32_t precision, const float* x,
     if (s != MLPF_OK) return s;
     Workspace& w = m.ws;
     cudaStream_t st = (cudaStream_t)stream;
-    if (total > 0) CK(cudaMemcpyAsync(w.hx, x, (size_t)total * 42 * 4, cudaMemcpyHostToDevice, st));
-    if (n_events > 0) CK(cudaMemcpyAsync(w.hcu, cu_seqlens, (size_t)(n_events + 1) * 4, cudaMemcpyHostToDevice, st));
-    s = forward_impl(m, precision, w.hx, w.hcu, n_events, total, max_n, w.hlogits, w.hreg_out,
-                     cls ? w.hcls : nullptr, event_sums ? w.hsums : nullptr, st);
-    if (s != MLPF_OK) return s;
-    if (total > 0) {
-        CK(cudaMemcpyAsync(logits, w.hlogits, (size_t)total * 6 * 4, cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(reg, w.hreg_out, (size_t)total * 5 * 4, cudaMemcpyDeviceToHost, st));
-        if (cls) CK(cudaMemcpyAsync(cls, w.hcls, (size_t)total * 4, cudaMemcpyDeviceToHost, st));
+    const int K = (total >= 65536 && n_events >= 2) ? std::min(m.host_chunks, (int)n_events) : 1;
+    if (K == 1) {
+        if (total > 0) CK(cudaMemcpyAsync(w.hx, x, (size_t)total * 42 * 4, cudaMemcpyHostToDevice, st));
+        if (n_events > 0)
+            CK(cudaMemcpyAsync(w.hcu, cu_seqlens, (size_t)(n_events + 1) * 4, cudaMemcpyHostToDevice, st));
+        s = forward_impl(m, precision, w.hx, w.hcu, n_events, total, max_n, w.hlogits, w.hreg_out,
+                         cls ? w.hcls : nullptr, event_sums ? w.hsums : nullptr, st);
+        if (s != MLPF_OK) return s;
+        if (total > 0) {
+            CK(cudaMemcpyAsync(logits, w.hlogits, (size_t)total * 6 * 4, cudaMemcpyDeviceToHost, st));
+            CK(cudaMemcpyAsync(reg, w.hreg_out, (size_t)total * 5 * 4, cudaMemcpyDeviceToHost, st));
+            if (cls) CK(cudaMemcpyAsync(cls, w.hcls, (size_t)total * 4, cudaMemcpyDeviceToHost, st));
+        }
+        if (event_sums && n_events > 0)
+            CK(cudaMemcpyAsync(event_sums, w.hsums, (size_t)n_events * 3 * 8, cudaMemcpyDeviceToHost, st));
+        return mlpf_sync(mm, stream);
     }
-    if (event_sums && n_events > 0)
-        CK(cudaMemcpyAsync(event_sums, w.hsums, (size_t)n_events * 3 * 8, cudaMemcpyDeviceToHost, st));
+    // chunks of consecutive events with about total / K elements each (at least one event)
+    std::vector<int> e0(K + 1);
+    e0[0] = 0;
+    e0[K] = n_events;
+    for (int c = 1; c < K; ++c) {
+        const int64_t target = (int64_t)total * c / K;
+        int e = e0[c - 1] + 1;
+        while (e < n_events - (K - c) && cu_seqlens[e] < target) ++e;
+        e0[c] = e;
+    }
+    // per-chunk cu_seqlens rebased to 0, chunk c at offset e0[c] + c, through pinned staging
+    const size_t ncu = (size_t)n_events + K;
+    if (m.cu_pinned_cap < ncu) {
+        if (m.cu_pinned) cudaFreeHost(m.cu_pinned);
+        m.cu_pinned = nullptr;
+        m.cu_pinned_cap = 0;
+        CK(cudaMallocHost(&m.cu_pinned, ncu * 4));
+        m.cu_pinned_cap = ncu;
+    }
+    for (int c = 0; c < K; ++c)
+        for (int i = 0; i <= e0[c + 1] - e0[c]; ++i)
+            m.cu_pinned[e0[c] + c + i] = cu_seqlens[e0[c] + i] - cu_seqlens[e0[c]];
+    if (!m.copy_in) CK(cudaStreamCreateWithFlags(&m.copy_in, cudaStreamNonBlocking));
+    if (!m.copy_out) CK(cudaStreamCreateWithFlags(&m.copy_out, cudaStreamNonBlocking));
+    while ((int)m.chunk_ev.size() < 2 + 2 * K) {
+        cudaEvent_t e;
+        CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        m.chunk_ev.push_back(e);
+    }
+    cudaEvent_t ev_start = m.chunk_ev[0], ev_out = m.chunk_ev[1];
+    // the copy streams start after the caller's earlier work on st
+    CK(cudaEventRecord(ev_start, st));
+    CK(cudaStreamWaitEvent(m.copy_in, ev_start, 0));
+    CK(cudaStreamWaitEvent(m.copy_out, ev_start, 0));
+    CK(cudaMemcpyAsync(w.hcu_chunks, m.cu_pinned, ncu * 4, cudaMemcpyHostToDevice, st));
+    for (int c = 0; c < K; ++c) {
+        const size_t r0 = (size_t)cu_seqlens[e0[c]], rows = (size_t)cu_seqlens[e0[c + 1]] - r0;
+        if (rows > 0)
+            CK(cudaMemcpyAsync(w.hx + r0 * 42, x + r0 * 42, rows * 42 * 4, cudaMemcpyHostToDevice, m.copy_in));
+        CK(cudaEventRecord(m.chunk_ev[2 + 2 * c], m.copy_in));
+    }
+    int64_t launches = 0;
+    for (int c = 0; c < K; ++c) {
+        const size_t r0 = (size_t)cu_seqlens[e0[c]], rows = (size_t)cu_seqlens[e0[c + 1]] - r0;
+        const int ne = e0[c + 1] - e0[c];
+        CK(cudaStreamWaitEvent(st, m.chunk_ev[2 + 2 * c], 0));
+        s = forward_impl(m, precision, w.hx + r0 * 42, w.hcu_chunks + e0[c] + c, ne, (int32_t)rows, max_n,
+                         w.hlogits + r0 * 6, w.hreg_out + r0 * 5, cls ? w.hcls + r0 : nullptr,
+                         event_sums ? w.hsums + (size_t)e0[c] * 3 : nullptr, st);
+        if (s != MLPF_OK) return s;
+        launches += m.last_launches;
+        CK(cudaEventRecord(m.chunk_ev[3 + 2 * c], st));
+        CK(cudaStreamWaitEvent(m.copy_out, m.chunk_ev[3 + 2 * c], 0));
+        if (rows > 0) {
+            CK(cudaMemcpyAsync(logits + r0 * 6, w.hlogits + r0 * 6, rows * 6 * 4, cudaMemcpyDeviceToHost, m.copy_out));
+            CK(cudaMemcpyAsync(reg + r0 * 5, w.hreg_out + r0 * 5, rows * 5 * 4, cudaMemcpyDeviceToHost, m.copy_out));
+            if (cls) CK(cudaMemcpyAsync(cls + r0, w.hcls + r0, rows * 4, cudaMemcpyDeviceToHost, m.copy_out));
+        }
+        if (event_sums && ne > 0)
+            CK(cudaMemcpyAsync(event_sums + (size_t)e0[c] * 3, w.hsums + (size_t)e0[c] * 3, (size_t)ne * 3 * 8,
+                               cudaMemcpyDeviceToHost, m.copy_out));
+    }
+    m.last_launches = launches;
+    CK(cudaEventRecord(ev_out, m.copy_out));
+    CK(cudaStreamWaitEvent(st, ev_out, 0));
     return mlpf_sync(mm, stream);
 }
 
@@ -737,6 +812,10 @@ mlpf_status mlpf_set_option(mlpf_model* mm, int32_t option, int64_t value) {
             if (value < 0 || value > 1) { set_error("gate confidence mode must be 0 or 1"); return MLPF_E_INVALID; }
             m.gate_confidence = (int)value;
             return MLPF_OK;   // host-side choice: no captured graph depends on it
+        case MLPF_OPT_HOST_CHUNKS:
+            if (value < 1 || value > 16) { set_error("host chunks must be 1..16"); return MLPF_E_INVALID; }
+            m.host_chunks = (int)value;
+            return MLPF_OK;   // host-side choice
         case MLPF_OPT_ATTN_VARIANT_BF16:
         case MLPF_OPT_ATTN_VARIANT_FP16:
         case MLPF_OPT_ATTN_VARIANT_FP8:
@@ -779,6 +858,7 @@ mlpf_status mlpf_get_option(const mlpf_model* mm, int32_t option, int64_t* value
         case MLPF_OPT_ATTN_VARIANT_FP8: *value = m.attn_variant[option - MLPF_OPT_ATTN_VARIANT_BF16]; return MLPF_OK;
         case MLPF_OPT_ATTN_WINDOW: *value = m.attn_window; return MLPF_OK;
         case MLPF_OPT_GATE_CONFIDENCE: *value = m.gate_confidence; return MLPF_OK;
+        case MLPF_OPT_HOST_CHUNKS: *value = m.host_chunks; return MLPF_OK;
         default: set_error("unknown option " + std::to_string(option)); return MLPF_E_INVALID;
     }
 }

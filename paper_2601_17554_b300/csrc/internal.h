@@ -73,6 +73,7 @@ struct Workspace {
     float *hx = nullptr, *hlogits = nullptr, *hreg_out = nullptr;
     int32_t *hcu = nullptr, *hcls = nullptr;
     double* hsums = nullptr;
+    int32_t* hcu_chunks = nullptr;       // per-chunk cu_seqlens (each rebased to 0), back to back
 };
 
 struct GraphKey {
@@ -113,6 +114,12 @@ struct Model {
     // gated inference (student models): event confidence = mean (0) or minimum (1)
     // of the per-element max softmax
     int gate_confidence = 0;
+    // host-buffer forward: event chunks pipelined over copy-in, compute and copy-out
+    int host_chunks = 8;
+    cudaStream_t copy_in = nullptr, copy_out = nullptr;
+    std::vector<cudaEvent_t> chunk_ev;   // [0] start, [1] copies out done, then 2 per chunk
+    int32_t* cu_pinned = nullptr;        // pinned host staging of the per-chunk cu_seqlens
+    size_t cu_pinned_cap = 0;
     // FP8: activation slots (one per GEMM input) and their static scales s_a = amax / 448
     std::map<std::string, int> act_slot;
     std::vector<float> act_scale;

@@ -181,6 +181,38 @@ def test_host_buffer_entry_point_matches_device(small_perturbed):
     np.testing.assert_array_equal(su.numpy(), dev[3])
 
 
+@pytest.mark.parametrize("chunks", [1, 3, 4, 16])
+def test_host_chunked_pipeline_matches_device(small_perturbed, chunks):
+    """mlpf_forward_host on a batch above the chunking threshold: chunks of
+    consecutive events with their copies overlapped by the neighbours' compute give
+    the device-buffer results bitwise (an event's outputs do not depend on the
+    other events)."""
+    import torch
+    from paper_2601_17554_b300._lib import OPT_HOST_CHUNKS
+    model, w = small_perturbed
+    sizes = synth.sizes_lognormal(31, 40)
+    x, cu = synth.gen_events(31, sizes)
+    assert len(x) >= 65536
+    T, E = len(x), len(sizes)
+    model.set_option(OPT_HOST_CHUNKS, chunks)
+    try:
+        for prec in ("bf16", "fp16"):
+            dev = run_gpu(model, x, cu, prec)
+            xh, cuh = torch.from_numpy(x).pin_memory(), torch.from_numpy(cu).pin_memory()
+            lo = torch.full((T, 6), float("nan")).pin_memory()
+            rg = torch.full((T, 5), float("nan")).pin_memory()
+            cl = torch.full((T,), -1, dtype=torch.int32).pin_memory()
+            su = torch.full((E, 3), float("nan"), dtype=torch.float64).pin_memory()
+            model.forward_host(xh, cuh, int(sizes.max()), precision=prec, logits=lo, reg=rg, cls=cl,
+                               event_sums=su)
+            np.testing.assert_array_equal(lo.numpy(), dev[0])
+            np.testing.assert_array_equal(rg.numpy(), dev[1])
+            np.testing.assert_array_equal(cl.numpy(), dev[2])
+            np.testing.assert_array_equal(su.numpy(), dev[3])
+    finally:
+        model.set_option(OPT_HOST_CHUNKS, 8)
+
+
 def calibrate(model, n=32, seed=999):
     import torch
     sizes = synth.sizes_lognormal(seed, n)
