@@ -5,6 +5,7 @@ import numpy as np
 
 import bench
 import oracle
+import synth
 
 
 def test_attention_pairs_full():
@@ -19,3 +20,16 @@ def test_attention_pairs_windowed_match_mask():
         assert bench.attention_pairs(sizes, w) == expect
     # a window reaching every block is full attention
     assert bench.attention_pairs(np.array([700]), 6) == 700 ** 2
+
+
+def test_gemm_flops_per_element_matches_the_survey_estimate():
+    """About 2.7e5 GEMM flops per element for the d=64, FFN 256, 1 + 1 model (the
+    scope table's estimate from the layer sizes); the full-size model scales with
+    d^2 and the layer count."""
+    import bench
+    f = bench.gemm_flops_per_element(synth.SMALL)
+    assert abs(f - 2.7e5) / 2.7e5 < 0.03, f
+    # one more encoder block adds 2 (3 d^2 + d^2 + 2 d F) flops
+    import dataclasses
+    deeper = dataclasses.replace(synth.SMALL, l_pid=2)
+    assert bench.gemm_flops_per_element(deeper) - f == 2 * (4 * 64 * 64 + 2 * 64 * 256)
