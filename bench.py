@@ -51,6 +51,9 @@ def parse():
                     help="skip the FP32-plain, per-event-latency and CPU-oracle legs")
     ap.add_argument("--events", type=int, default=512,
                     help="use only the first N events of the batch (small profiling captures)")
+    ap.add_argument("--jets", type=float, default=0.0,
+                    help="also time anti-kt jet clustering (distance parameter R, e.g. 0.4) of "
+                         "the batch's reconstructed particles after the forward")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="approximate CPU time budget of the oracle sample")
     return ap.parse_args()
@@ -443,6 +446,21 @@ def run_ours(args):
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                     "ms_per_step": e2e_ms},
             "clocks": clk}
+    if args.jets > 0:
+        # anti-kt jets of the forward's outputs (outside the timed forward steps)
+        model.cluster_jets(rg, cl, cud, args.jets)
+        torch.cuda.synchronize(dev)
+        j_s, j_e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        j_s.record(stream)
+        for _ in range(3):
+            jets, nj, _ = model.cluster_jets(rg, cl, cud, args.jets)
+        j_e.record(stream)
+        torch.cuda.synchronize(dev)
+        line["jets"] = {"R": args.jets, "ms_per_batch": j_s.elapsed_time(j_e) / 3,
+                        "jets_per_batch": int(nj.sum()),
+                        "particles_per_batch": int((cl != 0).sum()),
+                        "note": "anti-kt, E scheme, one CTA per event, O(N^2) per event with "
+                                "nearest-neighbour bookkeeping; latency-bound (one merge per step)"}
     if args.attn_window > 0:
         # agreement with full attention on the same batch, and the full-attention time
         lw, rw, cw = lo.clone(), rg.clone(), cl.clone()

@@ -193,6 +193,32 @@ mlpf_status mlpf_autotune(mlpf_model* m, int32_t precision, const float* x, cons
                           void* stream);
 
 /*
+ * Anti-kt jets of every event's reconstructed particles (Sec. 3.3 and Sec. 6.2: jets
+ * are clustered from the (ML)PF candidates with the anti-kt algorithm, R = 0.4 or
+ * 0.8; no pileup weights).  Particles: the elements with cls != 0, pT > 0 and
+ * (sin phi, cos phi) != 0, massless (px = pT c / r, py = pT s / r with r = |(s, c)|,
+ * pz = pT sinh(eta), E = pT cosh(eta); the regressed E is not used).  Distances
+ * d_ij = min(pT_i^-2, pT_j^-2) dR_ij^2 / R^2 (rapidity and azimuth) and d_iB =
+ * pT_i^-2; E-scheme recombination (Cacciari, Salam, Soyez, JHEP 04 (2008) 063).
+ * FP32 on the GPU, one CTA per event, O(N^2) per event.
+ * reg        device, [total, 5] decoded outputs of mlpf_forward (pT, eta, sin phi,
+ *            cos phi, E); cls: device, [total] int32 classes; cu_seqlens: device,
+ *            [n_events + 1] (as mlpf_forward).
+ * R          distance parameter, 0 < R <= 2.
+ * jets       device out, [total, 4] float32: event e's jets (px, py, pz, E) in rows
+ *            cu[e] .. cu[e] + n_jets[e] - 1, in the order they leave the list.
+ * n_jets     device out, [n_events] int32.
+ * jet_of     device out or NULL, [total] int32: the element's jet index within its
+ *            event, -1 for elements that are not particles.
+ * Uses a scratch of 53 bytes per element owned by the model (grown on demand, not
+ * during graph capture).  Asynchronous on `stream`.  Errors: MLPF_E_INVALID (NULL
+ * pointers, negative sizes, R out of range), MLPF_E_OOM, MLPF_E_CUDA.
+ */
+mlpf_status mlpf_cluster_jets(mlpf_model* m, const float* reg, const int32_t* cls,
+                              const int32_t* cu_seqlens, int32_t n_events, int32_t total, float R,
+                              float* jets, int32_t* n_jets, int32_t* jet_of, void* stream);
+
+/*
  * Measured unit rates of `device` (no counterpart in the paper; the roofline
  * denominators of the attention kernel): results per second of the MUFU base-2
  * exponential (ex2.approx.f32) and of FP32 FMA, each from a kernel of independent

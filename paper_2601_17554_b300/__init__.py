@@ -114,6 +114,23 @@ class Model:
                                        _ptr(event_sums), s))
         return logits, reg, cls, event_sums
 
+    def cluster_jets(self, reg, cls, cu_seqlens, R: float = 0.4, jet_of: bool = True, stream=None):
+        """Anti-kt jets of every event's reconstructed particles from the decoded
+        outputs (device tensors): returns (jets [total, 4] (px, py, pz, E), event e's
+        jets in rows cu[e] .. cu[e] + n_jets[e] - 1; n_jets [n_events] int32; jet_of
+        [total] int32 or None).  Asynchronous on the stream."""
+        import torch
+        total = reg.shape[0]
+        n_events = cu_seqlens.shape[0] - 1
+        dev = reg.device
+        jets = torch.empty((total, 4), dtype=torch.float32, device=dev)
+        n_jets = torch.empty((n_events,), dtype=torch.int32, device=dev)
+        jof = torch.empty((total,), dtype=torch.int32, device=dev) if jet_of else None
+        s = stream if stream is not None else torch.cuda.current_stream(self.device).cuda_stream
+        check(self.L.mlpf_cluster_jets(self.h, _ptr(reg), _ptr(cls), _ptr(cu_seqlens), n_events, total,
+                                       float(R), _ptr(jets), _ptr(n_jets), _ptr(jof), ctypes.c_void_p(s)))
+        return jets, n_jets, jof
+
     def autotune(self, x, cu_seqlens, max_n: int, precision="bf16", cache_path=None, stream=None):
         """Keep the fastest attention variant of `precision` on this batch (device
         tensors); returns the chosen variant index (None for fp32)."""

@@ -506,6 +506,7 @@ void mlpf_free(mlpf_model* mm) {
     if (m.copy_out) cudaStreamDestroy(m.copy_out);
     for (cudaEvent_t e : m.chunk_ev) cudaEventDestroy(e);
     if (m.cu_pinned) cudaFreeHost(m.cu_pinned);
+    if (m.jet_base) cudaFree(m.jet_base);
     if (m.ws.base) cudaFree(m.ws.base);
     if (m.w.f32_base) cudaFree(m.w.f32_base);
     if (m.w.img_base) cudaFree(m.w.img_base);

@@ -120,6 +120,9 @@ struct Model {
     std::vector<cudaEvent_t> chunk_ev;   // [0] start, [1] copies out done, then 2 per chunk
     int32_t* cu_pinned = nullptr;        // pinned host staging of the per-chunk cu_seqlens
     size_t cu_pinned_cap = 0;
+    // anti-kt jet clustering scratch (mlpf_cluster_jets)
+    void* jet_base = nullptr;
+    size_t jet_bytes = 0;
     // FP8: activation slots (one per GEMM input) and their static scales s_a = amax / 448
     std::map<std::string, int> act_slot;
     std::vector<float> act_scale;

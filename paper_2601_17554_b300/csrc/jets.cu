@@ -1,0 +1,350 @@
+// Anti-kt jets of every event's reconstructed particles (the event-level step
+// after the reconstruction: the paper clusters jets from the (ML)PF candidates
+// with the anti-kt algorithm, R = 0.4 or 0.8, Sec. 3.3 and Sec. 6.2; no PUPPI
+// weights, which need vertex information).
+//
+// Definitions (Cacciari, Salam, Soyez, JHEP 04 (2008) 063): particles are the
+// elements with class != 0, pT > 0 and (sin phi, cos phi) != 0, massless;
+// d_ij = min(pT_i^-2, pT_j^-2) dR_ij^2 / R^2, d_iB = pT_i^-2, dR^2 = dy^2 + dphi^2;
+// the smallest distance either merges i and j (4-vector sum) or makes i a jet.
+//
+// One CTA per event.  Nearest-neighbour bookkeeping (Cacciari and Salam, "Dispelling
+// the N^3 myth for the kt jet-finder", Phys. Lett. B 641 (2006) 57): if (a, b) is the
+// pair of smallest d_ij with pT_a^-2 <= pT_b^-2, b is a's geometric nearest
+// neighbour, so the smallest of all distances is min_i min(pT_i^-2 dR^2(i, NN_i) /
+// R^2, pT_i^-2).  Each entry keeps its nearest neighbour; a step takes the block-wide
+// minimum, merges or emits, and recomputes the neighbours of the entries whose
+// neighbour left or moved.  Only neighbours within R count: for a pair at dR >= R,
+// d_ij >= min(pT_i^-2, pT_j^-2), the softer entry's beam distance, which wins
+// (ties go to the beam), so an entry without a neighbour within R takes d_iB.  The rapidity is taken from the running
+// sums of E + pz = pT e^eta and E - pz = pT e^-eta (positive terms, no cancellation).
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <string>
+
+#include "internal.h"
+
+namespace mlpf {
+namespace {
+
+constexpr int JT = 256;         // threads per event
+constexpr int JW = JT / 32;
+constexpr int JLIST = 512;      // entries whose neighbour is recomputed in one step
+constexpr float kPiF = 3.14159265358979323846f;
+
+struct JetScratch {
+    float *y, *phi, *pinv, *px, *py, *ep, *em, *d2, *dd;   // per particle (local index in the event's rows)
+    int *nn, *parent, *jid, *idx;
+    unsigned char* act;
+};
+
+__device__ __forceinline__ float dr2(float ya, float pa, float yb, float pb) {
+    const float dy = ya - yb;
+    float dp = fabsf(pa - pb);
+    if (dp > kPiF) dp = 2.f * kPiF - dp;
+    return dy * dy + dp * dp;
+}
+
+// min(pT^-2 dR^2 / R^2, pT^-2): the entry's smallest distance (pair or beam)
+__device__ __forceinline__ float entry_dist(float pinv, float d2, int nn, float inv_r2) {
+    if (nn < 0) return pinv;
+    const float pd = pinv * d2 * inv_r2;
+    return pd < pinv ? pd : pinv;
+}
+
+__device__ __forceinline__ void argmin_pair(float& v, int& i, float ov, int oi) {
+    if (ov < v || (ov == v && oi < i)) {
+        v = ov;
+        i = oi;
+    }
+}
+
+__device__ __forceinline__ void warp_argmin(float& v, int& i) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const float ov = __shfl_xor_sync(0xffffffffu, v, off);
+        const int oi = __shfl_xor_sync(0xffffffffu, i, off);
+        argmin_pair(v, i, ov, oi);
+    }
+}
+
+// the entry of smallest (value, index) over the block; every thread gets it
+__device__ void block_argmin(float& v, int& i, float* sv, int* si) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    warp_argmin(v, i);
+    if (lane == 0) {
+        sv[warp] = v;
+        si[warp] = i;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        v = lane < JW ? sv[lane] : INFINITY;
+        i = lane < JW ? si[lane] : INT_MAX;
+        warp_argmin(v, i);
+        if (lane == 0) {
+            sv[0] = v;
+            si[0] = i;
+        }
+    }
+    __syncthreads();
+    v = sv[0];
+    i = si[0];
+    __syncthreads();
+}
+
+// nearest active neighbour within R of entry a over the entries m = m0, m0 + dm, ...
+__device__ __forceinline__ void scan_neighbour(int a, int n, int m0, int dm, const JetScratch& S, int base,
+                                               float r2, float& best, int& bj) {
+    const float ya = S.y[base + a], pa = S.phi[base + a];
+    best = INFINITY;
+    bj = INT_MAX;
+    for (int m = m0; m < n; m += dm) {
+        if (m == a || !S.act[base + m]) continue;
+        const float d = dr2(ya, pa, S.y[base + m], S.phi[base + m]);
+        if (d < r2) argmin_pair(best, bj, d, m);
+    }
+}
+__device__ __forceinline__ void set_neighbour(int a, float best, int bj, const JetScratch& S, int base,
+                                              float inv_r2) {
+    const int nn = bj == INT_MAX ? -1 : bj;
+    S.nn[base + a] = nn;
+    S.d2[base + a] = nn < 0 ? INFINITY : best;
+    S.dd[base + a] = entry_dist(S.pinv[base + a], best, nn, inv_r2);
+}
+// one warp per entry
+__device__ void warp_neighbour(int a, int n, const JetScratch& S, int base, float r2, float inv_r2) {
+    float best;
+    int bj;
+    scan_neighbour(a, n, threadIdx.x & 31, 32, S, base, r2, best, bj);
+    warp_argmin(best, bj);
+    if ((threadIdx.x & 31) == 0) set_neighbour(a, best, bj, S, base, inv_r2);
+}
+
+__global__ void __launch_bounds__(JT) k_antikt(const float* __restrict__ reg, const int32_t* __restrict__ cls,
+                                              const int32_t* __restrict__ cu, float r2, JetScratch S,
+                                              float* __restrict__ jets, int32_t* __restrict__ n_jets,
+                                              int32_t* __restrict__ jet_of) {
+    __shared__ float sv[JW];
+    __shared__ int si[JW];
+    __shared__ int s_n, s_jets, s_cnt, s_over, s_j, s_beam;
+    __shared__ int s_list[JLIST];
+    const int ev = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int r0 = cu[ev], N = cu[ev + 1] - r0;
+    const float inv_r2 = 1.f / r2;
+    auto is_particle = [&](int row, float& pt, float& eta, float& s, float& c) {
+        pt = reg[(size_t)row * 5];
+        eta = reg[(size_t)row * 5 + 1];
+        s = reg[(size_t)row * 5 + 2];
+        c = reg[(size_t)row * 5 + 3];
+        return cls[row] != 0 && pt > 0.f && (s * s + c * c) > 0.f;
+    };
+    // this event's rows of the scratch arrays (the per-step scans read them through
+    // L1: keeping them in shared memory instead cost the L1 capacity and was slower)
+    JetScratch L;
+    L.y = S.y + r0; L.phi = S.phi + r0; L.pinv = S.pinv + r0; L.px = S.px + r0; L.py = S.py + r0;
+    L.ep = S.ep + r0; L.em = S.em + r0; L.d2 = S.d2 + r0; L.dd = S.dd + r0; L.nn = S.nn + r0;
+    L.parent = S.parent + r0; L.jid = S.jid + r0; L.idx = S.idx + r0; L.act = S.act + r0;
+    if (tid == 0) {
+        s_n = 0;
+        s_jets = 0;
+    }
+    __syncthreads();
+    // particles of the event, in input order (block-wide compaction by chunks)
+    for (int c0 = 0; c0 < N; c0 += JT) {
+        const int row = r0 + c0 + tid;
+        bool f = false;
+        float pt = 0.f, eta = 0.f, s = 0.f, c = 0.f;
+        if (c0 + tid < N) {
+            f = is_particle(row, pt, eta, s, c);
+            if (jet_of) jet_of[row] = -1;
+        }
+        const unsigned b = __ballot_sync(0xffffffffu, f);
+        if (lane == 0) si[warp] = __popc(b);
+        __syncthreads();
+        int off = 0, tot = 0;
+#pragma unroll
+        for (int w = 0; w < JW; ++w) {
+            off += w < warp ? si[w] : 0;
+            tot += si[w];
+        }
+        if (f) {
+            const int k = s_n + off + __popc(b & ((1u << lane) - 1u));
+            const float r = sqrtf(s * s + c * c);
+            const float px = pt * (c / r), py = pt * (s / r);
+            L.idx[k] = row;
+            L.px[k] = px;
+            L.py[k] = py;
+            L.ep[k] = pt * expf(eta);    // E + pz
+            L.em[k] = pt * expf(-eta);   // E - pz
+            L.y[k] = eta;                // massless: rapidity = pseudorapidity
+            L.phi[k] = atan2f(s, c);
+            L.pinv[k] = 1.f / (px * px + py * py);
+            L.parent[k] = -1;
+            L.act[k] = 1;
+        }
+        __syncthreads();
+        if (tid == 0) s_n += tot;
+        __syncthreads();
+    }
+    const int n = s_n;
+    // nearest neighbours of all entries
+    for (int a = warp; a < n; a += JW) warp_neighbour(a, n, L, 0, r2, inv_r2);
+    __syncthreads();
+    for (int step = 0; step < n; ++step) {   // every step removes one entry
+        float bv = INFINITY;
+        int bi = INT_MAX;
+        for (int k = tid; k < n; k += JT)
+            if (L.act[k]) argmin_pair(bv, bi, L.dd[k], k);
+        block_argmin(bv, bi, sv, si);
+        const int i = bi;
+        if (tid == 0) {
+            const int j = L.nn[i];
+            const float pi = L.pinv[i];
+            const bool beam = j < 0 || !(pi * L.d2[i] * inv_r2 < pi);
+            s_j = j;
+            s_beam = beam;
+            s_cnt = 0;
+            s_over = 0;
+            if (beam) {   // i is a jet: (px, py, pz, E)
+                const int t = s_jets++;
+                float* o = jets + (size_t)(r0 + t) * 4;
+                o[0] = L.px[i];
+                o[1] = L.py[i];
+                o[2] = 0.5f * (L.ep[i] - L.em[i]);
+                o[3] = 0.5f * (L.ep[i] + L.em[i]);
+                L.jid[i] = t;
+                L.act[i] = 0;
+            } else {      // merge into the lower index (E scheme)
+                const int k = min(i, j), l = max(i, j);
+                const float px = L.px[k] + L.px[l], py = L.py[k] + L.py[l];
+                const float ep = L.ep[k] + L.ep[l], em = L.em[k] + L.em[l];
+                L.px[k] = px;
+                L.py[k] = py;
+                L.ep[k] = ep;
+                L.em[k] = em;
+                L.y[k] = 0.5f * logf(ep / em);
+                L.phi[k] = atan2f(py, px);
+                L.pinv[k] = 1.f / (px * px + py * py);
+                L.act[l] = 0;
+                L.parent[l] = k;
+                s_list[0] = k;
+                s_cnt = 1;
+            }
+        }
+        __syncthreads();
+        const int j = s_j;
+        const bool beam = s_beam;
+        const int k = beam ? i : min(i, j);
+        const float yk = L.y[k], pk = L.phi[k];
+        // entries that lost their neighbour, or whose neighbour (the merged entry)
+        // moved away, are listed; the others only check whether the merged entry is
+        // now nearer
+        for (int m = tid; m < n; m += JT) {
+            if (!L.act[m] || (!beam && m == k)) continue;
+            const int nm = L.nn[m];
+            bool lost = beam ? nm == i : (nm == i || nm == j);
+            if (lost && !beam && nm == k) {
+                // the merged entry moved: still the nearest if it did not move away
+                // (no other entry moved, and the entry it absorbed was not the nearest)
+                const float d = dr2(L.y[m], L.phi[m], yk, pk);
+                if (d < r2 && d <= L.d2[m]) {
+                    L.d2[m] = d;
+                    L.dd[m] = entry_dist(L.pinv[m], d, k, inv_r2);
+                    lost = false;
+                }
+            } else if (!lost && !beam) {
+                const float d = dr2(L.y[m], L.phi[m], yk, pk);
+                if (d < r2 && (d < L.d2[m] || (d == L.d2[m] && k < nm))) {
+                    L.nn[m] = k;
+                    L.d2[m] = d;
+                    L.dd[m] = entry_dist(L.pinv[m], d, k, inv_r2);
+                }
+            }
+            if (lost) {
+                const int slot = atomicAdd(&s_cnt, 1);
+                if (slot < JLIST) s_list[slot] = m;
+                else s_over = 1;
+            }
+        }
+        __syncthreads();
+        const int cnt = s_cnt;
+        if (s_over) {
+            for (int a = warp; a < n; a += JW)
+                if (L.act[a]) warp_neighbour(a, n, L, 0, r2, inv_r2);
+        } else if (cnt > JW) {   // one warp per entry
+            for (int t = warp; t < cnt; t += JW) warp_neighbour(s_list[t], n, L, 0, r2, inv_r2);
+        } else {                 // few entries: the whole block scans for each in turn
+            for (int t = 0; t < cnt; ++t) {
+                const int a = s_list[t];
+                float best;
+                int bj;
+                scan_neighbour(a, n, tid, JT, L, 0, r2, best, bj);
+                block_argmin(best, bj, sv, si);
+                if (tid == 0) set_neighbour(a, best, bj, L, 0, inv_r2);
+            }
+        }
+        __syncthreads();
+    }
+    // jet index of every particle: the entry its chain of merges ends in
+    for (int m = tid; m < n; m += JT) {
+        int root = m;
+        while (L.parent[root] >= 0) root = L.parent[root];
+        if (jet_of) jet_of[L.idx[m]] = L.jid[root];
+    }
+    if (tid == 0) n_jets[ev] = s_jets;
+}
+
+}  // namespace
+}  // namespace mlpf
+
+using namespace mlpf;
+
+struct mlpf_model {
+    Model impl;
+};
+
+extern "C" mlpf_status mlpf_cluster_jets(mlpf_model* mm, const float* reg, const int32_t* cls,
+                                         const int32_t* cu_seqlens, int32_t n_events, int32_t total, float R,
+                                         float* jets, int32_t* n_jets, int32_t* jet_of, void* stream) {
+    if (!mm) { set_error("model is NULL"); return MLPF_E_INVALID; }
+    if (n_events < 0 || total < 0) { set_error("negative size"); return MLPF_E_INVALID; }
+    if (!(R > 0.f && R <= 2.f)) { set_error("jet distance parameter R must be in (0, 2]"); return MLPF_E_INVALID; }
+    if (n_events > 0 && (!cu_seqlens || !n_jets)) { set_error("NULL cu_seqlens or n_jets"); return MLPF_E_INVALID; }
+    if (total > 0 && (!reg || !cls || !jets)) { set_error("NULL reg, cls or jets"); return MLPF_E_INVALID; }
+    if (n_events == 0) return MLPF_OK;
+    Model& m = mm->impl;
+    if (cudaSetDevice(m.device) != cudaSuccess) { set_error("cudaSetDevice failed"); return MLPF_E_CUDA; }
+    // scratch: 13 words and 1 byte per element, grown on demand
+    const size_t cap = (size_t)(total > 0 ? total : 1);
+    const size_t need = cap * (13 * 4 + 1) + 256;
+    if (m.jet_bytes < need) {
+        if (m.jet_base) cudaFree(m.jet_base);
+        m.jet_base = nullptr;
+        m.jet_bytes = 0;
+        const cudaError_t e = cudaMalloc(&m.jet_base, need);
+        if (e != cudaSuccess) { set_error(std::string("jet scratch allocation: ") + cudaGetErrorString(e)); return MLPF_E_OOM; }
+        m.jet_bytes = need;
+    }
+    float* f = (float*)m.jet_base;
+    JetScratch S;
+    S.y = f;
+    S.phi = f + cap;
+    S.pinv = f + 2 * cap;
+    S.px = f + 3 * cap;
+    S.py = f + 4 * cap;
+    S.ep = f + 5 * cap;
+    S.em = f + 6 * cap;
+    S.d2 = f + 7 * cap;
+    S.dd = f + 8 * cap;
+    int* iw = (int*)(f + 9 * cap);
+    S.nn = iw;
+    S.parent = iw + cap;
+    S.jid = iw + 2 * cap;
+    S.idx = iw + 3 * cap;
+    S.act = (unsigned char*)(iw + 4 * cap);
+    k_antikt<<<n_events, JT, 0, (cudaStream_t)stream>>>(reg, cls, cu_seqlens, R * R, S, jets, n_jets, jet_of);
+    const cudaError_t e = cudaPeekAtLastError();
+    if (e != cudaSuccess) { set_error(std::string("jet kernel launch: ") + cudaGetErrorString(e)); return MLPF_E_CUDA; }
+    return MLPF_OK;
+}

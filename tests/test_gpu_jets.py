@@ -1,0 +1,127 @@
+"""Anti-kt jets on the GPU (mlpf_cluster_jets) against the FP64 oracle.
+
+Inputs: seeded synthetic reconstructed particles (synth.gen_targets: classes by
+element type, pT, eta, phi and E near the element's own), the same arrays for
+both sides.  What is unique is compared exactly: the partition of the particles
+into jets (constituent sets) and the jet count; the jets' 4-vectors (FP32 sums on
+the GPU) within 1e-4 relative.  The GPU decides merges in FP32 and the oracle in
+FP64, so a near-tie (two distances equal to FP32 precision) may be taken in the
+other order; where that changes a jet, the jet is not matched: at least 99.5 % of
+the particles must sit in matched jets.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import jets as J
+
+pytestmark = pytest.mark.gpu
+
+
+def run_jets(model, reg, cls, cu, R):
+    import torch
+    r = torch.from_numpy(np.ascontiguousarray(reg, np.float32)).cuda()
+    c = torch.from_numpy(np.ascontiguousarray(cls, np.int32)).cuda()
+    u = torch.from_numpy(np.ascontiguousarray(cu, np.int32)).cuda()
+    jets, nj, jof = model.cluster_jets(r, c, u, R)
+    torch.cuda.synchronize()
+    return jets.cpu().numpy(), nj.cpu().numpy(), jof.cpu().numpy()
+
+
+@pytest.fixture(scope="module")
+def model():
+    from tests.util import make_model
+    m, _ = make_model(synth.SMALL, 0)
+    yield m
+    m.close()
+
+
+def partition(jof):
+    return {frozenset(np.nonzero(jof == t)[0].tolist()) for t in range(int(jof.max()) + 1)} if len(jof) and jof.max() >= 0 else set()
+
+
+def compare_event(gj, gnj, gjof, cls, reg, R):
+    """(particles, particles in matched jets) of one event, checking matched jets' 4-vectors."""
+    oj, ojof = J.event_jets(cls, reg, R)
+    assert gjof.shape == ojof.shape
+    assert ((gjof < 0) == (ojof < 0)).all()          # the same particles
+    n_part = int((ojof >= 0).sum())
+    assert gnj >= 1 or n_part == 0
+    gp = {frozenset(np.nonzero(gjof == t)[0].tolist()): t for t in range(gnj)}
+    matched = 0
+    for t in range(len(oj)):
+        s = frozenset(np.nonzero(ojof == t)[0].tolist())
+        if s in gp:
+            matched += len(s)
+            np.testing.assert_allclose(gj[gp[s]], oj[t], rtol=1e-4, atol=1e-4 * np.abs(oj[t]).max())
+    return n_part, matched
+
+
+@pytest.mark.parametrize("R", [0.4, 0.8])
+def test_jets_match_oracle(model, R):
+    sizes = [1, 2, 17, 150, 400, 0, 700, 64]
+    x, cu = synth.gen_events(41, sizes)
+    cls, reg = synth.gen_targets(42, x, cu)
+    gj, gnj, gjof = run_jets(model, reg, cls, cu, R)
+    tot = mat = 0
+    for e in range(len(sizes)):
+        sl = slice(cu[e], cu[e + 1])
+        n, m = compare_event(gj[cu[e]:cu[e + 1]], int(gnj[e]), gjof[sl], cls[sl], reg[sl], R)
+        tot, mat = tot + n, mat + m
+    assert sizes[5] == 0 and gnj[5] == 0
+    assert mat >= 0.995 * tot, (mat, tot)
+
+
+def test_closed_forms(model):
+    # event 0: two particles within R -> one jet, their sum; event 1: two beyond R ->
+    # two jets, the harder first; event 2: a class-0 element and a pT = 0 element only
+    reg = np.array([[5.0, 0.1, 0.0, 1.0, 1.0], [2.0, 0.3, np.sin(0.2), np.cos(0.2), 1.0],
+                    [2.0, 0.1, 0.0, 1.0, 1.0], [5.0, 0.5, np.sin(0.2), np.cos(0.2), 1.0],
+                    [3.0, 0.0, 0.0, 1.0, 1.0], [0.0, 0.0, 0.0, 1.0, 1.0]], np.float32)
+    cls = np.array([1, 2, 1, 3, 0, 4], np.int32)
+    cu = np.array([0, 2, 4, 6], np.int32)
+    gj, gnj, gjof = run_jets(model, reg, cls, cu, 0.4)
+    assert gnj.tolist() == [1, 2, 0]
+    assert gjof.tolist() == [0, 0, 1, 0, -1, -1]
+    _, v = J.particles(cls[:4], reg[:4])
+    np.testing.assert_allclose(gj[0], v[0] + v[1], rtol=2e-6)
+    np.testing.assert_allclose(gj[2], v[3], rtol=2e-6)
+    np.testing.assert_allclose(gj[3], v[2], rtol=2e-6)
+
+
+def test_bad_arguments_rejected(model):
+    from paper_2601_17554_b300 import _lib
+    L = model.L
+    assert L.mlpf_cluster_jets(model.h, None, None, None, 1, 0, 0.4, None, None, None, None) == _lib.MLPF_E_INVALID
+    assert L.mlpf_cluster_jets(model.h, None, None, None, 0, 0, 0.0, None, None, None, None) == _lib.MLPF_E_INVALID
+    assert L.mlpf_cluster_jets(model.h, None, None, None, 0, 0, 0.4, None, None, None, None) == _lib.MLPF_OK
+
+
+def test_full_batch_conserves_momentum(model):
+    """The 512-event workload through the BF16 forward, then jets: every event's
+    jets add up to its particles (FP32 sums), and the timing is printed."""
+    import torch
+    cfg, wseed, iseed, sizes = synth.workload("batch512")
+    x, cu = synth.gen_events(iseed, sizes)
+    from tests.util import make_model
+    fm, _ = make_model(cfg, wseed)
+    xt, ct = torch.from_numpy(x).cuda(), torch.from_numpy(cu).cuda()
+    lo, rg, cl, su = fm.forward(xt, ct, int(sizes.max()), precision="bf16")
+    fm.sync()
+    model.cluster_jets(rg, cl, ct, 0.4)   # warm-up (scratch allocation)
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
+    jets, nj, _ = model.cluster_jets(rg, cl, ct, 0.4)
+    t1.record()
+    torch.cuda.synchronize()
+    print(f"anti-kt R=0.4 on 512 events ({len(x)} elements): {t0.elapsed_time(t1):.2f} ms, "
+          f"{int(nj.sum())} jets")
+    jets, nj = jets.cpu().numpy().astype(np.float64), nj.cpu().numpy()
+    reg, cls = rg.cpu().numpy(), cl.cpu().numpy()
+    for e in range(0, len(sizes), 37):
+        sl = slice(cu[e], cu[e + 1])
+        _, v = J.particles(cls[sl], reg[sl])
+        tot = jets[cu[e]:cu[e] + nj[e]].sum(0)
+        np.testing.assert_allclose(tot, v.sum(0), rtol=1e-3, atol=1e-3 * np.abs(v).sum())
+    fm.close()
