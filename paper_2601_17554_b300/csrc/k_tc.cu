@@ -2008,7 +2008,82 @@ __global__ void __launch_bounds__(aw_threads<QR>(), QR == 128 ? 1 : 2)
                     nr[mt][e] = 0.f;
                 }
             }
+            // S - ref for keys 16q .. 16q+15 of the K tile at kbase (two 8-key column
+            // tiles); the swizzle of rows 16q + k_row does not depend on q
+            auto qkb = [&](uint32_t kbase, int q, float (&dst)[2][2][4]) {
+                uint32_t kf[4];
+                ldsm_x4(kbase + koff + 2048u * q, kf[0], kf[1], kf[2], kf[3]);
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                    for (int nt = 0; nt < 2; ++nt)
+                        mma16816_c<F16>(dst[mt][nt], qa[mt], kf[2 * nt], kf[2 * nt + 1], nr[mt]);
+            };
+            // the four 16-key steps of a full tile on the bound path (no maxima, no vote)
+            auto fast_tile = [&](uint32_t kbase, uint32_t vbase) {
+                if constexpr (kQReload) load_q();
+                // kTileSum: P summed over the tile's four steps (packed FP16 adds;
+                // the bound keeps each P <= 2^13.5, the sum of four inside the FP16
+                // range), then one row-sum MMA per tile instead of one per step
+                // (1 % faster with FP16 operands; slower with BF16)
+                uint32_t ps[2][4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    float sc[2][2][4];
+                    uint32_t vf[4], pa[2][4];
+                    ldsm_x4(vbase + (uint32_t)voff[q], vf[0], vf[1], vf[2], vf[3]);
+                    qkb(kbase, q, sc);
+#pragma unroll
+                    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                        for (int hr = 0; hr < 2; ++hr) {
+                            pa[mt][hr] = exp2_pair<F16>(sc[mt][0][2 * hr], sc[mt][0][2 * hr + 1]);
+                            pa[mt][2 + hr] = exp2_pair<F16>(sc[mt][1][2 * hr], sc[mt][1][2 * hr + 1]);
+                        }
+#pragma unroll
+                    for (int mt = 0; mt < 2; ++mt) {
+                        mma16816<F16>(o[mt][0], pa[mt], vf[0], vf[1]);
+                        mma16816<F16>(o[mt][1], pa[mt], vf[2], vf[3]);
+                        if constexpr (kTileSum) {
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) ps[mt][e] = q == 0 ? pa[mt][e] : add2<F16>(ps[mt][e], pa[mt][e]);
+                        } else {
+                            mma16816<F16>(la[mt], pa[mt], ONE2, ONE2);   // row sums
+                        }
+                    }
+                }
+                if constexpr (kTileSum) {
+#pragma unroll
+                    for (int mt = 0; mt < 2; ++mt) mma16816<F16>(la[mt], ps[mt], ONE2, ONE2);   // row sums
+                }
+            };
             for (int j = 0; j < nk; ++j, ++g) {
+                // two full tiles on the bound path with one check and one branch
+                // (halves the per-tile wait, check and release work); if the bound
+                // fails, tile j falls through to the single-tile code below
+                if (j > 0 && j + 1 < nk && ke - kb - 64 * (j + 1) >= 64) {
+                    const uint32_t s0 = g % ST, s1 = (g + 1) % ST;
+                    if (!warp_wait(&kv_full[s0], (g / ST) & 1, ab, p.status, p.wait_ns)) { ok = false; break; }
+                    if (!warp_wait(&kv_full[s1], ((g + 1) / ST) & 1, ab, p.status, p.wait_ns)) { ok = false; break; }
+                    const float km = fmaxf(kn[s0 * 4 + h], kn[s1 * 4 + h]);
+                    bool over = false;
+#pragma unroll
+                    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                        for (int hr = 0; hr < 2; ++hr) over |= fmaf(qn[mt][hr], km, nr[mt][2 * hr]) > kLimit<F16>;
+                    if (!__any_sync(0xffffffffu, over)) {
+                        fast_tile(sKa + s0 * AT_KB, sVa + s0 * AT_VB);
+                        fast_tile(sKa + s1 * AT_KB, sVa + s1 * AT_VB);
+                        __syncwarp();
+                        if (lane == 0) {
+                            mbar_arrive(&kv_empty[s0]);
+                            mbar_arrive(&kv_empty[s1]);
+                        }
+                        ++j;
+                        ++g;
+                        continue;
+                    }
+                }
                 const uint32_t s = g % ST;
                 if (!warp_wait(&kv_full[s], (g / ST) & 1, ab, p.status, p.wait_ns)) { ok = false; break; }
                 const int kvalid = ke - kb - 64 * j;
@@ -2041,41 +2116,7 @@ __global__ void __launch_bounds__(aw_threads<QR>(), QR == 128 ? 1 : 2)
                     fast = !__any_sync(0xffffffffu, over);
                 }
                 if (fast) {
-                    if constexpr (kQReload) load_q();
-                    // kTileSum: P summed over the tile's four steps (packed FP16 adds;
-                    // the bound keeps each P <= 2^13.5, the sum of four inside the FP16
-                    // range), then one row-sum MMA per tile instead of one per step
-                    // (1 % faster with FP16 operands; slower with BF16)
-                    uint32_t ps[2][4];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        float sc[2][2][4];
-                        uint32_t vf[4], pa[2][4];
-                        ldsm_x4(vb + (uint32_t)voff[q], vf[0], vf[1], vf[2], vf[3]);
-                        qk(q, sc);
-#pragma unroll
-                        for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-                            for (int hr = 0; hr < 2; ++hr) {
-                                pa[mt][hr] = exp2_pair<F16>(sc[mt][0][2 * hr], sc[mt][0][2 * hr + 1]);
-                                pa[mt][2 + hr] = exp2_pair<F16>(sc[mt][1][2 * hr], sc[mt][1][2 * hr + 1]);
-                            }
-#pragma unroll
-                        for (int mt = 0; mt < 2; ++mt) {
-                            mma16816<F16>(o[mt][0], pa[mt], vf[0], vf[1]);
-                            mma16816<F16>(o[mt][1], pa[mt], vf[2], vf[3]);
-                            if constexpr (kTileSum) {
-#pragma unroll
-                                for (int e = 0; e < 4; ++e) ps[mt][e] = q == 0 ? pa[mt][e] : add2<F16>(ps[mt][e], pa[mt][e]);
-                            } else {
-                                mma16816<F16>(la[mt], pa[mt], ONE2, ONE2);   // row sums
-                            }
-                        }
-                    }
-                    if constexpr (kTileSum) {
-#pragma unroll
-                        for (int mt = 0; mt < 2; ++mt) mma16816<F16>(la[mt], ps[mt], ONE2, ONE2);   // row sums
-                    }
+                    fast_tile(kb, vb);
                 } else {
                     // SB 16-key steps per maxima check: S of all of them first, one vote,
                     // then exponentials and PV (no branch between the steps of a block)
