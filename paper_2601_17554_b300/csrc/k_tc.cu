@@ -1822,15 +1822,6 @@ __global__ void __launch_bounds__(A32_THREADS, 1)
 // (half items, two CTAs per SM of 8 consumer warps).
 template <int QR>
 constexpr int aw_threads() { return NH * (QR / 32) * 32 + 32; }   // consumer warps + a TMA producer warp
-// Mode bits of the warp kernel's checked path (each measured on the 512-event
-// batch; the default uses none: with the key-tile bound, most tiles skip the
-// checked path and its register-lean form is fastest in both formats):
-//   2 exponentials before the maxima check, redone on a raised reference
-//   8 maxima checked once per two 16-key steps (fewer votes, more registers)
-//  16 Q fragments re-read from shared memory for every block of steps instead of
-//     held in registers (the Q tile then stays until the item's last key tile)
-template <bool F16>
-constexpr int kAwMode = 0;
 template <int ST, int QR = 128>
 struct AwLayout {
     static constexpr uint32_t QB = QR * 128;   // Q tile bytes
@@ -1842,16 +1833,14 @@ struct AwLayout {
 };
 static_assert((6 + 2 * 8) * 8 + 2 * 16 + 4 <= 256, "warp attention barrier area");
 
-template <bool F16, int ST, int AM, int QR = 128>
+template <bool F16, int ST, int QR = 128>
 __global__ void __launch_bounds__(aw_threads<QR>(), QR == 128 ? 1 : 2)
     k_attention_warp(const __grid_constant__ CUtensorMap map_q, const __grid_constant__ CUtensorMap map_k,
                      const __grid_constant__ CUtensorMap map_vt, AttnParams p) {
     constexpr int RB = QR / 32;   // 32-row blocks (one per warp) per item
     constexpr int NW = NH * RB;   // consumer warps
-    constexpr bool kOptimistic = AM & 2;
     constexpr bool kTileSum = F16;   // bound path: one row-sum MMA per tile (FP16 operands)
-    constexpr int SB = (AM & 8) ? 2 : 1;   // 16-key steps per maxima check
-    constexpr bool kQReload = AM & 16;
+    constexpr int SB = 1;   // 16-key steps per maxima check of the checked path (two: slower)
     constexpr uint32_t QB = AwLayout<ST, QR>::QB;
     using LY = AwLayout<ST, QR>;
     extern __shared__ uint8_t smem_raw[];
@@ -1988,10 +1977,8 @@ __global__ void __launch_bounds__(aw_threads<QR>(), QR == 128 ? 1 : 2)
                     t += __shfl_xor_sync(0xffffffffu, t, 2);
                     qn[mt][hr] = sqrtf(t) * 1.01f;
                 }
-            if constexpr (!kQReload) {
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&q_empty[qb]);
-            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&q_empty[qb]);
             // o: output accumulators; la: row sums (the ones-MMA accumulator, every
             // column holds its row's sum); nr: the negated exponent references of the
             // fragment's rows as an accumulator input, so that the QK^T MMA (Q
@@ -2021,7 +2008,6 @@ __global__ void __launch_bounds__(aw_threads<QR>(), QR == 128 ? 1 : 2)
             };
             // the four 16-key steps of a full tile on the bound path (no maxima, no vote)
             auto fast_tile = [&](uint32_t kbase, uint32_t vbase) {
-                if constexpr (kQReload) load_q();
                 // kTileSum: P summed over the tile's four steps (packed FP16 adds;
                 // the bound keeps each P <= 2^13.5, the sum of four inside the FP16
                 // range), then one row-sum MMA per tile instead of one per step
@@ -2125,8 +2111,7 @@ __global__ void __launch_bounds__(aw_threads<QR>(), QR == 128 ? 1 : 2)
                         if (16 * q0 >= kvalid) break;   // warp-uniform
                         float sc[SB][2][2][4];
                         uint32_t vf[SB][4];
-                        if constexpr (kQReload) load_q();
-#pragma unroll
+        #pragma unroll
                         for (int b = 0; b < SB; ++b) {
                             // V fragments (channels 0-7 / 8-15 of the head, keys 16q .. 16q+15)
                             // first: off the softmax's critical path
@@ -2146,8 +2131,6 @@ __global__ void __launch_bounds__(aw_threads<QR>(), QR == 128 ? 1 : 2)
                                                 sc[b][mt][nt][e] = -INFINITY;
                         }
                         // P = 2^(S - ref) as the A fragments of PV (16 keys = one K-step).
-                        // kOptimistic: exponentials first, against the current references,
-                        // redone if a reference is raised (else the maxima are checked first).
                         uint32_t pa[SB][2][4];
                         auto exps = [&]() {
 #pragma unroll
@@ -2163,9 +2146,6 @@ __global__ void __launch_bounds__(aw_threads<QR>(), QR == 128 ? 1 : 2)
                         const bool first = j == 0 && q0 == 0;
                         float lm[2][2];
                         bool raise = first;
-                        if constexpr (kOptimistic) {
-                            if (!first) exps();
-                        }
 #pragma unroll
                         for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
@@ -2207,7 +2187,7 @@ __global__ void __launch_bounds__(aw_threads<QR>(), QR == 128 ? 1 : 2)
                                     }
                                 }
                         }
-                        if (!kOptimistic || raised) exps();
+                        exps();
 #pragma unroll
                         for (int b = 0; b < SB; ++b)
 #pragma unroll
@@ -2222,10 +2202,6 @@ __global__ void __launch_bounds__(aw_threads<QR>(), QR == 128 ? 1 : 2)
                 if (lane == 0) mbar_arrive(&kv_empty[s]);
             }
             if (!ok) break;
-            if constexpr (kQReload) {   // the Q tile was read up to the last key tile
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&q_empty[qb]);
-            }
             const int qrow0 = it.x + it.y * ROWS + QR * it.w;   // it.w: half of the item (QR = 64)
             const int nrows = min(QR, it.z - it.y * ROWS - QR * it.w);
 #pragma unroll
@@ -2362,9 +2338,9 @@ std::string check_occupancy() {
                           occupancy(k_attention32<kOutF16<FMT>, 4>, A32_THREADS, At32Layout<4>::SMEM),
                           occupancy(k_attention<kOutF16<FMT>, 1, 6>, at_threads<1>(), AtLayout<6>::SMEM),
                           occupancy(k_attention32<kOutF16<FMT>, 6>, A32_THREADS, At32Layout<6>::SMEM),
-                          occupancy(k_attention_warp<kOutF16<FMT>, 4, kAwMode<kOutF16<FMT>>>, aw_threads<128>(), AwLayout<4>::SMEM),
-                          occupancy(k_attention_warp<kOutF16<FMT>, 8, kAwMode<kOutF16<FMT>>>, aw_threads<128>(), AwLayout<8>::SMEM),
-                          occupancy(k_attention_warp<kOutF16<FMT>, 4, kAwMode<kOutF16<FMT>>, 64>, aw_threads<64>(), AwLayout<4, 64>::SMEM) / 2};
+                          occupancy(k_attention_warp<kOutF16<FMT>, 4>, aw_threads<128>(), AwLayout<4>::SMEM),
+                          occupancy(k_attention_warp<kOutF16<FMT>, 8>, aw_threads<128>(), AwLayout<8>::SMEM),
+                          occupancy(k_attention_warp<kOutF16<FMT>, 4, 64>, aw_threads<64>(), AwLayout<4, 64>::SMEM) / 2};
     const int o[6] = {*std::min_element(o_att, o_att + 10),
                       occupancy(k_post<0, FMT>, PT_THREADS, post_smem(0, FMT)),
                       occupancy(k_post<1, FMT>, PT_THREADS, post_smem(1, FMT)),
@@ -2392,9 +2368,9 @@ void set_attrs() {
     cudaFuncSetAttribute(k_attention32<kOutF16<FMT>, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, At32Layout<4>::SMEM);
     cudaFuncSetAttribute(k_attention<kOutF16<FMT>, 1, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, AtLayout<6>::SMEM);
     cudaFuncSetAttribute(k_attention32<kOutF16<FMT>, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, At32Layout<6>::SMEM);
-    cudaFuncSetAttribute(k_attention_warp<kOutF16<FMT>, 4, kAwMode<kOutF16<FMT>>>, cudaFuncAttributeMaxDynamicSharedMemorySize, AwLayout<4>::SMEM);
-    cudaFuncSetAttribute(k_attention_warp<kOutF16<FMT>, 8, kAwMode<kOutF16<FMT>>>, cudaFuncAttributeMaxDynamicSharedMemorySize, AwLayout<8>::SMEM);
-    cudaFuncSetAttribute(k_attention_warp<kOutF16<FMT>, 4, kAwMode<kOutF16<FMT>>, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, AwLayout<4, 64>::SMEM);
+    cudaFuncSetAttribute(k_attention_warp<kOutF16<FMT>, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, AwLayout<4>::SMEM);
+    cudaFuncSetAttribute(k_attention_warp<kOutF16<FMT>, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, AwLayout<8>::SMEM);
+    cudaFuncSetAttribute(k_attention_warp<kOutF16<FMT>, 4, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, AwLayout<4, 64>::SMEM);
 }
 
 }  // namespace
@@ -2592,9 +2568,9 @@ static int64_t run_tc(Model& m, const float* x, const int32_t* cu, int n_events,
             case 4: k_attention32<AF, 4><<<g, A32_THREADS, At32Layout<4>::SMEM, st>>>(w.map_q, w.map_k, w.map_vt, ap); break;
             case 5: k_attention<AF, 1, 6><<<g, at_threads<1>(), AtLayout<6>::SMEM, st>>>(w.map_q, w.map_k, w.map_vt, ap); break;
             case 6: k_attention32<AF, 6><<<g, A32_THREADS, At32Layout<6>::SMEM, st>>>(w.map_q, w.map_k, w.map_vt, ap); break;
-            case 7: k_attention_warp<AF, 4, kAwMode<AF>><<<g, aw_threads<128>(), AwLayout<4>::SMEM, st>>>(w.map_q, w.map_k, w.map_vt, ap); break;
-            case 8: k_attention_warp<AF, 8, kAwMode<AF>><<<g, aw_threads<128>(), AwLayout<8>::SMEM, st>>>(w.map_q, w.map_k, w.map_vt, ap); break;
-            case 9: k_attention_warp<AF, 4, kAwMode<AF>, 64><<<2 * g.x, aw_threads<64>(), AwLayout<4, 64>::SMEM, st>>>(w.map_q64, w.map_k, w.map_vt, ap); break;
+            case 7: k_attention_warp<AF, 4><<<g, aw_threads<128>(), AwLayout<4>::SMEM, st>>>(w.map_q, w.map_k, w.map_vt, ap); break;
+            case 8: k_attention_warp<AF, 8><<<g, aw_threads<128>(), AwLayout<8>::SMEM, st>>>(w.map_q, w.map_k, w.map_vt, ap); break;
+            case 9: k_attention_warp<AF, 4, 64><<<2 * g.x, aw_threads<64>(), AwLayout<4, 64>::SMEM, st>>>(w.map_q64, w.map_k, w.map_vt, ap); break;
             default: k_attention<AF, 1, 4><<<g, at_threads<1>(), AtLayout<4>::SMEM, st>>>(w.map_q, w.map_k, w.map_vt, ap); break;
         }
         prof_end(m, st);
