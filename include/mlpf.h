@@ -358,8 +358,8 @@ enum {
                                        confidence = mean (0, default) or minimum (1) over
                                        the event's elements of the max softmax */
     MLPF_OPT_HOST_CHUNKS = 12       /* mlpf_forward_host: the batch is split into this many
-                                       chunks of consecutive events (about equal element
-                                       counts; 1..16, default 8); chunk c's input copy,
+                                       chunks of consecutive events (element counts in the
+                                       ratio 1/2 : 1 : ... : 1 : 1/2; 1..16, default 8); chunk c's input copy,
                                        forward and output copy run on three streams, so
                                        copies overlap the neighbouring chunks' compute.
                                        Batches under 65536 elements run as one chunk. */

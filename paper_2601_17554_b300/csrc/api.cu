@@ -582,12 +582,15 @@ mlpf_status mlpf_forward_host(mlpf_model* mm, int32_t precision, const float* x,
             CK(cudaMemcpyAsync(event_sums, w.hsums, (size_t)n_events * 3 * 8, cudaMemcpyDeviceToHost, st));
         return mlpf_sync(mm, stream);
     }
-    // chunks of consecutive events with about total / K elements each (at least one event)
+    // chunks of consecutive events (at least one event each); the first and the last
+    // chunk are half the size of the others (weights 1/2, 1, ..., 1, 1/2), since their
+    // input and output copies are the only ones no compute overlaps
     std::vector<int> e0(K + 1);
     e0[0] = 0;
     e0[K] = n_events;
     for (int c = 1; c < K; ++c) {
-        const int64_t target = (int64_t)total * c / K;
+        const int64_t target = K < 3 ? (int64_t)total * c / K
+                                     : (int64_t)((double)total * (2.0 * c - 1.0) / (2.0 * (K - 1)));
         int e = e0[c - 1] + 1;
         while (e < n_events - (K - c) && cu_seqlens[e] < target) ++e;
         e0[c] = e;
