@@ -29,7 +29,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     deps = [os.path.join(CSRC, h) for h in HEADERS] + [
         os.path.join(os.path.dirname(HERE), "include", "mlpf.h")]
     dep_t = max(_mtime(d) for d in deps)
-    objs = []
+    objs, jobs = [], []
     for s in SOURCES:
         src = os.path.join(CSRC, s)
         obj = os.path.join(BUILD, s.replace(".cu", ".o"))
@@ -38,11 +38,16 @@ def build(force: bool = False, verbose: bool = False) -> str:
             cmd = [NVCC, *FLAGS, "-c", src, "-o", obj]
             if verbose:
                 cmd.insert(1, "-Xptxas=-v")
-            r = subprocess.run(cmd, capture_output=True, text=True)
-            if r.returncode != 0:
-                raise RuntimeError(f"nvcc failed for {s}:\n{r.stdout}\n{r.stderr}")
-            if verbose:
-                print(r.stderr)
+            jobs.append((s, cmd))
+    # the translation units compile independently: one nvcc process each, in parallel
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 1))) as ex:
+        results = list(ex.map(lambda j: (j[0], subprocess.run(j[1], capture_output=True, text=True)), jobs))
+    for s, r in results:
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed for {s}:\n{r.stdout}\n{r.stderr}")
+        if verbose:
+            print(r.stderr)
     if force or _mtime(LIB) < max(_mtime(o) for o in objs):
         cmd = [NVCC, "-shared", "-gencode", "arch=compute_103a,code=sm_103a", "-o", LIB, *objs]
         r = subprocess.run(cmd, capture_output=True, text=True)
