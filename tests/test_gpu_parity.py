@@ -213,6 +213,36 @@ def test_host_chunked_pipeline_matches_device(small_perturbed, chunks):
         model.set_option(OPT_HOST_CHUNKS, 8)
 
 
+def test_host_chunked_pipeline_windowed_attention(small_perturbed):
+    """The chunked host pipeline with windowed attention: every chunk's forward
+    reuses the eta-order, gather and scatter buffers on the same stream; the results
+    equal the device-buffer forward's bitwise."""
+    import torch
+    from paper_2601_17554_b300._lib import OPT_ATTN_WINDOW, OPT_HOST_CHUNKS
+    model, w = small_perturbed
+    sizes = synth.sizes_lognormal(33, 40)
+    x, cu = synth.gen_events(33, sizes)
+    assert len(x) >= 65536
+    T, E = len(x), len(sizes)
+    model.set_option(OPT_ATTN_WINDOW, 2)
+    model.set_option(OPT_HOST_CHUNKS, 5)
+    try:
+        dev = run_gpu(model, x, cu, "bf16")
+        lo = torch.full((T, 6), float("nan")).pin_memory()
+        rg = torch.full((T, 5), float("nan")).pin_memory()
+        cl = torch.full((T,), -1, dtype=torch.int32).pin_memory()
+        su = torch.full((E, 3), float("nan"), dtype=torch.float64).pin_memory()
+        model.forward_host(torch.from_numpy(x).pin_memory(), torch.from_numpy(cu).pin_memory(), int(sizes.max()),
+                           precision="bf16", logits=lo, reg=rg, cls=cl, event_sums=su)
+        np.testing.assert_array_equal(lo.numpy(), dev[0])
+        np.testing.assert_array_equal(rg.numpy(), dev[1])
+        np.testing.assert_array_equal(cl.numpy(), dev[2])
+        np.testing.assert_array_equal(su.numpy(), dev[3])
+    finally:
+        model.set_option(OPT_ATTN_WINDOW, 0)
+        model.set_option(OPT_HOST_CHUNKS, 8)
+
+
 def calibrate(model, n=32, seed=999):
     import torch
     sizes = synth.sizes_lognormal(seed, n)
