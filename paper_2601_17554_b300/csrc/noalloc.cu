@@ -47,7 +47,7 @@ namespace {
 struct NoallocDevice {
     bool ready = false;
     unsigned char* base = nullptr;  // device address of g_mlpf_noalloc_scratch
-    CUtensorMap map_q, map_k, map_o, map_vt, map_hp;
+    CUtensorMap map_q, map_q64, map_k, map_o, map_vt, map_hp;   // every map the launch sequence uses
 };
 NoallocDevice g_na[64];
 std::mutex g_na_mu;
@@ -146,6 +146,7 @@ extern "C" mlpf_status mlpf_forward_noalloc(mlpf_model* mm, int32_t precision, c
             tmp.ws = na_workspace(nd.base);
             if (!tc_make_maps(tmp)) return MLPF_E_CUDA;
             nd.map_q = tmp.ws.map_q;
+            nd.map_q64 = tmp.ws.map_q64;   // 64-row Q tiles (attention variant 9)
             nd.map_k = tmp.ws.map_k;
             nd.map_o = tmp.ws.map_o;
             nd.map_vt = tmp.ws.map_vt;
@@ -156,6 +157,7 @@ extern "C" mlpf_status mlpf_forward_noalloc(mlpf_model* mm, int32_t precision, c
     // run the same launch sequence with the model's workspace swapped for the view
     Workspace view = na_workspace(nd.base);
     view.map_q = nd.map_q;
+    view.map_q64 = nd.map_q64;
     view.map_k = nd.map_k;
     view.map_o = nd.map_o;
     view.map_vt = nd.map_vt;

@@ -52,6 +52,22 @@ def test_noalloc_matches_forward_twice(prec):
     model.close()
 
 
+@pytest.mark.parametrize("variant", [0, 4, 7, 8, 9])
+def test_noalloc_every_attention_family(variant):
+    """Each attention kernel family (tcgen05 64-key and 32-key tiles, warp-level MMAs
+    on 128-row and on 64-row items, the last with its own Q tensor map) through the
+    no-allocation entry point, as the autotuner may leave any of them selected."""
+    model, _ = make_model(synth.SMALL, 3, perturbed=True)
+    model.set_option(_lib.OPT_ATTN_VARIANT_BF16, variant)
+    x, cu = synth.gen_events(44, [2000, 1, 129, 700])
+    ref = _call("mlpf_forward", model, x, cu, _lib.MLPF_BF16, 2000)
+    got = _call("mlpf_forward_noalloc", model, x, cu, _lib.MLPF_BF16, 2000)
+    for a, b in zip(got, ref):
+        np.testing.assert_allclose(a, b, rtol=1e-6, atol=1e-6)
+    assert (got[2] == ref[2]).all()
+    model.close()
+
+
 def test_noalloc_rejects_oversize_and_fp32():
     model, _ = make_model(synth.SMALL, 0)
     x, cu = synth.gen_events(43, [16385])
