@@ -93,7 +93,8 @@ mlpf_status mlpf_get_config(const mlpf_model* m, mlpf_config* cfg);
  * Batched forward over packed events (Sec. 5.3; inference decoding as in
  * Sec. 5.3; missing-pT sums as in Sec. 3.3).  Asynchronous on `stream`.
  *
- * x          device, [total, 42] float32 row-major; event e occupies rows
+ * x          device, [total, 42] float32 row-major, 8-byte aligned (every
+ *            cudaMalloc'd or torch buffer is); event e occupies rows
  *            cu_seqlens[e] .. cu_seqlens[e+1]-1.  Feature layout: x[:,0:8]
  *            type one-hot, x[:,8] log pT, x[:,9] log E, x[:,10] eta,
  *            x[:,11:13] sin/cos phi, x[:,13:42] other features.
@@ -112,8 +113,8 @@ mlpf_status mlpf_get_config(const mlpf_model* m, mlpf_config* cfg);
  * total = 0 is a no-op.  Inputs are not validated on the device: offsets
  * that break the contract give undefined results (but stay in bounds of
  * the workspace sized from total/max_n/n_events).
- * Errors: MLPF_E_INVALID (null pointers, negative sizes, max_n > 65536,
- *         unknown precision), MLPF_E_UNSUPPORTED (precision not built for this
+ * Errors: MLPF_E_INVALID (null pointers, x not 8-byte aligned, negative
+ *         sizes, max_n > 65536, unknown precision), MLPF_E_UNSUPPORTED (precision not built for this
  *         configuration), MLPF_E_OOM (workspace growth), MLPF_E_CUDA.
  * Device-side timeouts and non-finite outputs are reported by mlpf_sync().
  */

@@ -306,6 +306,7 @@ static mlpf_status validate(const Model* m, int32_t prec, const void* x, const v
     if (total > 0 && n_events == 0) { set_error("total > 0 with no events"); return MLPF_E_INVALID; }
     if (total > 0 && (!x || !cu || !logits || !reg)) { set_error("NULL input or output pointer"); return MLPF_E_INVALID; }
     if (n_events > 0 && !cu) { set_error("cu_seqlens is NULL"); return MLPF_E_INVALID; }
+    if (total > 0 && ((uintptr_t)x & 7)) { set_error("x is not 8-byte aligned"); return MLPF_E_INVALID; }
     if (prec != MLPF_FP32 && !m->tc_supported) {
         set_error("tensor-core path is built for d=64, 4 heads, FFN 256, arch 0 models only");
         return MLPF_E_UNSUPPORTED;

@@ -509,6 +509,9 @@ MLPF_DEV void layernorm_split(const float* z32, float* out32, const float* g, co
 // through shared memory.
 constexpr int EM_THREADS = 512;   // two teams (tiles in flight) x two warpgroups
 constexpr int EV_N = 64 * 4 + 192;  // bias / LayerNorm floats of the embedding kernel
+// Staging of a 64-row block's input rows (at most 64 x 168 contiguous bytes of x) widened
+// to whole 16-byte granules: up to 15 bytes in front, the rest rounded up to 16.
+constexpr uint32_t EM_XB = 16 * ((15 + 64 * 42 * 4 + 15) / 16);
 template <int MODE, int FMT>  // MODE 0: input x (K = 42 -> 64); 1: concat(x, h_pid) (K = 106 -> 128)
 __global__ void __launch_bounds__(EM_THREADS, 1) k_embed_qkv(const __grid_constant__ CUtensorMap map_hp,
                                                              EmbedParams p) {
@@ -531,14 +534,16 @@ __global__ void __launch_bounds__(EM_THREADS, 1) k_embed_qkv(const __grid_consta
     float* red = (float*)(sH + ATOM);          // [pass][wg][row] LayerNorm partial sums
     // bias and LayerNorm vectors: b1 [64], b2 [64], ln gain [64], ln shift [64], bqkv [192]
     float* pv = (float*)(sWq + WQB + 2 * TEAM_B);
-    uint64_t* bars = (uint64_t*)(pv + EV_N);   // 0 weights; team t: 1 + 2t tma, 2 + 2t mma
+    uint64_t* bars = (uint64_t*)(pv + EV_N);   // 0 weights; team t: 1 + 2t tma, 2 + 2t mma, 5 + t x rows
     uint64_t* tma_bar = &bars[1 + 2 * team];
     uint64_t* mma_bar = &bars[2 + 2 * team];
-    uint32_t* tmem_hold = (uint32_t*)(bars + 6);
+    uint64_t* x_bar = &bars[5 + team];
+    uint32_t* tmem_hold = (uint32_t*)(bars + 8);
     int* abort_flag = (int*)(tmem_hold + 1);
+    uint8_t* sX = (uint8_t*)(bars + 16) + team * 2 * EM_XB;   // the team's tile: two blocks of x rows
 
     if (tid == 0) {
-        for (int i = 0; i < 5; ++i) mbar_init(&bars[i], 1);
+        for (int i = 0; i < 7; ++i) mbar_init(&bars[i], 1);
         *abort_flag = 0;
         fence_mbar_init();
     }
@@ -567,7 +572,37 @@ __global__ void __launch_bounds__(EM_THREADS, 1) k_embed_qkv(const __grid_consta
     const int tpad = p.counters[1];
     const int nblk = tpad >> 6;
     const int ntiles = (tpad + ROWS - 1) / ROWS;
-    uint32_t mph = 0, aph = 0;
+    uint32_t mph = 0, aph = 0, xph = 0;
+    // The input rows of tile t: each of its two 64-row blocks holds consecutive packed rows,
+    // one contiguous range of x, copied whole by the bulk-copy engine.  The range is widened
+    // to whole 16-byte granules (a granule holding a byte of x lies in x's mapped page).
+    // blk_of(t, e): the leader's copy of tile t's block entries (valid rows 0 past the end)
+    auto blk_of = [&](int t, int4 (&e)[2]) {
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+            e[b] = t < ntiles && 2 * t + b < nblk ? p.blk[2 * t + b] : make_int4(0, 0, 0, 0);
+    };
+    auto issue_x = [&](const int4 (&e)[2]) {
+        uint32_t bytes[2];
+        const uint8_t* src[2];
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const uintptr_t a = (uintptr_t)(p.x + (size_t)e[b].y * 42);
+            const uintptr_t a0 = a & ~(uintptr_t)15;
+            const uintptr_t a1 = (a + (size_t)e[b].z * 168 + 15) & ~(uintptr_t)15;
+            src[b] = (const uint8_t*)a0;
+            bytes[b] = e[b].z > 0 ? (uint32_t)(a1 - a0) : 0u;
+        }
+        mbar_arrive_expect_tx(x_bar, bytes[0] + bytes[1]);
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+            if (bytes[b]) bulk_load(sX + b * EM_XB, src[b], bytes[b], x_bar);
+    };
+    int4 enext[2];
+    if (leader && blockIdx.x * 2 + team < ntiles) {
+        blk_of(blockIdx.x * 2 + team, enext);
+        issue_x(enext);
+    }
     // the team syncs, its leader issues, everyone waits for the MMA; false on failure
     auto run_mma = [&](auto issue) -> bool {
         tc_fence_before();
@@ -589,31 +624,29 @@ __global__ void __launch_bounds__(EM_THREADS, 1) k_embed_qkv(const __grid_consta
         const int p0 = tile * ROWS;
         const int prow_pad = p0 + r;
         const RowInfo ri = row_info(p.blk, nblk, prow_pad);
-        // the team's next tile: its row's block entry now, its feature row into L2
-        // after the first GEMM (a tile otherwise starts with two dependent HBM reads)
-        const int pn = prow_pad + 2 * (int)gridDim.x * ROWS;
-        int2 nb = make_int2(0, 0);   // packed row of the block's first row, valid rows
-        if (tile + 2 * (int)gridDim.x < ntiles && (pn >> 6) < nblk) {
-            const int4 e = p.blk[pn >> 6];
-            nb = make_int2(e.y, e.z);
-        }
+        const bool more = tile + 2 * (int)gridDim.x < ntiles;
+        if (leader && more) blk_of(tile + 2 * (int)gridDim.x, enext);   // used after the first GEMM
         if (TMA_HP && leader) {
             mbar_arrive_expect_tx(tma_bar, ATOM);
             tma_load_2d(sA + ATOM, &map_hp, 0, p0, tma_bar);
             if (tile + 2 * (int)gridDim.x < ntiles) tma_prefetch_2d(&map_hp, 0, p0 + 2 * gridDim.x * ROWS);
         }
         float v[32];
-        // this warpgroup's 32 of the row's 42 features (zero padded to 64)
+        // this warpgroup's 32 of the row's 42 features (zero padded to 64), from the
+        // staged block, at the row's offset from the block's first granule
+        fail |= !mbar_wait(x_bar, xph, ab, p.status, ST_TIMEOUT_GEMM, p.wait_ns);
+        xph ^= 1;
 #pragma unroll
         for (int i = 0; i < 32; ++i) v[i] = 0.f;
         if (ri.valid) {
-            const float2* src = (const float2*)(p.x + (size_t)ri.prow * 42 + 32 * wg);
+            const uintptr_t a = (uintptr_t)(p.x + (size_t)(ri.prow - (r & 63)) * 42);
+            const float2* src = (const float2*)(sX + (r >> 6) * EM_XB + (a & 15) + (r & 63) * 168 + 128 * wg);
             if (wg == 0) {
 #pragma unroll
-                for (int i = 0; i < 16; ++i) { const float2 t = __ldg(src + i); v[2 * i] = t.x; v[2 * i + 1] = t.y; }
+                for (int i = 0; i < 16; ++i) { const float2 t = src[i]; v[2 * i] = t.x; v[2 * i + 1] = t.y; }
             } else {
 #pragma unroll
-                for (int i = 0; i < 5; ++i) { const float2 t = __ldg(src + i); v[2 * i] = t.x; v[2 * i + 1] = t.y; }
+                for (int i = 0; i < 5; ++i) { const float2 t = src[i]; v[2 * i] = t.x; v[2 * i + 1] = t.y; }
             }
         }
         st_op<FE>(sA, r, v, 32, 32 * wg, 1.f);
@@ -640,11 +673,8 @@ __global__ void __launch_bounds__(EM_THREADS, 1) k_embed_qkv(const __grid_consta
         aph ^= 1;
         // embedding FFN, first layer
         if (!run_mma([&] { issue_gemm<FE>(tbase, sA, sW1, 64, KA); })) break;
-        if ((pn & 63) < nb.y) {
-            const float* xn = p.x + (size_t)(nb.x + (pn & 63)) * 42 + 32 * wg;   // this warpgroup's features
-            prefetch_l2(xn);
-            prefetch_l2(xn + (wg == 0 ? 31 : 9));
-        }
+        // every thread of the team has read its row: stage the team's next tile
+        if (leader && more) issue_x(enext);
         tmem_ld32(trow + 32 * wg, v);
         tmem_wait_ld();
 #pragma unroll
@@ -2243,7 +2273,8 @@ uint32_t embed_smem(int mode, int fmt) {
     // weights + two teams x (A operand, hidden tile, LayerNorm sums) + barriers + alignment;
     // at least 116 KB so that no two CTAs (512 TMEM columns each) share an SM
     const uint32_t need =
-        64 * 128 * ka + 64 * 128 + 192 * 128 + 2 * (ka * ATOM + ATOM + 2 * 2 * 128 * 4) + EV_N * 4 + 64 + 1024;
+        64 * 128 * ka + 64 * 128 + 192 * 128 + 2 * (ka * ATOM + ATOM + 2 * 2 * 128 * 4) + EV_N * 4 + 128 +
+        4 * EM_XB + 1024;
     return need < 116 * 1024 ? 116 * 1024 : need;
 }
 uint32_t post_smem(int mode, int fmt) {

@@ -118,6 +118,7 @@ extern "C" mlpf_status mlpf_forward_noalloc(mlpf_model* mm, int32_t precision, c
         set_error("NULL input or output pointer");
         return MLPF_E_INVALID;
     }
+    if (total > 0 && ((uintptr_t)x & 7)) { set_error("x is not 8-byte aligned"); return MLPF_E_INVALID; }
     if (cudaSetDevice(m.device) != cudaSuccess) { set_error("cudaSetDevice failed"); return MLPF_E_CUDA; }
     if (m.device < 0 || m.device >= 64) { set_error("device index out of range"); return MLPF_E_INVALID; }
     cudaStream_t st = (cudaStream_t)stream;

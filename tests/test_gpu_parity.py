@@ -347,3 +347,32 @@ def test_fp32_deterministic(small_perturbed):
     b = run_gpu(model, x, cu, "fp32")
     for u, v in zip(a, b):
         np.testing.assert_array_equal(u, v)
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp16"])
+def test_x_alignment(precision):
+    """x may start at any 8-byte boundary: a view one row (168 bytes) into a buffer gives the
+    same outputs, bit for bit, as an aligned copy; an x that is not 8-byte aligned is
+    rejected before anything is launched."""
+    import torch
+    from paper_2601_17554_b300 import MlpfError, _lib
+    model, _ = make_model(synth.SMALL, 0)
+    sizes = [1, 63, 64, 65, 130, 700, 0, 257]
+    x, cu = synth.gen_events(45, sizes)
+    ct = torch.from_numpy(cu).cuda()
+    ref = run_gpu(model, x, cu, precision)
+    buf = torch.zeros((len(x) + 1, 42), dtype=torch.float32, device="cuda")
+    buf[1:] = torch.from_numpy(x).cuda()
+    xv = buf[1:]
+    assert xv.data_ptr() % 16 == 8
+    got = model.forward(xv, ct, max(sizes), precision=precision)
+    model.sync()
+    for a, b in zip(got, ref):
+        np.testing.assert_array_equal(a.cpu().numpy(), b)
+    flat = torch.zeros(len(x) * 42 + 1, dtype=torch.float32, device="cuda")
+    xm = flat[1:].view(len(x), 42)
+    assert xm.data_ptr() % 8 == 4
+    with pytest.raises(MlpfError) as ei:
+        model.forward(xm, ct, max(sizes), precision=precision)
+    assert ei.value.status == _lib.MLPF_E_INVALID
+    model.close()
