@@ -129,8 +129,9 @@ mlpf_status mlpf_forward(mlpf_model* m, int32_t precision,
  * device workspace, runs the forward and copies the outputs back; returns when
  * the host outputs are written.  Large batches are processed in chunks of
  * consecutive events (MLPF_OPT_HOST_CHUNKS) whose host-to-device copies,
- * forwards and device-to-host copies are pipelined on the caller's stream and
- * two copy streams of the model; the results are those of a single-chunk call
+ * forwards and device-to-host copies are pipelined on the caller's stream,
+ * two copy streams of the model and (MLPF_OPT_HOST_STREAMS) a second compute
+ * stream; the results are those of a single-chunk call
  * (an event's outputs do not depend on the other events).  x, cu_seqlens: host inputs (pinned memory lets the copies run
  * asynchronously); logits, reg: host outputs; cls, event_sums: host outputs or
  * NULL.  Errors as mlpf_forward plus those of mlpf_sync.
@@ -358,12 +359,18 @@ enum {
     MLPF_OPT_GATE_CONFIDENCE = 11,  /* student models in mlpf_forward_gated: event
                                        confidence = mean (0, default) or minimum (1) over
                                        the event's elements of the max softmax */
-    MLPF_OPT_HOST_CHUNKS = 12       /* mlpf_forward_host: the batch is split into this many
+    MLPF_OPT_HOST_CHUNKS = 12,      /* mlpf_forward_host: the batch is split into this many
                                        chunks of consecutive events (element counts in the
                                        ratio 1/2 : 1 : ... : 1 : 1/2; 1..16, default 8); chunk c's input copy,
                                        forward and output copy run on three streams, so
                                        copies overlap the neighbouring chunks' compute.
                                        Batches under 65536 elements run as one chunk. */
+    MLPF_OPT_HOST_STREAMS = 13      /* mlpf_forward_host: compute streams the chunks
+                                       alternate over, 1 or 2 (default 2).  With 2, odd
+                                       chunks run on a second stream of the model with a
+                                       second workspace (sized for the largest chunk), so
+                                       a chunk's last attention items overlap the next
+                                       chunk's kernels.  The results do not depend on it. */
 };
 #define MLPF_ATTN_VARIANTS 10
 mlpf_status mlpf_set_option(mlpf_model* m, int32_t option, int64_t value);

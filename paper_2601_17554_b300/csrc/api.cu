@@ -48,8 +48,8 @@ static void prof_destroy(Profile& p) {
 }
 
 bool GraphKey::operator<(const GraphKey& o) const {
-    return std::tie(prec, x, cu, lo, rg, cl, su, n_events, total, max_n) <
-           std::tie(o.prec, o.x, o.cu, o.lo, o.rg, o.cl, o.su, o.n_events, o.total, o.max_n);
+    return std::tie(prec, x, cu, lo, rg, cl, su, n_events, total, max_n, ws) <
+           std::tie(o.prec, o.x, o.cu, o.lo, o.rg, o.cl, o.su, o.n_events, o.total, o.max_n, o.ws);
 }
 
 // ------------------------------------------------------------ blob parsing
@@ -385,7 +385,7 @@ static mlpf_status forward_impl(Model& m, int32_t prec, const float* x, const in
         m.last_launches = n;
         return s;
     }
-    GraphKey key{prec, x, cu, logits, reg, cls, sums, n_events, total, max_n};
+    GraphKey key{prec, x, cu, logits, reg, cls, sums, n_events, total, max_n, m.ws.base};
     auto it = m.graphs.find(key);
     if (it == m.graphs.end()) {
         if (m.graphs.size() >= 16) {
@@ -505,10 +505,12 @@ void mlpf_free(mlpf_model* mm) {
     if (m.cap_stream) cudaStreamDestroy(m.cap_stream);
     if (m.copy_in) cudaStreamDestroy(m.copy_in);
     if (m.copy_out) cudaStreamDestroy(m.copy_out);
+    if (m.compute2) cudaStreamDestroy(m.compute2);
     for (cudaEvent_t e : m.chunk_ev) cudaEventDestroy(e);
     if (m.cu_pinned) cudaFreeHost(m.cu_pinned);
     if (m.jet_base) cudaFree(m.jet_base);
     if (m.ws.base) cudaFree(m.ws.base);
+    if (m.ws_alt.base) cudaFree(m.ws_alt.base);
     if (m.w.f32_base) cudaFree(m.w.f32_base);
     if (m.w.img_base) cudaFree(m.w.img_base);
     if (m.w.img8_base) cudaFree(m.w.img8_base);
@@ -610,6 +612,28 @@ mlpf_status mlpf_forward_host(mlpf_model* mm, int32_t precision, const float* x,
             m.cu_pinned[e0[c] + c + i] = cu_seqlens[e0[c] + i] - cu_seqlens[e0[c]];
     if (!m.copy_in) CK(cudaStreamCreateWithFlags(&m.copy_in, cudaStreamNonBlocking));
     if (!m.copy_out) CK(cudaStreamCreateWithFlags(&m.copy_out, cudaStreamNonBlocking));
+    // the host staging buffers of this call (in the main workspace)
+    float* const hx = w.hx;
+    int32_t* const hcc = w.hcu_chunks;
+    float* const hlo = w.hlogits;
+    float* const hrg = w.hreg_out;
+    int32_t* const hcl = w.hcls;
+    double* const hsu = w.hsums;
+    // odd chunks on a second compute stream with a workspace of their own, sized for the
+    // largest chunk before anything is launched (a workspace that grows drops the graphs)
+    const bool two = m.host_streams > 1;
+    if (two) {
+        int max_rows = 0, max_ev = 0;
+        for (int c = 0; c < K; ++c) {
+            max_rows = std::max(max_rows, cu_seqlens[e0[c + 1]] - cu_seqlens[e0[c]]);
+            max_ev = std::max(max_ev, e0[c + 1] - e0[c]);
+        }
+        std::swap(m.ws, m.ws_alt);
+        s = ensure_workspace(m, max_rows, max_ev, precision != MLPF_FP32);
+        std::swap(m.ws, m.ws_alt);
+        if (s != MLPF_OK) return s;
+        if (!m.compute2) CK(cudaStreamCreateWithFlags(&m.compute2, cudaStreamNonBlocking));
+    }
     while ((int)m.chunk_ev.size() < 2 + 2 * K) {
         cudaEvent_t e;
         CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
@@ -620,32 +644,40 @@ mlpf_status mlpf_forward_host(mlpf_model* mm, int32_t precision, const float* x,
     CK(cudaEventRecord(ev_start, st));
     CK(cudaStreamWaitEvent(m.copy_in, ev_start, 0));
     CK(cudaStreamWaitEvent(m.copy_out, ev_start, 0));
-    CK(cudaMemcpyAsync(w.hcu_chunks, m.cu_pinned, ncu * 4, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(hcc, m.cu_pinned, ncu * 4, cudaMemcpyHostToDevice, st));
+    if (two) {
+        // the second compute stream starts after the per-chunk offsets are on the device
+        CK(cudaEventRecord(ev_start, st));
+        CK(cudaStreamWaitEvent(m.compute2, ev_start, 0));
+    }
     for (int c = 0; c < K; ++c) {
         const size_t r0 = (size_t)cu_seqlens[e0[c]], rows = (size_t)cu_seqlens[e0[c + 1]] - r0;
         if (rows > 0)
-            CK(cudaMemcpyAsync(w.hx + r0 * 42, x + r0 * 42, rows * 42 * 4, cudaMemcpyHostToDevice, m.copy_in));
+            CK(cudaMemcpyAsync(hx + r0 * 42, x + r0 * 42, rows * 42 * 4, cudaMemcpyHostToDevice, m.copy_in));
         CK(cudaEventRecord(m.chunk_ev[2 + 2 * c], m.copy_in));
     }
     int64_t launches = 0;
     for (int c = 0; c < K; ++c) {
         const size_t r0 = (size_t)cu_seqlens[e0[c]], rows = (size_t)cu_seqlens[e0[c + 1]] - r0;
         const int ne = e0[c + 1] - e0[c];
-        CK(cudaStreamWaitEvent(st, m.chunk_ev[2 + 2 * c], 0));
-        s = forward_impl(m, precision, w.hx + r0 * 42, w.hcu_chunks + e0[c] + c, ne, (int32_t)rows, max_n,
-                         w.hlogits + r0 * 6, w.hreg_out + r0 * 5, cls ? w.hcls + r0 : nullptr,
-                         event_sums ? w.hsums + (size_t)e0[c] * 3 : nullptr, st);
+        const bool alt = two && (c & 1);
+        cudaStream_t cs = alt ? m.compute2 : st;
+        CK(cudaStreamWaitEvent(cs, m.chunk_ev[2 + 2 * c], 0));
+        if (alt) std::swap(m.ws, m.ws_alt);
+        s = forward_impl(m, precision, hx + r0 * 42, hcc + e0[c] + c, ne, (int32_t)rows, max_n, hlo + r0 * 6,
+                         hrg + r0 * 5, cls ? hcl + r0 : nullptr, event_sums ? hsu + (size_t)e0[c] * 3 : nullptr, cs);
+        if (alt) std::swap(m.ws, m.ws_alt);
         if (s != MLPF_OK) return s;
         launches += m.last_launches;
-        CK(cudaEventRecord(m.chunk_ev[3 + 2 * c], st));
+        CK(cudaEventRecord(m.chunk_ev[3 + 2 * c], cs));
         CK(cudaStreamWaitEvent(m.copy_out, m.chunk_ev[3 + 2 * c], 0));
         if (rows > 0) {
-            CK(cudaMemcpyAsync(logits + r0 * 6, w.hlogits + r0 * 6, rows * 6 * 4, cudaMemcpyDeviceToHost, m.copy_out));
-            CK(cudaMemcpyAsync(reg + r0 * 5, w.hreg_out + r0 * 5, rows * 5 * 4, cudaMemcpyDeviceToHost, m.copy_out));
-            if (cls) CK(cudaMemcpyAsync(cls + r0, w.hcls + r0, rows * 4, cudaMemcpyDeviceToHost, m.copy_out));
+            CK(cudaMemcpyAsync(logits + r0 * 6, hlo + r0 * 6, rows * 6 * 4, cudaMemcpyDeviceToHost, m.copy_out));
+            CK(cudaMemcpyAsync(reg + r0 * 5, hrg + r0 * 5, rows * 5 * 4, cudaMemcpyDeviceToHost, m.copy_out));
+            if (cls) CK(cudaMemcpyAsync(cls + r0, hcl + r0, rows * 4, cudaMemcpyDeviceToHost, m.copy_out));
         }
         if (event_sums && ne > 0)
-            CK(cudaMemcpyAsync(event_sums + (size_t)e0[c] * 3, w.hsums + (size_t)e0[c] * 3, (size_t)ne * 3 * 8,
+            CK(cudaMemcpyAsync(event_sums + (size_t)e0[c] * 3, hsu + (size_t)e0[c] * 3, (size_t)ne * 3 * 8,
                                cudaMemcpyDeviceToHost, m.copy_out));
     }
     m.last_launches = launches;
@@ -821,6 +853,10 @@ mlpf_status mlpf_set_option(mlpf_model* mm, int32_t option, int64_t value) {
             if (value < 1 || value > 16) { set_error("host chunks must be 1..16"); return MLPF_E_INVALID; }
             m.host_chunks = (int)value;
             return MLPF_OK;   // host-side choice
+        case MLPF_OPT_HOST_STREAMS:
+            if (value < 1 || value > 2) { set_error("host streams must be 1 or 2"); return MLPF_E_INVALID; }
+            m.host_streams = (int)value;
+            return MLPF_OK;   // host-side choice
         case MLPF_OPT_ATTN_VARIANT_BF16:
         case MLPF_OPT_ATTN_VARIANT_FP16:
         case MLPF_OPT_ATTN_VARIANT_FP8:
@@ -864,6 +900,7 @@ mlpf_status mlpf_get_option(const mlpf_model* mm, int32_t option, int64_t* value
         case MLPF_OPT_ATTN_WINDOW: *value = m.attn_window; return MLPF_OK;
         case MLPF_OPT_GATE_CONFIDENCE: *value = m.gate_confidence; return MLPF_OK;
         case MLPF_OPT_HOST_CHUNKS: *value = m.host_chunks; return MLPF_OK;
+        case MLPF_OPT_HOST_STREAMS: *value = m.host_streams; return MLPF_OK;
         default: set_error("unknown option " + std::to_string(option)); return MLPF_E_INVALID;
     }
 }

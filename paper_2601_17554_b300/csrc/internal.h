@@ -80,6 +80,7 @@ struct GraphKey {
     int prec;
     const void *x, *cu, *lo, *rg, *cl, *su;
     int32_t n_events, total, max_n;
+    const void* ws;   // base of the workspace the graph's kernels use
     bool operator<(const GraphKey& o) const;
 };
 
@@ -116,7 +117,11 @@ struct Model {
     int gate_confidence = 0;
     // host-buffer forward: event chunks pipelined over copy-in, compute and copy-out
     int host_chunks = 8;
-    cudaStream_t copy_in = nullptr, copy_out = nullptr;
+    // compute streams the chunks alternate over (2: odd chunks run on compute2 with
+    // their own workspace ws_alt, so a chunk's attention tail overlaps the next chunk)
+    int host_streams = 2;
+    cudaStream_t copy_in = nullptr, copy_out = nullptr, compute2 = nullptr;
+    Workspace ws_alt;
     std::vector<cudaEvent_t> chunk_ev;   // [0] start, [1] copies out done, then 2 per chunk
     int32_t* cu_pinned = nullptr;        // pinned host staging of the per-chunk cu_seqlens
     size_t cu_pinned_cap = 0;

@@ -197,20 +197,24 @@ def test_host_buffer_entry_point_matches_device(small_perturbed):
     np.testing.assert_array_equal(su.numpy(), dev[3])
 
 
+@pytest.mark.parametrize("streams", [1, 2])
 @pytest.mark.parametrize("chunks", [1, 3, 4, 16])
-def test_host_chunked_pipeline_matches_device(small_perturbed, chunks):
+def test_host_chunked_pipeline_matches_device(small_perturbed, chunks, streams):
     """mlpf_forward_host on a batch above the chunking threshold: chunks of
-    consecutive events with their copies overlapped by the neighbours' compute give
+    consecutive events with their copies overlapped by the neighbours' compute (and,
+    with two compute streams, alternate chunks on a second stream and workspace) give
     the device-buffer results bitwise (an event's outputs do not depend on the
     other events)."""
     import torch
-    from paper_2601_17554_b300._lib import OPT_HOST_CHUNKS
+    from paper_2601_17554_b300._lib import OPT_HOST_CHUNKS, OPT_HOST_STREAMS
     model, w = small_perturbed
     sizes = synth.sizes_lognormal(31, 40)
     x, cu = synth.gen_events(31, sizes)
     assert len(x) >= 65536
     T, E = len(x), len(sizes)
     model.set_option(OPT_HOST_CHUNKS, chunks)
+    model.set_option(OPT_HOST_STREAMS, streams)
+    assert model.get_option(OPT_HOST_STREAMS) == streams
     try:
         for prec in ("bf16", "fp16"):
             dev = run_gpu(model, x, cu, prec)
@@ -227,6 +231,7 @@ def test_host_chunked_pipeline_matches_device(small_perturbed, chunks):
             np.testing.assert_array_equal(su.numpy(), dev[3])
     finally:
         model.set_option(OPT_HOST_CHUNKS, 8)
+        model.set_option(OPT_HOST_STREAMS, 2)
 
 
 def test_host_chunked_pipeline_windowed_attention(small_perturbed):
