@@ -33,3 +33,27 @@ def test_gemm_flops_per_element_d64_model():
     import dataclasses
     deeper = dataclasses.replace(synth.SMALL, l_pid=2)
     assert bench.gemm_flops_per_element(deeper) - f == 2 * (4 * 64 * 64 + 2 * 64 * 256)
+
+
+def test_reference_arm_json_line(capsys, monkeypatch):
+    """`bench.py --impl reference`: one JSON line with the contract's keys (the oracle
+    timed on the host cores, no host-device copies), printed by rank 0 only."""
+    import argparse
+    import json
+    monkeypatch.setenv("RANK", "0")
+    args = argparse.Namespace(gpus=1, steps=1, warmup=0)
+    bench.run_reference(args)
+    lines = [l for l in capsys.readouterr().out.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "events/s"
+    assert d["value"] > 0 and d["higher_is_better"] is True and d["dtype"] == "f64"
+    assert d["steps"] == 1 and d["n_gpus"] == 1 and d["vs_baseline"] is None
+    assert d["config"]["workload"].startswith(bench.WORKLOAD)
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
+    e = d["e2e"]
+    assert e["value"] == d["value"] and e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+    monkeypatch.setenv("RANK", "1")
+    bench.run_reference(args)
+    assert capsys.readouterr().out.strip() == ""
