@@ -216,7 +216,7 @@ def test_host_chunked_pipeline_matches_device(small_perturbed, chunks, streams):
     model.set_option(OPT_HOST_STREAMS, streams)
     assert model.get_option(OPT_HOST_STREAMS) == streams
     try:
-        for prec in ("bf16", "fp16"):
+        for prec in ("bf16", "fp16", "fp32"):
             dev = run_gpu(model, x, cu, prec)
             xh, cuh = torch.from_numpy(x).pin_memory(), torch.from_numpy(cu).pin_memory()
             lo = torch.full((T, 6), float("nan")).pin_memory()
