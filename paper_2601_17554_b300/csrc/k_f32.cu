@@ -209,17 +209,21 @@ __global__ void k_decode(const float* __restrict__ x, const float* __restrict__ 
     o[4] = expf(x[(size_t)r * 42 + 9] + a[4]);
 }
 
-// One block of 256 threads per event: class = argmax (lowest index on ties);
+// One block of ES_THREADS threads per event: class = argmax (lowest index on ties);
 // FP64 sums of -px, -py and pT over elements with class != 0.  Threads stride
 // over the event's rows; the partial sums are combined by a fixed xor
-// butterfly per warp and then in warp order, so the result is deterministic.
-__global__ void __launch_bounds__(256) k_event_sums(const int32_t* __restrict__ cu, int n_events,
+// butterfly per warp and then in warp order, so the result is deterministic (and
+// does not depend on the other events of the batch).  512 threads: the largest
+// events set the kernel's time, and 512-thread blocks of a 512-event batch are
+// still resident at once (four per SM).
+constexpr int ES_THREADS = 512, ES_WARPS = ES_THREADS / 32;
+__global__ void __launch_bounds__(ES_THREADS) k_event_sums(const int32_t* __restrict__ cu, int n_events,
                                                     const float* __restrict__ logits,
                                                     const float* __restrict__ reg,
                                                     int32_t* __restrict__ cls_out,
                                                     double* __restrict__ sums, int n_cls,
                                                     int arch, unsigned* status) {
-    __shared__ double part[3][8];
+    __shared__ double part[3][ES_WARPS];
     __shared__ int bad;
     const int e = blockIdx.x;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -228,7 +232,7 @@ __global__ void __launch_bounds__(256) k_event_sums(const int32_t* __restrict__ 
     const int s = cu[e], t = cu[e + 1];
     double px = 0.0, py = 0.0, pt = 0.0;
     bool finite = true;
-    for (int r = s + threadIdx.x; r < t; r += 256) {
+    for (int r = s + threadIdx.x; r < t; r += ES_THREADS) {
         const float* lo = logits + (size_t)r * n_cls;
         // arch 0: argmax of all scores (lowest index on ties); arch 1: a particle
         // where the binary logit (column 0) is > 0, PID = 1 + argmax of columns 1..
@@ -274,7 +278,7 @@ __global__ void __launch_bounds__(256) k_event_sums(const int32_t* __restrict__ 
     __syncthreads();
     if (threadIdx.x == 0) {
         double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-        for (int w = 0; w < 8; ++w) {
+        for (int w = 0; w < ES_WARPS; ++w) {
             a0 += part[0][w];
             a1 += part[1][w];
             a2 += part[2][w];
@@ -532,7 +536,7 @@ int64_t run_event_sums(Model& m, const int32_t* cu, int n_events, const float* l
                        cudaStream_t st) {
     if (n_events <= 0 || (!cls && !sums)) return 0;
     prof_begin(m, st, "event_sums");
-    k_event_sums<<<n_events, 256, 0, st>>>(cu, n_events, logits, reg, cls, sums, n_cls, m.cfg.arch, m.status);
+    k_event_sums<<<n_events, ES_THREADS, 0, st>>>(cu, n_events, logits, reg, cls, sums, n_cls, m.cfg.arch, m.status);
     prof_end(m, st);
     if (cudaPeekAtLastError() != cudaSuccess) return -1;
     return 1;
