@@ -312,16 +312,36 @@ __global__ void __launch_bounds__(1024) k_schedule(const int32_t* __restrict__ c
         if (n > 0) atomicAdd(&hist[(n + 63) >> 6], (n + 127) >> 7);
     }
     __syncthreads();
-    if (tid == 0) {  // exclusive offsets, larger events first
-        int acc = 0;
-        for (int b = NB - 1; b >= 0; --b) {
-            const int c = hist[b];
-            hist[b] = acc;
-            acc += c;
+    {   // exclusive offsets, larger events first: a block-wide scan of buckets 1024 .. 1
+        // (thread t takes bucket NB - 1 - t; bucket 0 holds no items, events of N = 0)
+        const int b = NB - 1 - tid;
+        const int c = hist[b];
+        int incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
         }
-        counters[0] = acc;
+        if (lane == 31) wsum[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            int w = wsum[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += t;
+            }
+            wsum[lane] = w;
+        }
+        __syncthreads();
+        const int excl = incl - c + (wid > 0 ? wsum[wid - 1] : 0);
+        hist[b] = excl;
+        if (tid == 1023) {
+            hist[0] = excl + c;
+            counters[0] = excl + c;
+        }
+        __syncthreads();
     }
-    __syncthreads();
     for (int base = 0; base < n_events; base += 1024) {
         const int e = base + tid;
         const int n = e < n_events ? min(max(cu[e + 1] - cu[e], 0), 65536) : 0;
