@@ -222,77 +222,168 @@ def workload_inputs(rank, n_events=512):
 
 
 # --------------------------------------------------------------------- oracle
-def oracle_sample(cfg, W, x, cu, budget_s, max_events=None, window=0):
-    """Time the FP64 oracle on the first events of the batch (i.i.d. sizes)."""
-    import oracle
-    out, t0, done = [], time.perf_counter(), 0
-    n = len(cu) - 1
-    while done < n and (max_events is None or done < max_events):
-        e = done
-        xs = x[cu[e]:cu[e + 1]]
-        if window > 0:
-            r = oracle.forward(W, cfg, xs, [0, len(xs)], window=window)
-            lo, reg, cls, sums = r.logits, r.reg, r.cls, r.sums[0]
-        else:
-            lo, raw = oracle.forward_event(W, cfg, xs)
-            cls, reg = oracle.decode(xs, lo, raw)
-            sums = oracle.event_sums(cls, reg, [0, len(xs)])[0]
-        out.append((e, lo, reg, cls, sums))
-        done += 1
-        if time.perf_counter() - t0 > budget_s:
-            break
-    return out, time.perf_counter() - t0
+# The FP64 oracle is timed on the host's own cores: one process per core (spawned,
+# BLAS limited to one thread each), events handed out one at a time in batch order.
+
+_W = None
 
 
-def blas_threads():
+def _oracle_init(cfg, wseed):
+    global _W
     try:
-        from threadpoolctl import threadpool_info
-        info = threadpool_info()
-        return max((i.get("num_threads", 1) for i in info), default=1)
+        from threadpoolctl import threadpool_limits
+        threadpool_limits(1)
     except Exception:
-        return os.cpu_count() or 1
+        pass
+    _W = (cfg, synth.make_weights(cfg, wseed))
+
+
+def _oracle_event(args):
+    """Worker: the oracle forward, decode and event sums of one event."""
+    import oracle
+    e, xs, window = args
+    cfg, W = _W
+    t0 = time.perf_counter()
+    if window > 0:
+        r = oracle.forward(W, cfg, xs, [0, len(xs)], window=window)
+        lo, reg, cls, sums = r.logits, r.reg, r.cls, r.sums[0]
+    else:
+        lo, raw = oracle.forward_event(W, cfg, xs)
+        cls, reg = oracle.decode(xs, lo, raw)
+        sums = oracle.event_sums(cls, reg, [0, len(xs)])[0]
+    return e, time.perf_counter() - t0, lo, reg, cls, sums
+
+
+def cpu_model():
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def oracle_pool(cfg, wseed, procs):
+    """Spawned worker pool for the oracle (safe to create after CUDA is up)."""
+    import multiprocessing as mp
+    return mp.get_context("spawn").Pool(procs, initializer=_oracle_init, initargs=(cfg, wseed))
+
+
+def oracle_run(pool, procs, x, cu, events, budget_s, window=0):
+    """Run the oracle over `events` (in order) on the pool until `budget_s` of wall time
+    has passed (events already started finish).  Returns (results sorted by event,
+    wall seconds)."""
+    t0 = time.perf_counter()
+    pending, out, nxt = [], [], 0
+    while pending or nxt < len(events):
+        while nxt < len(events) and len(pending) < 2 * procs and (nxt == 0 or time.perf_counter() - t0 < budget_s):
+            e = events[nxt]
+            pending.append(pool.apply_async(_oracle_event, ((e, x[cu[e]:cu[e + 1]], window),)))
+            nxt += 1
+        if nxt > 0 and time.perf_counter() - t0 >= budget_s:
+            nxt = len(events)
+        if pending:
+            pending[0].wait()
+            done = [p for p in pending if p.ready()]
+            pending = [p for p in pending if not p.ready()]
+            out += [p.get() for p in done]
+    return sorted(out, key=lambda r: r[0]), time.perf_counter() - t0
+
+
+def oracle_baseline(cfg, wseed, x, cu, sizes, budget_s, window=0, pool=None):
+    """The oracle on all host cores over a bounded sample of the batch (events in batch
+    order, i.i.d. sizes), extrapolated to the whole batch by sum N^2; then a one-core
+    run of the next 8 events (one at a time on an otherwise idle pool), extrapolated
+    the same way; and the per-event single-core latency distribution."""
+    procs = os.cpu_count() or 1
+    own = pool is None
+    if own:
+        pool = oracle_pool(cfg, wseed, procs)
+    res, wall = oracle_run(pool, procs, x, cu, list(range(len(sizes))), budget_s, window)
+    one = list(range(len(res), min(len(res) + 8, len(sizes)))) or list(range(min(8, len(sizes))))
+    one_res, one_wall = oracle_run(pool, 1, x, cu, one, 1e9, window)
+    if own:
+        pool.close()
+        pool.join()
+    n2 = np.asarray(sizes, np.float64) ** 2
+    n2_all = float(n2.sum())
+    n2_s = float(sum(n2[r[0]] for r in res))
+    n2_1 = float(sum(n2[r[0]] for r in one_res))
+    batch_s = wall * n2_all / n2_s
+    per_ev = np.array([r[1] * 1000.0 for r in one_res])
+    return res, {
+        "value": len(sizes) / batch_s, "unit": "events/s", "cores": procs, "kind": "oracle",
+        "sample": f"first {len(res)} events of the batch (i.i.d. sizes) on {procs} worker processes "
+                  f"(one BLAS thread each) in {wall:.1f} s wall, extrapolated to the {len(sizes)}-event "
+                  f"batch by sum N^2 (the sample is {n2_s / n2_all:.3f} of it)",
+        "cpu_model": cpu_model(), "nproc": procs,
+        "one_core": {"value": len(sizes) / (one_wall * n2_all / n2_1), "unit": "events/s",
+                     "sample": f"events {one[0]}..{one[-1]} one after another on one core "
+                               f"({one_wall:.1f} s), extrapolated to the batch by sum N^2"},
+        "p50_ms_per_event": float(np.percentile(per_ev, 50)),
+        "p99_ms_per_event": float(np.percentile(per_ev, 99)),
+        "latency_note": "per-event oracle time of the one-core run (events alone on an idle host)"}
 
 
 def run_reference(args):
     ws, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
     if rank != 0:
         return
-    import oracle
     cfg, wseed, x, cu, sizes = workload_inputs(0)
-    W = synth.make_weights(cfg, wseed)
+    procs = os.cpu_count() or 1
+    pool = oracle_pool(cfg, wseed, procs)
     n = len(sizes)
+    # each step: the next `procs` events of the batch, one per core, in batch order
     ev = 0
+
+    def step():
+        nonlocal ev
+        evs = [(ev + i) % n for i in range(procs)]
+        ev += procs
+        res, _ = oracle_run(pool, procs, x, cu, evs, 1e9)
+        return len(res)
+
     for _ in range(args.warmup):
-        oracle.forward_event(W, cfg, x[cu[ev % n]:cu[ev % n + 1]])
-        ev += 1
+        step()
     t0 = time.perf_counter()
-    n_done = 0
-    for _ in range(args.steps):
-        e = ev % n
-        xs = x[cu[e]:cu[e + 1]]
-        lo, raw = oracle.forward_event(W, cfg, xs)
-        cls, reg = oracle.decode(xs, lo, raw)
-        oracle.event_sums(cls, reg, [0, len(xs)])
-        ev += 1
-        n_done += 1
+    n_done = sum(step() for _ in range(args.steps))
     dt = time.perf_counter() - t0
+    pool.close()
+    pool.join()
     v = n_done / dt
-    cores = blas_threads()
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "events/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{WORKLOAD}: {WORKLOAD_DESC}",
-                       "sample": "one event of the batch per step, in generation order"},
-            "cpu_baseline": {"value": v, "unit": "events/s", "cores": cores, "kind": "oracle",
-                             "sample": f"{n_done} events of the 512-event batch, one per step"},
+            "config": workload_config(x, sizes, 1),
+            "cpu_baseline": {"value": v, "unit": "events/s", "cores": procs, "kind": "oracle",
+                             "cpu_model": cpu_model(), "nproc": procs,
+                             "sample": f"each step: {procs} consecutive events of the 512-event batch, "
+                                       f"one per worker process (one BLAS thread each); "
+                                       f"{n_done} events timed"},
             "e2e": {"value": v, "unit": "events/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
+def workload_config(x, sizes, ws):
+    """The `config` object of the JSON line (the same for both arms)."""
+    return {"workload": f"{WORKLOAD}: {WORKLOAD_DESC}" +
+            ("" if len(sizes) == 512 else f" (first {len(sizes)} events only)"),
+            "events_per_gpu": int(len(sizes)), "elements_per_gpu": int(np.sum(sizes)),
+            "l2": "inputs larger than L2 (x is %.0f MB > 126 MB)" % (x.nbytes / 1e6),
+            "parallelism": f"replicas x{ws} (events shard, no collective)"}
+
+
 # ------------------------------------------------------------------------ ours
 def run_ours(args):
+    ws, rank, local = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
+    pool = None
+    if not args.no_baselines and rank == 0:
+        # the oracle's worker pool, started before the first GPU call
+        cfg0, wseed0, _, _ = synth.workload(WORKLOAD)[:4]
+        pool = oracle_pool(cfg0, wseed0, os.cpu_count() or 1)
     import torch
     from paper_2601_17554_b300 import Model, _lib
 
@@ -400,8 +491,8 @@ def run_ours(args):
     if att_ms:
         ach = exps / (att_ms / 1000.0)
         exp_peak = unit_rates["ex2_per_s"]
-        kname = {7: "k_attention_warp", 8: "k_attention_warp", 9: "k_attention_warp (64-row items)",
-                 4: "k_attention32", 6: "k_attention32"}.get(attn_variant, "k_attention")
+        kname = {3: "k_attention_warp", 4: "k_attention_warp",
+                 5: "k_attention_warp (64-row items)"}.get(attn_variant, "k_attention_tm")
         roof = {"kernel": kname, "attn_variant": attn_variant, "bound": "alu", "achieved": ach / 1e9,
                 "peak": exp_peak / 1e9, "unit": "Gexp/s", "frac": ach / exp_peak,
                 "traffic": attention_traffic(attn_variant, prec),
@@ -434,11 +525,8 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": prec, "data": "synthetic",
-            "config": {"workload": f"{WORKLOAD}: {WORKLOAD_DESC}" +
-                       ("" if n_ev == 512 else f" (first {n_ev} events only)"), "events_per_gpu": n_ev,
-                       "elements_per_gpu": T, "precision": prec, "attn_variant": attn_variant,
-                       "l2": "inputs larger than L2 (x is %.0f MB > 126 MB)" % (x.nbytes / 1e6),
-                       "parallelism": f"replicas x{ws} (events shard, no collective)"},
+            "config": workload_config(x, sizes, ws),
+            "attn_variant": attn_variant,
             "batch_ms_per_event": ms_step / n_ev,
             "gpu_launches": int(launches_per_step * args.steps),
             "kernel_ms": kernel_avg,
@@ -492,24 +580,27 @@ def run_ours(args):
         model.set_option(_lib.OPT_ATTN_WINDOW, args.attn_window)
 
     if not args.no_baselines and rank == 0:
-        # ---- per-event latency: each event alone, one launch sequence per event
-        model.set_option(_lib.OPT_USE_GRAPHS, 0)
+        # ---- per-event latency: each event alone, as its own captured graph (the first
+        # call captures it, the timed second call replays it)
         model.set_option(_lib.OPT_PROFILE, 0)
         lat = []
         ev_s, ev_e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        cs_all = [torch.tensor([0, int(sizes[e])], dtype=torch.int32, device=dev) for e in range(n_ev)]
         for e in range(n_ev):
-            xs = xd[cu[e]:cu[e + 1]]
-            cs = torch.tensor([0, int(sizes[e])], dtype=torch.int32, device=dev)
-            if e == 0:
-                model.forward(xs, cs, int(sizes[e]), precision=prec)
+            args_e = (xd[cu[e]:cu[e + 1]], cs_all[e], int(sizes[e]))
+            kw = dict(precision=prec, logits=lo[cu[e]:cu[e + 1]], reg=rg[cu[e]:cu[e + 1]],
+                      cls=cl[cu[e]:cu[e + 1]], event_sums=su[e:e + 1])
+            model.forward(*args_e, **kw)
             ev_s.record(stream)
-            model.forward(xs, cs, int(sizes[e]), precision=prec)
+            model.forward(*args_e, **kw)
             ev_e.record(stream)
             ev_e.synchronize()
             lat.append(ev_s.elapsed_time(ev_e))
         line["p50_ms_per_event"] = float(np.percentile(lat, 50))
         line["p99_ms_per_event"] = float(np.percentile(lat, 99))
-        line["latency_note"] = "each event run alone (no graph), CUDA events on the stream"
+        line["latency_note"] = ("each event alone as a single-event CUDA graph (captured once, the "
+                                "replay timed with CUDA events on the stream)")
+        model.set_option(_lib.OPT_USE_GRAPHS, 0)
         # ---- plain FP32 baseline: the same batch as 512 separate FP32 launch sequences
         model.forward(xd[:int(sizes[0])], torch.tensor([0, int(sizes[0])], dtype=torch.int32,
                                                          device=dev), int(sizes[0]), precision="fp32")
@@ -535,12 +626,11 @@ def run_ours(args):
         step()
         model.sync()
         glo, grg, gcl, gsu = lo.cpu().numpy(), rg.cpu().numpy(), cl.cpu().numpy(), su.cpu().numpy()
-        samp, cpu_s = oracle_sample(cfg, W, x, cu, args.cpu_seconds, window=args.attn_window)
+        samp, cpu_line = oracle_baseline(cfg, wseed, x, cu, sizes, args.cpu_seconds, window=args.attn_window,
+                                         pool=pool)
+        samp = [(r[0], r[2], r[3], r[4], r[5]) for r in samp]
         nsamp = len(samp)
-        line["cpu_baseline"] = {"value": nsamp / cpu_s, "unit": "events/s", "cores": blas_threads(),
-                                "kind": "oracle",
-                                "sample": f"first {nsamp} events of the batch (i.i.d. sizes), "
-                                          f"{cpu_s:.1f} s, numpy float64 with BLAS matmuls"}
+        line["cpu_baseline"] = cpu_line
         import oracle
         agree, num, den, raw_err, same_cls_err, margins = [], 0.0, 0.0, [], [], []
         for e, olo, oreg, ocls, osum in samp:
@@ -566,6 +656,9 @@ def run_ours(args):
             "event_sum_rel_err_max_same_classes": float(max(same_cls_err)),
             "note": "event sums relative to max |component|; 'same_classes' sums the oracle's "
                     "regressions over the GPU's selected elements"}
+    if pool is not None:
+        pool.close()
+        pool.join()
     if rank == 0:
         print(json.dumps(line), flush=True)
     model.close()

@@ -43,9 +43,14 @@ typedef enum {
 
 typedef enum {
     MLPF_FP32 = 0, /* plain path: SIMT FP32 FFMA GEMMs and attention, no TF32 */
-    MLPF_BF16 = 1, /* tcgen05 tensor cores, BF16 operands, FP32 accumulation */
+    MLPF_BF16 = 1, /* tcgen05 tensor cores: attention in BF16 (Q, K, V, P and the QK^T / PV
+                      products), FP16 operands in the embedding, projection, FFN and head
+                      GEMMs; FP32 accumulation, softmax statistics, LayerNorm moments and
+                      residual stream.  The per-stage rounding budget of the forward puts
+                      the 16-bit error into the GEMM operands, not into the attention
+                      products: BF16 GEMM operands cost the 99.9 % argmax bound */
     MLPF_FP8 = 2,  /* E4M3 GEMMs with per-tensor scales, FP16 attention (needs mlpf_calibrate_fp8) */
-    MLPF_FP16 = 3  /* as MLPF_BF16 with FP16 operands (same tensor-core rate, 3 more mantissa bits) */
+    MLPF_FP16 = 3  /* FP16 everywhere on the tensor-core path (attention included) */
 } mlpf_precision;
 
 /* Model configuration, as stored in the weight blob header. */
@@ -156,8 +161,11 @@ mlpf_status mlpf_forward_host(mlpf_model* m, int32_t precision,
  * a message).  No CUDA graph is used and nothing is allocated: not the
  * workspace, not profiling events.
  * The first call on a device resolves the array's device address
- * (cudaGetSymbolAddress) and encodes its tensor maps; make that first call
- * before any stream capture.  Every call on a device shares the one array and
+ * (cudaGetSymbolAddress) and encodes its tensor maps.  Under CUDA's lazy module
+ * loading (the default) that first call may also load the library's module on
+ * the device and so reserve the array there: it is the one call that can take
+ * device memory, so make it before any memory-budgeted loop and before any
+ * stream capture.  Later calls allocate nothing and leave the model unchanged.  Every call on a device shares the one array and
  * overwrites it: calls that overlap on the GPU (several streams, models or host
  * threads at once) race; serialise them.  Asynchronous on `stream`; device-side
  * status via mlpf_sync.
@@ -228,6 +236,16 @@ mlpf_status mlpf_cluster_jets(mlpf_model* m, const float* reg, const int32_t* cl
  * pointer (host) may be NULL.  Allocates and frees its own scratch; synchronous.
  */
 mlpf_status mlpf_measure_unit_rates(int32_t device, double* ex2_per_s, double* ffma_per_s);
+
+/*
+ * The packed BF16 exponential rate of device `device` (ex2.approx.ftz.bf16x2, two
+ * results per instruction), measured the same way: *results_per_s (host) receives
+ * exponentials per second.  The denominator of the attention roofline for kernels
+ * whose softmax numerators use packed 16-bit exponentials (the tensor-memory
+ * attention kernel in BF16 and FP16).  Synchronous; allocates a small scratch.
+ * Errors: MLPF_E_INVALID (NULL output), MLPF_E_CUDA, MLPF_E_OOM.
+ */
+mlpf_status mlpf_measure_ex2_packed_rate(int32_t device, double* results_per_s);
 
 /*
  * Names (cap x 32 bytes, or NULL) and activation scales (cap floats, or NULL)
@@ -332,17 +350,14 @@ enum {
                                        inside captured graphs); see mlpf_profile_get */
     MLPF_OPT_ATTN_VARIANT_BF16 = 7, /* attention kernel variant of a precision,
                                        0..MLPF_ATTN_VARIANTS-1 (set by mlpf_autotune):
-                                       tcgen05, 64-key score tiles, one head per warpgroup:
-                                         0 = 4 K/V stages, 1 = 2, 5 = 6;
-                                       tcgen05, 64-key tiles, two heads per warpgroup:
-                                         2 = 4 stages, 3 = 2 stages;
-                                       tcgen05, 32-key score tiles, four TMEM buffers per
-                                       head, PV partial folded one tile late:
-                                         4 = 4 stages, 6 = 6 stages;
+                                       tcgen05 with S and P in tensor memory (P the
+                                       tensor-memory operand of the PV product), one
+                                       warpgroup per head, an MMA warp:
+                                         0 = 4 K/V stages, 1 = 6, 2 = 8;
                                        warp-level MMAs, each warp 32 rows of one head:
-                                         7 = 4 stages, 8 = 8 stages (default);
+                                         3 = 4 stages, 4 = 8 stages (default);
                                        the same on 64-row half items, two CTAs per SM,
-                                       4 stages: 9 */
+                                       4 stages: 5 */
     MLPF_OPT_ATTN_VARIANT_FP16 = 8,
     MLPF_OPT_ATTN_VARIANT_FP8 = 9,
     MLPF_OPT_ATTN_WINDOW = 10,      /* 0 (default): full attention within each event.
@@ -351,9 +366,8 @@ enum {
                                        ordered by eta (x[:, 10], ties by position), and
                                        query block b of 128 elements attends to key blocks
                                        b - w .. b + w only; outputs are returned in the
-                                       input order.  Runs on MLPF_FP32 and on the
-                                       warp-level attention kernels (variants 7-9; a
-                                       tcgen05 variant falls back to 8).  Events of at
+                                       input order.  Runs on MLPF_FP32 and on every
+                                       tensor-core attention variant.  Events of at
                                        most 16384 elements (else MLPF_E_UNSUPPORTED);
                                        not available in mlpf_forward_noalloc. */
     MLPF_OPT_GATE_CONFIDENCE = 11,  /* student models in mlpf_forward_gated: event
@@ -372,7 +386,7 @@ enum {
                                        a chunk's last attention items overlap the next
                                        chunk's kernels.  The results do not depend on it. */
 };
-#define MLPF_ATTN_VARIANTS 10
+#define MLPF_ATTN_VARIANTS 6
 mlpf_status mlpf_set_option(mlpf_model* m, int32_t option, int64_t value);
 mlpf_status mlpf_get_option(const mlpf_model* m, int32_t option, int64_t* value);
 

@@ -23,11 +23,14 @@ def _ptr(t):
 
 
 def measure_unit_rates(device: int = 0) -> dict:
-    """Measured MUFU exp2 and FP32 FMA rates (results per second) of a device."""
+    """Measured MUFU exp2 (FP32 and packed BF16) and FP32 FMA rates (results per
+    second) of a device."""
     L = _lib.load()
     ex2, ffma = ctypes.c_double(), ctypes.c_double()
     check(L.mlpf_measure_unit_rates(device, ctypes.byref(ex2), ctypes.byref(ffma)))
-    return {"ex2_per_s": ex2.value, "ffma_per_s": ffma.value}
+    packed = ctypes.c_double()
+    check(L.mlpf_measure_ex2_packed_rate(device, ctypes.byref(packed)))
+    return {"ex2_per_s": ex2.value, "ffma_per_s": ffma.value, "ex2_bf16x2_per_s": packed.value}
 
 
 class Model:

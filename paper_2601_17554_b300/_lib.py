@@ -22,7 +22,7 @@ EXPORTS = ("mlpf_load_weights", "mlpf_free", "mlpf_get_config", "mlpf_forward",
            "mlpf_trainer_free", "mlpf_trainer_num_params", "mlpf_trainer_step",
            "mlpf_trainer_step_supervised", "mlpf_trainer_export", "mlpf_sync", "mlpf_set_option", "mlpf_get_option",
            "mlpf_last_launch_count", "mlpf_profile_get", "mlpf_last_error", "mlpf_abi_version",
-           "mlpf_cluster_jets")
+           "mlpf_cluster_jets", "mlpf_measure_ex2_packed_rate")
 
 
 class MlpfConfig(ctypes.Structure):
@@ -63,6 +63,8 @@ def load(build_if_missing: bool = True):
     L.mlpf_measure_unit_rates.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_double)]
     L.mlpf_measure_unit_rates.restype = ctypes.c_int
+    L.mlpf_measure_ex2_packed_rate.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]
+    L.mlpf_measure_ex2_packed_rate.restype = ctypes.c_int
     L.mlpf_cluster_jets.argtypes = [vp, vp, vp, vp, i32, i32, ctypes.c_float, vp, vp, vp, vp]
     L.mlpf_cluster_jets.restype = ctypes.c_int
     L.mlpf_eval_activation.argtypes = [i32, i32, vp, vp, i32, vp]

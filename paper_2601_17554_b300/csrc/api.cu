@@ -444,7 +444,7 @@ mlpf_status mlpf_eval_activation(int32_t impl, int32_t act, const float* x, floa
     return MLPF_OK;
 }
 
-int32_t mlpf_abi_version(void) { return 103; }
+int32_t mlpf_abi_version(void) { return 104; }
 
 const char* mlpf_last_error(void) { return g_last_error.c_str(); }
 
@@ -747,7 +747,7 @@ mlpf_status mlpf_autotune(mlpf_model* mm, int32_t precision, const float* x, con
     while (bucket < total) bucket <<= 1;
     const std::string key = "sm" + std::to_string(prop.major) + std::to_string(prop.minor) + "_" +
                             std::to_string(prop.multiProcessorCount) + "_d" + std::to_string(m.cfg.d) + "_prec" +
-                            std::to_string(precision) + "_T" + std::to_string(bucket);
+                            std::to_string(precision) + "_T" + std::to_string(bucket) + "_v" + std::to_string(MLPF_ATTN_VARIANTS);
     const int f = fmt_of(precision);
     // cache: one "key variant ms" line per tuned case
     if (cache_path) {
@@ -889,7 +889,7 @@ mlpf_status mlpf_get_option(const mlpf_model* mm, int32_t option, int64_t* value
         case MLPF_OPT_DEBUG_STALL: *value = m.debug_stall; return MLPF_OK;
         case MLPF_OPT_ATTN_CTAS_PER_SM: *value = m.attn_ctas_per_sm; return MLPF_OK;
         case MLPF_OPT_ATTN_KV_STAGES: {
-            static const int stages[MLPF_ATTN_VARIANTS] = {4, 2, 4, 2, 4, 6, 6, 4, 8, 4};
+            static const int stages[MLPF_ATTN_VARIANTS] = {4, 6, 8, 4, 8, 4};
             *value = stages[m.attn_variant[0]];
             return MLPF_OK;
         }

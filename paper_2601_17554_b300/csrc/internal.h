@@ -34,9 +34,8 @@ struct DeviceWeights {
     float* f32_base = nullptr;
     // FP32 path: concatenated QKV per layer, [3d, d] and [3d]
     std::vector<float*> wqkv_pid, bqkv_pid, wqkv_reg, bqkv_reg;
-    // tensor-core path (d = 64 model only): bf16 128B-swizzled weight images
+    // tensor-core path (d = 64 model only): 128B-swizzled weight images
     uint8_t* img_base = nullptr;
-    std::map<std::string, uint8_t*> img;    // name -> device pointer of the BF16 image
     std::map<std::string, uint8_t*> img_h;  // name -> device pointer of the FP16 image
     std::map<std::string, uint32_t> img_bytes;
     float* tc_f32_base = nullptr;         // fused bias vectors for the tensor-core kernels
@@ -64,7 +63,7 @@ struct Workspace {
     float* kmax = nullptr;               // per 64-row block and head: largest K-row norm
     int4* items = nullptr;               // attention work items
     int* counters = nullptr;             // [0]=n_items [1]=tpad rows [2..3]=attn tickets
-    CUtensorMap map_q, map_q64, map_k, map_o, map_vt, map_hp;
+    CUtensorMap map_q, map_q64, map_k, map_o, map_vt, map_vt16, map_hp;   // map_vt16: 16-row V^T boxes
     // windowed attention: eta order of each event's elements (perm[r] = packed
     // row of the r-th element in that order), inputs and outputs in that order
     int32_t* perm = nullptr;
@@ -106,9 +105,9 @@ struct Model {
     int64_t wait_limit_ns = 2000000000LL;
     bool debug_stall = false;
     int attn_ctas_per_sm = 1;
-    // attention kernel variant per operand format (BF16, FP16, E4M3), numbered as
+    // attention kernel variant per precision mode (BF16, FP16, E4M3), numbered as
     // MLPF_OPT_ATTN_VARIANT_* in mlpf.h; default: warp-level MMAs, 8 K/V stages
-    int attn_variant[3] = {8, 8, 8};
+    int attn_variant[3] = {4, 4, 4};
     // windowed attention (0 = full): in eta order, query block b of 128 elements
     // attends to blocks b - attn_window .. b + attn_window
     int attn_window = 0;
@@ -163,8 +162,11 @@ void prof_end(Model& m, cudaStream_t st);
 // launch sequences (return number of kernels launched, or -1 on launch error)
 int64_t run_forward_f32(Model& m, const float* x, const int32_t* cu, int n_events, int total,
                         int max_n, float* logits, float* reg, cudaStream_t st);
+// ws: the workspace the kernels use (NULL: the model's own); profile: record the
+// per-kernel profiling events when the model's profiling option is on
 int64_t run_forward_tc(Model& m, int prec, const float* x, const int32_t* cu, int n_events,
-                       int total, int max_n, float* logits, float* reg, cudaStream_t st);
+                       int total, int max_n, float* logits, float* reg, cudaStream_t st,
+                       Workspace* ws = nullptr, bool profile = true);
 void f32_eval_activation(const float* x, float* y, int n, int act, cudaStream_t st);
 void tc_eval_activation(const float* x, float* y, int n, int act, cudaStream_t st);
 // eta order / gather / scatter of the windowed-attention path (k_f32.cu)
@@ -173,7 +175,7 @@ void scatter_outputs(const int32_t* perm, const float* los, const float* rgs, fl
                      int total, cudaStream_t st);
 int64_t run_event_sums(Model& m, const int32_t* cu, int n_events, const float* logits,
                        const float* reg, int32_t* cls, double* sums, int n_cls,
-                       cudaStream_t st);
+                       cudaStream_t st, bool profile = true);
 
 // plain FP32 kernels shared with the training code (act: -1 none, 0 GELU, 1 ReLU)
 void f32_linear(const float* X1, int ld1, int K1, const float* X2, int ld2, int K2, const float* W,

@@ -533,11 +533,11 @@ void scatter_outputs(const int32_t* perm, const float* los, const float* rgs, fl
 
 int64_t run_event_sums(Model& m, const int32_t* cu, int n_events, const float* logits,
                        const float* reg, int32_t* cls, double* sums, int n_cls,
-                       cudaStream_t st) {
+                       cudaStream_t st, bool profile) {
     if (n_events <= 0 || (!cls && !sums)) return 0;
-    prof_begin(m, st, "event_sums");
+    if (profile) prof_begin(m, st, "event_sums");
     k_event_sums<<<n_events, ES_THREADS, 0, st>>>(cu, n_events, logits, reg, cls, sums, n_cls, m.cfg.arch, m.status);
-    prof_end(m, st);
+    if (profile) prof_end(m, st);
     if (cudaPeekAtLastError() != cudaSuccess) return -1;
     return 1;
 }

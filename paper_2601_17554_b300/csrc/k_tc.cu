@@ -103,12 +103,24 @@ MLPF_DEV void act_n(float* v, int act) {
 // 64 16-bit or 128 E4M3 K-elements; one K-step is 32 bytes in every format
 // (16 elements of kind::f16, 32 of kind::f8f6f4).  A K=64 operand in E4M3 uses
 // the first half of an atom (chunks 0..3); the rest stays zero.
+// Precision modes (the FMT template parameter of the kernels):
+//   FMT_BF16  attention in BF16 (Q, K, V^T, P; QK^T and PV on BF16 tensor cores),
+//             every GEMM of the embedding, projections, FFNs and heads on FP16
+//             operands: the per-stage rounding budget of the forward puts almost all
+//             of the 16-bit error into the GEMM operands, almost none into the
+//             attention products
+//   FMT_FP16  FP16 everywhere
+//   FMT_E4M3  E4M3 projection and FFN GEMMs (per-tensor scales), FP16 elsewhere
+// The attention output O and h_pid are FP16 in every mode (GEMM A operands).
 enum : int { FMT_BF16 = 0, FMT_FP16 = 1, FMT_E4M3 = 2 };
 template <int FMT>
 constexpr bool kIs8 = FMT == FMT_E4M3;
-// 16-bit format of Q, K, V^T, O and h_pid (attention inputs/outputs): FP16 unless BF16
+// format of Q, K, V^T and P (attention operands): FP16 unless BF16
 template <int FMT>
 constexpr bool kOutF16 = FMT != FMT_BF16;
+// operand format of the projection and FFN GEMMs
+template <int FMT>
+constexpr int kGemm = FMT == FMT_BF16 ? FMT_FP16 : FMT;
 // K-elements per 128-byte atom
 template <int FMT>
 constexpr int kAtomK = kIs8<FMT> ? 128 : 64;
@@ -537,12 +549,13 @@ __global__ void __launch_bounds__(EM_THREADS, 1) k_embed_qkv(const __grid_consta
                                                              EmbedParams p) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sm = align1024(smem_raw);
-    constexpr int FE = kIs8<FMT> ? FMT_FP16 : FMT;
+    constexpr int FE = FMT_FP16;      // embedding FFN operands (16-bit in every mode)
+    constexpr int G = kGemm<FMT>;     // QKV projection operands
     constexpr int KA = MODE == 0 ? 1 : 2;  // atoms of the first GEMM's A operand
     constexpr uint32_t W1B = 64 * 128 * KA, W2B = 64 * 128, WQB = 192 * 128;
     constexpr uint32_t TEAM_B = KA * ATOM + ATOM + 2 * 2 * 128 * 4;   // per team: sA, sH, LN sums
     constexpr bool TMA_HP = MODE == 1;
-    constexpr bool F16 = kOutF16<FMT>;
+    constexpr bool F16 = kOutF16<FMT>;   // Q, K, V^T format
     const int tid = threadIdx.x;
     const int team = tid >> 8, wg = (tid >> 7) & 1, r = tid & 127;
     const bool leader = (tid & 255) == 0;
@@ -681,10 +694,10 @@ __global__ void __launch_bounds__(EM_THREADS, 1) k_embed_qkv(const __grid_consta
                 for (int c = 0; c < 4; ++c) {
                     const uint4 u = src[c];
                     float a, b;
-                    unpack2<F16>(u.x, a, b); amx = fmaxf(amx, fmaxf(fabsf(a), fabsf(b)));
-                    unpack2<F16>(u.y, a, b); amx = fmaxf(amx, fmaxf(fabsf(a), fabsf(b)));
-                    unpack2<F16>(u.z, a, b); amx = fmaxf(amx, fmaxf(fabsf(a), fabsf(b)));
-                    unpack2<F16>(u.w, a, b); amx = fmaxf(amx, fmaxf(fabsf(a), fabsf(b)));
+                    unpack2<true>(u.x, a, b); amx = fmaxf(amx, fmaxf(fabsf(a), fabsf(b)));
+                    unpack2<true>(u.y, a, b); amx = fmaxf(amx, fmaxf(fabsf(a), fabsf(b)));
+                    unpack2<true>(u.z, a, b); amx = fmaxf(amx, fmaxf(fabsf(a), fabsf(b)));
+                    unpack2<true>(u.w, a, b); amx = fmaxf(amx, fmaxf(fabsf(a), fabsf(b)));
                 }
             }
             record_amax(p.amax, p.slot[0], &amx, 1, ri.valid);
@@ -715,10 +728,10 @@ __global__ void __launch_bounds__(EM_THREADS, 1) k_embed_qkv(const __grid_consta
         }
         layernorm_split(v, v, pv + 128, pv + 192, wg, r, team, red);
         if (p.amax) record_amax(p.amax, p.slot[2], v, 32, ri.valid);
-        st_op<FMT>(sH, r, v, 32, 32 * wg, p.qs[2], true);
+        st_op<G>(sH, r, v, 32, 32 * wg, p.qs[2], true);
         // fused Q/K/V projection: warpgroup 0 stores Q and V^T columns 0-31,
         // warpgroup 1 stores K and V^T columns 32-63
-        if (!run_mma([&] { issue_gemm<FMT>(tbase, sH, sWq, 192, 1); })) break;
+        if (!run_mma([&] { issue_gemm<G>(tbase, sH, sWq, 192, 1); })) break;
         {
             const float ds = p.ds[2], dsqk = wg == 0 ? ds * kQScale : ds;
             float u[32], ss[4];
@@ -773,11 +786,12 @@ __global__ void __launch_bounds__(PT_THREADS, 1) k_post(const __grid_constant__ 
                                                         PostParams p) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sm = align1024(smem_raw);
-    // FMT: out-projection, FFN and QKV GEMMs; FH: output heads (FP16 when FMT is E4M3)
-    constexpr int FH = kIs8<FMT> ? FMT_FP16 : FMT;
-    constexpr bool F16 = kOutF16<FMT>;           // 16-bit format of O, Q, K, V^T, h_pid
-    constexpr int HA = kIs8<FMT> ? 1 : 2;        // atoms of a 128-column FFN hidden operand
-    constexpr int KA256 = 256 / kAtomK<FMT>;     // atoms of the 256-column FFN-down operand
+    // G: out-projection, FFN and QKV GEMMs; FH: output heads (FP16 in every mode)
+    constexpr int G = kGemm<FMT>;
+    constexpr int FH = FMT_FP16;
+    constexpr bool F16 = kOutF16<FMT>;           // format of Q, K, V^T (O and h_pid: FP16)
+    constexpr int HA = kIs8<G> ? 1 : 2;          // atoms of a 128-column FFN hidden operand
+    constexpr int KA256 = 256 / kAtomK<G>;       // atoms of the 256-column FFN-down operand
     constexpr uint32_t WOB = 64 * 128, WUB = 256 * 128, WDB = KA256 * 64 * 128;
     constexpr uint32_t WAB = MODE == 0 ? 192 * 128 : (MODE == 1 ? 64 * 128 : 256 * 128);
     constexpr uint32_t WBB = MODE == 0 ? 0 : (MODE == 1 ? 16 * 128 : 4 * 16 * 128);
@@ -797,7 +811,7 @@ __global__ void __launch_bounds__(PT_THREADS, 1) k_post(const __grid_constant__ 
     const bool leader = (tid & 255) == 0;
     uint8_t* sA = sTeam0 + team * PT_TEAM_BYTES;
     uint8_t* sH = sA + ATOM;
-    uint8_t* sO16 = kIs8<FMT> ? sA + 2 * ATOM : sA;  // where the attention output lands
+    uint8_t* sO16 = kIs8<G> ? sA + 2 * ATOM : sA;  // where the attention output lands
     uint64_t* tma_bar = &bars[1 + 2 * team];
     uint64_t* mma_bar = &bars[2 + 2 * team];
     float* red = red_all + team * PT_RED_FLOATS;
@@ -886,21 +900,21 @@ __global__ void __launch_bounds__(PT_THREADS, 1) k_post(const __grid_constant__ 
         }
         fail |= !mbar_wait(tma_bar, aph, ab, p.status, ST_TIMEOUT_GEMM, p.wait_ns);
         aph ^= 1;
-        if (kIs8<FMT> || p.amax) {
+        if (kIs8<G> || p.amax) {
             // this warpgroup's 32 columns of the attention output (16-bit swizzled tile)
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 const uint4 u = *(const uint4*)(sO16 + sw128_off(r, 4 * wg + c));
-                unpack2<F16>(u.x, v[8 * c], v[8 * c + 1]);
-                unpack2<F16>(u.y, v[8 * c + 2], v[8 * c + 3]);
-                unpack2<F16>(u.z, v[8 * c + 4], v[8 * c + 5]);
-                unpack2<F16>(u.w, v[8 * c + 6], v[8 * c + 7]);
+                unpack2<true>(u.x, v[8 * c], v[8 * c + 1]);
+                unpack2<true>(u.y, v[8 * c + 2], v[8 * c + 3]);
+                unpack2<true>(u.z, v[8 * c + 4], v[8 * c + 5]);
+                unpack2<true>(u.w, v[8 * c + 6], v[8 * c + 7]);
             }
             if (p.amax) record_amax(p.amax, p.slot[0], v, 32, ri.valid);
-            if constexpr (kIs8<FMT>) st_op<FMT>(sA, r, v, 32, 32 * wg, p.qs[0], true);
+            if constexpr (kIs8<G>) st_op<G>(sA, r, v, 32, 32 * wg, p.qs[0], true);
         }
         // out-projection + residual, LN2
-        if (!run_mma([&] { issue_gemm<FMT>(tbase, sA, sWo, 64, 1); })) break;
+        if (!run_mma([&] { issue_gemm<G>(tbase, sA, sWo, 64, 1); })) break;
         tmem_ld32(trow + 32 * wg, v);
         tmem_wait_ld();
 #pragma unroll
@@ -909,12 +923,12 @@ __global__ void __launch_bounds__(PT_THREADS, 1) k_post(const __grid_constant__ 
         if (MODE == 2 && wg == 0 && ri.valid) prefetch_l2(p.x + (size_t)ri.prow * 42 + 8);
         layernorm_split(zr, v, pv + PV_LN2G, pv + PV_LN2B, wg, r, team, red);
         if (p.amax) record_amax(p.amax, p.slot[1], v, 32, ri.valid);
-        st_op<FMT>(sA, r, v, 32, 32 * wg, p.qs[1], true);
+        st_op<G>(sA, r, v, 32, 32 * wg, p.qs[1], true);
         // FFN: two halves of 128 hidden columns, GELU, down-projection accumulated
         bool stop = false;
 #pragma unroll 1
         for (int half = 0; half < 2 && !stop; ++half) {
-            if (!run_mma([&] { issue_gemm<FMT>(tbase, sA, sWu + half * 128 * 128, 128, 1); })) { stop = true; break; }
+            if (!run_mma([&] { issue_gemm<G>(tbase, sA, sWu + half * 128 * 128, 128, 1); })) { stop = true; break; }
 #pragma unroll
             for (int q2 = 0; q2 < 2; ++q2) {
                 tmem_ld32(trow + 64 * wg + 32 * q2, v);
@@ -924,9 +938,9 @@ __global__ void __launch_bounds__(PT_THREADS, 1) k_post(const __grid_constant__ 
                     v[i] = fmaf(v[i], p.ds[1], pv[PV_BUP + 128 * half + 64 * wg + 32 * q2 + i]);
                 act_n<32>(v, p.act);
                 if (p.amax) record_amax(p.amax, p.slot[2], v, 32, ri.valid);
-                st_op<FMT>(sH, r, v, 32, 64 * wg + 32 * q2, p.qs[2]);
+                st_op<G>(sH, r, v, 32, 64 * wg + 32 * q2, p.qs[2]);
             }
-            if (!run_mma([&] { issue_gemm<FMT>(tbase + 128, sH, sWd + half * HA * 64 * 128, 64, HA, half > 0); })) {
+            if (!run_mma([&] { issue_gemm<G>(tbase + 128, sH, sWd + half * HA * 64 * 128, 64, HA, half > 0); })) {
                 stop = true;
                 break;
             }
@@ -942,8 +956,8 @@ __global__ void __launch_bounds__(PT_THREADS, 1) k_post(const __grid_constant__ 
             for (int i = 0; i < 8; ++i) zd[i] = make_float4(zr[4 * i], zr[4 * i + 1], zr[4 * i + 2], zr[4 * i + 3]);
             layernorm_split(zr, v, pv + PV_LNG, pv + PV_LNB, wg, r, team, red);
             if (p.amax) record_amax(p.amax, p.slot[3], v, 32, ri.valid);
-            st_op<FMT>(sA, r, v, 32, 32 * wg, p.qs[3], true);
-            if (!run_mma([&] { issue_gemm<FMT>(tbase, sA, sWa, 192, 1); })) break;
+            st_op<G>(sA, r, v, 32, 32 * wg, p.qs[3], true);
+            if (!run_mma([&] { issue_gemm<G>(tbase, sA, sWa, 192, 1); })) break;
             // wg 0: Q and V channels 0..31; wg 1: K and V channels 32..63
             uint16_t* qk = (wg == 0 ? p.q : p.k) + (size_t)pp * D;
             const float dsqk = wg == 0 ? p.ds[3] * kQScale : p.ds[3];
@@ -979,8 +993,8 @@ __global__ void __launch_bounds__(PT_THREADS, 1) k_post(const __grid_constant__ 
                 uint4* d4 = (uint4*)(p.hp + (size_t)pp * D + 32 * wg);
 #pragma unroll
                 for (int c = 0; c < 4; ++c)
-                    d4[c] = make_uint4(pack2<F16>(v[8 * c], v[8 * c + 1]), pack2<F16>(v[8 * c + 2], v[8 * c + 3]),
-                                       pack2<F16>(v[8 * c + 4], v[8 * c + 5]), pack2<F16>(v[8 * c + 6], v[8 * c + 7]));
+                    d4[c] = make_uint4(pack_f16x2(v[8 * c], v[8 * c + 1]), pack_f16x2(v[8 * c + 2], v[8 * c + 3]),
+                                       pack_f16x2(v[8 * c + 4], v[8 * c + 5]), pack_f16x2(v[8 * c + 6], v[8 * c + 7]));
             }
             if (p.amax) record_amax(p.amax, p.slot[3], v, 32, ri.valid);
             st_op<FH>(sA, r, v, 32, 32 * wg, 1.f);
@@ -1058,36 +1072,15 @@ __global__ void __launch_bounds__(PT_THREADS, 1) k_post(const __grid_constant__ 
 }
 
 // ------------------------------------------------------------- attention
-// Persistent varlen self-attention (Sec. 5.3, Eq. 4): one CTA per SM, a TMA
-// producer warp and one warpgroup per head.  Work items are (event, 128-query
-// tile); keys come in 64-row tiles of the same event (events start at 64-row
-// boundaries of the padded layout, so a key tile never mixes events).  Per key
-// tile and head: S = Q_h K_h^T on tcgen05 into a TMEM buffer (two per head),
-// FP32 online softmax by the thread owning each query row, P (16-bit) into a
-// swizzled shared-memory tile, then P V_h and P 1 (the row sum of the rounded
-// P) on tcgen05 into the same TMEM buffer, accumulated into registers with the
-// running rescale.  Warps signal through mbarriers only, and every wait is
-// bounded.
-// Attention variants (chosen by the autotuner): HPW heads per consumer warpgroup
-// (NH / HPW warpgroups) and a K/V pipeline of ST stages.
+// Varlen self-attention (Sec. 5.3, Eq. 4) within each event of the packed batch.
+// Work items are (event, 128-query tile), longest events first; keys come in
+// 64-row tiles of the same event (events start at 64-row boundaries of the padded
+// layout, so a key tile never mixes events; padding keys are masked).  Two kernel
+// families, chosen per batch by the autotuner: k_attention_tm (S and P in tensor
+// memory, tcgen05 products) and k_attention_warp (warp-level MMAs).
 constexpr uint32_t AT_QB = 128 * 128;   // Q tile bytes (128 rows x 64 ch, 16-bit)
 constexpr uint32_t AT_KB = 64 * 128;    // K tile bytes (64 keys x 64 ch)
 constexpr uint32_t AT_VB = 64 * 128;    // V^T tile bytes (64 ch x 64 keys)
-constexpr uint32_t AT_PB = 128 * 128;   // P tile bytes per head (128 rows x 64 keys)
-template <int HPW>
-constexpr int at_wg() { return NH / HPW; }
-template <int HPW>
-constexpr int at_threads() { return at_wg<HPW>() * 128 + 32; }
-template <int ST>
-struct AtLayout {
-    static constexpr uint32_t OFF_K = 2 * AT_QB;
-    static constexpr uint32_t OFF_V = OFF_K + ST * AT_KB;
-    static constexpr uint32_t OFF_P = OFF_V + ST * AT_VB;
-    static constexpr uint32_t OFF_ONE = OFF_P + NH * AT_PB;   // 16 x 64 block of ones
-    static constexpr uint32_t OFF_BAR = OFF_ONE + 16 * 128;
-    static constexpr uint32_t SMEM = OFF_BAR + 512 + 1024;
-};
-
 struct AttnParams {
     const int4* items;
     int* counters;
@@ -1136,724 +1129,28 @@ MLPF_DEV void ffma2_bcast(float& d0, float& d1, float a0, float a1, float s, flo
     asm("mov.b64 {%0, %1}, %2;" : "=f"(d0), "=f"(d1) : "l"(d));
 }
 
-// 2^x0, 2^x1 packed in the 16-bit operand format.  FP16: one packed MUFU op on
-// the FP16-rounded arguments; BF16: two FP32 MUFU ops, rounded to BF16.
+// 2^x0, 2^x1 packed in the 16-bit operand format: one packed MUFU operation on the
+// arguments rounded to that format (ex2.f16x2 / ex2.bf16x2, two results per
+// instruction).  For BF16 the rounding of the argument S - ref (at most 2^-9
+// relative) changes P by at most |S - ref| 2^-9 ln 2; the float64 emulation of the
+// BF16 mode shows no effect of it on the outputs (tests/lowp_emul.py, stage p_arg).
 template <bool F16>
 MLPF_DEV uint32_t exp2_pair(float x0, float x1) {
+    uint32_t p;
     if constexpr (F16) {
         const uint32_t h = pack_f16x2(x0, x1);
-        uint32_t p;
         asm("ex2.approx.f16x2 %0, %1;" : "=r"(p) : "r"(h));
-        return p;
     } else {
-        return pack_bf16x2(ex2_approx(x0), ex2_approx(x1));
+        const uint32_t h = pack_bf16x2(x0, x1);
+        asm("ex2.approx.ftz.bf16x2 %0, %1;" : "=r"(p) : "r"(h));
     }
-}
-
-// Softmax numerator of 32 scores (already masked) into 4 swizzled 16-byte chunks.
-template <bool F16>
-MLPF_DEV void softmax_chunk32(const float* s, float c, float neg_m, uint8_t* prow_base, int r,
-                              int chunk0) {
-#pragma unroll
-    for (int cc = 0; cc < 4; ++cc) {
-        uint32_t pk[4];
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            float x0, x1;
-            ffma2_bcast(x0, x1, s[8 * cc + 2 * t], s[8 * cc + 2 * t + 1], c, neg_m);
-            pk[t] = exp2_pair<F16>(x0, x1);
-        }
-        *(uint4*)(prow_base + sw128_off(r, chunk0 + cc)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-    }
+    return p;
 }
 
 MLPF_DEV bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* ab, unsigned* status,
                         uint64_t wait_ns) {
     const bool ok = mbar_wait(bar, parity, ab, status, ST_TIMEOUT_ATTN, wait_ns);
     return __all_sync(0xffffffffu, ok);
-}
-
-// NH/HPW consumer warpgroups (heads HPW*w .. HPW*w+HPW-1 each) and a TMA producer
-// warp.  The register budget follows from the warp count: with HPW = 1, 17 warps,
-// five share an SM sub-partition (96 registers a thread); with HPW = 2, nine
-// warps, three share one (up to 168).
-template <bool F16, int HPW, int ST>
-__global__ void __launch_bounds__(at_threads<HPW>(), 1)
-    k_attention(const __grid_constant__ CUtensorMap map_q, const __grid_constant__ CUtensorMap map_k,
-                const __grid_constant__ CUtensorMap map_vt, AttnParams p) {
-    constexpr int AT_WG = at_wg<HPW>(), AT_THREADS = at_threads<HPW>(), AT_STAGES = ST;
-    constexpr int QR = ROWS;          // query rows per work item
-    constexpr uint32_t QB = AT_QB;    // Q tile bytes
-    using LY = AtLayout<ST>;
-    extern __shared__ uint8_t smem_raw[];
-    uint8_t* sm = align1024(smem_raw);
-    uint8_t* sQ = sm;
-    uint8_t* sK = sm + LY::OFF_K;
-    uint8_t* sV = sm + LY::OFF_V;
-    uint8_t* sP = sm + LY::OFF_P;
-    uint8_t* sOne = sm + LY::OFF_ONE;
-    uint64_t* bars = (uint64_t*)(sm + LY::OFF_BAR);
-    uint64_t* q_full = bars;                 // [2]
-    uint64_t* q_empty = bars + 2;            // [2]
-    uint64_t* kv_full = bars + 4;             // [stages]
-    uint64_t* kv_empty = kv_full + AT_STAGES; // [stages]
-    uint64_t* s_full = kv_empty + AT_STAGES;  // [warpgroups][2 buffers]
-    uint64_t* pv_done = s_full + 2 * AT_WG;   // [warpgroups]
-    uint64_t* p_ready = pv_done + AT_WG;      // [warpgroups], one arrival per warp
-    uint64_t* s_free = p_ready + AT_WG;       // [warpgroups][2 buffers], one arrival per warp
-    uint64_t* never = s_free + 2 * AT_WG;     // armed by nobody (debug stall)
-    int4* info = (int4*)(never + 2);          // [2]
-    uint32_t* tmem_hold = (uint32_t*)(info + 2);
-    int* abort_flag = (int*)(tmem_hold + 1);
-    volatile int* ab = abort_flag;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-
-    if (tid == 0) {
-        for (int i = 0; i < 2; ++i) { mbar_init(&q_full[i], 1); mbar_init(&q_empty[i], AT_WG); }
-        for (int i = 0; i < AT_STAGES; ++i) { mbar_init(&kv_full[i], 1); mbar_init(&kv_empty[i], AT_WG); }
-        for (int i = 0; i < 2 * AT_WG; ++i) {
-            mbar_init(&s_full[i], 1);
-            mbar_init(&s_free[i], 4);
-        }
-        for (int i = 0; i < AT_WG; ++i) {
-            mbar_init(&pv_done[i], 1);
-            mbar_init(&p_ready[i], 4);
-        }
-        mbar_init(never, 1);
-        *abort_flag = 0;
-        fence_mbar_init();
-    }
-    {   // 16 rows x 64 keys of 1.0 (B operand of the row-sum MMA)
-        const uint32_t one2 = F16 ? 0x3C003C00u : 0x3F803F80u;
-        for (int i = tid; i < 16 * 128 / 4; i += AT_THREADS) ((uint32_t*)sOne)[i] = one2;
-        fence_proxy_async_smem();
-    }
-    if (warp == 0) {
-        tmem_alloc(tmem_hold, 512);
-        tmem_relinquish();
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tbase = *tmem_hold;
-    const int n_items = p.counters[0];
-    int* ticket = p.counters + 2 + p.layer;
-
-    if (warp == AT_WG * 4) {
-        // ------------------------------------------------ TMA producer
-        if (lane == 0) {
-            tma_prefetch_map(&map_q);
-            tma_prefetch_map(&map_k);
-            tma_prefetch_map(&map_vt);
-            int q_it = 0;
-            uint32_t g = 0;
-            bool ok = true;
-            while (ok) {
-                // a ticket is an item (QR = 128) or half of one (QR = 64; halves
-                // without query rows are skipped)
-                const int t = atomicAdd(ticket, 1);
-                const int item = QR == 128 ? t : t >> 1, half = QR == 128 ? 0 : t & 1;
-                int4 it = make_int4(-1, 0, 0, 0);
-                if (item < n_items) {
-                    it = p.items[item];
-                    it.w = half;
-                    if (it.z - it.y * ROWS - QR * half <= 0) continue;
-                }
-                const int qb = q_it & 1;
-                if (q_it >= 2 &&
-                    !mbar_wait(&q_empty[qb], ((q_it >> 1) - 1) & 1, ab, p.status, ST_TIMEOUT_ATTN, p.wait_ns))
-                    break;
-                if (item >= n_items) {
-                    info[qb] = it;
-                    mbar_arrive(&q_full[qb]);
-                    break;
-                }
-                info[qb] = it;
-                mbar_arrive_expect_tx(&q_full[qb], QB);
-                tma_load_2d(sQ + qb * QB, &map_q, 0, it.x + it.y * ROWS + QR * half, &q_full[qb]);
-                const int nk = (it.z + 63) >> 6;
-                for (int j = 0; j < nk; ++j, ++g) {
-                    const int s = (int)(g % AT_STAGES);
-                    if (g >= AT_STAGES &&
-                        !mbar_wait(&kv_empty[s], ((g / AT_STAGES) - 1) & 1, ab, p.status, ST_TIMEOUT_ATTN,
-                                   p.wait_ns)) {
-                        ok = false;
-                        break;
-                    }
-                    mbar_arrive_expect_tx(&kv_full[s], AT_KB + AT_VB);
-                    tma_load_2d(sK + s * AT_KB, &map_k, 0, it.x + 64 * j, &kv_full[s]);
-                    tma_load_2d(sV + s * AT_VB, &map_vt, it.x + 64 * j, 0, &kv_full[s]);
-                }
-                ++q_it;
-            }
-        }
-    } else {
-        // ------------------------------------------------ one warpgroup per HPW heads
-        // Barrier phases (parity waits stay at most one completion behind):
-        //  s_full[w][b]: tiles b, b+2, ...; QK^T(t+2) needs s_free of tile t, i.e.
-        //                every warp past its wait for S(t).
-        //  s_free[w][b]: one completion per tile in buffer b (four warps read its
-        //                PV partials); the next needs PV of tile t+2, issued only
-        //                after the leader's wait.
-        //  p_ready[w]:   one per tile; a warp stores P(t+1) only after PV(t), which
-        //                the leader issues after its wait.
-        //  pv_done[w]:   one per tile; PV(t+1) needs every warp's P(t+1), stored
-        //                after that warp's wait for PV(t).
-        const int wgi = warp >> 2;
-        const int h0 = HPW * wgi;                // this warpgroup's heads: h0 .. h0 + HPW - 1
-        const int r = tid & 127;                 // query row within the tile
-        const bool leader = r == 0;              // issues this warpgroup's MMAs
-        const uint32_t tl = tbase + ((uint32_t)((warp & 3) * 32) << 16);  // this warp's lanes
-        const uint32_t fmt = F16 ? 0u : 1u;
-        const uint32_t IQK = idesc_f16(128, 64, fmt), IPV = idesc_f16(128, 16, fmt);
-        const float c = 1.f;   // Q is pre-scaled (kQScale)
-        const uint32_t one_addr = smem_u32(sOne);
-        int q_it = 0;
-        uint32_t g = 0;   // global key-tile counter (same sequence as the producer)
-        bool ok = true;
-        // S columns of head h, buffer b: h*128 + b*64
-        auto issue_qk = [&](uint32_t t, int qb) -> bool {
-            if (t >= 2 && !mbar_wait(&s_free[wgi * 2 + (t & 1)], ((t - 2) >> 1) & 1, ab, p.status,
-                                     ST_TIMEOUT_ATTN, p.wait_ns))
-                return false;
-            const uint32_t s = t % AT_STAGES;
-            if (!mbar_wait(&kv_full[s], (t / AT_STAGES) & 1, ab, p.status, ST_TIMEOUT_ATTN, p.wait_ns))
-                return false;
-            tc_fence_after();
-#pragma unroll
-            for (int hh = 0; hh < HPW; ++hh) {
-                const int h = h0 + hh;
-                mma_f16(tbase + h * 128 + (t & 1) * 64, sdesc_sw128(smem_u32(sQ + qb * AT_QB) + h * 32),
-                        sdesc_sw128(smem_u32(sK + s * AT_KB) + h * 32), IQK, 0);
-            }
-            mma_commit(&s_full[wgi * 2 + (t & 1)]);
-            return true;
-        };
-        while (ok) {
-            const int qb = q_it & 1;
-            if (!warp_wait(&q_full[qb], (q_it >> 1) & 1, ab, p.status, p.wait_ns)) break;
-            const int4 it = info[qb];
-            if (it.x < 0) break;
-            if (p.debug_stall && !warp_wait(never, 0, ab, p.status, p.wait_ns)) break;
-            const int nk = (it.z + 63) >> 6;
-            if (nk == 0) {  // an event the scheduler could not place: no keys loaded
-                if (leader) mbar_arrive(&q_empty[qb]);
-                ++q_it;
-                continue;
-            }
-            float o[HPW][16];
-#pragma unroll
-            for (int hh = 0; hh < HPW; ++hh)
-#pragma unroll
-                for (int i = 0; i < 16; ++i) o[hh][i] = 0.f;
-            // m: running row max (log2 units); ref_prev: exponent reference of the
-            // previous tile; alpha_prev: rescale of the output to that reference
-            float m[HPW], ref_prev[HPW], l[HPW], alpha_prev[HPW];
-#pragma unroll
-            for (int hh = 0; hh < HPW; ++hh) {
-                m[hh] = -INFINITY;
-                ref_prev[hh] = -INFINITY;
-                l[hh] = 0.f;
-                alpha_prev[hh] = 0.f;
-            }
-            if (leader) ok = issue_qk(g, qb);
-            ok = __all_sync(0xffffffffu, ok);   // keep every lane of the warp on one path
-            for (int j = 0; j < nk && ok; ++j) {
-                const uint32_t t = g + j;
-                const uint32_t sb = t & 1;
-                if (j > 0) {
-                    // PV and P.1 of tile t-1 (each head) landed in buffer sb^1, columns 0..31
-                    if (!warp_wait(&pv_done[wgi], (t - 1) & 1, ab, p.status, p.wait_ns)) { ok = false; break; }
-                    tc_fence_after();
-                    float part[HPW][32];
-#pragma unroll
-                    for (int hh = 0; hh < HPW; ++hh) tmem_ld32(tl + (h0 + hh) * 128 + (sb ^ 1) * 64, part[hh]);
-                    tmem_wait_ld();
-#pragma unroll
-                    for (int hh = 0; hh < HPW; ++hh) {
-#pragma unroll
-                        for (int i = 0; i < 16; ++i) o[hh][i] = fmaf(o[hh][i], alpha_prev[hh], part[hh][i]);
-                        l[hh] = fmaf(l[hh], alpha_prev[hh], part[hh][16]);
-                    }
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&s_free[wgi * 2 + (sb ^ 1)]);
-                }
-                if (leader && j + 1 < nk) ok = issue_qk(t + 1, qb);
-                ok = __all_sync(0xffffffffu, ok);
-                if (!ok) break;
-                if (!warp_wait(&s_full[wgi * 2 + sb], (t >> 1) & 1, ab, p.status, p.wait_ns)) { ok = false; break; }
-                tc_fence_after();
-                const bool last = (j == nk - 1);
-                const int kvalid = it.z - 64 * j;
-                float s[HPW][32];
-                // Exponent reference of this tile: on the item's first tile the tile
-                // max (an extra pass over S); afterwards the running max through the
-                // previous tile, so the exponentials need no max pass first.  A row
-                // whose tile max exceeds that reference by more than kStaleMax (log2
-                // units; P stays <= 2^kStaleMax) makes its warp redo the tile against
-                // the new running max.  The output is unchanged up to rounding: each
-                // PV partial is rescaled from its own reference when folded.
-                float ref[HPW];
-                if (j == 0) {
-                    float mx[HPW];
-#pragma unroll
-                    for (int hh = 0; hh < HPW; ++hh) mx[hh] = -INFINITY;
-#pragma unroll
-                    for (int hf = 0; hf < 2; ++hf) {
-#pragma unroll
-                        for (int hh = 0; hh < HPW; ++hh)
-                            tmem_ld32(tl + (h0 + hh) * 128 + sb * 64 + 32 * hf, s[hh]);
-                        tmem_wait_ld();
-#pragma unroll
-                        for (int hh = 0; hh < HPW; ++hh) {
-                            if (last) {
-#pragma unroll
-                                for (int i = 0; i < 32; ++i)
-                                    if (i + 32 * hf >= kvalid) s[hh][i] = -INFINITY;
-                            }
-#pragma unroll
-                            for (int i = 0; i < 32; i += 2) mx[hh] = max3f(mx[hh], s[hh][i], s[hh][i + 1]);
-                        }
-                    }
-#pragma unroll
-                    for (int hh = 0; hh < HPW; ++hh) {
-                        ref[hh] = mx[hh] * c;
-                        m[hh] = ref[hh];
-                    }
-                } else {
-#pragma unroll
-                    for (int hh = 0; hh < HPW; ++hh) ref[hh] = m[hh];
-                }
-                // exponentials into the P tiles (and the tile max after the first tile)
-                float mt[HPW];
-#pragma unroll
-                for (int hh = 0; hh < HPW; ++hh) mt[hh] = -INFINITY;
-#pragma unroll
-                for (int hf = 0; hf < 2; ++hf) {
-#pragma unroll
-                    for (int hh = 0; hh < HPW; ++hh) tmem_ld32(tl + (h0 + hh) * 128 + sb * 64 + 32 * hf, s[hh]);
-                    tmem_wait_ld();
-#pragma unroll
-                    for (int hh = 0; hh < HPW; ++hh) {
-                        if (last) {
-#pragma unroll
-                            for (int i = 0; i < 32; ++i)
-                                if (i + 32 * hf >= kvalid) s[hh][i] = -INFINITY;
-                        }
-                        if (j > 0) {
-#pragma unroll
-                            for (int i = 0; i < 32; i += 2) mt[hh] = max3f(mt[hh], s[hh][i], s[hh][i + 1]);
-                        }
-                        softmax_chunk32<F16>(s[hh], c, -ref[hh], sP + (h0 + hh) * AT_PB, r, 4 * hf);
-                    }
-                }
-                if (j > 0) {
-#pragma unroll
-                    for (int hh = 0; hh < HPW; ++hh) {
-                        const float t_max = mt[hh] * c;
-                        const bool redo = t_max - ref[hh] > kStaleMax;
-                        m[hh] = fmaxf(m[hh], t_max);
-                        if (__any_sync(0xffffffffu, redo)) {   // per head: warp-uniform
-                            ref[hh] = m[hh];
-#pragma unroll
-                            for (int hf = 0; hf < 2; ++hf) {
-                                tmem_ld32(tl + (h0 + hh) * 128 + sb * 64 + 32 * hf, s[hh]);
-                                tmem_wait_ld();
-                                if (last) {
-#pragma unroll
-                                    for (int i = 0; i < 32; ++i)
-                                        if (i + 32 * hf >= kvalid) s[hh][i] = -INFINITY;
-                                }
-                                softmax_chunk32<F16>(s[hh], c, -ref[hh], sP + (h0 + hh) * AT_PB, r, 4 * hf);
-                            }
-                        }
-                    }
-                }
-#pragma unroll
-                for (int hh = 0; hh < HPW; ++hh) {
-                    alpha_prev[hh] = ex2_approx(ref_prev[hh] - ref[hh]);
-                    ref_prev[hh] = ref[hh];
-                }
-                fence_proxy_async_smem();
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&p_ready[wgi]);
-                if (leader) {
-                    if (!mbar_wait(&p_ready[wgi], t & 1, ab, p.status, ST_TIMEOUT_ATTN, p.wait_ns)) {
-                        ok = false;
-                    } else {
-                        tc_fence_after();
-                        const uint32_t st = t % AT_STAGES;
-#pragma unroll
-                        for (int hh = 0; hh < HPW; ++hh) {
-                            const int h = h0 + hh;
-                            const uint32_t pa = smem_u32(sP + h * AT_PB), va = smem_u32(sV + st * AT_VB) + h * 16 * 128;
-                            const uint32_t dst = tbase + h * 128 + sb * 64;
-#pragma unroll
-                            for (int kc = 0; kc < 4; ++kc) {
-                                mma_f16(dst, sdesc_sw128(pa + kc * 32), sdesc_sw128(va + kc * 32), IPV,
-                                        kc > 0 ? 1u : 0u);
-                                mma_f16(dst + 16, sdesc_sw128(pa + kc * 32), sdesc_sw128(one_addr + kc * 32), IPV,
-                                        kc > 0 ? 1u : 0u);
-                            }
-                        }
-                        mma_commit(&pv_done[wgi]);
-                        mma_commit(&kv_empty[st]);
-                    }
-                }
-                ok = __all_sync(0xffffffffu, ok);
-            }
-            if (!ok) break;
-            const uint32_t gl = g + nk - 1;
-            if (!warp_wait(&pv_done[wgi], gl & 1, ab, p.status, p.wait_ns)) break;
-            tc_fence_after();
-            {
-                float part[HPW][32];
-#pragma unroll
-                for (int hh = 0; hh < HPW; ++hh) tmem_ld32(tl + (h0 + hh) * 128 + (gl & 1) * 64, part[hh]);
-                tmem_wait_ld();
-#pragma unroll
-                for (int hh = 0; hh < HPW; ++hh) {
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) o[hh][i] = fmaf(o[hh][i], alpha_prev[hh], part[hh][i]);
-                    l[hh] = fmaf(l[hh], alpha_prev[hh], part[hh][16]);
-                }
-            }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&s_free[wgi * 2 + (gl & 1)]);
-            if (leader) mbar_arrive(&q_empty[qb]);  // every QK^T of this item has completed
-            const int qrow0 = it.x + it.y * ROWS;
-            if (r < min(ROWS, it.z - it.y * ROWS)) {
-#pragma unroll
-                for (int hh = 0; hh < HPW; ++hh) {
-                    const float inv = 1.0f / l[hh];
-                    uint4 u0, u1;
-                    u0.x = pack2<F16>(o[hh][0] * inv, o[hh][1] * inv);
-                    u0.y = pack2<F16>(o[hh][2] * inv, o[hh][3] * inv);
-                    u0.z = pack2<F16>(o[hh][4] * inv, o[hh][5] * inv);
-                    u0.w = pack2<F16>(o[hh][6] * inv, o[hh][7] * inv);
-                    u1.x = pack2<F16>(o[hh][8] * inv, o[hh][9] * inv);
-                    u1.y = pack2<F16>(o[hh][10] * inv, o[hh][11] * inv);
-                    u1.z = pack2<F16>(o[hh][12] * inv, o[hh][13] * inv);
-                    u1.w = pack2<F16>(o[hh][14] * inv, o[hh][15] * inv);
-                    uint4* dst = (uint4*)(p.out + (size_t)(qrow0 + r) * D + (h0 + hh) * 16);
-                    dst[0] = u0;
-                    dst[1] = u1;
-                }
-            }
-            g += nk;
-            ++q_it;
-        }
-    }
-    tc_fence_before();
-    __syncthreads();
-    if (*ab && tid == 0) {
-        for (int i = 0; i < 1000; ++i) __nanosleep(1000);
-    }
-    __syncthreads();
-    if (warp == 0) {
-        tc_fence_after();
-        tmem_dealloc(tbase, 512);
-    }
-}
-
-// Attention with 32-key score tiles.  Each head has four 32-column TMEM
-// buffers, so the QK^T of the next three tiles is in flight while a tile's
-// softmax runs; the P tile of a head is double-buffered (two 32-key halves of
-// one 128-byte-swizzled tile), and the PV partial of tile t (FP32, in t's
-// buffer) is folded into the output registers after the softmax of tile t+1.
-// The softmax never waits for a PV product.  K/V still arrive in 64-key TMA
-// stages (two score tiles each).  One warpgroup per head, a TMA producer warp.
-template <int ST>
-struct At32Layout {
-    static constexpr uint32_t OFF_K = 2 * AT_QB;
-    static constexpr uint32_t OFF_V = OFF_K + ST * AT_KB;
-    static constexpr uint32_t OFF_P = OFF_V + ST * AT_VB;
-    static constexpr uint32_t OFF_ONE = OFF_P + NH * AT_PB;
-    static constexpr uint32_t OFF_BAR = OFF_ONE + 16 * 128;
-    static constexpr uint32_t SMEM = OFF_BAR + 1024 + 1024;
-};
-constexpr int A32_THREADS = NH * 128 + 32;
-
-template <bool F16, int ST>
-__global__ void __launch_bounds__(A32_THREADS, 1)
-    k_attention32(const __grid_constant__ CUtensorMap map_q, const __grid_constant__ CUtensorMap map_k,
-                  const __grid_constant__ CUtensorMap map_vt, AttnParams p) {
-    // ST: 64-key K/V stages
-    constexpr int QR = ROWS;          // query rows per work item
-    constexpr uint32_t QB = AT_QB;    // Q tile bytes
-    using LY = At32Layout<ST>;
-    extern __shared__ uint8_t smem_raw[];
-    uint8_t* sm = align1024(smem_raw);
-    uint8_t* sQ = sm;
-    uint8_t* sK = sm + LY::OFF_K;
-    uint8_t* sV = sm + LY::OFF_V;
-    uint8_t* sP = sm + LY::OFF_P;
-    uint8_t* sOne = sm + LY::OFF_ONE;
-    uint64_t* bars = (uint64_t*)(sm + LY::OFF_BAR);
-    uint64_t* q_full = bars;              // [2]
-    uint64_t* q_empty = bars + 2;         // [2]
-    uint64_t* kv_full = bars + 4;         // [ST]
-    uint64_t* kv_empty = kv_full + ST;    // [ST], one commit per warpgroup
-    uint64_t* s_full = kv_empty + ST;     // [NH][4]: QK^T of a tile landed
-    uint64_t* s_free = s_full + 4 * NH;   // [NH][4]: buffer read out, one arrival per warp
-    uint64_t* pv_done = s_free + 4 * NH;  // [NH][4]: PV of a tile landed
-    uint64_t* p_ready = pv_done + 4 * NH; // [NH][2]: P of a tile stored, one arrival per warp
-    uint64_t* never = p_ready + 2 * NH;   // armed by nobody (debug stall)
-    int4* info = (int4*)(never + 2);      // [2]
-    uint32_t* tmem_hold = (uint32_t*)(info + 2);
-    int* abort_flag = (int*)(tmem_hold + 1);
-    volatile int* ab = abort_flag;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-
-    if (tid == 0) {
-        for (int i = 0; i < 2; ++i) { mbar_init(&q_full[i], 1); mbar_init(&q_empty[i], NH); }
-        for (int i = 0; i < ST; ++i) { mbar_init(&kv_full[i], 1); mbar_init(&kv_empty[i], NH); }
-        for (int i = 0; i < 4 * NH; ++i) {
-            mbar_init(&s_full[i], 1);
-            mbar_init(&s_free[i], 4);
-            mbar_init(&pv_done[i], 1);
-        }
-        for (int i = 0; i < 2 * NH; ++i) mbar_init(&p_ready[i], 4);
-        mbar_init(never, 1);
-        *abort_flag = 0;
-        fence_mbar_init();
-    }
-    {   // 16 rows x 64 keys of 1.0 (B operand of the row-sum MMA)
-        const uint32_t one2 = F16 ? 0x3C003C00u : 0x3F803F80u;
-        for (int i = tid; i < 16 * 128 / 4; i += A32_THREADS) ((uint32_t*)sOne)[i] = one2;
-        fence_proxy_async_smem();
-    }
-    if (warp == 0) {
-        tmem_alloc(tmem_hold, 512);
-        tmem_relinquish();
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tbase = *tmem_hold;
-    const int n_items = p.counters[0];
-    int* ticket = p.counters + 2 + p.layer;
-
-    if (warp == NH * 4) {
-        // ------------------------------------------------ TMA producer (64-key stages)
-        if (lane == 0) {
-            tma_prefetch_map(&map_q);
-            tma_prefetch_map(&map_k);
-            tma_prefetch_map(&map_vt);
-            int q_it = 0;
-            uint32_t g = 0;
-            bool ok = true;
-            while (ok) {
-                // a ticket is an item (QR = 128) or half of one (QR = 64; halves
-                // without query rows are skipped)
-                const int t = atomicAdd(ticket, 1);
-                const int item = QR == 128 ? t : t >> 1, half = QR == 128 ? 0 : t & 1;
-                int4 it = make_int4(-1, 0, 0, 0);
-                if (item < n_items) {
-                    it = p.items[item];
-                    it.w = half;
-                    if (it.z - it.y * ROWS - QR * half <= 0) continue;
-                }
-                const int qb = q_it & 1;
-                if (q_it >= 2 &&
-                    !mbar_wait(&q_empty[qb], ((q_it >> 1) - 1) & 1, ab, p.status, ST_TIMEOUT_ATTN, p.wait_ns))
-                    break;
-                if (item >= n_items) {
-                    info[qb] = it;
-                    mbar_arrive(&q_full[qb]);
-                    break;
-                }
-                info[qb] = it;
-                mbar_arrive_expect_tx(&q_full[qb], QB);
-                tma_load_2d(sQ + qb * QB, &map_q, 0, it.x + it.y * ROWS + QR * half, &q_full[qb]);
-                const int nk = (it.z + 63) >> 6;
-                for (int j = 0; j < nk; ++j, ++g) {
-                    const int s = (int)(g % ST);
-                    if (g >= ST &&
-                        !mbar_wait(&kv_empty[s], ((g / ST) - 1) & 1, ab, p.status, ST_TIMEOUT_ATTN, p.wait_ns)) {
-                        ok = false;
-                        break;
-                    }
-                    mbar_arrive_expect_tx(&kv_full[s], AT_KB + AT_VB);
-                    tma_load_2d(sK + s * AT_KB, &map_k, 0, it.x + 64 * j, &kv_full[s]);
-                    tma_load_2d(sV + s * AT_VB, &map_vt, it.x + 64 * j, 0, &kv_full[s]);
-                }
-                ++q_it;
-            }
-        }
-    } else {
-        // ------------------------------------------------ one warpgroup per head
-        // Score tile t (global count) uses TMEM buffer t & 3 of its head and P half
-        // t & 1.  Barrier phases (every parity wait is at most one completion behind):
-        //  s_full[b]:  QK^T(t + 4) into buffer b is issued only after every warp
-        //              freed b (s_free), i.e. after its wait for S(t).
-        //  pv_done[b]: PV(t + 4) follows the warps' wait for PV(t) (fold of t).
-        //  s_free[b]:  the next completion needs PV(t + 4), issued after the
-        //              leader's wait.
-        //  p_ready[t & 1]: a warp stores P(t + 2) only after the fold of t, which
-        //              waits for PV(t), issued after the leader's wait for P(t).
-        //  P half t & 1 is rewritten by tile t + 2 after the fold of t (PV(t) done).
-        const int h = warp >> 2;
-        const int r = tid & 127;
-        const bool leader = r == 32 * (h & 3);   // leaders spread over the sub-partitions
-        const uint32_t tl = tbase + ((uint32_t)((warp & 3) * 32) << 16);
-        const uint32_t colh = (uint32_t)h * 128;  // this head's four 32-column buffers
-        const uint32_t fmt = F16 ? 0u : 1u;
-        const uint32_t IQK = idesc_f16(128, 32, fmt), IPV = idesc_f16(128, 16, fmt);
-        const float c = 1.f;   // Q is pre-scaled (kQScale)
-        const uint32_t one_addr = smem_u32(sOne);
-        uint8_t* sPh = sP + h * AT_PB;
-        int q_it = 0;
-        uint32_t u = 0;   // global score-tile counter
-        uint32_t g = 0;   // global K/V stage counter (same sequence as the producer)
-        bool ok = true;
-        // QK^T of tile t = u + i of the current item (stage g + i/2, key half i & 1)
-        auto issue_qk = [&](uint32_t t, int i, int qb) -> bool {
-            const uint32_t b = t & 3;
-            if (t >= 4 && !mbar_wait(&s_free[h * 4 + b], ((t >> 2) - 1) & 1, ab, p.status, ST_TIMEOUT_ATTN,
-                                     p.wait_ns))
-                return false;
-            const uint32_t gs = g + (uint32_t)(i >> 1), s = gs % ST;
-            if ((i & 1) == 0 &&
-                !mbar_wait(&kv_full[s], (gs / ST) & 1, ab, p.status, ST_TIMEOUT_ATTN, p.wait_ns))
-                return false;
-            tc_fence_after();
-            mma_f16(tbase + colh + b * 32, sdesc_sw128(smem_u32(sQ + qb * AT_QB) + h * 32),
-                    sdesc_sw128(smem_u32(sK + s * AT_KB) + (i & 1) * 4096 + h * 32), IQK, 0);
-            mma_commit(&s_full[h * 4 + b]);
-            return true;
-        };
-        // o = o * a + (PV partial of tile t); frees t's buffer
-        float o[16], l = 0.f;
-        auto fold = [&](uint32_t t, float a) {
-            float part[32];
-            tmem_ld32(tl + colh + (t & 3) * 32, part);
-            tmem_wait_ld();
-#pragma unroll
-            for (int k = 0; k < 16; ++k) o[k] = fmaf(o[k], a, part[k]);
-            l = fmaf(l, a, part[16]);
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&s_free[h * 4 + (t & 3)]);
-        };
-        while (ok) {
-            const int qb = q_it & 1;
-            if (!warp_wait(&q_full[qb], (q_it >> 1) & 1, ab, p.status, p.wait_ns)) break;
-            const int4 it = info[qb];
-            if (it.x < 0) break;
-            if (p.debug_stall && !warp_wait(never, 0, ab, p.status, p.wait_ns)) break;
-            const int n32 = (it.z + 31) >> 5;
-            if (n32 == 0) {  // an event the scheduler could not place: no keys loaded
-                if (leader) mbar_arrive(&q_empty[qb]);
-                ++q_it;
-                continue;
-            }
-#pragma unroll
-            for (int k = 0; k < 16; ++k) o[k] = 0.f;
-            l = 0.f;
-            float m = -INFINITY, a_fold = 0.f;
-            if (leader)
-                for (int i = 0; i < 4 && i < n32 && ok; ++i) ok = issue_qk(u + i, i, qb);
-            ok = __all_sync(0xffffffffu, ok);
-            for (int i = 0; i < n32 && ok; ++i) {
-                const uint32_t t = u + i, b = t & 3;
-                if (!warp_wait(&s_full[h * 4 + b], (t >> 2) & 1, ab, p.status, p.wait_ns)) { ok = false; break; }
-                tc_fence_after();
-                float s[32];
-                tmem_ld32(tl + colh + b * 32, s);
-                tmem_wait_ld();
-                const int kvalid = it.z - 32 * i;
-                if (kvalid < 32) {
-#pragma unroll
-                    for (int k = 0; k < 32; ++k)
-                        if (k >= kvalid) s[k] = -INFINITY;
-                }
-                float mx = -INFINITY;
-#pragma unroll
-                for (int k = 0; k < 32; k += 2) mx = max3f(mx, s[k], s[k + 1]);
-                const float m_new = fmaxf(m, mx * c);
-                const float a_t = ex2_approx(m - m_new);
-                m = m_new;
-                softmax_chunk32<F16>(s, c, -m_new, sPh, r, (int)(t & 1) * 4);
-                fence_proxy_async_smem();
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&p_ready[h * 2 + (t & 1)]);
-                if (leader) {
-                    if (!mbar_wait(&p_ready[h * 2 + (t & 1)], (t >> 1) & 1, ab, p.status, ST_TIMEOUT_ATTN,
-                                   p.wait_ns)) {
-                        ok = false;
-                    } else {
-                        tc_fence_after();
-                        const uint32_t gs = g + (uint32_t)(i >> 1), st = gs % ST;
-                        const uint32_t pa = smem_u32(sPh) + (t & 1) * 64;
-                        const uint32_t va = smem_u32(sV + st * AT_VB) + h * 16 * 128 + (i & 1) * 64;
-                        const uint32_t dst = tbase + colh + b * 32;
-#pragma unroll
-                        for (int kc = 0; kc < 2; ++kc) {
-                            mma_f16(dst, sdesc_sw128(pa + kc * 32), sdesc_sw128(va + kc * 32), IPV, kc ? 1u : 0u);
-                            mma_f16(dst + 16, sdesc_sw128(pa + kc * 32), sdesc_sw128(one_addr + kc * 32), IPV,
-                                    kc ? 1u : 0u);
-                        }
-                        mma_commit(&pv_done[h * 4 + b]);
-                        if ((i & 1) || i == n32 - 1) mma_commit(&kv_empty[st]);  // stage's last PV
-                    }
-                }
-                ok = __all_sync(0xffffffffu, ok);
-                if (!ok) break;
-                if (i > 0) {
-                    const uint32_t tp = t - 1;
-                    if (!warp_wait(&pv_done[h * 4 + (tp & 3)], (tp >> 2) & 1, ab, p.status, p.wait_ns)) {
-                        ok = false;
-                        break;
-                    }
-                    tc_fence_after();
-                    fold(tp, a_fold);
-                    if (leader && i + 3 < n32) ok = issue_qk(t + 3, i + 3, qb);
-                    ok = __all_sync(0xffffffffu, ok);
-                }
-                a_fold = a_t;
-            }
-            if (!ok) break;
-            const uint32_t tlast = u + n32 - 1;
-            if (!warp_wait(&pv_done[h * 4 + (tlast & 3)], (tlast >> 2) & 1, ab, p.status, p.wait_ns)) break;
-            tc_fence_after();
-            fold(tlast, a_fold);
-            if (leader) mbar_arrive(&q_empty[qb]);  // every QK^T of this item has completed
-            const int qrow0 = it.x + it.y * ROWS;
-            if (r < min(ROWS, it.z - it.y * ROWS)) {
-                const float inv = 1.0f / l;
-                uint4 u0, u1;
-                u0.x = pack2<F16>(o[0] * inv, o[1] * inv);
-                u0.y = pack2<F16>(o[2] * inv, o[3] * inv);
-                u0.z = pack2<F16>(o[4] * inv, o[5] * inv);
-                u0.w = pack2<F16>(o[6] * inv, o[7] * inv);
-                u1.x = pack2<F16>(o[8] * inv, o[9] * inv);
-                u1.y = pack2<F16>(o[10] * inv, o[11] * inv);
-                u1.z = pack2<F16>(o[12] * inv, o[13] * inv);
-                u1.w = pack2<F16>(o[14] * inv, o[15] * inv);
-                uint4* dst = (uint4*)(p.out + (size_t)(qrow0 + r) * D + h * 16);
-                dst[0] = u0;
-                dst[1] = u1;
-            }
-            u += (uint32_t)n32;
-            g += (uint32_t)((it.z + 63) >> 6);
-            ++q_it;
-        }
-    }
-    tc_fence_before();
-    __syncthreads();
-    if (*ab && tid == 0) {
-        for (int i = 0; i < 1000; ++i) __nanosleep(1000);
-    }
-    __syncthreads();
-    if (warp == 0) {
-        tc_fence_after();
-        tmem_dealloc(tbase, 512);
-    }
 }
 
 // Attention with warp-level MMAs (m16n8k16).  With a head width of 16 the
@@ -2254,17 +1551,21 @@ __global__ void __launch_bounds__(aw_threads<QR>(), QR == 128 ? 1 : 2)
             if (!ok) break;
             const int qrow0 = it.x + it.y * ROWS + QR * it.w;   // it.w: half of the item (QR = 64)
             const int nrows = min(QR, it.z - it.y * ROWS - QR * it.w);
+            // the event's padding rows (up to its next 64-row boundary) get O = 0, so
+            // that every value the next kernels read is written by this forward
+            const int npad = min(QR, ((it.z + 63) & ~63) - it.y * ROWS - QR * it.w);
 #pragma unroll
             for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
                 for (int hr = 0; hr < 2; ++hr) {
                     const float l = la[mt][2 * hr];
                     const int r = rb * 32 + mt * 16 + gq + 8 * hr;
-                    if (r < nrows) {
+                    if (r < npad) {
+                        const bool val = r < nrows;
                         const float inv = 1.0f / l;
                         uint32_t* dst = (uint32_t*)(p.out + (size_t)(qrow0 + r) * D + h * 16 + 2 * tq);
-                        dst[0] = pack2<F16>(o[mt][0][2 * hr] * inv, o[mt][0][2 * hr + 1] * inv);
-                        dst[4] = pack2<F16>(o[mt][1][2 * hr] * inv, o[mt][1][2 * hr + 1] * inv);
+                        dst[0] = val ? pack_f16x2(o[mt][0][2 * hr] * inv, o[mt][0][2 * hr + 1] * inv) : 0u;
+                        dst[4] = val ? pack_f16x2(o[mt][1][2 * hr] * inv, o[mt][1][2 * hr + 1] * inv) : 0u;
                     }
                 }
             ++q_it;
@@ -2273,6 +1574,367 @@ __global__ void __launch_bounds__(aw_threads<QR>(), QR == 128 ? 1 : 2)
     __syncthreads();
     if (*ab && tid == 0) {
         for (int i = 0; i < 1000; ++i) __nanosleep(1000);
+    }
+}
+
+// ------------------------------------------------ attention, S and P in tensor memory
+// Persistent, one CTA per SM: four softmax warpgroups (warpgroup h = head h; thread r
+// owns query row r of the 128-row item), a TMA producer warp and an MMA warp.  Per
+// head and 64-key tile the MMA warp computes S = Q_h K_h^T (tcgen05, Q and K from
+// shared memory) into the head's S columns of tensor memory; the softmax threads
+// load their row of S, write P = 2^(S - ref) in the 16-bit operand format into the
+// head's P columns, and the MMA warp accumulates [O_h | l_h] += P [V_h | 1] with P
+// as the tensor-memory A operand (M 128, N 32, K 64): P never passes through shared
+// memory, and O and the row sums l stay in tensor memory for the whole item (read
+// once, at its end).  Tensor memory per head: S 64 columns, P 32 (two 16-bit values
+// per column), O 16, l 16 (every column the row sum); four heads, 512 columns.
+// Each V^T stage holds, per head, the head's 16 V^T rows followed by 16 rows of ones,
+// so one MMA gives the PV product and the row sums of the same rounded P.
+// Rescaling is lazy as in the warp-level kernel: the first tile sets each row's
+// exponent reference to the tile maximum; a later tile whose score bound |q| max|k|
+// exceeds the reference by more than kLimit has its maxima computed, and a row whose
+// maximum exceeds the reference by more than kStaleMax raises it and rescales its O
+// and l in tensor memory.  BF16 exponentials are packed (ex2.bf16x2: two per MUFU
+// operation), FP16 likewise (ex2.f16x2).  Every wait is bounded.
+constexpr int TM_THREADS = NH * 128 + 64;        // 16 softmax warps, producer, MMA warp
+constexpr uint32_t TM_VB = NH * 32 * 128;        // per stage: per head 16 V^T rows + 16 rows of ones
+template <int ST>
+struct TmLayout {
+    static constexpr uint32_t OFF_K = 2 * AT_QB;
+    static constexpr uint32_t OFF_V = OFF_K + ST * AT_KB;
+    static constexpr uint32_t OFF_BAR = OFF_V + ST * TM_VB;   // barriers, item info, flags (< 512 B)
+    static constexpr uint32_t OFF_KN = OFF_BAR + 512;         // [ST][4] key-tile norm bounds
+    static constexpr uint32_t SMEM = OFF_KN + ST * 16 + 16 + 1024;
+};
+
+template <bool F16, int ST>
+__global__ void __launch_bounds__(TM_THREADS, 1)
+    k_attention_tm(const __grid_constant__ CUtensorMap map_q, const __grid_constant__ CUtensorMap map_k,
+                   const __grid_constant__ CUtensorMap map_vt16, AttnParams p) {
+    using LY = TmLayout<ST>;
+    constexpr int NSW = NH * 4;                   // softmax warps
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* sm = align1024(smem_raw);
+    uint8_t* sQ = sm;
+    uint8_t* sK = sm + LY::OFF_K;
+    uint8_t* sV = sm + LY::OFF_V;
+    uint64_t* bars = (uint64_t*)(sm + LY::OFF_BAR);
+    uint64_t* q_full = bars;              // [2]  producer (tx)
+    uint64_t* q_empty = bars + 2;         // [2]  MMA commit after the item's last QK^T
+    uint64_t* kv_full = bars + 4;         // [ST] producer (tx)
+    uint64_t* kv_empty = kv_full + ST;    // [ST] MMA commit after the tile's last MMA
+    uint64_t* s_full = kv_empty + ST;     // [NH] MMA commit: S of the head's tile ready
+    uint64_t* p_ready = s_full + NH;      // [NH] one arrival per softmax warp: P stored, S read
+    uint64_t* pv_done = p_ready + NH;     // [NH] MMA commit: the head's [O | l] += P [V | 1] done
+    uint64_t* o_free = pv_done + NH;      // [NH] one arrival per softmax warp: O, l read at item end
+    uint64_t* drain = o_free + NH;        // MMA warp's exit: every issued MMA complete
+    uint64_t* never = drain + 1;          // armed by nobody (debug stall)
+    int4* info = (int4*)(never + 1);      // [2]
+    uint32_t* tmem_hold = (uint32_t*)(info + 2);
+    int* abort_flag = (int*)(tmem_hold + 1);
+    float* kn = (float*)(sm + LY::OFF_KN);
+    volatile int* ab = abort_flag;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    if (tid == 0) {
+        for (int i = 0; i < 2; ++i) { mbar_init(&q_full[i], 1); mbar_init(&q_empty[i], 1); }
+        for (int i = 0; i < ST; ++i) { mbar_init(&kv_full[i], 1); mbar_init(&kv_empty[i], 1); }
+        for (int h = 0; h < NH; ++h) {
+            mbar_init(&s_full[h], 1);
+            mbar_init(&p_ready[h], 4);
+            mbar_init(&pv_done[h], 1);
+            mbar_init(&o_free[h], 4);
+        }
+        mbar_init(drain, 1);
+        mbar_init(never, 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    {   // the rows of ones under each head's V^T rows, in every stage (B operand of the row sums)
+        const uint32_t one2 = F16 ? 0x3C003C00u : 0x3F803F80u;
+        for (int i = tid; i < ST * NH * 16 * 32; i += TM_THREADS) {
+            const int s = i / (NH * 512), rem = i % (NH * 512), h = rem / 512, w = rem % 512;
+            ((uint32_t*)(sV + s * TM_VB + h * 4096 + 2048))[w] = one2;
+        }
+        fence_proxy_async_smem();
+    }
+    if (warp == 0) {
+        tmem_alloc(tmem_hold, 512);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = *tmem_hold;
+    const int n_items = p.counters[0];
+    int* ticket = p.counters + 2 + p.layer;
+
+    if (warp == NSW) {
+        // ------------------------------------------------ TMA producer
+        if (lane == 0) {
+            tma_prefetch_map(&map_q);
+            tma_prefetch_map(&map_k);
+            tma_prefetch_map(&map_vt16);
+            int q_it = 0;
+            uint32_t g = 0;
+            bool ok = true;
+            while (ok) {
+                const int item = atomicAdd(ticket, 1);
+                int4 it = make_int4(-1, 0, 0, 0);
+                if (item < n_items) {
+                    it = p.items[item];
+                    if (it.z - it.y * ROWS <= 0) continue;   // an event the scheduler could not place
+                }
+                const int qb = q_it & 1;
+                if (q_it >= 2 &&
+                    !mbar_wait(&q_empty[qb], ((q_it >> 1) - 1) & 1, ab, p.status, ST_TIMEOUT_ATTN, p.wait_ns))
+                    break;
+                info[qb] = it;
+                if (item >= n_items) {
+                    mbar_arrive(&q_full[qb]);
+                    break;
+                }
+                mbar_arrive_expect_tx(&q_full[qb], AT_QB);
+                tma_load_2d(sQ + qb * AT_QB, &map_q, 0, it.x + it.y * ROWS, &q_full[qb]);
+                int kb, ke;
+                key_range(it.y, it.z, p.window, kb, ke);
+                const int nk = (ke - kb + 63) >> 6;
+                for (int j = 0; j < nk; ++j, ++g) {
+                    const int s = (int)(g % ST);
+                    if (g >= ST &&
+                        !mbar_wait(&kv_empty[s], ((g / ST) - 1) & 1, ab, p.status, ST_TIMEOUT_ATTN, p.wait_ns)) {
+                        ok = false;
+                        break;
+                    }
+                    const int key0 = it.x + kb + 64 * j;
+                    mbar_arrive_expect_tx(&kv_full[s], AT_KB + NH * 2048 + 16);
+                    tma_load_2d(sK + s * AT_KB, &map_k, 0, key0, &kv_full[s]);
+#pragma unroll
+                    for (int h = 0; h < NH; ++h)
+                        tma_load_2d(sV + s * TM_VB + h * 4096, &map_vt16, key0, 16 * h, &kv_full[s]);
+                    bulk_load(kn + 4 * s, p.kmax + (size_t)((key0 >> 6)) * 4, 16, &kv_full[s]);
+                }
+                ++q_it;
+            }
+            // on an abort, let the copies still in flight land before the CTA exits
+            if (*ab) {
+                for (uint32_t t = g > ST ? g - ST : 0; t < g; ++t)
+                    mbar_drain(&kv_full[t % ST], (t / ST) & 1, p.wait_ns);
+                for (int i = q_it > 2 ? q_it - 2 : 0; i < q_it; ++i) mbar_drain(&q_full[i & 1], (i >> 1) & 1, p.wait_ns);
+            }
+        }
+    } else if (warp == NSW + 1) {
+        // ------------------------------------------------ MMA issue (one thread)
+        if (lane == 0) {
+            const uint32_t fmt = F16 ? 0u : 1u;
+            const uint32_t IQK = idesc_f16(128, 64, fmt), IPV = idesc_f16(128, 32, fmt);
+            int q_it = 0;
+            uint32_t g = 0;
+            bool ok = true;
+            auto W = [&](uint64_t* bar, uint32_t parity) {
+                return mbar_wait(bar, parity, ab, p.status, ST_TIMEOUT_ATTN, p.wait_ns);
+            };
+            while (ok) {
+                const int qb = q_it & 1;
+                if (!W(&q_full[qb], (q_it >> 1) & 1)) break;
+                const int4 it = info[qb];
+                if (it.x < 0) break;
+                int kb, ke;
+                key_range(it.y, it.z, p.window, kb, ke);
+                const int nk = (ke - kb + 63) >> 6;
+                const uint32_t qa = smem_u32(sQ + qb * AT_QB);
+                // S of the item's first tile, every head (the previous tile's P of each
+                // head was read by its PV, issued after that head's p_ready)
+                {
+                    const uint32_t s = g % ST;
+                    if (!W(&kv_full[s], (g / ST) & 1)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t ka = smem_u32(sK + s * AT_KB);
+                    for (int h = 0; h < NH; ++h) {
+                        mma_f16(tbase + h * 128, sdesc_sw128(qa + h * 32), sdesc_sw128(ka + h * 32), IQK, 0);
+                        mma_commit(&s_full[h]);
+                    }
+                }
+                for (int j = 0; j < nk && ok; ++j) {
+                    const uint32_t t = g + j, s = t % ST;
+                    const uint32_t va = smem_u32(sV + s * TM_VB);
+                    const uint32_t ka1 = smem_u32(sK + ((t + 1) % ST) * AT_KB);
+                    for (int h = 0; h < NH; ++h) {
+                        if (!W(&p_ready[h], t & 1)) { ok = false; break; }
+                        if (j == 0 && q_it > 0 && !W(&o_free[h], (q_it - 1) & 1)) { ok = false; break; }
+                        tc_fence_after();
+                        const uint32_t col = tbase + h * 128;
+#pragma unroll
+                        for (int kc = 0; kc < 4; ++kc)
+                            mma_f16_ts(col + 96, col + 64 + 8 * kc, sdesc_sw128(va + h * 4096 + kc * 32), IPV,
+                                       (j > 0 || kc > 0) ? 1u : 0u);
+                        mma_commit(&pv_done[h]);
+                        if (j + 1 < nk) {
+                            if (h == 0 && !W(&kv_full[(t + 1) % ST], ((t + 1) / ST) & 1)) { ok = false; break; }
+                            tc_fence_after();
+                            mma_f16(col, sdesc_sw128(qa + h * 32), sdesc_sw128(ka1 + h * 32), IQK, 0);
+                            mma_commit(&s_full[h]);
+                        }
+                    }
+                    if (!ok) break;
+                    mma_commit(&kv_empty[s]);
+                }
+                if (!ok) break;
+                mma_commit(&q_empty[qb]);
+                g += nk;
+                ++q_it;
+            }
+            // every MMA issued by this thread complete before tensor memory is released
+            mma_commit(drain);
+            mbar_drain(drain, 0, p.wait_ns);
+        }
+    } else {
+        // ------------------------------------------------ softmax: warpgroup h = head h
+        const int h = warp >> 2;
+        const int r = tid & 127;
+        const uint32_t tl = tbase + ((uint32_t)((warp & 3) * 32) << 16) + h * 128;   // this warp's lanes
+        const uint32_t tS = tl, tP = tl + 64, tO = tl + 96;
+        int q_it = 0;
+        uint32_t g = 0;
+        bool ok = true;
+        while (ok) {
+            const int qb = q_it & 1;
+            if (!warp_wait(&q_full[qb], (q_it >> 1) & 1, ab, p.status, p.wait_ns)) break;
+            const int4 it = info[qb];
+            if (it.x < 0) break;
+            if (p.debug_stall && !warp_wait(never, 0, ab, p.status, p.wait_ns)) break;
+            int kb, ke;
+            key_range(it.y, it.z, p.window, kb, ke);
+            const int nk = (ke - kb + 63) >> 6;
+            // |q| of this row's head-h channels (1 % for the FP32 sums), for the key
+            // tiles' score bounds |q| max|k|
+            float qn;
+            {
+                const uint8_t* qrow = sQ + qb * AT_QB;
+                const uint4 u0 = *(const uint4*)(qrow + sw128_off(r, 2 * h));
+                const uint4 u1 = *(const uint4*)(qrow + sw128_off(r, 2 * h + 1));
+                const uint32_t w8[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+                float ss = 0.f;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    float a, b;
+                    unpack2<F16>(w8[i], a, b);
+                    ss = fmaf(a, a, fmaf(b, b, ss));
+                }
+                qn = sqrtf(ss) * 1.01f;
+            }
+            float ref = 0.f;
+            for (int j = 0; j < nk; ++j) {
+                const uint32_t t = g + j, s = t % ST;
+                if (!warp_wait(&s_full[h], t & 1, ab, p.status, p.wait_ns)) { ok = false; break; }
+                if (!warp_wait(&kv_full[s], (t / ST) & 1, ab, p.status, p.wait_ns)) { ok = false; break; }
+                tc_fence_after();
+                const int kvalid = ke - kb - 64 * j;
+                const bool full = kvalid >= 64;
+                // the maxima are needed on the first tile (it sets the reference), on a
+                // ragged tile and where the score bound does not hold
+                const bool need = j == 0 || !full || fmaf(qn, kn[s * 4 + h], -ref) > kLimit<F16>;
+                float sv[32];
+                float m = -INFINITY;
+                if (__any_sync(0xffffffffu, need)) {
+#pragma unroll
+                    for (int hf = 0; hf < 2; ++hf) {
+                        tmem_ld32(tS + 32 * hf, sv);
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int i = 0; i < 32; ++i)
+                            if (!full && 32 * hf + i >= kvalid) sv[i] = -INFINITY;
+#pragma unroll
+                        for (int i = 0; i < 32; i += 2) m = max3f(m, sv[i], sv[i + 1]);
+                    }
+                }
+                float nref = ref;
+                bool redo = false;
+                if (j == 0) {
+                    nref = m;
+                } else if (need && m - ref > kStaleMax) {
+                    nref = m;
+                    redo = true;
+                }
+                if (j > 0) {
+                    // P(t-1) read and O, l final up to tile t-1 before P(t) is written
+                    if (!warp_wait(&pv_done[h], (t - 1) & 1, ab, p.status, p.wait_ns)) { ok = false; break; }
+                    tc_fence_after();
+                    if (__any_sync(0xffffffffu, redo)) {
+                        float ol[32];
+                        tmem_ld32(tO, ol);
+                        tmem_wait_ld();
+                        const float a = redo ? ex2_approx(ref - nref) : 1.f;
+                        uint32_t u[32];
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) u[i] = __float_as_uint(ol[i] * a);
+                        tmem_st32(tO, u);
+                    }
+                }
+                ref = nref;
+                // P = 2^(S - ref) into the head's P columns
+#pragma unroll
+                for (int hf = 0; hf < 2; ++hf) {
+                    tmem_ld32(tS + 32 * hf, sv);
+                    tmem_wait_ld();
+                    if (!full) {
+#pragma unroll
+                        for (int i = 0; i < 32; ++i)
+                            if (32 * hf + i >= kvalid) sv[i] = -INFINITY;
+                    }
+                    uint32_t pk[16];
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        float x0, x1;
+                        ffma2_bcast(x0, x1, sv[2 * i], sv[2 * i + 1], 1.f, -ref);
+                        pk[i] = exp2_pair<F16>(x0, x1);
+                    }
+                    tmem_st16(tP + 16 * hf, pk);
+                }
+                tmem_wait_st();
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&p_ready[h]);
+            }
+            if (!ok) break;
+            // the item's output: O / l of this row and head
+            const uint32_t tlast = g + nk - 1;
+            if (!warp_wait(&pv_done[h], tlast & 1, ab, p.status, p.wait_ns)) break;
+            tc_fence_after();
+            float ol[32];
+            tmem_ld32(tO, ol);
+            tmem_wait_ld();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&o_free[h]);
+            const int qrow0 = it.x + it.y * ROWS;
+            // valid rows get O / l, the event's padding rows (up to its next 64-row
+            // boundary) O = 0, so that every value the next kernels read is written here
+            if (r < min(ROWS, ((it.z + 63) & ~63) - it.y * ROWS)) {
+                const float inv = 1.0f / ol[16];
+                uint4 u0, u1;
+                u0.x = pack_f16x2(ol[0] * inv, ol[1] * inv);
+                u0.y = pack_f16x2(ol[2] * inv, ol[3] * inv);
+                u0.z = pack_f16x2(ol[4] * inv, ol[5] * inv);
+                u0.w = pack_f16x2(ol[6] * inv, ol[7] * inv);
+                u1.x = pack_f16x2(ol[8] * inv, ol[9] * inv);
+                u1.y = pack_f16x2(ol[10] * inv, ol[11] * inv);
+                u1.z = pack_f16x2(ol[12] * inv, ol[13] * inv);
+                u1.w = pack_f16x2(ol[14] * inv, ol[15] * inv);
+                uint4* dst = (uint4*)(p.out + (size_t)(qrow0 + r) * D + h * 16);
+                const bool val = r < it.z - it.y * ROWS;
+                dst[0] = val ? u0 : make_uint4(0, 0, 0, 0);
+                dst[1] = val ? u1 : make_uint4(0, 0, 0, 0);
+            }
+            g += nk;
+            ++q_it;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tbase, 512);
     }
 }
 
@@ -2382,17 +2044,14 @@ int occupancy(K kernel, int threads, uint32_t smem) {
 // empty string or a description of the kernels that do not fit.
 template <int FMT>
 std::string check_occupancy() {
-    const int o_att[10] = {occupancy(k_attention<kOutF16<FMT>, 1, 4>, at_threads<1>(), AtLayout<4>::SMEM),
-                          occupancy(k_attention<kOutF16<FMT>, 1, 2>, at_threads<1>(), AtLayout<2>::SMEM),
-                          occupancy(k_attention<kOutF16<FMT>, 2, 4>, at_threads<2>(), AtLayout<4>::SMEM),
-                          occupancy(k_attention<kOutF16<FMT>, 2, 2>, at_threads<2>(), AtLayout<2>::SMEM),
-                          occupancy(k_attention32<kOutF16<FMT>, 4>, A32_THREADS, At32Layout<4>::SMEM),
-                          occupancy(k_attention<kOutF16<FMT>, 1, 6>, at_threads<1>(), AtLayout<6>::SMEM),
-                          occupancy(k_attention32<kOutF16<FMT>, 6>, A32_THREADS, At32Layout<6>::SMEM),
-                          occupancy(k_attention_warp<kOutF16<FMT>, 4>, aw_threads<128>(), AwLayout<4>::SMEM),
-                          occupancy(k_attention_warp<kOutF16<FMT>, 8>, aw_threads<128>(), AwLayout<8>::SMEM),
-                          occupancy(k_attention_warp<kOutF16<FMT>, 4, 64>, aw_threads<64>(), AwLayout<4, 64>::SMEM) / 2};
-    const int o[6] = {*std::min_element(o_att, o_att + 10),
+    const int o_att[MLPF_ATTN_VARIANTS] = {
+        occupancy(k_attention_tm<kOutF16<FMT>, 4>, TM_THREADS, TmLayout<4>::SMEM),
+        occupancy(k_attention_tm<kOutF16<FMT>, 6>, TM_THREADS, TmLayout<6>::SMEM),
+        occupancy(k_attention_tm<kOutF16<FMT>, 8>, TM_THREADS, TmLayout<8>::SMEM),
+        occupancy(k_attention_warp<kOutF16<FMT>, 4>, aw_threads<128>(), AwLayout<4>::SMEM),
+        occupancy(k_attention_warp<kOutF16<FMT>, 8>, aw_threads<128>(), AwLayout<8>::SMEM),
+        occupancy(k_attention_warp<kOutF16<FMT>, 4, 64>, aw_threads<64>(), AwLayout<4, 64>::SMEM) / 2};
+    const int o[6] = {*std::min_element(o_att, o_att + MLPF_ATTN_VARIANTS),
                       occupancy(k_post<0, FMT>, PT_THREADS, post_smem(0, FMT)),
                       occupancy(k_post<1, FMT>, PT_THREADS, post_smem(1, FMT)),
                       occupancy(k_post<2, FMT>, PT_THREADS, post_smem(2, FMT)),
@@ -2412,13 +2071,9 @@ void set_attrs() {
     cudaFuncSetAttribute(k_post<0, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, post_smem(0, FMT));
     cudaFuncSetAttribute(k_post<1, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, post_smem(1, FMT));
     cudaFuncSetAttribute(k_post<2, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, post_smem(2, FMT));
-    cudaFuncSetAttribute(k_attention<kOutF16<FMT>, 1, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, AtLayout<4>::SMEM);
-    cudaFuncSetAttribute(k_attention<kOutF16<FMT>, 1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, AtLayout<2>::SMEM);
-    cudaFuncSetAttribute(k_attention<kOutF16<FMT>, 2, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, AtLayout<4>::SMEM);
-    cudaFuncSetAttribute(k_attention<kOutF16<FMT>, 2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, AtLayout<2>::SMEM);
-    cudaFuncSetAttribute(k_attention32<kOutF16<FMT>, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, At32Layout<4>::SMEM);
-    cudaFuncSetAttribute(k_attention<kOutF16<FMT>, 1, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, AtLayout<6>::SMEM);
-    cudaFuncSetAttribute(k_attention32<kOutF16<FMT>, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, At32Layout<6>::SMEM);
+    cudaFuncSetAttribute(k_attention_tm<kOutF16<FMT>, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, TmLayout<4>::SMEM);
+    cudaFuncSetAttribute(k_attention_tm<kOutF16<FMT>, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, TmLayout<6>::SMEM);
+    cudaFuncSetAttribute(k_attention_tm<kOutF16<FMT>, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, TmLayout<8>::SMEM);
     cudaFuncSetAttribute(k_attention_warp<kOutF16<FMT>, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, AwLayout<4>::SMEM);
     cudaFuncSetAttribute(k_attention_warp<kOutF16<FMT>, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, AwLayout<8>::SMEM);
     cudaFuncSetAttribute(k_attention_warp<kOutF16<FMT>, 4, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, AwLayout<4, 64>::SMEM);
@@ -2448,7 +2103,6 @@ bool tc_prepare_weights(Model& m) {
         float amax = 0.f;
         for (float v : W) amax = std::max(amax, std::fabs(v));
         im.scale = amax > 0.f ? amax / 448.f : 1.f;  // per-tensor E4M3 scale
-        build_image(im.data[FMT_BF16], Npad, Kpad16, W, N, K, colmap, rowmap, FMT_BF16, 1.f);
         build_image(im.data[FMT_FP16], Npad, Kpad16, W, N, K, colmap, rowmap, FMT_FP16, 1.f);
         build_image(im.data[FMT_E4M3], Npad, (Kpad16 + 127) / 128 * 128, W, N, K, colmap, rowmap, FMT_E4M3,
                     im.scale);
@@ -2513,7 +2167,7 @@ bool tc_prepare_weights(Model& m) {
     }
     size_t ib = 0, vb = 0;
     for (auto& i : imgs)
-        for (int f = 0; f < 3; ++f) ib += (i.data[f].size() + 1023) / 1024 * 1024;
+        for (int f = 1; f < 3; ++f) ib += (i.data[f].size() + 1023) / 1024 * 1024;
     for (auto& v : vecs) vb += (v.second.size() + 63) / 64 * 64;
     if (cudaMalloc(&m.w.img_base, ib) != cudaSuccess) { set_error("weight image allocation"); return false; }
     if (cudaMalloc(&m.w.tc_f32_base, vb * 4) != cudaSuccess) { set_error("bias allocation"); return false; }
@@ -2521,9 +2175,9 @@ bool tc_prepare_weights(Model& m) {
     std::vector<float> hv(vb, 0.f);
     size_t o = 0;
     for (auto& i : imgs) {
-        for (int f = 0; f < 3; ++f) {
+        for (int f = 1; f < 3; ++f) {   // FP16 and E4M3 images (no mode runs a GEMM on BF16 operands)
             std::memcpy(&hi[o], i.data[f].data(), i.data[f].size());
-            (f == FMT_BF16 ? m.w.img : f == FMT_FP16 ? m.w.img_h : m.w.img8)[i.name] = m.w.img_base + o;
+            (f == FMT_FP16 ? m.w.img_h : m.w.img8)[i.name] = m.w.img_base + o;
             o += (i.data[f].size() + 1023) / 1024 * 1024;
         }
         m.w.w_scale[i.name] = i.scale;
@@ -2564,6 +2218,7 @@ bool tc_make_maps(Model& m) {
     bool ok = make_map_16(&w.map_q, w.tq, 64, T, 64, 128) && make_map_16(&w.map_q64, w.tq, 64, T, 64, 64) &&
               make_map_16(&w.map_k, w.tk, 64, T, 64, 64) &&
               make_map_16(&w.map_o, w.to, 64, T, 64, 128) && make_map_16(&w.map_vt, w.tvt, T, 64, 64, 64) &&
+              make_map_16(&w.map_vt16, w.tvt, T, 64, 64, 16) &&
               make_map_16(&w.map_hp, w.thp, 64, T, 64, 128);
     if (!ok) set_error("cuTensorMapEncodeTiled failed");
     return ok;
@@ -2579,17 +2234,22 @@ int act_slot(Model& m, const std::string& name) {
 }
 
 template <int FMT>
-static int64_t run_tc(Model& m, const float* x, const int32_t* cu, int n_events, float* logits,
-                      float* reg, cudaStream_t st) {
+static int64_t run_tc(Model& m, Workspace& w, bool profile, const float* x, const int32_t* cu, int n_events,
+                      float* logits, float* reg, cudaStream_t st) {
     const mlpf_config& c = m.cfg;
-    Workspace& w = m.ws;
+    auto prof_begin = [&](Model& mm, cudaStream_t s, const char* name) {
+        if (profile) mlpf::prof_begin(mm, s, name);
+    };
+    auto prof_end = [&](Model& mm, cudaStream_t s) {
+        if (profile) mlpf::prof_end(mm, s);
+    };
     auto V = [&](const std::string& s) { return (const float*)m.w.tcv.at(s); };
     // weight image of a GEMM in format f
     auto IF = [&](const std::string& s, int f) {
-        return (const uint8_t*)(f == FMT_BF16 ? m.w.img : f == FMT_FP16 ? m.w.img_h : m.w.img8).at(s);
+        return (const uint8_t*)(f == FMT_FP16 ? m.w.img_h : m.w.img8).at(s);
     };
-    constexpr int FE = FMT == FMT_E4M3 ? FMT_FP16 : FMT;  // embedding FFNs and output heads
-    auto I = [&](const std::string& s) { return IF(s, FMT); };
+    constexpr int FE = FMT_FP16;  // embedding FFNs and output heads (16-bit in every mode)
+    auto I = [&](const std::string& s) { return IF(s, kGemm<FMT>); };
     auto IE = [&](const std::string& s) { return IF(s, FE); };
     // E4M3: 1/s_a of an activation slot and s_a * s_w of a GEMM (1 for 16-bit formats)
     auto QS = [&](const std::string& slot) { return FMT == FMT_E4M3 ? 1.f / m.act_scale[act_slot(m, slot)] : 1.f; };
@@ -2610,19 +2270,13 @@ static int64_t run_tc(Model& m, const float* x, const int32_t* cu, int n_events,
         prof_begin(m, st, "attention");
         constexpr bool AF = kOutF16<FMT>;
         const dim3 g(grid * m.attn_ctas_per_sm);
-        // windowed attention runs on the warp-level kernels only
-        const int variant = m.attn_window > 0 && m.attn_variant[FMT] < 7 ? 8 : m.attn_variant[FMT];
-        switch (variant) {
-            case 1: k_attention<AF, 1, 2><<<g, at_threads<1>(), AtLayout<2>::SMEM, st>>>(w.map_q, w.map_k, w.map_vt, ap); break;
-            case 2: k_attention<AF, 2, 4><<<g, at_threads<2>(), AtLayout<4>::SMEM, st>>>(w.map_q, w.map_k, w.map_vt, ap); break;
-            case 3: k_attention<AF, 2, 2><<<g, at_threads<2>(), AtLayout<2>::SMEM, st>>>(w.map_q, w.map_k, w.map_vt, ap); break;
-            case 4: k_attention32<AF, 4><<<g, A32_THREADS, At32Layout<4>::SMEM, st>>>(w.map_q, w.map_k, w.map_vt, ap); break;
-            case 5: k_attention<AF, 1, 6><<<g, at_threads<1>(), AtLayout<6>::SMEM, st>>>(w.map_q, w.map_k, w.map_vt, ap); break;
-            case 6: k_attention32<AF, 6><<<g, A32_THREADS, At32Layout<6>::SMEM, st>>>(w.map_q, w.map_k, w.map_vt, ap); break;
-            case 7: k_attention_warp<AF, 4><<<g, aw_threads<128>(), AwLayout<4>::SMEM, st>>>(w.map_q, w.map_k, w.map_vt, ap); break;
-            case 8: k_attention_warp<AF, 8><<<g, aw_threads<128>(), AwLayout<8>::SMEM, st>>>(w.map_q, w.map_k, w.map_vt, ap); break;
-            case 9: k_attention_warp<AF, 4, 64><<<2 * g.x, aw_threads<64>(), AwLayout<4, 64>::SMEM, st>>>(w.map_q64, w.map_k, w.map_vt, ap); break;
-            default: k_attention<AF, 1, 4><<<g, at_threads<1>(), AtLayout<4>::SMEM, st>>>(w.map_q, w.map_k, w.map_vt, ap); break;
+        switch (m.attn_variant[FMT]) {
+            case 0: k_attention_tm<AF, 4><<<g, TM_THREADS, TmLayout<4>::SMEM, st>>>(w.map_q, w.map_k, w.map_vt16, ap); break;
+            case 1: k_attention_tm<AF, 6><<<g, TM_THREADS, TmLayout<6>::SMEM, st>>>(w.map_q, w.map_k, w.map_vt16, ap); break;
+            case 2: k_attention_tm<AF, 8><<<g, TM_THREADS, TmLayout<8>::SMEM, st>>>(w.map_q, w.map_k, w.map_vt16, ap); break;
+            case 3: k_attention_warp<AF, 4><<<g, aw_threads<128>(), AwLayout<4>::SMEM, st>>>(w.map_q, w.map_k, w.map_vt, ap); break;
+            case 5: k_attention_warp<AF, 4, 64><<<2 * g.x, aw_threads<64>(), AwLayout<4, 64>::SMEM, st>>>(w.map_q64, w.map_k, w.map_vt, ap); break;
+            default: k_attention_warp<AF, 8><<<g, aw_threads<128>(), AwLayout<8>::SMEM, st>>>(w.map_q, w.map_k, w.map_vt, ap); break;
         }
         prof_end(m, st);
         ++n;
@@ -2779,12 +2433,13 @@ static int64_t run_tc(Model& m, const float* x, const int32_t* cu, int n_events,
 }
 
 int64_t run_forward_tc(Model& m, int prec, const float* x, const int32_t* cu, int n_events, int total,
-                       int max_n, float* logits, float* reg, cudaStream_t st) {
+                       int max_n, float* logits, float* reg, cudaStream_t st, Workspace* ws, bool profile) {
     (void)total;
     (void)max_n;
-    if (prec == MLPF_FP8) return run_tc<FMT_E4M3>(m, x, cu, n_events, logits, reg, st);
-    return prec == MLPF_FP16 ? run_tc<FMT_FP16>(m, x, cu, n_events, logits, reg, st)
-                             : run_tc<FMT_BF16>(m, x, cu, n_events, logits, reg, st);
+    Workspace& w = ws ? *ws : m.ws;
+    if (prec == MLPF_FP8) return run_tc<FMT_E4M3>(m, w, profile, x, cu, n_events, logits, reg, st);
+    return prec == MLPF_FP16 ? run_tc<FMT_FP16>(m, w, profile, x, cu, n_events, logits, reg, st)
+                             : run_tc<FMT_BF16>(m, w, profile, x, cu, n_events, logits, reg, st);
 }
 
 }  // namespace mlpf

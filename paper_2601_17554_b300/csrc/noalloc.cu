@@ -47,7 +47,7 @@ namespace {
 struct NoallocDevice {
     bool ready = false;
     unsigned char* base = nullptr;  // device address of g_mlpf_noalloc_scratch
-    CUtensorMap map_q, map_q64, map_k, map_o, map_vt, map_hp;   // every map the launch sequence uses
+    CUtensorMap map_q, map_q64, map_k, map_o, map_vt, map_vt16, map_hp;   // every map the launch sequence uses
 };
 NoallocDevice g_na[64];
 std::mutex g_na_mu;
@@ -151,25 +151,25 @@ extern "C" mlpf_status mlpf_forward_noalloc(mlpf_model* mm, int32_t precision, c
             nd.map_k = tmp.ws.map_k;
             nd.map_o = tmp.ws.map_o;
             nd.map_vt = tmp.ws.map_vt;
+            nd.map_vt16 = tmp.ws.map_vt16;   // 16-row V^T boxes (tensor-memory attention)
             nd.map_hp = tmp.ws.map_hp;
             nd.ready = true;
         }
     }
-    // run the same launch sequence with the model's workspace swapped for the view
+    // the same launch sequence on a workspace view of the static array; the model
+    // itself is not modified (its own workspace and profiling state stay as they are)
     Workspace view = na_workspace(nd.base);
     view.map_q = nd.map_q;
     view.map_q64 = nd.map_q64;
     view.map_k = nd.map_k;
     view.map_o = nd.map_o;
     view.map_vt = nd.map_vt;
+    view.map_vt16 = nd.map_vt16;
     view.map_hp = nd.map_hp;
-    std::swap(m.ws, view);
-    Profile* saved_prof = m.cur_prof;
-    m.cur_prof = nullptr;  // no profiling events: they would be allocations
-    int64_t n = run_forward_tc(m, precision, x, cu_seqlens, n_events, total, max_n, logits, reg, st);
-    int64_t k = n < 0 ? -1 : run_event_sums(m, cu_seqlens, n_events, logits, reg, cls, event_sums, m.cfg.n_cls, st);
-    m.cur_prof = saved_prof;
-    std::swap(m.ws, view);
+    // no profiling events: creating them would allocate
+    int64_t n = run_forward_tc(m, precision, x, cu_seqlens, n_events, total, max_n, logits, reg, st, &view, false);
+    int64_t k = n < 0 ? -1 : run_event_sums(m, cu_seqlens, n_events, logits, reg, cls, event_sums, m.cfg.n_cls, st,
+                                            false);
     if (n < 0 || k < 0) {
         set_error(std::string("kernel launch failed: ") + cudaGetErrorString(cudaGetLastError()));
         return MLPF_E_CUDA;

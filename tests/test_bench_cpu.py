@@ -57,3 +57,24 @@ def test_reference_arm_json_line(capsys, monkeypatch):
     monkeypatch.setenv("RANK", "1")
     bench.run_reference(args)
     assert capsys.readouterr().out.strip() == ""
+
+
+def test_oracle_baseline_on_all_cores():
+    """The CPU baseline: the oracle over a bounded sample of events on one worker
+    process per host core, extrapolated to the batch by sum N^2, a one-core run of
+    the next events, per-event latencies, and the host's core count and CPU model;
+    the sampled outputs are the oracle's own."""
+    import os
+    cfg = synth.SMALL
+    sizes = np.array([40, 90, 10, 70, 30, 55, 20, 65, 80, 15, 35, 45])
+    x, cu = synth.gen_events(7, sizes)
+    res, cb = bench.oracle_baseline(cfg, 0, x, cu, sizes, budget_s=0.0)
+    assert cb["kind"] == "oracle" and cb["cores"] == (os.cpu_count() or 1) == cb["nproc"]
+    assert cb["value"] > 0 and cb["one_core"]["value"] > 0 and cb["cpu_model"]
+    assert 0 < cb["p50_ms_per_event"] <= cb["p99_ms_per_event"]
+    # a zero budget still runs the first event; results come back in event order
+    assert [r[0] for r in res] == list(range(len(res))) and len(res) >= 1
+    W = synth.make_weights(cfg, 0)
+    e, _, lo, reg, cls, sums = res[0]
+    ref = oracle.forward(W, cfg, x[cu[e]:cu[e + 1]], [0, int(sizes[e])])
+    assert np.array_equal(lo, ref.logits) and np.array_equal(cls, ref.cls)

@@ -25,10 +25,13 @@ from tests.util import rel_err_cols, run_gpu
 pytestmark = pytest.mark.gpu
 
 SIZES = [1000, 4097, 300, 65, 129, 64, 1]
-# measured: x 1.4: FP16 99.97 % / 1.7e-3, BF16 99.63 % / 1.24e-2; x 2: FP16 99.98 % /
-# 2.3e-3, BF16 99.47 % / 1.98e-2
-BOUNDS = {("fp16", 1.4): (0.999, 5e-3), ("bf16", 1.4): (0.993, 2e-2),
-          ("fp16", 2.0): (0.999, 5e-3), ("bf16", 2.0): (0.99, 3e-2)}
+# The specified bounds (>= 99.9 % argmax agreement, <= 1e-2 regression error), except
+# BF16 at Q and K x 2: scores four times larger than the model's make the BF16
+# rounding of Q and K (an error proportional to the score) cost more; the float64
+# emulation of the BF16 mode's roundings (tests/lowp_emul.py) gives 99.77 % and
+# 6.5e-3 on exactly these inputs, and the floor allows four flips more (of 5656).
+BOUNDS = {("fp16", 1.4): (0.999, 1e-2), ("bf16", 1.4): (0.999, 1e-2),
+          ("fp16", 2.0): (0.999, 1e-2), ("bf16", 2.0): (0.997, 1e-2)}
 
 
 def scaled_model(f):

@@ -1,10 +1,9 @@
 """Attention kernel variants and the autotuner (through the C ABI).
 
 Variants in one group run the same per-head arithmetic in the same order and
-must be bit-identical: the tcgen05 kernels with 64-key score tiles (one or two
-heads per warpgroup, two to six K/V stages), the tcgen05 kernels with 32-key
-tiles, and the warp-level-MMA kernels (four or eight stages, 128- or 64-row
-items).  Groups differ in
+must be bit-identical: the tcgen05 kernels with S and P in tensor memory (four,
+six or eight K/V stages) and the warp-level-MMA kernels (four or eight stages,
+128- or 64-row items).  Groups differ in
 summation order and exponent references: each must meet the oracle bounds of
 the precision and stay close to variant 0.  The autotuner must pick a valid
 variant, write its cache line and reuse it.
@@ -19,8 +18,8 @@ from tests.util import make_model, rel_err_cols, run_gpu
 pytestmark = pytest.mark.gpu
 
 SIZES = [1, 17, 64, 65, 129, 300, 0, 511, 1024, 2]
-N_VARIANTS = 10
-GROUPS = ((0, 1, 2, 3, 5), (4, 6), (7, 8, 9))
+N_VARIANTS = 6
+GROUPS = ((0, 1, 2), (3, 4, 5))
 
 
 @pytest.fixture(scope="module")
@@ -29,14 +28,14 @@ def model():
 
 
 @pytest.mark.parametrize("precision,opt,argmax_min,reg_tol", [
-    ("bf16", 7, 0.99, 3e-2), ("fp16", 8, 0.995, 1.5e-2)])
+    ("bf16", 7, 0.999, 1e-2), ("fp16", 8, 0.999, 1e-2)])
 def test_variants_identical(model, precision, opt, argmax_min, reg_tol):
     m, w = model
     x, cu = synth.gen_events(77, SIZES)
     ref = oracle.forward(w, synth.SMALL, x, cu)
     outs = []
     default = m.get_option(opt)
-    assert default == 8   # warp-level MMAs, 8 K/V stages
+    assert default == 4   # warp-level MMAs, 8 K/V stages
     try:
         for v in range(N_VARIANTS):
             m.set_option(opt, v)
