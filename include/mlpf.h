@@ -331,6 +331,39 @@ mlpf_status mlpf_trainer_step_supervised(mlpf_trainer* t, const float* x, const 
 mlpf_status mlpf_trainer_export(const mlpf_trainer* t, void* blob, size_t cap, size_t* nbytes);
 
 /*
+ * The trainer's forward and backward as separate calls, for frameworks that own
+ * the loss and the optimizer (torch.autograd.Function; the paper trains with
+ * LAMB, Sec. 5.3, which mlpf_trainer_step runs itself).
+ *
+ * mlpf_trainer_forward: the hand-written FP32 forward of the trainer's model on a
+ * packed batch (device buffers as in mlpf_forward, at least one event and one
+ * element), keeping every activation the backward needs in the trainer.
+ *   logits  device out, [total, 6] float32 class scores;
+ *   raw     device out, [total, 5] float32 raw head outputs (pT', eta, sin phi,
+ *           cos phi, E'; decoded pT = exp(x[:,8] + pT'), E = exp(x[:,9] + E')).
+ * mlpf_trainer_backward: the gradient of a scalar loss with respect to every
+ * parameter, from dL/dlogits and dL/draw (device, [total, 6] and [total, 5]
+ * float32), through the hand-written backward kernels (GEMM, LayerNorm, GELU, and
+ * varlen attention recomputing the probabilities from Q, K and the saved row
+ * log-sum-exp).  It must follow mlpf_trainer_forward on the same batch (the same
+ * x and cu_seqlens pointers and sizes) with no other forward or step in between,
+ * else MLPF_E_INVALID.  grads_out: device out, [num_params] float32 in blob tensor
+ * order (overwritten).
+ * mlpf_trainer_params: device copies of the flat parameter vector ([num_params]
+ * float32, blob tensor order): `get` (or NULL) receives the current parameters,
+ * then `set` (or NULL) replaces them.
+ * All three are asynchronous on `stream`.
+ */
+mlpf_status mlpf_trainer_forward(mlpf_trainer* t, const float* x, const int32_t* cu_seqlens,
+                                 int32_t n_events, int32_t total, int32_t max_n,
+                                 float* logits, float* raw, void* stream);
+mlpf_status mlpf_trainer_backward(mlpf_trainer* t, const float* x, const int32_t* cu_seqlens,
+                                  int32_t n_events, int32_t total, int32_t max_n,
+                                  const float* dlogits, const float* draw, float* grads_out,
+                                  void* stream);
+mlpf_status mlpf_trainer_params(mlpf_trainer* t, float* get, const float* set, void* stream);
+
+/*
  * Wait for the model's work on `stream` and report device-side status:
  * MLPF_E_TIMEOUT if a bounded wait inside a kernel ran out since the last
  * mlpf_sync (the kernel returned early; outputs are invalid), otherwise

@@ -22,7 +22,8 @@ EXPORTS = ("mlpf_load_weights", "mlpf_free", "mlpf_get_config", "mlpf_forward",
            "mlpf_trainer_free", "mlpf_trainer_num_params", "mlpf_trainer_step",
            "mlpf_trainer_step_supervised", "mlpf_trainer_export", "mlpf_sync", "mlpf_set_option", "mlpf_get_option",
            "mlpf_last_launch_count", "mlpf_profile_get", "mlpf_last_error", "mlpf_abi_version",
-           "mlpf_cluster_jets", "mlpf_measure_ex2_packed_rate")
+           "mlpf_cluster_jets", "mlpf_measure_ex2_packed_rate", "mlpf_trainer_forward",
+           "mlpf_trainer_backward", "mlpf_trainer_params")
 
 
 class MlpfConfig(ctypes.Structure):
@@ -89,6 +90,12 @@ def load(build_if_missing: bool = True):
                                                ctypes.c_float, ctypes.c_float, ctypes.c_float, i32, vp,
                                                ctypes.POINTER(ctypes.c_double), vp]
     L.mlpf_trainer_step_supervised.restype = ctypes.c_int
+    L.mlpf_trainer_forward.argtypes = [vp, vp, vp, i32, i32, i32, vp, vp, vp]
+    L.mlpf_trainer_forward.restype = ctypes.c_int
+    L.mlpf_trainer_backward.argtypes = [vp, vp, vp, i32, i32, i32, vp, vp, vp, vp]
+    L.mlpf_trainer_backward.restype = ctypes.c_int
+    L.mlpf_trainer_params.argtypes = [vp, vp, vp, vp]
+    L.mlpf_trainer_params.restype = ctypes.c_int
     L.mlpf_trainer_export.argtypes = [vp, vp, sz, ctypes.POINTER(sz)]
     L.mlpf_trainer_export.restype = ctypes.c_int
     L.mlpf_sync.argtypes = [vp, vp]

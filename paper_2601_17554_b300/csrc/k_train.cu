@@ -562,6 +562,12 @@ struct Trainer {
     size_t cap_rows = 0;
     float* act = nullptr;
     size_t act_floats = 0;
+    // the batch whose activations the workspace holds after mlpf_trainer_forward (the
+    // batch mlpf_trainer_backward must be called on); fwd_ok is cleared by any step
+    bool fwd_ok = false;
+    const float* fwd_x = nullptr;
+    const int32_t* fwd_cu = nullptr;
+    int32_t fwd_n = 0, fwd_total = 0;
 };
 
 namespace {
@@ -878,6 +884,21 @@ struct mlpf_trainer {
         }                                                                           \
     } while (0)
 
+// Activation workspace for `total` rows (grown, never shrunk).
+static mlpf_status ensure_acts(Trainer& t, int32_t total) {
+    if ((size_t)total > t.cap_rows) {
+        const size_t rows = std::max<size_t>(total, t.cap_rows * 5 / 4);
+        if (t.act) cudaFree(t.act);
+        t.act = nullptr;
+        t.cap_rows = 0;
+        const size_t n = acts_layout(t.m.cfg, rows, nullptr, nullptr);
+        TCK(cudaMalloc(&t.act, n * sizeof(float)));
+        t.cap_rows = rows;
+        t.act_floats = n;
+    }
+    return MLPF_OK;
+}
+
 // One step: forward, `loss` (fills a.dlog, a.draw and the loss accumulator), backward,
 // optional LAMB update.
 template <typename LossFn>
@@ -887,15 +908,9 @@ static mlpf_status trainer_step_impl(mlpf_trainer* tt, const float* x, const int
     Trainer& t = tt->t;
     cudaStream_t st = (cudaStream_t)stream;
     TCK(cudaSetDevice(t.m.device));
-    if ((size_t)total > t.cap_rows) {
-        if (t.act) cudaFree(t.act);
-        t.act = nullptr;
-        const size_t rows = std::max<size_t>(total, t.cap_rows * 5 / 4);
-        const size_t n = acts_layout(t.m.cfg, rows, nullptr, nullptr);
-        TCK(cudaMalloc(&t.act, n * sizeof(float)));
-        t.cap_rows = rows;
-        t.act_floats = n;
-    }
+    t.fwd_ok = false;
+    const mlpf_status rs = ensure_acts(t, total);
+    if (rs != MLPF_OK) return rs;
     Acts a;
     acts_layout(t.m.cfg, t.cap_rows, &a, t.act);
     TCK(cudaMemsetAsync(t.g, 0, t.n_params * 4, st));
@@ -1042,6 +1057,79 @@ mlpf_status mlpf_trainer_step_supervised(mlpf_trainer* tt, const float* x, const
                                                              acc);
     };
     return trainer_step_impl(tt, x, cu, n_events, total, max_n, loss, lr, update, grads_out, loss_out, stream);
+}
+
+static mlpf_status check_batch(const mlpf_trainer* tt, const float* x, const int32_t* cu, int32_t n_events,
+                               int32_t total, int32_t max_n) {
+    if (!tt) { set_error("trainer is NULL"); return MLPF_E_INVALID; }
+    if (n_events < 1 || total < 1 || max_n < 1 || max_n > 65536 || !x || !cu) {
+        set_error("bad batch (the trainer needs at least one event and one element)");
+        return MLPF_E_INVALID;
+    }
+    return MLPF_OK;
+}
+
+mlpf_status mlpf_trainer_forward(mlpf_trainer* tt, const float* x, const int32_t* cu, int32_t n_events,
+                                 int32_t total, int32_t max_n, float* logits, float* raw, void* stream) {
+    mlpf_status s = check_batch(tt, x, cu, n_events, total, max_n);
+    if (s != MLPF_OK) return s;
+    if (!logits || !raw) { set_error("NULL output"); return MLPF_E_INVALID; }
+    Trainer& t = tt->t;
+    cudaStream_t st = (cudaStream_t)stream;
+    TCK(cudaSetDevice(t.m.device));
+    t.fwd_ok = false;
+    s = ensure_acts(t, total);
+    if (s != MLPF_OK) return s;
+    Acts a;
+    acts_layout(t.m.cfg, t.cap_rows, &a, t.act);
+    train_forward(t, a, x, cu, n_events, total, max_n, st);
+    TCK(cudaMemcpyAsync(logits, a.logits, (size_t)total * 6 * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    TCK(cudaMemcpyAsync(raw, a.raw, (size_t)total * 5 * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    TCK(cudaGetLastError());
+    t.fwd_ok = true;
+    t.fwd_x = x;
+    t.fwd_cu = cu;
+    t.fwd_n = n_events;
+    t.fwd_total = total;
+    return MLPF_OK;
+}
+
+mlpf_status mlpf_trainer_backward(mlpf_trainer* tt, const float* x, const int32_t* cu, int32_t n_events,
+                                  int32_t total, int32_t max_n, const float* dlogits, const float* draw,
+                                  float* grads_out, void* stream) {
+    mlpf_status s = check_batch(tt, x, cu, n_events, total, max_n);
+    if (s != MLPF_OK) return s;
+    if (!dlogits || !draw || !grads_out) { set_error("NULL gradient pointer"); return MLPF_E_INVALID; }
+    Trainer& t = tt->t;
+    if (!t.fwd_ok || t.fwd_x != x || t.fwd_cu != cu || t.fwd_n != n_events || t.fwd_total != total) {
+        set_error("mlpf_trainer_backward needs the activations of mlpf_trainer_forward on the same batch "
+                  "(no other forward or step in between)");
+        return MLPF_E_INVALID;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    TCK(cudaSetDevice(t.m.device));
+    Acts a;
+    acts_layout(t.m.cfg, t.cap_rows, &a, t.act);
+    TCK(cudaMemcpyAsync(a.dlog, dlogits, (size_t)total * 6 * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    TCK(cudaMemcpyAsync(a.draw, draw, (size_t)total * 5 * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    TCK(cudaMemsetAsync(t.g, 0, t.n_params * 4, st));
+    train_backward(t, a, x, cu, n_events, total, max_n, st);
+    TCK(cudaMemcpyAsync(grads_out, t.g, t.n_params * 4, cudaMemcpyDeviceToDevice, st));
+    TCK(cudaGetLastError());
+    return MLPF_OK;
+}
+
+mlpf_status mlpf_trainer_params(mlpf_trainer* tt, float* get, const float* set, void* stream) {
+    if (!tt) { set_error("trainer is NULL"); return MLPF_E_INVALID; }
+    Trainer& t = tt->t;
+    cudaStream_t st = (cudaStream_t)stream;
+    TCK(cudaSetDevice(t.m.device));
+    if (get) TCK(cudaMemcpyAsync(get, t.w, t.n_params * 4, cudaMemcpyDeviceToDevice, st));
+    if (set) {
+        TCK(cudaMemcpyAsync(t.w, set, t.n_params * 4, cudaMemcpyDeviceToDevice, st));
+        t.fwd_ok = false;
+    }
+    return MLPF_OK;
 }
 
 mlpf_status mlpf_trainer_export(const mlpf_trainer* tt, void* blob, size_t cap, size_t* nbytes) {

@@ -7,11 +7,10 @@ model) and against torch float64 autograd of the same loss.
 import numpy as np
 import pytest
 import torch
-import torch.nn.functional as F
 
 import oracle
 import synth
-from tests.util import run_gpu
+from tests.util import f64_distill_reference, run_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -84,43 +83,13 @@ def test_gradients_match_oracle_finite_differences(tiny_case):
 
 def test_gradients_match_torch_autograd(tiny_case):
     W, x, cu, tl, tr, loss, G = tiny_case
-    cfg = TINY
-    P = {k: torch.tensor(np.asarray(v, np.float64), requires_grad=True) for k, v in W.items()}
-    act = lambda t: F.gelu(t, approximate="none")
-    mlp = lambda t, p: F.linear(act(F.linear(t, P[p + "w1"], P[p + "b1"])), P[p + "w2"], P[p + "b2"])
-    ln = lambda t, p: F.layer_norm(t, (cfg.d,), P[p + ".g"], P[p + ".b"], eps=1e-5)
-
-    def stack(z, pre, n):
-        for l in range(n):
-            p = f"{pre}.{l}."
-            zn = ln(z, p + "ln1")
-            split = lambda t: t.view(-1, cfg.heads, cfg.dh).transpose(0, 1)
-            q, k, v = (split(F.linear(zn, P[p + "w" + c], P[p + "b" + c])) for c in "qkv")
-            o = F.scaled_dot_product_attention(q, k, v).transpose(0, 1).reshape(-1, cfg.d)
-            z = z + F.linear(o, P[p + "wo"], P[p + "bo"])
-            z = z + F.linear(act(F.linear(ln(z, p + "ln2"), P[p + "ffn.w1"], P[p + "ffn.b1"])),
-                             P[p + "ffn.w2"], P[p + "ffn.b2"])
-        return ln(z, pre + ".lnf")
-
-    total = 0.0
-    for e in range(len(cu) - 1):
-        xe = torch.tensor(x[cu[e]:cu[e + 1]], dtype=torch.float64)
-        hp = stack(mlp(xe, "emb."), "pid", cfg.l_pid)
-        hr = stack(mlp(torch.cat([xe, hp], 1), "remb."), "reg", cfg.l_reg)
-        logits = mlp(hp, "head.cls.")
-        raw = torch.cat([mlp(hr, f"head.{n}.") for n, _ in synth.REG_HEADS], 1)
-        tlog = torch.tensor(tl[cu[e]:cu[e + 1]], dtype=torch.float64)
-        traw = torch.tensor(oracle.raw_from_decoded(x[cu[e]:cu[e + 1]], tr[cu[e]:cu[e + 1]]))
-        lt = F.log_softmax(tlog, 1)
-        kl = (lt.exp() * (lt - F.log_softmax(logits, 1))).sum(1)
-        total = total + (kl + ((raw - traw) ** 2).sum(1)).sum()
-    (total / x.shape[0]).backward()
+    _, ref_g = f64_distill_reference(W, TINY, x, cu, tl, tr)
     # The key bias has an exactly zero gradient (the softmax of a row is invariant to
     # a constant added to all its scores), so errors are taken relative to
     # max(|grad of the tensor|, 1e-3 |whole gradient|).
-    gnorm = np.sqrt(sum(np.linalg.norm(P[n].grad.numpy()) ** 2 for n in W))
+    gnorm = np.sqrt(sum(np.linalg.norm(ref_g[n]) ** 2 for n in W))
     for name in W:
-        ref = P[name].grad.numpy()
+        ref = ref_g[name]
         err = np.linalg.norm(G[name] - ref) / max(np.linalg.norm(ref), 1e-3 * gnorm)
         assert err <= 1e-4, (name, err)
 

@@ -39,3 +39,47 @@ def make_model(cfg, seed, perturbed=False, cls_scale=1.0):
     from paper_2601_17554_b300 import Model
     w = synth.make_weights(cfg, seed, perturbed=perturbed, cls_scale=cls_scale)
     return Model(synth.pack_blob(cfg, w)), w
+
+
+def f64_distill_reference(W, cfg, x, cu, tl, tr):
+    """The distillation loss of a sequential-architecture model and its gradient
+    from an independent torch float64 model (torch.nn.functional layers, exact
+    scaled-dot-product attention, autograd).  Returns (loss, {name: grad})."""
+    import torch
+    import torch.nn.functional as F
+
+    import oracle
+    P = {k: torch.tensor(np.asarray(v, np.float64), requires_grad=True) for k, v in W.items()}
+    act = (lambda t: F.relu(t)) if cfg.act == 1 else (lambda t: F.gelu(t, approximate="none"))
+    mlp = lambda t, p: F.linear(act(F.linear(t, P[p + "w1"], P[p + "b1"])), P[p + "w2"], P[p + "b2"])
+    ln = lambda t, p: F.layer_norm(t, (cfg.d,), P[p + ".g"], P[p + ".b"], eps=1e-5)
+
+    def stack(z, pre, n):
+        for l in range(n):
+            p = f"{pre}.{l}."
+            zn = ln(z, p + "ln1")
+            split = lambda t: t.view(-1, cfg.heads, cfg.dh).transpose(0, 1)
+            q, k, v = (split(F.linear(zn, P[p + "w" + c], P[p + "b" + c])) for c in "qkv")
+            o = F.scaled_dot_product_attention(q, k, v).transpose(0, 1).reshape(-1, cfg.d)
+            z = z + F.linear(o, P[p + "wo"], P[p + "bo"])
+            z = z + F.linear(act(F.linear(ln(z, p + "ln2"), P[p + "ffn.w1"], P[p + "ffn.b1"])),
+                             P[p + "ffn.w2"], P[p + "ffn.b2"])
+        return ln(z, pre + ".lnf")
+
+    total = 0.0
+    for e in range(len(cu) - 1):
+        if cu[e + 1] == cu[e]:
+            continue
+        xe = torch.tensor(x[cu[e]:cu[e + 1]], dtype=torch.float64)
+        hp = stack(mlp(xe, "emb."), "pid", cfg.l_pid)
+        hr = stack(mlp(torch.cat([xe, hp], 1), "remb."), "reg", cfg.l_reg)
+        logits = mlp(hp, "head.cls.")
+        raw = torch.cat([mlp(hr, f"head.{n}.") for n, _ in synth.REG_HEADS], 1)
+        tlog = torch.tensor(tl[cu[e]:cu[e + 1]], dtype=torch.float64)
+        traw = torch.tensor(oracle.raw_from_decoded(x[cu[e]:cu[e + 1]], tr[cu[e]:cu[e + 1]]))
+        lt = F.log_softmax(tlog, 1)
+        kl = (lt.exp() * (lt - F.log_softmax(logits, 1))).sum(1)
+        total = total + (kl + ((raw - traw) ** 2).sum(1)).sum()
+    loss = total / x.shape[0]
+    loss.backward()
+    return float(loss.detach()), {n: P[n].grad.numpy() for n in W}
