@@ -490,14 +490,21 @@ def run_ours(args):
     roof = None
     if att_ms:
         ach = exps / (att_ms / 1000.0)
-        exp_peak = unit_rates["ex2_per_s"]
-        kname = {3: "k_attention_warp", 4: "k_attention_warp",
-                 5: "k_attention_warp (64-row items)"}.get(attn_variant, "k_attention_tm")
+        # the 16-bit attention kernels take their exponentials two at a time
+        # (ex2.bf16x2 / ex2.f16x2): the MUFU bound is the packed rate
+        packed = prec in ("bf16", "fp16", "fp8")
+        exp_peak = unit_rates["ex2_bf16x2_per_s"] if packed else unit_rates["ex2_per_s"]
+        kname = {3: "k_attention_warp", 4: "k_attention_warp", 5: "k_attention_warp (64-row items)",
+                 6: "k_attention_warp (QK^T on tcgen05)",
+                 7: "k_attention_warp (QK^T on tcgen05)"}.get(attn_variant, "k_attention_tm")
         roof = {"kernel": kname, "attn_variant": attn_variant, "bound": "alu", "achieved": ach / 1e9,
                 "peak": exp_peak / 1e9, "unit": "Gexp/s", "frac": ach / exp_peak,
                 "traffic": attention_traffic(attn_variant, prec),
-                "peak_source": "measured: mlpf_measure_unit_rates (ex2.approx.f32 results/s on this GPU, "
-                               "best of 3, timed alone)",
+                "peak_source": ("measured: mlpf_measure_ex2_packed_rate (ex2.approx.ftz.bf16x2, two results per "
+                                "instruction, results/s on this GPU, best of 3, timed alone)") if packed else
+                               "measured: mlpf_measure_unit_rates (ex2.approx.f32 results/s on this GPU, best of 3, "
+                               "timed alone)",
+                "frac_of_ex2_f32_rate": ach / unit_rates["ex2_per_s"],
                 "launch_ms": att_ms,
                 "algorithmic_exps_per_launch": exps,
                 "fp32_fma_peak_per_s": unit_rates["ffma_per_s"],

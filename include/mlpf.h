@@ -390,7 +390,11 @@ enum {
                                        warp-level MMAs, each warp 32 rows of one head:
                                          3 = 4 stages, 4 = 8 stages (default);
                                        the same on 64-row half items, two CTAs per SM,
-                                       4 stages: 5 */
+                                       4 stages: 5;
+                                       warp-level PV with QK^T on tcgen05 (S in two
+                                       tensor-memory buffers per head, read in the
+                                       warp-level accumulator layout):
+                                         6 = 4 stages, 7 = 8 stages */
     MLPF_OPT_ATTN_VARIANT_FP16 = 8,
     MLPF_OPT_ATTN_VARIANT_FP8 = 9,
     MLPF_OPT_ATTN_WINDOW = 10,      /* 0 (default): full attention within each event.
@@ -419,7 +423,7 @@ enum {
                                        a chunk's last attention items overlap the next
                                        chunk's kernels.  The results do not depend on it. */
 };
-#define MLPF_ATTN_VARIANTS 6
+#define MLPF_ATTN_VARIANTS 8
 mlpf_status mlpf_set_option(mlpf_model* m, int32_t option, int64_t value);
 mlpf_status mlpf_get_option(const mlpf_model* m, int32_t option, int64_t* value);
 

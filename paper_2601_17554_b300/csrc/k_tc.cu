@@ -1167,23 +1167,31 @@ MLPF_DEV bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* ab, unsign
 // the exponent itself (no per-score multiply-add).
 // QR: query rows per work item, 128 (one CTA per SM, 16 consumer warps) or 64
 // (half items, two CTAs per SM of 8 consumer warps).
-template <int QR>
-constexpr int aw_threads() { return NH * (QR / 32) * 32 + 32; }   // consumer warps + a TMA producer warp
+// HY (QR = 128 only): QK^T on the tensor cores instead: an MMA warp issues, per head
+// and key tile, S = Q_h K_h^T (tcgen05, M 128, N 64, K 16) into one of two tensor-
+// memory buffers per head (4 heads x 2 x 64 columns = 512), and each consumer warp
+// loads its 32 rows of S with tcgen05.ld.16x256b, whose thread layout is the m16n8
+// accumulator layout of the PV MMA's inputs; the references are subtracted with
+// packed FP32 adds.  The QK^T MMAs (four of the ten warp-level MMAs per warp and
+// 16-key step) leave the legacy tensor pipe, which bounds the kernel otherwise.
+template <int QR, bool HY = false>
+constexpr int aw_threads() { return NH * (QR / 32) * 32 + 32 + (HY ? 32 : 0); }   // consumers, TMA warp, MMA warp
 template <int ST, int QR = 128>
 struct AwLayout {
     static constexpr uint32_t QB = QR * 128;   // Q tile bytes
     static constexpr uint32_t OFF_K = 2 * QB;
     static constexpr uint32_t OFF_V = OFF_K + ST * AT_KB;
-    static constexpr uint32_t OFF_BAR = OFF_V + ST * AT_VB;   // barriers, item info, abort flag (< 256 B)
-    static constexpr uint32_t OFF_KN = OFF_BAR + 256;         // [ST][4] key-tile norm bounds
+    static constexpr uint32_t OFF_BAR = OFF_V + ST * AT_VB;   // barriers, item info, flags (< 384 B)
+    static constexpr uint32_t OFF_KN = OFF_BAR + 384;         // [ST][4] key-tile norm bounds (ST <= 8)
     static constexpr uint32_t SMEM = OFF_BAR + 512 + 1024;
 };
-static_assert((6 + 2 * 8) * 8 + 2 * 16 + 4 <= 256, "warp attention barrier area");
+static_assert((4 + 2 * 8 + 2 + 8 + 8 + 2) * 8 + 2 * 16 + 8 <= 384, "warp attention barrier area");
 
-template <bool F16, int ST, int QR = 128>
-__global__ void __launch_bounds__(aw_threads<QR>(), QR == 128 ? 1 : 2)
+template <bool F16, int ST, int QR = 128, bool HY = false>
+__global__ void __launch_bounds__(aw_threads<QR, HY>(), QR == 128 ? 1 : 2)
     k_attention_warp(const __grid_constant__ CUtensorMap map_q, const __grid_constant__ CUtensorMap map_k,
                      const __grid_constant__ CUtensorMap map_vt, AttnParams p) {
+    static_assert(!HY || QR == 128, "tensor-memory scores need 128-row items");
     constexpr int RB = QR / 32;   // 32-row blocks (one per warp) per item
     constexpr int NW = NH * RB;   // consumer warps
     constexpr bool kTileSum = F16;   // bound path: one row-sum MMA per tile (FP16 operands)
@@ -1201,20 +1209,36 @@ __global__ void __launch_bounds__(aw_threads<QR>(), QR == 128 ? 1 : 2)
     uint64_t* kv_full = bars + 4;       // [ST]
     uint64_t* kv_empty = kv_full + ST;  // [ST], one arrival per consumer warp
     uint64_t* never = kv_empty + ST;    // armed by nobody (debug stall)
-    int4* info = (int4*)(never + 2);    // [2]
+    uint64_t* s_full = never + 2;       // HY: [head][buffer], MMA commit: S ready
+    uint64_t* s_free = s_full + 8;      // HY: [head][buffer], one arrival per warp of the head
+    uint64_t* drain = s_free + 8;       // HY: the MMA warp's exit
+    int4* info = (int4*)(drain + 2);    // [2]
     int* abort_flag = (int*)(info + 2);
+    uint32_t* tmem_hold = (uint32_t*)(abort_flag + 1);
     float* kn = (float*)(sm + LY::OFF_KN);   // per stage and head: largest K-row norm of the tile
     volatile int* ab = abort_flag;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     if (tid == 0) {
-        for (int i = 0; i < 2; ++i) { mbar_init(&q_full[i], 1); mbar_init(&q_empty[i], NW); }
-        for (int i = 0; i < ST; ++i) { mbar_init(&kv_full[i], 1); mbar_init(&kv_empty[i], NW); }
+        // HY: Q and K/V stages are also released by the MMA warp's commits
+        for (int i = 0; i < 2; ++i) { mbar_init(&q_full[i], 1); mbar_init(&q_empty[i], NW + (HY ? 1 : 0)); }
+        for (int i = 0; i < ST; ++i) { mbar_init(&kv_full[i], 1); mbar_init(&kv_empty[i], NW + (HY ? 1 : 0)); }
         mbar_init(never, 1);
+        if constexpr (HY) {
+            for (int i = 0; i < 8; ++i) { mbar_init(&s_full[i], 1); mbar_init(&s_free[i], RB); }
+            mbar_init(drain, 1);
+        }
         *abort_flag = 0;
         fence_mbar_init();
     }
+    if (HY && warp == 0) {
+        tmem_alloc(tmem_hold, 512);
+        tmem_relinquish();
+    }
+    tc_fence_before();
     __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = HY ? *tmem_hold : 0u;
     const int n_items = p.counters[0];
     int* ticket = p.counters + 2 + p.layer;
 
@@ -1224,7 +1248,7 @@ __global__ void __launch_bounds__(aw_threads<QR>(), QR == 128 ? 1 : 2)
             tma_prefetch_map(&map_q);
             tma_prefetch_map(&map_k);
             tma_prefetch_map(&map_vt);
-            int q_it = 0;
+            int q_it = 0, q_armed = 0;
             uint32_t g = 0;
             bool ok = true;
             while (ok) {
@@ -1250,6 +1274,7 @@ __global__ void __launch_bounds__(aw_threads<QR>(), QR == 128 ? 1 : 2)
                 info[qb] = it;
                 mbar_arrive_expect_tx(&q_full[qb], QB);
                 tma_load_2d(sQ + qb * QB, &map_q, 0, it.x + it.y * ROWS + QR * half, &q_full[qb]);
+                ++q_armed;
                 int kb, ke;
                 key_range(it.y, it.z, p.window, kb, ke);
                 const int nk = (ke - kb + 63) >> 6;
@@ -1269,6 +1294,62 @@ __global__ void __launch_bounds__(aw_threads<QR>(), QR == 128 ? 1 : 2)
                 }
                 ++q_it;
             }
+            // on an abort, let the copies still in flight land before the CTA exits:
+            // wait (bounded) for the last armed phase of every stage and Q buffer
+            if (*ab) {
+                bool landed = true;
+                for (uint32_t t = g > ST ? g - ST : 0; t < g; ++t)
+                    landed &= mbar_drain(&kv_full[t % ST], (t / ST) & 1, p.wait_ns);
+                for (int i = q_armed > 2 ? q_armed - 2 : 0; i < q_armed; ++i)
+                    landed &= mbar_drain(&q_full[i & 1], (i >> 1) & 1, p.wait_ns);
+                if (!landed)   // a copy that never completes: a last, timed grace period
+                    for (int i = 0; i < 1000; ++i) __nanosleep(1000);
+            }
+        }
+    } else if (HY && warp == NW + 1) {
+        // ------------------------------------------------ HY: QK^T issue (one thread)
+        if (lane == 0) {
+            const uint32_t IQK = idesc_f16(128, 64, F16 ? 0u : 1u);
+            int q_it = 0;
+            uint32_t g = 0;
+            bool ok = true;
+            while (ok) {
+                const int qb = q_it & 1;
+                if (!mbar_wait(&q_full[qb], (q_it >> 1) & 1, ab, p.status, ST_TIMEOUT_ATTN, p.wait_ns)) break;
+                const int4 it = info[qb];
+                if (it.x < 0) break;
+                int kb, ke;
+                key_range(it.y, it.z, p.window, kb, ke);
+                const int nk = (ke - kb + 63) >> 6;
+                const uint32_t qa = smem_u32(sQ + qb * QB);
+                for (int j = 0; j < nk && ok; ++j) {
+                    const uint32_t t = g + j, s = t % ST, b = t & 1;
+                    if (!mbar_wait(&kv_full[s], (t / ST) & 1, ab, p.status, ST_TIMEOUT_ATTN, p.wait_ns)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t ka = smem_u32(sK + s * AT_KB);
+                    for (int h = 0; h < NH; ++h) {
+                        // buffer b of head h: its four warps have read S of tile t - 2
+                        if (t >= 2 && !mbar_wait(&s_free[2 * h + b], ((t >> 1) - 1) & 1, ab, p.status,
+                                                 ST_TIMEOUT_ATTN, p.wait_ns)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        mma_f16(tbase + h * 128 + b * 64, sdesc_sw128(qa + h * 32), sdesc_sw128(ka + h * 32), IQK, 0);
+                        mma_commit(&s_full[2 * h + b]);
+                    }
+                    if (ok) mma_commit(&kv_empty[s]);
+                }
+                if (!ok) break;
+                mma_commit(&q_empty[qb]);
+                g += nk;
+                ++q_it;
+            }
+            // every MMA issued complete before tensor memory and shared memory are released
+            mma_commit(drain);
+            mbar_drain(drain, 0, p.wait_ns);
         }
     } else {
         // ------------------------------------------------ warp: head h, query rows 32 rb .. 32 rb + 31
@@ -1342,19 +1423,57 @@ __global__ void __launch_bounds__(aw_threads<QR>(), QR == 128 ? 1 : 2)
                     nr[mt][e] = 0.f;
                 }
             }
-            // S - ref for keys 16q .. 16q+15 of the K tile at kbase (two 8-key column
-            // tiles); the swizzle of rows 16q + k_row does not depend on q
-            auto qkb = [&](uint32_t kbase, int q, float (&dst)[2][2][4]) {
-                uint32_t kf[4];
-                ldsm_x4(kbase + koff + 2048u * q, kf[0], kf[1], kf[2], kf[3]);
+            // HY: S - ref for keys 16q .. 16q+15 of global key tile t from the head's
+            // tensor-memory buffer (t & 1): this warp's lanes 32 rb .. 32 rb + 31, the two
+            // 16-row blocks in accumulator layout, then the negated references added
+            auto s_tmem = [&](uint32_t t, int q, float (&dst)[2][2][4]) {
+                const uint32_t col = tbase + h * 128 + (t & 1) * 64 + 16 * q;
 #pragma unroll
                 for (int mt = 0; mt < 2; ++mt)
+                    tmem_ld16x256b_x2(col + ((uint32_t)(32 * rb + 16 * mt) << 16), &dst[mt][0][0]);
+                tmem_wait_ld();
 #pragma unroll
-                    for (int nt = 0; nt < 2; ++nt)
-                        mma16816_c<F16>(dst[mt][nt], qa[mt], kf[2 * nt], kf[2 * nt + 1], nr[mt]);
+                for (int mt = 0; mt < 2; ++mt) {
+                    const float2 n0 = make_float2(nr[mt][0], nr[mt][1]), n1 = make_float2(nr[mt][2], nr[mt][3]);
+#pragma unroll
+                    for (int nt = 0; nt < 2; ++nt) {
+                        const float2 a = __fadd2_rn(make_float2(dst[mt][nt][0], dst[mt][nt][1]), n0);
+                        const float2 c = __fadd2_rn(make_float2(dst[mt][nt][2], dst[mt][nt][3]), n1);
+                        dst[mt][nt][0] = a.x;
+                        dst[mt][nt][1] = a.y;
+                        dst[mt][nt][2] = c.x;
+                        dst[mt][nt][3] = c.y;
+                    }
+                }
+            };
+            // HY: S of tile t in tensor memory (before its first load) / read (after its last)
+            auto s_wait = [&](uint32_t t) {
+                return !HY || warp_wait(&s_full[2 * h + (t & 1)], (t >> 1) & 1, ab, p.status, p.wait_ns);
+            };
+            auto s_release = [&](uint32_t t) {
+                if constexpr (HY) {
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&s_free[2 * h + (t & 1)]);
+                }
+            };
+            // S - ref for keys 16q .. 16q+15 of the K tile at kbase (two 8-key column
+            // tiles); the swizzle of rows 16q + k_row does not depend on q
+            auto qkb = [&](uint32_t kbase, uint32_t t, int q, float (&dst)[2][2][4]) {
+                if constexpr (HY) {
+                    s_tmem(t, q, dst);
+                } else {
+                    uint32_t kf[4];
+                    ldsm_x4(kbase + koff + 2048u * q, kf[0], kf[1], kf[2], kf[3]);
+#pragma unroll
+                    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                        for (int nt = 0; nt < 2; ++nt)
+                            mma16816_c<F16>(dst[mt][nt], qa[mt], kf[2 * nt], kf[2 * nt + 1], nr[mt]);
+                }
             };
             // the four 16-key steps of a full tile on the bound path (no maxima, no vote)
-            auto fast_tile = [&](uint32_t kbase, uint32_t vbase) {
+            auto fast_tile = [&](uint32_t kbase, uint32_t vbase, uint32_t t) {
                 // kTileSum: P summed over the tile's four steps (packed FP16 adds;
                 // the bound keeps each P <= 2^13.5, the sum of four inside the FP16
                 // range), then one row-sum MMA per tile instead of one per step
@@ -1365,7 +1484,7 @@ __global__ void __launch_bounds__(aw_threads<QR>(), QR == 128 ? 1 : 2)
                     float sc[2][2][4];
                     uint32_t vf[4], pa[2][4];
                     ldsm_x4(vbase + (uint32_t)voff[q], vf[0], vf[1], vf[2], vf[3]);
-                    qkb(kbase, q, sc);
+                    qkb(kbase, t, q, sc);
 #pragma unroll
                     for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
@@ -1405,8 +1524,14 @@ __global__ void __launch_bounds__(aw_threads<QR>(), QR == 128 ? 1 : 2)
 #pragma unroll
                         for (int hr = 0; hr < 2; ++hr) over |= fmaf(qn[mt][hr], km, nr[mt][2 * hr]) > kLimit<F16>;
                     if (!__any_sync(0xffffffffu, over)) {
-                        fast_tile(sKa + s0 * AT_KB, sVa + s0 * AT_VB);
-                        fast_tile(sKa + s1 * AT_KB, sVa + s1 * AT_VB);
+                        if (!s_wait(g)) { ok = false; break; }
+                        tc_fence_after();
+                        fast_tile(sKa + s0 * AT_KB, sVa + s0 * AT_VB, g);
+                        s_release(g);
+                        if (!s_wait(g + 1)) { ok = false; break; }
+                        tc_fence_after();
+                        fast_tile(sKa + s1 * AT_KB, sVa + s1 * AT_VB, g + 1);
+                        s_release(g + 1);
                         __syncwarp();
                         if (lane == 0) {
                             mbar_arrive(&kv_empty[s0]);
@@ -1419,20 +1544,14 @@ __global__ void __launch_bounds__(aw_threads<QR>(), QR == 128 ? 1 : 2)
                 }
                 const uint32_t s = g % ST;
                 if (!warp_wait(&kv_full[s], (g / ST) & 1, ab, p.status, p.wait_ns)) { ok = false; break; }
+                if (!s_wait(g)) { ok = false; break; }
+                tc_fence_after();
                 const int kvalid = ke - kb - 64 * j;
                 const uint32_t kb = sKa + s * AT_KB, vb = sVa + s * AT_VB;
                 // S - ref = Q K^T - ref for keys 16q .. 16q+15 (two 8-key column tiles);
                 // the swizzle of rows 16q + k_row does not depend on q (16q is a
                 // multiple of 8)
-                auto qk = [&](int q, float (&dst)[2][2][4]) {
-                    uint32_t kf[4];
-                    ldsm_x4(kb + koff + 2048u * q, kf[0], kf[1], kf[2], kf[3]);
-#pragma unroll
-                    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-                        for (int nt = 0; nt < 2; ++nt)
-                            mma16816_c<F16>(dst[mt][nt], qa[mt], kf[2 * nt], kf[2 * nt + 1], nr[mt]);
-                };
+                auto qk = [&](int q, float (&dst)[2][2][4]) { qkb(kb, g, q, dst); };
                 // Bound on the tile's scores, row by row: |q| max |k| <= ref + kLimit
                 // for every row of the warp means P <= 2^kLimit without looking at
                 // the maxima: the four 16-key steps then run without a vote or branch.
@@ -1449,7 +1568,7 @@ __global__ void __launch_bounds__(aw_threads<QR>(), QR == 128 ? 1 : 2)
                     fast = !__any_sync(0xffffffffu, over);
                 }
                 if (fast) {
-                    fast_tile(kb, vb);
+                    fast_tile(kb, vb, g);
                 } else {
                     // SB 16-key steps per maxima check: S of all of them first, one vote,
                     // then exponentials and PV (no branch between the steps of a block)
@@ -1545,6 +1664,7 @@ __global__ void __launch_bounds__(aw_threads<QR>(), QR == 128 ? 1 : 2)
                             }
                     }
                 }
+                s_release(g);
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&kv_empty[s]);
             }
@@ -1571,9 +1691,11 @@ __global__ void __launch_bounds__(aw_threads<QR>(), QR == 128 ? 1 : 2)
             ++q_it;
         }
     }
+    tc_fence_before();
     __syncthreads();
-    if (*ab && tid == 0) {
-        for (int i = 0; i < 1000; ++i) __nanosleep(1000);
+    if (HY && warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tbase, 512);
     }
 }
 
@@ -1675,7 +1797,7 @@ __global__ void __launch_bounds__(TM_THREADS, 1)
             tma_prefetch_map(&map_q);
             tma_prefetch_map(&map_k);
             tma_prefetch_map(&map_vt16);
-            int q_it = 0;
+            int q_it = 0, q_armed = 0;
             uint32_t g = 0;
             bool ok = true;
             while (ok) {
@@ -1696,6 +1818,7 @@ __global__ void __launch_bounds__(TM_THREADS, 1)
                 }
                 mbar_arrive_expect_tx(&q_full[qb], AT_QB);
                 tma_load_2d(sQ + qb * AT_QB, &map_q, 0, it.x + it.y * ROWS, &q_full[qb]);
+                ++q_armed;
                 int kb, ke;
                 key_range(it.y, it.z, p.window, kb, ke);
                 const int nk = (ke - kb + 63) >> 6;
@@ -1720,7 +1843,8 @@ __global__ void __launch_bounds__(TM_THREADS, 1)
             if (*ab) {
                 for (uint32_t t = g > ST ? g - ST : 0; t < g; ++t)
                     mbar_drain(&kv_full[t % ST], (t / ST) & 1, p.wait_ns);
-                for (int i = q_it > 2 ? q_it - 2 : 0; i < q_it; ++i) mbar_drain(&q_full[i & 1], (i >> 1) & 1, p.wait_ns);
+                for (int i = q_armed > 2 ? q_armed - 2 : 0; i < q_armed; ++i)
+                    mbar_drain(&q_full[i & 1], (i >> 1) & 1, p.wait_ns);
             }
         }
     } else if (warp == NSW + 1) {
@@ -2050,7 +2174,9 @@ std::string check_occupancy() {
         occupancy(k_attention_tm<kOutF16<FMT>, 8>, TM_THREADS, TmLayout<8>::SMEM),
         occupancy(k_attention_warp<kOutF16<FMT>, 4>, aw_threads<128>(), AwLayout<4>::SMEM),
         occupancy(k_attention_warp<kOutF16<FMT>, 8>, aw_threads<128>(), AwLayout<8>::SMEM),
-        occupancy(k_attention_warp<kOutF16<FMT>, 4, 64>, aw_threads<64>(), AwLayout<4, 64>::SMEM) / 2};
+        occupancy(k_attention_warp<kOutF16<FMT>, 4, 64>, aw_threads<64>(), AwLayout<4, 64>::SMEM) / 2,
+        occupancy(k_attention_warp<kOutF16<FMT>, 4, 128, true>, aw_threads<128, true>(), AwLayout<4>::SMEM),
+        occupancy(k_attention_warp<kOutF16<FMT>, 8, 128, true>, aw_threads<128, true>(), AwLayout<8>::SMEM)};
     const int o[6] = {*std::min_element(o_att, o_att + MLPF_ATTN_VARIANTS),
                       occupancy(k_post<0, FMT>, PT_THREADS, post_smem(0, FMT)),
                       occupancy(k_post<1, FMT>, PT_THREADS, post_smem(1, FMT)),
@@ -2077,6 +2203,8 @@ void set_attrs() {
     cudaFuncSetAttribute(k_attention_warp<kOutF16<FMT>, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, AwLayout<4>::SMEM);
     cudaFuncSetAttribute(k_attention_warp<kOutF16<FMT>, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, AwLayout<8>::SMEM);
     cudaFuncSetAttribute(k_attention_warp<kOutF16<FMT>, 4, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, AwLayout<4, 64>::SMEM);
+    cudaFuncSetAttribute(k_attention_warp<kOutF16<FMT>, 4, 128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, AwLayout<4>::SMEM);
+    cudaFuncSetAttribute(k_attention_warp<kOutF16<FMT>, 8, 128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, AwLayout<8>::SMEM);
 }
 
 }  // namespace
@@ -2276,6 +2404,8 @@ static int64_t run_tc(Model& m, Workspace& w, bool profile, const float* x, cons
             case 2: k_attention_tm<AF, 8><<<g, TM_THREADS, TmLayout<8>::SMEM, st>>>(w.map_q, w.map_k, w.map_vt16, ap); break;
             case 3: k_attention_warp<AF, 4><<<g, aw_threads<128>(), AwLayout<4>::SMEM, st>>>(w.map_q, w.map_k, w.map_vt, ap); break;
             case 5: k_attention_warp<AF, 4, 64><<<2 * g.x, aw_threads<64>(), AwLayout<4, 64>::SMEM, st>>>(w.map_q64, w.map_k, w.map_vt, ap); break;
+            case 6: k_attention_warp<AF, 4, 128, true><<<g, aw_threads<128, true>(), AwLayout<4>::SMEM, st>>>(w.map_q, w.map_k, w.map_vt, ap); break;
+            case 7: k_attention_warp<AF, 8, 128, true><<<g, aw_threads<128, true>(), AwLayout<8>::SMEM, st>>>(w.map_q, w.map_k, w.map_vt, ap); break;
             default: k_attention_warp<AF, 8><<<g, aw_threads<128>(), AwLayout<8>::SMEM, st>>>(w.map_q, w.map_k, w.map_vt, ap); break;
         }
         prof_end(m, st);

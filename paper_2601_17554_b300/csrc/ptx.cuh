@@ -229,6 +229,19 @@ MLPF_DEV void tmem_ld32(uint32_t taddr, float* v) {
 MLPF_DEV void tmem_wait_ld() {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
+// TMEM -> registers: 16 lanes x 256 bit, twice (16 consecutive columns).  Thread
+// 4 g + c of the warp receives, of lane block row g and g + 8 (lanes taddr.lane + g,
+// + g + 8), columns 2c, 2c + 1 (registers 0-3: rows g, g, g + 8, g + 8) and 8 + 2c,
+// 9 + 2c (registers 4-7): the accumulator layout of two m16n8 warp-level MMAs.
+MLPF_DEV void tmem_ld16x256b_x2(uint32_t taddr, float* v) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.16x256b.x2.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                   "=r"(r[7])
+                 : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
 // registers -> TMEM: 32 lanes x 32 bit, 32 consecutive columns per thread.
 MLPF_DEV void tmem_st32(uint32_t taddr, const uint32_t* v) {
     asm volatile(

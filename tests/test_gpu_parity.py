@@ -279,9 +279,14 @@ def test_fp8_needs_calibration():
     assert np.isfinite(run_gpu(model, x, cu, "fp8")[1]).all()
 
 
-# argmax agreement, regression rel. error with E4M3 (3 mantissa bits) in the projection and
-# FFN GEMMs: measured 0.974 / 0.100 on this subset; bounds leave margin for rounding changes
-FP8_BOUNDS = (0.96, 0.15)
+# E4M3 (3 mantissa bits, unit roundoff 2^-4) in the projection and FFN GEMMs cannot meet the
+# 16-bit bounds on this model: in the float64 emulation of the E4M3 roundings
+# (tests/lowp_emul.py) every single E4M3 GEMM stage alone already costs 0.4-1.5 % of argmax
+# agreement and 1.5-5 % regression error.  The bounds here are the emulation's prediction on
+# exactly these inputs (static scales from the same 32 calibration events: 97.46 % agreement,
+# 9.97 % largest column error) with 0.5 % and 10 % relative margin for the GPU's summation
+# order.
+FP8_BOUNDS = (0.970, 0.11)
 
 
 def test_fp8_prec64_subset(small_plain):
@@ -302,10 +307,10 @@ def test_fp8_prec64_subset(small_plain):
 
 def test_fp8_two_blocks_per_stack():
     """FP8 (E4M3 projections and FFN, calibrated scales) through the middle-layer
-    kernel of a d=64, 2 + 2 block model.  Measured: 94.8 % argmax agreement, at most
-    7.6 % column regression error (two more E4M3-quantised blocks flip more near-tied
-    logits than in the 1 + 1 model; the same kernel in 16-bit formats passes the
-    16-bit bounds above): bounds 0.93 and 0.12."""
+    kernel of a d=64, 2 + 2 block model.  The float64 emulation of the E4M3 roundings
+    on exactly these inputs predicts 94.64 % argmax agreement and 7.64 % largest
+    column regression error (two more E4M3-quantised blocks than the 1 + 1 model);
+    bounds: that prediction with 1.1 % (of 2894 elements) and 10 % relative margin."""
     import dataclasses
     cfg = dataclasses.replace(synth.SMALL, l_pid=2, l_reg=2)
     model, w = make_model(cfg, 0)
@@ -317,7 +322,7 @@ def test_fp8_two_blocks_per_stack():
     err = rel_err_cols(out[1], ref.reg)
     print(f"FP8 2+2 blocks: argmax agreement {agree:.5f}, reg rel err {err}")
     assert np.isfinite(out[0]).all() and np.isfinite(out[1]).all()
-    assert agree >= 0.93 and err.max() <= 0.12, (agree, err)
+    assert agree >= 0.935 and err.max() <= 0.085, (agree, err)
     model.close()
 
 
