@@ -54,6 +54,10 @@ def parse():
     ap.add_argument("--jets", type=float, default=0.0,
                     help="also time anti-kt jet clustering (distance parameter R, e.g. 0.4) of "
                          "the batch's reconstructed particles after the forward")
+    ap.add_argument("--split", default="replicas", choices=["replicas", "lpt"],
+                    help="N > 1: replicas (weak scaling, every GPU its own 512-event batch) or lpt "
+                         "(strong scaling: one batch split over the GPUs by the cost-balanced LPT "
+                         "rule on N^2)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="approximate CPU time budget of the oracle sample")
     return ap.parse_args()
@@ -211,12 +215,27 @@ def attention_traffic(variant, precision):
         return None
 
 
-def workload_inputs(rank, n_events=512):
+def workload_inputs(rank, n_events=512, split="replicas", ws=1):
+    """The rank's events.  replicas (weak scaling): every rank its own batch of the
+    same distribution.  lpt (strong scaling): one batch, its events split over the
+    ranks by the library's cost-balanced LPT rule on N^2 (no exchange step: events are
+    independent)."""
     cfg, wseed, iseed, sizes = synth.workload(WORKLOAD)
-    if rank > 0:  # weak scaling: every rank its own batch of the same distribution
+    if split == "replicas" and rank > 0:
         iseed = iseed + 1000 * rank
         sizes = synth.sizes_lognormal(iseed, len(sizes))
     sizes = sizes[:n_events]
+    if split == "lpt" and ws > 1:
+        from paper_2601_17554_b300 import shard_events
+        shard, _ = shard_events(sizes, ws)
+        mine = np.nonzero(shard == rank)[0]
+        # the same elements as in the whole batch: generated event by event
+        xs = [synth.gen_events(iseed, [int(sizes[e])], first_event=int(e))[0] for e in mine]
+        x = np.concatenate(xs) if xs else np.zeros((0, synth.IN_DIM), np.float32)
+        sizes = sizes[mine]
+        cu = np.zeros(len(sizes) + 1, np.int32)
+        cu[1:] = np.cumsum(sizes)
+        return cfg, wseed, x, cu, sizes
     x, cu = synth.gen_events(iseed, sizes)
     return cfg, wseed, x, cu, sizes
 
@@ -367,8 +386,12 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def workload_config(x, sizes, ws):
+def workload_config(x, sizes, ws, split="replicas"):
     """The `config` object of the JSON line (the same for both arms)."""
+    if split == "lpt" and ws > 1:
+        return {"workload": f"{WORKLOAD}: {WORKLOAD_DESC}", "events_per_job": 512,
+                "l2": "inputs larger than L2", "parallelism":
+                f"one batch split over {ws} GPUs by LPT on N^2 (no collective on the data path)"}
     return {"workload": f"{WORKLOAD}: {WORKLOAD_DESC}" +
             ("" if len(sizes) == 512 else f" (first {len(sizes)} events only)"),
             "events_per_gpu": int(len(sizes)), "elements_per_gpu": int(np.sum(sizes)),
@@ -390,7 +413,7 @@ def run_ours(args):
     ws, rank, local = dist_setup()
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    cfg, wseed, x, cu, sizes = workload_inputs(rank, args.events)
+    cfg, wseed, x, cu, sizes = workload_inputs(rank, args.events, args.split, ws)
     W = synth.make_weights(cfg, wseed)
     model = Model(synth.pack_blob(cfg, W), device=local)
     T, n_ev, max_n = x.shape[0], len(sizes), int(sizes.max())
@@ -530,9 +553,9 @@ def run_ours(args):
 
     line = {"metric": METRIC, "value": value, "unit": "events/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": prec, "data": "synthetic",
-            "config": workload_config(x, sizes, ws),
+            "higher_is_better": True, "scaling": "strong" if (args.split == "lpt" and ws > 1) else "weak",
+            "vs_baseline": None, "dtype": prec, "data": "synthetic",
+            "config": workload_config(x, sizes, ws, args.split),
             "attn_variant": attn_variant,
             "batch_ms_per_event": ms_step / n_ev,
             "gpu_launches": int(launches_per_step * args.steps),

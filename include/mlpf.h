@@ -456,6 +456,21 @@ const char* mlpf_last_error(void);
 mlpf_status mlpf_eval_activation(int32_t impl, int32_t act, const float* x, float* y, int32_t n,
                                  void* stream);
 
+/*
+ * Cost-balanced split of one packed batch over n_shards devices (host only, no
+ * CUDA call).  Events are independent, so a batch shards with no exchange step;
+ * the attention cost of an event grows as N_e^2, so each event goes, longest
+ * first (largest N_e^2; equal costs in index order), to the shard whose summed
+ * N^2 is smallest so far (lowest shard index on ties): the LPT rule, whose
+ * largest shard is within 4/3 of the best possible split.
+ * sizes: host, [n_events] element counts (>= 0); shard_of_event: host out,
+ * [n_events] shard index in 0..n_shards-1; shard_cost: host out or NULL,
+ * [n_shards] sum of N_e^2 of each shard.  Deterministic.
+ * Errors: MLPF_E_INVALID (n_shards < 1, NULL pointers, negative sizes).
+ */
+mlpf_status mlpf_shard_events(const int32_t* sizes, int32_t n_events, int32_t n_shards,
+                              int32_t* shard_of_event, double* shard_cost);
+
 /* ABI version of this library (major * 100 + minor). */
 int32_t mlpf_abi_version(void);
 

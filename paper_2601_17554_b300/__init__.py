@@ -33,6 +33,20 @@ def measure_unit_rates(device: int = 0) -> dict:
     return {"ex2_per_s": ex2.value, "ffma_per_s": ffma.value, "ex2_bf16x2_per_s": packed.value}
 
 
+def shard_events(sizes, n_shards: int):
+    """Cost-balanced split of a batch's events over n_shards devices (LPT on N^2, in the
+    library; host arrays).  Returns (shard_of_event int32 [n_events], shard_cost
+    float64 [n_shards])."""
+    import numpy as np
+    L = _lib.load()
+    sz = np.ascontiguousarray(sizes, np.int32)
+    shard = np.empty(len(sz), np.int32)
+    cost = np.empty(int(n_shards), np.float64)
+    check(L.mlpf_shard_events(sz.ctypes.data_as(ctypes.c_void_p), len(sz), int(n_shards),
+                              shard.ctypes.data_as(ctypes.c_void_p), cost.ctypes.data_as(ctypes.c_void_p)))
+    return shard, cost
+
+
 class Model:
     """A loaded MLPF model on one CUDA device (owns weights and workspace)."""
 

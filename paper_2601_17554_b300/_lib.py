@@ -23,7 +23,7 @@ EXPORTS = ("mlpf_load_weights", "mlpf_free", "mlpf_get_config", "mlpf_forward",
            "mlpf_trainer_step_supervised", "mlpf_trainer_export", "mlpf_sync", "mlpf_set_option", "mlpf_get_option",
            "mlpf_last_launch_count", "mlpf_profile_get", "mlpf_last_error", "mlpf_abi_version",
            "mlpf_cluster_jets", "mlpf_measure_ex2_packed_rate", "mlpf_trainer_forward",
-           "mlpf_trainer_backward", "mlpf_trainer_params")
+           "mlpf_trainer_backward", "mlpf_trainer_params", "mlpf_shard_events")
 
 
 class MlpfConfig(ctypes.Structure):
@@ -110,6 +110,8 @@ def load(build_if_missing: bool = True):
     L.mlpf_profile_get.restype = i32
     L.mlpf_last_error.argtypes = []
     L.mlpf_last_error.restype = ctypes.c_char_p
+    L.mlpf_shard_events.argtypes = [vp, i32, i32, vp, vp]
+    L.mlpf_shard_events.restype = ctypes.c_int
     L.mlpf_abi_version.argtypes = []
     L.mlpf_abi_version.restype = i32
     _handle = L

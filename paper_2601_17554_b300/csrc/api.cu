@@ -446,6 +446,34 @@ mlpf_status mlpf_eval_activation(int32_t impl, int32_t act, const float* x, floa
 
 int32_t mlpf_abi_version(void) { return 104; }
 
+mlpf_status mlpf_shard_events(const int32_t* sizes, int32_t n_events, int32_t n_shards, int32_t* shard_of_event,
+                              double* shard_cost) {
+    if (n_events < 0 || n_shards < 1 || (n_events > 0 && (!sizes || !shard_of_event))) {
+        set_error("mlpf_shard_events: bad arguments");
+        return MLPF_E_INVALID;
+    }
+    // longest processing time first: events by cost N^2 (ties: lower index first), each
+    // to the shard of least cost so far (ties: lower shard index)
+    std::vector<int32_t> order((size_t)n_events);
+    for (int32_t e = 0; e < n_events; ++e) {
+        if (sizes[e] < 0) { set_error("mlpf_shard_events: negative event size"); return MLPF_E_INVALID; }
+        order[(size_t)e] = e;
+    }
+    auto cost = [&](int32_t e) { return (double)sizes[e] * (double)sizes[e]; };
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return cost(a) > cost(b); });
+    std::vector<double> load((size_t)n_shards, 0.0);
+    for (int32_t e : order) {
+        int32_t best = 0;
+        for (int32_t k = 1; k < n_shards; ++k)
+            if (load[(size_t)k] < load[(size_t)best]) best = k;
+        shard_of_event[e] = best;
+        load[(size_t)best] += cost(e);
+    }
+    if (shard_cost)
+        for (int32_t k = 0; k < n_shards; ++k) shard_cost[k] = load[(size_t)k];
+    return MLPF_OK;
+}
+
 const char* mlpf_last_error(void) { return g_last_error.c_str(); }
 
 mlpf_status mlpf_load_weights(const void* blob, size_t nbytes, int device, mlpf_model** out) {
