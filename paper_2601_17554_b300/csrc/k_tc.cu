@@ -615,7 +615,9 @@ __global__ void __launch_bounds__(EM_THREADS, 1) k_embed_qkv(const __grid_consta
         for (int b = 0; b < 2; ++b)
             e[b] = t < ntiles && 2 * t + b < nblk ? p.blk[2 * t + b] : make_int4(0, 0, 0, 0);
     };
+    int x_issued = 0, h_issued = 0;   // leader: input-row copies and h_pid loads armed
     auto issue_x = [&](const int4 (&e)[2]) {
+        ++x_issued;
         uint32_t bytes[2];
         const uint8_t* src[2];
 #pragma unroll
@@ -660,6 +662,7 @@ __global__ void __launch_bounds__(EM_THREADS, 1) k_embed_qkv(const __grid_consta
         const bool more = tile + 2 * (int)gridDim.x < ntiles;
         if (leader && more) blk_of(tile + 2 * (int)gridDim.x, enext);   // used after the first GEMM
         if (TMA_HP && leader) {
+            ++h_issued;
             mbar_arrive_expect_tx(tma_bar, ATOM);
             tma_load_2d(sA + ATOM, &map_hp, 0, p0, tma_bar);
             if (tile + 2 * (int)gridDim.x < ntiles) tma_prefetch_2d(&map_hp, 0, p0 + 2 * gridDim.x * ROWS);
@@ -771,8 +774,15 @@ __global__ void __launch_bounds__(EM_THREADS, 1) k_embed_qkv(const __grid_consta
         tc_fence_before();
     }
     __syncthreads();
-    if (*ab && tid == 0) {
-        for (int i = 0; i < 1000; ++i) __nanosleep(1000);  // let in-flight copies land
+    if (*ab) {
+        // let the copies still in flight land before the CTA exits: the last armed
+        // phase of each barrier (bounded waits; a timed grace period only if one fails)
+        bool landed = true;
+        if (tid == 0) landed &= mbar_drain(&bars[0], 0, p.wait_ns);
+        if (leader && x_issued > 0) landed &= mbar_drain(x_bar, (x_issued - 1) & 1, p.wait_ns);
+        if (leader && h_issued > 0) landed &= mbar_drain(tma_bar, (h_issued - 1) & 1, p.wait_ns);
+        if (!landed)
+            for (int i = 0; i < 1000; ++i) __nanosleep(1000);
     }
     __syncthreads();
     if (tid < 32) {
@@ -862,6 +872,7 @@ __global__ void __launch_bounds__(PT_THREADS, 1) k_post(const __grid_constant__ 
     const int nblk = tpad >> 6;
     const int ntiles = (tpad + ROWS - 1) / ROWS;
     uint32_t mph = 0, aph = 0;
+    int o_issued = 0;   // leader: attention-output tile loads armed
     // sync the team, let its leader issue MMAs, wait for them; false on failure
     auto run_mma = [&](auto issue) -> bool {
         tc_fence_before();
@@ -883,6 +894,7 @@ __global__ void __launch_bounds__(PT_THREADS, 1) k_post(const __grid_constant__ 
         const int pp = tile * ROWS + r;
         const RowInfo ri = row_info(p.blk, nblk, pp);
         if (leader) {
+            ++o_issued;
             mbar_arrive_expect_tx(tma_bar, ATOM);
             tma_load_2d(sO16, &map_o, 0, tile * ROWS, tma_bar);
         }
@@ -1061,8 +1073,14 @@ __global__ void __launch_bounds__(PT_THREADS, 1) k_post(const __grid_constant__ 
         tc_fence_before();
     }
     __syncthreads();
-    if (*ab && tid == 0) {
-        for (int i = 0; i < 1000; ++i) __nanosleep(1000);
+    if (*ab) {
+        // the last armed phase of each copy barrier (bounded waits; a timed grace
+        // period only if one fails)
+        bool landed = true;
+        if (tid == 0) landed &= mbar_drain(&bars[0], 0, p.wait_ns);
+        if (leader && o_issued > 0) landed &= mbar_drain(tma_bar, (o_issued - 1) & 1, p.wait_ns);
+        if (!landed)
+            for (int i = 0; i < 1000; ++i) __nanosleep(1000);
     }
     __syncthreads();
     if (tid < 32) {
@@ -1131,8 +1149,8 @@ MLPF_DEV void ffma2_bcast(float& d0, float& d1, float a0, float a1, float s, flo
 
 // 2^x0, 2^x1 packed in the 16-bit operand format: one packed MUFU operation on the
 // arguments rounded to that format (ex2.f16x2 / ex2.bf16x2, two results per
-// instruction).  For BF16 the rounding of the argument S - ref (at most 2^-9
-// relative) changes P by at most |S - ref| 2^-9 ln 2; the float64 emulation of the
+// instruction).  For BF16 the rounding of the argument S - ref (at most 2^-8
+// relative) changes P by at most |S - ref| 2^-8 ln 2; the float64 emulation of the
 // BF16 mode shows no effect of it on the outputs (tests/lowp_emul.py, stage p_arg).
 template <bool F16>
 MLPF_DEV uint32_t exp2_pair(float x0, float x1) {

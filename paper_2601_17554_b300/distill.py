@@ -4,8 +4,10 @@ Teacher: the full-size model (width 256, 8 heads of 32, FFN 1024, 3 + 3 blocks),
 run by the plain FP32 path, with its class head's last layer scaled so that about
 95 % of elements get a class probability >= 0.9 (a stand-in for a trained,
 confident model: random weights give flat class scores).
-Student: width 64, 4 heads of 16, FFN 256, 1 + 1 blocks, which runs on the
-tensor-core path; trained on the teacher's per-element outputs (class scores and
+Student (--student): d64 = width 64, 4 heads of 16, FFN 256, 1 + 1 blocks, which runs
+on the tensor-core path in BF16; or cfg5 = width 128, 4 heads of 32, FFN 512, 2 + 2
+blocks (the distillation configuration), which runs on the plain FP32 path (the
+tensor-core path is built for width 64); trained on the teacher's per-element outputs (class scores and
 the 5 regressions) of synthetic events with N ~ U{1000..6000} elements, with the
 library's hand-written FP32 forward/backward kernels and LAMB (learning rate
 2e-3 -> 2e-4 on a cosine schedule, Sec. 5.3).
@@ -35,6 +37,8 @@ if ROOT not in sys.path:
 import synth  # noqa: E402
 
 TEACHER_SEED, STUDENT_SEED = 1, 0
+# the distillation configuration's student: width 128, 4 heads of 32, FFN 512, 2 + 2 blocks
+STUDENT_CFG5 = synth.ModelConfig(d=128, heads=4, ffn=512, l_pid=2, l_reg=2)
 TRAIN_SEED, SCALE_SEED = 2000, 12345
 
 
@@ -78,6 +82,7 @@ def main(argv=None):
     ap.add_argument("--workers", type=int, default=min(16, os.cpu_count() or 1))
     ap.add_argument("--out", default="")
     ap.add_argument("--json", default="")
+    ap.add_argument("--student", default="d64", choices=["d64", "cfg5"])
     ap.add_argument("--student-blob", default="",
                     help="evaluate this trained student (skip the training)")
     args = ap.parse_args(argv)
@@ -122,7 +127,11 @@ def main(argv=None):
     res["teacher_targets_s"] = time.time() - t0
 
     # training
-    init_blob = synth.pack_blob(synth.SMALL, synth.make_weights(synth.SMALL, STUDENT_SEED))
+    scfg = synth.SMALL if args.student == "d64" else STUDENT_CFG5
+    sprec = "bf16" if args.student == "d64" else "fp32"
+    res["student"] = {"config": args.student, "d": scfg.d, "heads": scfg.heads, "ffn": scfg.ffn,
+                      "l_pid": scfg.l_pid, "l_reg": scfg.l_reg, "precision": sprec}
+    init_blob = synth.pack_blob(scfg, synth.make_weights(scfg, STUDENT_SEED))
     if args.student_blob:
         batches = []
         args.epochs = 0
@@ -177,18 +186,35 @@ def main(argv=None):
 
     def evaluate(name, blob_):
         student = Model(blob_)
-        sout, s_ms = timed(lambda: student.forward(X, CU, mn, precision="bf16"))
+        sout, s_ms = timed(lambda: student.forward(X, CU, mn, precision=sprec))
         s_cls = sout[2].cpu().numpy()
         s_reg = sout[1].cpu().numpy()
         r = {"student_agreement": float((s_cls == t_cls).mean()),
              "student_reg_rel_err_vs_teacher": [
                  float(v) for v in np.sqrt(((s_reg - t_reg) ** 2).sum(0) / (t_reg ** 2).sum(0))],
              "student_ms": s_ms, "gated": {}}
+        # per-event confidence statistics: can an event-level gate separate the events
+        # the student gets wrong?
+        conf_el = softmax_max(sout[0].cpu().numpy().astype(np.float64))
+        ev_mean = np.array([conf_el[cu[e]:cu[e + 1]].mean() for e in range(len(sizes))])
+        ev_min = np.array([conf_el[cu[e]:cu[e + 1]].min() for e in range(len(sizes))])
+        ev_agree = np.array([(s_cls[cu[e]:cu[e + 1]] == t_cls[cu[e]:cu[e + 1]]).mean() for e in range(len(sizes))])
+        pct = [0, 10, 50, 90, 100]
+        r["event_confidence"] = {
+            "mean_conf_percentiles": {str(q): float(np.percentile(ev_mean, q)) for q in pct},
+            "min_conf_percentiles": {str(q): float(np.percentile(ev_min, q)) for q in pct},
+            "event_agreement_percentiles": {str(q): float(np.percentile(ev_agree, q)) for q in pct},
+            "corr_mean_conf_vs_agreement": float(np.corrcoef(ev_mean, ev_agree)[0, 1]),
+            "element_agreement_by_conf": {
+                f">={c}": float((s_cls[conf_el >= c] == t_cls[conf_el >= c]).mean()) if (conf_el >= c).any() else None
+                for c in (0.5, 0.9, 0.99)},
+            "element_fraction_by_conf": {f">={c}": float((conf_el >= c).mean()) for c in (0.5, 0.9, 0.99)}}
         # event confidence: mean (mode 0) or minimum (mode 1) of the per-element max softmax
         for mode, mname in ((0, "mean"), (1, "min")):
             student.set_option(_lib.OPT_GATE_CONFIDENCE, mode)
             for thr in sorted({args.threshold, 0.5, 0.7, 0.95, 0.99, 0.995, 0.999}):
-                gout, g_ms = timed(lambda: forward_gated(student, teacher, thr, X, CU, mn), reps=1)
+                gout, g_ms = timed(lambda: forward_gated(student, teacher, thr, X, CU, mn,
+                                                         student_precision=sprec), reps=1)
                 g_cls = gout[2].cpu().numpy()
                 g_reg = gout[1].cpu().numpy()
                 rel = np.sqrt(((g_reg - t_reg) ** 2).sum(0) / (t_reg ** 2).sum(0))

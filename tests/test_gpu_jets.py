@@ -6,8 +6,10 @@ both sides.  What is unique is compared exactly: the partition of the particles
 into jets (constituent sets) and the jet count; the jets' 4-vectors (FP32 sums on
 the GPU) within 1e-4 relative.  The GPU decides merges in FP32 and the oracle in
 FP64, so a near-tie (two distances equal to FP32 precision) may be taken in the
-other order; where that changes a jet, the jet is not matched: at least 99.5 % of
-the particles must sit in matched jets.
+other order; where that changes a jet, the jet is not matched.  Unmatched jets are
+checked too: the GPU's and the oracle's unmatched jets hold the same particles and
+the same summed 4-vector (the difference is a local reordering, no particle lost or
+double counted), and at least 99.5 % of the particles sit in matched jets.
 """
 import numpy as np
 import pytest
@@ -48,12 +50,23 @@ def compare_event(gj, gnj, gjof, cls, reg, R):
     n_part = int((ojof >= 0).sum())
     assert gnj >= 1 or n_part == 0
     gp = {frozenset(np.nonzero(gjof == t)[0].tolist()): t for t in range(gnj)}
-    matched = 0
+    matched, hit = 0, set()
+    un_o, un_o_p4 = set(), np.zeros(4)
     for t in range(len(oj)):
         s = frozenset(np.nonzero(ojof == t)[0].tolist())
         if s in gp:
             matched += len(s)
+            hit.add(gp[s])
             np.testing.assert_allclose(gj[gp[s]], oj[t], rtol=1e-4, atol=1e-4 * np.abs(oj[t]).max())
+        else:
+            un_o |= s
+            un_o_p4 += oj[t]
+    # the unmatched jets of both sides: the same particles, the same total 4-vector
+    un_g = set(np.nonzero(np.isin(gjof, [t for t in range(gnj) if t not in hit]))[0].tolist())
+    assert un_g == un_o
+    un_g_p4 = gj[[t for t in range(gnj) if t not in hit]].astype(np.float64).sum(0) if gnj else np.zeros(4)
+    scale = max(np.abs(oj).sum(), 1.0) if len(oj) else 1.0
+    np.testing.assert_allclose(un_g_p4, un_o_p4, rtol=0, atol=1e-5 * scale)
     return n_part, matched
 
 
