@@ -147,7 +147,7 @@ extern "C" mlpf_status mlpf_forward_noalloc(mlpf_model* mm, int32_t precision, c
             tmp.ws = na_workspace(nd.base);
             if (!tc_make_maps(tmp)) return MLPF_E_CUDA;
             nd.map_q = tmp.ws.map_q;
-            nd.map_q64 = tmp.ws.map_q64;   // 64-row Q tiles (attention variant 9)
+            nd.map_q64 = tmp.ws.map_q64;   // 64-row Q tiles (attention variant 5)
             nd.map_k = tmp.ws.map_k;
             nd.map_o = tmp.ws.map_o;
             nd.map_vt = tmp.ws.map_vt;
