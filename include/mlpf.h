@@ -327,6 +327,20 @@ mlpf_status mlpf_trainer_step_supervised(mlpf_trainer* t, const float* x, const 
                                          float focal_gamma, float delta, float lr, int32_t update,
                                          float* grads_out, double* loss_out, void* stream);
 
+/*
+ * GEMM arithmetic of the trainer's linear layers (forward, input and weight
+ * gradients; Sec. 5.3 trains the model in mixed precision).  MLPF_FP32 (default):
+ * SIMT FP32 FMAs.  MLPF_BF16 / MLPF_FP16: the operands of every linear-layer GEMM are
+ * rounded to that 16-bit format and multiplied on the tcgen05 tensor cores (mlpf_gemm_tc)
+ * with FP32 accumulation; master weights, optimizer state, activations, LayerNorm,
+ * attention (forward and backward) and the loss stay FP32.  Takes effect from the next
+ * forward or step (a pending mlpf_trainer_forward is invalidated).  A bounded wait
+ * that runs out inside a tensor-core GEMM is reported as MLPF_E_TIMEOUT by the next
+ * synchronous step (loss_out given).  Errors: MLPF_E_INVALID (NULL),
+ * MLPF_E_UNSUPPORTED (another precision), MLPF_E_OOM (operand scratch).
+ */
+mlpf_status mlpf_trainer_set_precision(mlpf_trainer* t, int32_t precision);
+
 /* Current weights as a blob (host buffer of cap bytes, or NULL to query *nbytes). */
 mlpf_status mlpf_trainer_export(const mlpf_trainer* t, void* blob, size_t cap, size_t* nbytes);
 
@@ -362,6 +376,28 @@ mlpf_status mlpf_trainer_backward(mlpf_trainer* t, const float* x, const int32_t
                                   const float* dlogits, const float* draw, float* grads_out,
                                   void* stream);
 mlpf_status mlpf_trainer_params(mlpf_trainer* t, float* get, const float* set, void* stream);
+
+/*
+ * The trainer's tensor-core GEMM (the dense map of every linear layer, Sec. 5.3):
+ *   C[M, N] (op)= act(A[M, K] B[N, K]^T + bias) + R
+ * precision: MLPF_BF16 or MLPF_FP16 (the format of A and B), FP32 accumulation.
+ * A: device [M, lda], B: device [N, ldb], 16-bit row-major, 16-byte aligned, lda and
+ *    ldb multiples of 8 and >= K; K > 0 a multiple of 64 (zero-pad shorter rows).
+ * C: device [M, ldc] float32 (ldc >= N).  bias: device [N] or NULL.  R: device
+ *    [M, ldr] float32 or NULL.  act: -1 none, 0 GELU (erf form), 1 ReLU, applied to
+ *    the product plus bias; R is added after it.
+ * mode: 0 C = result, 1 C += result, 2 C += result with the K range split in chunks of
+ *    kchunk (a multiple of 64; 0 = one chunk) whose partial products are added
+ *    atomically (bias and R once).
+ * status: device uint32 word; the value 2 is ORed into it if a bounded wait inside
+ *    the kernel ran out (C is then incomplete).  Asynchronous on `stream`.
+ * Errors: MLPF_E_UNSUPPORTED (precision), MLPF_E_INVALID (NULL, sizes, alignment),
+ *         MLPF_E_CUDA (launch or tensor-map encoding failed).
+ */
+mlpf_status mlpf_gemm_tc(int32_t precision, const void* A, int64_t lda, const void* B, int64_t ldb,
+                         int32_t M, int32_t N, int32_t K, float* C, int64_t ldc, const float* bias,
+                         const float* R, int64_t ldr, int32_t act, int32_t mode, int32_t kchunk,
+                         uint32_t* status, void* stream);
 
 /*
  * Wait for the model's work on `stream` and report device-side status:

@@ -186,10 +186,12 @@ class Model:
 
 
 class Trainer:
-    """Trainer of a model (hand-written FP32 forward/backward kernels, LAMB): distillation
-    (arch 0, step) or the supervised loss of Eq. 1 (arch 1, step_supervised)."""
+    """Trainer of a model (hand-written forward/backward kernels, LAMB): distillation
+    (arch 0, step) or the supervised loss of Eq. 1 (arch 1, step_supervised).
+    precision: "fp32" (SIMT GEMMs) or "bf16" / "fp16" (linear-layer GEMMs on the tensor
+    cores with 16-bit operands and FP32 accumulation; everything else FP32)."""
 
-    def __init__(self, blob: bytes, device: int = 0):
+    def __init__(self, blob: bytes, device: int = 0, precision: str = "fp32"):
         self.L = _lib.load()
         h = ctypes.c_void_p()
         buf = ctypes.create_string_buffer(blob, len(blob))
@@ -197,6 +199,12 @@ class Trainer:
         self.h = h
         self.device = device
         self.num_params = int(self.L.mlpf_trainer_num_params(self.h))
+        self.set_precision(precision)
+
+    def set_precision(self, precision):
+        p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        check(self.L.mlpf_trainer_set_precision(self.h, p))
+        self.precision = precision
 
     def close(self):
         if getattr(self, "h", None):
@@ -241,6 +249,26 @@ class Trainer:
         buf = ctypes.create_string_buffer(n.value)
         check(self.L.mlpf_trainer_export(self.h, buf, n.value, ctypes.byref(n)))
         return buf.raw
+
+
+def gemm_tc(A, B, C, bias=None, R=None, act: int = -1, mode: int = 0, kchunk: int = 0, status=None,
+            stream=None):
+    """C (op)= act(A B^T + bias) + R on the tensor cores (mlpf_gemm_tc): A [M, >=K], B [N, >=K]
+    torch.bfloat16 or torch.float16 CUDA tensors with K = A's logical width (a multiple of 64),
+    C [M, >=N] float32.  status: int32 CUDA tensor of one element (allocated if None);
+    returned."""
+    import torch
+    L = _lib.load()
+    prec = PRECISIONS["bf16"] if A.dtype == torch.bfloat16 else PRECISIONS["fp16"]
+    if status is None:
+        status = torch.zeros(1, dtype=torch.int32, device=A.device)
+    s = stream if stream is not None else torch.cuda.current_stream(A.device).cuda_stream
+    M, K = A.shape
+    N = B.shape[0]
+    check(L.mlpf_gemm_tc(prec, _ptr(A), A.stride(0), _ptr(B), B.stride(0), M, N, K, _ptr(C), C.stride(0),
+                         _ptr(bias), _ptr(R), R.stride(0) if R is not None else 0, act, mode, kchunk,
+                         _ptr(status), ctypes.c_void_p(s)))
+    return status
 
 
 def forward_gated(student: Model, teacher: Model, threshold: float, x, cu_seqlens, max_n: int,

@@ -23,7 +23,8 @@ EXPORTS = ("mlpf_load_weights", "mlpf_free", "mlpf_get_config", "mlpf_forward",
            "mlpf_trainer_step_supervised", "mlpf_trainer_export", "mlpf_sync", "mlpf_set_option", "mlpf_get_option",
            "mlpf_last_launch_count", "mlpf_profile_get", "mlpf_last_error", "mlpf_abi_version",
            "mlpf_cluster_jets", "mlpf_measure_ex2_packed_rate", "mlpf_trainer_forward",
-           "mlpf_trainer_backward", "mlpf_trainer_params", "mlpf_shard_events")
+           "mlpf_trainer_backward", "mlpf_trainer_params", "mlpf_shard_events",
+           "mlpf_trainer_set_precision", "mlpf_gemm_tc")
 
 
 class MlpfConfig(ctypes.Structure):
@@ -96,6 +97,10 @@ def load(build_if_missing: bool = True):
     L.mlpf_trainer_backward.restype = ctypes.c_int
     L.mlpf_trainer_params.argtypes = [vp, vp, vp, vp]
     L.mlpf_trainer_params.restype = ctypes.c_int
+    L.mlpf_trainer_set_precision.argtypes = [vp, i32]
+    L.mlpf_trainer_set_precision.restype = ctypes.c_int
+    L.mlpf_gemm_tc.argtypes = [i32, vp, i64, vp, i64, i32, i32, i32, vp, i64, vp, vp, i64, i32, i32, i32, vp, vp]
+    L.mlpf_gemm_tc.restype = ctypes.c_int
     L.mlpf_trainer_export.argtypes = [vp, vp, sz, ctypes.POINTER(sz)]
     L.mlpf_trainer_export.restype = ctypes.c_int
     L.mlpf_sync.argtypes = [vp, vp]

@@ -57,9 +57,9 @@ class StudentMLPF(torch.nn.Module):
     """An MLPF model (weight blob) as a torch module trained through the library's
     hand-written forward and backward kernels."""
 
-    def __init__(self, blob: bytes, device: int = 0):
+    def __init__(self, blob: bytes, device: int = 0, precision: str = "fp32"):
         super().__init__()
-        self.trainer = Trainer(blob, device)
+        self.trainer = Trainer(blob, device, precision)
         p = torch.empty((self.trainer.num_params,), dtype=torch.float32, device=torch.device("cuda", device))
         s = ctypes.c_void_p(torch.cuda.current_stream(p.device).cuda_stream)
         check(self.trainer.L.mlpf_trainer_params(self.trainer.h, _ptr(p), None, s))

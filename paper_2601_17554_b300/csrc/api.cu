@@ -444,7 +444,7 @@ mlpf_status mlpf_eval_activation(int32_t impl, int32_t act, const float* x, floa
     return MLPF_OK;
 }
 
-int32_t mlpf_abi_version(void) { return 104; }
+int32_t mlpf_abi_version(void) { return 105; }
 
 mlpf_status mlpf_shard_events(const int32_t* sizes, int32_t n_events, int32_t n_shards, int32_t* shard_of_event,
                               double* shard_cost) {

@@ -186,6 +186,23 @@ void f32_attention(const float* qkv, float* out, const int32_t* cu, int n_events
                    int heads, float* lse, cudaStream_t st);
 mlpf_status parse_blob_into(const uint8_t* p, size_t nbytes, Model& m);
 
+// 16-bit tensor-core GEMM of the training step (k_gemm_tc.cu):
+//   C[M, N] (op)= act(A[M, Kp] B[N, Kp]^T + bias) + R
+// A, B row-major 16-bit (f16: FP16, else BF16), row strides lda, ldb (multiples of 8
+// elements, bases 16-byte aligned), Kp a multiple of 64 with zeros beyond the true K.
+// mode 0: C = ..., 1: C += ..., 2: C += ... split over K in chunks of kchunk (a multiple
+// of 64; 0 = no split) with atomic adds; bias and R are added once (first split).  act:
+// -1 none, 0 GELU, 1 ReLU.  C16 (or null): 16-bit copy of the result (mode 0).  Returns
+// false if a tensor map cannot be encoded.  Bounded waits set ST_TIMEOUT_GEMM in *status.
+bool gemm_tc(int f16, const void* A, long lda, const void* B, long ldb, int M, int N, int Kp, float* C, long ldc,
+             const float* bias, const float* R, long ldr, int act, int mode, int kchunk, uint16_t* C16, long ldc16,
+             unsigned* status, uint64_t wait_ns, cudaStream_t st);
+// FP32 -> 16-bit operand copies: dst[r, c] = [s1 | s2][r, c] for c < k1 + k2, zero up to ldd
+// (ldd even); cvt_16_t: dst[c, r] = src[r, c] for r < rows, c < cols, zero for rows <= r < ldd.
+void cvt_16(const float* s1, long ld1, int k1, const float* s2, long ld2, int k2, int rows, uint16_t* dst, long ldd,
+            int f16, cudaStream_t st);
+void cvt_16_t(const float* src, long lds, int rows, int cols, uint16_t* dst, long ldd, int f16, cudaStream_t st);
+
 // tensor-core path preparation (weights images, tensor maps)
 bool tc_prepare_weights(Model& m);
 bool tc_make_maps(Model& m);

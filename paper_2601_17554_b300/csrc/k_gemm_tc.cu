@@ -1,0 +1,365 @@
+// 16-bit tensor-core GEMM with a fused FP32 epilogue, for the training step's linear layers
+// (Sec. 5.3: every layer of the model is a dense map y = x W^T + b; its backward needs
+// dX = dY W and dW = dY^T X).  One CTA computes a 128 x BN tile of
+//     C (op)= act(A[M, Kp] B[N, Kp]^T + bias) + R
+// with A and B row-major 16-bit (BF16 or FP16) in global memory, Kp a multiple of 64:
+// TMA copies 128 x 64 and BN x 64 boxes (128-byte swizzle) into a ring of shared stages,
+// one thread issues tcgen05.mma (M = 128, N = BN, K = 16 per instruction) into a
+// BN-column FP32 accumulator in tensor memory, and four warps read it back with
+// tcgen05.ld (thread = row) for the epilogue.  Split-K over blockIdx.z adds partial tiles
+// with atomics (weight gradients, whose reduction runs over all elements of the batch).
+// Every wait is bounded: on a timeout the CTA sets the status word, lets its copies and
+// MMAs in flight land, frees its tensor memory and returns.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "internal.h"
+#include "ptx.cuh"
+
+namespace mlpf {
+namespace {
+
+constexpr int TG_BM = 128;   // tile rows (M of one MMA)
+constexpr int TG_BK = 64;    // K elements per stage: one 128-byte swizzle atom of 16-bit values
+
+struct TgArgs {
+    int M, N, Kp, kchunk;
+    float* C;
+    long ldc;
+    uint16_t* C16;      // optional 16-bit copy of the result (mode 0 only)
+    long ldc16;
+    const float* bias;  // [N] or null (split 0 only)
+    const float* R;     // residual [M, ldr] or null (split 0 only)
+    long ldr;
+    int mode;           // 0: C = ..., 1: C += ..., 2: C += ... with atomics (split-K)
+    int act;            // -1 none, 0 GELU (erf), 1 ReLU: applied to (acc + bias), before R
+    int f16;            // operand and C16 format: 1 FP16, 0 BF16
+    unsigned* status;
+    uint64_t wait_ns;
+};
+
+__device__ __forceinline__ float tg_act(float v, int act) {
+    if (act == 1) return fmaxf(v, 0.f);
+    if (act == 0) return 0.5f * v * (1.f + erff(v * 0.70710678118654752f));
+    return v;
+}
+
+template <int BN, int ST>
+struct TgLayout {
+    static constexpr int A_BYTES = TG_BM * TG_BK * 2;
+    static constexpr int B_BYTES = BN * TG_BK * 2;
+    static constexpr int STAGE = A_BYTES + B_BYTES;          // multiple of 1024
+    static constexpr int OFF_BAR = ST * STAGE;                // full[ST], empty[ST], done
+    static constexpr int OFF_MISC = OFF_BAR + (2 * ST + 1) * 8;
+    static constexpr int BYTES = OFF_MISC + 64 + 1024;        // + alignment slack
+    static constexpr uint32_t TMEM_COLS = BN < 32 ? 32 : BN;
+};
+
+template <int BN, int ST>
+__global__ void __launch_bounds__(128) k_gemm_tc(const __grid_constant__ CUtensorMap map_a,
+                                                 const __grid_constant__ CUtensorMap map_b, TgArgs g) {
+    using L = TgLayout<BN, ST>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t* full = (uint64_t*)(smem + L::OFF_BAR);
+    uint64_t* empty = full + ST;
+    uint64_t* done = empty + ST;
+    uint32_t* tmem_slot = (uint32_t*)(smem + L::OFF_MISC);
+    volatile int* abort_flag = (volatile int*)(smem + L::OFF_MISC + 4);
+    int* issued_s = (int*)(smem + L::OFF_MISC + 8);
+    int* consumed_s = (int*)(smem + L::OFF_MISC + 12);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * TG_BM, n0 = blockIdx.y * BN;
+    const int kbeg = blockIdx.z * g.kchunk;
+    const int kend = min(g.Kp, kbeg + g.kchunk);
+    const int nk = kend > kbeg ? (kend - kbeg) / TG_BK : 0;
+
+    if (tid == 0) {
+        for (int s = 0; s < ST; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(done, 1);
+        fence_mbar_init();
+        *abort_flag = 0;
+        *issued_s = 0;
+        *consumed_s = 0;
+        tma_prefetch_map(&map_a);
+        tma_prefetch_map(&map_b);
+    }
+    if (warp == 2) {
+        tmem_alloc(tmem_slot, L::TMEM_COLS);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {   // TMA producer
+        int i = 0;
+        for (; i < nk; ++i) {
+            const int s = i % ST;
+            if (i >= ST && !mbar_wait(&empty[s], ((i / ST) - 1) & 1, abort_flag, g.status, ST_TIMEOUT_GEMM,
+                                      g.wait_ns))
+                break;
+            uint8_t* sa = smem + s * L::STAGE;
+            mbar_arrive_expect_tx(&full[s], L::STAGE);
+            tma_load_2d(sa, &map_a, kbeg + i * TG_BK, m0, &full[s]);
+            tma_load_2d(sa + L::A_BYTES, &map_b, kbeg + i * TG_BK, n0, &full[s]);
+        }
+        *issued_s = i;
+    } else if (warp == 1 && lane == 0) {   // MMA issuer
+        constexpr uint32_t idesc_bf = idesc_f16(TG_BM, BN, 1), idesc_h = idesc_f16(TG_BM, BN, 0);
+        const uint32_t idesc = g.f16 ? idesc_h : idesc_bf;
+        int i = 0;
+        for (; i < nk; ++i) {
+            const int s = i % ST;
+            if (!mbar_wait(&full[s], (i / ST) & 1, abort_flag, g.status, ST_TIMEOUT_GEMM, g.wait_ns)) break;
+            tc_fence_after();
+            const uint32_t sa = smem_u32(smem + s * L::STAGE), sb = sa + L::A_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < TG_BK / 16; ++kk)
+                mma_f16(tmem, sdesc_sw128(sa + kk * 32), sdesc_sw128(sb + kk * 32), idesc, (i | kk) != 0);
+            mma_commit(&empty[s]);
+        }
+        *consumed_s = i;
+        mma_commit(done);   // arrives once every MMA issued above has completed
+    }
+    __syncwarp();
+    const bool ok = mbar_wait(done, 0, abort_flag, g.status, ST_TIMEOUT_GEMM, g.wait_ns) && nk > 0;
+    tc_fence_after();
+
+    // epilogue: warp w owns tensor-memory lanes (tile rows) 32 w .. 32 w + 31
+    const int r = m0 + warp * 32 + lane;
+    const bool row_ok = ok && r < g.M;
+    const bool lead = blockIdx.z == 0;
+#pragma unroll 1
+    for (int c = 0; c < BN / 32; ++c) {
+        if (!__any_sync(0xffffffffu, ok)) break;
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + c * 32, v);
+        tmem_wait_ld();
+        const int nb = n0 + c * 32;
+        if (!row_ok || nb >= g.N) continue;
+        const int nn = min(32, g.N - nb);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            if (j >= nn) break;
+            float y = v[j];
+            if (lead && g.bias) y += g.bias[nb + j];
+            y = tg_act(y, g.act);
+            if (lead && g.R) y += g.R[(long)r * g.ldr + nb + j];
+            v[j] = y;
+        }
+        float* crow = g.C ? g.C + (long)r * g.ldc + nb : nullptr;
+        if (crow) {
+            if (g.mode == 2) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                    if (j < nn) atomicAdd(crow + j, v[j]);
+            } else if (nn == 32 && ((g.ldc | nb) & 3) == 0 && ((uintptr_t)g.C & 15) == 0) {
+                float4* c4 = (float4*)crow;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    float4 o = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                    if (g.mode == 1) {
+                        const float4 p = c4[q];
+                        o.x += p.x;
+                        o.y += p.y;
+                        o.z += p.z;
+                        o.w += p.w;
+                    }
+                    c4[q] = o;
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                    if (j < nn) crow[j] = g.mode == 1 ? crow[j] + v[j] : v[j];
+            }
+        }
+        if (g.C16) {
+            uint16_t* hrow = g.C16 + (long)r * g.ldc16 + nb;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                if (j >= nn) break;
+                const uint32_t p = g.f16 ? pack_f16x2(v[j], 0.f) : pack_bf16x2(v[j], 0.f);
+                hrow[j] = (uint16_t)(p & 0xffffu);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0 && *abort_flag) {
+        // let what is still in flight land before shared and tensor memory are released
+        mbar_drain(done, 0, g.wait_ns);
+        for (int i = *consumed_s; i < *issued_s; ++i) mbar_drain(&full[i % ST], (i / ST) & 1, g.wait_ns);
+    }
+    __syncthreads();
+    if (warp == 2) tmem_dealloc(tmem, L::TMEM_COLS);
+}
+
+// 32 x 32 tile transpose through shared memory: dst[c, r] = src[r, c] for r < rows, c < cols;
+// dst columns rows .. ldd - 1 of each written row are zero.  dst row c0 + c for the source
+// column c (a column offset into a wider destination).
+__global__ void k_cvt_t(const float* __restrict__ src, long lds, int rows, int cols, uint16_t* __restrict__ dst,
+                        long ldd, int f16) {
+    __shared__ float tile[32][33];
+    const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 256 threads: 8 rows per pass
+    for (int i = ty; i < 32; i += 8) {
+        const int r = r0 + i, c = c0 + tx;
+        tile[i][tx] = (r < rows && c < cols) ? src[(long)r * lds + c] : 0.f;
+    }
+    __syncthreads();
+    for (int i = ty; i < 32; i += 8) {
+        const int c = c0 + i, r = r0 + tx;
+        if (c < cols && r < ldd) {
+            const float v = tile[tx][i];
+            const uint32_t p = f16 ? pack_f16x2(v, 0.f) : pack_bf16x2(v, 0.f);
+            dst[(long)c * ldd + r] = (uint16_t)(p & 0xffffu);
+        }
+    }
+}
+
+// dst[r, c] = src1[r, c] (c < k1), src2[r, c - k1] (k1 <= c < k1 + k2), 0 (up to ldd)
+__global__ void k_cvt(const float* __restrict__ s1, long ld1, int k1, const float* __restrict__ s2, long ld2,
+                      int k2, int rows, uint16_t* __restrict__ dst, long ldd, int f16) {
+    const long n = (long)rows * (ldd / 2);
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const long r = i / (ldd / 2);
+        const int c = (int)(i % (ldd / 2)) * 2;
+        float v[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int cc = c + u;
+            v[u] = cc < k1 ? s1[r * ld1 + cc] : (cc < k1 + k2 ? s2[r * ld2 + cc - k1] : 0.f);
+        }
+        ((uint32_t*)dst)[r * (ldd / 2) + c / 2] = f16 ? pack_f16x2(v[0], v[1]) : pack_bf16x2(v[0], v[1]);
+    }
+}
+
+typedef CUresult (*TgEncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                               const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                               CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+TgEncodeFn tg_encode() {
+    static TgEncodeFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (TgEncodeFn)p;
+    }
+    return fn;
+}
+
+// rows x Kp 16-bit matrix with row stride ld elements, boxes of box_rows x 64
+bool tg_map(CUtensorMap* map, const void* base, long Kp, long rows, long ld, uint32_t box_rows) {
+    TgEncodeFn fn = tg_encode();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    cuuint32_t box[2] = {(cuuint32_t)TG_BK, box_rows};
+    cuuint32_t es[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int BN, int ST>
+void tg_launch(const CUtensorMap& ma, const CUtensorMap& mb, const TgArgs& a, int splits, cudaStream_t st) {
+    using L = TgLayout<BN, ST>;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_gemm_tc<BN, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::BYTES);
+        attr = true;
+    }
+    dim3 grid((a.M + TG_BM - 1) / TG_BM, (a.N + BN - 1) / BN, splits);
+    k_gemm_tc<BN, ST><<<grid, 128, L::BYTES, st>>>(ma, mb, a);
+}
+
+}  // namespace
+
+bool gemm_tc(int f16, const void* A, long lda, const void* B, long ldb, int M, int N, int Kp, float* C, long ldc,
+             const float* bias, const float* R, long ldr, int act, int mode, int kchunk, uint16_t* C16, long ldc16,
+             unsigned* status, uint64_t wait_ns, cudaStream_t st) {
+    if (M <= 0 || N <= 0 || Kp <= 0) return true;
+    const int BN = N <= 64 ? 64 : (N <= 128 ? 128 : 256);
+    CUtensorMap ma, mb;
+    if (!tg_map(&ma, A, Kp, M, lda, TG_BM) || !tg_map(&mb, B, Kp, N, ldb, BN)) return false;
+    TgArgs a;
+    a.M = M;
+    a.N = N;
+    a.Kp = Kp;
+    if (kchunk <= 0 || kchunk >= Kp) kchunk = Kp;
+    a.kchunk = kchunk;
+    a.C = C;
+    a.ldc = ldc;
+    a.C16 = C16;
+    a.ldc16 = ldc16;
+    a.bias = bias;
+    a.R = R;
+    a.ldr = ldr;
+    a.mode = mode;
+    a.act = act;
+    a.f16 = f16;
+    a.status = status;
+    a.wait_ns = wait_ns;
+    const int splits = (Kp + kchunk - 1) / kchunk;
+    // three to four stages of 24-48 KB: two CTAs (and 2 x BN tensor-memory columns) per SM
+    if (BN == 64)
+        tg_launch<64, 4>(ma, mb, a, splits, st);
+    else if (BN == 128)
+        tg_launch<128, 3>(ma, mb, a, splits, st);
+    else
+        tg_launch<256, 2>(ma, mb, a, splits, st);
+    return true;
+}
+
+void cvt_16(const float* s1, long ld1, int k1, const float* s2, long ld2, int k2, int rows, uint16_t* dst, long ldd,
+            int f16, cudaStream_t st) {
+    const long n = (long)rows * (ldd / 2);
+    if (n <= 0) return;
+    const unsigned blocks = (unsigned)std::min<long>((n + 255) / 256, 148L * 16);
+    k_cvt<<<blocks, 256, 0, st>>>(s1, ld1, k1, s2, ld2, k2, rows, dst, ldd, f16);
+}
+
+void cvt_16_t(const float* src, long lds, int rows, int cols, uint16_t* dst, long ldd, int f16, cudaStream_t st) {
+    if (rows <= 0 || cols <= 0) return;
+    dim3 grid((unsigned)((ldd + 31) / 32), (unsigned)((cols + 31) / 32));
+    k_cvt_t<<<grid, 256, 0, st>>>(src, lds, rows, cols, dst, ldd, f16);
+}
+
+}  // namespace mlpf
+
+using namespace mlpf;
+
+extern "C" mlpf_status mlpf_gemm_tc(int32_t precision, const void* A, int64_t lda, const void* B, int64_t ldb,
+                                    int32_t M, int32_t N, int32_t K, float* C, int64_t ldc, const float* bias,
+                                    const float* R, int64_t ldr, int32_t act, int32_t mode, int32_t kchunk,
+                                    uint32_t* status, void* stream) {
+    if (precision != MLPF_BF16 && precision != MLPF_FP16) {
+        set_error("mlpf_gemm_tc: precision must be MLPF_BF16 or MLPF_FP16");
+        return MLPF_E_UNSUPPORTED;
+    }
+    if (!A || !B || !C || !status || M < 0 || N < 0 || K <= 0 || K % 64 || lda < K || ldb < K || lda % 8 ||
+        ldb % 8 || ((uintptr_t)A & 15) || ((uintptr_t)B & 15) || ldc < N || mode < 0 || mode > 2 || act < -1 ||
+        act > 1 || kchunk < 0 || kchunk % 64 || (R && ldr < N)) {
+        set_error("mlpf_gemm_tc: bad arguments");
+        return MLPF_E_INVALID;
+    }
+    if (!gemm_tc(precision == MLPF_FP16, A, lda, B, ldb, M, N, K, C, ldc, bias, R, ldr, act, mode, kchunk, nullptr,
+                 0, status, 2000000000ull, (cudaStream_t)stream)) {
+        set_error("mlpf_gemm_tc: tensor map encoding failed");
+        return MLPF_E_CUDA;
+    }
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_error(std::string("mlpf_gemm_tc: ") + cudaGetErrorString(e));
+        return MLPF_E_CUDA;
+    }
+    return MLPF_OK;
+}

@@ -568,6 +568,14 @@ struct Trainer {
     const float* fwd_x = nullptr;
     const int32_t* fwd_cu = nullptr;
     int32_t fwd_n = 0, fwd_total = 0;
+    // GEMM arithmetic: MLPF_FP32 (SIMT FFMA) or 16-bit tensor-core operands (MLPF_BF16,
+    // MLPF_FP16) with FP32 accumulation, FP32 master weights and FP32 activations
+    int prec = MLPF_FP32;
+    uint16_t* h16 = nullptr;       // operand scratch of the tensor-core GEMMs
+    uint16_t *ha = nullptr, *hb = nullptr, *ht1 = nullptr, *ht2 = nullptr;
+    size_t h16_rows = 0;
+    unsigned* status = nullptr;    // device status word of the bounded waits
+    bool tc_fail = false;          // a tensor map could not be encoded
 };
 
 namespace {
@@ -675,6 +683,59 @@ static void gemm_dx(const float* dY, long ldy, const float* W, long ldw, float* 
     dim3 grid(cdivu(K, GB), cdivu(T, GB), 1);
     k_gemm<<<grid, 256, 0, st>>>(T, K, N, dY, ldy, 1, W, ldw, 1, dX, ldx, accumulate, N);
 }
+static long r64(long v) { return (v + 63) / 64 * 64; }
+static constexpr uint64_t TRAIN_WAIT_NS = 2000000000ull;   // 2 s per bounded wait
+
+// y[T, N] = [X1 | X2] W^T + b (+ R): W row-major [N, K1 + K2]
+static void lin(Trainer& t, const float* X1, int ld1, int K1, const float* X2, int ld2, int K2, const float* W,
+                const float* b, const float* R, int ldr, float* Y, int ldy, int T, int N, cudaStream_t st) {
+    if (t.prec == MLPF_FP32) {
+        f32_linear(X1, ld1, K1, X2, ld2, K2, W, b, R, ldr, Y, ldy, T, N, -1, st);
+        return;
+    }
+    const int f16 = t.prec == MLPF_FP16, K = K1 + K2;
+    const long Kp = r64(K);
+    cvt_16(X1, ld1, K1, X2, ld2, K2, T, t.ha, Kp, f16, st);
+    cvt_16(W, K, K, nullptr, 0, 0, N, t.hb, Kp, f16, st);
+    if (!gemm_tc(f16, t.ha, Kp, t.hb, Kp, T, N, (int)Kp, Y, ldy, b, R, ldr, -1, 0, 0, nullptr, 0, t.status,
+                 TRAIN_WAIT_NS, st))
+        t.tc_fail = true;
+}
+// dW[N, K] += dY[T, N]^T X[T, K]
+static void dw(Trainer& t, const float* dY, long ldy, const float* X, long ldx, float* dW, long ldw, int T, int N,
+               int K, cudaStream_t st) {
+    if (t.prec == MLPF_FP32) {
+        gemm_dw(dY, ldy, X, ldx, dW, ldw, T, N, K, st);
+        return;
+    }
+    const int f16 = t.prec == MLPF_FP16;
+    const long Tp = r64(T);
+    cvt_16_t(dY, ldy, T, N, t.ht1, Tp, f16, st);   // [N, Tp]
+    cvt_16_t(X, ldx, T, K, t.ht2, Tp, f16, st);    // [K, Tp]
+    // split the reduction over the batch so that about two CTAs per SM work
+    const long bn = K <= 64 ? 64 : (K <= 128 ? 128 : 256);   // the GEMM's tile width for N = K
+    const long tiles = ((N + 127) / 128) * ((K + bn - 1) / bn);
+    const long splits = std::max(1L, std::min(Tp / 512, 296 / std::max(1L, tiles)));
+    const long kchunk = r64((Tp + splits - 1) / splits);
+    if (!gemm_tc(f16, t.ht1, Tp, t.ht2, Tp, N, K, (int)Tp, dW, ldw, nullptr, nullptr, 0, -1, 2, (int)kchunk, nullptr,
+                 0, t.status, TRAIN_WAIT_NS, st))
+        t.tc_fail = true;
+}
+// dX[T, K] (+)= dY[T, N] W[N, K] (W row stride ldw)
+static void dx(Trainer& t, const float* dY, long ldy, const float* W, long ldw, float* dX, long ldx, int T, int N,
+               int K, int accumulate, cudaStream_t st) {
+    if (t.prec == MLPF_FP32) {
+        gemm_dx(dY, ldy, W, ldw, dX, ldx, T, N, K, accumulate, st);
+        return;
+    }
+    const int f16 = t.prec == MLPF_FP16;
+    const long Np = r64(N);
+    cvt_16(dY, ldy, N, nullptr, 0, 0, T, t.ha, Np, f16, st);   // [T, Np]
+    cvt_16_t(W, ldw, N, K, t.hb, Np, f16, st);                 // W^T: [K, Np]
+    if (!gemm_tc(f16, t.ha, Np, t.hb, Np, T, K, (int)Np, dX, ldx, nullptr, nullptr, 0, -1, accumulate ? 1 : 0, 0,
+                 nullptr, 0, t.status, TRAIN_WAIT_NS, st))
+        t.tc_fail = true;
+}
 static void colsum(const float* Y, long ldy, int T, int N, float* out, cudaStream_t st) {
     const int rchunk = 2048;
     dim3 grid(cdivu(N, 32), cdivu(T, rchunk));
@@ -698,18 +759,18 @@ static void train_forward(Trainer& t, const Acts& a, const float* x, const int32
     const int d = c.d, F = c.ffn, act = c.act;
     const bool paper = c.arch == 1;
     if (paper) {   // track and cluster embeddings, selected per element type
-        f32_linear(x, 42, 42, nullptr, 0, 0, P(t, "emb.trk.w1"), P(t, "emb.trk.b1"), nullptr, 0, a.a1, d, T, d, -1, st);
+        lin(t, x, 42, 42, nullptr, 0, 0, P(t, "emb.trk.w1"), P(t, "emb.trk.b1"), nullptr, 0, a.a1, d, T, d, st);
         act_fwd(a.a1, a.h1, (long)T * d, act, st);
-        f32_linear(a.h1, d, d, nullptr, 0, 0, P(t, "emb.trk.w2"), P(t, "emb.trk.b2"), nullptr, 0, a.et, d, T, d, -1, st);
-        f32_linear(x, 42, 42, nullptr, 0, 0, P(t, "emb.clu.w1"), P(t, "emb.clu.b1"), nullptr, 0, a.a1c, d, T, d, -1, st);
+        lin(t, a.h1, d, d, nullptr, 0, 0, P(t, "emb.trk.w2"), P(t, "emb.trk.b2"), nullptr, 0, a.et, d, T, d, st);
+        lin(t, x, 42, 42, nullptr, 0, 0, P(t, "emb.clu.w1"), P(t, "emb.clu.b1"), nullptr, 0, a.a1c, d, T, d, st);
         act_fwd(a.a1c, a.h1c, (long)T * d, act, st);
-        f32_linear(a.h1c, d, d, nullptr, 0, 0, P(t, "emb.clu.w2"), P(t, "emb.clu.b2"), nullptr, 0, a.ec, d, T, d, -1, st);
+        lin(t, a.h1c, d, d, nullptr, 0, 0, P(t, "emb.clu.w2"), P(t, "emb.clu.b2"), nullptr, 0, a.ec, d, T, d, st);
         k_type_merge<<<cdivu((long)T * d, 256), 256, 0, st>>>(x, a.et, a.ec, a.zp[0], T, d);
         cudaMemcpyAsync(a.zr[0], a.zp[0], (size_t)T * d * sizeof(float), cudaMemcpyDeviceToDevice, st);
     } else {
-        f32_linear(x, 42, 42, nullptr, 0, 0, P(t, "emb.w1"), P(t, "emb.b1"), nullptr, 0, a.a1, d, T, d, -1, st);
+        lin(t, x, 42, 42, nullptr, 0, 0, P(t, "emb.w1"), P(t, "emb.b1"), nullptr, 0, a.a1, d, T, d, st);
         act_fwd(a.a1, a.h1, (long)T * d, act, st);
-        f32_linear(a.h1, d, d, nullptr, 0, 0, P(t, "emb.w2"), P(t, "emb.b2"), nullptr, 0, a.zp[0], d, T, d, -1, st);
+        lin(t, a.h1, d, d, nullptr, 0, 0, P(t, "emb.w2"), P(t, "emb.b2"), nullptr, 0, a.zp[0], d, T, d, st);
     }
     auto stack = [&](const char* pre, int L, const std::vector<float*>& z, const std::vector<float*>& ln1,
                      const std::vector<float*>& qkv, const std::vector<float*>& o, const std::vector<float*>& lse,
@@ -720,49 +781,48 @@ static void train_forward(Trainer& t, const Acts& a, const float* x, const int32
             f32_layernorm(z[l], P(t, p + "ln1.g"), P(t, p + "ln1.b"), ln1[l], T, d, st);
             const char* qn[3] = {"q", "k", "v"};
             for (int i = 0; i < 3; ++i)
-                f32_linear(ln1[l], d, d, nullptr, 0, 0, P(t, p + "w" + qn[i]), P(t, p + "b" + qn[i]), nullptr, 0,
-                           qkv[l] + i * d, 3 * d, T, d, -1, st);
+                lin(t, ln1[l], d, d, nullptr, 0, 0, P(t, p + "w" + qn[i]), P(t, p + "b" + qn[i]), nullptr, 0,
+                           qkv[l] + i * d, 3 * d, T, d, st);
             f32_attention(qkv[l], o[l], cu, n_events, max_n, d, c.heads, lse[l], st);
-            f32_linear(o[l], d, d, nullptr, 0, 0, P(t, p + "wo"), P(t, p + "bo"), z[l], d, zm[l], d, T, d, -1, st);
+            lin(t, o[l], d, d, nullptr, 0, 0, P(t, p + "wo"), P(t, p + "bo"), z[l], d, zm[l], d, T, d, st);
             f32_layernorm(zm[l], P(t, p + "ln2.g"), P(t, p + "ln2.b"), ln2[l], T, d, st);
-            f32_linear(ln2[l], d, d, nullptr, 0, 0, P(t, p + "ffn.w1"), P(t, p + "ffn.b1"), nullptr, 0, af[l], F, T, F,
-                       -1, st);
+            lin(t, ln2[l], d, d, nullptr, 0, 0, P(t, p + "ffn.w1"), P(t, p + "ffn.b1"), nullptr, 0, af[l], F, T, F,
+                       st);
             act_fwd(af[l], hf[l], (long)T * F, act, st);
-            f32_linear(hf[l], F, F, nullptr, 0, 0, P(t, p + "ffn.w2"), P(t, p + "ffn.b2"), zm[l], d, z[l + 1], d, T, d,
-                       -1, st);
+            lin(t, hf[l], F, F, nullptr, 0, 0, P(t, p + "ffn.w2"), P(t, p + "ffn.b2"), zm[l], d, z[l + 1], d, T, d,
+                       st);
         }
         f32_layernorm(z[L], P(t, std::string(pre) + ".lnf.g"), P(t, std::string(pre) + ".lnf.b"), out, T, d, st);
     };
     stack("pid", c.l_pid, a.zp, a.ln1p, a.qkvp, a.op, a.lsep, a.zmp, a.ln2p, a.afp, a.hfp, a.hp);
     if (!paper) {
-        f32_linear(x, 42, 42, a.hp, d, d, P(t, "remb.w1"), P(t, "remb.b1"), nullptr, 0, a.ar, d, T, d, -1, st);
+        lin(t, x, 42, 42, a.hp, d, d, P(t, "remb.w1"), P(t, "remb.b1"), nullptr, 0, a.ar, d, T, d, st);
         act_fwd(a.ar, a.hr, (long)T * d, act, st);
-        f32_linear(a.hr, d, d, nullptr, 0, 0, P(t, "remb.w2"), P(t, "remb.b2"), nullptr, 0, a.zr[0], d, T, d, -1, st);
+        lin(t, a.hr, d, d, nullptr, 0, 0, P(t, "remb.w2"), P(t, "remb.b2"), nullptr, 0, a.zr[0], d, T, d, st);
     }
     stack("reg", c.l_reg, a.zr, a.ln1r, a.qkvr, a.orr, a.lser, a.zmr, a.ln2r, a.afr, a.hfr, a.hreg);
     if (paper) {   // binary head -> logit column 0, PID head -> columns 1..5
-        f32_linear(a.hp, d, d, nullptr, 0, 0, P(t, "head.bin.w1"), P(t, "head.bin.b1"), nullptr, 0, a.ac, d, T, d, -1, st);
+        lin(t, a.hp, d, d, nullptr, 0, 0, P(t, "head.bin.w1"), P(t, "head.bin.b1"), nullptr, 0, a.ac, d, T, d, st);
         act_fwd(a.ac, a.hc, (long)T * d, act, st);
-        f32_linear(a.hc, d, d, nullptr, 0, 0, P(t, "head.bin.w2"), P(t, "head.bin.b2"), nullptr, 0, a.logits, 6, T, 1,
-                   -1, st);
-        f32_linear(a.hp, d, d, nullptr, 0, 0, P(t, "head.pid.w1"), P(t, "head.pid.b1"), nullptr, 0, a.ac2, d, T, d, -1,
+        lin(t, a.hc, d, d, nullptr, 0, 0, P(t, "head.bin.w2"), P(t, "head.bin.b2"), nullptr, 0, a.logits, 6, T, 1,
                    st);
+        lin(t, a.hp, d, d, nullptr, 0, 0, P(t, "head.pid.w1"), P(t, "head.pid.b1"), nullptr, 0, a.ac2, d, T, d, st);
         act_fwd(a.ac2, a.hc2, (long)T * d, act, st);
-        f32_linear(a.hc2, d, d, nullptr, 0, 0, P(t, "head.pid.w2"), P(t, "head.pid.b2"), nullptr, 0, a.logits + 1, 6, T,
-                   5, -1, st);
+        lin(t, a.hc2, d, d, nullptr, 0, 0, P(t, "head.pid.w2"), P(t, "head.pid.b2"), nullptr, 0, a.logits + 1, 6, T,
+                   5, st);
     } else {
-        f32_linear(a.hp, d, d, nullptr, 0, 0, P(t, "head.cls.w1"), P(t, "head.cls.b1"), nullptr, 0, a.ac, d, T, d, -1, st);
+        lin(t, a.hp, d, d, nullptr, 0, 0, P(t, "head.cls.w1"), P(t, "head.cls.b1"), nullptr, 0, a.ac, d, T, d, st);
         act_fwd(a.ac, a.hc, (long)T * d, act, st);
-        f32_linear(a.hc, d, d, nullptr, 0, 0, P(t, "head.cls.w2"), P(t, "head.cls.b2"), nullptr, 0, a.logits, 6, T, 6,
-                   -1, st);
+        lin(t, a.hc, d, d, nullptr, 0, 0, P(t, "head.cls.w2"), P(t, "head.cls.b2"), nullptr, 0, a.logits, 6, T, 6,
+                   st);
     }
     int off = 0;
     for (int k = 0; k < 4; ++k) {
         const std::string p = std::string("head.") + RH[k] + ".";
-        f32_linear(a.hreg, d, d, nullptr, 0, 0, P(t, p + "w1"), P(t, p + "b1"), nullptr, 0, a.ah[k], d, T, d, -1, st);
+        lin(t, a.hreg, d, d, nullptr, 0, 0, P(t, p + "w1"), P(t, p + "b1"), nullptr, 0, a.ah[k], d, T, d, st);
         act_fwd(a.ah[k], a.hh[k], (long)T * d, act, st);
-        f32_linear(a.hh[k], d, d, nullptr, 0, 0, P(t, p + "w2"), P(t, p + "b2"), nullptr, 0, a.raw + off, 5, T, RW[k],
-                   -1, st);
+        lin(t, a.hh[k], d, d, nullptr, 0, 0, P(t, p + "w2"), P(t, p + "b2"), nullptr, 0, a.raw + off, 5, T, RW[k],
+                   st);
         off += RW[k];
     }
 }
@@ -776,9 +836,9 @@ static void train_backward(Trainer& t, const Acts& a, const float* x, const int3
     // linear y = x W^T + b: weight, bias and (optionally) input gradients
     auto lin_bwd = [&](const float* dY, int ldy, const float* X, int ldx, const std::string& wn,
                        const std::string& bn, int N, int K, float* dX, int ldxo, int acc) {
-        gemm_dw(dY, ldy, X, ldx, G(t, wn), K, T, N, K, st);
+        dw(t, dY, ldy, X, ldx, G(t, wn), K, T, N, K, st);
         colsum(dY, ldy, T, N, G(t, bn), st);
-        if (dX) gemm_dx(dY, ldy, P(t, wn), K, dX, ldxo, T, N, K, acc, st);
+        if (dX) dx(t, dY, ldy, P(t, wn), K, dX, ldxo, T, N, K, acc, st);
     };
     const bool paper = c.arch == 1;
     if (paper) {   // binary head (logit column 0) and PID head (columns 1..5)
@@ -855,10 +915,10 @@ static void train_backward(Trainer& t, const Acts& a, const float* x, const int3
     act_bwd(a.ar, a.dx1, a.dx2, (long)T * d, act, st);
     {
         const int Kin = 42 + d;
-        gemm_dw(a.dx2, d, x, 42, G(t, "remb.w1"), Kin, T, d, 42, st);
-        gemm_dw(a.dx2, d, a.hp, d, G(t, "remb.w1") + 42, Kin, T, d, d, st);
+        dw(t, a.dx2, d, x, 42, G(t, "remb.w1"), Kin, T, d, 42, st);
+        dw(t, a.dx2, d, a.hp, d, G(t, "remb.w1") + 42, Kin, T, d, d, st);
         colsum(a.dx2, d, T, d, G(t, "remb.b1"), st);
-        gemm_dx(a.dx2, d, P(t, "remb.w1") + 42, Kin, a.dhp, d, T, d, d, 1, st);
+        dx(t, a.dx2, d, P(t, "remb.w1") + 42, Kin, a.dhp, d, T, d, d, 1, st);
     }
     stack_bwd("pid", c.l_pid, a.zp, a.ln1p, a.qkvp, a.op, a.lsep, a.zmp, a.ln2p, a.afp, a.hfp, a.dhp);
     // embedding
@@ -884,6 +944,30 @@ struct mlpf_trainer {
         }                                                                           \
     } while (0)
 
+// Operand scratch of the tensor-core GEMMs for `rows` rows: the widest GEMM operand
+// (K or N up to max(42 + d, ffn), padded to 64) row-major, a weight image, and two
+// transposed operands whose reduction runs over the rows.
+static size_t h16_elems(const mlpf_config& c, size_t rows, size_t* kw_out = nullptr) {
+    const size_t kw = (size_t)r64(std::max(42 + c.d, std::max(c.ffn, c.d)));
+    if (kw_out) *kw_out = kw;
+    return rows * kw + kw * kw + 2 * kw * (size_t)r64((long)rows);
+}
+static mlpf_status ensure_h16(Trainer& t) {
+    if (t.prec == MLPF_FP32 || (t.h16 && t.h16_rows == t.cap_rows)) return MLPF_OK;
+    if (t.h16) cudaFree(t.h16);
+    t.h16 = nullptr;
+    t.h16_rows = 0;
+    size_t kw;
+    const size_t n = h16_elems(t.m.cfg, t.cap_rows, &kw);
+    TCK(cudaMalloc(&t.h16, n * sizeof(uint16_t)));
+    t.h16_rows = t.cap_rows;
+    t.ha = t.h16;
+    t.hb = t.ha + t.cap_rows * kw;
+    t.ht1 = t.hb + kw * kw;
+    t.ht2 = t.ht1 + kw * (size_t)r64((long)t.cap_rows);
+    return MLPF_OK;
+}
+
 // Activation workspace for `total` rows (grown, never shrunk).
 static mlpf_status ensure_acts(Trainer& t, int32_t total) {
     if ((size_t)total > t.cap_rows) {
@@ -895,6 +979,19 @@ static mlpf_status ensure_acts(Trainer& t, int32_t total) {
         TCK(cudaMalloc(&t.act, n * sizeof(float)));
         t.cap_rows = rows;
         t.act_floats = n;
+    }
+    return ensure_h16(t);
+}
+
+// Reads and clears the device status word (after a synchronization): MLPF_E_TIMEOUT if a
+// bounded wait of a tensor-core GEMM ran out.
+static mlpf_status trainer_status(Trainer& t) {
+    unsigned h = 0;
+    TCK(cudaMemcpy(&h, t.status, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    if (h) {
+        TCK(cudaMemset(t.status, 0, sizeof(unsigned)));
+        set_error("a bounded wait in a training GEMM ran out");
+        return MLPF_E_TIMEOUT;
     }
     return MLPF_OK;
 }
@@ -929,9 +1026,15 @@ static mlpf_status trainer_step_impl(mlpf_trainer* tt, const float* x, const int
         k_lamb_apply<<<t.n_chunks, 256, 0, st>>>(t.w, t.g, t.chunks, t.scratch + 1, t.scratch + 1 + nt, lr);
     }
     TCK(cudaGetLastError());
+    if (t.tc_fail) {
+        t.tc_fail = false;
+        set_error("tensor map encoding failed for a training GEMM");
+        return MLPF_E_CUDA;
+    }
     if (loss_out) {
         TCK(cudaMemcpyAsync(loss_out, t.scratch, sizeof(double), cudaMemcpyDeviceToHost, st));
         TCK(cudaStreamSynchronize(st));
+        return trainer_status(t);
     }
     return MLPF_OK;
 }
@@ -944,7 +1047,7 @@ void mlpf_trainer_free(mlpf_trainer* tt) {
     Trainer& t = tt->t;
     cudaSetDevice(t.m.device);
     for (void* p : {(void*)t.w, (void*)t.g, (void*)t.mom, (void*)t.var, (void*)t.chunks, (void*)t.scratch,
-                    (void*)t.act})
+                    (void*)t.act, (void*)t.h16, (void*)t.status})
         if (p) cudaFree(p);
     delete tt;
 }
@@ -1002,6 +1105,8 @@ mlpf_status mlpf_trainer_create(const void* blob, size_t nbytes, int device, mlp
         if (e == cudaSuccess) e = cudaMalloc(p, t.n_params * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&t.chunks, ch.size() * sizeof(int4));
     if (e == cudaSuccess) e = cudaMalloc(&t.scratch, (1 + 2 * t.names.size()) * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&t.status, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(t.status, 0, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemcpy(t.w, hw.data(), t.n_params * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(t.chunks, ch.data(), ch.size() * sizeof(int4), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(t.mom, 0, t.n_params * 4);
@@ -1016,6 +1121,19 @@ mlpf_status mlpf_trainer_create(const void* blob, size_t nbytes, int device, mlp
 }
 
 int64_t mlpf_trainer_num_params(const mlpf_trainer* tt) { return tt ? (int64_t)tt->t.n_params : -1; }
+
+mlpf_status mlpf_trainer_set_precision(mlpf_trainer* tt, int32_t precision) {
+    if (!tt) { set_error("NULL trainer"); return MLPF_E_INVALID; }
+    if (precision != MLPF_FP32 && precision != MLPF_BF16 && precision != MLPF_FP16) {
+        set_error("trainer GEMM precision must be MLPF_FP32, MLPF_BF16 or MLPF_FP16");
+        return MLPF_E_UNSUPPORTED;
+    }
+    Trainer& t = tt->t;
+    t.prec = precision;
+    t.fwd_ok = false;
+    TCK(cudaSetDevice(t.m.device));
+    return ensure_h16(t);
+}
 
 mlpf_status mlpf_trainer_step(mlpf_trainer* tt, const float* x, const int32_t* cu, int32_t n_events,
                               int32_t total, int32_t max_n, const float* t_logits, const float* t_reg, float lr,

@@ -27,7 +27,7 @@ def test_header_symbols_match_binding():
 def test_library_exports_every_declared_symbol(lib):
     for name in declared_symbols():
         assert hasattr(lib, name), name
-    assert lib.mlpf_abi_version() == 104
+    assert lib.mlpf_abi_version() == 105
 
 
 def load_status(lib, blob):

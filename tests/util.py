@@ -41,16 +41,42 @@ def make_model(cfg, seed, perturbed=False, cls_scale=1.0):
     return Model(synth.pack_blob(cfg, w)), w
 
 
-def f64_distill_reference(W, cfg, x, cu, tl, tr):
+def f64_distill_reference(W, cfg, x, cu, tl, tr, operand_format=None):
     """The distillation loss of a sequential-architecture model and its gradient
     from an independent torch float64 model (torch.nn.functional layers, exact
-    scaled-dot-product attention, autograd).  Returns (loss, {name: grad})."""
+    scaled-dot-product attention, autograd).  Returns (loss, {name: grad}).
+
+    operand_format "bf16" / "fp16": every linear layer rounds its GEMM operands to that
+    format, in the forward (input and weight) and in the backward (the output gradient,
+    with the rounded weight for the input gradient and the rounded input for the weight
+    gradient): the arithmetic of a mixed-precision training step whose GEMMs run on
+    16-bit tensor cores with exact accumulation; everything else stays float64."""
     import torch
     import torch.nn.functional as F
 
     import oracle
     P = {k: torch.tensor(np.asarray(v, np.float64), requires_grad=True) for k, v in W.items()}
     act = (lambda t: F.relu(t)) if cfg.act == 1 else (lambda t: F.gelu(t, approximate="none"))
+    if operand_format is not None:
+        dt = {"bf16": torch.bfloat16, "fp16": torch.float16}[operand_format]
+        rnd = lambda t: t.float().to(dt).double()
+
+        class RoundedLinear(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, t, w, b):
+                tr_, wr = rnd(t), rnd(w)
+                ctx.save_for_backward(tr_, wr)
+                return tr_ @ wr.T + b
+
+            @staticmethod
+            def backward(ctx, gy):
+                tr_, wr = ctx.saved_tensors
+                gr = rnd(gy)
+                return gr @ wr, gr.T @ tr_, gy.sum(0)
+
+        F = type("F", (), {k: staticmethod(getattr(torch.nn.functional, k)) for k in
+                           ("relu", "gelu", "layer_norm", "scaled_dot_product_attention", "log_softmax")})
+        F.linear = staticmethod(lambda t, w, b: RoundedLinear.apply(t, w, b))
     mlp = lambda t, p: F.linear(act(F.linear(t, P[p + "w1"], P[p + "b1"])), P[p + "w2"], P[p + "b2"])
     ln = lambda t, p: F.layer_norm(t, (cfg.d,), P[p + ".g"], P[p + ".b"], eps=1e-5)
 
