@@ -328,12 +328,14 @@ mlpf_status mlpf_trainer_step_supervised(mlpf_trainer* t, const float* x, const 
                                          float* grads_out, double* loss_out, void* stream);
 
 /*
- * GEMM arithmetic of the trainer's linear layers (forward, input and weight
- * gradients; Sec. 5.3 trains the model in mixed precision).  MLPF_FP32 (default):
- * SIMT FP32 FMAs.  MLPF_BF16 / MLPF_FP16: the operands of every linear-layer GEMM are
- * rounded to that 16-bit format and multiplied on the tcgen05 tensor cores (mlpf_gemm_tc)
- * with FP32 accumulation; master weights, optimizer state, activations, LayerNorm,
- * attention (forward and backward) and the loss stay FP32.  Takes effect from the next
+ * Arithmetic of the trainer's products (Sec. 5.3 trains the model in mixed
+ * precision).  MLPF_FP32 (default): SIMT FP32 FMAs everywhere.  MLPF_BF16 / MLPF_FP16:
+ * the operands of every linear-layer GEMM (forward, input and weight gradients) are
+ * rounded to that 16-bit format and multiplied on the tcgen05 tensor cores (mlpf_gemm_tc),
+ * and the attention forward and backward run on warp-level tensor-core MMAs with 16-bit
+ * Q, K, V, probabilities, output and score gradients; FP32 accumulation, softmax
+ * statistics and log-sum-exp.  Master weights, optimizer state, activations, LayerNorm
+ * and the loss stay FP32.  Takes effect from the next
  * forward or step (a pending mlpf_trainer_forward is invalidated).  A bounded wait
  * that runs out inside a tensor-core GEMM is reported as MLPF_E_TIMEOUT by the next
  * synchronous step (loss_out given).  Errors: MLPF_E_INVALID (NULL),

@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmlpf.so")
-SOURCES = ["api.cu", "k_f32.cu", "k_tc.cu", "noalloc.cu", "k_train.cu", "gate.cu", "probe.cu", "jets.cu", "k_gemm_tc.cu"]
+SOURCES = ["api.cu", "k_f32.cu", "k_tc.cu", "noalloc.cu", "k_train.cu", "gate.cu", "probe.cu", "jets.cu", "k_gemm_tc.cu", "k_attn_train.cu"]
 HEADERS = ["ptx.cuh", "internal.h"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",

@@ -203,6 +203,16 @@ void cvt_16(const float* s1, long ld1, int k1, const float* s2, long ld2, int k2
             int f16, cudaStream_t st);
 void cvt_16_t(const float* src, long lds, int rows, int cols, uint16_t* dst, long ldd, int f16, cudaStream_t st);
 
+// Varlen self-attention of the training step on the tensor cores (k_attn_train.cu):
+// qkv [T, 3d] FP32 (Q | K | V, heads of dh = d / heads in {16, 32, 64}), out / dO [T, d],
+// lse / D [T, heads] (natural-log log-sum-exp of the scaled scores; rowsum(dO o O)),
+// dqkv [T, 3d].  16-bit operands (f16: FP16, else BF16), FP32 accumulation and
+// statistics.  Return false for an unsupported head width.
+bool attn_train_fwd_tc(int f16, const float* qkv, float* out, float* lse, const int32_t* cu, int n_events, int max_n,
+                       int d, int heads, cudaStream_t st);
+bool attn_train_bwd_tc(int f16, const float* qkv, const float* dO, const float* lse, const float* D, float* dqkv,
+                       const int32_t* cu, int n_events, int max_n, int d, int heads, cudaStream_t st);
+
 // tensor-core path preparation (weights images, tensor maps)
 bool tc_prepare_weights(Model& m);
 bool tc_make_maps(Model& m);

@@ -1,0 +1,346 @@
+// Varlen self-attention of the training step on the tensor cores (warp-level m16n8k16
+// MMAs, BF16 or FP16 operands, FP32 accumulation and softmax statistics): forward with
+// the rows' log-sum-exp kept for the backward, and the backward as two kernels that
+// recompute the probabilities from Q, K and the log-sum-exp (Sec. 5.3, Eq. 4: per head
+// softmax(Q K^T / sqrt(dh)) V within each event; its gradient
+//   dV = P^T dO,  dP = dO V^T,  dS = P o (dP - rowsum(dO o O)),
+//   dQ = dS K / sqrt(dh),  dK = dS^T Q / sqrt(dh)).
+// Activations stay FP32 in HBM ([T, 3d] Q|K|V, [T, d] O and dO); each CTA converts the
+// 64-row tiles it stages into shared memory.  One CTA per (64-row tile, head, event),
+// four warps of 16 rows; scores in log2 units (Q pre-multiplied by log2(e)/sqrt(dh)).
+#include <cuda_runtime.h>
+
+#include "internal.h"
+#include "ptx.cuh"
+
+namespace mlpf {
+namespace {
+
+constexpr float kLog2e = 1.4426950408889634f;
+
+// Stage rows r0 .. r0 + 63 of an event (rows >= n are zero) of DH columns starting at
+// `col` of a row-major FP32 matrix (row stride ld) into shared memory as 16-bit values
+// times `mul`, row stride DH + 8 elements (16-byte padded rows: conflict-free ldmatrix).
+template <int DH, bool F16>
+__device__ __forceinline__ void stage_tile(uint16_t* dst, const float* __restrict__ src, long ld, int col,
+                                           int start, int r0, int n, float mul) {
+    constexpr int LD = DH + 8, PER_ROW = DH / 4;
+    for (int i = threadIdx.x; i < 64 * PER_ROW; i += 128) {
+        const int r = i / PER_ROW, c4 = (i % PER_ROW) * 4;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (r0 + r < n) v = *reinterpret_cast<const float4*>(src + (long)(start + r0 + r) * ld + col + c4);
+        uint2 p;
+        p.x = pack2<F16>(v.x * mul, v.y * mul);
+        p.y = pack2<F16>(v.z * mul, v.w * mul);
+        *reinterpret_cast<uint2*>(dst + r * LD + c4) = p;
+    }
+}
+
+// A fragment (16 x 16) of rows rb.., columns kc.. of a [rows][LD] tile
+template <int LD>
+__device__ __forceinline__ void load_a(const uint16_t* t, int rb, int kc, uint32_t* a) {
+    const int l = threadIdx.x & 31;
+    const uint16_t* p = t + (rb + (l & 7) + ((l >> 3) & 1) * 8) * LD + kc + (l >> 4) * 8;
+    ldsm_x4(smem_u32(p), a[0], a[1], a[2], a[3]);
+}
+// B fragments of two n-tiles (n = nb .. nb + 15) for k = kc .. kc + 15 from a tile
+// stored [n][k]: b[0], b[1] for n-tile 0, b[2], b[3] for n-tile 1
+template <int LD>
+__device__ __forceinline__ void load_b_nk(const uint16_t* t, int nb, int kc, uint32_t* b) {
+    const int l = threadIdx.x & 31, i = l >> 3;
+    const uint16_t* p = t + (nb + (l & 7) + (i >> 1) * 8) * LD + kc + (i & 1) * 8;
+    ldsm_x4(smem_u32(p), b[0], b[1], b[2], b[3]);
+}
+// the same from a tile stored [k][n] (k = kb .. kb + 15, n = nc .. nc + 15)
+template <int LD>
+__device__ __forceinline__ void load_b_kn(const uint16_t* t, int kb, int nc, uint32_t* b) {
+    const int l = threadIdx.x & 31, i = l >> 3;
+    const uint16_t* p = t + (kb + (l & 7) + (i & 1) * 8) * LD + nc + (i >> 1) * 8;
+    ldsm_x4_t(smem_u32(p), b[0], b[1], b[2], b[3]);
+}
+// accumulator fragments of n-tiles 2 kk and 2 kk + 1 -> A fragment for k = 16 kk ..
+template <bool F16>
+__device__ __forceinline__ void c_to_a(const float* c0, const float* c1, uint32_t* a) {
+    a[0] = pack2<F16>(c0[0], c0[1]);
+    a[1] = pack2<F16>(c0[2], c0[3]);
+    a[2] = pack2<F16>(c1[0], c1[1]);
+    a[3] = pack2<F16>(c1[2], c1[3]);
+}
+
+// S (16 rows x 64 columns, 8 n-tiles) = A (16 x DH, fragments a) times the tile `t`
+// stored [n][k] (64 x DH)^T
+template <int DH, bool F16>
+__device__ __forceinline__ void scores(const uint32_t (*a)[4], const uint16_t* t, float (*s)[4]) {
+    constexpr int LD = DH + 8;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) s[j][0] = s[j][1] = s[j][2] = s[j][3] = 0.f;
+#pragma unroll
+    for (int kk = 0; kk < DH / 16; ++kk)
+#pragma unroll
+        for (int np = 0; np < 4; ++np) {
+            uint32_t b[4];
+            load_b_nk<LD>(t, np * 16, kk * 16, b);
+            mma16816<F16>(s[2 * np], a[kk], b[0], b[1]);
+            mma16816<F16>(s[2 * np + 1], a[kk], b[2], b[3]);
+        }
+}
+// acc (16 x DH) += P (16 x 64, accumulator fragments p) times the tile `t` stored [k][n]
+template <int DH, bool F16>
+__device__ __forceinline__ void accumulate(const float (*p)[4], const uint16_t* t, float (*acc)[4]) {
+    constexpr int LD = DH + 8;
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+        uint32_t a[4];
+        c_to_a<F16>(p[2 * kk], p[2 * kk + 1], a);
+#pragma unroll
+        for (int dp = 0; dp < DH / 16; ++dp) {
+            uint32_t b[4];
+            load_b_kn<LD>(t, kk * 16, dp * 16, b);
+            mma16816<F16>(acc[2 * dp], a, b[0], b[1]);
+            mma16816<F16>(acc[2 * dp + 1], a, b[2], b[3]);
+        }
+    }
+}
+
+template <int DH, bool F16>
+__global__ void __launch_bounds__(128) k_attn_fwd_tc(const float* __restrict__ qkv, float* __restrict__ out,
+                                                     float* __restrict__ lse, const int32_t* __restrict__ cu, int d,
+                                                     float scale) {
+    constexpr int LD = DH + 8;
+    __shared__ __align__(16) uint16_t Qs[64 * LD], Ks[64 * LD], Vs[64 * LD];
+    const int e = blockIdx.z, h = blockIdx.y, H = gridDim.y;
+    const int start = cu[e], n = cu[e + 1] - start, q0 = blockIdx.x * 64;
+    if (q0 >= n) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
+    const long ld = 3L * d;
+    stage_tile<DH, F16>(Qs, qkv, ld, h * DH, start, q0, n, scale * kLog2e);
+    __syncthreads();
+    uint32_t qa[DH / 16][4];
+#pragma unroll
+    for (int kk = 0; kk < DH / 16; ++kk) load_a<LD>(Qs, warp * 16, kk * 16, qa[kk]);
+    float o[DH / 8][4] = {};
+    float m[2] = {-INFINITY, -INFINITY}, l[2] = {0.f, 0.f};
+    for (int kb = 0; kb < n; kb += 64) {
+        __syncthreads();
+        stage_tile<DH, F16>(Ks, qkv, ld, d + h * DH, start, kb, n, 1.f);
+        stage_tile<DH, F16>(Vs, qkv, ld, 2 * d + h * DH, start, kb, n, 1.f);
+        __syncthreads();
+        float s[8][4];
+        scores<DH, F16>(qa, Ks, s);
+        float mx[2] = {m[0], m[1]};
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (kb + j * 8 + 2 * c + (u & 1) >= n) s[j][u] = -INFINITY;
+                mx[u >> 1] = fmaxf(mx[u >> 1], s[j][u]);
+            }
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            mx[r] = fmaxf(mx[r], __shfl_xor_sync(0xffffffffu, mx[r], 1));
+            mx[r] = fmaxf(mx[r], __shfl_xor_sync(0xffffffffu, mx[r], 2));
+        }
+        const float al[2] = {ex2_approx(m[0] - mx[0]), ex2_approx(m[1] - mx[1])};
+        l[0] *= al[0];
+        l[1] *= al[1];
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                s[j][u] = ex2_approx(s[j][u] - mx[u >> 1]);
+                l[u >> 1] += s[j][u];
+            }
+#pragma unroll
+        for (int j = 0; j < DH / 8; ++j)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) o[j][u] *= al[u >> 1];
+        m[0] = mx[0];
+        m[1] = mx[1];
+        accumulate<DH, F16>(s, Vs, o);
+    }
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        l[r] += __shfl_xor_sync(0xffffffffu, l[r], 1);
+        l[r] += __shfl_xor_sync(0xffffffffu, l[r], 2);
+    }
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int row = q0 + warp * 16 + g + 8 * r;
+        if (row >= n) continue;
+        const float inv = 1.f / l[r];
+        float* orow = out + (long)(start + row) * d + h * DH;
+#pragma unroll
+        for (int j = 0; j < DH / 8; ++j)
+            *reinterpret_cast<float2*>(orow + j * 8 + 2 * c) = make_float2(o[j][2 * r] * inv, o[j][2 * r + 1] * inv);
+        if (c == 0) lse[(long)(start + row) * H + h] = (m[r] + __log2f(l[r])) / kLog2e;
+    }
+}
+
+// dQ: one CTA per 64 query rows; loops over the event's key tiles.
+template <int DH, bool F16>
+__global__ void __launch_bounds__(128) k_attn_dq_tc(const float* __restrict__ qkv, const float* __restrict__ dO,
+                                                    const float* __restrict__ lse, const float* __restrict__ D,
+                                                    float* __restrict__ dqkv, const int32_t* __restrict__ cu, int d,
+                                                    float scale) {
+    constexpr int LD = DH + 8;
+    __shared__ __align__(16) uint16_t Qs[64 * LD], Gs[64 * LD], Ks[64 * LD], Vs[64 * LD];
+    const int e = blockIdx.z, h = blockIdx.y, H = gridDim.y;
+    const int start = cu[e], n = cu[e + 1] - start, q0 = blockIdx.x * 64;
+    if (q0 >= n) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
+    const long ld = 3L * d;
+    stage_tile<DH, F16>(Qs, qkv, ld, h * DH, start, q0, n, scale * kLog2e);
+    stage_tile<DH, F16>(Gs, dO, d, h * DH, start, q0, n, 1.f);
+    __syncthreads();
+    uint32_t qa[DH / 16][4], ga[DH / 16][4];
+#pragma unroll
+    for (int kk = 0; kk < DH / 16; ++kk) {
+        load_a<LD>(Qs, warp * 16, kk * 16, qa[kk]);
+        load_a<LD>(Gs, warp * 16, kk * 16, ga[kk]);
+    }
+    float L2[2], Dr[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int row = q0 + warp * 16 + g + 8 * r;
+        L2[r] = row < n ? lse[(long)(start + row) * H + h] * kLog2e : 0.f;
+        Dr[r] = row < n ? D[(long)(start + row) * H + h] : 0.f;
+    }
+    float dq[DH / 8][4] = {};
+    for (int kb = 0; kb < n; kb += 64) {
+        __syncthreads();
+        stage_tile<DH, F16>(Ks, qkv, ld, d + h * DH, start, kb, n, 1.f);
+        stage_tile<DH, F16>(Vs, qkv, ld, 2 * d + h * DH, start, kb, n, 1.f);
+        __syncthreads();
+        float s[8][4], dp[8][4];
+        scores<DH, F16>(qa, Ks, s);
+        scores<DH, F16>(ga, Vs, dp);
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const bool valid = kb + j * 8 + 2 * c + (u & 1) < n;
+                const float p = valid ? ex2_approx(s[j][u] - L2[u >> 1]) : 0.f;
+                s[j][u] = p * (dp[j][u] - Dr[u >> 1]);   // dS
+            }
+        accumulate<DH, F16>(s, Ks, dq);
+    }
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int row = q0 + warp * 16 + g + 8 * r;
+        if (row >= n) continue;
+        float* dst = dqkv + (long)(start + row) * ld + h * DH;
+#pragma unroll
+        for (int j = 0; j < DH / 8; ++j)
+            *reinterpret_cast<float2*>(dst + j * 8 + 2 * c) = make_float2(dq[j][2 * r] * scale, dq[j][2 * r + 1] * scale);
+    }
+}
+
+// dK, dV: one CTA per 64 key rows; loops over the event's query tiles.
+template <int DH, bool F16>
+__global__ void __launch_bounds__(128) k_attn_dkv_tc(const float* __restrict__ qkv, const float* __restrict__ dO,
+                                                     const float* __restrict__ lse, const float* __restrict__ D,
+                                                     float* __restrict__ dqkv, const int32_t* __restrict__ cu, int d,
+                                                     float scale) {
+    constexpr int LD = DH + 8;
+    __shared__ __align__(16) uint16_t Ks[64 * LD], Vs[64 * LD], Qs[64 * LD], Gs[64 * LD];
+    __shared__ float L2s[64], Ds[64];
+    const int e = blockIdx.z, h = blockIdx.y, H = gridDim.y;
+    const int start = cu[e], n = cu[e + 1] - start, k0 = blockIdx.x * 64;
+    if (k0 >= n) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, c = lane & 3;
+    const int g = lane >> 2;
+    const long ld = 3L * d;
+    stage_tile<DH, F16>(Ks, qkv, ld, d + h * DH, start, k0, n, 1.f);
+    stage_tile<DH, F16>(Vs, qkv, ld, 2 * d + h * DH, start, k0, n, 1.f);
+    __syncthreads();
+    uint32_t ka[DH / 16][4], va[DH / 16][4];
+#pragma unroll
+    for (int kk = 0; kk < DH / 16; ++kk) {
+        load_a<LD>(Ks, warp * 16, kk * 16, ka[kk]);
+        load_a<LD>(Vs, warp * 16, kk * 16, va[kk]);
+    }
+    float dk[DH / 8][4] = {}, dv[DH / 8][4] = {};
+    for (int qb = 0; qb < n; qb += 64) {
+        __syncthreads();
+        stage_tile<DH, F16>(Qs, qkv, ld, h * DH, start, qb, n, scale * kLog2e);
+        stage_tile<DH, F16>(Gs, dO, d, h * DH, start, qb, n, 1.f);
+        if (threadIdx.x < 64) {
+            const int row = qb + threadIdx.x;
+            L2s[threadIdx.x] = row < n ? lse[(long)(start + row) * H + h] * kLog2e : INFINITY;
+            Ds[threadIdx.x] = row < n ? D[(long)(start + row) * H + h] : 0.f;
+        }
+        __syncthreads();
+        float s[8][4], dp[8][4];
+        scores<DH, F16>(ka, Qs, s);    // S^T: keys x queries
+        scores<DH, F16>(va, Gs, dp);   // dP^T
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int qc = j * 8 + 2 * c + (u & 1);
+                s[j][u] = ex2_approx(s[j][u] - L2s[qc]);   // P^T (0 for queries beyond the event)
+                dp[j][u] = s[j][u] * (dp[j][u] - Ds[qc]);    // dS^T
+            }
+        accumulate<DH, F16>(s, Gs, dv);
+        accumulate<DH, F16>(dp, Qs, dk);
+    }
+    (void)g;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int row = k0 + warp * 16 + (lane >> 2) + 8 * r;
+        if (row >= n) continue;
+        float* dst = dqkv + (long)(start + row) * ld + h * DH;
+#pragma unroll
+        for (int j = 0; j < DH / 8; ++j) {
+            *reinterpret_cast<float2*>(dst + d + j * 8 + 2 * c) =
+                make_float2(dk[j][2 * r] / kLog2e, dk[j][2 * r + 1] / kLog2e);
+            *reinterpret_cast<float2*>(dst + 2 * d + j * 8 + 2 * c) = make_float2(dv[j][2 * r], dv[j][2 * r + 1]);
+        }
+    }
+}
+
+template <bool F16>
+bool attn_tc_launch(int which, const float* qkv, const float* dO, float* out, float* lse, const float* D,
+                    float* dqkv, const int32_t* cu, int n_events, int max_n, int d, int heads, cudaStream_t st) {
+    const int dh = d / heads;
+    const float scale = 1.f / sqrtf((float)dh);
+    dim3 grid((max_n + 63) / 64, heads, n_events);
+#define MLPF_ATTN_TC(DH)                                                                              \
+    if (which == 0)                                                                                   \
+        k_attn_fwd_tc<DH, F16><<<grid, 128, 0, st>>>(qkv, out, lse, cu, d, scale);                    \
+    else {                                                                                            \
+        k_attn_dq_tc<DH, F16><<<grid, 128, 0, st>>>(qkv, dO, lse, D, dqkv, cu, d, scale);             \
+        k_attn_dkv_tc<DH, F16><<<grid, 128, 0, st>>>(qkv, dO, lse, D, dqkv, cu, d, scale);            \
+    }
+    if (dh == 16) {
+        MLPF_ATTN_TC(16)
+    } else if (dh == 32) {
+        MLPF_ATTN_TC(32)
+    } else if (dh == 64) {
+        MLPF_ATTN_TC(64)
+    } else {
+        return false;
+    }
+#undef MLPF_ATTN_TC
+    return true;
+}
+
+}  // namespace
+
+bool attn_train_fwd_tc(int f16, const float* qkv, float* out, float* lse, const int32_t* cu, int n_events, int max_n,
+                       int d, int heads, cudaStream_t st) {
+    if (n_events <= 0 || max_n <= 0) return true;
+    return f16 ? attn_tc_launch<true>(0, qkv, nullptr, out, lse, nullptr, nullptr, cu, n_events, max_n, d, heads, st)
+               : attn_tc_launch<false>(0, qkv, nullptr, out, lse, nullptr, nullptr, cu, n_events, max_n, d, heads, st);
+}
+
+bool attn_train_bwd_tc(int f16, const float* qkv, const float* dO, const float* lse, const float* D, float* dqkv,
+                       const int32_t* cu, int n_events, int max_n, int d, int heads, cudaStream_t st) {
+    if (n_events <= 0 || max_n <= 0) return true;
+    return f16 ? attn_tc_launch<true>(1, qkv, dO, nullptr, const_cast<float*>(lse), D, dqkv, cu, n_events, max_n, d,
+                                      heads, st)
+               : attn_tc_launch<false>(1, qkv, dO, nullptr, const_cast<float*>(lse), D, dqkv, cu, n_events, max_n, d,
+                                       heads, st);
+}
+
+}  // namespace mlpf

@@ -783,7 +783,11 @@ static void train_forward(Trainer& t, const Acts& a, const float* x, const int32
             for (int i = 0; i < 3; ++i)
                 lin(t, ln1[l], d, d, nullptr, 0, 0, P(t, p + "w" + qn[i]), P(t, p + "b" + qn[i]), nullptr, 0,
                            qkv[l] + i * d, 3 * d, T, d, st);
-            f32_attention(qkv[l], o[l], cu, n_events, max_n, d, c.heads, lse[l], st);
+            if (t.prec == MLPF_FP32)
+                f32_attention(qkv[l], o[l], cu, n_events, max_n, d, c.heads, lse[l], st);
+            else if (!attn_train_fwd_tc(t.prec == MLPF_FP16, qkv[l], o[l], lse[l], cu, n_events, max_n, d, c.heads,
+                                        st))
+                t.tc_fail = true;
             lin(t, o[l], d, d, nullptr, 0, 0, P(t, p + "wo"), P(t, p + "bo"), z[l], d, zm[l], d, T, d, st);
             f32_layernorm(zm[l], P(t, p + "ln2.g"), P(t, p + "ln2.b"), ln2[l], T, d, st);
             lin(t, ln2[l], d, d, nullptr, 0, 0, P(t, p + "ffn.w1"), P(t, p + "ffn.b1"), nullptr, 0, af[l], F, T, F,
@@ -879,7 +883,11 @@ static void train_backward(Trainer& t, const Acts& a, const float* x, const int3
             lin_bwd(a.dz, d, o[l], d, p + "wo", p + "bo", d, d, a.dx1, d, 0);   // dx1 = dO
             k_attn_rowdot<<<cdivu((long)T * H, 256), 256, 0, st>>>(a.dx1, o[l], a.D, T, d, H);
             dim3 grid(cdivu(max_n, 64), H, n_events);
-            if (dh == 16) {
+            if (t.prec != MLPF_FP32) {
+                if (!attn_train_bwd_tc(t.prec == MLPF_FP16, qkv[l], a.dx1, lse[l], a.D, a.dx2, cu, n_events, max_n, d,
+                                       H, st))
+                    t.tc_fail = true;
+            } else if (dh == 16) {
                 k_attn_bwd_dq<16><<<grid, 64, 0, st>>>(qkv[l], a.dx1, lse[l], a.D, a.dx2, cu, d, scale);
                 k_attn_bwd_dkv<16><<<grid, 64, 0, st>>>(qkv[l], a.dx1, lse[l], a.D, a.dx2, cu, d, scale);
             } else if (dh == 32) {
@@ -1028,7 +1036,7 @@ static mlpf_status trainer_step_impl(mlpf_trainer* tt, const float* x, const int
     TCK(cudaGetLastError());
     if (t.tc_fail) {
         t.tc_fail = false;
-        set_error("tensor map encoding failed for a training GEMM");
+        set_error("a tensor-core kernel of the training step could not be launched (tensor map or head width)");
         return MLPF_E_CUDA;
     }
     if (loss_out) {

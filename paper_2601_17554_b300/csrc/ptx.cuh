@@ -317,6 +317,13 @@ MLPF_DEV void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, u
                  : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
                  : "r"(addr));
 }
+// Same with each 8x8 matrix transposed: lane 4 r + c receives elements (2c, r) and
+// (2c + 1, r) of matrix i in register i (rows of the stored matrix pair up).
+MLPF_DEV void ldsm_x4_t(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
 // d[16x8] = a[16x16] * b[16x8] + c[16x8] with c in separate registers (kept
 // across calls), FP32 accumulate; 16-bit operands FP16 or BF16
 template <bool F16>

@@ -1,8 +1,9 @@
 """Training with 16-bit tensor-core GEMMs (GPU): mlpf_trainer_set_precision(BF16 / FP16).
 
 In that mode every linear layer's GEMM (forward, input gradient, weight gradient) takes
-its operands rounded to the 16-bit format and accumulates in FP32 on tcgen05; the rest
-of the step is FP32.  Its gradient therefore differs from the float64 gradient by the
+its operands rounded to the 16-bit format and accumulates in FP32 on tcgen05, and the
+attention forward and backward multiply 16-bit Q, K, V, probabilities, output and score
+gradients on warp-level tensor-core MMAs; the rest of the step is FP32.  Its gradient therefore differs from the float64 gradient by the
 effect of that rounding, whose size a float64 model that rounds the same operands at the
 same places measures (tests.util.f64_distill_reference with operand_format).  The GPU
 does not reproduce that model's rounding errors one by one beyond the first layer: an

@@ -49,8 +49,9 @@ def f64_distill_reference(W, cfg, x, cu, tl, tr, operand_format=None):
     operand_format "bf16" / "fp16": every linear layer rounds its GEMM operands to that
     format, in the forward (input and weight) and in the backward (the output gradient,
     with the rounded weight for the input gradient and the rounded input for the weight
-    gradient): the arithmetic of a mixed-precision training step whose GEMMs run on
-    16-bit tensor cores with exact accumulation; everything else stays float64."""
+    gradient), and attention rounds the operands of its products (RoundedAttention): the
+    arithmetic of a mixed-precision training step whose GEMMs and attention products run
+    on 16-bit tensor cores with exact accumulation; everything else stays float64."""
     import torch
     import torch.nn.functional as F
 
@@ -74,9 +75,41 @@ def f64_distill_reference(W, cfg, x, cu, tl, tr, operand_format=None):
                 gr = rnd(gy)
                 return gr @ wr, gr.T @ tr_, gy.sum(0)
 
+        LOG2E = 1.0 / np.log(2.0)
+
+        class RoundedAttention(torch.autograd.Function):
+            """softmax(q k^T / sqrt(dh)) v per head with the operands of its four products
+            rounded: q / sqrt(dh) log2(e), k, v and the unnormalised probabilities in the
+            forward; the output gradient, the probabilities and the score gradient in the
+            backward (probabilities recomputed from the log-sum-exp)."""
+
+            @staticmethod
+            def forward(ctx, q, k, v):
+                sc = 1.0 / np.sqrt(q.shape[-1])
+                qr, kr, vr = rnd(q * sc * LOG2E), rnd(k), rnd(v)
+                s2 = qr @ kr.transpose(-1, -2)
+                m = s2.amax(-1, keepdim=True)
+                e = torch.exp2(s2 - m)
+                l = e.sum(-1, keepdim=True)
+                o = (rnd(e) @ vr) / l
+                ctx.save_for_backward(qr, kr, vr, m + torch.log2(l), o)
+                ctx.sc = sc
+                return o
+
+            @staticmethod
+            def backward(ctx, go):
+                qr, kr, vr, lse2, o = ctx.saved_tensors
+                p = torch.exp2(qr @ kr.transpose(-1, -2) - lse2)
+                Dr = (go * o).sum(-1, keepdim=True)
+                gr = rnd(go)
+                ds = p * (gr @ vr.transpose(-1, -2) - Dr)
+                dsr = rnd(ds)
+                return ctx.sc * (dsr @ kr), (dsr.transpose(-1, -2) @ qr) / LOG2E, rnd(p).transpose(-1, -2) @ gr
+
         F = type("F", (), {k: staticmethod(getattr(torch.nn.functional, k)) for k in
-                           ("relu", "gelu", "layer_norm", "scaled_dot_product_attention", "log_softmax")})
+                           ("relu", "gelu", "layer_norm", "log_softmax")})
         F.linear = staticmethod(lambda t, w, b: RoundedLinear.apply(t, w, b))
+        F.scaled_dot_product_attention = staticmethod(lambda q, k, v: RoundedAttention.apply(q, k, v))
     mlp = lambda t, p: F.linear(act(F.linear(t, P[p + "w1"], P[p + "b1"])), P[p + "w2"], P[p + "b2"])
     ln = lambda t, p: F.layer_norm(t, (cfg.d,), P[p + ".g"], P[p + ".b"], eps=1e-5)
 
