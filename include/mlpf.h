@@ -43,13 +43,19 @@ typedef enum {
 
 typedef enum {
     MLPF_FP32 = 0, /* plain path: SIMT FP32 FFMA GEMMs and attention, no TF32 */
-    MLPF_BF16 = 1, /* tcgen05 tensor cores: attention in BF16 (Q, K, V, P and the QK^T / PV
+    MLPF_BF16 = 1, /* tensor cores: attention in BF16 (Q, K, V, P and the QK^T / PV
                       products), FP16 operands in the embedding, projection, FFN and head
                       GEMMs; FP32 accumulation, softmax statistics, LayerNorm moments and
                       residual stream.  The per-stage rounding budget of the forward puts
                       the 16-bit error into the GEMM operands, not into the attention
-                      products: BF16 GEMM operands cost the 99.9 % argmax bound */
-    MLPF_FP8 = 2,  /* E4M3 GEMMs with per-tensor scales, FP16 attention (needs mlpf_calibrate_fp8) */
+                      products: BF16 GEMM operands cost the 99.9 % argmax bound.
+                      The d=64, 4 x 16, FFN 256 arch-0 model runs fused persistent kernels;
+                      every other model (any width with heads of 16, 32 or 64, both
+                      architectures) runs the generic-width path: one tcgen05 GEMM per
+                      linear layer with two-term FP16 weights (FP16 rounding plus the
+                      rounding of the remainder), warp-level MMA attention */
+    MLPF_FP8 = 2,  /* E4M3 GEMMs with per-tensor scales, FP16 attention (needs mlpf_calibrate_fp8);
+                      the d=64, 4 x 16, FFN 256 arch-0 model only */
     MLPF_FP16 = 3  /* FP16 everywhere on the tensor-core path (attention included) */
 } mlpf_precision;
 
@@ -119,8 +125,9 @@ mlpf_status mlpf_get_config(const mlpf_model* m, mlpf_config* cfg);
  * that break the contract give undefined results (but stay in bounds of
  * the workspace sized from total/max_n/n_events).
  * Errors: MLPF_E_INVALID (null pointers, x not 8-byte aligned, negative
- *         sizes, max_n > 65536, unknown precision), MLPF_E_UNSUPPORTED (precision not built for this
- *         configuration), MLPF_E_OOM (workspace growth), MLPF_E_CUDA.
+ *         sizes, max_n > 65536, unknown precision), MLPF_E_UNSUPPORTED (MLPF_FP8 on a model
+ *         other than the d=64 one, or a 16-bit precision on a device other than sm_103),
+ *         MLPF_E_OOM (workspace growth), MLPF_E_CUDA.
  * Device-side timeouts and non-finite outputs are reported by mlpf_sync().
  */
 mlpf_status mlpf_forward(mlpf_model* m, int32_t precision,

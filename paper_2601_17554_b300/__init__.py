@@ -13,7 +13,7 @@ import ctypes
 from . import _lib
 from ._lib import (MLPF_FP32, MLPF_BF16, MLPF_FP8, MLPF_FP16, MlpfError, check,  # noqa: F401
                    OPT_USE_GRAPHS, OPT_WAIT_LIMIT_NS, OPT_DEBUG_STALL, OPT_ATTN_VARIANT_BF16,
-                   OPT_ATTN_VARIANT_FP16, OPT_ATTN_VARIANT_FP8)
+                   OPT_ATTN_VARIANT_FP16, OPT_ATTN_VARIANT_FP8, OPT_ATTN_WINDOW)
 
 PRECISIONS = {"fp32": MLPF_FP32, "bf16": MLPF_BF16, "fp8": MLPF_FP8, "fp16": MLPF_FP16}
 

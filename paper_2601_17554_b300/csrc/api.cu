@@ -221,12 +221,13 @@ static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 static mlpf_status ensure_workspace(Model& m, int total, int n_events, bool tc) {
     Workspace& w = m.ws;
     const bool fits = (size_t)total <= w.cap_total && (size_t)n_events <= w.cap_events &&
-                      (!tc || w.tz != nullptr) && w.base != nullptr;
+                      (!tc || (m.tc_supported ? w.tz != nullptr : w.a16 != nullptr)) && w.base != nullptr;
     if (fits) return MLPF_OK;
     // grow geometrically; keep both paths' buffers in one allocation
     const size_t cap_t = std::max<size_t>({(size_t)total, w.cap_total * 5 / 4, 1024});
     const size_t cap_e = std::max<size_t>({(size_t)n_events, w.cap_events * 5 / 4, 16});
-    const bool want_tc = tc || w.tz != nullptr;
+    const bool want_tc = (tc && m.tc_supported) || w.tz != nullptr;
+    const bool want_wide = (tc && !m.tc_supported) || w.a16 != nullptr;
     if (w.base) {
         cudaFree(w.base);
         w = Workspace{};
@@ -254,6 +255,9 @@ static mlpf_status ensure_workspace(Model& m, int total, int n_events, bool tc) 
         o_kmax = take((tpad / 64) * 4 * sizeof(float));
         o_items = take((tpad / 128 + cap_e + 1) * sizeof(int4));
     }
+    // wide path: GEMM operand scratch of the widest linear-layer input (42 + d, d or FFN)
+    const size_t a16_cols = align_up(std::max<size_t>({42 + d, d, F}), 64);
+    const size_t o_a16 = want_wide ? take(cap_t * 2 * a16_cols * 2) : 0;   // [a | a] rows
     const size_t o_cnt = take(64 * sizeof(int));
     const size_t o_hx = take(cap_t * 42 * 4), o_hcu = take((cap_e + 1) * 4), o_hcc = take((cap_e + 17) * 4),
                  o_hlo = take(cap_t * 6 * 4), o_hrg = take(cap_t * 5 * 4), o_hcl = take(cap_t * 4),
@@ -272,6 +276,7 @@ static mlpf_status ensure_workspace(Model& m, int total, int n_events, bool tc) 
     w.o = (float*)(b + o_o); w.hid = (float*)(b + o_hid); w.hpid = (float*)(b + o_hp);
     w.hreg = (float*)(b + o_hr); w.raw = (float*)(b + o_raw);
     w.counters = (int*)(b + o_cnt);
+    if (want_wide) w.a16 = (uint16_t*)(b + o_a16);
     w.hx = (float*)(b + o_hx); w.hcu = (int32_t*)(b + o_hcu); w.hlogits = (float*)(b + o_hlo);
     w.hcu_chunks = (int32_t*)(b + o_hcc);
     w.hreg_out = (float*)(b + o_hrg); w.hcls = (int32_t*)(b + o_hcl); w.hsums = (double*)(b + o_hsu);
@@ -307,8 +312,9 @@ static mlpf_status validate(const Model* m, int32_t prec, const void* x, const v
     if (total > 0 && (!x || !cu || !logits || !reg)) { set_error("NULL input or output pointer"); return MLPF_E_INVALID; }
     if (n_events > 0 && !cu) { set_error("cu_seqlens is NULL"); return MLPF_E_INVALID; }
     if (total > 0 && ((uintptr_t)x & 7)) { set_error("x is not 8-byte aligned"); return MLPF_E_INVALID; }
-    if (prec != MLPF_FP32 && !m->tc_supported) {
-        set_error("tensor-core path is built for d=64, 4 heads, FFN 256, arch 0 models only");
+    if (prec != MLPF_FP32 && !m->tc_supported && !(m->wide_supported && prec != MLPF_FP8)) {
+        set_error(prec == MLPF_FP8 ? "MLPF_FP8 is built for the d=64, 4 heads, FFN 256, arch 0 model only"
+                                   : "no tensor-core path for this model on this device");
         return MLPF_E_UNSUPPORTED;
     }
     if (m->attn_window > 0 && max_n > 16384) {
@@ -342,7 +348,8 @@ static mlpf_status launch_sequence(Model& m, int32_t prec, const float* x, const
         const int64_t k = n < 0 ? -1
                           : (prec == MLPF_FP32)
                                 ? run_forward_f32(m, xin, cu, n_events, total, max_n, lo, rg, st)
-                                : run_forward_tc(m, prec, xin, cu, n_events, total, max_n, lo, rg, st);
+                          : m.tc_supported ? run_forward_tc(m, prec, xin, cu, n_events, total, max_n, lo, rg, st)
+                                           : run_forward_wide(m, prec, xin, cu, n_events, total, max_n, lo, rg, st);
         if (k < 0) {
             set_error(std::string("kernel launch failed: ") + cudaGetErrorString(cudaGetLastError()));
             return MLPF_E_CUDA;
@@ -513,7 +520,9 @@ mlpf_status mlpf_load_weights(const void* blob, size_t nbytes, int device, mlpf_
         cudaGetDeviceProperties(&prop, device);
         const bool arch_ok = prop.major == 10 && prop.minor == 3;
         m.tc_supported = arch_ok && c.d == 64 && c.heads == 4 && c.ffn == 256 && c.arch == 0;
+        m.wide_supported = arch_ok && !m.tc_supported;
         if (m.tc_supported && !tc_prepare_weights(m)) s = MLPF_E_CUDA;
+        if (m.wide_supported && !wide_prepare_weights(m)) s = MLPF_E_CUDA;
     }
     if (s != MLPF_OK) {
         if (m.w.f32_base || m.status) mlpf_free(mm);
@@ -541,6 +550,7 @@ void mlpf_free(mlpf_model* mm) {
     if (m.ws_alt.base) cudaFree(m.ws_alt.base);
     if (m.w.f32_base) cudaFree(m.w.f32_base);
     if (m.w.img_base) cudaFree(m.w.img_base);
+    if (m.w.w16_base) cudaFree(m.w.w16_base);
     if (m.w.img8_base) cudaFree(m.w.img8_base);
     if (m.w.tc_f32_base) cudaFree(m.w.tc_f32_base);
     if (m.status) cudaFree(m.status);
@@ -720,6 +730,10 @@ mlpf_status mlpf_calibrate_fp8(mlpf_model* mm, const float* x, const int32_t* cu
                              x, x);
     if (s != MLPF_OK) return s;
     if (total == 0) { set_error("calibration needs at least one element"); return MLPF_E_INVALID; }
+    if (!mm->impl.tc_supported) {
+        set_error("MLPF_FP8 is built for the d=64, 4 heads, FFN 256, arch 0 model only");
+        return MLPF_E_UNSUPPORTED;
+    }
     Model& m = mm->impl;
     CK(cudaSetDevice(m.device));
     s = ensure_workspace(m, total, n_events, true);
@@ -765,7 +779,7 @@ mlpf_status mlpf_autotune(mlpf_model* mm, int32_t precision, const float* x, con
                           void* stream) {
     mlpf_status s = validate(mm ? &mm->impl : nullptr, precision, x, cu_seqlens, n_events, total, max_n, x, x);
     if (s != MLPF_OK) return s;
-    if (precision == MLPF_FP32) return MLPF_OK;  // nothing to choose on the plain path
+    if (precision == MLPF_FP32 || !mm->impl.tc_supported) return MLPF_OK;  // one kernel per step: nothing to choose
     if (total == 0) { set_error("autotuning needs at least one element"); return MLPF_E_INVALID; }
     Model& m = mm->impl;
     CK(cudaSetDevice(m.device));

@@ -38,6 +38,10 @@ struct DeviceWeights {
     uint8_t* img_base = nullptr;
     std::map<std::string, uint8_t*> img_h;  // name -> device pointer of the FP16 image
     std::map<std::string, uint32_t> img_bytes;
+    // wide tensor-core path: two-term FP16 images of every weight matrix, [N, 2 kp] with
+    // kp = K padded to 64, keyed by the FP32 tensor's device pointer -> (image, kp)
+    uint16_t* w16_base = nullptr;
+    std::map<const float*, std::pair<const uint16_t*, int>> w16;
     float* tc_f32_base = nullptr;         // fused bias vectors for the tensor-core kernels
     std::map<std::string, float*> tcv;
     // FP8 E4M3 images (same layout, one byte per element) and per-tensor scales
@@ -68,6 +72,8 @@ struct Workspace {
     // row of the r-th element in that order), inputs and outputs in that order
     int32_t* perm = nullptr;
     float *xs = nullptr, *los = nullptr, *rgs = nullptr;
+    // wide tensor-core path: 16-bit GEMM operand scratch [cap_total, 2 x the widest padded input]
+    uint16_t* a16 = nullptr;
     // host-buffer entry point: device staging
     float *hx = nullptr, *hlogits = nullptr, *hreg_out = nullptr;
     int32_t *hcu = nullptr, *hcls = nullptr;
@@ -100,6 +106,7 @@ struct Model {
     unsigned* status = nullptr;  // device status word
     int sm_count = 148;
     bool tc_supported = false;   // tensor-core path built for this configuration
+    bool wide_supported = false; // generic-width tensor-core path (models the fused kernels do not cover)
     // options
     bool use_graphs = true;
     int64_t wait_limit_ns = 2000000000LL;
@@ -202,6 +209,12 @@ bool gemm_tc(int f16, const void* A, long lda, const void* B, long ldb, int M, i
 void cvt_16(const float* s1, long ld1, int k1, const float* s2, long ld2, int k2, int rows, uint16_t* dst, long ldd,
             int f16, cudaStream_t st);
 void cvt_16_t(const float* src, long lds, int rows, int cols, uint16_t* dst, long ldd, int f16, cudaStream_t st);
+// Two-term weight image [N, 2 kp]: columns 0.. the 16-bit rounding of W, columns kp.. the
+// rounding of its residual (kp a multiple of 64); cvt_16_dup writes each activation row
+// twice, [a | a] (row stride 2 kp), so that one GEMM over 2 kp multiplies a by both terms.
+void cvt_16_split(const float* W, long ldw, int N, int K, uint16_t* dst, int kp, int f16, cudaStream_t st);
+void cvt_16_dup(const float* s1, long ld1, int k1, const float* s2, long ld2, int k2, int rows, uint16_t* dst, int kp,
+                int f16, cudaStream_t st);
 
 // Varlen self-attention of the training step on the tensor cores (k_attn_train.cu):
 // qkv [T, 3d] FP32 (Q | K | V, heads of dh = d / heads in {16, 32, 64}), out / dO [T, d],
@@ -209,7 +222,13 @@ void cvt_16_t(const float* src, long lds, int rows, int cols, uint16_t* dst, lon
 // dqkv [T, 3d].  16-bit operands (f16: FP16, else BF16), FP32 accumulation and
 // statistics.  Return false for an unsupported head width.
 bool attn_train_fwd_tc(int f16, const float* qkv, float* out, float* lse, const int32_t* cu, int n_events, int max_n,
-                       int d, int heads, cudaStream_t st);
+                       int d, int heads, cudaStream_t st, int window = 0);
+// sets the tensor-core GEMM kernels' shared-memory attributes (call outside graph capture)
+void gemm_tc_prepare();
+// generic-width tensor-core forward (k_f32.cu) and its weight images
+bool wide_prepare_weights(Model& m);
+int64_t run_forward_wide(Model& m, int prec, const float* x, const int32_t* cu, int n_events, int total, int max_n,
+                         float* logits, float* reg, cudaStream_t st);
 bool attn_train_bwd_tc(int f16, const float* qkv, const float* dO, const float* lse, const float* D, float* dqkv,
                        const int32_t* cu, int n_events, int max_n, int d, int heads, cudaStream_t st);
 

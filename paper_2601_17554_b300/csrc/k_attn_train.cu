@@ -102,10 +102,12 @@ __device__ __forceinline__ void accumulate(const float (*p)[4], const uint16_t* 
     }
 }
 
+// window > 0: the query rows of 128-row block y attend to the keys of blocks y - window ..
+// y + window only (the eta-ordered block-banded reading of windowed attention)
 template <int DH, bool F16>
 __global__ void __launch_bounds__(128) k_attn_fwd_tc(const float* __restrict__ qkv, float* __restrict__ out,
                                                      float* __restrict__ lse, const int32_t* __restrict__ cu, int d,
-                                                     float scale) {
+                                                     float scale, int window) {
     constexpr int LD = DH + 8;
     __shared__ __align__(16) uint16_t Qs[64 * LD], Ks[64 * LD], Vs[64 * LD];
     const int e = blockIdx.z, h = blockIdx.y, H = gridDim.y;
@@ -120,10 +122,16 @@ __global__ void __launch_bounds__(128) k_attn_fwd_tc(const float* __restrict__ q
     for (int kk = 0; kk < DH / 16; ++kk) load_a<LD>(Qs, warp * 16, kk * 16, qa[kk]);
     float o[DH / 8][4] = {};
     float m[2] = {-INFINITY, -INFINITY}, l[2] = {0.f, 0.f};
-    for (int kb = 0; kb < n; kb += 64) {
+    int kbeg = 0, kend = n;
+    if (window > 0) {
+        const int y = q0 / 128;
+        kbeg = max(0, (y - window) * 128);
+        kend = min(n, (y + window + 1) * 128);
+    }
+    for (int kb = kbeg; kb < kend; kb += 64) {
         __syncthreads();
-        stage_tile<DH, F16>(Ks, qkv, ld, d + h * DH, start, kb, n, 1.f);
-        stage_tile<DH, F16>(Vs, qkv, ld, 2 * d + h * DH, start, kb, n, 1.f);
+        stage_tile<DH, F16>(Ks, qkv, ld, d + h * DH, start, kb, kend, 1.f);
+        stage_tile<DH, F16>(Vs, qkv, ld, 2 * d + h * DH, start, kb, kend, 1.f);
         __syncthreads();
         float s[8][4];
         scores<DH, F16>(qa, Ks, s);
@@ -132,7 +140,7 @@ __global__ void __launch_bounds__(128) k_attn_fwd_tc(const float* __restrict__ q
         for (int j = 0; j < 8; ++j)
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                if (kb + j * 8 + 2 * c + (u & 1) >= n) s[j][u] = -INFINITY;
+                if (kb + j * 8 + 2 * c + (u & 1) >= kend) s[j][u] = -INFINITY;
                 mx[u >> 1] = fmaxf(mx[u >> 1], s[j][u]);
             }
 #pragma unroll
@@ -172,7 +180,7 @@ __global__ void __launch_bounds__(128) k_attn_fwd_tc(const float* __restrict__ q
 #pragma unroll
         for (int j = 0; j < DH / 8; ++j)
             *reinterpret_cast<float2*>(orow + j * 8 + 2 * c) = make_float2(o[j][2 * r] * inv, o[j][2 * r + 1] * inv);
-        if (c == 0) lse[(long)(start + row) * H + h] = (m[r] + __log2f(l[r])) / kLog2e;
+        if (lse && c == 0) lse[(long)(start + row) * H + h] = (m[r] + __log2f(l[r])) / kLog2e;
     }
 }
 
@@ -301,13 +309,14 @@ __global__ void __launch_bounds__(128) k_attn_dkv_tc(const float* __restrict__ q
 
 template <bool F16>
 bool attn_tc_launch(int which, const float* qkv, const float* dO, float* out, float* lse, const float* D,
-                    float* dqkv, const int32_t* cu, int n_events, int max_n, int d, int heads, cudaStream_t st) {
+                    float* dqkv, const int32_t* cu, int n_events, int max_n, int d, int heads, cudaStream_t st,
+                    int window) {
     const int dh = d / heads;
     const float scale = 1.f / sqrtf((float)dh);
     dim3 grid((max_n + 63) / 64, heads, n_events);
 #define MLPF_ATTN_TC(DH)                                                                              \
     if (which == 0)                                                                                   \
-        k_attn_fwd_tc<DH, F16><<<grid, 128, 0, st>>>(qkv, out, lse, cu, d, scale);                    \
+        k_attn_fwd_tc<DH, F16><<<grid, 128, 0, st>>>(qkv, out, lse, cu, d, scale, window);            \
     else {                                                                                            \
         k_attn_dq_tc<DH, F16><<<grid, 128, 0, st>>>(qkv, dO, lse, D, dqkv, cu, d, scale);             \
         k_attn_dkv_tc<DH, F16><<<grid, 128, 0, st>>>(qkv, dO, lse, D, dqkv, cu, d, scale);            \
@@ -328,19 +337,21 @@ bool attn_tc_launch(int which, const float* qkv, const float* dO, float* out, fl
 }  // namespace
 
 bool attn_train_fwd_tc(int f16, const float* qkv, float* out, float* lse, const int32_t* cu, int n_events, int max_n,
-                       int d, int heads, cudaStream_t st) {
+                       int d, int heads, cudaStream_t st, int window) {
     if (n_events <= 0 || max_n <= 0) return true;
-    return f16 ? attn_tc_launch<true>(0, qkv, nullptr, out, lse, nullptr, nullptr, cu, n_events, max_n, d, heads, st)
-               : attn_tc_launch<false>(0, qkv, nullptr, out, lse, nullptr, nullptr, cu, n_events, max_n, d, heads, st);
+    return f16 ? attn_tc_launch<true>(0, qkv, nullptr, out, lse, nullptr, nullptr, cu, n_events, max_n, d, heads, st,
+                                      window)
+               : attn_tc_launch<false>(0, qkv, nullptr, out, lse, nullptr, nullptr, cu, n_events, max_n, d, heads, st,
+                                       window);
 }
 
 bool attn_train_bwd_tc(int f16, const float* qkv, const float* dO, const float* lse, const float* D, float* dqkv,
                        const int32_t* cu, int n_events, int max_n, int d, int heads, cudaStream_t st) {
     if (n_events <= 0 || max_n <= 0) return true;
     return f16 ? attn_tc_launch<true>(1, qkv, dO, nullptr, const_cast<float*>(lse), D, dqkv, cu, n_events, max_n, d,
-                                      heads, st)
+                                      heads, st, 0)
                : attn_tc_launch<false>(1, qkv, dO, nullptr, const_cast<float*>(lse), D, dqkv, cu, n_events, max_n, d,
-                                       heads, st);
+                                       heads, st, 0);
 }
 
 }  // namespace mlpf

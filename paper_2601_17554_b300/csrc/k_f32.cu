@@ -417,6 +417,138 @@ int64_t run_forward_f32(Model& m, const float* x, const int32_t* cu, int n_event
     return n;
 }
 
+// ------------------------------------------------------------------ wide tensor-core path
+// Forward of models outside the fused d = 64 kernels (any width with heads of 16, 32 or
+// 64; both architectures) on the tensor cores: every linear layer is one tcgen05 GEMM
+// (FP16 operands with two-term weights, FP32 accumulation, bias / activation / residual in
+// its epilogue) fed by a conversion of its FP32 input, attention runs on warp-level MMAs (BF16 operands in the
+// BF16 mode, FP16 in the FP16 mode; FP32 softmax statistics), LayerNorm and the decode
+// stay FP32.  Same launch sequence as the plain path otherwise.
+static constexpr uint64_t WIDE_WAIT_NS = 2000000000ull;
+
+static void tlinear(Model& m, const float* X1, int ld1, int K1, const float* X2, int ld2, int K2, const float* W,
+                    const float* b, const float* R, int ldr, float* Y, int ldy, int T, int N, int act,
+                    cudaStream_t st, int64_t& n, bool& ok) {
+    const auto it = m.w.w16.find(W);
+    if (it == m.w.w16.end()) {
+        ok = false;
+        return;
+    }
+    const int Kp = it->second.second;
+    prof_begin(m, st, "wide_cvt");
+    cvt_16_dup(X1, ld1, K1, X2, ld2, K2, T, m.ws.a16, Kp, 1, st);
+    prof_end(m, st);
+    prof_begin(m, st, "wide_gemm");
+    if (!gemm_tc(1, m.ws.a16, 2 * Kp, it->second.first, 2 * Kp, T, N, 2 * Kp, Y, ldy, b, R, ldr, act, 0, 0, nullptr, 0,
+                 m.status, WIDE_WAIT_NS, st))
+        ok = false;
+    prof_end(m, st);
+    n += 2;
+}
+
+int64_t run_forward_wide(Model& m, int prec, const float* x, const int32_t* cu, int n_events, int total, int max_n,
+                         float* logits, float* reg, cudaStream_t st) {
+    const mlpf_config& c = m.cfg;
+    const int T = total, d = c.d, F = c.ffn, act = c.act;
+    Workspace& w = m.ws;
+    auto W = [&](const std::string& s) { return m.w.f32.at(s); };
+    int64_t n = 0;
+    bool ok = true;
+    g_model = &m;
+    auto stack = [&](const char* prefix, int layers, std::vector<float*>& wqkv, std::vector<float*>& bqkv,
+                     float* out) {
+        for (int l = 0; l < layers; ++l) {
+            const std::string p = std::string(prefix) + "." + std::to_string(l) + ".";
+            layernorm(w.z, W(p + "ln1.g"), W(p + "ln1.b"), w.zn, T, d, st, n);
+            tlinear(m, w.zn, d, d, nullptr, 0, 0, wqkv[l], bqkv[l], nullptr, 0, w.qkv, 3 * d, T, 3 * d, -1, st, n,
+                    ok);
+            prof_begin(m, st, "wide_attention");
+            if (!attn_train_fwd_tc(prec == MLPF_FP16, w.qkv, w.o, nullptr, cu, n_events, max_n, d, c.heads, st,
+                                   m.attn_window))
+                ok = false;
+            prof_end(m, st);
+            ++n;
+            tlinear(m, w.o, d, d, nullptr, 0, 0, W(p + "wo"), W(p + "bo"), w.z, d, w.z, d, T, d, -1, st, n, ok);
+            layernorm(w.z, W(p + "ln2.g"), W(p + "ln2.b"), w.zn, T, d, st, n);
+            tlinear(m, w.zn, d, d, nullptr, 0, 0, W(p + "ffn.w1"), W(p + "ffn.b1"), nullptr, 0, w.hid, F, T, F, act,
+                    st, n, ok);
+            tlinear(m, w.hid, F, F, nullptr, 0, 0, W(p + "ffn.w2"), W(p + "ffn.b2"), w.z, d, w.z, d, T, d, -1, st, n,
+                    ok);
+        }
+        layernorm(w.z, W(std::string(prefix) + ".lnf.g"), W(std::string(prefix) + ".lnf.b"), out, T, d, st, n);
+    };
+    auto mlp = [&](const float* in, int k_in, const char* p, float* out, int ldo, int n_out) {
+        const std::string s(p);
+        tlinear(m, in, k_in, k_in, nullptr, 0, 0, W(s + ".w1"), W(s + ".b1"), nullptr, 0, w.hid, d, T, d, act, st, n,
+                ok);
+        tlinear(m, w.hid, d, d, nullptr, 0, 0, W(s + ".w2"), W(s + ".b2"), nullptr, 0, out, ldo, T, n_out, -1, st, n,
+                ok);
+    };
+    if (c.arch == 1) {
+        mlp(x, 42, "emb.trk", w.hreg, d, d);
+        mlp(x, 42, "emb.clu", w.zn, d, d);
+        prof_begin(m, st, "f32_type_select");
+        k_type_select<<<cdiv(T, 8), 256, 0, st>>>(x, w.zn, w.hreg, T, d);
+        prof_end(m, st);
+        ++n;
+        if (cudaMemcpyAsync(w.z, w.hreg, (size_t)T * d * sizeof(float), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            return -1;
+        stack("pid", c.l_pid, m.w.wqkv_pid, m.w.bqkv_pid, w.hpid);
+        if (cudaMemcpyAsync(w.z, w.hreg, (size_t)T * d * sizeof(float), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            return -1;
+        stack("reg", c.l_reg, m.w.wqkv_reg, m.w.bqkv_reg, w.hreg);
+        mlp(w.hpid, d, "head.bin", logits, c.n_cls, 1);
+        mlp(w.hpid, d, "head.pid", logits + 1, c.n_cls, c.n_cls - 1);
+    } else {
+        mlp(x, 42, "emb", w.z, d, d);
+        stack("pid", c.l_pid, m.w.wqkv_pid, m.w.bqkv_pid, w.hpid);
+        tlinear(m, x, 42, 42, w.hpid, d, d, W("remb.w1"), W("remb.b1"), nullptr, 0, w.hid, d, T, d, act, st, n, ok);
+        tlinear(m, w.hid, d, d, nullptr, 0, 0, W("remb.w2"), W("remb.b2"), nullptr, 0, w.z, d, T, d, -1, st, n, ok);
+        stack("reg", c.l_reg, m.w.wqkv_reg, m.w.bqkv_reg, w.hreg);
+        mlp(w.hpid, d, "head.cls", logits, c.n_cls, c.n_cls);
+    }
+    const char* names[4] = {"pt", "eta", "phi", "e"};
+    const int widths[4] = {1, 1, 2, 1};
+    int off = 0;
+    for (int h = 0; h < 4; ++h) {
+        mlp(w.hreg, d, (std::string("head.") + names[h]).c_str(), w.raw + off, 5, widths[h]);
+        off += widths[h];
+    }
+    prof_begin(m, st, "f32_decode");
+    k_decode<<<cdiv(T, 256), 256, 0, st>>>(x, w.raw, reg, T);
+    prof_end(m, st);
+    ++n;
+    if (!ok || cudaPeekAtLastError() != cudaSuccess) return -1;
+    return n;
+}
+
+// Two-term FP16 images of every weight matrix the wide path multiplies (the weight as
+// the sum of its FP16 rounding and the FP16 rounding of the remainder, about 22
+// significant bits: the rounding of a weight shifts every element's output alike, which
+// moves threshold decisions of a whole batch; activation roundings do not), each half
+// padded with zeros to a multiple of 64 columns, keyed by the FP32 tensor's device pointer.
+bool wide_prepare_weights(Model& m) {
+    std::vector<std::pair<const float*, std::pair<int, int>>> mats;   // pointer, (N, K)
+    for (const auto& kv : m.host)
+        if (kv.second.shape.size() == 2) mats.push_back({m.w.f32.at(kv.first), {kv.second.shape[0], kv.second.shape[1]}});
+    const int d = m.cfg.d;
+    for (float* p : m.w.wqkv_pid) mats.push_back({p, {3 * d, d}});
+    for (float* p : m.w.wqkv_reg) mats.push_back({p, {3 * d, d}});
+    size_t total = 0;
+    for (const auto& mt : mats) total += (size_t)mt.second.first * 2 * ((mt.second.second + 63) / 64 * 64);
+    if (cudaMalloc(&m.w.w16_base, total * sizeof(uint16_t)) != cudaSuccess) return false;
+    size_t off = 0;
+    for (const auto& mt : mats) {
+        const int N = mt.second.first, K = mt.second.second, Kp = (K + 63) / 64 * 64;
+        uint16_t* dst = m.w.w16_base + off;
+        cvt_16_split(mt.first, K, N, K, dst, Kp, 1, 0);
+        m.w.w16[mt.first] = {dst, Kp};
+        off += (size_t)N * 2 * Kp;
+    }
+    gemm_tc_prepare();
+    return cudaDeviceSynchronize() == cudaSuccess;
+}
+
 void f32_linear(const float* X1, int ld1, int K1, const float* X2, int ld2, int K2, const float* W,
                 const float* b, const float* R, int ldr, float* Y, int ldy, int T, int N, int act,
                 cudaStream_t st) {

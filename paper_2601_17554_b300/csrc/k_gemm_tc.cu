@@ -13,6 +13,8 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <cuda_fp16.h>
+
 #include "internal.h"
 #include "ptx.cuh"
 
@@ -239,6 +241,51 @@ __global__ void k_cvt(const float* __restrict__ s1, long ld1, int k1, const floa
     }
 }
 
+// Two-term 16-bit image of a weight matrix: dst[n, k] = rn16(W[n, k]) and
+// dst[n, kp + k] = rn16(W[n, k] - rn16(W[n, k])) for k < K, zero elsewhere (row stride 2 kp).
+__global__ void k_cvt_split(const float* __restrict__ W, long ldw, int N, int K, uint16_t* __restrict__ dst, int kp,
+                            int f16) {
+    const long n = (long)N * 2 * kp;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const long r = i / (2 * kp);
+        const int c = (int)(i % (2 * kp)), k = c % kp;
+        uint16_t out = 0;
+        if (k < K) {
+            const float w = W[r * ldw + k];
+            const uint32_t hi = f16 ? pack_f16x2(w, 0.f) : pack_bf16x2(w, 0.f);
+            if (c < kp) {
+                out = (uint16_t)(hi & 0xffffu);
+            } else {
+                const float h = f16 ? __half2float(__ushort_as_half((unsigned short)(hi & 0xffffu)))
+                                    : __bfloat162float(__ushort_as_bfloat16((unsigned short)(hi & 0xffffu)));
+                const uint32_t lo = f16 ? pack_f16x2(w - h, 0.f) : pack_bf16x2(w - h, 0.f);
+                out = (uint16_t)(lo & 0xffffu);
+            }
+        }
+        dst[i] = out;
+    }
+}
+
+// dst[r, 0 .. kp) = dst[r, kp .. 2 kp) = 16-bit [s1 | s2][r, :] zero padded (row stride 2 kp)
+__global__ void k_cvt_dup(const float* __restrict__ s1, long ld1, int k1, const float* __restrict__ s2, long ld2,
+                          int k2, int rows, uint16_t* __restrict__ dst, int kp, int f16) {
+    const long n = (long)rows * (kp / 2);
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const long r = i / (kp / 2);
+        const int c = (int)(i % (kp / 2)) * 2;
+        float v[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int cc = c + u;
+            v[u] = cc < k1 ? s1[r * ld1 + cc] : (cc < k1 + k2 ? s2[r * ld2 + cc - k1] : 0.f);
+        }
+        const uint32_t p = f16 ? pack_f16x2(v[0], v[1]) : pack_bf16x2(v[0], v[1]);
+        uint32_t* row = (uint32_t*)(dst + r * 2 * kp);
+        row[c / 2] = p;
+        row[kp / 2 + c / 2] = p;
+    }
+}
+
 typedef CUresult (*TgEncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -272,16 +319,22 @@ bool tg_map(CUtensorMap* map, const void* base, long Kp, long rows, long ld, uin
 template <int BN, int ST>
 void tg_launch(const CUtensorMap& ma, const CUtensorMap& mb, const TgArgs& a, int splits, cudaStream_t st) {
     using L = TgLayout<BN, ST>;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_gemm_tc<BN, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::BYTES);
-        attr = true;
-    }
     dim3 grid((a.M + TG_BM - 1) / TG_BM, (a.N + BN - 1) / BN, splits);
     k_gemm_tc<BN, ST><<<grid, 128, L::BYTES, st>>>(ma, mb, a);
 }
 
 }  // namespace
+
+void gemm_tc_prepare() {
+    static bool done[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || done[dev]) return;
+    cudaFuncSetAttribute(k_gemm_tc<64, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, TgLayout<64, 4>::BYTES);
+    cudaFuncSetAttribute(k_gemm_tc<128, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, TgLayout<128, 3>::BYTES);
+    cudaFuncSetAttribute(k_gemm_tc<256, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, TgLayout<256, 2>::BYTES);
+    done[dev] = true;
+}
 
 bool gemm_tc(int f16, const void* A, long lda, const void* B, long ldb, int M, int N, int Kp, float* C, long ldc,
              const float* bias, const float* R, long ldr, int act, int mode, int kchunk, uint16_t* C16, long ldc16,
@@ -327,6 +380,20 @@ void cvt_16(const float* s1, long ld1, int k1, const float* s2, long ld2, int k2
     k_cvt<<<blocks, 256, 0, st>>>(s1, ld1, k1, s2, ld2, k2, rows, dst, ldd, f16);
 }
 
+void cvt_16_split(const float* W, long ldw, int N, int K, uint16_t* dst, int kp, int f16, cudaStream_t st) {
+    const long n = (long)N * 2 * kp;
+    if (n <= 0) return;
+    k_cvt_split<<<(unsigned)std::min<long>((n + 255) / 256, 148L * 16), 256, 0, st>>>(W, ldw, N, K, dst, kp, f16);
+}
+
+void cvt_16_dup(const float* s1, long ld1, int k1, const float* s2, long ld2, int k2, int rows, uint16_t* dst, int kp,
+                int f16, cudaStream_t st) {
+    const long n = (long)rows * (kp / 2);
+    if (n <= 0) return;
+    k_cvt_dup<<<(unsigned)std::min<long>((n + 255) / 256, 148L * 16), 256, 0, st>>>(s1, ld1, k1, s2, ld2, k2, rows,
+                                                                                      dst, kp, f16);
+}
+
 void cvt_16_t(const float* src, long lds, int rows, int cols, uint16_t* dst, long ldd, int f16, cudaStream_t st) {
     if (rows <= 0 || cols <= 0) return;
     dim3 grid((unsigned)((ldd + 31) / 32), (unsigned)((cols + 31) / 32));
@@ -351,6 +418,7 @@ extern "C" mlpf_status mlpf_gemm_tc(int32_t precision, const void* A, int64_t ld
         set_error("mlpf_gemm_tc: bad arguments");
         return MLPF_E_INVALID;
     }
+    gemm_tc_prepare();
     if (!gemm_tc(precision == MLPF_FP16, A, lda, B, ldb, M, N, K, C, ldc, bias, R, ldr, act, mode, kchunk, nullptr,
                  0, status, 2000000000ull, (cudaStream_t)stream)) {
         set_error("mlpf_gemm_tc: tensor map encoding failed");

@@ -1140,6 +1140,7 @@ mlpf_status mlpf_trainer_set_precision(mlpf_trainer* tt, int32_t precision) {
     t.prec = precision;
     t.fwd_ok = false;
     TCK(cudaSetDevice(t.m.device));
+    gemm_tc_prepare();
     return ensure_h16(t);
 }
 
