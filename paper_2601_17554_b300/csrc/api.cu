@@ -257,7 +257,9 @@ static mlpf_status ensure_workspace(Model& m, int total, int n_events, bool tc) 
     }
     // wide path: GEMM operand scratch of the widest linear-layer input (42 + d, d or FFN)
     const size_t a16_cols = align_up(std::max<size_t>({42 + d, d, F}), 64);
-    const size_t o_a16 = want_wide ? take(cap_t * 2 * a16_cols * 2) : 0;   // [a | a] rows
+    const size_t o_a16 = want_wide ? take(cap_t * a16_cols * 2) : 0;
+    const size_t o_b16 = want_wide ? take(cap_t * a16_cols * 2) : 0;
+    const size_t o_qkv16 = want_wide ? take(cap_t * 3 * d * 2) : 0;
     const size_t o_cnt = take(64 * sizeof(int));
     const size_t o_hx = take(cap_t * 42 * 4), o_hcu = take((cap_e + 1) * 4), o_hcc = take((cap_e + 17) * 4),
                  o_hlo = take(cap_t * 6 * 4), o_hrg = take(cap_t * 5 * 4), o_hcl = take(cap_t * 4),
@@ -276,7 +278,11 @@ static mlpf_status ensure_workspace(Model& m, int total, int n_events, bool tc) 
     w.o = (float*)(b + o_o); w.hid = (float*)(b + o_hid); w.hpid = (float*)(b + o_hp);
     w.hreg = (float*)(b + o_hr); w.raw = (float*)(b + o_raw);
     w.counters = (int*)(b + o_cnt);
-    if (want_wide) w.a16 = (uint16_t*)(b + o_a16);
+    if (want_wide) {
+        w.a16 = (uint16_t*)(b + o_a16);
+        w.b16 = (uint16_t*)(b + o_b16);
+        w.qkv16 = (uint16_t*)(b + o_qkv16);
+    }
     w.hx = (float*)(b + o_hx); w.hcu = (int32_t*)(b + o_hcu); w.hlogits = (float*)(b + o_hlo);
     w.hcu_chunks = (int32_t*)(b + o_hcc);
     w.hreg_out = (float*)(b + o_hrg); w.hcls = (int32_t*)(b + o_hcl); w.hsums = (double*)(b + o_hsu);

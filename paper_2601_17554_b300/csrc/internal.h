@@ -72,8 +72,11 @@ struct Workspace {
     // row of the r-th element in that order), inputs and outputs in that order
     int32_t* perm = nullptr;
     float *xs = nullptr, *los = nullptr, *rgs = nullptr;
-    // wide tensor-core path: 16-bit GEMM operand scratch [cap_total, 2 x the widest padded input]
+    // wide tensor-core path: two FP16 GEMM operand buffers [cap_total, the widest padded
+    // input] (a layer's input and its hidden activations) and 16-bit Q | K | V [cap_total, 3 d]
     uint16_t* a16 = nullptr;
+    uint16_t* b16 = nullptr;
+    uint16_t* qkv16 = nullptr;
     // host-buffer entry point: device staging
     float *hx = nullptr, *hlogits = nullptr, *hreg_out = nullptr;
     int32_t *hcu = nullptr, *hcls = nullptr;
@@ -199,22 +202,23 @@ mlpf_status parse_blob_into(const uint8_t* p, size_t nbytes, Model& m);
 // elements, bases 16-byte aligned), Kp a multiple of 64 with zeros beyond the true K.
 // mode 0: C = ..., 1: C += ..., 2: C += ... split over K in chunks of kchunk (a multiple
 // of 64; 0 = no split) with atomic adds; bias and R are added once (first split).  act:
-// -1 none, 0 GELU, 1 ReLU.  C16 (or null): 16-bit copy of the result (mode 0).  Returns
+// -1 none, 0 GELU, 1 ReLU.  C16 (or null): 16-bit copy of the result (mode 0; FP16 if
+// c16_f16, else BF16) over max(N, c16_cols) columns, zeros beyond N; C may be null when
+// only the 16-bit copy is wanted.  two_term: B is [N, 2 Kp] = [B_hi | B_lo] and the
+// product is A (B_hi + B_lo)^T (weights carried as two 16-bit terms).  Returns
 // false if a tensor map cannot be encoded.  Bounded waits set ST_TIMEOUT_GEMM in *status.
 bool gemm_tc(int f16, const void* A, long lda, const void* B, long ldb, int M, int N, int Kp, float* C, long ldc,
              const float* bias, const float* R, long ldr, int act, int mode, int kchunk, uint16_t* C16, long ldc16,
-             unsigned* status, uint64_t wait_ns, cudaStream_t st);
+             unsigned* status, uint64_t wait_ns, cudaStream_t st, int c16_f16 = 1, int two_term = 0,
+             int c16_cols = 0);
 // FP32 -> 16-bit operand copies: dst[r, c] = [s1 | s2][r, c] for c < k1 + k2, zero up to ldd
 // (ldd even); cvt_16_t: dst[c, r] = src[r, c] for r < rows, c < cols, zero for rows <= r < ldd.
 void cvt_16(const float* s1, long ld1, int k1, const float* s2, long ld2, int k2, int rows, uint16_t* dst, long ldd,
             int f16, cudaStream_t st);
 void cvt_16_t(const float* src, long lds, int rows, int cols, uint16_t* dst, long ldd, int f16, cudaStream_t st);
 // Two-term weight image [N, 2 kp]: columns 0.. the 16-bit rounding of W, columns kp.. the
-// rounding of its residual (kp a multiple of 64); cvt_16_dup writes each activation row
-// twice, [a | a] (row stride 2 kp), so that one GEMM over 2 kp multiplies a by both terms.
+// rounding of its residual (kp a multiple of 64), the B operand of a two_term gemm_tc.
 void cvt_16_split(const float* W, long ldw, int N, int K, uint16_t* dst, int kp, int f16, cudaStream_t st);
-void cvt_16_dup(const float* s1, long ld1, int k1, const float* s2, long ld2, int k2, int rows, uint16_t* dst, int kp,
-                int f16, cudaStream_t st);
 
 // Varlen self-attention of the training step on the tensor cores (k_attn_train.cu):
 // qkv [T, 3d] FP32 (Q | K | V, heads of dh = d / heads in {16, 32, 64}), out / dO [T, d],
@@ -231,6 +235,11 @@ int64_t run_forward_wide(Model& m, int prec, const float* x, const int32_t* cu, 
                          float* logits, float* reg, cudaStream_t st);
 bool attn_train_bwd_tc(int f16, const float* qkv, const float* dO, const float* lse, const float* D, float* dqkv,
                        const int32_t* cu, int n_events, int max_n, int d, int heads, cudaStream_t st);
+// Forward attention of the generic-width inference path on 16-bit Q | K | V [T, 3d] (FP16 if
+// f16, else BF16); writes O as FP16 rows of stride ldo16 (the next GEMM's operand).
+bool attn_fwd16(int f16, const uint16_t* qkv16, uint16_t* o16, int ldo16, const int32_t* cu, int n_events, int max_n,
+                int d, int heads, cudaStream_t st, int window);
+void attn_fwd16_prepare();   // shared-memory attribute of the dh = 64 variant (outside capture)
 
 // tensor-core path preparation (weights images, tensor maps)
 bool tc_prepare_weights(Model& m);

@@ -307,6 +307,109 @@ __global__ void __launch_bounds__(128) k_attn_dkv_tc(const float* __restrict__ q
     }
 }
 
+// Forward of the generic-width inference path on 16-bit Q | K | V ([T, 3d], written by the
+// QKV GEMM's epilogue): 128 query rows per CTA (eight warps), K / V tiles of 64 rows
+// double-buffered with asynchronous copies, scores scaled by log2(e)/sqrt(dh) in FP32.
+// Writes O as FP16 rows of stride ldo16 (the operand of the output projection's GEMM).
+template <int DH, bool F16>
+__global__ void __launch_bounds__(256) k_attn_fwd16(const uint16_t* __restrict__ qkv16, uint16_t* __restrict__ o16,
+                                                    int ldo16, const int32_t* __restrict__ cu, int d, float c2,
+                                                    int window) {
+    constexpr int LD = DH + 8, CH = DH / 8;   // 16-byte chunks per row
+    extern __shared__ __align__(16) uint16_t att_smem[];   // (128 + 4 x 64) rows of LD
+    uint16_t* Qs = att_smem;
+    auto Kt = [&](int b) { return att_smem + (128 + 64 * b) * LD; };
+    auto Vt = [&](int b) { return att_smem + (256 + 64 * b) * LD; };
+    const int e = blockIdx.z, h = blockIdx.y;
+    const int start = cu[e], n = cu[e + 1] - start, q0 = blockIdx.x * 128;
+    if (q0 >= n) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
+    const long ld = 3L * d;
+    int kbeg = 0, kend = n;
+    if (window > 0) {
+        const int y = q0 / 128;
+        kbeg = max(0, (y - window) * 128);
+        kend = min(n, (y + window + 1) * 128);
+    }
+    // rows r0 .. r0 + rows - 1 of column block col (rows at or beyond lim are zero)
+    auto stage = [&](uint16_t* dst, int rows, int r0, int lim, int col) {
+        for (int i = threadIdx.x; i < rows * CH; i += 256) {
+            const int r = i / CH, ch = i % CH;
+            const bool in = r0 + r < lim;
+            const uint16_t* src = qkv16 + (long)(start + (in ? r0 + r : 0)) * ld + col + ch * 8;
+            cp_async16(dst + r * LD + ch * 8, src, in ? 16u : 0u);
+        }
+    };
+    stage(Qs, 128, q0, n, h * DH);
+    stage(Kt(0), 64, kbeg, kend, d + h * DH);
+    stage(Vt(0), 64, kbeg, kend, 2 * d + h * DH);
+    cp_async_commit();
+    float o[DH / 8][4] = {};
+    float m[2] = {-INFINITY, -INFINITY}, l[2] = {0.f, 0.f};
+    uint32_t qa[DH / 16][4];
+    int buf = 0;
+    for (int kb = kbeg; kb < kend; kb += 64, buf ^= 1) {
+        if (kb + 64 < kend) {
+            stage(Kt(buf ^ 1), 64, kb + 64, kend, d + h * DH);
+            stage(Vt(buf ^ 1), 64, kb + 64, kend, 2 * d + h * DH);
+        }
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncthreads();
+        if (kb == kbeg) {
+#pragma unroll
+            for (int kk = 0; kk < DH / 16; ++kk) load_a<LD>(Qs, warp * 16, kk * 16, qa[kk]);
+        }
+        float s[8][4];
+        scores<DH, F16>(qa, Kt(buf), s);
+        float mx[2] = {m[0], m[1]};
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                s[j][u] = kb + j * 8 + 2 * c + (u & 1) < kend ? s[j][u] * c2 : -INFINITY;
+                mx[u >> 1] = fmaxf(mx[u >> 1], s[j][u]);
+            }
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            mx[r] = fmaxf(mx[r], __shfl_xor_sync(0xffffffffu, mx[r], 1));
+            mx[r] = fmaxf(mx[r], __shfl_xor_sync(0xffffffffu, mx[r], 2));
+        }
+        const float al[2] = {ex2_approx(m[0] - mx[0]), ex2_approx(m[1] - mx[1])};
+        l[0] *= al[0];
+        l[1] *= al[1];
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                s[j][u] = ex2_approx(s[j][u] - mx[u >> 1]);
+                l[u >> 1] += s[j][u];
+            }
+#pragma unroll
+        for (int j = 0; j < DH / 8; ++j)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) o[j][u] *= al[u >> 1];
+        m[0] = mx[0];
+        m[1] = mx[1];
+        accumulate<DH, F16>(s, Vt(buf), o);
+        __syncthreads();   // every warp is done with this buffer before it is refilled
+    }
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        l[r] += __shfl_xor_sync(0xffffffffu, l[r], 1);
+        l[r] += __shfl_xor_sync(0xffffffffu, l[r], 2);
+    }
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int row = q0 + warp * 16 + g + 8 * r;
+        if (row >= n) continue;
+        const float inv = 1.f / l[r];
+        uint32_t* orow = reinterpret_cast<uint32_t*>(o16 + (long)(start + row) * ldo16 + h * DH);
+#pragma unroll
+        for (int j = 0; j < DH / 8; ++j) orow[(j * 8 + 2 * c) / 2] = pack_f16x2(o[j][2 * r] * inv, o[j][2 * r + 1] * inv);
+    }
+}
+
 template <bool F16>
 bool attn_tc_launch(int which, const float* qkv, const float* dO, float* out, float* lse, const float* D,
                     float* dqkv, const int32_t* cu, int n_events, int max_n, int d, int heads, cudaStream_t st,
@@ -343,6 +446,42 @@ bool attn_train_fwd_tc(int f16, const float* qkv, float* out, float* lse, const 
                                       window)
                : attn_tc_launch<false>(0, qkv, nullptr, out, lse, nullptr, nullptr, cu, n_events, max_n, d, heads, st,
                                        window);
+}
+
+static constexpr int attn16_smem(int dh) { return 384 * (dh + 8) * 2; }
+
+void attn_fwd16_prepare() {
+    static bool done[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || done[dev]) return;
+    cudaFuncSetAttribute(k_attn_fwd16<64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, attn16_smem(64));
+    cudaFuncSetAttribute(k_attn_fwd16<64, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, attn16_smem(64));
+    done[dev] = true;
+}
+
+bool attn_fwd16(int f16, const uint16_t* qkv16, uint16_t* o16, int ldo16, const int32_t* cu, int n_events, int max_n,
+                int d, int heads, cudaStream_t st, int window) {
+    if (n_events <= 0 || max_n <= 0) return true;
+    const int dh = d / heads;
+    const float c2 = kLog2e / sqrtf((float)dh);
+    dim3 grid((max_n + 127) / 128, heads, n_events);
+#define MLPF_ATTN16(DH)                                                                               \
+    if (f16)                                                                                          \
+        k_attn_fwd16<DH, true><<<grid, 256, attn16_smem(DH), st>>>(qkv16, o16, ldo16, cu, d, c2, window); \
+    else                                                                                              \
+        k_attn_fwd16<DH, false><<<grid, 256, attn16_smem(DH), st>>>(qkv16, o16, ldo16, cu, d, c2, window);
+    if (dh == 16) {
+        MLPF_ATTN16(16)
+    } else if (dh == 32) {
+        MLPF_ATTN16(32)
+    } else if (dh == 64) {
+        MLPF_ATTN16(64)
+    } else {
+        return false;
+    }
+#undef MLPF_ATTN16
+    return true;
 }
 
 bool attn_train_bwd_tc(int f16, const float* qkv, const float* dO, const float* lse, const float* D, float* dqkv,

@@ -111,6 +111,45 @@ __global__ void k_layernorm(const float* __restrict__ X, const float* __restrict
     }
 }
 
+// The same LayerNorm writing FP16 rows of stride ldy (columns d .. ldy - 1 zero; ldy <= 256):
+// the operand of the next GEMM of the generic-width tensor-core path.
+__global__ void k_layernorm16(const float* __restrict__ X, const float* __restrict__ g, const float* __restrict__ b,
+                              uint16_t* __restrict__ Y, int ldy, int T, int d) {
+    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (row >= T) return;
+    const float* x = X + (size_t)row * d;
+    float v[8];
+    float s = 0.f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int c = lane + 32 * i;
+        v[i] = (c < d) ? x[c] : 0.f;
+        s += v[i];
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    const float mu = s / d;
+    float q = 0.f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int c = lane + 32 * i;
+        const float t = (c < d) ? v[i] - mu : 0.f;
+        q += t * t;
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+    const float rs = rsqrtf(q / d + 1e-5f);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int c = lane + 32 * i;
+        if (c < ldy) {
+            const float y = c < d ? (v[i] - mu) * rs * g[c] + b[c] : 0.f;
+            Y[(size_t)row * ldy + c] = (uint16_t)(pack_f16x2(y, 0.f) & 0xffffu);
+        }
+    }
+}
+
 // Self-attention within each event; one thread per query row, 64 keys per
 // shared-memory tile, FP32 online softmax (exact expf).  qkv rows are
 // [q | k | v] with head h in columns h*DH .. h*DH+DH-1 of each part.
@@ -421,29 +460,47 @@ int64_t run_forward_f32(Model& m, const float* x, const int32_t* cu, int n_event
 // Forward of models outside the fused d = 64 kernels (any width with heads of 16, 32 or
 // 64; both architectures) on the tensor cores: every linear layer is one tcgen05 GEMM
 // (FP16 operands with two-term weights, FP32 accumulation, bias / activation / residual in
-// its epilogue) fed by a conversion of its FP32 input, attention runs on warp-level MMAs (BF16 operands in the
-// BF16 mode, FP16 in the FP16 mode; FP32 softmax statistics), LayerNorm and the decode
-// stay FP32.  Same launch sequence as the plain path otherwise.
+// its epilogue); the blocks' LayerNorms, the QKV GEMM, attention and the FFN's first GEMM
+// hand their outputs to the next GEMM as 16-bit rows, the embedding and head inputs are
+// converted; attention runs on warp-level MMAs (BF16 operands in the BF16 mode, FP16 in
+// the FP16 mode; FP32 softmax statistics); LayerNorm moments, the residual stream and the
+// decode stay FP32.  Same launch sequence as the plain path otherwise.
 static constexpr uint64_t WIDE_WAIT_NS = 2000000000ull;
 
-static void tlinear(Model& m, const float* X1, int ld1, int K1, const float* X2, int ld2, int K2, const float* W,
-                    const float* b, const float* R, int ldr, float* Y, int ldy, int T, int N, int act,
-                    cudaStream_t st, int64_t& n, bool& ok) {
+// y[T, N] = act([X1 | X2] W^T + b) (+ R) with two-term FP16 weights.  A16 (or null): the
+// FP16 operand rows are already there (stride = W's padded K); otherwise [X1 | X2] is
+// converted into the scratch first.  Y (or null): FP32 result; Y16 (or null): 16-bit copy
+// (format c16_f16) of stride y16_ld, zero beyond N.
+static void tlinear(Model& m, const uint16_t* A16, const float* X1, int ld1, int K1, const float* X2, int ld2, int K2,
+                    const float* W, const float* b, const float* R, int ldr, float* Y, int ldy, int T, int N, int act,
+                    cudaStream_t st, int64_t& n, bool& ok, uint16_t* Y16 = nullptr, int y16_ld = 0, int c16_f16 = 1) {
     const auto it = m.w.w16.find(W);
     if (it == m.w.w16.end()) {
         ok = false;
         return;
     }
     const int Kp = it->second.second;
-    prof_begin(m, st, "wide_cvt");
-    cvt_16_dup(X1, ld1, K1, X2, ld2, K2, T, m.ws.a16, Kp, 1, st);
-    prof_end(m, st);
+    if (!A16) {
+        prof_begin(m, st, "wide_cvt");
+        cvt_16(X1, ld1, K1, X2, ld2, K2, T, m.ws.a16, Kp, 1, st);
+        prof_end(m, st);
+        ++n;
+        A16 = m.ws.a16;
+    }
     prof_begin(m, st, "wide_gemm");
-    if (!gemm_tc(1, m.ws.a16, 2 * Kp, it->second.first, 2 * Kp, T, N, 2 * Kp, Y, ldy, b, R, ldr, act, 0, 0, nullptr, 0,
-                 m.status, WIDE_WAIT_NS, st))
+    if (!gemm_tc(1, A16, Kp, it->second.first, 2 * Kp, T, N, Kp, Y, ldy, b, R, ldr, act, 0, 0, Y16, y16_ld, m.status,
+                 WIDE_WAIT_NS, st, c16_f16, 1, y16_ld))
         ok = false;
     prof_end(m, st);
-    n += 2;
+    ++n;
+}
+
+static void layernorm16(Model& m, const float* X, const float* g, const float* b, uint16_t* Y, int ldy, int T, int d,
+                        cudaStream_t st, int64_t& n) {
+    prof_begin(m, st, "wide_layernorm");
+    k_layernorm16<<<cdiv(T, 8), 256, 0, st>>>(X, g, b, Y, ldy, T, d);
+    prof_end(m, st);
+    ++n;
 }
 
 int64_t run_forward_wide(Model& m, int prec, const float* x, const int32_t* cu, int n_events, int total, int max_n,
@@ -455,34 +512,36 @@ int64_t run_forward_wide(Model& m, int prec, const float* x, const int32_t* cu, 
     int64_t n = 0;
     bool ok = true;
     g_model = &m;
+    const int Kd = (d + 63) / 64 * 64, Kf = (F + 63) / 64 * 64;   // padded operand widths
     auto stack = [&](const char* prefix, int layers, std::vector<float*>& wqkv, std::vector<float*>& bqkv,
                      float* out) {
         for (int l = 0; l < layers; ++l) {
             const std::string p = std::string(prefix) + "." + std::to_string(l) + ".";
-            layernorm(w.z, W(p + "ln1.g"), W(p + "ln1.b"), w.zn, T, d, st, n);
-            tlinear(m, w.zn, d, d, nullptr, 0, 0, wqkv[l], bqkv[l], nullptr, 0, w.qkv, 3 * d, T, 3 * d, -1, st, n,
-                    ok);
+            layernorm16(m, w.z, W(p + "ln1.g"), W(p + "ln1.b"), w.a16, Kd, T, d, st, n);
+            // Q | K | V only as 16-bit values (the attention operands' format)
+            tlinear(m, w.a16, nullptr, 0, d, nullptr, 0, 0, wqkv[l], bqkv[l], nullptr, 0, nullptr, 0, T, 3 * d, -1, st,
+                    n, ok, w.qkv16, 3 * d, prec == MLPF_FP16);
             prof_begin(m, st, "wide_attention");
-            if (!attn_train_fwd_tc(prec == MLPF_FP16, w.qkv, w.o, nullptr, cu, n_events, max_n, d, c.heads, st,
-                                   m.attn_window))
+            if (!attn_fwd16(prec == MLPF_FP16, w.qkv16, w.a16, Kd, cu, n_events, max_n, d, c.heads, st, m.attn_window))
                 ok = false;
             prof_end(m, st);
             ++n;
-            tlinear(m, w.o, d, d, nullptr, 0, 0, W(p + "wo"), W(p + "bo"), w.z, d, w.z, d, T, d, -1, st, n, ok);
-            layernorm(w.z, W(p + "ln2.g"), W(p + "ln2.b"), w.zn, T, d, st, n);
-            tlinear(m, w.zn, d, d, nullptr, 0, 0, W(p + "ffn.w1"), W(p + "ffn.b1"), nullptr, 0, w.hid, F, T, F, act,
-                    st, n, ok);
-            tlinear(m, w.hid, F, F, nullptr, 0, 0, W(p + "ffn.w2"), W(p + "ffn.b2"), w.z, d, w.z, d, T, d, -1, st, n,
+            tlinear(m, w.a16, nullptr, 0, d, nullptr, 0, 0, W(p + "wo"), W(p + "bo"), w.z, d, w.z, d, T, d, -1, st, n,
                     ok);
+            layernorm16(m, w.z, W(p + "ln2.g"), W(p + "ln2.b"), w.a16, Kd, T, d, st, n);
+            tlinear(m, w.a16, nullptr, 0, d, nullptr, 0, 0, W(p + "ffn.w1"), W(p + "ffn.b1"), nullptr, 0, nullptr, 0, T,
+                    F, act, st, n, ok, w.b16, Kf);
+            tlinear(m, w.b16, nullptr, 0, F, nullptr, 0, 0, W(p + "ffn.w2"), W(p + "ffn.b2"), w.z, d, w.z, d, T, d, -1,
+                    st, n, ok);
         }
         layernorm(w.z, W(std::string(prefix) + ".lnf.g"), W(std::string(prefix) + ".lnf.b"), out, T, d, st, n);
     };
     auto mlp = [&](const float* in, int k_in, const char* p, float* out, int ldo, int n_out) {
         const std::string s(p);
-        tlinear(m, in, k_in, k_in, nullptr, 0, 0, W(s + ".w1"), W(s + ".b1"), nullptr, 0, w.hid, d, T, d, act, st, n,
-                ok);
-        tlinear(m, w.hid, d, d, nullptr, 0, 0, W(s + ".w2"), W(s + ".b2"), nullptr, 0, out, ldo, T, n_out, -1, st, n,
-                ok);
+        tlinear(m, nullptr, in, k_in, k_in, nullptr, 0, 0, W(s + ".w1"), W(s + ".b1"), nullptr, 0, nullptr, 0, T, d,
+                act, st, n, ok, w.b16, Kd);
+        tlinear(m, w.b16, nullptr, 0, d, nullptr, 0, 0, W(s + ".w2"), W(s + ".b2"), nullptr, 0, out, ldo, T, n_out, -1,
+                st, n, ok);
     };
     if (c.arch == 1) {
         mlp(x, 42, "emb.trk", w.hreg, d, d);
@@ -502,8 +561,10 @@ int64_t run_forward_wide(Model& m, int prec, const float* x, const int32_t* cu, 
     } else {
         mlp(x, 42, "emb", w.z, d, d);
         stack("pid", c.l_pid, m.w.wqkv_pid, m.w.bqkv_pid, w.hpid);
-        tlinear(m, x, 42, 42, w.hpid, d, d, W("remb.w1"), W("remb.b1"), nullptr, 0, w.hid, d, T, d, act, st, n, ok);
-        tlinear(m, w.hid, d, d, nullptr, 0, 0, W("remb.w2"), W("remb.b2"), nullptr, 0, w.z, d, T, d, -1, st, n, ok);
+        tlinear(m, nullptr, x, 42, 42, w.hpid, d, d, W("remb.w1"), W("remb.b1"), nullptr, 0, nullptr, 0, T, d, act, st,
+                n, ok, w.b16, Kd);
+        tlinear(m, w.b16, nullptr, 0, d, nullptr, 0, 0, W("remb.w2"), W("remb.b2"), nullptr, 0, w.z, d, T, d, -1, st, n,
+                ok);
         stack("reg", c.l_reg, m.w.wqkv_reg, m.w.bqkv_reg, w.hreg);
         mlp(w.hpid, d, "head.cls", logits, c.n_cls, c.n_cls);
     }
@@ -546,6 +607,7 @@ bool wide_prepare_weights(Model& m) {
         off += (size_t)N * 2 * Kp;
     }
     gemm_tc_prepare();
+    attn_fwd16_prepare();
     return cudaDeviceSynchronize() == cudaSuccess;
 }
 

@@ -35,7 +35,9 @@ struct TgArgs {
     long ldr;
     int mode;           // 0: C = ..., 1: C += ..., 2: C += ... with atomics (split-K)
     int act;            // -1 none, 0 GELU (erf), 1 ReLU: applied to (acc + bias), before R
-    int f16;            // operand and C16 format: 1 FP16, 0 BF16
+    int f16;            // operand format: 1 FP16, 0 BF16
+    int c16_f16;        // C16 format: 1 FP16, 0 BF16
+    int c16_cols;       // C16 columns written (>= N: the padding columns beyond N get zeros)
     unsigned* status;
     uint64_t wait_ns;
 };
@@ -46,21 +48,23 @@ __device__ __forceinline__ float tg_act(float v, int act) {
     return v;
 }
 
-template <int BN, int ST>
+// TWO: the weight operand is two-term, B = [B_hi | B_lo] of 2 Kp columns; each K step
+// multiplies the A tile by both terms into the same accumulator.
+template <int BN, int ST, bool TWO = false>
 struct TgLayout {
     static constexpr int A_BYTES = TG_BM * TG_BK * 2;
     static constexpr int B_BYTES = BN * TG_BK * 2;
-    static constexpr int STAGE = A_BYTES + B_BYTES;          // multiple of 1024
+    static constexpr int STAGE = A_BYTES + (TWO ? 2 : 1) * B_BYTES;   // multiple of 1024
     static constexpr int OFF_BAR = ST * STAGE;                // full[ST], empty[ST], done
     static constexpr int OFF_MISC = OFF_BAR + (2 * ST + 1) * 8;
     static constexpr int BYTES = OFF_MISC + 64 + 1024;        // + alignment slack
     static constexpr uint32_t TMEM_COLS = BN < 32 ? 32 : BN;
 };
 
-template <int BN, int ST>
+template <int BN, int ST, bool TWO>
 __global__ void __launch_bounds__(128) k_gemm_tc(const __grid_constant__ CUtensorMap map_a,
                                                  const __grid_constant__ CUtensorMap map_b, TgArgs g) {
-    using L = TgLayout<BN, ST>;
+    using L = TgLayout<BN, ST, TWO>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t* full = (uint64_t*)(smem + L::OFF_BAR);
@@ -109,6 +113,7 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const __grid_constant__ CUtenso
             mbar_arrive_expect_tx(&full[s], L::STAGE);
             tma_load_2d(sa, &map_a, kbeg + i * TG_BK, m0, &full[s]);
             tma_load_2d(sa + L::A_BYTES, &map_b, kbeg + i * TG_BK, n0, &full[s]);
+            if constexpr (TWO) tma_load_2d(sa + L::A_BYTES + L::B_BYTES, &map_b, g.Kp + kbeg + i * TG_BK, n0, &full[s]);
         }
         *issued_s = i;
     } else if (warp == 1 && lane == 0) {   // MMA issuer
@@ -121,8 +126,10 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const __grid_constant__ CUtenso
             tc_fence_after();
             const uint32_t sa = smem_u32(smem + s * L::STAGE), sb = sa + L::A_BYTES;
 #pragma unroll
-            for (int kk = 0; kk < TG_BK / 16; ++kk)
+            for (int kk = 0; kk < TG_BK / 16; ++kk) {
                 mma_f16(tmem, sdesc_sw128(sa + kk * 32), sdesc_sw128(sb + kk * 32), idesc, (i | kk) != 0);
+                if constexpr (TWO) mma_f16(tmem, sdesc_sw128(sa + kk * 32), sdesc_sw128(sb + L::B_BYTES + kk * 32), idesc, 1);
+            }
             mma_commit(&empty[s]);
         }
         *consumed_s = i;
@@ -143,8 +150,9 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const __grid_constant__ CUtenso
         tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + c * 32, v);
         tmem_wait_ld();
         const int nb = n0 + c * 32;
-        if (!row_ok || nb >= g.N) continue;
-        const int nn = min(32, g.N - nb);
+        if (!row_ok || nb >= max(g.N, g.c16_cols)) continue;
+        const int nn = max(0, min(32, g.N - nb));          // columns of the result
+        const int n16 = max(0, min(32, g.c16_cols - nb));   // columns of the 16-bit copy (zero beyond N)
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
             if (j >= nn) break;
@@ -154,7 +162,10 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const __grid_constant__ CUtenso
             if (lead && g.R) y += g.R[(long)r * g.ldr + nb + j];
             v[j] = y;
         }
-        float* crow = g.C ? g.C + (long)r * g.ldc + nb : nullptr;
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+            if (j >= nn) v[j] = 0.f;
+        float* crow = g.C && nn > 0 ? g.C + (long)r * g.ldc + nb : nullptr;
         if (crow) {
             if (g.mode == 2) {
 #pragma unroll
@@ -182,11 +193,23 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const __grid_constant__ CUtenso
         }
         if (g.C16) {
             uint16_t* hrow = g.C16 + (long)r * g.ldc16 + nb;
+            if (n16 == 32 && ((g.ldc16 | nb) & 7) == 0 && ((uintptr_t)g.C16 & 15) == 0) {
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                if (j >= nn) break;
-                const uint32_t p = g.f16 ? pack_f16x2(v[j], 0.f) : pack_bf16x2(v[j], 0.f);
-                hrow[j] = (uint16_t)(p & 0xffffu);
+                for (int q = 0; q < 4; ++q) {
+                    uint4 p;
+                    p.x = g.c16_f16 ? pack_f16x2(v[8 * q], v[8 * q + 1]) : pack_bf16x2(v[8 * q], v[8 * q + 1]);
+                    p.y = g.c16_f16 ? pack_f16x2(v[8 * q + 2], v[8 * q + 3]) : pack_bf16x2(v[8 * q + 2], v[8 * q + 3]);
+                    p.z = g.c16_f16 ? pack_f16x2(v[8 * q + 4], v[8 * q + 5]) : pack_bf16x2(v[8 * q + 4], v[8 * q + 5]);
+                    p.w = g.c16_f16 ? pack_f16x2(v[8 * q + 6], v[8 * q + 7]) : pack_bf16x2(v[8 * q + 6], v[8 * q + 7]);
+                    reinterpret_cast<uint4*>(hrow)[q] = p;
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    if (j >= n16) break;
+                    const uint32_t p = g.c16_f16 ? pack_f16x2(v[j], 0.f) : pack_bf16x2(v[j], 0.f);
+                    hrow[j] = (uint16_t)(p & 0xffffu);
+                }
             }
         }
     }
@@ -266,26 +289,6 @@ __global__ void k_cvt_split(const float* __restrict__ W, long ldw, int N, int K,
     }
 }
 
-// dst[r, 0 .. kp) = dst[r, kp .. 2 kp) = 16-bit [s1 | s2][r, :] zero padded (row stride 2 kp)
-__global__ void k_cvt_dup(const float* __restrict__ s1, long ld1, int k1, const float* __restrict__ s2, long ld2,
-                          int k2, int rows, uint16_t* __restrict__ dst, int kp, int f16) {
-    const long n = (long)rows * (kp / 2);
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-        const long r = i / (kp / 2);
-        const int c = (int)(i % (kp / 2)) * 2;
-        float v[2];
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            const int cc = c + u;
-            v[u] = cc < k1 ? s1[r * ld1 + cc] : (cc < k1 + k2 ? s2[r * ld2 + cc - k1] : 0.f);
-        }
-        const uint32_t p = f16 ? pack_f16x2(v[0], v[1]) : pack_bf16x2(v[0], v[1]);
-        uint32_t* row = (uint32_t*)(dst + r * 2 * kp);
-        row[c / 2] = p;
-        row[kp / 2 + c / 2] = p;
-    }
-}
-
 typedef CUresult (*TgEncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -316,11 +319,11 @@ bool tg_map(CUtensorMap* map, const void* base, long Kp, long rows, long ld, uin
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int BN, int ST>
+template <int BN, int ST, bool TWO = false>
 void tg_launch(const CUtensorMap& ma, const CUtensorMap& mb, const TgArgs& a, int splits, cudaStream_t st) {
-    using L = TgLayout<BN, ST>;
-    dim3 grid((a.M + TG_BM - 1) / TG_BM, (a.N + BN - 1) / BN, splits);
-    k_gemm_tc<BN, ST><<<grid, 128, L::BYTES, st>>>(ma, mb, a);
+    using L = TgLayout<BN, ST, TWO>;
+    dim3 grid((a.M + TG_BM - 1) / TG_BM, (std::max(a.N, a.c16_cols) + BN - 1) / BN, splits);
+    k_gemm_tc<BN, ST, TWO><<<grid, 128, L::BYTES, st>>>(ma, mb, a);
 }
 
 }  // namespace
@@ -330,19 +333,26 @@ void gemm_tc_prepare() {
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64 || done[dev]) return;
-    cudaFuncSetAttribute(k_gemm_tc<64, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, TgLayout<64, 4>::BYTES);
-    cudaFuncSetAttribute(k_gemm_tc<128, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, TgLayout<128, 3>::BYTES);
-    cudaFuncSetAttribute(k_gemm_tc<256, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, TgLayout<256, 2>::BYTES);
+    cudaFuncSetAttribute(k_gemm_tc<64, 4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, TgLayout<64, 4>::BYTES);
+    cudaFuncSetAttribute(k_gemm_tc<128, 3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         TgLayout<128, 3>::BYTES);
+    cudaFuncSetAttribute(k_gemm_tc<256, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         TgLayout<256, 2>::BYTES);
+    cudaFuncSetAttribute(k_gemm_tc<64, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         TgLayout<64, 3, true>::BYTES);
+    cudaFuncSetAttribute(k_gemm_tc<128, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         TgLayout<128, 2, true>::BYTES);
     done[dev] = true;
 }
 
 bool gemm_tc(int f16, const void* A, long lda, const void* B, long ldb, int M, int N, int Kp, float* C, long ldc,
              const float* bias, const float* R, long ldr, int act, int mode, int kchunk, uint16_t* C16, long ldc16,
-             unsigned* status, uint64_t wait_ns, cudaStream_t st) {
+             unsigned* status, uint64_t wait_ns, cudaStream_t st, int c16_f16, int two_term, int c16_cols) {
     if (M <= 0 || N <= 0 || Kp <= 0) return true;
-    const int BN = N <= 64 ? 64 : (N <= 128 ? 128 : 256);
+    const int Nt = std::max(N, C16 ? c16_cols : 0);
+    const int BN = Nt <= 64 ? 64 : ((Nt <= 128 || two_term) ? 128 : 256);
     CUtensorMap ma, mb;
-    if (!tg_map(&ma, A, Kp, M, lda, TG_BM) || !tg_map(&mb, B, Kp, N, ldb, BN)) return false;
+    if (!tg_map(&ma, A, Kp, M, lda, TG_BM) || !tg_map(&mb, B, two_term ? 2L * Kp : Kp, N, ldb, BN)) return false;
     TgArgs a;
     a.M = M;
     a.N = N;
@@ -359,11 +369,18 @@ bool gemm_tc(int f16, const void* A, long lda, const void* B, long ldb, int M, i
     a.mode = mode;
     a.act = act;
     a.f16 = f16;
+    a.c16_f16 = c16_f16;
+    a.c16_cols = C16 ? std::max(c16_cols, N) : 0;
     a.status = status;
     a.wait_ns = wait_ns;
     const int splits = (Kp + kchunk - 1) / kchunk;
-    // three to four stages of 24-48 KB: two CTAs (and 2 x BN tensor-memory columns) per SM
-    if (BN == 64)
+    // two to four stages of 24-48 KB: two CTAs (and 2 x BN tensor-memory columns) per SM
+    if (two_term) {
+        if (BN == 64)
+            tg_launch<64, 3, true>(ma, mb, a, splits, st);
+        else
+            tg_launch<128, 2, true>(ma, mb, a, splits, st);
+    } else if (BN == 64)
         tg_launch<64, 4>(ma, mb, a, splits, st);
     else if (BN == 128)
         tg_launch<128, 3>(ma, mb, a, splits, st);
@@ -384,14 +401,6 @@ void cvt_16_split(const float* W, long ldw, int N, int K, uint16_t* dst, int kp,
     const long n = (long)N * 2 * kp;
     if (n <= 0) return;
     k_cvt_split<<<(unsigned)std::min<long>((n + 255) / 256, 148L * 16), 256, 0, st>>>(W, ldw, N, K, dst, kp, f16);
-}
-
-void cvt_16_dup(const float* s1, long ld1, int k1, const float* s2, long ld2, int k2, int rows, uint16_t* dst, int kp,
-                int f16, cudaStream_t st) {
-    const long n = (long)rows * (kp / 2);
-    if (n <= 0) return;
-    k_cvt_dup<<<(unsigned)std::min<long>((n + 255) / 256, 148L * 16), 256, 0, st>>>(s1, ld1, k1, s2, ld2, k2, rows,
-                                                                                      dst, kp, f16);
 }
 
 void cvt_16_t(const float* src, long lds, int rows, int cols, uint16_t* dst, long ldd, int f16, cudaStream_t st) {

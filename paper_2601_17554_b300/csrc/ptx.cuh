@@ -117,6 +117,18 @@ MLPF_DEV void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* ba
         : "memory");
 }
 
+// 16-byte asynchronous copy global -> shared; src_bytes = 0 fills the 16 bytes with zeros
+// (src is then not read)
+MLPF_DEV void cp_async16(void* dst, const void* src, uint32_t src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+MLPF_DEV void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+MLPF_DEV void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // ------------------------------------------------------------------ tcgen05
 MLPF_DEV void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {  // whole warp
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(

@@ -1,22 +1,23 @@
 """Distil a student MLPF from the full model and measure gated inference.
 
-Teacher: the full-size model (width 256, 8 heads of 32, FFN 1024, 3 + 3 blocks),
-run by the plain FP32 path, with its class head's last layer scaled so that about
-95 % of elements get a class probability >= 0.9 (a stand-in for a trained,
-confident model: random weights give flat class scores).
-Student (--student): d64 = width 64, 4 heads of 16, FFN 256, 1 + 1 blocks, which runs
-on the tensor-core path in BF16; or cfg5 = width 128, 4 heads of 32, FFN 512, 2 + 2
-blocks (the distillation configuration), which runs on the plain FP32 path (the
-tensor-core path is built for width 64); trained on the teacher's per-element outputs (class scores and
-the 5 regressions) of synthetic events with N ~ U{1000..6000} elements, with the
-library's hand-written FP32 forward/backward kernels and LAMB (learning rate
-2e-3 -> 2e-4 on a cosine schedule, Sec. 5.3).
-Evaluation: the 512-event workload run by the teacher alone, the student alone
-and the student with per-event fallback to the teacher below a mean class
-confidence of 0.9.
+Teacher: the full-size model (width 256, 8 heads of 32, FFN 1024, 3 + 3 blocks), with
+its class head's last layer scaled so that about 95 % of elements get a class
+probability >= 0.9 (a stand-in for a trained, confident model: random weights give
+flat class scores); run in BF16 on the generic-width tensor-core path for the training
+targets and the gated fallback (--teacher-precision), and in FP32 as the reference the
+agreement is measured against.
+Student (--student): d64 = width 64, 4 heads of 16, FFN 256, 1 + 1 blocks (the fused
+tensor-core kernels), or cfg5 = width 128, 4 heads of 32, FFN 512, 2 + 2 blocks (the
+distillation configuration; the generic-width tensor-core path), both run in BF16;
+trained on the teacher's per-element outputs (class scores and the 5 regressions) of
+synthetic events with N ~ U{1000..6000} elements, with the library's hand-written
+forward/backward kernels (BF16 tensor-core GEMMs and attention by default,
+--train-precision) and LAMB (learning rate 2e-3 -> 2e-4 on a cosine schedule, Sec. 5.3).
+Evaluation: the 512-event workload run by the teacher alone, the student alone and
+the student with per-event fallback to the teacher below a class confidence threshold.
 
     python -m paper_2601_17554_b300.distill [--train-events 20000] [--epochs 2]
-        [--batch-events 32] [--out student.blob] [--json result.json]
+        [--batch-events 32] [--student d64|cfg5] [--out student.blob] [--json result.json]
 """
 from __future__ import annotations
 
@@ -83,6 +84,11 @@ def main(argv=None):
     ap.add_argument("--out", default="")
     ap.add_argument("--json", default="")
     ap.add_argument("--student", default="d64", choices=["d64", "cfg5"])
+    ap.add_argument("--train-precision", default="bf16", choices=["fp32", "bf16", "fp16"],
+                    help="trainer arithmetic: 16-bit tensor-core GEMMs and attention, or FP32")
+    ap.add_argument("--teacher-precision", default="bf16", choices=["fp32", "bf16", "fp16"],
+                    help="teacher forward for the training targets and the gated fallback "
+                         "(agreement is always measured against the FP32 teacher)")
     ap.add_argument("--student-blob", default="",
                     help="evaluate this trained student (skip the training)")
     args = ap.parse_args(argv)
@@ -121,21 +127,24 @@ def main(argv=None):
         X = torch.from_numpy(x).to(dev)
         CU = torch.from_numpy(cu).to(dev)
         mn = int(np.diff(cu).max())
-        tl, tr, _, _ = teacher.forward(X, CU, mn, precision="fp32", want_cls=False, want_sums=False)
+        tl, tr, _, _ = teacher.forward(X, CU, mn, precision=args.teacher_precision, want_cls=False,
+                                       want_sums=False)
         batches.append((X, CU, mn, tl, tr))
     torch.cuda.synchronize()
     res["teacher_targets_s"] = time.time() - t0
 
     # training
     scfg = synth.SMALL if args.student == "d64" else STUDENT_CFG5
-    sprec = "bf16" if args.student == "d64" else "fp32"
+    sprec = "bf16"   # d64: the fused kernels; cfg5: the generic-width tensor-core path
     res["student"] = {"config": args.student, "d": scfg.d, "heads": scfg.heads, "ffn": scfg.ffn,
-                      "l_pid": scfg.l_pid, "l_reg": scfg.l_reg, "precision": sprec}
+                      "l_pid": scfg.l_pid, "l_reg": scfg.l_reg, "precision": sprec,
+                      "train_precision": args.train_precision}
+    res["teacher_precision"] = args.teacher_precision
     init_blob = synth.pack_blob(scfg, synth.make_weights(scfg, STUDENT_SEED))
     if args.student_blob:
         batches = []
         args.epochs = 0
-    trainer = Trainer(init_blob)
+    trainer = Trainer(init_blob, precision=args.train_precision)
     total_steps = args.epochs * len(batches)
     rng = np.random.default_rng(0)
     losses = []
@@ -153,6 +162,7 @@ def main(argv=None):
     torch.cuda.synchronize()
     res["train_s"] = time.time() - t0
     res["train_steps"] = total_steps
+    res["train_ms_per_step"] = 1e3 * res["train_s"] / max(1, total_steps)
     res["loss_curve"] = losses
     blob = trainer.export()
     trainer.close()
@@ -180,9 +190,13 @@ def main(argv=None):
         torch.cuda.synchronize()
         return out, a.elapsed_time(b) / reps
 
-    tout, t_ms = timed(lambda: teacher.forward(X, CU, mn, precision="fp32"), reps=1)
+    tout, t32_ms = timed(lambda: teacher.forward(X, CU, mn, precision="fp32"), reps=1)
     t_cls = tout[2].cpu().numpy()
     t_reg = tout[1].cpu().numpy()
+    # the teacher as the gated path runs it (its own agreement with the FP32 teacher)
+    tlp, t_ms = timed(lambda: teacher.forward(X, CU, mn, precision=args.teacher_precision), reps=1)
+    res["teacher_lowp_agreement"] = float((tlp[2].cpu().numpy() == t_cls).mean())
+    res["teacher_fp32_ms"] = t32_ms
 
     def evaluate(name, blob_):
         student = Model(blob_)
@@ -214,7 +228,8 @@ def main(argv=None):
             student.set_option(_lib.OPT_GATE_CONFIDENCE, mode)
             for thr in sorted({args.threshold, 0.5, 0.7, 0.95, 0.99, 0.995, 0.999}):
                 gout, g_ms = timed(lambda: forward_gated(student, teacher, thr, X, CU, mn,
-                                                         student_precision=sprec), reps=1)
+                                                         student_precision=sprec,
+                                                         teacher_precision=args.teacher_precision), reps=1)
                 g_cls = gout[2].cpu().numpy()
                 g_reg = gout[1].cpu().numpy()
                 rel = np.sqrt(((g_reg - t_reg) ** 2).sum(0) / (t_reg ** 2).sum(0))
