@@ -1,13 +1,13 @@
-// 16-bit tensor-core GEMM with a fused FP32 epilogue, for the training step's linear layers
-// (Sec. 5.3: every layer of the model is a dense map y = x W^T + b; its backward needs
-// dX = dY W and dW = dY^T X).  One CTA computes a 128 x BN tile of
+// 16-bit tensor-core GEMM with a fused FP32 epilogue, for the linear layers of the training
+// step and of the generic-width forward (Sec. 5.3: every layer of the model is a dense map
+// y = x W^T + b; its backward needs dX = dY W and dW = dY^T X).  Each 128 x BN tile of
 //     C (op)= act(A[M, Kp] B[N, Kp]^T + bias) + R
 // with A and B row-major 16-bit (BF16 or FP16) in global memory, Kp a multiple of 64:
 // TMA copies 128 x 64 and BN x 64 boxes (128-byte swizzle) into a ring of shared stages,
 // one thread issues tcgen05.mma (M = 128, N = BN, K = 16 per instruction) into a
 // BN-column FP32 accumulator in tensor memory, and four warps read it back with
-// tcgen05.ld (thread = row) for the epilogue.  Split-K over blockIdx.z adds partial tiles
-// with atomics (weight gradients, whose reduction runs over all elements of the batch).
+// tcgen05.ld (thread = row) for the epilogue.  Split-K adds partial tiles with atomics
+// (weight gradients, whose reduction runs over all elements of the batch).
 // Every wait is bounded: on a timeout the CTA sets the status word, lets its copies and
 // MMAs in flight land, frees its tensor memory and returns.
 #include <cuda.h>
@@ -55,37 +55,159 @@ struct TgLayout {
     static constexpr int A_BYTES = TG_BM * TG_BK * 2;
     static constexpr int B_BYTES = BN * TG_BK * 2;
     static constexpr int STAGE = A_BYTES + (TWO ? 2 : 1) * B_BYTES;   // multiple of 1024
-    static constexpr int OFF_BAR = ST * STAGE;                // full[ST], empty[ST], done
-    static constexpr int OFF_MISC = OFF_BAR + (2 * ST + 1) * 8;
+    // full[ST], empty[ST], acc_full[2], acc_empty[2], drain
+    static constexpr int OFF_BAR = ST * STAGE;
+    static constexpr int OFF_MISC = OFF_BAR + (2 * ST + 5) * 8;
     static constexpr int BYTES = OFF_MISC + 64 + 1024;        // + alignment slack
-    static constexpr uint32_t TMEM_COLS = BN < 32 ? 32 : BN;
+    static constexpr uint32_t TMEM_COLS = 2 * BN;              // two accumulators
 };
 
+// The epilogue of one 32-column chunk of one row: bias, activation, residual, FP32 and
+// 16-bit stores.  r: the row, nb: the chunk's first column, lead: the split that adds
+// bias and residual.
+__device__ __forceinline__ void red_add_v4(float* p, float4 v) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tg_store_chunk(const TgArgs& g, float* v, int r, int nb, bool lead) {
+    const int nn = max(0, min(32, g.N - nb));          // columns of the result
+    const int n16 = max(0, min(32, g.c16_cols - nb));   // columns of the 16-bit copy (zero beyond N)
+    if (nn == 32 && (nb & 3) == 0) {   // full chunk: 16-byte loads of bias and residual
+        if (lead && g.bias && ((uintptr_t)g.bias & 15) == 0) {
+            const float4* b4 = reinterpret_cast<const float4*>(g.bias + nb);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const float4 b = __ldg(b4 + q);
+                v[4 * q] += b.x;
+                v[4 * q + 1] += b.y;
+                v[4 * q + 2] += b.z;
+                v[4 * q + 3] += b.w;
+            }
+        } else if (lead && g.bias) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) v[j] += g.bias[nb + j];
+        }
+        if (g.act >= 0)
+#pragma unroll
+            for (int j = 0; j < 32; ++j) v[j] = tg_act(v[j], g.act);
+        if (lead && g.R && ((g.ldr & 3) == 0) && ((uintptr_t)g.R & 15) == 0) {
+            const float4* r4 = reinterpret_cast<const float4*>(g.R + (long)r * g.ldr + nb);
+            float4 rr[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) rr[q] = r4[q];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                v[4 * q] += rr[q].x;
+                v[4 * q + 1] += rr[q].y;
+                v[4 * q + 2] += rr[q].z;
+                v[4 * q + 3] += rr[q].w;
+            }
+        } else if (lead && g.R) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) v[j] += g.R[(long)r * g.ldr + nb + j];
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            if (j >= nn) break;
+            float y = v[j];
+            if (lead && g.bias) y += g.bias[nb + j];
+            y = tg_act(y, g.act);
+            if (lead && g.R) y += g.R[(long)r * g.ldr + nb + j];
+            v[j] = y;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+        if (j >= nn) v[j] = 0.f;
+    float* crow = g.C && nn > 0 ? g.C + (long)r * g.ldc + nb : nullptr;
+    if (crow) {
+        if (g.mode == 2 && nn == 32 && ((g.ldc | nb) & 3) == 0 && ((uintptr_t)g.C & 15) == 0) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                red_add_v4(crow + 4 * q, make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]));
+        } else if (g.mode == 2) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+                if (j < nn) atomicAdd(crow + j, v[j]);
+        } else if (nn == 32 && ((g.ldc | nb) & 3) == 0 && ((uintptr_t)g.C & 15) == 0) {
+            float4* c4 = (float4*)crow;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                float4 o = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                if (g.mode == 1) {
+                    const float4 p = c4[q];
+                    o.x += p.x;
+                    o.y += p.y;
+                    o.z += p.z;
+                    o.w += p.w;
+                }
+                c4[q] = o;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+                if (j < nn) crow[j] = g.mode == 1 ? crow[j] + v[j] : v[j];
+        }
+    }
+    if (g.C16 && n16 > 0) {
+        uint16_t* hrow = g.C16 + (long)r * g.ldc16 + nb;
+        if (n16 == 32 && ((g.ldc16 | nb) & 7) == 0 && ((uintptr_t)g.C16 & 15) == 0) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                uint4 p;
+                p.x = g.c16_f16 ? pack_f16x2(v[8 * q], v[8 * q + 1]) : pack_bf16x2(v[8 * q], v[8 * q + 1]);
+                p.y = g.c16_f16 ? pack_f16x2(v[8 * q + 2], v[8 * q + 3]) : pack_bf16x2(v[8 * q + 2], v[8 * q + 3]);
+                p.z = g.c16_f16 ? pack_f16x2(v[8 * q + 4], v[8 * q + 5]) : pack_bf16x2(v[8 * q + 4], v[8 * q + 5]);
+                p.w = g.c16_f16 ? pack_f16x2(v[8 * q + 6], v[8 * q + 7]) : pack_bf16x2(v[8 * q + 6], v[8 * q + 7]);
+                reinterpret_cast<uint4*>(hrow)[q] = p;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                if (j >= n16) break;
+                const uint32_t p = g.c16_f16 ? pack_f16x2(v[j], 0.f) : pack_bf16x2(v[j], 0.f);
+                hrow[j] = (uint16_t)(p & 0xffffu);
+            }
+        }
+    }
+}
+
+// Persistent, warp-specialised: two CTAs per SM walk the tiles (n fastest, then m, then
+// the K split) with stride gridDim.x.  Warp 0 (one lane) streams A and B boxes through
+// an ST-deep ring of shared stages; warp 1 (one lane) issues the MMAs of a tile into one
+// of two tensor-memory accumulators; warps 2-5 drain the other accumulator (the previous
+// tile) through the epilogue meanwhile, warp w reading lanes 32 (w mod 4) .. + 31.
 template <int BN, int ST, bool TWO>
-__global__ void __launch_bounds__(128) k_gemm_tc(const __grid_constant__ CUtensorMap map_a,
-                                                 const __grid_constant__ CUtensorMap map_b, TgArgs g) {
+__global__ void __launch_bounds__(192, 2) k_gemm_tc(const __grid_constant__ CUtensorMap map_a,
+                                                    const __grid_constant__ CUtensorMap map_b, TgArgs g,
+                                                    int tiles_m, int tiles_n, int splits) {
     using L = TgLayout<BN, ST, TWO>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t* full = (uint64_t*)(smem + L::OFF_BAR);
     uint64_t* empty = full + ST;
-    uint64_t* done = empty + ST;
+    uint64_t* acc_full = empty + ST;
+    uint64_t* acc_empty = acc_full + 2;
+    uint64_t* drain = acc_empty + 2;
     uint32_t* tmem_slot = (uint32_t*)(smem + L::OFF_MISC);
     volatile int* abort_flag = (volatile int*)(smem + L::OFF_MISC + 4);
     int* issued_s = (int*)(smem + L::OFF_MISC + 8);
     int* consumed_s = (int*)(smem + L::OFF_MISC + 12);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int m0 = blockIdx.x * TG_BM, n0 = blockIdx.y * BN;
-    const int kbeg = blockIdx.z * g.kchunk;
-    const int kend = min(g.Kp, kbeg + g.kchunk);
-    const int nk = kend > kbeg ? (kend - kbeg) / TG_BK : 0;
+    const int per_split = tiles_m * tiles_n, total = per_split * splits;
 
     if (tid == 0) {
         for (int s = 0; s < ST; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(done, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], 4);   // one arrival per epilogue warp
+        }
+        mbar_init(drain, 1);
         fence_mbar_init();
         *abort_flag = 0;
         *issued_s = 0;
@@ -101,124 +223,107 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const __grid_constant__ CUtenso
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    auto k_range = [&](int t, int& kbeg) {
+        kbeg = (t / per_split) * g.kchunk;
+        const int kend = min(g.Kp, kbeg + g.kchunk);
+        return kend > kbeg ? (kend - kbeg) / TG_BK : 0;
+    };
 
-    if (warp == 0 && lane == 0) {   // TMA producer
-        int i = 0;
-        for (; i < nk; ++i) {
-            const int s = i % ST;
-            if (i >= ST && !mbar_wait(&empty[s], ((i / ST) - 1) & 1, abort_flag, g.status, ST_TIMEOUT_GEMM,
-                                      g.wait_ns))
-                break;
-            uint8_t* sa = smem + s * L::STAGE;
-            mbar_arrive_expect_tx(&full[s], L::STAGE);
-            tma_load_2d(sa, &map_a, kbeg + i * TG_BK, m0, &full[s]);
-            tma_load_2d(sa + L::A_BYTES, &map_b, kbeg + i * TG_BK, n0, &full[s]);
-            if constexpr (TWO) tma_load_2d(sa + L::A_BYTES + L::B_BYTES, &map_b, g.Kp + kbeg + i * TG_BK, n0, &full[s]);
-        }
-        *issued_s = i;
-    } else if (warp == 1 && lane == 0) {   // MMA issuer
-        constexpr uint32_t idesc_bf = idesc_f16(TG_BM, BN, 1), idesc_h = idesc_f16(TG_BM, BN, 0);
-        const uint32_t idesc = g.f16 ? idesc_h : idesc_bf;
-        int i = 0;
-        for (; i < nk; ++i) {
-            const int s = i % ST;
-            if (!mbar_wait(&full[s], (i / ST) & 1, abort_flag, g.status, ST_TIMEOUT_GEMM, g.wait_ns)) break;
-            tc_fence_after();
-            const uint32_t sa = smem_u32(smem + s * L::STAGE), sb = sa + L::A_BYTES;
-#pragma unroll
-            for (int kk = 0; kk < TG_BK / 16; ++kk) {
-                mma_f16(tmem, sdesc_sw128(sa + kk * 32), sdesc_sw128(sb + kk * 32), idesc, (i | kk) != 0);
-                if constexpr (TWO) mma_f16(tmem, sdesc_sw128(sa + kk * 32), sdesc_sw128(sb + L::B_BYTES + kk * 32), idesc, 1);
+    if (warp == 0) {
+        if (lane == 0) {   // TMA producer
+            int it = 0;
+            bool go = true;
+            for (int t = blockIdx.x; t < total && go; t += gridDim.x) {
+                const int rem = t % per_split, m0 = (rem / tiles_n) * TG_BM, n0 = (rem % tiles_n) * BN;
+                int kbeg;
+                const int nk = k_range(t, kbeg);
+                for (int i = 0; i < nk; ++i, ++it) {
+                    const int s = it % ST;
+                    if (it >= ST && !mbar_wait(&empty[s], ((it / ST) - 1) & 1, abort_flag, g.status, ST_TIMEOUT_GEMM,
+                                               g.wait_ns)) {
+                        go = false;
+                        break;
+                    }
+                    uint8_t* sa = smem + s * L::STAGE;
+                    mbar_arrive_expect_tx(&full[s], L::STAGE);
+                    tma_load_2d(sa, &map_a, kbeg + i * TG_BK, m0, &full[s]);
+                    tma_load_2d(sa + L::A_BYTES, &map_b, kbeg + i * TG_BK, n0, &full[s]);
+                    if constexpr (TWO)
+                        tma_load_2d(sa + L::A_BYTES + L::B_BYTES, &map_b, g.Kp + kbeg + i * TG_BK, n0, &full[s]);
+                }
             }
-            mma_commit(&empty[s]);
+            *issued_s = it;
         }
-        *consumed_s = i;
-        mma_commit(done);   // arrives once every MMA issued above has completed
+    } else if (warp == 1) {
+        if (lane == 0) {   // MMA issuer
+            constexpr uint32_t idesc_bf = idesc_f16(TG_BM, BN, 1), idesc_h = idesc_f16(TG_BM, BN, 0);
+            const uint32_t idesc = g.f16 ? idesc_h : idesc_bf;
+            int it = 0, j = 0;
+            bool go = true;
+            for (int t = blockIdx.x; t < total && go; t += gridDim.x, ++j) {
+                const int b = j & 1;
+                int kbeg;
+                const int nk = k_range(t, kbeg);
+                if (j >= 2 && !mbar_wait(&acc_empty[b], ((j >> 1) - 1) & 1, abort_flag, g.status, ST_TIMEOUT_GEMM,
+                                         g.wait_ns))
+                    break;
+                tc_fence_after();
+                const uint32_t acc = tmem + b * BN;
+                for (int i = 0; i < nk; ++i, ++it) {
+                    const int s = it % ST;
+                    if (!mbar_wait(&full[s], (it / ST) & 1, abort_flag, g.status, ST_TIMEOUT_GEMM, g.wait_ns)) {
+                        go = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sa = smem_u32(smem + s * L::STAGE), sb = sa + L::A_BYTES;
+#pragma unroll
+                    for (int kk = 0; kk < TG_BK / 16; ++kk) {
+                        mma_f16(acc, sdesc_sw128(sa + kk * 32), sdesc_sw128(sb + kk * 32), idesc, (i | kk) != 0);
+                        if constexpr (TWO)
+                            mma_f16(acc, sdesc_sw128(sa + kk * 32), sdesc_sw128(sb + L::B_BYTES + kk * 32), idesc, 1);
+                    }
+                    mma_commit(&empty[s]);
+                }
+                if (go) mma_commit(&acc_full[b]);
+            }
+            *consumed_s = it;
+            mma_commit(drain);   // arrives once every MMA issued above has completed
+        }
+    } else {   // epilogue warps 2..5
+        const int q = warp & 3;
+        int j = 0;
+        for (int t = blockIdx.x; t < total; t += gridDim.x, ++j) {
+            const int b = j & 1;
+            const int split = t / per_split, rem = t % per_split;
+            const int m0 = (rem / tiles_n) * TG_BM, n0 = (rem % tiles_n) * BN;
+            int kbeg;
+            const int nk = k_range(t, kbeg);
+            const bool ok = mbar_wait(&acc_full[b], (j >> 1) & 1, abort_flag, g.status, ST_TIMEOUT_GEMM, g.wait_ns);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            tc_fence_after();
+            const int r = m0 + q * 32 + lane;
+#pragma unroll 1
+            for (int c = 0; c < BN / 32; ++c) {
+                float v[32];
+                __syncwarp();
+                tmem_ld32(tmem + b * BN + ((uint32_t)(q * 32) << 16) + c * 32, v);
+                tmem_wait_ld();
+                const int nb = n0 + c * 32;
+                if (r < g.M && nk > 0 && nb < max(g.N, g.c16_cols)) tg_store_chunk(g, v, r, nb, split == 0);
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[b]);
+        }
     }
     __syncwarp();
-    const bool ok = mbar_wait(done, 0, abort_flag, g.status, ST_TIMEOUT_GEMM, g.wait_ns) && nk > 0;
-    tc_fence_after();
-
-    // epilogue: warp w owns tensor-memory lanes (tile rows) 32 w .. 32 w + 31
-    const int r = m0 + warp * 32 + lane;
-    const bool row_ok = ok && r < g.M;
-    const bool lead = blockIdx.z == 0;
-#pragma unroll 1
-    for (int c = 0; c < BN / 32; ++c) {
-        if (!__any_sync(0xffffffffu, ok)) break;
-        float v[32];
-        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + c * 32, v);
-        tmem_wait_ld();
-        const int nb = n0 + c * 32;
-        if (!row_ok || nb >= max(g.N, g.c16_cols)) continue;
-        const int nn = max(0, min(32, g.N - nb));          // columns of the result
-        const int n16 = max(0, min(32, g.c16_cols - nb));   // columns of the 16-bit copy (zero beyond N)
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-            if (j >= nn) break;
-            float y = v[j];
-            if (lead && g.bias) y += g.bias[nb + j];
-            y = tg_act(y, g.act);
-            if (lead && g.R) y += g.R[(long)r * g.ldr + nb + j];
-            v[j] = y;
-        }
-#pragma unroll
-        for (int j = 0; j < 32; ++j)
-            if (j >= nn) v[j] = 0.f;
-        float* crow = g.C && nn > 0 ? g.C + (long)r * g.ldc + nb : nullptr;
-        if (crow) {
-            if (g.mode == 2) {
-#pragma unroll
-                for (int j = 0; j < 32; ++j)
-                    if (j < nn) atomicAdd(crow + j, v[j]);
-            } else if (nn == 32 && ((g.ldc | nb) & 3) == 0 && ((uintptr_t)g.C & 15) == 0) {
-                float4* c4 = (float4*)crow;
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    float4 o = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-                    if (g.mode == 1) {
-                        const float4 p = c4[q];
-                        o.x += p.x;
-                        o.y += p.y;
-                        o.z += p.z;
-                        o.w += p.w;
-                    }
-                    c4[q] = o;
-                }
-            } else {
-#pragma unroll
-                for (int j = 0; j < 32; ++j)
-                    if (j < nn) crow[j] = g.mode == 1 ? crow[j] + v[j] : v[j];
-            }
-        }
-        if (g.C16) {
-            uint16_t* hrow = g.C16 + (long)r * g.ldc16 + nb;
-            if (n16 == 32 && ((g.ldc16 | nb) & 7) == 0 && ((uintptr_t)g.C16 & 15) == 0) {
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    uint4 p;
-                    p.x = g.c16_f16 ? pack_f16x2(v[8 * q], v[8 * q + 1]) : pack_bf16x2(v[8 * q], v[8 * q + 1]);
-                    p.y = g.c16_f16 ? pack_f16x2(v[8 * q + 2], v[8 * q + 3]) : pack_bf16x2(v[8 * q + 2], v[8 * q + 3]);
-                    p.z = g.c16_f16 ? pack_f16x2(v[8 * q + 4], v[8 * q + 5]) : pack_bf16x2(v[8 * q + 4], v[8 * q + 5]);
-                    p.w = g.c16_f16 ? pack_f16x2(v[8 * q + 6], v[8 * q + 7]) : pack_bf16x2(v[8 * q + 6], v[8 * q + 7]);
-                    reinterpret_cast<uint4*>(hrow)[q] = p;
-                }
-            } else {
-#pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    if (j >= n16) break;
-                    const uint32_t p = g.c16_f16 ? pack_f16x2(v[j], 0.f) : pack_bf16x2(v[j], 0.f);
-                    hrow[j] = (uint16_t)(p & 0xffffu);
-                }
-            }
-        }
-    }
-    tc_fence_before();
     __syncthreads();
-    if (tid == 0 && *abort_flag) {
+    if (tid == 0) {
         // let what is still in flight land before shared and tensor memory are released
-        mbar_drain(done, 0, g.wait_ns);
-        for (int i = *consumed_s; i < *issued_s; ++i) mbar_drain(&full[i % ST], (i / ST) & 1, g.wait_ns);
+        mbar_drain(drain, 0, g.wait_ns);
+        if (*abort_flag)
+            for (int i = *consumed_s; i < *issued_s; ++i) mbar_drain(&full[i % ST], (i / ST) & 1, g.wait_ns);
     }
     __syncthreads();
     if (warp == 2) tmem_dealloc(tmem, L::TMEM_COLS);
@@ -320,11 +425,21 @@ bool tg_map(CUtensorMap* map, const void* base, long Kp, long rows, long ld, uin
 }
 
 template <int BN, int ST, bool TWO = false>
-void tg_launch(const CUtensorMap& ma, const CUtensorMap& mb, const TgArgs& a, int splits, cudaStream_t st) {
+void tg_launch(const CUtensorMap& ma, const CUtensorMap& mb, const TgArgs& a, int splits, int sms, cudaStream_t st) {
     using L = TgLayout<BN, ST, TWO>;
-    dim3 grid((a.M + TG_BM - 1) / TG_BM, (std::max(a.N, a.c16_cols) + BN - 1) / BN, splits);
-    k_gemm_tc<BN, ST, TWO><<<grid, 128, L::BYTES, st>>>(ma, mb, a);
+    const int tiles_m = (a.M + TG_BM - 1) / TG_BM, tiles_n = (std::max(a.N, a.c16_cols) + BN - 1) / BN;
+    const long total = (long)tiles_m * tiles_n * splits;
+    const int grid = (int)std::min<long>(total, sms);
+    k_gemm_tc<BN, ST, TWO><<<grid, 192, L::BYTES, st>>>(ma, mb, a, tiles_m, tiles_n, splits);
 }
+
+template <int BN, int ST, bool TWO>
+void tg_attr() {
+    cudaFuncSetAttribute(k_gemm_tc<BN, ST, TWO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         TgLayout<BN, ST, TWO>::BYTES);
+}
+
+int g_sms[64] = {};
 
 }  // namespace
 
@@ -333,15 +448,13 @@ void gemm_tc_prepare() {
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64 || done[dev]) return;
-    cudaFuncSetAttribute(k_gemm_tc<64, 4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, TgLayout<64, 4>::BYTES);
-    cudaFuncSetAttribute(k_gemm_tc<128, 3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         TgLayout<128, 3>::BYTES);
-    cudaFuncSetAttribute(k_gemm_tc<256, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         TgLayout<256, 2>::BYTES);
-    cudaFuncSetAttribute(k_gemm_tc<64, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         TgLayout<64, 3, true>::BYTES);
-    cudaFuncSetAttribute(k_gemm_tc<128, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         TgLayout<128, 2, true>::BYTES);
+    // stages of 24-48 KB filling about 192 KB of shared memory: one CTA per SM
+    tg_attr<64, 4, false>();
+    tg_attr<128, 3, false>();
+    tg_attr<64, 3, true>();
+    tg_attr<128, 2, true>();
+    cudaDeviceProp prop;
+    g_sms[dev] = cudaGetDeviceProperties(&prop, dev) == cudaSuccess ? prop.multiProcessorCount : 148;
     done[dev] = true;
 }
 
@@ -350,7 +463,7 @@ bool gemm_tc(int f16, const void* A, long lda, const void* B, long ldb, int M, i
              unsigned* status, uint64_t wait_ns, cudaStream_t st, int c16_f16, int two_term, int c16_cols) {
     if (M <= 0 || N <= 0 || Kp <= 0) return true;
     const int Nt = std::max(N, C16 ? c16_cols : 0);
-    const int BN = Nt <= 64 ? 64 : ((Nt <= 128 || two_term) ? 128 : 256);
+    const int BN = Nt <= 64 ? 64 : 128;
     CUtensorMap ma, mb;
     if (!tg_map(&ma, A, Kp, M, lda, TG_BM) || !tg_map(&mb, B, two_term ? 2L * Kp : Kp, N, ldb, BN)) return false;
     TgArgs a;
@@ -374,18 +487,20 @@ bool gemm_tc(int f16, const void* A, long lda, const void* B, long ldb, int M, i
     a.status = status;
     a.wait_ns = wait_ns;
     const int splits = (Kp + kchunk - 1) / kchunk;
-    // two to four stages of 24-48 KB: two CTAs (and 2 x BN tensor-memory columns) per SM
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int sms = (dev >= 0 && dev < 64 && g_sms[dev] > 0) ? g_sms[dev] : 148;
+    // stages of 24-48 KB filling about 96 KB of shared memory: two CTAs (each with two
+    // accumulators of BN <= 128 columns) per SM
     if (two_term) {
         if (BN == 64)
-            tg_launch<64, 3, true>(ma, mb, a, splits, st);
+            tg_launch<64, 3, true>(ma, mb, a, splits, 2 * sms, st);
         else
-            tg_launch<128, 2, true>(ma, mb, a, splits, st);
+            tg_launch<128, 2, true>(ma, mb, a, splits, 2 * sms, st);
     } else if (BN == 64)
-        tg_launch<64, 4>(ma, mb, a, splits, st);
-    else if (BN == 128)
-        tg_launch<128, 3>(ma, mb, a, splits, st);
+        tg_launch<64, 4>(ma, mb, a, splits, 2 * sms, st);
     else
-        tg_launch<256, 2>(ma, mb, a, splits, st);
+        tg_launch<128, 3>(ma, mb, a, splits, 2 * sms, st);
     return true;
 }
 
