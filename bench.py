@@ -32,7 +32,19 @@ WORKLOAD = "batch512"
 WORKLOAD_DESC = ("512 events, N ~ LogNormal(median 2500, sigma 0.5) clipped to [100, 12000], "
                  "42 features; model d=64, 4 heads x 16, FFN 256, 1 PID + 1 regression block")
 METRIC = "events/s & p50 ms/event, MLPF forward, BF16/FP8 vs FP32 plain at stated error"
-HEADS = 4
+# --model: the architecture run on the 512-event batch (weights seeded as in the tests).
+# small = the workload's own model (fused d=64 kernels); the others run the generic-width
+# tensor-core path: the full-size d=256 model (8 heads of 32, FFN 1024, 3 + 3), the
+# architecture as Sec. 5.3 prints it (d=256, 16 heads of 16, ReLU, 3 + 3) and the
+# distillation student (d=128, 4 heads of 32, FFN 512, 2 + 2).
+MODELS = {
+    "small": None,
+    "full": (synth.FULL, 1, "full-size model d=256, 8 heads x 32, FFN 1024, 3 PID + 3 regression blocks"),
+    "paper": (synth.PAPER, 4, "the architecture as printed: d=256, 16 heads x 16, FFN 1024, ReLU, per-type "
+                              "embedding, parallel 3 + 3 blocks, binary + PID heads"),
+    "student": (synth.ModelConfig(d=128, heads=4, ffn=512, l_pid=2, l_reg=2), 2,
+                "distillation student d=128, 4 heads x 32, FFN 512, 2 PID + 2 regression blocks"),
+}
 
 
 def parse():
@@ -60,7 +72,17 @@ def parse():
                          "rule on N^2)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="approximate CPU time budget of the oracle sample")
+    ap.add_argument("--model", default="small", choices=sorted(MODELS),
+                    help="architecture run on the batch (small: the workload's d=64 model)")
     return ap.parse_args()
+
+
+def model_of(name):
+    """(config, weight seed, description) of --model; small = the workload's own."""
+    if MODELS[name] is None:
+        cfg, wseed, _, _ = synth.workload(WORKLOAD)
+        return cfg, wseed, "model d=64, 4 heads x 16, FFN 256, 1 PID + 1 regression block"
+    return MODELS[name]
 
 
 def dist_setup():
@@ -215,12 +237,13 @@ def attention_traffic(variant, precision):
         return None
 
 
-def workload_inputs(rank, n_events=512, split="replicas", ws=1):
+def workload_inputs(rank, n_events=512, split="replicas", ws=1, model="small"):
     """The rank's events.  replicas (weak scaling): every rank its own batch of the
     same distribution.  lpt (strong scaling): one batch, its events split over the
     ranks by the library's cost-balanced LPT rule on N^2 (no exchange step: events are
     independent)."""
-    cfg, wseed, iseed, sizes = synth.workload(WORKLOAD)
+    _, _, iseed, sizes = synth.workload(WORKLOAD)
+    cfg, wseed, _ = model_of(model)
     if split == "replicas" and rank > 0:
         iseed = iseed + 1000 * rank
         sizes = synth.sizes_lognormal(iseed, len(sizes))
@@ -349,7 +372,7 @@ def run_reference(args):
     ws, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
     if rank != 0:
         return
-    cfg, wseed, x, cu, sizes = workload_inputs(0)
+    cfg, wseed, x, cu, sizes = workload_inputs(0, model=args.model)
     procs = os.cpu_count() or 1
     pool = oracle_pool(cfg, wseed, procs)
     n = len(sizes)
@@ -375,7 +398,7 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(x, sizes, 1),
+            "config": workload_config(x, sizes, 1, model=args.model),
             "cpu_baseline": {"value": v, "unit": "events/s", "cores": procs, "kind": "oracle",
                              "cpu_model": cpu_model(), "nproc": procs,
                              "sample": f"each step: {procs} consecutive events of the 512-event batch, "
@@ -386,13 +409,14 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def workload_config(x, sizes, ws, split="replicas"):
+def workload_config(x, sizes, ws, split="replicas", model="small"):
     """The `config` object of the JSON line (the same for both arms)."""
+    desc = WORKLOAD_DESC if model == "small" else WORKLOAD_DESC.split("; model")[0] + "; " + model_of(model)[2]
     if split == "lpt" and ws > 1:
-        return {"workload": f"{WORKLOAD}: {WORKLOAD_DESC}", "events_per_job": 512,
+        return {"workload": f"{WORKLOAD}: {desc}", "events_per_job": 512,
                 "l2": "inputs larger than L2", "parallelism":
                 f"one batch split over {ws} GPUs by LPT on N^2 (no collective on the data path)"}
-    return {"workload": f"{WORKLOAD}: {WORKLOAD_DESC}" +
+    return {"workload": f"{WORKLOAD}: {desc}" +
             ("" if len(sizes) == 512 else f" (first {len(sizes)} events only)"),
             "events_per_gpu": int(len(sizes)), "elements_per_gpu": int(np.sum(sizes)),
             "l2": "inputs larger than L2 (x is %.0f MB > 126 MB)" % (x.nbytes / 1e6),
@@ -405,7 +429,7 @@ def run_ours(args):
     pool = None
     if not args.no_baselines and rank == 0:
         # the oracle's worker pool, started before the first GPU call
-        cfg0, wseed0, _, _ = synth.workload(WORKLOAD)[:4]
+        cfg0, wseed0, _ = model_of(args.model)
         pool = oracle_pool(cfg0, wseed0, os.cpu_count() or 1)
     import torch
     from paper_2601_17554_b300 import Model, _lib
@@ -413,7 +437,7 @@ def run_ours(args):
     ws, rank, local = dist_setup()
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    cfg, wseed, x, cu, sizes = workload_inputs(rank, args.events, args.split, ws)
+    cfg, wseed, x, cu, sizes = workload_inputs(rank, args.events, args.split, ws, args.model)
     W = synth.make_weights(cfg, wseed)
     model = Model(synth.pack_blob(cfg, W), device=local)
     T, n_ev, max_n = x.shape[0], len(sizes), int(sizes.max())
@@ -505,9 +529,10 @@ def run_ours(args):
     d2h = T * 6 * 4 + T * 5 * 4 + T * 4 + n_ev * 3 * 8
 
     # ---- roofline of the dominant kernel (attention): exponentials per launch
-    att = kernel_ms.get("attention", [])
+    wide = "wide_attention" in kernel_ms
+    att = kernel_ms.get("wide_attention" if wide else "attention", [])
     att_ms = sum(att) / len(att) if att else None
-    exps = attention_pairs(sizes, args.attn_window) * HEADS
+    exps = attention_pairs(sizes, args.attn_window) * cfg.heads
     # peak: the MUFU exp2 rate measured on this device by the library's probe
     # kernel (independent chains on every SM), taken before the timed region
     roof = None
@@ -515,14 +540,16 @@ def run_ours(args):
         ach = exps / (att_ms / 1000.0)
         # the 16-bit attention kernels take their exponentials two at a time
         # (ex2.bf16x2 / ex2.f16x2): the MUFU bound is the packed rate
-        packed = prec in ("bf16", "fp16", "fp8")
+        packed = prec in ("bf16", "fp16", "fp8") and not wide
         exp_peak = unit_rates["ex2_bf16x2_per_s"] if packed else unit_rates["ex2_per_s"]
         kname = {3: "k_attention_warp", 4: "k_attention_warp", 5: "k_attention_warp (64-row items)",
                  6: "k_attention_warp (QK^T on tcgen05)",
                  7: "k_attention_warp (QK^T on tcgen05)"}.get(attn_variant, "k_attention_tm")
+        if wide:
+            kname = "k_attn_fwd16"
         roof = {"kernel": kname, "attn_variant": attn_variant, "bound": "alu", "achieved": ach / 1e9,
                 "peak": exp_peak / 1e9, "unit": "Gexp/s", "frac": ach / exp_peak,
-                "traffic": attention_traffic(attn_variant, prec),
+                "traffic": None if wide else attention_traffic(attn_variant, prec),
                 "peak_source": ("measured: mlpf_measure_ex2_packed_rate (ex2.approx.ftz.bf16x2, two results per "
                                 "instruction, results/s on this GPU, best of 3, timed alone)") if packed else
                                "measured: mlpf_measure_unit_rates (ex2.approx.f32 results/s on this GPU, best of 3, "
@@ -531,8 +558,11 @@ def run_ours(args):
                 "launch_ms": att_ms,
                 "algorithmic_exps_per_launch": exps,
                 "fp32_fma_peak_per_s": unit_rates["ffma_per_s"],
-                "mma_tflops": 4 * attention_pairs(sizes, args.attn_window) * 64 / (att_ms / 1000.0) / 1e12}
+                "launches_per_step": len(att) // max(1, args.steps),
+                "mma_tflops": cfg.heads * attention_pairs(sizes, args.attn_window) * 4 * (cfg.d // cfg.heads)
+                / (att_ms / 1000.0) / 1e12}
     kernel_avg = {k: sum(v) / len(v) for k, v in kernel_ms.items()}
+    kernel_step = {k: sum(v) / max(1, args.steps) for k, v in kernel_ms.items()}
     # ---- the GEMM-chain kernels against the dense tensor peak of their operand type
     gemm = None
     gemm_names = [k for k in ("embed_qkv", "post_qkv", "post_cls_head", "reg_embed_qkv", "post_reg_heads")
@@ -550,16 +580,30 @@ def run_ours(args):
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops (cuBLAS burst)" + (" x 2 for E4M3" if prec == "fp8" else ""),
                 "note": "fused per-tile GEMM chains (K = 64..256) with LayerNorm/GELU epilogues: latency-bound, "
                         "not tensor-bound"}
+    if prec != "fp32" and "wide_gemm" in kernel_ms:
+        g_ms = kernel_step["wide_gemm"]
+        g_flop = gemm_flops_per_element(cfg) * T
+        pk = measured_bf16_tflops()
+        gemm = {"kernels": ["k_gemm_tc (persistent, two-term FP16 weights)"], "flop_per_step": g_flop,
+                "ms_per_step": g_ms, "tflops": g_flop / (g_ms / 1000.0) / 1e12,
+                "issued_tflops": 2 * g_flop / (g_ms / 1000.0) / 1e12,
+                "peak_tflops": pk, "frac": (g_flop / (g_ms / 1000.0) / 1e12 / pk) if pk else None,
+                "issued_frac": (2 * g_flop / (g_ms / 1000.0) / 1e12 / pk) if pk else None,
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops (cuBLAS burst)",
+                "note": "every weight is carried as two FP16 terms (two MMAs per K step): 'tflops' counts "
+                        "the model's flops, 'issued_tflops' the tensor-core work"}
 
     line = {"metric": METRIC, "value": value, "unit": "events/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "strong" if (args.split == "lpt" and ws > 1) else "weak",
             "vs_baseline": None, "dtype": prec, "data": "synthetic",
-            "config": workload_config(x, sizes, ws, args.split),
+            "config": workload_config(x, sizes, ws, args.split, model=args.model),
             "attn_variant": attn_variant,
             "batch_ms_per_event": ms_step / n_ev,
             "gpu_launches": int(launches_per_step * args.steps),
             "kernel_ms": kernel_avg,
+            "kernel_ms_per_step": kernel_step,
+            "model": args.model,
             "roofline": roof,
             "gemm_tensor": gemm,
             "e2e": {"value": events_all / (e2e_ms / 1000.0), "unit": "events/s",

@@ -41,7 +41,7 @@ def test_reference_arm_json_line(capsys, monkeypatch):
     import argparse
     import json
     monkeypatch.setenv("RANK", "0")
-    args = argparse.Namespace(gpus=1, steps=1, warmup=0)
+    args = argparse.Namespace(gpus=1, steps=1, warmup=0, model="small")
     bench.run_reference(args)
     lines = [l for l in capsys.readouterr().out.splitlines() if l.startswith("{")]
     assert len(lines) == 1
