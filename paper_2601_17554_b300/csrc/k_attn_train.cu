@@ -362,35 +362,45 @@ __global__ void __launch_bounds__(256) k_attn_fwd16(const uint16_t* __restrict__
         }
         float s[8][4];
         scores<DH, F16>(qa, Kt(buf), s);
-        float mx[2] = {m[0], m[1]};
+        if (kb + 64 > kend) {   // the event's last keys: mask the tile's tail
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (kb + j * 8 + 2 * c + (u & 1) >= kend) s[j][u] = -INFINITY;
+        }
+        // raw (unscaled) row maxima of the tile; the running maxima m are in log2 units
+        float mr[2] = {-INFINITY, -INFINITY};
 #pragma unroll
         for (int j = 0; j < 8; ++j)
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                s[j][u] = kb + j * 8 + 2 * c + (u & 1) < kend ? s[j][u] * c2 : -INFINITY;
-                mx[u >> 1] = fmaxf(mx[u >> 1], s[j][u]);
-            }
+            for (int u = 0; u < 4; ++u) mr[u >> 1] = fmaxf(mr[u >> 1], s[j][u]);
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
-            mx[r] = fmaxf(mx[r], __shfl_xor_sync(0xffffffffu, mx[r], 1));
-            mx[r] = fmaxf(mx[r], __shfl_xor_sync(0xffffffffu, mx[r], 2));
+            mr[r] = fmaxf(mr[r], __shfl_xor_sync(0xffffffffu, mr[r], 1));
+            mr[r] = fmaxf(mr[r], __shfl_xor_sync(0xffffffffu, mr[r], 2));
         }
-        const float al[2] = {ex2_approx(m[0] - mx[0]), ex2_approx(m[1] - mx[1])};
-        l[0] *= al[0];
-        l[1] *= al[1];
+        const float mx0 = fmaxf(m[0], mr[0] * c2), mx1 = fmaxf(m[1], mr[1] * c2);
+        // rescale only when some row of the warp has a new maximum (otherwise the factors
+        // are exactly 1)
+        if (__any_sync(0xffffffffu, mx0 > m[0] || mx1 > m[1])) {
+            const float al[2] = {ex2_approx(m[0] - mx0), ex2_approx(m[1] - mx1)};
+            l[0] *= al[0];
+            l[1] *= al[1];
+#pragma unroll
+            for (int j = 0; j < DH / 8; ++j)
+#pragma unroll
+                for (int u = 0; u < 4; ++u) o[j][u] *= al[u >> 1];
+            m[0] = mx0;
+            m[1] = mx1;
+        }
 #pragma unroll
         for (int j = 0; j < 8; ++j)
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                s[j][u] = ex2_approx(s[j][u] - mx[u >> 1]);
+                s[j][u] = ex2_approx(fmaf(s[j][u], c2, -m[u >> 1]));
                 l[u >> 1] += s[j][u];
             }
-#pragma unroll
-        for (int j = 0; j < DH / 8; ++j)
-#pragma unroll
-            for (int u = 0; u < 4; ++u) o[j][u] *= al[u >> 1];
-        m[0] = mx[0];
-        m[1] = mx[1];
         accumulate<DH, F16>(s, Vt(buf), o);
         __syncthreads();   // every warp is done with this buffer before it is refilled
     }

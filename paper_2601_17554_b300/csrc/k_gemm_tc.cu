@@ -42,9 +42,21 @@ struct TgArgs {
     uint64_t wait_ns;
 };
 
+// GELU x Phi(x) with erf from Abramowitz & Stegun 7.1.26 (|error of erf| <= 1.5e-7):
+// erf(z) = 1 - (a1 t + a2 t^2 + a3 t^3 + a4 t^4 + a5 t^5) exp(-z^2), t = 1 / (1 + p z), z >= 0
+__device__ __forceinline__ float gelu_as(float v) {
+    const float z = fabsf(v) * 0.70710678118654752f;
+    const float t = __fdividef(1.f, fmaf(0.3275911f, z, 1.f));
+    const float poly =
+        t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f),
+                 0.254829592f);
+    const float erf_abs = fmaf(-poly, ex2_approx(-z * z * 1.4426950408889634f), 1.f);
+    return 0.5f * v * (1.f + copysignf(erf_abs, v));
+}
+
 __device__ __forceinline__ float tg_act(float v, int act) {
     if (act == 1) return fmaxf(v, 0.f);
-    if (act == 0) return 0.5f * v * (1.f + erff(v * 0.70710678118654752f));
+    if (act == 0) return gelu_as(v);
     return v;
 }
 
@@ -177,10 +189,11 @@ __device__ __forceinline__ void tg_store_chunk(const TgArgs& g, float* v, int r,
 // Persistent, warp-specialised: two CTAs per SM walk the tiles (n fastest, then m, then
 // the K split) with stride gridDim.x.  Warp 0 (one lane) streams A and B boxes through
 // an ST-deep ring of shared stages; warp 1 (one lane) issues the MMAs of a tile into one
-// of two tensor-memory accumulators; warps 2-5 drain the other accumulator (the previous
-// tile) through the epilogue meanwhile, warp w reading lanes 32 (w mod 4) .. + 31.
+// of two tensor-memory accumulators; warps 2-9 drain the other accumulator (the previous
+// tile) through the epilogue meanwhile, warp w reading lanes 32 (w mod 4) .. + 31 and every
+// other 32-column chunk (two warps per lane quarter).
 template <int BN, int ST, bool TWO>
-__global__ void __launch_bounds__(192, 2) k_gemm_tc(const __grid_constant__ CUtensorMap map_a,
+__global__ void __launch_bounds__(320, 2) k_gemm_tc(const __grid_constant__ CUtensorMap map_a,
                                                     const __grid_constant__ CUtensorMap map_b, TgArgs g,
                                                     int tiles_m, int tiles_n, int splits) {
     using L = TgLayout<BN, ST, TWO>;
@@ -205,7 +218,7 @@ __global__ void __launch_bounds__(192, 2) k_gemm_tc(const __grid_constant__ CUte
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&acc_full[b], 1);
-            mbar_init(&acc_empty[b], 4);   // one arrival per epilogue warp
+            mbar_init(&acc_empty[b], 8);   // one arrival per epilogue warp
         }
         mbar_init(drain, 1);
         fence_mbar_init();
@@ -290,8 +303,8 @@ __global__ void __launch_bounds__(192, 2) k_gemm_tc(const __grid_constant__ CUte
             *consumed_s = it;
             mma_commit(drain);   // arrives once every MMA issued above has completed
         }
-    } else {   // epilogue warps 2..5
-        const int q = warp & 3;
+    } else {   // epilogue warps 2..9: two per lane quarter, alternate 32-column chunks
+        const int q = warp & 3, half = (warp - 2) >> 2;
         int j = 0;
         for (int t = blockIdx.x; t < total; t += gridDim.x, ++j) {
             const int b = j & 1;
@@ -304,7 +317,7 @@ __global__ void __launch_bounds__(192, 2) k_gemm_tc(const __grid_constant__ CUte
             tc_fence_after();
             const int r = m0 + q * 32 + lane;
 #pragma unroll 1
-            for (int c = 0; c < BN / 32; ++c) {
+            for (int c = half; c < BN / 32; c += 2) {
                 float v[32];
                 __syncwarp();
                 tmem_ld32(tmem + b * BN + ((uint32_t)(q * 32) << 16) + c * 32, v);
@@ -430,7 +443,7 @@ void tg_launch(const CUtensorMap& ma, const CUtensorMap& mb, const TgArgs& a, in
     const int tiles_m = (a.M + TG_BM - 1) / TG_BM, tiles_n = (std::max(a.N, a.c16_cols) + BN - 1) / BN;
     const long total = (long)tiles_m * tiles_n * splits;
     const int grid = (int)std::min<long>(total, sms);
-    k_gemm_tc<BN, ST, TWO><<<grid, 192, L::BYTES, st>>>(ma, mb, a, tiles_m, tiles_n, splits);
+    k_gemm_tc<BN, ST, TWO><<<grid, 320, L::BYTES, st>>>(ma, mb, a, tiles_m, tiles_n, splits);
 }
 
 template <int BN, int ST, bool TWO>

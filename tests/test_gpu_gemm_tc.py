@@ -32,6 +32,7 @@ def check(A, B, K, C, *, bias=None, R=None, act=-1, C0=None, mode=0, ldc_pad=0):
     scale = (a.abs() @ b.abs().T)
     if bias is not None:
         ref = ref + bias.double().cpu()
+    pre = ref.abs()
     if act == 1:
         ref = ref.clamp_min(0.0)
     elif act == 0:
@@ -44,7 +45,9 @@ def check(A, B, K, C, *, bias=None, R=None, act=-1, C0=None, mode=0, ldc_pad=0):
     got = C[:, :N].double().cpu()
     tol = 2.0 ** -14 * scale + 4e-7 * ref.abs() + 1e-30
     if act == 0:
-        tol = tol + 2e-7   # erff in the epilogue
+        # GELU with the Abramowitz & Stegun 7.1.26 erf (|error| <= 1.5e-7): at most
+        # 0.75e-7 |x|, plus the FP32 reciprocal and exponential approximations inside it
+        tol = tol + 2e-7 + 2e-7 * pre
     err = (got - ref).abs()
     assert bool((err <= tol).all()), (float((err / tol).max()), err.argmax())
     if ldc_pad:
