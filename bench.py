@@ -419,7 +419,8 @@ def workload_config(x, sizes, ws, split="replicas", model="small"):
     return {"workload": f"{WORKLOAD}: {desc}" +
             ("" if len(sizes) == 512 else f" (first {len(sizes)} events only)"),
             "events_per_gpu": int(len(sizes)), "elements_per_gpu": int(np.sum(sizes)),
-            "l2": "inputs larger than L2 (x is %.0f MB > 126 MB)" % (x.nbytes / 1e6),
+            "l2": ("inputs larger than L2 (x is %.0f MB > 126 MB)" if x.nbytes > 126e6 else
+                   "inputs smaller than L2 (x is %.0f MB): a profiling slice, not a bench value") % (x.nbytes / 1e6),
             "parallelism": f"replicas x{ws} (events shard, no collective)"}
 
 
