@@ -291,7 +291,7 @@ def _oracle_event(args):
         lo, reg, cls, sums = r.logits, r.reg, r.cls, r.sums[0]
     else:
         lo, raw = oracle.forward_event(W, cfg, xs)
-        cls, reg = oracle.decode(xs, lo, raw)
+        cls, reg = oracle.decode(xs, lo, raw, arch=cfg.arch)
         sums = oracle.event_sums(cls, reg, [0, len(xs)])[0]
     return e, time.perf_counter() - t0, lo, reg, cls, sums
 
@@ -711,8 +711,15 @@ def run_ours(args):
         for e, olo, oreg, ocls, osum in samp:
             sl = slice(cu[e], cu[e + 1])
             agree.append(gcl[sl] == ocls)
-            s2 = np.sort(np.asarray(olo, np.float64), axis=1)
-            margins.append(s2[:, -1] - s2[:, -2])   # FP64 top-2 logit margin
+            olo64 = np.asarray(olo, np.float64)
+            if cfg.arch == 1:   # the decision's margin: binary logit, then the PID top-2
+                s2 = np.sort(olo64[:, 1:], axis=1)
+                pid = s2[:, -1] - s2[:, -2]
+                margins.append(np.where(olo64[:, 0] > 0, np.minimum(np.abs(olo64[:, 0]), pid),
+                                        np.abs(olo64[:, 0])))
+            else:
+                s2 = np.sort(olo64, axis=1)
+                margins.append(s2[:, -1] - s2[:, -2])   # FP64 top-2 logit margin
             num = num + ((grg[sl] - oreg) ** 2).sum(0)
             den = den + (oreg ** 2).sum(0)
             scale = max(np.abs(osum).max(), 1e-12)
