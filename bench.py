@@ -545,7 +545,8 @@ def run_ours(args):
         exp_peak = unit_rates["ex2_bf16x2_per_s"] if packed else unit_rates["ex2_per_s"]
         kname = {3: "k_attention_warp", 4: "k_attention_warp", 5: "k_attention_warp (64-row items)",
                  6: "k_attention_warp (QK^T on tcgen05)",
-                 7: "k_attention_warp (QK^T on tcgen05)"}.get(attn_variant, "k_attention_tm")
+                 7: "k_attention_warp (QK^T on tcgen05)", 8: "k_attention_pt (PV on tcgen05)",
+                 9: "k_attention_pt (PV on tcgen05)"}.get(attn_variant, "k_attention_tm")
         if wide:
             kname = "k_attn_fwd16"
         roof = {"kernel": kname, "attn_variant": attn_variant, "bound": "alu", "achieved": ach / 1e9,

@@ -439,7 +439,11 @@ enum {
                                        warp-level PV with QK^T on tcgen05 (S in two
                                        tensor-memory buffers per head, read in the
                                        warp-level accumulator layout):
-                                         6 = 4 stages, 7 = 8 stages */
+                                         6 = 4 stages, 7 = 8 stages;
+                                       warp-level QK^T with P written to tensor
+                                       memory and PV plus row sums on tcgen05 (O and
+                                       l in tensor memory), an MMA warp:
+                                         8 = 4 stages, 9 = 8 stages */
     MLPF_OPT_ATTN_VARIANT_FP16 = 8,
     MLPF_OPT_ATTN_VARIANT_FP8 = 9,
     MLPF_OPT_ATTN_WINDOW = 10,      /* 0 (default): full attention within each event.
@@ -468,7 +472,7 @@ enum {
                                        a chunk's last attention items overlap the next
                                        chunk's kernels.  The results do not depend on it. */
 };
-#define MLPF_ATTN_VARIANTS 8
+#define MLPF_ATTN_VARIANTS 10
 mlpf_status mlpf_set_option(mlpf_model* m, int32_t option, int64_t value);
 mlpf_status mlpf_get_option(const mlpf_model* m, int32_t option, int64_t* value);
 

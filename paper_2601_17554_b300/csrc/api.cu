@@ -937,7 +937,7 @@ mlpf_status mlpf_get_option(const mlpf_model* mm, int32_t option, int64_t* value
         case MLPF_OPT_DEBUG_STALL: *value = m.debug_stall; return MLPF_OK;
         case MLPF_OPT_ATTN_CTAS_PER_SM: *value = m.attn_ctas_per_sm; return MLPF_OK;
         case MLPF_OPT_ATTN_KV_STAGES: {
-            static const int stages[MLPF_ATTN_VARIANTS] = {4, 6, 8, 4, 8, 4, 4, 8};
+            static const int stages[MLPF_ATTN_VARIANTS] = {4, 6, 8, 4, 8, 4, 4, 8, 4, 8};
             *value = stages[m.attn_variant[0]];
             return MLPF_OK;
         }

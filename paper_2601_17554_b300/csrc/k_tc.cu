@@ -1165,10 +1165,87 @@ MLPF_DEV uint32_t exp2_pair(float x0, float x1) {
     return p;
 }
 
+// 2^x0, 2^x1 as two FP32 MUFU exponentials of the unrounded arguments, then packed
+// (rounded once) into the 16-bit operand format.
+template <bool F16>
+MLPF_DEV uint32_t exp2_pair_f32(float x0, float x1) {
+    return pack2<F16>(ex2_approx(x0), ex2_approx(x1));
+}
+
 MLPF_DEV bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* ab, unsigned* status,
                         uint64_t wait_ns) {
     const bool ok = mbar_wait(bar, parity, ab, status, ST_TIMEOUT_ATTN, wait_ns);
     return __all_sync(0xffffffffu, ok);
+}
+
+// The TMA producer of the warp-level attention kernels (one thread): takes work
+// items with the atomic ticket (a ticket is an item for QR = 128, or half of one for
+// QR = 64; halves without query rows are skipped), loads each item's Q tile into one
+// of two buffers and streams its 64-key K and V^T tiles with their per-head K-norm
+// bounds through ST stages.  info[qb] carries the item (x < 0: no more items) to the
+// consumers of Q buffer qb.  On an abort it lets the copies still in flight land.
+template <int ST, int QR>
+MLPF_DEV void attn_produce(const CUtensorMap* map_q, const CUtensorMap* map_k, const CUtensorMap* map_vt,
+                           const AttnParams& p, uint8_t* sQ, uint8_t* sK, uint8_t* sV, float* kn,
+                           uint64_t* q_full, uint64_t* q_empty, uint64_t* kv_full, uint64_t* kv_empty, int4* info,
+                           volatile int* ab, int n_items, int* ticket) {
+    constexpr uint32_t QB = QR * 128;
+    tma_prefetch_map(map_q);
+    tma_prefetch_map(map_k);
+    tma_prefetch_map(map_vt);
+    int q_it = 0, q_armed = 0;
+    uint32_t g = 0;
+    bool ok = true;
+    while (ok) {
+        const int t = atomicAdd(ticket, 1);
+        const int item = QR == 128 ? t : t >> 1, half = QR == 128 ? 0 : t & 1;
+        int4 it = make_int4(-1, 0, 0, 0);
+        if (item < n_items) {
+            it = p.items[item];
+            it.w = half;
+            if (it.z - it.y * ROWS - QR * half <= 0) continue;
+        }
+        const int qb = q_it & 1;
+        if (q_it >= 2 && !mbar_wait(&q_empty[qb], ((q_it >> 1) - 1) & 1, ab, p.status, ST_TIMEOUT_ATTN, p.wait_ns))
+            break;
+        if (item >= n_items) {
+            info[qb] = it;
+            mbar_arrive(&q_full[qb]);
+            break;
+        }
+        info[qb] = it;
+        mbar_arrive_expect_tx(&q_full[qb], QB);
+        tma_load_2d(sQ + qb * QB, map_q, 0, it.x + it.y * ROWS + QR * half, &q_full[qb]);
+        ++q_armed;
+        int kb, ke;
+        key_range(it.y, it.z, p.window, kb, ke);
+        const int nk = (ke - kb + 63) >> 6;
+        for (int j = 0; j < nk; ++j, ++g) {
+            const int s = (int)(g % ST);
+            if (g >= ST && !mbar_wait(&kv_empty[s], ((g / ST) - 1) & 1, ab, p.status, ST_TIMEOUT_ATTN, p.wait_ns)) {
+                ok = false;
+                break;
+            }
+            // the tile's K and V^T and its per-head K-norm bounds (a 64-row block:
+            // events start at 64-row boundaries, kb is a multiple of 128)
+            mbar_arrive_expect_tx(&kv_full[s], AT_KB + AT_VB + 16);
+            tma_load_2d(sK + s * AT_KB, map_k, 0, it.x + kb + 64 * j, &kv_full[s]);
+            tma_load_2d(sV + s * AT_VB, map_vt, it.x + kb + 64 * j, 0, &kv_full[s]);
+            bulk_load(kn + 4 * s, p.kmax + (size_t)(((it.x + kb) >> 6) + j) * 4, 16, &kv_full[s]);
+        }
+        ++q_it;
+    }
+    // on an abort, let the copies still in flight land before the CTA exits: wait
+    // (bounded) for the last armed phase of every stage and Q buffer
+    if (*ab) {
+        bool landed = true;
+        for (uint32_t t = g > ST ? g - ST : 0; t < g; ++t)
+            landed &= mbar_drain(&kv_full[t % ST], (t / ST) & 1, p.wait_ns);
+        for (int i = q_armed > 2 ? q_armed - 2 : 0; i < q_armed; ++i)
+            landed &= mbar_drain(&q_full[i & 1], (i >> 1) & 1, p.wait_ns);
+        if (!landed)   // a copy that never completes: a last, timed grace period
+            for (int i = 0; i < 1000; ++i) __nanosleep(1000);
+    }
 }
 
 // Attention with warp-level MMAs (m16n8k16).  With a head width of 16 the
@@ -1262,68 +1339,9 @@ __global__ void __launch_bounds__(aw_threads<QR, HY>(), QR == 128 ? 1 : 2)
 
     if (warp == NW) {
         // ------------------------------------------------ TMA producer (64-key stages)
-        if (lane == 0) {
-            tma_prefetch_map(&map_q);
-            tma_prefetch_map(&map_k);
-            tma_prefetch_map(&map_vt);
-            int q_it = 0, q_armed = 0;
-            uint32_t g = 0;
-            bool ok = true;
-            while (ok) {
-                // a ticket is an item (QR = 128) or half of one (QR = 64; halves
-                // without query rows are skipped)
-                const int t = atomicAdd(ticket, 1);
-                const int item = QR == 128 ? t : t >> 1, half = QR == 128 ? 0 : t & 1;
-                int4 it = make_int4(-1, 0, 0, 0);
-                if (item < n_items) {
-                    it = p.items[item];
-                    it.w = half;
-                    if (it.z - it.y * ROWS - QR * half <= 0) continue;
-                }
-                const int qb = q_it & 1;
-                if (q_it >= 2 &&
-                    !mbar_wait(&q_empty[qb], ((q_it >> 1) - 1) & 1, ab, p.status, ST_TIMEOUT_ATTN, p.wait_ns))
-                    break;
-                if (item >= n_items) {
-                    info[qb] = it;
-                    mbar_arrive(&q_full[qb]);
-                    break;
-                }
-                info[qb] = it;
-                mbar_arrive_expect_tx(&q_full[qb], QB);
-                tma_load_2d(sQ + qb * QB, &map_q, 0, it.x + it.y * ROWS + QR * half, &q_full[qb]);
-                ++q_armed;
-                int kb, ke;
-                key_range(it.y, it.z, p.window, kb, ke);
-                const int nk = (ke - kb + 63) >> 6;
-                for (int j = 0; j < nk; ++j, ++g) {
-                    const int s = (int)(g % ST);
-                    if (g >= ST &&
-                        !mbar_wait(&kv_empty[s], ((g / ST) - 1) & 1, ab, p.status, ST_TIMEOUT_ATTN, p.wait_ns)) {
-                        ok = false;
-                        break;
-                    }
-                    // the tile's K and V^T and its per-head K-norm bounds (a 64-row block:
-                    // events start at 64-row boundaries, kb is a multiple of 128)
-                    mbar_arrive_expect_tx(&kv_full[s], AT_KB + AT_VB + 16);
-                    tma_load_2d(sK + s * AT_KB, &map_k, 0, it.x + kb + 64 * j, &kv_full[s]);
-                    tma_load_2d(sV + s * AT_VB, &map_vt, it.x + kb + 64 * j, 0, &kv_full[s]);
-                    bulk_load(kn + 4 * s, p.kmax + (size_t)(((it.x + kb) >> 6) + j) * 4, 16, &kv_full[s]);
-                }
-                ++q_it;
-            }
-            // on an abort, let the copies still in flight land before the CTA exits:
-            // wait (bounded) for the last armed phase of every stage and Q buffer
-            if (*ab) {
-                bool landed = true;
-                for (uint32_t t = g > ST ? g - ST : 0; t < g; ++t)
-                    landed &= mbar_drain(&kv_full[t % ST], (t / ST) & 1, p.wait_ns);
-                for (int i = q_armed > 2 ? q_armed - 2 : 0; i < q_armed; ++i)
-                    landed &= mbar_drain(&q_full[i & 1], (i >> 1) & 1, p.wait_ns);
-                if (!landed)   // a copy that never completes: a last, timed grace period
-                    for (int i = 0; i < 1000; ++i) __nanosleep(1000);
-            }
-        }
+        if (lane == 0)
+            attn_produce<ST, QR>(&map_q, &map_k, &map_vt, p, sQ, sK, sV, kn, q_full, q_empty, kv_full, kv_empty,
+                                 info, ab, n_items, ticket);
     } else if (HY && warp == NW + 1) {
         // ------------------------------------------------ HY: QK^T issue (one thread)
         if (lane == 0) {
@@ -1712,6 +1730,451 @@ __global__ void __launch_bounds__(aw_threads<QR, HY>(), QR == 128 ? 1 : 2)
     tc_fence_before();
     __syncthreads();
     if (HY && warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tbase, 512);
+    }
+}
+
+// ------------------------------------ attention, warp-level QK^T, PV on tcgen05
+// The warp-level kernel with the PV product and the row sums moved to the tensor
+// cores.  Each consumer warp still owns 32 query rows of one head and computes
+// S - ref with m16n8k16 MMAs (Q pre-scaled, the negated references as the
+// accumulator input) and the packed exponentials, but writes P (16-bit pairs) into
+// tensor memory with tcgen05.st.16x128b, whose thread layout is the MMA's A-fragment
+// layout.  One MMA warp then accumulates O_h += P_h V_h and l_h += P_h 1 per head and
+// 64-key tile (tcgen05, P as the tensor-memory A operand, M 128, N 16, K 64), so the
+// legacy tensor pipe carries only the four QK^T MMAs of the ten per warp and 16-key
+// step.  One MMA warp per head, so that a head's MMAs never wait for another head's
+// warps.  P has three buffers per head (the warps write tile t while the MMAs of
+// tiles t - 1 and t - 2 may still run); O and l stay in tensor memory for the whole
+// item and are read once, at its end.  Tensor memory: P 4 heads x 3 buffers x 32
+// columns, [O_h | l_h] 4 x 32 columns: all 512.
+// Rescaling: one exponent reference per row for the whole tile, since the tile's P
+// is summed by one MMA.  The bound path (|q| max |k| <= ref + kLimit for every row
+// of the warp) runs the four steps straight through as in the warp-level kernel.
+// Otherwise (the first tile of an item, a ragged last tile, a failed bound) the
+// tile's row maxima are computed first (QK^T of every step, recomputed for the
+// exponentials); the first tile sets the references, a later one raises a row's
+// reference only when the row maximum exceeds it by more than kStaleMax, and then
+// rescales the row's O and l in tensor memory once the previous tile's MMA is
+// complete.  Steps wholly past the end of the event store P = 0.
+constexpr int PT_NB = 3;                              // P buffers per head
+constexpr int PT_ATT_THREADS = NH * 4 * 32 + 32 + NH * 32;   // 16 consumer warps, TMA warp, 4 MMA warps
+template <int ST>
+struct PtLayout {
+    static constexpr uint32_t OFF_K = 2 * AT_QB;
+    static constexpr uint32_t OFF_V = OFF_K + ST * AT_KB;
+    static constexpr uint32_t OFF_ONES = OFF_V + ST * AT_VB;   // 16 rows of ones (row-sum B operand)
+    static constexpr uint32_t OFF_BAR = OFF_ONES + 2048;      // barriers, item info, flags (< 512 B)
+    static constexpr uint32_t OFF_KN = OFF_BAR + 512;         // [ST][4] key-tile norm bounds
+    static constexpr uint32_t SMEM = OFF_KN + 8 * 16 + 1024;
+};
+// the item info (two int4) after the barriers, at a 16-byte aligned offset
+constexpr uint32_t PT_INFO_OFF = 448;
+static_assert((2 + 2 + 8 + 8 + 1 + 2 * NH * PT_NB + NH) * 8 <= PT_INFO_OFF, "PV-on-tcgen05 attention barriers");
+static_assert(PT_INFO_OFF % 16 == 0 && PT_INFO_OFF + 2 * 16 + 8 <= 512, "PV-on-tcgen05 attention info area");
+
+template <bool F16, int ST, bool XF = false>
+__global__ void __launch_bounds__(PT_ATT_THREADS, 1)
+    k_attention_pt(const __grid_constant__ CUtensorMap map_q, const __grid_constant__ CUtensorMap map_k,
+                   const __grid_constant__ CUtensorMap map_vt, AttnParams p) {
+    constexpr int RB = 4;          // 32-row blocks (one per warp) per 128-row item
+    constexpr int NW = NH * RB;    // consumer warps
+    using LY = PtLayout<ST>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* sm = align1024(smem_raw);
+    uint8_t* sQ = sm;
+    uint8_t* sK = sm + LY::OFF_K;
+    uint8_t* sV = sm + LY::OFF_V;
+    uint8_t* sOnes = sm + LY::OFF_ONES;
+    uint64_t* bars = (uint64_t*)(sm + LY::OFF_BAR);
+    uint64_t* q_full = bars;            // [2]
+    uint64_t* q_empty = bars + 2;       // [2]: one arrival per consumer warp and per MMA warp
+    uint64_t* kv_full = bars + 4;       // [ST]
+    uint64_t* kv_empty = kv_full + ST;  // [ST]: one arrival per consumer warp, one commit per MMA warp
+    uint64_t* never = kv_empty + ST;    // armed by nobody (debug stall)
+    uint64_t* p_full = never + 1;             // [head][buffer]: one arrival per warp of the head
+    uint64_t* p_free = p_full + NH * PT_NB;   // [head][buffer]: MMA commit, the tile's PV and row sums done
+    uint64_t* drain = p_free + NH * PT_NB;    // [head]: the MMA warp's exit
+    int4* info = (int4*)(sm + LY::OFF_BAR + PT_INFO_OFF);   // [2], 16-byte aligned
+    int* abort_flag = (int*)(info + 2);
+    uint32_t* tmem_hold = (uint32_t*)(abort_flag + 1);
+    float* kn = (float*)(sm + LY::OFF_KN);
+    volatile int* ab = abort_flag;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    if (tid == 0) {
+        for (int i = 0; i < 2; ++i) { mbar_init(&q_full[i], 1); mbar_init(&q_empty[i], NW + NH); }
+        for (int i = 0; i < ST; ++i) { mbar_init(&kv_full[i], 1); mbar_init(&kv_empty[i], NW + NH); }
+        mbar_init(never, 1);
+        for (int i = 0; i < NH * PT_NB; ++i) { mbar_init(&p_full[i], RB); mbar_init(&p_free[i], 1); }
+        for (int i = 0; i < NH; ++i) mbar_init(&drain[i], 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    {   // the B operand of the row sums: 16 rows x 64 keys of ones
+        const uint32_t one2 = F16 ? 0x3C003C00u : 0x3F803F80u;
+        for (int i = tid; i < 512; i += PT_ATT_THREADS) ((uint32_t*)sOnes)[i] = one2;
+        fence_proxy_async_smem();
+    }
+    if (warp == 0) {
+        tmem_alloc(tmem_hold, 512);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = *tmem_hold;
+    const int n_items = p.counters[0];
+    int* ticket = p.counters + 2 + p.layer;
+    // tensor-memory columns: P of head h, buffer b; O_h (16 columns) and l_h (16)
+    auto colP = [](int h, uint32_t b) { return (uint32_t)(h * 32 * PT_NB) + b * 32u; };
+    auto colO = [](int h) { return (uint32_t)(NH * 32 * PT_NB) + (uint32_t)(h * 32); };
+    // tile t uses P buffer t % PT_NB; the k-th completion of a buffer's barriers is
+    // its k-th tile, so the phase parity of tile t is (t / PT_NB) & 1
+    auto pbuf = [](uint32_t t) { return t % PT_NB; };
+    auto ppar = [](uint32_t t) { return (t / PT_NB) & 1u; };
+
+    if (warp == NW) {
+        // ------------------------------------------------ TMA producer (64-key stages)
+        if (lane == 0)
+            attn_produce<ST, 128>(&map_q, &map_k, &map_vt, p, sQ, sK, sV, kn, q_full, q_empty, kv_full, kv_empty,
+                                  info, ab, n_items, ticket);
+    } else if (warp > NW) {
+        // ------------------------------------------------ PV and row-sum MMAs of head h (one thread)
+        const int h = warp - NW - 1;
+        if (lane == 0) {
+            const uint32_t IPV = idesc_f16(128, 16, F16 ? 0u : 1u);
+            const uint32_t onesa = smem_u32(sOnes);
+            int q_it = 0;
+            uint32_t g = 0;
+            bool ok = true;
+            while (ok) {
+                const int qb = q_it & 1;
+                if (!mbar_wait(&q_full[qb], (q_it >> 1) & 1, ab, p.status, ST_TIMEOUT_ATTN, p.wait_ns)) break;
+                const int4 it = info[qb];
+                mbar_arrive(&q_empty[qb]);   // info read (the MMAs do not read Q)
+                if (it.x < 0) break;
+                int kb, ke;
+                key_range(it.y, it.z, p.window, kb, ke);
+                const int nk = (ke - kb + 63) >> 6;
+                for (int j = 0; j < nk && ok; ++j) {
+                    const uint32_t t = g + j, s = t % ST, b = pbuf(t);
+                    if (!mbar_wait(&kv_full[s], (t / ST) & 1, ab, p.status, ST_TIMEOUT_ATTN, p.wait_ns) ||
+                        !mbar_wait(&p_full[PT_NB * h + b], ppar(t), ab, p.status, ST_TIMEOUT_ATTN, p.wait_ns)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t va = smem_u32(sV + s * AT_VB);
+                    const uint32_t pa = tbase + colP(h, b), od = tbase + colO(h);
+#pragma unroll
+                    for (int kc = 0; kc < 4; ++kc) {
+                        const uint32_t acc = (j > 0 || kc > 0) ? 1u : 0u;
+                        mma_f16_ts(od, pa + 8 * kc, sdesc_sw128(va + h * 2048 + kc * 32), IPV, acc);
+                        mma_f16_ts(od + 16, pa + 8 * kc, sdesc_sw128(onesa + kc * 32), IPV, acc);
+                    }
+                    mma_commit(&p_free[PT_NB * h + b]);
+                    mma_commit(&kv_empty[s]);
+                }
+                if (!ok) break;
+                g += nk;
+                ++q_it;
+            }
+            // every MMA issued complete before tensor memory and shared memory are released
+            mma_commit(&drain[h]);
+            mbar_drain(&drain[h], 0, p.wait_ns);
+        }
+    } else {
+        // ------------------------------------------------ warp: head h, query rows 32 rb .. 32 rb + 31
+        const int h = warp / RB, rb = warp % RB;
+        const int gq = lane >> 2, tq = lane & 3;
+        const int mi = lane >> 3;
+        const uint32_t sQa = smem_u32(sQ), sKa = smem_u32(sK);
+        const int k_row = (lane & 7) + 8 * (mi >> 1), k_chunk = 2 * h + (mi & 1);
+        const uint32_t koff = sw128_off(k_row, k_chunk);
+        const uint32_t tlane = tbase + ((uint32_t)(32 * rb) << 16);   // this warp's lanes
+        int q_it = 0;
+        uint32_t g = 0;
+        bool ok = true;
+        while (ok) {
+            const int qb = q_it & 1;
+            if (!warp_wait(&q_full[qb], (q_it >> 1) & 1, ab, p.status, p.wait_ns)) break;
+            const int4 it = info[qb];
+            if (it.x < 0) break;
+            if (p.debug_stall && !warp_wait(never, 0, ab, p.status, p.wait_ns)) break;
+            int kb, ke;
+            key_range(it.y, it.z, p.window, kb, ke);
+            const int nk = (ke - kb + 63) >> 6;
+            const uint32_t qfa = sQa + qb * AT_QB + sw128_off(rb * 32 + (lane & 15), 2 * h + (lane >> 4));
+            uint32_t qa[2][4];
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) ldsm_x4(qfa + 2048u * mt, qa[mt][0], qa[mt][1], qa[mt][2], qa[mt][3]);
+            float qn[2][2];
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                for (int hr = 0; hr < 2; ++hr) {
+                    float a0, a1, a2, a3;
+                    unpack2<F16>(qa[mt][hr], a0, a1);
+                    unpack2<F16>(qa[mt][2 + hr], a2, a3);
+                    float t = fmaf(a0, a0, fmaf(a1, a1, fmaf(a2, a2, a3 * a3)));
+                    t += __shfl_xor_sync(0xffffffffu, t, 1);
+                    t += __shfl_xor_sync(0xffffffffu, t, 2);
+                    qn[mt][hr] = sqrtf(t) * 1.01f;
+                }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&q_empty[qb]);
+            // nr: the negated exponent references of the fragment's rows, as the QK^T
+            // MMA's accumulator input (its output is the exponent S - ref itself)
+            float nr[2][4];
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) nr[mt][e] = 0.f;
+            // K fragments of step q (keys 16 q .. 16 q + 15) and S - ref from them
+            auto kfrag = [&](uint32_t kbase, int q, uint32_t (&kf)[4]) {
+                ldsm_x4(kbase + koff + 2048u * q, kf[0], kf[1], kf[2], kf[3]);
+            };
+            auto qk_f = [&](const uint32_t (&kf)[4], float (&dst)[2][2][4]) {
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                    for (int nt = 0; nt < 2; ++nt) mma16816_c<F16>(dst[mt][nt], qa[mt], kf[2 * nt], kf[2 * nt + 1], nr[mt]);
+            };
+            auto qk = [&](uint32_t kbase, int q, float (&dst)[2][2][4]) {
+                uint32_t kf[4];
+                kfrag(kbase, q, kf);
+                qk_f(kf, dst);
+            };
+            // P of step q into the columns pcol + 8 q .. + 7 (buffer of the tile), lanes
+            // of the two 16-row blocks
+            auto store_p = [&](uint32_t pcol, int q, const float (&sc)[2][2][4]) {
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt) {
+                    uint32_t pa[4];
+#pragma unroll
+                    for (int hr = 0; hr < 2; ++hr) {
+                        if constexpr (XF) {
+                            pa[hr] = exp2_pair_f32<F16>(sc[mt][0][2 * hr], sc[mt][0][2 * hr + 1]);
+                            pa[2 + hr] = exp2_pair_f32<F16>(sc[mt][1][2 * hr], sc[mt][1][2 * hr + 1]);
+                        } else {
+                            pa[hr] = exp2_pair<F16>(sc[mt][0][2 * hr], sc[mt][0][2 * hr + 1]);
+                            pa[2 + hr] = exp2_pair<F16>(sc[mt][1][2 * hr], sc[mt][1][2 * hr + 1]);
+                        }
+                    }
+                    tmem_st16x128b_x2(pcol + ((uint32_t)(16 * mt) << 16) + 8 * q, pa);
+                }
+            };
+            // the buffer of tile t may be written once the MMAs of tile t - PT_NB are complete
+            auto p_acquire = [&](uint32_t t) {
+                if (t < PT_NB) return true;
+                const bool r = warp_wait(&p_free[PT_NB * h + pbuf(t)], ppar(t - PT_NB), ab, p.status, p.wait_ns);
+                tc_fence_after();
+                return r;
+            };
+            auto p_publish = [&](uint32_t t) {
+                tmem_wait_st();
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&p_full[PT_NB * h + pbuf(t)]);
+            };
+            // the four steps of a full tile on the bound path: the K fragments of every
+            // step first (the loads stay ahead of the tensor-memory stores)
+            auto fast_tile = [&](uint32_t kbase, uint32_t t) {
+                uint32_t kf[4][4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) kfrag(kbase, q, kf[q]);
+                const uint32_t pcol = tlane + colP(h, pbuf(t));
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    float sc[2][2][4];
+                    qk_f(kf[q], sc);
+                    store_p(pcol, q, sc);
+                }
+            };
+            for (int j = 0; j < nk; ++j, ++g) {
+                // two full tiles on the bound path with one check and one branch
+                if (j > 0 && j + 1 < nk && ke - kb - 64 * (j + 1) >= 64) {
+                    const uint32_t s0 = g % ST, s1 = (g + 1) % ST;
+                    if (!warp_wait(&kv_full[s0], (g / ST) & 1, ab, p.status, p.wait_ns)) { ok = false; break; }
+                    if (!warp_wait(&kv_full[s1], ((g + 1) / ST) & 1, ab, p.status, p.wait_ns)) { ok = false; break; }
+                    const float km = fmaxf(kn[s0 * 4 + h], kn[s1 * 4 + h]);
+                    bool over = false;
+#pragma unroll
+                    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                        for (int hr = 0; hr < 2; ++hr) over |= fmaf(qn[mt][hr], km, nr[mt][2 * hr]) > kLimit<F16>;
+                    if (!__any_sync(0xffffffffu, over)) {
+                        if (!p_acquire(g)) { ok = false; break; }
+                        fast_tile(sKa + s0 * AT_KB, g);
+                        p_publish(g);
+                        if (!p_acquire(g + 1)) { ok = false; break; }
+                        fast_tile(sKa + s1 * AT_KB, g + 1);
+                        p_publish(g + 1);
+                        __syncwarp();
+                        if (lane == 0) {
+                            mbar_arrive(&kv_empty[s0]);
+                            mbar_arrive(&kv_empty[s1]);
+                        }
+                        ++j;
+                        ++g;
+                        continue;
+                    }
+                }
+                const uint32_t s = g % ST;
+                if (!warp_wait(&kv_full[s], (g / ST) & 1, ab, p.status, p.wait_ns)) { ok = false; break; }
+                const int kvalid = ke - kb - 64 * j;
+                const uint32_t kbs = sKa + s * AT_KB;
+                bool fast = false;
+                if (j > 0 && kvalid >= 64) {
+                    const float km = kn[s * 4 + h];
+                    bool over = false;
+#pragma unroll
+                    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                        for (int hr = 0; hr < 2; ++hr) over |= fmaf(qn[mt][hr], km, nr[mt][2 * hr]) > kLimit<F16>;
+                    fast = !__any_sync(0xffffffffu, over);
+                }
+                if (!p_acquire(g)) { ok = false; break; }
+                if (fast) {
+                    fast_tile(kbs, g);
+                } else {
+                    // the tile's row maxima (S - ref over its valid keys)
+                    auto mask = [&](int q, float (&sc)[2][2][4]) {
+                        if (16 * (q + 1) > kvalid) {
+#pragma unroll
+                            for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                                for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+                                    for (int e = 0; e < 4; ++e)
+                                        if (16 * q + 8 * nt + 2 * tq + (e & 1) >= kvalid) sc[mt][nt][e] = -INFINITY;
+                        }
+                    };
+                    float lm[2][2];
+#pragma unroll
+                    for (int mt = 0; mt < 2; ++mt) lm[mt][0] = lm[mt][1] = -INFINITY;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        if (16 * q >= kvalid) break;   // warp-uniform
+                        float sc[2][2][4];
+                        qk(kbs, q, sc);
+                        mask(q, sc);
+#pragma unroll
+                        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                            for (int hr = 0; hr < 2; ++hr)
+                                lm[mt][hr] = fmaxf(lm[mt][hr], max3f(fmaxf(sc[mt][0][2 * hr], sc[mt][0][2 * hr + 1]),
+                                                                     sc[mt][1][2 * hr], sc[mt][1][2 * hr + 1]));
+                    }
+                    const bool first = j == 0;
+                    bool raise = first;
+#pragma unroll
+                    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                        for (int hr = 0; hr < 2; ++hr) {
+                            float mx = lm[mt][hr];
+                            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+                            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+                            lm[mt][hr] = mx;
+                            raise |= mx > kStaleMax;
+                        }
+                    if (__any_sync(0xffffffffu, raise)) {
+                        // raise each row's reference by dr (the first tile: to its maximum;
+                        // later: only upwards); a later tile rescales the row's O and l
+                        float a[2][2];
+#pragma unroll
+                        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                            for (int hr = 0; hr < 2; ++hr) {
+                                const float dr = first ? lm[mt][hr] : fmaxf(lm[mt][hr], 0.f);
+                                a[mt][hr] = first ? 1.f : ex2_approx(-dr);
+                                nr[mt][2 * hr] -= dr;
+                                nr[mt][2 * hr + 1] -= dr;
+                            }
+                        if (!first) {
+                            // O and l of tile t - 1 complete, then row (lane) of this warp scaled
+                            if (!warp_wait(&p_free[PT_NB * h + pbuf(g - 1)], ppar(g - 1), ab, p.status, p.wait_ns)) {
+                                ok = false;
+                                break;
+                            }
+                            tc_fence_after();
+                            // the factor of row `lane` (16-row block lane / 16, half (lane / 8) & 1,
+                            // fragment row lane & 7) is held by fragment lane 4 (lane & 7)
+                            const int src = 4 * (lane & 7);
+                            const float f00 = __shfl_sync(0xffffffffu, a[0][0], src);
+                            const float f01 = __shfl_sync(0xffffffffu, a[0][1], src);
+                            const float f10 = __shfl_sync(0xffffffffu, a[1][0], src);
+                            const float f11 = __shfl_sync(0xffffffffu, a[1][1], src);
+                            const float f = lane < 16 ? (lane < 8 ? f00 : f01) : (lane < 24 ? f10 : f11);
+                            float ol[32];
+                            tmem_ld32(tlane + colO(h), ol);
+                            tmem_wait_ld();
+                            uint32_t u[32];
+#pragma unroll
+                            for (int i = 0; i < 32; ++i) u[i] = __float_as_uint(ol[i] * f);
+                            tmem_st32(tlane + colO(h), u);
+                        }
+                    }
+                    // the exponentials with the tile's references; steps past the end of
+                    // the event store P = 0
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        float sc[2][2][4];
+                        if (16 * q < kvalid) {
+                            qk(kbs, q, sc);
+                            mask(q, sc);
+                        } else {
+#pragma unroll
+                            for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                                for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+                                    for (int e = 0; e < 4; ++e) sc[mt][nt][e] = -INFINITY;
+                        }
+                        store_p(tlane + colP(h, pbuf(g)), q, sc);
+                    }
+                }
+                p_publish(g);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&kv_empty[s]);
+            }
+            if (!ok) break;
+            // the item's output: O / l of row (lane) of this warp, head h
+            const uint32_t tlast = g - 1;
+            if (!warp_wait(&p_free[PT_NB * h + pbuf(tlast)], ppar(tlast), ab, p.status, p.wait_ns)) break;
+            tc_fence_after();
+            float ol[32];
+            tmem_ld32(tlane + colO(h), ol);
+            tmem_wait_ld();
+            const int r = rb * 32 + lane;
+            const int qrow0 = it.x + it.y * ROWS;
+            // the event's padding rows (up to its next 64-row boundary) get O = 0, so
+            // that every value the next kernels read is written by this forward
+            if (r < min(ROWS, ((it.z + 63) & ~63) - it.y * ROWS)) {
+                const float inv = 1.0f / ol[16];
+                uint4 u0, u1;
+                u0.x = pack_f16x2(ol[0] * inv, ol[1] * inv);
+                u0.y = pack_f16x2(ol[2] * inv, ol[3] * inv);
+                u0.z = pack_f16x2(ol[4] * inv, ol[5] * inv);
+                u0.w = pack_f16x2(ol[6] * inv, ol[7] * inv);
+                u1.x = pack_f16x2(ol[8] * inv, ol[9] * inv);
+                u1.y = pack_f16x2(ol[10] * inv, ol[11] * inv);
+                u1.z = pack_f16x2(ol[12] * inv, ol[13] * inv);
+                u1.w = pack_f16x2(ol[14] * inv, ol[15] * inv);
+                uint4* dst = (uint4*)(p.out + (size_t)(qrow0 + r) * D + h * 16);
+                const bool val = r < it.z - it.y * ROWS;
+                dst[0] = val ? u0 : make_uint4(0, 0, 0, 0);
+                dst[1] = val ? u1 : make_uint4(0, 0, 0, 0);
+            }
+            ++q_it;
+        }
+        tmem_wait_st();
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
         tc_fence_after();
         tmem_dealloc(tbase, 512);
     }
@@ -2194,7 +2657,15 @@ std::string check_occupancy() {
         occupancy(k_attention_warp<kOutF16<FMT>, 8>, aw_threads<128>(), AwLayout<8>::SMEM),
         occupancy(k_attention_warp<kOutF16<FMT>, 4, 64>, aw_threads<64>(), AwLayout<4, 64>::SMEM) / 2,
         occupancy(k_attention_warp<kOutF16<FMT>, 4, 128, true>, aw_threads<128, true>(), AwLayout<4>::SMEM),
-        occupancy(k_attention_warp<kOutF16<FMT>, 8, 128, true>, aw_threads<128, true>(), AwLayout<8>::SMEM)};
+        occupancy(k_attention_warp<kOutF16<FMT>, 8, 128, true>, aw_threads<128, true>(), AwLayout<8>::SMEM),
+        occupancy(k_attention_pt<kOutF16<FMT>, 4>, PT_ATT_THREADS, PtLayout<4>::SMEM),
+        occupancy(k_attention_pt<kOutF16<FMT>, 8>, PT_ATT_THREADS, PtLayout<8>::SMEM)};
+    // the kernels that hold all 512 tensor-memory columns must not share an SM
+    const int o_tm[] = {o_att[0], o_att[1], o_att[2], o_att[6], o_att[7], o_att[8], o_att[9]};
+    for (int v : o_tm)
+        if (v != 1)
+            return "format " + std::to_string(FMT) + ": a tensor-memory attention kernel fits " + std::to_string(v) +
+                   " CTAs per SM; ";
     const int o[6] = {*std::min_element(o_att, o_att + MLPF_ATTN_VARIANTS),
                       occupancy(k_post<0, FMT>, PT_THREADS, post_smem(0, FMT)),
                       occupancy(k_post<1, FMT>, PT_THREADS, post_smem(1, FMT)),
@@ -2223,6 +2694,8 @@ void set_attrs() {
     cudaFuncSetAttribute(k_attention_warp<kOutF16<FMT>, 4, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, AwLayout<4, 64>::SMEM);
     cudaFuncSetAttribute(k_attention_warp<kOutF16<FMT>, 4, 128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, AwLayout<4>::SMEM);
     cudaFuncSetAttribute(k_attention_warp<kOutF16<FMT>, 8, 128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, AwLayout<8>::SMEM);
+    cudaFuncSetAttribute(k_attention_pt<kOutF16<FMT>, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, PtLayout<4>::SMEM);
+    cudaFuncSetAttribute(k_attention_pt<kOutF16<FMT>, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, PtLayout<8>::SMEM);
 }
 
 }  // namespace
@@ -2424,6 +2897,8 @@ static int64_t run_tc(Model& m, Workspace& w, bool profile, const float* x, cons
             case 5: k_attention_warp<AF, 4, 64><<<2 * g.x, aw_threads<64>(), AwLayout<4, 64>::SMEM, st>>>(w.map_q64, w.map_k, w.map_vt, ap); break;
             case 6: k_attention_warp<AF, 4, 128, true><<<g, aw_threads<128, true>(), AwLayout<4>::SMEM, st>>>(w.map_q, w.map_k, w.map_vt, ap); break;
             case 7: k_attention_warp<AF, 8, 128, true><<<g, aw_threads<128, true>(), AwLayout<8>::SMEM, st>>>(w.map_q, w.map_k, w.map_vt, ap); break;
+            case 8: k_attention_pt<AF, 4><<<g, PT_ATT_THREADS, PtLayout<4>::SMEM, st>>>(w.map_q, w.map_k, w.map_vt, ap); break;
+            case 9: k_attention_pt<AF, 8><<<g, PT_ATT_THREADS, PtLayout<8>::SMEM, st>>>(w.map_q, w.map_k, w.map_vt, ap); break;
             default: k_attention_warp<AF, 8><<<g, aw_threads<128>(), AwLayout<8>::SMEM, st>>>(w.map_q, w.map_k, w.map_vt, ap); break;
         }
         prof_end(m, st);

@@ -274,6 +274,17 @@ MLPF_DEV void tmem_st16(uint32_t taddr, const uint32_t* v) {
         "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
         : "memory");
 }
+// registers -> TMEM: 16 lanes x 128 bit, twice (8 consecutive columns).  Thread
+// 4 g + c of the warp writes lane taddr.lane + g (registers 0 and 2) and + g + 8
+// (registers 1 and 3), column c (registers 0, 1) and 4 + c (registers 2, 3): the
+// A-fragment layout of an m16n8k16 warp-level MMA with two 16-bit values per column.
+// No memory clobber: tensor memory is not C++ memory, and the store stays ordered
+// with the tcgen05.wait::st that publishes it (both volatile); the compiler may move
+// register arithmetic and loads across it.
+MLPF_DEV void tmem_st16x128b_x2(uint32_t taddr, const uint32_t* v) {
+    asm volatile("tcgen05.st.sync.aligned.16x128b.x2.b32 [%0], {%1,%2,%3,%4};" ::"r"(taddr), "r"(v[0]),
+                 "r"(v[1]), "r"(v[2]), "r"(v[3]));
+}
 MLPF_DEV void tmem_wait_st() {
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }

@@ -1,4 +1,4 @@
-"""Both paths of the warp-MMA attention kernel against the oracle.
+"""Both paths of the warp-MMA attention kernels against the oracle.
 
 The kernel bounds a key tile's scores row by row, |q . k| <= |q| max|k|
 (Cauchy-Schwarz, the per-block maxima of |k| written by the QKV epilogues).  A
@@ -14,6 +14,11 @@ item); x 2 -> 0.4 % on the bound path.
 Bounds: sharper attention amplifies the 16-bit rounding of Q and K (the score
 error grows with |S|, up to about 40 log2 units at x 2), so the floors are
 looser than the parity tests' for the unscaled model.
+
+Both warp-level kernels are checked: the default (variant 4: P V and the row sums
+on warp-level MMAs, O rescaled in registers) and the one with P V and the row sums
+on tcgen05 (variant 9: one reference per row and key tile, O and l rescaled in
+tensor memory).
 """
 import numpy as np
 import pytest
@@ -44,9 +49,13 @@ def scaled_model(f):
     return Model(synth.pack_blob(cfg, w)), w
 
 
+@pytest.mark.parametrize("variant", [4, 9])
 @pytest.mark.parametrize("f", [1.4, 2.0])
-def test_bound_and_checked_paths_match_oracle(f):
+def test_bound_and_checked_paths_match_oracle(f, variant):
+    from paper_2601_17554_b300 import _lib
     model, w = scaled_model(f)
+    model.set_option(_lib.OPT_ATTN_VARIANT_BF16, variant)
+    model.set_option(_lib.OPT_ATTN_VARIANT_FP16, variant)
     x, cu = synth.gen_events(22, SIZES)
     ref = oracle.forward(w, synth.SMALL, x, cu)
     for prec in ("fp16", "bf16"):
@@ -54,7 +63,7 @@ def test_bound_and_checked_paths_match_oracle(f):
         assert np.isfinite(lo).all() and np.isfinite(rg).all() and np.isfinite(su).all()
         agree = (cl == ref.cls).mean()
         err = rel_err_cols(rg, ref.reg)
-        print(f"scale {f} {prec}: argmax agreement {agree:.5f}, max column rel err {err.max():.3e}")
+        print(f"variant {variant} scale {f} {prec}: argmax agreement {agree:.5f}, max column rel err {err.max():.3e}")
         amin, etol = BOUNDS[(prec, f)]
         assert agree >= amin, (prec, f, agree)
         assert err.max() <= etol, (prec, f, err)

@@ -3,8 +3,9 @@
 Variants in one group run the same per-head arithmetic in the same order and
 must be bit-identical: the tcgen05 kernels with S and P in tensor memory (four,
 six or eight K/V stages), the warp-level-MMA kernels (four or eight stages,
-128- or 64-row items) and the warp-level kernels with QK^T on tcgen05 (four or
-eight stages).  Groups differ in
+128- or 64-row items), the warp-level kernels with QK^T on tcgen05 (four or
+eight stages) and the warp-level kernels with PV and the row sums on tcgen05
+(four or eight stages).  Groups differ in
 summation order and exponent references: each must meet the oracle bounds of
 the precision and stay close to variant 0.  The autotuner must pick a valid
 variant, write its cache line and reuse it.
@@ -19,8 +20,8 @@ from tests.util import make_model, rel_err_cols, run_gpu
 pytestmark = pytest.mark.gpu
 
 SIZES = [1, 17, 64, 65, 129, 300, 0, 511, 1024, 2]
-N_VARIANTS = 8
-GROUPS = ((0, 1, 2), (3, 4, 5), (6, 7))
+N_VARIANTS = 10
+GROUPS = ((0, 1, 2), (3, 4, 5), (6, 7), (8, 9))
 
 
 @pytest.fixture(scope="module")

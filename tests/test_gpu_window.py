@@ -71,17 +71,18 @@ def test_window_variants_agree(model):
     x, cu = synth.gen_events(84, SIZES)
     outs = []
     try:
-        # warp-level MMAs (4, 3, 5), tensor-memory kernel (2, 0), QK^T on tcgen05 (7, 6)
-        for v in (4, 3, 5, 2, 0, 7, 6):
+        # warp-level MMAs (4, 3, 5), tensor-memory kernel (2, 0), QK^T on tcgen05 (7, 6),
+        # PV on tcgen05 (9, 8)
+        for v in (4, 3, 5, 2, 0, 7, 6, 9, 8):
             m.set_option(7, v)
             outs.append(_with_window(m, 1, lambda: run_gpu(m, x, cu, "bf16")))
     finally:
         m.set_option(7, 4)
-    for grp in ((0, 1, 2), (3, 4), (5, 6)):
+    for grp in ((0, 1, 2), (3, 4), (5, 6), (7, 8)):
         for i in grp[1:]:
             for a, b in zip(outs[grp[0]], outs[i]):
                 np.testing.assert_array_equal(a, b)
-    for o in (outs[3], outs[5]):
+    for o in (outs[3], outs[5], outs[7]):
         assert (outs[0][2] == o[2]).mean() >= 0.999
         assert rel_err_cols(o[1], outs[0][1]).max() <= 1e-2
 

@@ -52,11 +52,12 @@ def test_noalloc_matches_forward_twice(prec):
     model.close()
 
 
-@pytest.mark.parametrize("variant", [0, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("variant", [0, 2, 3, 4, 5, 6, 8])
 def test_noalloc_every_attention_family(variant):
     """Each attention kernel family (tcgen05 with S and P in tensor memory and its
     16-row V^T tensor map, warp-level MMAs on 128-row and on 64-row items, the latter
-    with its own Q tensor map, warp-level PV with QK^T on tcgen05) through the
+    with its own Q tensor map, warp-level PV with QK^T on tcgen05, warp-level QK^T
+    with PV on tcgen05) through the
     no-allocation entry point, as the autotuner may leave any of them selected."""
     model, _ = make_model(synth.SMALL, 3, perturbed=True)
     model.set_option(_lib.OPT_ATTN_VARIANT_BF16, variant)
