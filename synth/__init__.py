@@ -362,6 +362,64 @@ def gen_targets(seed: int, x, cu_seqlens, first_event: int = 0):
     return cls, reg
 
 
+# deterministic truth (a learnable task for training the full model as a teacher)
+TRUTH_MUON_CUT = 1.5     # first track feature above which a track is a muon
+TRUTH_CLUSTER_CUT = 0.5  # a cluster makes a particle if log E > its event's mean - this
+
+
+def gen_pf_truth(x, cu_seqlens):
+    """Deterministic per-element truth of a PF-like rule, for training the full model
+    on a learnable task (the CMS training targets are not available): cls [T] int32 and
+    decoded regression targets reg [T, 5] float32 (pT, eta, sin phi, cos phi, E).
+
+    Classes by element type: track -> muon (5) if its first track feature x[13] >
+    TRUTH_MUON_CUT (a muon-system match), else charged hadron (1); GSF track -> electron
+    (4); brem -> none (0); ECAL cluster -> photon (3) if its log E exceeds the mean log E
+    of the event's ECAL clusters by more than -TRUTH_CLUSTER_CUT, else none (below the
+    event's calibrated noise level); HCAL cluster -> neutral hadron (2) under the same
+    rule over the event's HCAL clusters; HF-EM -> photon; HF-HAD -> neutral hadron;
+    supercluster -> photon.  The cluster rule needs the event (a mean over other
+    elements), the rest the element alone.
+    Regression: tracks, GSF tracks and brems carry pT = the element's pT and
+    E = pT cosh(eta) (massless); clusters carry E = the element's E and
+    pT = E / cosh(eta); eta and phi are the element's own.
+    """
+    x = np.asarray(x, np.float64)
+    cu = np.asarray(cu_seqlens, np.int64)
+    sizes = np.diff(cu)
+    total = int(cu[-1])
+    cls = np.zeros(total, np.int32)
+    reg = np.zeros((total, 5), np.float32)
+    if total == 0:
+        return cls, reg
+    ev = np.repeat(np.arange(len(sizes)), sizes)
+    typ = np.argmax(x[:, :N_TYPES], axis=1)
+    loge = x[:, 9]
+    cls[typ == 0] = np.where(x[typ == 0, 13] > TRUTH_MUON_CUT, 5, 1)
+    cls[typ == 5] = 4
+    cls[typ == 6] = 0
+    for t, k in ((1, 3), (2, 2)):
+        sel = typ == t
+        cnt = np.bincount(ev[sel], minlength=len(sizes))
+        tot = np.bincount(ev[sel], weights=loge[sel], minlength=len(sizes))
+        mean = tot / np.maximum(cnt, 1)
+        cls[sel] = np.where(loge[sel] > mean[ev[sel]] - TRUTH_CLUSTER_CUT, k, 0)
+    cls[typ == 3] = 3
+    cls[typ == 4] = 2
+    cls[typ == 7] = 3
+    eta = x[:, 10]
+    ch = np.cosh(eta)
+    is_trk = np.isin(typ, (0, 5, 6))
+    pt = np.where(is_trk, np.exp(x[:, 8]), np.exp(loge) / ch)
+    e = np.where(is_trk, np.exp(x[:, 8]) * ch, np.exp(loge))
+    reg[:, 0] = pt
+    reg[:, 1] = eta
+    reg[:, 2] = x[:, 11]
+    reg[:, 3] = x[:, 12]
+    reg[:, 4] = e
+    return cls, reg
+
+
 # --------------------------------------------------------------------------
 # named workloads
 # --------------------------------------------------------------------------
