@@ -32,6 +32,13 @@ constexpr int JT = 1024;        // threads per event (the per-step scans want th
                                 // 256 threads 430 ms, 512 242 ms, 1024 166 ms per 512-event batch)
 constexpr int JW = JT / 32;
 constexpr int JLIST = 512;      // entries whose neighbour is recomputed in one step
+// k_antikt_sm: events of at most JCAP elements keep the fields every step reads (y, phi,
+// the entry distance dd, the squared distance d2 to the neighbour, the neighbour nn) in
+// shared memory, 18 bytes per particle; larger events run k_antikt on global memory.
+constexpr int JCAP = 12288;
+constexpr size_t kJetSmem = (size_t)JCAP * (4 * sizeof(float) + sizeof(int16_t));
+constexpr int JG = 4;           // listed entries whose neighbours one block scan recomputes
+constexpr int JT_SM = 1024;     // threads per event of k_antikt_sm
 constexpr float kPiF = 3.14159265358979323846f;
 
 struct JetScratch {
@@ -132,6 +139,7 @@ __global__ void __launch_bounds__(JT) k_antikt(const float* __restrict__ reg, co
     __shared__ int s_list[JLIST];
     const int ev = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int r0 = cu[ev], N = cu[ev + 1] - r0;
+    if (N <= JCAP) return;   // k_antikt_sm takes this event
     const float inv_r2 = 1.f / r2;
     auto is_particle = [&](int row, float& pt, float& eta, float& s, float& c) {
         pt = reg[(size_t)row * 5];
@@ -296,6 +304,288 @@ __global__ void __launch_bounds__(JT) k_antikt(const float* __restrict__ reg, co
     if (tid == 0) n_jets[ev] = s_jets;
 }
 
+// the entry of smallest (value, index) over the block, in every thread, with one
+// barrier: each warp reduces the per-warp minima itself (sv is rewritten only after
+// the caller's next barrier)
+template <int NW>
+__device__ void block_argmin_all(float& v, int& i, float* sv, int* si) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    warp_argmin(v, i);
+    if (lane == 0) {
+        sv[warp] = v;
+        si[warp] = i;
+    }
+    __syncthreads();
+    v = lane < NW ? sv[lane] : INFINITY;
+    i = lane < NW ? si[lane] : INT_MAX;
+    warp_argmin(v, i);
+}
+
+// Anti-kt with the per-step fields in shared memory (the algorithm, order of merges
+// and tie rules of k_antikt; see the top of this file).  An entry is inactive when
+// its dd is NaN.  Each step: the block-wide minimum of dd (every thread carries the
+// minimum over its own entries from the previous step's update pass), the merge or
+// jet by thread 0, one pass in which every entry checks the merged entry and the
+// entries that lost their neighbour are listed, and the neighbours of the listed
+// entries recomputed, JG at a time per block scan.
+template <int NT>
+__global__ void __launch_bounds__(NT) k_antikt_sm(const float* __restrict__ reg, const int32_t* __restrict__ cls,
+                                                 const int32_t* __restrict__ cu, float r2, JetScratch S,
+                                                 float* __restrict__ jets, int32_t* __restrict__ n_jets,
+                                                 int32_t* __restrict__ jet_of) {
+    constexpr int NW = NT / 32;
+    extern __shared__ float jsm[];
+    float* sy = jsm;
+    float* sphi = sy + JCAP;
+    float* sdd = sphi + JCAP;
+    float* sd2 = sdd + JCAP;
+    int16_t* snn = (int16_t*)(sd2 + JCAP);
+    __shared__ float sv[NW];
+    __shared__ int si[NW];
+    __shared__ float gv[2][NW * JG];   // group reductions, double-buffered
+    __shared__ int gi[2][NW * JG];
+    __shared__ int s_n, s_jets, s_cnt, s_over, s_j, s_beam;
+    __shared__ int s_list[JLIST];
+    const int ev = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int r0 = cu[ev], N = cu[ev + 1] - r0;
+    if (N > JCAP) return;   // k_antikt takes this event
+    const float inv_r2 = 1.f / r2;
+    JetScratch L;   // the cold fields in global memory (this event's rows)
+    L.pinv = S.pinv + r0; L.px = S.px + r0; L.py = S.py + r0; L.ep = S.ep + r0; L.em = S.em + r0;
+    L.parent = S.parent + r0; L.jid = S.jid + r0; L.idx = S.idx + r0;
+    if (tid == 0) {
+        s_n = 0;
+        s_jets = 0;
+    }
+    __syncthreads();
+    // particles of the event, in input order (block-wide compaction by chunks)
+    for (int c0 = 0; c0 < N; c0 += NT) {
+        const int row = r0 + c0 + tid;
+        bool f = false;
+        float pt = 0.f, eta = 0.f, s = 0.f, c = 0.f;
+        if (c0 + tid < N) {
+            pt = reg[(size_t)row * 5];
+            eta = reg[(size_t)row * 5 + 1];
+            s = reg[(size_t)row * 5 + 2];
+            c = reg[(size_t)row * 5 + 3];
+            f = cls[row] != 0 && pt > 0.f && (s * s + c * c) > 0.f;
+            if (jet_of) jet_of[row] = -1;
+        }
+        const unsigned b = __ballot_sync(0xffffffffu, f);
+        if (lane == 0) si[warp] = __popc(b);
+        __syncthreads();
+        int off = 0, tot = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            off += w < warp ? si[w] : 0;
+            tot += si[w];
+        }
+        if (f) {
+            const int k = s_n + off + __popc(b & ((1u << lane) - 1u));
+            const float r = sqrtf(s * s + c * c);
+            const float px = pt * (c / r), py = pt * (s / r);
+            L.idx[k] = row;
+            L.px[k] = px;
+            L.py[k] = py;
+            L.ep[k] = pt * expf(eta);    // E + pz
+            L.em[k] = pt * expf(-eta);   // E - pz
+            sy[k] = eta;                 // massless: rapidity = pseudorapidity
+            sphi[k] = atan2f(s, c);
+            L.pinv[k] = 1.f / (px * px + py * py);
+            L.parent[k] = -1;
+            sdd[k] = 0.f;                // active
+        }
+        __syncthreads();
+        if (tid == 0) s_n += tot;
+        __syncthreads();
+    }
+    const int n = s_n;
+    auto active = [&](int m) { const float d = sdd[m]; return d == d; };
+    // nearest active neighbour within R of entry a over the entries m0, m0 + dm, ...
+    auto scan = [&](int a, int m0, int dm, float& best, int& bj) {
+        const float ya = sy[a], pa = sphi[a];
+        best = INFINITY;
+        bj = INT_MAX;
+        for (int m = m0; m < n; m += dm) {
+            if (m == a || !active(m)) continue;
+            const float d = dr2(ya, pa, sy[m], sphi[m]);
+            if (d < r2) argmin_pair(best, bj, d, m);
+        }
+    };
+    auto set_nn = [&](int a, float best, int bj) {
+        const int nn = bj == INT_MAX ? -1 : bj;
+        snn[a] = (int16_t)nn;
+        sd2[a] = nn < 0 ? INFINITY : best;
+        sdd[a] = entry_dist(L.pinv[a], best, nn, inv_r2);
+    };
+    auto warp_nn = [&](int a) {
+        float best;
+        int bj;
+        scan(a, lane, 32, best, bj);
+        warp_argmin(best, bj);
+        if (lane == 0) set_nn(a, best, bj);
+    };
+    // nearest neighbours of all entries (every entry is active here: dd = 0 or final)
+    for (int a = warp; a < n; a += NW) warp_nn(a);
+    __syncthreads();
+    float bv = INFINITY;
+    int bi = INT_MAX;
+    for (int k = tid; k < n; k += NT) argmin_pair(bv, bi, sdd[k], k);
+    int gbuf = 0;
+    for (int step = 0; step < n; ++step) {   // every step removes one entry
+        block_argmin_all<NW>(bv, bi, sv, si);
+        const int i = bi;
+        if (tid == 0) {
+            const int j = snn[i];
+            const float pi = L.pinv[i];
+            const bool beam = j < 0 || !(pi * sd2[i] * inv_r2 < pi);
+            s_j = j;
+            s_beam = beam;
+            s_cnt = 0;
+            s_over = 0;
+            if (beam) {   // i is a jet: (px, py, pz, E)
+                const int t = s_jets++;
+                float* o = jets + (size_t)(r0 + t) * 4;
+                o[0] = L.px[i];
+                o[1] = L.py[i];
+                o[2] = 0.5f * (L.ep[i] - L.em[i]);
+                o[3] = 0.5f * (L.ep[i] + L.em[i]);
+                L.jid[i] = t;
+                sdd[i] = __int_as_float(0x7fc00000);   // inactive
+            } else {      // merge into the lower index (E scheme)
+                const int k = min(i, j), l = max(i, j);
+                const float px = L.px[k] + L.px[l], py = L.py[k] + L.py[l];
+                const float ep = L.ep[k] + L.ep[l], em = L.em[k] + L.em[l];
+                L.px[k] = px;
+                L.py[k] = py;
+                L.ep[k] = ep;
+                L.em[k] = em;
+                sy[k] = 0.5f * logf(ep / em);
+                sphi[k] = atan2f(py, px);
+                L.pinv[k] = 1.f / (px * px + py * py);
+                sdd[l] = __int_as_float(0x7fc00000);
+                L.parent[l] = k;
+                s_list[0] = k;
+                s_cnt = 1;
+            }
+        }
+        __syncthreads();
+        const int j = s_j;
+        const bool beam = s_beam;
+        const int k = beam ? i : min(i, j);
+        const float yk = sy[k], pk = sphi[k];
+        // entries that lost their neighbour, or whose neighbour (the merged entry) moved
+        // away, are listed; the others check whether the merged entry is now nearer and
+        // carry their distance into the next step's minimum
+        bv = INFINITY;
+        bi = INT_MAX;
+        for (int m = tid; m < n; m += NT) {
+            float dm = sdd[m];
+            if (!(dm == dm) || (!beam && m == k)) continue;
+            const int nm = snn[m];
+            bool lost = beam ? nm == i : (nm == i || nm == j);
+            if (lost && !beam && nm == k) {
+                // the merged entry moved: still the nearest if it did not move away
+                // (no other entry moved, and the entry it absorbed was not the nearest)
+                const float d = dr2(sy[m], sphi[m], yk, pk);
+                if (d < r2 && d <= sd2[m]) {
+                    sd2[m] = d;
+                    dm = entry_dist(L.pinv[m], d, k, inv_r2);
+                    sdd[m] = dm;
+                    lost = false;
+                }
+            } else if (!lost && !beam) {
+                const float d = dr2(sy[m], sphi[m], yk, pk);
+                if (d < r2 && (d < sd2[m] || (d == sd2[m] && k < nm))) {
+                    snn[m] = (int16_t)k;
+                    sd2[m] = d;
+                    dm = entry_dist(L.pinv[m], d, k, inv_r2);
+                    sdd[m] = dm;
+                }
+            }
+            if (lost) {
+                const int slot = atomicAdd(&s_cnt, 1);
+                if (slot < JLIST) s_list[slot] = m;
+                else s_over = 1;
+            } else {
+                argmin_pair(bv, bi, dm, m);
+            }
+        }
+        __syncthreads();
+        const int cnt = s_cnt;
+        if (s_over) {   // many entries lost their neighbour: recompute all, then the minimum
+            for (int a = warp; a < n; a += NW)
+                if (active(a)) warp_nn(a);
+            __syncthreads();
+            bv = INFINITY;
+            bi = INT_MAX;
+            for (int m = tid; m < n; m += NT)
+                if (active(m)) argmin_pair(bv, bi, sdd[m], m);
+        } else if (cnt > NW) {   // one warp per listed entry
+            for (int t = warp; t < cnt; t += NW) warp_nn(s_list[t]);
+            __syncthreads();
+            for (int t = tid; t < cnt; t += NT) argmin_pair(bv, bi, sdd[s_list[t]], s_list[t]);
+        } else {                 // JG listed entries per block scan
+            for (int t0 = 0; t0 < cnt; t0 += JG) {
+                int aa[JG];
+                float ya[JG], pa[JG], best[JG];
+                int bj[JG];
+#pragma unroll
+                for (int q = 0; q < JG; ++q) {
+                    aa[q] = t0 + q < cnt ? s_list[t0 + q] : -1;
+                    ya[q] = aa[q] >= 0 ? sy[aa[q]] : 0.f;
+                    pa[q] = aa[q] >= 0 ? sphi[aa[q]] : 0.f;
+                    best[q] = INFINITY;
+                    bj[q] = INT_MAX;
+                }
+                for (int m = tid; m < n; m += NT) {
+                    if (!active(m)) continue;
+                    const float ym = sy[m], pm = sphi[m];
+#pragma unroll
+                    for (int q = 0; q < JG; ++q) {
+                        if (aa[q] < 0 || m == aa[q]) continue;
+                        const float d = dr2(ya[q], pa[q], ym, pm);
+                        if (d < r2) argmin_pair(best[q], bj[q], d, m);
+                    }
+                }
+                const int g = min(JG, cnt - t0);
+#pragma unroll
+                for (int q = 0; q < JG; ++q) {
+                    if (q >= g) break;   // warp-uniform
+                    warp_argmin(best[q], bj[q]);
+                    if (lane == 0) {
+                        gv[gbuf][warp * JG + q] = best[q];
+                        gi[gbuf][warp * JG + q] = bj[q];
+                    }
+                }
+                __syncthreads();
+                if (warp == 0) {
+#pragma unroll
+                    for (int q = 0; q < JG; ++q) {
+                        if (q >= g) break;
+                        float v = lane < NW ? gv[gbuf][lane * JG + q] : INFINITY;
+                        int ix = lane < NW ? gi[gbuf][lane * JG + q] : INT_MAX;
+                        warp_argmin(v, ix);
+                        if (lane == 0 && aa[q] >= 0) {
+                            set_nn(aa[q], v, ix);
+                            argmin_pair(bv, bi, sdd[aa[q]], aa[q]);
+                        }
+                    }
+                }
+                gbuf ^= 1;
+            }
+        }
+    }
+    __syncthreads();
+    // jet index of every particle: the entry its chain of merges ends in
+    for (int m = tid; m < n; m += NT) {
+        int root = m;
+        while (L.parent[root] >= 0) root = L.parent[root];
+        if (jet_of) jet_of[L.idx[m]] = L.jid[root];
+    }
+    if (tid == 0) n_jets[ev] = s_jets;
+}
+
 }  // namespace
 }  // namespace mlpf
 
@@ -344,7 +634,13 @@ extern "C" mlpf_status mlpf_cluster_jets(mlpf_model* mm, const float* reg, const
     S.jid = iw + 2 * cap;
     S.idx = iw + 3 * cap;
     S.act = (unsigned char*)(iw + 4 * cap);
-    k_antikt<<<n_events, JT, 0, (cudaStream_t)stream>>>(reg, cls, cu_seqlens, R * R, S, jets, n_jets, jet_of);
+    // events of at most JCAP elements in shared memory; larger ones (possible only when
+    // the batch holds more than JCAP elements) on global memory
+    cudaFuncSetAttribute(k_antikt_sm<JT_SM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kJetSmem);
+    k_antikt_sm<JT_SM><<<n_events, JT_SM, kJetSmem, (cudaStream_t)stream>>>(reg, cls, cu_seqlens, R * R, S, jets,
+                                                                             n_jets, jet_of);
+    if (total > JCAP)
+        k_antikt<<<n_events, JT, 0, (cudaStream_t)stream>>>(reg, cls, cu_seqlens, R * R, S, jets, n_jets, jet_of);
     const cudaError_t e = cudaPeekAtLastError();
     if (e != cudaSuccess) { set_error(std::string("jet kernel launch: ") + cudaGetErrorString(e)); return MLPF_E_CUDA; }
     return MLPF_OK;

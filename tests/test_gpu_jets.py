@@ -1,6 +1,8 @@
 """Anti-kt jets on the GPU (mlpf_cluster_jets) against the FP64 oracle.
 
-Inputs: seeded synthetic reconstructed particles (synth.gen_targets: classes by
+Events of at most 12,288 elements run on the shared-memory kernel, larger ones on
+the global-memory kernel (same algorithm and tie rules).  Inputs: seeded synthetic
+reconstructed particles (synth.gen_targets: classes by
 element type, pT, eta, phi and E near the element's own), the same arrays for
 both sides.  What is unique is compared exactly: the partition of the particles
 into jets (constituent sets) and the jet count; the jets' 4-vectors (FP32 sums on
@@ -42,9 +44,10 @@ def partition(jof):
     return {frozenset(np.nonzero(jof == t)[0].tolist()) for t in range(int(jof.max()) + 1)} if len(jof) and jof.max() >= 0 else set()
 
 
-def compare_event(gj, gnj, gjof, cls, reg, R):
-    """(particles, particles in matched jets) of one event, checking matched jets' 4-vectors."""
-    oj, ojof = J.event_jets(cls, reg, R)
+def compare_event(gj, gnj, gjof, cls, reg, R, ref=None):
+    """(particles, particles in matched jets) of one event, checking matched jets' 4-vectors;
+    ref: the oracle's (jets, jet index per element), computed here if None."""
+    oj, ojof = J.event_jets(cls, reg, R) if ref is None else ref
     assert gjof.shape == ojof.shape
     assert ((gjof < 0) == (ojof < 0)).all()          # the same particles
     n_part = int((ojof >= 0).sum())
@@ -138,3 +141,41 @@ def test_full_batch_conserves_momentum(model):
         tot = jets[cu[e]:cu[e] + nj[e]].sum(0)
         np.testing.assert_allclose(tot, v.sum(0), rtol=1e-3, atol=1e-3 * np.abs(v).sum())
     fm.close()
+
+
+def test_large_event_matches_oracle_golden(model):
+    """One event of 7,200 elements (4,992 particles) against the FP64 oracle's jets,
+    stored in tests/golden/antikt_large_r04.json by tests/golden/make_antikt_large.py
+    (the oracle's plain O(N^3) clustering takes about 20 minutes on it)."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "antikt_large_r04.json")
+    g = json.load(open(path))
+    x, cu = synth.gen_events(g["seed_events"], [g["size"]])
+    cls, reg = synth.gen_targets(g["seed_targets"], x, cu)
+    gj, gnj, gjof = run_jets(model, reg, cls, cu, g["R"])
+    oj, ojof = np.asarray(g["jets"], np.float64).reshape(-1, 4), np.asarray(g["jet_of"], np.int64)
+    n, m = compare_event(gj, int(gnj[0]), gjof, cls, reg, g["R"], ref=(oj, ojof))
+    assert n == g["n_particles"]
+    assert m >= 0.995 * n, (m, n)
+
+
+def test_event_above_shared_memory_capacity(model):
+    """An event of 13,000 elements (beyond the 12,288 that the shared-memory kernel
+    holds) runs on the global-memory kernel in the same call as small events: every
+    particle is in exactly one jet and each event's jets add up to its particles; the
+    small events match the oracle."""
+    sizes = [13000, 150, 700]
+    x, cu = synth.gen_events(47, sizes)
+    cls, reg = synth.gen_targets(48, x, cu)
+    gj, gnj, gjof = run_jets(model, reg, cls, cu, 0.4)
+    sl = slice(cu[0], cu[1])
+    rows, v = J.particles(cls[sl], reg[sl])
+    assert ((gjof[sl] >= 0) == np.isin(np.arange(sizes[0]), rows)).all()
+    assert set(np.unique(gjof[sl][gjof[sl] >= 0]).tolist()) == set(range(int(gnj[0])))
+    tot = gj[cu[0]:cu[0] + gnj[0]].astype(np.float64).sum(0)
+    np.testing.assert_allclose(tot, v.sum(0), rtol=1e-3, atol=1e-3 * np.abs(v).sum())
+    for e in (1, 2):
+        sl = slice(cu[e], cu[e + 1])
+        n, m = compare_event(gj[cu[e]:cu[e + 1]], int(gnj[e]), gjof[sl], cls[sl], reg[sl], 0.4)
+        assert m >= 0.995 * n
