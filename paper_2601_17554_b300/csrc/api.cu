@@ -557,6 +557,7 @@ void mlpf_free(mlpf_model* mm) {
     if (m.w.f32_base) cudaFree(m.w.f32_base);
     if (m.w.img_base) cudaFree(m.w.img_base);
     if (m.w.w16_base) cudaFree(m.w.w16_base);
+    if (m.w.wide_base) cudaFree(m.w.wide_base);
     if (m.w.img8_base) cudaFree(m.w.img8_base);
     if (m.w.tc_f32_base) cudaFree(m.w.tc_f32_base);
     if (m.status) cudaFree(m.status);

@@ -42,6 +42,10 @@ struct DeviceWeights {
     // kp = K padded to 64, keyed by the FP32 tensor's device pointer -> (image, kp)
     uint16_t* w16_base = nullptr;
     std::map<const float*, std::pair<const uint16_t*, int>> w16;
+    // the wide path's QKV biases with the Q part times log2(e)/sqrt(dh) (its QKV weight
+    // images carry the same factor), [3d] per layer
+    float* wide_base = nullptr;
+    std::vector<float*> bqkv_wide_pid, bqkv_wide_reg;
     float* tc_f32_base = nullptr;         // fused bias vectors for the tensor-core kernels
     std::map<std::string, float*> tcv;
     // FP8 E4M3 images (same layout, one byte per element) and per-tensor scales

@@ -308,14 +308,22 @@ __global__ void __launch_bounds__(128) k_attn_dkv_tc(const float* __restrict__ q
 }
 
 // Forward of the generic-width inference path on 16-bit Q | K | V ([T, 3d], written by the
-// QKV GEMM's epilogue): 128 query rows per CTA (eight warps), K / V tiles of 64 rows
-// double-buffered with asynchronous copies, scores scaled by log2(e)/sqrt(dh) in FP32.
-// Writes O as FP16 rows of stride ldo16 (the operand of the output projection's GEMM).
+// QKV GEMM's epilogue, Q pre-multiplied by log2(e)/sqrt(dh): the wide path folds that
+// factor into the Q rows of its two-term QKV weights and biases): 128 query rows per CTA
+// (eight warps of 16 rows), K / V tiles of 64 rows double-buffered with asynchronous
+// copies.  The QK^T MMA starts from the rows' negated exponent references, so its output
+// is the base-2 exponent itself; the references are raised lazily (the first tile sets
+// them to the row maxima, a later tile only when a row maximum exceeds its reference by
+// more than kRaise, so P <= 2^kRaise), P = 2^(S - ref) is taken two at a time with packed
+// MUFU exponentials straight into the A fragments of the PV MMA, and the row sums are
+// one more MMA of the same P against a block of ones (the sums of the rounded P that the
+// PV product uses).  Writes O as FP16 rows of stride ldo16 (the operand of the output
+// projection's GEMM).
 template <int DH, bool F16>
 __global__ void __launch_bounds__(256) k_attn_fwd16(const uint16_t* __restrict__ qkv16, uint16_t* __restrict__ o16,
-                                                    int ldo16, const int32_t* __restrict__ cu, int d, float c2,
-                                                    int window) {
+                                                    int ldo16, const int32_t* __restrict__ cu, int d, int window) {
     constexpr int LD = DH + 8, CH = DH / 8;   // 16-byte chunks per row
+    constexpr float kRaise = 4.f;
     extern __shared__ __align__(16) uint16_t att_smem[];   // (128 + 4 x 64) rows of LD
     uint16_t* Qs = att_smem;
     auto Kt = [&](int b) { return att_smem + (128 + 64 * b) * LD; };
@@ -325,6 +333,7 @@ __global__ void __launch_bounds__(256) k_attn_fwd16(const uint16_t* __restrict__
     if (q0 >= n) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
     const long ld = 3L * d;
+    const uint32_t ONE2 = F16 ? 0x3C003C00u : 0x3F803F80u;
     int kbeg = 0, kend = n;
     if (window > 0) {
         const int y = q0 / 128;
@@ -345,7 +354,8 @@ __global__ void __launch_bounds__(256) k_attn_fwd16(const uint16_t* __restrict__
     stage(Vt(0), 64, kbeg, kend, 2 * d + h * DH);
     cp_async_commit();
     float o[DH / 8][4] = {};
-    float m[2] = {-INFINITY, -INFINITY}, l[2] = {0.f, 0.f};
+    float la[4] = {0.f, 0.f, 0.f, 0.f};   // row sums: the ones-MMA accumulator (every column its row's sum)
+    float nr[4] = {0.f, 0.f, 0.f, 0.f};   // negated references of rows g (0, 1) and g + 8 (2, 3)
     uint32_t qa[DH / 16][4];
     int buf = 0;
     for (int kb = kbeg; kb < kend; kb += 64, buf ^= 1) {
@@ -360,8 +370,18 @@ __global__ void __launch_bounds__(256) k_attn_fwd16(const uint16_t* __restrict__
 #pragma unroll
             for (int kk = 0; kk < DH / 16; ++kk) load_a<LD>(Qs, warp * 16, kk * 16, qa[kk]);
         }
+        // S - ref (16 rows x 64 keys, 8 n-tiles)
         float s[8][4];
-        scores<DH, F16>(qa, Kt(buf), s);
+        const uint16_t* kt = Kt(buf);
+#pragma unroll
+        for (int kk = 0; kk < DH / 16; ++kk)
+#pragma unroll
+            for (int np = 0; np < 4; ++np) {
+                uint32_t b[4];
+                load_b_nk<LD>(kt, np * 16, kk * 16, b);
+                mma16816_c<F16>(s[2 * np], qa[kk], b[0], b[1], kk == 0 ? nr : s[2 * np]);
+                mma16816_c<F16>(s[2 * np + 1], qa[kk], b[2], b[3], kk == 0 ? nr : s[2 * np + 1]);
+            }
         if (kb + 64 > kend) {   // the event's last keys: mask the tile's tail
 #pragma unroll
             for (int j = 0; j < 8; ++j)
@@ -369,51 +389,66 @@ __global__ void __launch_bounds__(256) k_attn_fwd16(const uint16_t* __restrict__
                 for (int u = 0; u < 4; ++u)
                     if (kb + j * 8 + 2 * c + (u & 1) >= kend) s[j][u] = -INFINITY;
         }
-        // raw (unscaled) row maxima of the tile; the running maxima m are in log2 units
+        // the tile's row maxima of S - ref; raise the references where needed
         float mr[2] = {-INFINITY, -INFINITY};
 #pragma unroll
-        for (int j = 0; j < 8; ++j)
-#pragma unroll
-            for (int u = 0; u < 4; ++u) mr[u >> 1] = fmaxf(mr[u >> 1], s[j][u]);
+        for (int j = 0; j < 8; ++j) {
+            mr[0] = fmaxf(mr[0], fmaxf(s[j][0], s[j][1]));
+            mr[1] = fmaxf(mr[1], fmaxf(s[j][2], s[j][3]));
+        }
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
             mr[r] = fmaxf(mr[r], __shfl_xor_sync(0xffffffffu, mr[r], 1));
             mr[r] = fmaxf(mr[r], __shfl_xor_sync(0xffffffffu, mr[r], 2));
         }
-        const float mx0 = fmaxf(m[0], mr[0] * c2), mx1 = fmaxf(m[1], mr[1] * c2);
-        // rescale only when some row of the warp has a new maximum (otherwise the factors
-        // are exactly 1)
-        if (__any_sync(0xffffffffu, mx0 > m[0] || mx1 > m[1])) {
-            const float al[2] = {ex2_approx(m[0] - mx0), ex2_approx(m[1] - mx1)};
-            l[0] *= al[0];
-            l[1] *= al[1];
+        const bool first = kb == kbeg;
+        if (__any_sync(0xffffffffu, first || mr[0] > kRaise || mr[1] > kRaise)) {
 #pragma unroll
-            for (int j = 0; j < DH / 8; ++j)
+            for (int r = 0; r < 2; ++r) {
+                const float dr = first ? mr[r] : fmaxf(mr[r], 0.f);
+                const float al = first ? 1.f : ex2_approx(-dr);
+                nr[2 * r] -= dr;
+                nr[2 * r + 1] -= dr;
+                la[2 * r] *= al;
+                la[2 * r + 1] *= al;
 #pragma unroll
-                for (int u = 0; u < 4; ++u) o[j][u] *= al[u >> 1];
-            m[0] = mx0;
-            m[1] = mx1;
-        }
+                for (int j = 0; j < DH / 8; ++j) {
+                    o[j][2 * r] *= al;
+                    o[j][2 * r + 1] *= al;
+                }
 #pragma unroll
-        for (int j = 0; j < 8; ++j)
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                s[j][u] = ex2_approx(fmaf(s[j][u], c2, -m[u >> 1]));
-                l[u >> 1] += s[j][u];
+                for (int j = 0; j < 8; ++j) {
+                    s[j][2 * r] -= dr;
+                    s[j][2 * r + 1] -= dr;
+                }
             }
-        accumulate<DH, F16>(s, Vt(buf), o);
-        __syncthreads();   // every warp is done with this buffer before it is refilled
-    }
+        }
+        // P = 2^(S - ref) as the A fragments of PV (16 keys per K-step), the row sums from
+        // the same P
+        const uint16_t* vt = Vt(buf);
 #pragma unroll
-    for (int r = 0; r < 2; ++r) {
-        l[r] += __shfl_xor_sync(0xffffffffu, l[r], 1);
-        l[r] += __shfl_xor_sync(0xffffffffu, l[r], 2);
+        for (int kk = 0; kk < 4; ++kk) {
+            uint32_t pa[4];
+            pa[0] = exp2_pair<F16>(s[2 * kk][0], s[2 * kk][1]);
+            pa[1] = exp2_pair<F16>(s[2 * kk][2], s[2 * kk][3]);
+            pa[2] = exp2_pair<F16>(s[2 * kk + 1][0], s[2 * kk + 1][1]);
+            pa[3] = exp2_pair<F16>(s[2 * kk + 1][2], s[2 * kk + 1][3]);
+            mma16816<F16>(la, pa, ONE2, ONE2);
+#pragma unroll
+            for (int dp = 0; dp < DH / 16; ++dp) {
+                uint32_t b[4];
+                load_b_kn<LD>(vt, kk * 16, dp * 16, b);
+                mma16816<F16>(o[2 * dp], pa, b[0], b[1]);
+                mma16816<F16>(o[2 * dp + 1], pa, b[2], b[3]);
+            }
+        }
+        __syncthreads();   // every warp is done with this buffer before it is refilled
     }
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
         const int row = q0 + warp * 16 + g + 8 * r;
         if (row >= n) continue;
-        const float inv = 1.f / l[r];
+        const float inv = 1.f / la[2 * r];
         uint32_t* orow = reinterpret_cast<uint32_t*>(o16 + (long)(start + row) * ldo16 + h * DH);
 #pragma unroll
         for (int j = 0; j < DH / 8; ++j) orow[(j * 8 + 2 * c) / 2] = pack_f16x2(o[j][2 * r] * inv, o[j][2 * r + 1] * inv);
@@ -474,13 +509,12 @@ bool attn_fwd16(int f16, const uint16_t* qkv16, uint16_t* o16, int ldo16, const 
                 int d, int heads, cudaStream_t st, int window) {
     if (n_events <= 0 || max_n <= 0) return true;
     const int dh = d / heads;
-    const float c2 = kLog2e / sqrtf((float)dh);
     dim3 grid((max_n + 127) / 128, heads, n_events);
 #define MLPF_ATTN16(DH)                                                                               \
     if (f16)                                                                                          \
-        k_attn_fwd16<DH, true><<<grid, 256, attn16_smem(DH), st>>>(qkv16, o16, ldo16, cu, d, c2, window); \
+        k_attn_fwd16<DH, true><<<grid, 256, attn16_smem(DH), st>>>(qkv16, o16, ldo16, cu, d, window); \
     else                                                                                              \
-        k_attn_fwd16<DH, false><<<grid, 256, attn16_smem(DH), st>>>(qkv16, o16, ldo16, cu, d, c2, window);
+        k_attn_fwd16<DH, false><<<grid, 256, attn16_smem(DH), st>>>(qkv16, o16, ldo16, cu, d, window);
     if (dh == 16) {
         MLPF_ATTN16(16)
     } else if (dh == 32) {

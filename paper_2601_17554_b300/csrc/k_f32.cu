@@ -3,6 +3,7 @@
 // the tensor-core path is measured against.  Also holds the per-event missing-pT
 // sum kernel shared by every precision.
 #include <cuda_runtime.h>
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 
@@ -552,20 +553,20 @@ int64_t run_forward_wide(Model& m, int prec, const float* x, const int32_t* cu, 
         ++n;
         if (cudaMemcpyAsync(w.z, w.hreg, (size_t)T * d * sizeof(float), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
             return -1;
-        stack("pid", c.l_pid, m.w.wqkv_pid, m.w.bqkv_pid, w.hpid);
+        stack("pid", c.l_pid, m.w.wqkv_pid, m.w.bqkv_wide_pid, w.hpid);
         if (cudaMemcpyAsync(w.z, w.hreg, (size_t)T * d * sizeof(float), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
             return -1;
-        stack("reg", c.l_reg, m.w.wqkv_reg, m.w.bqkv_reg, w.hreg);
+        stack("reg", c.l_reg, m.w.wqkv_reg, m.w.bqkv_wide_reg, w.hreg);
         mlp(w.hpid, d, "head.bin", logits, c.n_cls, 1);
         mlp(w.hpid, d, "head.pid", logits + 1, c.n_cls, c.n_cls - 1);
     } else {
         mlp(x, 42, "emb", w.z, d, d);
-        stack("pid", c.l_pid, m.w.wqkv_pid, m.w.bqkv_pid, w.hpid);
+        stack("pid", c.l_pid, m.w.wqkv_pid, m.w.bqkv_wide_pid, w.hpid);
         tlinear(m, nullptr, x, 42, 42, w.hpid, d, d, W("remb.w1"), W("remb.b1"), nullptr, 0, nullptr, 0, T, d, act, st,
                 n, ok, w.b16, Kd);
         tlinear(m, w.b16, nullptr, 0, d, nullptr, 0, 0, W("remb.w2"), W("remb.b2"), nullptr, 0, w.z, d, T, d, -1, st, n,
                 ok);
-        stack("reg", c.l_reg, m.w.wqkv_reg, m.w.bqkv_reg, w.hreg);
+        stack("reg", c.l_reg, m.w.wqkv_reg, m.w.bqkv_wide_reg, w.hreg);
         mlp(w.hpid, d, "head.cls", logits, c.n_cls, c.n_cls);
     }
     const char* names[4] = {"pt", "eta", "phi", "e"};
@@ -583,26 +584,55 @@ int64_t run_forward_wide(Model& m, int prec, const float* x, const int32_t* cu, 
     return n;
 }
 
+// v[i] *= s for i < n
+__global__ void k_scale_prefix(float* __restrict__ v, long n, float s) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) v[i] *= s;
+}
+
 // Two-term FP16 images of every weight matrix the wide path multiplies (the weight as
 // the sum of its FP16 rounding and the FP16 rounding of the remainder, about 22
 // significant bits: the rounding of a weight shifts every element's output alike, which
 // moves threshold decisions of a whole batch; activation roundings do not), each half
 // padded with zeros to a multiple of 64 columns, keyed by the FP32 tensor's device pointer.
+// The QKV images carry the Q rows times log2(e)/sqrt(dh), and so do the wide path's own
+// copies of the QKV biases: the attention kernel takes its base-2 softmax exponent
+// straight from Q K^T (one rounding of the scaled Q, in the GEMM's epilogue).
 bool wide_prepare_weights(Model& m) {
     std::vector<std::pair<const float*, std::pair<int, int>>> mats;   // pointer, (N, K)
     for (const auto& kv : m.host)
         if (kv.second.shape.size() == 2) mats.push_back({m.w.f32.at(kv.first), {kv.second.shape[0], kv.second.shape[1]}});
     const int d = m.cfg.d;
-    for (float* p : m.w.wqkv_pid) mats.push_back({p, {3 * d, d}});
-    for (float* p : m.w.wqkv_reg) mats.push_back({p, {3 * d, d}});
+    const float qscale = 1.4426950408889634f / sqrtf((float)(d / m.cfg.heads));
+    std::vector<const float*> qkv(m.w.wqkv_pid.begin(), m.w.wqkv_pid.end());
+    qkv.insert(qkv.end(), m.w.wqkv_reg.begin(), m.w.wqkv_reg.end());
+    for (const float* p : qkv) mats.push_back({p, {3 * d, d}});
     size_t total = 0;
     for (const auto& mt : mats) total += (size_t)mt.second.first * 2 * ((mt.second.second + 63) / 64 * 64);
     if (cudaMalloc(&m.w.w16_base, total * sizeof(uint16_t)) != cudaSuccess) return false;
+    // scaled QKV biases (kept) and one scaled QKV weight matrix at a time (scratch)
+    const size_t nb = qkv.size() * 3 * (size_t)d;
+    if (cudaMalloc(&m.w.wide_base, (nb + 3 * (size_t)d * d) * sizeof(float)) != cudaSuccess) return false;
+    float* wtmp = m.w.wide_base + nb;
+    for (size_t l = 0; l < qkv.size(); ++l) {
+        const bool pid = l < m.w.wqkv_pid.size();
+        const float* b = pid ? m.w.bqkv_pid[l] : m.w.bqkv_reg[l - m.w.wqkv_pid.size()];
+        float* bw = m.w.wide_base + l * 3 * d;
+        cudaMemcpy(bw, b, 3 * (size_t)d * sizeof(float), cudaMemcpyDeviceToDevice);
+        k_scale_prefix<<<cdiv(d, 256), 256>>>(bw, d, qscale);
+        (pid ? m.w.bqkv_wide_pid : m.w.bqkv_wide_reg).push_back(bw);
+    }
     size_t off = 0;
     for (const auto& mt : mats) {
         const int N = mt.second.first, K = mt.second.second, Kp = (K + 63) / 64 * 64;
         uint16_t* dst = m.w.w16_base + off;
-        cvt_16_split(mt.first, K, N, K, dst, Kp, 1, 0);
+        const float* src = mt.first;
+        if (std::find(qkv.begin(), qkv.end(), mt.first) != qkv.end()) {
+            cudaMemcpy(wtmp, mt.first, 3 * (size_t)d * d * sizeof(float), cudaMemcpyDeviceToDevice);
+            k_scale_prefix<<<cdiv(d * d, 256), 256>>>(wtmp, (long)d * d, qscale);
+            src = wtmp;
+        }
+        cvt_16_split(src, K, N, K, dst, Kp, 1, 0);
+        if (src == wtmp && cudaDeviceSynchronize() != cudaSuccess) return false;   // the scratch is reused
         m.w.w16[mt.first] = {dst, Kp};
         off += (size_t)N * 2 * Kp;
     }

@@ -1147,31 +1147,6 @@ MLPF_DEV void ffma2_bcast(float& d0, float& d1, float a0, float a1, float s, flo
     asm("mov.b64 {%0, %1}, %2;" : "=f"(d0), "=f"(d1) : "l"(d));
 }
 
-// 2^x0, 2^x1 packed in the 16-bit operand format: one packed MUFU operation on the
-// arguments rounded to that format (ex2.f16x2 / ex2.bf16x2, two results per
-// instruction).  For BF16 the rounding of the argument S - ref (at most 2^-8
-// relative) changes P by at most |S - ref| 2^-8 ln 2; the float64 emulation of the
-// BF16 mode shows no effect of it on the outputs (tests/lowp_emul.py, stage p_arg).
-template <bool F16>
-MLPF_DEV uint32_t exp2_pair(float x0, float x1) {
-    uint32_t p;
-    if constexpr (F16) {
-        const uint32_t h = pack_f16x2(x0, x1);
-        asm("ex2.approx.f16x2 %0, %1;" : "=r"(p) : "r"(h));
-    } else {
-        const uint32_t h = pack_bf16x2(x0, x1);
-        asm("ex2.approx.ftz.bf16x2 %0, %1;" : "=r"(p) : "r"(h));
-    }
-    return p;
-}
-
-// 2^x0, 2^x1 as two FP32 MUFU exponentials of the unrounded arguments, then packed
-// (rounded once) into the 16-bit operand format.
-template <bool F16>
-MLPF_DEV uint32_t exp2_pair_f32(float x0, float x1) {
-    return pack2<F16>(ex2_approx(x0), ex2_approx(x1));
-}
-
 MLPF_DEV bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* ab, unsigned* status,
                         uint64_t wait_ns) {
     const bool ok = mbar_wait(bar, parity, ab, status, ST_TIMEOUT_ATTN, wait_ns);
@@ -1774,7 +1749,7 @@ constexpr uint32_t PT_INFO_OFF = 448;
 static_assert((2 + 2 + 8 + 8 + 1 + 2 * NH * PT_NB + NH) * 8 <= PT_INFO_OFF, "PV-on-tcgen05 attention barriers");
 static_assert(PT_INFO_OFF % 16 == 0 && PT_INFO_OFF + 2 * 16 + 8 <= 512, "PV-on-tcgen05 attention info area");
 
-template <bool F16, int ST, bool XF = false>
+template <bool F16, int ST>
 __global__ void __launch_bounds__(PT_ATT_THREADS, 1)
     k_attention_pt(const __grid_constant__ CUtensorMap map_q, const __grid_constant__ CUtensorMap map_k,
                    const __grid_constant__ CUtensorMap map_vt, AttnParams p) {
@@ -1955,13 +1930,8 @@ __global__ void __launch_bounds__(PT_ATT_THREADS, 1)
                     uint32_t pa[4];
 #pragma unroll
                     for (int hr = 0; hr < 2; ++hr) {
-                        if constexpr (XF) {
-                            pa[hr] = exp2_pair_f32<F16>(sc[mt][0][2 * hr], sc[mt][0][2 * hr + 1]);
-                            pa[2 + hr] = exp2_pair_f32<F16>(sc[mt][1][2 * hr], sc[mt][1][2 * hr + 1]);
-                        } else {
-                            pa[hr] = exp2_pair<F16>(sc[mt][0][2 * hr], sc[mt][0][2 * hr + 1]);
-                            pa[2 + hr] = exp2_pair<F16>(sc[mt][1][2 * hr], sc[mt][1][2 * hr + 1]);
-                        }
+                        pa[hr] = exp2_pair<F16>(sc[mt][0][2 * hr], sc[mt][0][2 * hr + 1]);
+                        pa[2 + hr] = exp2_pair<F16>(sc[mt][1][2 * hr], sc[mt][1][2 * hr + 1]);
                     }
                     tmem_st16x128b_x2(pcol + ((uint32_t)(16 * mt) << 16) + 8 * q, pa);
                 }

@@ -315,6 +315,24 @@ MLPF_DEV uint32_t pack2(float lo, float hi) {
         return pack_bf16x2(lo, hi);
 }
 
+// 2^x0, 2^x1 packed in the 16-bit operand format: one packed MUFU operation on the
+// arguments rounded to that format (ex2.f16x2 / ex2.bf16x2, two results per
+// instruction).  For BF16 the rounding of the argument S - ref (at most 2^-8
+// relative) changes P by at most |S - ref| 2^-8 ln 2; the float64 emulation of the
+// BF16 mode shows no effect of it on the outputs (tests/lowp_emul.py, stage p_arg).
+template <bool F16>
+MLPF_DEV uint32_t exp2_pair(float x0, float x1) {
+    uint32_t p;
+    if constexpr (F16) {
+        const uint32_t h = pack_f16x2(x0, x1);
+        asm("ex2.approx.f16x2 %0, %1;" : "=r"(p) : "r"(h));
+    } else {
+        const uint32_t h = pack_bf16x2(x0, x1);
+        asm("ex2.approx.ftz.bf16x2 %0, %1;" : "=r"(p) : "r"(h));
+    }
+    return p;
+}
+
 // Packed 16-bit add of two pairs in the operand format (round to nearest).
 template <bool F16>
 MLPF_DEV uint32_t add2(uint32_t a, uint32_t b) {
