@@ -72,6 +72,8 @@ def parse():
                          "rule on N^2)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="approximate CPU time budget of the oracle sample")
+    ap.add_argument("--wide-attn-kernel", type=int, default=0, choices=[0, 1],
+                    help="generic-width models: 0 = warp-level attention (default), 1 = PV on tcgen05")
     ap.add_argument("--model", default="small", choices=sorted(MODELS),
                     help="architecture run on the batch (small: the workload's d=64 model)")
     return ap.parse_args()
@@ -460,6 +462,8 @@ def run_ours(args):
         model.calibrate_fp8(torch.from_numpy(cx).to(dev), torch.from_numpy(ccu).to(dev), int(csz.max()))
     if args.attn_window > 0:
         model.set_option(_lib.OPT_ATTN_WINDOW, args.attn_window)
+    if args.wide_attn_kernel:
+        model.set_option(_lib.OPT_WIDE_ATTN_KERNEL, args.wide_attn_kernel)
     # roofline denominators measured on this device (before anything is timed)
     from paper_2601_17554_b300 import measure_unit_rates
     unit_rates = measure_unit_rates(local)
@@ -548,7 +552,7 @@ def run_ours(args):
                  7: "k_attention_warp (QK^T on tcgen05)", 8: "k_attention_pt (PV on tcgen05)",
                  9: "k_attention_pt (PV on tcgen05)"}.get(attn_variant, "k_attention_tm")
         if wide:
-            kname = "k_attn_fwd16"
+            kname = "k_attn_wide_pt (PV on tcgen05)" if args.wide_attn_kernel else "k_attn_fwd16"
         roof = {"kernel": kname, "attn_variant": attn_variant, "bound": "alu", "achieved": ach / 1e9,
                 "peak": exp_peak / 1e9, "unit": "Gexp/s", "frac": ach / exp_peak,
                 "traffic": None if wide else attention_traffic(attn_variant, prec),
@@ -627,6 +631,8 @@ def run_ours(args):
                         "particles_per_batch": int((cl != 0).sum()),
                         "note": "anti-kt, E scheme, one CTA per event, O(N^2) per event with "
                                 "nearest-neighbour bookkeeping; latency-bound (one merge per step)"}
+    if args.wide_attn_kernel:
+        line["config"]["wide_attn_kernel"] = "PV and row sums on tcgen05"
     if args.attn_window > 0:
         # agreement with full attention on the same batch, and the full-attention time
         lw, rw, cw = lo.clone(), rg.clone(), cl.clone()

@@ -465,12 +465,20 @@ enum {
                                        forward and output copy run on three streams, so
                                        copies overlap the neighbouring chunks' compute.
                                        Batches under 65536 elements run as one chunk. */
-    MLPF_OPT_HOST_STREAMS = 13      /* mlpf_forward_host: compute streams the chunks
+    MLPF_OPT_HOST_STREAMS = 13,     /* mlpf_forward_host: compute streams the chunks
                                        alternate over, 1 or 2 (default 2).  With 2, odd
                                        chunks run on a second stream of the model with a
                                        second workspace (sized for the largest chunk), so
                                        a chunk's last attention items overlap the next
                                        chunk's kernels.  The results do not depend on it. */
+    MLPF_OPT_WIDE_ATTN_KERNEL = 14  /* models outside the fused d = 64 kernels (generic-width
+                                       tensor-core path): 0 (default) = the warp-level
+                                       attention kernel (every product on warp-level MMAs);
+                                       1 = the kernel with the PV products and row sums on
+                                       tcgen05 for heads of 16 or 32 in groups of four heads
+                                       (the warp-level kernel otherwise; slower on the
+                                       models measured).  Results differ only in rounding
+                                       (both are oracle-checked). */
 };
 #define MLPF_ATTN_VARIANTS 10
 mlpf_status mlpf_set_option(mlpf_model* m, int32_t option, int64_t value);

@@ -12,7 +12,7 @@ MLPF_OK, MLPF_E_INVALID, MLPF_E_FORMAT, MLPF_E_CUDA, MLPF_E_OOM, MLPF_E_TIMEOUT,
 MLPF_FP32, MLPF_BF16, MLPF_FP8, MLPF_FP16 = 0, 1, 2, 3
 OPT_USE_GRAPHS, OPT_WAIT_LIMIT_NS, OPT_DEBUG_STALL, OPT_ATTN_CTAS_PER_SM, OPT_ATTN_KV_STAGES, \
     OPT_PROFILE, OPT_ATTN_VARIANT_BF16, OPT_ATTN_VARIANT_FP16, OPT_ATTN_VARIANT_FP8, \
-    OPT_ATTN_WINDOW, OPT_GATE_CONFIDENCE, OPT_HOST_CHUNKS, OPT_HOST_STREAMS = range(1, 14)
+    OPT_ATTN_WINDOW, OPT_GATE_CONFIDENCE, OPT_HOST_CHUNKS, OPT_HOST_STREAMS, OPT_WIDE_ATTN_KERNEL = range(1, 15)
 
 # every symbol include/mlpf.h declares
 EXPORTS = ("mlpf_load_weights", "mlpf_free", "mlpf_get_config", "mlpf_forward",

@@ -906,6 +906,10 @@ mlpf_status mlpf_set_option(mlpf_model* mm, int32_t option, int64_t value) {
             if (value < 1 || value > 2) { set_error("host streams must be 1 or 2"); return MLPF_E_INVALID; }
             m.host_streams = (int)value;
             return MLPF_OK;   // host-side choice
+        case MLPF_OPT_WIDE_ATTN_KERNEL:
+            if (value < 0 || value > 1) { set_error("wide attention kernel must be 0 or 1"); return MLPF_E_INVALID; }
+            m.wide_attn_kernel = (int)value;
+            break;
         case MLPF_OPT_ATTN_VARIANT_BF16:
         case MLPF_OPT_ATTN_VARIANT_FP16:
         case MLPF_OPT_ATTN_VARIANT_FP8:
@@ -950,6 +954,7 @@ mlpf_status mlpf_get_option(const mlpf_model* mm, int32_t option, int64_t* value
         case MLPF_OPT_GATE_CONFIDENCE: *value = m.gate_confidence; return MLPF_OK;
         case MLPF_OPT_HOST_CHUNKS: *value = m.host_chunks; return MLPF_OK;
         case MLPF_OPT_HOST_STREAMS: *value = m.host_streams; return MLPF_OK;
+        case MLPF_OPT_WIDE_ATTN_KERNEL: *value = m.wide_attn_kernel; return MLPF_OK;
         default: set_error("unknown option " + std::to_string(option)); return MLPF_E_INVALID;
     }
 }

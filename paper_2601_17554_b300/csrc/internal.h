@@ -133,6 +133,7 @@ struct Model {
     // compute streams the chunks alternate over (2: odd chunks run on compute2 with
     // their own workspace ws_alt, so a chunk's attention tail overlaps the next chunk)
     int host_streams = 2;
+    int wide_attn_kernel = 0;   // MLPF_OPT_WIDE_ATTN_KERNEL: 0 warp-level, 1 PV on tcgen05
     cudaStream_t copy_in = nullptr, copy_out = nullptr, compute2 = nullptr;
     Workspace ws_alt;
     std::vector<cudaEvent_t> chunk_ev;   // [0] start, [1] copies out done, then 2 per chunk
@@ -242,7 +243,7 @@ bool attn_train_bwd_tc(int f16, const float* qkv, const float* dO, const float* 
 // Forward attention of the generic-width inference path on 16-bit Q | K | V [T, 3d] (FP16 if
 // f16, else BF16); writes O as FP16 rows of stride ldo16 (the next GEMM's operand).
 bool attn_fwd16(int f16, const uint16_t* qkv16, uint16_t* o16, int ldo16, const int32_t* cu, int n_events, int max_n,
-                int d, int heads, cudaStream_t st, int window);
+                int d, int heads, cudaStream_t st, int window, int kernel, unsigned* status, uint64_t wait_ns);
 void attn_fwd16_prepare();   // shared-memory attribute of the dh = 64 variant (outside capture)
 
 // tensor-core path preparation (weights images, tensor maps)

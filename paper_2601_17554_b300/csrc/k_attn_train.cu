@@ -455,6 +455,401 @@ __global__ void __launch_bounds__(256) k_attn_fwd16(const uint16_t* __restrict__
     }
 }
 
+// Generic-width attention with the PV products and the row sums on tcgen05 (heads of 16
+// or 32, a multiple of four heads): one CTA per (event, 128 query rows, four heads).  The
+// 16 consumer warps (warp 4 hl + rb: head hl of the group, query rows 32 rb .. 32 rb + 31,
+// tensor-memory lanes of the same quarter) stage Q, K and V with asynchronous copies,
+// compute S - ref with m16n8k16 MMAs (Q pre-scaled, the negated references as the
+// accumulator input), take P = 2^(S - ref) with packed exponentials and store it into
+// tensor memory with tcgen05.st.16x128b (the MMA A-fragment layout); each also transposes
+// its 16 keys of the head's V tile into a K-major, 128-byte-swizzled V^T tile.  One MMA
+// warp per head accumulates O_h += P_h V_h and l_h += P_h 1 per 64-key tile (tcgen05, P the
+// tensor-memory A operand, M 128, K 64); O and l stay in tensor memory until the item
+// ends.  P and V^T are double-buffered (tile j is written while the MMAs of tile j - 1
+// run).  References: the first tile's row maxima (its QK^T is computed twice), then raised
+// only when a 16-key step exceeds a row's reference by more than kRaise; such a raise
+// (rare) rescales the tile's P already stored and, once the previous tile's MMAs are
+// complete, the row's O and l in tensor memory.  On the legacy pipe only QK^T remains,
+// which binds this kernel at heads of 32 when PV runs there too.  Every wait is bounded.
+constexpr int WP_HG = 4;                           // heads per CTA
+constexpr int WP_THREADS = 16 * 32 + WP_HG * 32;   // 16 consumer warps, 4 MMA warps
+template <int DH>
+struct WpLayout {
+    static constexpr int LDQ = WP_HG * DH + 8;                        // staged row stride (elements)
+    static constexpr uint32_t Q = 0;                                  // [128][LDQ]
+    static constexpr uint32_t K = Q + 128 * LDQ * 2;                  // [2][64][LDQ]
+    static constexpr uint32_t V = K + 2 * 64 * LDQ * 2;               // [2][64][LDQ], row-major
+    static constexpr uint32_t VT = (V + 2 * 64 * LDQ * 2 + 1023) / 1024 * 1024;   // [2][HG][DH][128 B]
+    static constexpr uint32_t VTB = WP_HG * DH * 128;                 // one V^T buffer
+    static constexpr uint32_t ONES = VT + 2 * VTB;                    // [16][128 B]
+    static constexpr uint32_t BAR = ONES + 2048;                      // barriers and flags
+    static constexpr uint32_t SMEM = BAR + 256 + 1024;
+    static constexpr int TCOLS = 128;   // tensor-memory columns per head: P 2 x 32, O DH, l 16 (aligned)
+};
+
+// named barrier `id` of n threads that returns whether any thread passed pred = true
+__device__ __forceinline__ bool bar_any(int id, int n, bool pred) {
+    uint32_t r;
+    asm volatile("{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.or.pred q, %2, %3, p;\n\t"
+                 "selp.u32 %0, 1, 0, q;\n\t}"
+                 : "=r"(r)
+                 : "r"((uint32_t)pred), "r"(id), "r"(n)
+                 : "memory");
+    return r != 0;
+}
+
+template <int DH, bool F16>
+__global__ void __launch_bounds__(WP_THREADS, 1)
+    k_attn_wide_pt(const uint16_t* __restrict__ qkv16, uint16_t* __restrict__ o16, int ldo16,
+                   const int32_t* __restrict__ cu, int d, int window, unsigned* status, uint64_t wait_ns) {
+    using LY = WpLayout<DH>;
+    constexpr int LDQ = LY::LDQ, CH = WP_HG * DH / 8;   // 16-byte chunks per staged row
+    constexpr float kRaise = 4.f;
+    static_assert(WP_HG * LY::TCOLS <= 512 && 64 + DH + 16 <= LY::TCOLS, "tensor-memory columns");
+    extern __shared__ uint8_t wp_raw[];
+    uint8_t* sm = (uint8_t*)(((uintptr_t)wp_raw + 1023) & ~(uintptr_t)1023);
+    uint16_t* Qs = (uint16_t*)(sm + LY::Q);
+    auto Ks = [&](int b) { return (uint16_t*)(sm + LY::K) + b * 64 * LDQ; };
+    auto Vs = [&](int b) { return (uint16_t*)(sm + LY::V) + b * 64 * LDQ; };
+    uint8_t* VT = sm + LY::VT;
+    uint64_t* bars = (uint64_t*)(sm + LY::BAR);
+    uint64_t* p_full = bars;              // [head][buffer]: one arrival per warp of the head
+    uint64_t* p_free = bars + 8;          // [head][buffer]: MMA commit
+    uint64_t* drain = bars + 16;          // [head]: the MMA warp's exit
+    int* abort_flag = (int*)(bars + 20);
+    uint32_t* tmem_hold = (uint32_t*)(abort_flag + 1);
+    volatile int* ab = abort_flag;
+    const int e = blockIdx.z, hg = blockIdx.y;
+    const int start = cu[e], n = cu[e + 1] - start, q0 = blockIdx.x * 128;
+    if (q0 >= n) return;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long ld = 3L * d;
+    int kbeg = 0, kend = n;
+    if (window > 0) {
+        const int y = q0 / 128;
+        kbeg = max(0, (y - window) * 128);
+        kend = min(n, (y + window + 1) * 128);
+    }
+    const int nk = (kend - kbeg + 63) / 64;
+    if (tid == 0) {
+        for (int i = 0; i < 8; ++i) { mbar_init(&p_full[i], 4); mbar_init(&p_free[i], 1); }
+        for (int i = 0; i < WP_HG; ++i) mbar_init(&drain[i], 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    {   // the B operand of the row sums: 16 rows x 64 keys of ones
+        const uint32_t one2 = F16 ? 0x3C003C00u : 0x3F803F80u;
+        for (int i = tid; i < 512; i += WP_THREADS) ((uint32_t*)(sm + LY::ONES))[i] = one2;
+        fence_proxy_async_smem();
+    }
+    if (warp == 0) {
+        tmem_alloc(tmem_hold, 512);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = *tmem_hold;
+    auto colP = [](int hl, int b) { return (uint32_t)(hl * LY::TCOLS + 32 * b); };
+    auto colO = [](int hl) { return (uint32_t)(hl * LY::TCOLS + 64); };
+    auto vt_buf = [&](int b, int hl) { return VT + b * LY::VTB + hl * DH * 128; };
+
+    if (warp >= 16) {
+        // ------------------------------------------------ PV and row-sum MMAs of head hl
+        const int hl = warp - 16;
+        if (lane == 0) {
+            const uint32_t IPV = idesc_f16(128, DH, F16 ? 0u : 1u), IL = idesc_f16(128, 16, F16 ? 0u : 1u);
+            const uint32_t onesa = smem_u32(sm + LY::ONES);
+            for (int j = 0; j < nk; ++j) {
+                const int b = j & 1;
+                if (!mbar_wait(&p_full[2 * hl + b], (j >> 1) & 1, ab, status, ST_TIMEOUT_ATTN, wait_ns)) break;
+                tc_fence_after();
+                const uint32_t pa = tbase + colP(hl, b), od = tbase + colO(hl);
+                const uint32_t va = smem_u32(vt_buf(b, hl));
+#pragma unroll
+                for (int kc = 0; kc < 4; ++kc) {
+                    const uint32_t acc = (j > 0 || kc > 0) ? 1u : 0u;
+                    mma_f16_ts(od, pa + 8 * kc, sdesc_sw128(va + kc * 32), IPV, acc);
+                    mma_f16_ts(od + DH, pa + 8 * kc, sdesc_sw128(onesa + kc * 32), IL, acc);
+                }
+                mma_commit(&p_free[2 * hl + b]);
+            }
+            mma_commit(&drain[hl]);
+            mbar_drain(&drain[hl], 0, wait_ns);
+        }
+    } else {
+        // ------------------------------------------------ consumer warp: head hl, rows 32 rb ..
+        const int hl = warp >> 2, rb = warp & 3;
+        const int c = lane & 3;
+        const uint32_t tlane = tbase + ((uint32_t)(32 * rb) << 16);
+        // rows r0 .. r0 + rows - 1 of the group's columns col0 .. (rows at or beyond lim are zero)
+        auto stage = [&](uint16_t* dst, int rows, int r0, int lim, int col0) {
+            for (int i = tid; i < rows * CH; i += 512) {
+                const int r = i / CH, ch = i % CH;
+                const bool in = r0 + r < lim;
+                const uint16_t* src = qkv16 + (long)(start + (in ? r0 + r : 0)) * ld + col0 + ch * 8;
+                cp_async16(dst + r * LDQ + ch * 8, src, in ? 16u : 0u);
+            }
+        };
+        const int gcol = hg * WP_HG * DH;
+        stage(Qs, 128, q0, n, gcol);
+        stage(Ks(0), 64, kbeg, kend, d + gcol);
+        stage(Vs(0), 64, kbeg, kend, 2 * d + gcol);
+        cp_async_commit();
+        float nr[2][4];
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) nr[mt][u] = 0.f;
+        uint32_t qa[2][DH / 16][4];
+        bool ok = true;
+        // S - ref of keys 16 q .. 16 q + 15 of the staged tile kt (two 8-key column tiles)
+        auto qk = [&](const uint16_t* kt, int q, float (&s)[2][2][4]) {
+#pragma unroll
+            for (int kk = 0; kk < DH / 16; ++kk) {
+                uint32_t b[4];
+                load_b_nk<LDQ>(kt, 16 * q, hl * DH + 16 * kk, b);
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt) {
+                    mma16816_c<F16>(s[mt][0], qa[mt][kk], b[0], b[1], kk == 0 ? nr[mt] : s[mt][0]);
+                    mma16816_c<F16>(s[mt][1], qa[mt][kk], b[2], b[3], kk == 0 ? nr[mt] : s[mt][1]);
+                }
+            }
+        };
+        auto mask = [&](int q, int kvalid, float (&s)[2][2][4]) {
+            if (16 * (q + 1) > kvalid) {
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+                            if (16 * q + 8 * nt + 2 * c + (u & 1) >= kvalid) s[mt][nt][u] = -INFINITY;
+            }
+        };
+        // row maxima of a step (rows g, g + 8 of each 16-row block), over the quad
+        auto rowmax = [&](const float (&s)[2][2][4], float (&mx)[2][2]) {
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                for (int hr = 0; hr < 2; ++hr) {
+                    float m = fmaxf(fmaxf(s[mt][0][2 * hr], s[mt][0][2 * hr + 1]),
+                                    fmaxf(s[mt][1][2 * hr], s[mt][1][2 * hr + 1]));
+                    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
+                    mx[mt][hr] = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
+                }
+        };
+        auto pack_p = [&](const float (&s)[2][2][4], int mt, uint32_t (&pa)[4]) {
+#pragma unroll
+            for (int hr = 0; hr < 2; ++hr) {
+                pa[hr] = exp2_pair<F16>(s[mt][0][2 * hr], s[mt][0][2 * hr + 1]);
+                pa[2 + hr] = exp2_pair<F16>(s[mt][1][2 * hr], s[mt][1][2 * hr + 1]);
+            }
+        };
+        for (int j = 0; j < nk && ok; ++j) {
+            const int kb = kbeg + 64 * j, b = j & 1, kvalid = kend - kb;
+            if (j + 1 < nk) {
+                stage(Ks(b ^ 1), 64, kb + 64, kend, d + gcol);
+                stage(Vs(b ^ 1), 64, kb + 64, kend, 2 * d + gcol);
+            }
+            cp_async_commit();
+            cp_async_wait<1>();
+            if (bar_any(1, 512, !ok)) break;   // a failed wait anywhere: every consumer leaves
+            if (j == 0) {
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                    for (int kk = 0; kk < DH / 16; ++kk) load_a<LDQ>(Qs, 32 * rb + 16 * mt, hl * DH + 16 * kk, qa[mt][kk]);
+            }
+            // P and V^T of buffer b: the MMAs of tile j - 2 are complete
+            if (j >= 2) {
+                ok = __all_sync(0xffffffffu, mbar_wait(&p_free[2 * hl + b], ((j >> 1) - 1) & 1, ab, status,
+                                                        ST_TIMEOUT_ATTN, wait_ns));
+                tc_fence_after();
+            }
+            if (ok) {
+            // V^T of this warp's 16 keys: transposed 8 x 8 blocks (keys 16 rb + 8 kb2, channels
+            // 8 cb) land as pairs of keys of one channel, stored into the swizzled K-major tile
+            {
+                const uint16_t* vs = Vs(b);
+                uint8_t* vt = vt_buf(b, hl);
+#pragma unroll
+                for (int blk = 0; blk < DH / 8 * 2; blk += 4) {
+                    const int mi = blk + (lane >> 3);               // this lane's matrix
+                    const int kb2 = mi & 1, cb = mi >> 1;
+                    const uint16_t* src = vs + (16 * rb + 8 * kb2 + (lane & 7)) * LDQ + hl * DH + 8 * cb;
+                    uint32_t r[4];
+                    ldsm_x4_t(smem_u32(src), r[0], r[1], r[2], r[3]);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int m2 = blk + i, kb3 = m2 & 1, cb3 = m2 >> 1;
+                        const int ch = 8 * cb3 + (lane >> 2);             // channel = V^T row
+                        const int chunk = 2 * rb + kb3;                    // 16-byte chunk of 8 keys
+                        *(uint32_t*)(vt + ch * 128 + ((chunk ^ (ch & 7)) << 4) + 4 * (lane & 3)) = r[i];
+                    }
+                }
+            }
+            const uint16_t* kt = Ks(b);
+            const uint32_t pcol = tlane + colP(hl, b);
+            if (j == 0) {
+                // the first tile sets the references to its row maxima
+                float mx[2][2] = {{-INFINITY, -INFINITY}, {-INFINITY, -INFINITY}};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (16 * q >= kvalid) break;
+                    float s[2][2][4], m2[2][2];
+                    qk(kt, q, s);
+                    mask(q, kvalid, s);
+                    rowmax(s, m2);
+#pragma unroll
+                    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                        for (int hr = 0; hr < 2; ++hr) mx[mt][hr] = fmaxf(mx[mt][hr], m2[mt][hr]);
+                }
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                    for (int hr = 0; hr < 2; ++hr) {
+                        nr[mt][2 * hr] = -mx[mt][hr];
+                        nr[mt][2 * hr + 1] = -mx[mt][hr];
+                    }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                float s[2][2][4];
+                if (16 * q < kvalid) {
+                    qk(kt, q, s);
+                    mask(q, kvalid, s);
+                } else {
+#pragma unroll
+                    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                        for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) s[mt][nt][u] = -INFINITY;
+                }
+                if (j > 0 && 16 * q < kvalid) {
+                    // a raise is needed when any score of the warp exceeds its reference by
+                    // more than kRaise: this thread's maximum and one vote; the rows' maxima
+                    // only then
+                    float tm = -INFINITY;
+#pragma unroll
+                    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                        for (int nt = 0; nt < 2; ++nt)
+                            tm = fmaxf(tm, fmaxf(fmaxf(s[mt][nt][0], s[mt][nt][1]), fmaxf(s[mt][nt][2], s[mt][nt][3])));
+                    if (__any_sync(0xffffffffu, tm > kRaise)) {
+                        float mx[2][2];
+                        rowmax(s, mx);
+                        // raise the rows' references by dr >= 0; P of this tile's earlier
+                        // steps, O and l (after the previous tile's MMAs) scale by 2^-dr
+                        float al[2][2];
+#pragma unroll
+                        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                            for (int hr = 0; hr < 2; ++hr) {
+                                const float dr = fmaxf(mx[mt][hr], 0.f);
+                                al[mt][hr] = ex2_approx(-dr);
+                                nr[mt][2 * hr] -= dr;
+                                nr[mt][2 * hr + 1] -= dr;
+#pragma unroll
+                                for (int nt = 0; nt < 2; ++nt) {
+                                    s[mt][nt][2 * hr] -= dr;
+                                    s[mt][nt][2 * hr + 1] -= dr;
+                                }
+                            }
+                        for (int q2 = 0; q2 < q; ++q2)
+#pragma unroll
+                            for (int mt = 0; mt < 2; ++mt) {
+                                const uint32_t a = pcol + ((uint32_t)(16 * mt) << 16) + 8 * q2;
+                                uint32_t u[4];
+                                tmem_ld16x128b_x2(a, u);
+                                tmem_wait_ld();
+#pragma unroll
+                                for (int i = 0; i < 4; ++i) {
+                                    float x0, x1;
+                                    unpack2<F16>(u[i], x0, x1);
+                                    const float f = al[mt][i & 1];   // registers 0, 2: row g; 1, 3: row g + 8
+                                    u[i] = pack2<F16>(x0 * f, x1 * f);
+                                }
+                                tmem_st16x128b_x2(a, u);
+                            }
+                        ok = __all_sync(0xffffffffu, mbar_wait(&p_free[2 * hl + (b ^ 1)], ((j - 1) >> 1) & 1, ab,
+                                                                status, ST_TIMEOUT_ATTN, wait_ns));
+                        if (!ok) break;
+                        tc_fence_after();
+                        // the factor of row `lane` (block lane / 16, half (lane / 8) & 1,
+                        // fragment row lane & 7) is held by fragment lane 4 (lane & 7)
+                        const int src = 4 * (lane & 7);
+                        const float f00 = __shfl_sync(0xffffffffu, al[0][0], src);
+                        const float f01 = __shfl_sync(0xffffffffu, al[0][1], src);
+                        const float f10 = __shfl_sync(0xffffffffu, al[1][0], src);
+                        const float f11 = __shfl_sync(0xffffffffu, al[1][1], src);
+                        const float f = lane < 16 ? (lane < 8 ? f00 : f01) : (lane < 24 ? f10 : f11);
+                        // O and l, 16 columns at a time
+#pragma unroll 1
+                        for (int c16 = 0; c16 < DH + 16; c16 += 16) {
+                            float ol[16];
+                            tmem_ld16(tlane + colO(hl) + c16, ol);
+                            tmem_wait_ld();
+                            uint32_t uo[16];
+#pragma unroll
+                            for (int i = 0; i < 16; ++i) uo[i] = __float_as_uint(ol[i] * f);
+                            tmem_st16(tlane + colO(hl) + c16, uo);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt) {
+                    uint32_t pa[4];
+                    pack_p(s, mt, pa);
+                    tmem_st16x128b_x2(pcol + ((uint32_t)(16 * mt) << 16) + 8 * q, pa);
+                }
+            }
+            }
+            if (ok) {   // publish P and V^T of tile j to the head's MMA warp
+                fence_proxy_async_smem();
+                tmem_wait_st();
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&p_full[2 * hl + b]);
+            }
+            // every consumer is done with K(j), V(j) before they are refilled
+            if (bar_any(1, 512, !ok)) break;
+        }
+        if (ok) {
+            // the item's output: O / l of row `lane` of this warp
+            const int jl = nk - 1;
+            ok = mbar_wait(&p_free[2 * hl + (jl & 1)], (jl >> 1) & 1, ab, status, ST_TIMEOUT_ATTN, wait_ns);
+            if (__all_sync(0xffffffffu, ok)) {
+                tc_fence_after();
+                float ol[DH + 16];
+                if constexpr (DH == 32) {
+                    tmem_ld32(tlane + colO(hl), ol);
+                    tmem_ld16(tlane + colO(hl) + 32, ol + 32);
+                } else {
+                    tmem_ld32(tlane + colO(hl), ol);
+                }
+                tmem_wait_ld();
+                const int row = q0 + 32 * rb + lane;
+                if (row < n) {
+                    const float inv = 1.f / ol[DH];
+                    uint32_t* orow = reinterpret_cast<uint32_t*>(o16 + (long)(start + row) * ldo16 + hg * WP_HG * DH + hl * DH);
+#pragma unroll
+                    for (int i = 0; i < DH / 2; ++i) orow[i] = pack_f16x2(ol[2 * i] * inv, ol[2 * i + 1] * inv);
+                }
+            }
+        }
+        tmem_wait_st();
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tbase, 512);
+    }
+}
+
 template <bool F16>
 bool attn_tc_launch(int which, const float* qkv, const float* dO, float* out, float* lse, const float* D,
                     float* dqkv, const int32_t* cu, int n_events, int max_n, int d, int heads, cudaStream_t st,
@@ -502,13 +897,35 @@ void attn_fwd16_prepare() {
     if (dev < 0 || dev >= 64 || done[dev]) return;
     cudaFuncSetAttribute(k_attn_fwd16<64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, attn16_smem(64));
     cudaFuncSetAttribute(k_attn_fwd16<64, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, attn16_smem(64));
+    cudaFuncSetAttribute(k_attn_wide_pt<16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, WpLayout<16>::SMEM);
+    cudaFuncSetAttribute(k_attn_wide_pt<16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, WpLayout<16>::SMEM);
+    cudaFuncSetAttribute(k_attn_wide_pt<32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, WpLayout<32>::SMEM);
+    cudaFuncSetAttribute(k_attn_wide_pt<32, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, WpLayout<32>::SMEM);
     done[dev] = true;
 }
 
 bool attn_fwd16(int f16, const uint16_t* qkv16, uint16_t* o16, int ldo16, const int32_t* cu, int n_events, int max_n,
-                int d, int heads, cudaStream_t st, int window) {
+                int d, int heads, cudaStream_t st, int window, int kernel, unsigned* status, uint64_t wait_ns) {
     if (n_events <= 0 || max_n <= 0) return true;
     const int dh = d / heads;
+    if (kernel == 1 && (dh == 16 || dh == 32) && heads % WP_HG == 0) {
+        // PV and row sums on tcgen05
+        dim3 gp((max_n + 127) / 128, heads / WP_HG, n_events);
+#define MLPF_ATTN_PT(DH)                                                                                            \
+    if (f16)                                                                                                        \
+        k_attn_wide_pt<DH, true><<<gp, WP_THREADS, WpLayout<DH>::SMEM, st>>>(qkv16, o16, ldo16, cu, d, window, status, \
+                                                                            wait_ns);                              \
+    else                                                                                                            \
+        k_attn_wide_pt<DH, false><<<gp, WP_THREADS, WpLayout<DH>::SMEM, st>>>(qkv16, o16, ldo16, cu, d, window,       \
+                                                                             status, wait_ns);
+        if (dh == 16) {
+            MLPF_ATTN_PT(16)
+        } else {
+            MLPF_ATTN_PT(32)
+        }
+#undef MLPF_ATTN_PT
+        return true;
+    }
     dim3 grid((max_n + 127) / 128, heads, n_events);
 #define MLPF_ATTN16(DH)                                                                               \
     if (f16)                                                                                          \

@@ -523,7 +523,8 @@ int64_t run_forward_wide(Model& m, int prec, const float* x, const int32_t* cu, 
             tlinear(m, w.a16, nullptr, 0, d, nullptr, 0, 0, wqkv[l], bqkv[l], nullptr, 0, nullptr, 0, T, 3 * d, -1, st,
                     n, ok, w.qkv16, 3 * d, prec == MLPF_FP16);
             prof_begin(m, st, "wide_attention");
-            if (!attn_fwd16(prec == MLPF_FP16, w.qkv16, w.a16, Kd, cu, n_events, max_n, d, c.heads, st, m.attn_window))
+            if (!attn_fwd16(prec == MLPF_FP16, w.qkv16, w.a16, Kd, cu, n_events, max_n, d, c.heads, st, m.attn_window,
+                            m.wide_attn_kernel, m.status, WIDE_WAIT_NS))
                 ok = false;
             prof_end(m, st);
             ++n;

@@ -206,19 +206,6 @@ MLPF_DEV void st_global_row64(uint16_t* dst, const float* v) {
     }
 }
 
-// 16-bit pair -> two floats
-template <bool F16>
-MLPF_DEV void unpack2(uint32_t u, float& a, float& b) {
-    if constexpr (F16) {
-        const __half2 h = *reinterpret_cast<const __half2*>(&u);
-        const float2 f = __half22float2(h);
-        a = f.x;
-        b = f.y;
-    } else {
-        a = __uint_as_float(u << 16);
-        b = __uint_as_float(u & 0xffff0000u);
-    }
-}
 
 // Record max |v| of valid rows into amax[slot] (calibration of FP8 scales).
 MLPF_DEV void record_amax(unsigned* amax, int slot, const float* v, int n, bool valid) {
@@ -1863,7 +1850,7 @@ __global__ void __launch_bounds__(PT_ATT_THREADS, 1)
     } else {
         // ------------------------------------------------ warp: head h, query rows 32 rb .. 32 rb + 31
         const int h = warp / RB, rb = warp % RB;
-        const int gq = lane >> 2, tq = lane & 3;
+        const int tq = lane & 3;
         const int mi = lane >> 3;
         const uint32_t sQa = smem_u32(sQ), sKa = smem_u32(sK);
         const int k_row = (lane & 7) + 8 * (mi >> 1), k_chunk = 2 * h + (mi & 1);

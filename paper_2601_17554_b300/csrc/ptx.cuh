@@ -4,6 +4,7 @@
 #pragma once
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cstdint>
 
 #define MLPF_DEV __device__ __forceinline__
@@ -285,6 +286,13 @@ MLPF_DEV void tmem_st16x128b_x2(uint32_t taddr, const uint32_t* v) {
     asm volatile("tcgen05.st.sync.aligned.16x128b.x2.b32 [%0], {%1,%2,%3,%4};" ::"r"(taddr), "r"(v[0]),
                  "r"(v[1]), "r"(v[2]), "r"(v[3]));
 }
+// TMEM -> registers in the same 16x128b.x2 layout (lanes g and g + 8 of the 16-lane block,
+// columns c and 4 + c of 8 consecutive columns)
+MLPF_DEV void tmem_ld16x128b_x2(uint32_t taddr, uint32_t* v) {
+    asm volatile("tcgen05.ld.sync.aligned.16x128b.x2.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
+                 : "r"(taddr));
+}
 MLPF_DEV void tmem_wait_st() {
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
@@ -331,6 +339,20 @@ MLPF_DEV uint32_t exp2_pair(float x0, float x1) {
         asm("ex2.approx.ftz.bf16x2 %0, %1;" : "=r"(p) : "r"(h));
     }
     return p;
+}
+
+// 16-bit pair in the operand format (F16 or BF16) -> two floats
+template <bool F16>
+MLPF_DEV void unpack2(uint32_t u, float& a, float& b) {
+    if constexpr (F16) {
+        const __half2 h = *reinterpret_cast<const __half2*>(&u);
+        const float2 f = __half22float2(h);
+        a = f.x;
+        b = f.y;
+    } else {
+        a = __uint_as_float(u << 16);
+        b = __uint_as_float(u & 0xffff0000u);
+    }
 }
 
 // Packed 16-bit add of two pairs in the operand format (round to nearest).

@@ -65,8 +65,9 @@ def test_paper_arch_sampled_full_workload(paper_model):
         np.testing.assert_array_equal(cl[sl][keep], ref.cls[sl][keep])
 
 
+@pytest.mark.parametrize("kernel", [0, 1])
 @pytest.mark.parametrize("prec", ["bf16", "fp16"])
-def test_paper_arch_tensor_cores(paper_model, prec):
+def test_paper_arch_tensor_cores(paper_model, prec, kernel):
     """The generic-width tensor-core path.  This architecture decides the class by a
     threshold on the binary logit (then the PID argmax), and the weight seed makes both
     decisions common: 35 of these 2994 elements (1.2 %) lie within 2e-3 of a decision
@@ -74,10 +75,16 @@ def test_paper_arch_tensor_cores(paper_model, prec):
     A float64 forward that only rounds the GEMM activations to FP16 (weights exact)
     already flips 2 of the 2994 (99.93 %).  So every element whose margins exceed 2e-3
     must agree, the raw agreement must reach 99.8 %, and the regression error stays
-    within 1e-2 per column."""
+    within 1e-2 per column.  Both attention kernels of the path (heads of 16): warp-level
+    MMAs (kernel 0) and PV on tcgen05 (kernel 1)."""
+    from paper_2601_17554_b300._lib import OPT_WIDE_ATTN_KERNEL
     model, w = paper_model
     x, cu = synth.gen_events(31, [300, 1, 129, 700, 0, 64, 1800])
-    lo, rg, cl, su = run_gpu(model, x, cu, prec)
+    model.set_option(OPT_WIDE_ATTN_KERNEL, kernel)
+    try:
+        lo, rg, cl, su = run_gpu(model, x, cu, prec)
+    finally:
+        model.set_option(OPT_WIDE_ATTN_KERNEL, 0)
     ref = oracle.forward(w, synth.PAPER, x, cu)
     assert np.isfinite(lo).all() and np.isfinite(rg).all()
     top2 = np.sort(ref.logits[:, 1:], axis=1)[:, -2:]
@@ -85,7 +92,7 @@ def test_paper_arch_tensor_cores(paper_model, prec):
     decisive = (np.abs(ref.logits[:, 0]) > 2e-3) & ((ref.logits[:, 0] <= 0) | (pid_margin > 2e-3))
     agree = (cl == ref.cls).mean()
     e_rg = rel_err_cols(rg, ref.reg)
-    print(f"{prec}: agreement {agree:.5f} over {len(cl)} ({(~decisive).sum()} near a boundary), "
+    print(f"{prec} kernel {kernel}: agreement {agree:.5f} over {len(cl)} ({(~decisive).sum()} near a boundary), "
           f"regression errors {np.round(e_rg, 5)}")
     np.testing.assert_array_equal(cl[decisive], ref.cls[decisive])
     assert agree >= 0.998, agree

@@ -6,7 +6,9 @@ oracle, at the bounds of the 16-bit path: >= 99.9 % per-element argmax agreement
 owes by construction: graph replay equals direct launches bitwise, an event alone
 equals the same event inside a batch bitwise (every GEMM row and attention row is
 computed independently of its neighbours), windowed attention matches the oracle's
-windowed forward, and FP8 is refused.
+windowed forward, and FP8 is refused.  Both attention kernels of the path run: the one
+with the PV products on tcgen05 (MLPF_OPT_WIDE_ATTN_KERNEL = 1) and the warp-level
+one (MLPF_OPT_WIDE_ATTN_KERNEL = 0, the default).
 """
 import dataclasses
 
@@ -38,14 +40,48 @@ def full_model():
     return make_model(synth.FULL, 1, perturbed=True)
 
 
+def _with_kernel(model, kernel, fn):
+    from paper_2601_17554_b300._lib import OPT_WIDE_ATTN_KERNEL
+    model.set_option(OPT_WIDE_ATTN_KERNEL, kernel)
+    assert model.get_option(OPT_WIDE_ATTN_KERNEL) == kernel
+    try:
+        return fn()
+    finally:
+        model.set_option(OPT_WIDE_ATTN_KERNEL, 0)
+
+
+# attention kernels of the path: 0 = every product on warp-level MMAs (default), 1 = PV
+# and row sums on tcgen05 (heads of 16 or 32 in groups of four)
+@pytest.mark.parametrize("kernel", [0, 1])
 @pytest.mark.parametrize("prec", ["bf16", "fp16"])
-def test_full_size_model(full_model, prec):
+def test_full_size_model(full_model, prec, kernel):
     model, w = full_model
     x, cu = synth.gen_events(102, [700, 1, 129, 2100, 64, 0, 300])
-    out = run_gpu(model, x, cu, prec)
+    out = _with_kernel(model, kernel, lambda: run_gpu(model, x, cu, prec))
     ref = oracle.forward(w, synth.FULL, x, cu)
     check_lowp(out, ref)
     assert out[3][5].tolist() == [0.0, 0.0, 0.0]
+
+
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_sharpened_attention(kernel):
+    """The full-size model with its Q and K projections scaled by 2 (scores four times
+    the model's): the running references are raised within and between key tiles, which
+    the tcgen05 kernel handles by rescaling the tile's stored P and the row's O and l in
+    tensor memory.  Both kernels against the oracle."""
+    from paper_2601_17554_b300 import Model
+    w = synth.make_weights(synth.FULL, 1, perturbed=True)
+    for stack, n in (("pid", synth.FULL.l_pid), ("reg", synth.FULL.l_reg)):
+        for l in range(n):
+            for t in ("wq", "bq", "wk", "bk"):
+                w[f"{stack}.{l}.{t}"] = w[f"{stack}.{l}.{t}"] * 2.0
+    model = Model(synth.pack_blob(synth.FULL, w))
+    x, cu = synth.gen_events(107, [1500, 129, 700])
+    ref = oracle.forward(w, synth.FULL, x, cu)
+    for prec in ("bf16", "fp16"):
+        out = _with_kernel(model, kernel, lambda: run_gpu(model, x, cu, prec))
+        check_lowp(out, ref, argmax_min=0.995)
+    model.close()
 
 
 def test_full_size_workload_sampled(full_model):
@@ -65,11 +101,12 @@ def test_full_size_workload_sampled(full_model):
     check_lowp((sub(lo), sub(rg), sub(cl), None), R)
 
 
+@pytest.mark.parametrize("kernel", [0, 1])
 @pytest.mark.parametrize("prec", ["bf16", "fp16"])
-def test_student_model(prec):
+def test_student_model(prec, kernel):
     model, w = make_model(STUDENT, 2, perturbed=True)
     x, cu = synth.gen_events(103, [1500, 2, 640, 129])
-    out = run_gpu(model, x, cu, prec)
+    out = _with_kernel(model, kernel, lambda: run_gpu(model, x, cu, prec))
     check_lowp(out, oracle.forward(w, STUDENT, x, cu))
     model.close()
 
@@ -94,13 +131,14 @@ def test_graph_replay_and_batch_invariance(full_model):
     np.testing.assert_array_equal(c[1], a[1][cu[2]:cu[3]])
 
 
-def test_windowed_attention(full_model):
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_windowed_attention(full_model, kernel):
     from paper_2601_17554_b300 import OPT_ATTN_WINDOW
     model, w = full_model
     x, cu = synth.gen_events(105, [700, 129, 1000])
     model.set_option(OPT_ATTN_WINDOW, 2)   # 128-row blocks +- 2 in eta order
     try:
-        out = run_gpu(model, x, cu, "bf16")
+        out = _with_kernel(model, kernel, lambda: run_gpu(model, x, cu, "bf16"))
     finally:
         model.set_option(OPT_ATTN_WINDOW, 0)
     check_lowp(out, oracle.forward(w, synth.FULL, x, cu, window=2))
