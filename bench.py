@@ -72,8 +72,9 @@ def parse():
                          "rule on N^2)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="approximate CPU time budget of the oracle sample")
-    ap.add_argument("--wide-attn-kernel", type=int, default=0, choices=[0, 1],
-                    help="generic-width models: 0 = warp-level attention (default), 1 = PV on tcgen05")
+    ap.add_argument("--wide-attn-kernel", type=int, default=None, choices=[0, 1],
+                    help="generic-width models: 0 = warp-level attention, 1 = PV on tcgen05 "
+                         "(default: autotuned on the batch)")
     ap.add_argument("--model", default="small", choices=sorted(MODELS),
                     help="architecture run on the batch (small: the workload's d=64 model)")
     return ap.parse_args()
@@ -462,8 +463,6 @@ def run_ours(args):
         model.calibrate_fp8(torch.from_numpy(cx).to(dev), torch.from_numpy(ccu).to(dev), int(csz.max()))
     if args.attn_window > 0:
         model.set_option(_lib.OPT_ATTN_WINDOW, args.attn_window)
-    if args.wide_attn_kernel:
-        model.set_option(_lib.OPT_WIDE_ATTN_KERNEL, args.wide_attn_kernel)
     # roofline denominators measured on this device (before anything is timed)
     from paper_2601_17554_b300 import measure_unit_rates
     unit_rates = measure_unit_rates(local)
@@ -475,6 +474,10 @@ def run_ours(args):
         if prec != "fp32":
             model.set_option({"bf16": _lib.OPT_ATTN_VARIANT_BF16, "fp16": _lib.OPT_ATTN_VARIANT_FP16,
                               "fp8": _lib.OPT_ATTN_VARIANT_FP8}[prec], attn_variant)
+    # generic-width models: the attention kernel kept by the autotuner, unless fixed
+    if args.wide_attn_kernel is not None:
+        model.set_option(_lib.OPT_WIDE_ATTN_KERNEL, args.wide_attn_kernel)
+    wide_kernel = model.get_option(_lib.OPT_WIDE_ATTN_KERNEL)
     model.set_option(_lib.OPT_PROFILE, 1)
     for _ in range(max(args.warmup, 3)):
         step()
@@ -552,7 +555,7 @@ def run_ours(args):
                  7: "k_attention_warp (QK^T on tcgen05)", 8: "k_attention_pt (PV on tcgen05)",
                  9: "k_attention_pt (PV on tcgen05)"}.get(attn_variant, "k_attention_tm")
         if wide:
-            kname = "k_attn_wide_pt (PV on tcgen05)" if args.wide_attn_kernel else "k_attn_fwd16"
+            kname = "k_attn_wide_pt (PV on tcgen05)" if wide_kernel == 1 else "k_attn_fwd16"
         roof = {"kernel": kname, "attn_variant": attn_variant, "bound": "alu", "achieved": ach / 1e9,
                 "peak": exp_peak / 1e9, "unit": "Gexp/s", "frac": ach / exp_peak,
                 "traffic": None if wide else attention_traffic(attn_variant, prec),
@@ -631,8 +634,9 @@ def run_ours(args):
                         "particles_per_batch": int((cl != 0).sum()),
                         "note": "anti-kt, E scheme, one CTA per event, O(N^2) per event with "
                                 "nearest-neighbour bookkeeping; latency-bound (one merge per step)"}
-    if args.wide_attn_kernel:
-        line["config"]["wide_attn_kernel"] = "PV and row sums on tcgen05"
+    if wide:
+        line["config"]["wide_attn_kernel"] = ("PV and row sums on tcgen05" if wide_kernel == 1
+                                              else "warp-level MMAs")
     if args.attn_window > 0:
         # agreement with full attention on the same batch, and the full-attention time
         lw, rw, cw = lo.clone(), rg.clone(), cl.clone()

@@ -199,7 +199,9 @@ mlpf_status mlpf_calibrate_fp8(mlpf_model* m, const float* x, const int32_t* cu_
  * Autotuner (no counterpart in the paper): times every attention variant (heads
  * per warpgroup x K/V pipeline depth) of `precision` on the given batch (device
  * buffers, laid out as in mlpf_forward; outputs go to the model's scratch) and
- * keeps the fastest for this model.  cache_path (host string, or NULL for no
+ * keeps the fastest for this model.  Models on the generic-width path: times their two
+ * attention kernels instead and keeps the faster in MLPF_OPT_WIDE_ATTN_KERNEL (cache
+ * key suffix "_wide").  cache_path (host string, or NULL for no
  * cache): a text file of "key variant ms" lines keyed by GPU arch, SM count, model
  * width, precision and element count rounded up to a power of two; a cached key is
  * applied without timing, a new one is appended.  Synchronous on `stream`.

@@ -150,7 +150,9 @@ class Model:
 
     def autotune(self, x, cu_seqlens, max_n: int, precision="bf16", cache_path=None, stream=None):
         """Keep the fastest attention variant of `precision` on this batch (device
-        tensors); returns the chosen variant index (None for fp32)."""
+        tensors); returns the chosen variant index (None for fp32).  For models on the
+        generic-width path the choice is the attention kernel (MLPF_OPT_WIDE_ATTN_KERNEL,
+        read it with get_option); the returned variant then does not apply."""
         import torch
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         s = stream if stream is not None else torch.cuda.current_stream(self.device).cuda_stream

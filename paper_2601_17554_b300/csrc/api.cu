@@ -781,12 +781,83 @@ static void drop_graphs(Model& m) {
 
 static int fmt_of(int32_t prec) { return prec == MLPF_FP16 ? 1 : prec == MLPF_FP8 ? 2 : 0; }
 
+// Generic-width models: the attention kernel (warp-level MMAs, or PV on tcgen05) timed on the
+// batch, the faster kept in MLPF_OPT_WIDE_ATTN_KERNEL; cached like the fused path's variants
+// (key suffix "_wide", the kernel index as the variant).
+static mlpf_status autotune_wide(Model& m, int32_t precision, const float* x, const int32_t* cu_seqlens,
+                                 int32_t n_events, int32_t total, int32_t max_n, const char* cache_path,
+                                 cudaStream_t st, const cudaDeviceProp& prop, int bucket) {
+    if (precision != MLPF_BF16 && precision != MLPF_FP16) return MLPF_OK;   // FP8: refused by the forward
+    const std::string key = "sm" + std::to_string(prop.major) + std::to_string(prop.minor) + "_" +
+                            std::to_string(prop.multiProcessorCount) + "_d" + std::to_string(m.cfg.d) + "_h" +
+                            std::to_string(m.cfg.heads) + "_prec" + std::to_string(precision) + "_T" +
+                            std::to_string(bucket) + "_wide";
+    if (cache_path) {
+        FILE* fp = std::fopen(cache_path, "r");
+        if (fp) {
+            char k[256];
+            int v;
+            float ms;
+            bool hit = false;
+            while (!hit && std::fscanf(fp, "%255s %d %f", k, &v, &ms) == 3)
+                if (key == k && (v == 0 || v == 1)) hit = true;
+            std::fclose(fp);
+            if (hit) {
+                m.wide_attn_kernel = v;
+                drop_graphs(m);
+                return MLPF_OK;
+            }
+        }
+    }
+    mlpf_status s = ensure_workspace(m, total, n_events, true);
+    if (s != MLPF_OK) return s;
+    Workspace& w = m.ws;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best_ms = 1e30f;
+    int best = 0;
+    m.cur_prof = nullptr;
+    for (int v = 0; v < 2; ++v) {
+        m.wide_attn_kernel = v;
+        float ms_sum = 0.f;
+        for (int rep = 0; rep < 3; ++rep) {
+            cudaEventRecord(e0, st);
+            if (run_forward_wide(m, precision, x, cu_seqlens, n_events, total, max_n, w.hlogits, w.hreg_out, st) < 0) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                set_error("autotune launch failed");
+                return MLPF_E_CUDA;
+            }
+            cudaEventRecord(e1, st);
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) ms_sum += ms;  // the first run warms up
+        }
+        if (ms_sum / 2 < best_ms) { best_ms = ms_sum / 2; best = v; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    m.wide_attn_kernel = best;
+    drop_graphs(m);
+    if (cache_path) {
+        FILE* fp = std::fopen(cache_path, "a");
+        if (fp) {
+            std::fprintf(fp, "%s %d %.4f\n", key.c_str(), best, best_ms);
+            std::fclose(fp);
+        }
+    }
+    return MLPF_OK;
+}
+
 mlpf_status mlpf_autotune(mlpf_model* mm, int32_t precision, const float* x, const int32_t* cu_seqlens,
                           int32_t n_events, int32_t total, int32_t max_n, const char* cache_path,
                           void* stream) {
     mlpf_status s = validate(mm ? &mm->impl : nullptr, precision, x, cu_seqlens, n_events, total, max_n, x, x);
     if (s != MLPF_OK) return s;
-    if (precision == MLPF_FP32 || !mm->impl.tc_supported) return MLPF_OK;  // one kernel per step: nothing to choose
+    if (precision == MLPF_FP32) return MLPF_OK;  // one kernel per step: nothing to choose
+    if (!mm->impl.tc_supported && !mm->impl.wide_supported) return MLPF_OK;
     if (total == 0) { set_error("autotuning needs at least one element"); return MLPF_E_INVALID; }
     Model& m = mm->impl;
     CK(cudaSetDevice(m.device));
@@ -794,6 +865,8 @@ mlpf_status mlpf_autotune(mlpf_model* mm, int32_t precision, const float* x, con
     CK(cudaGetDeviceProperties(&prop, m.device));
     int bucket = 1;
     while (bucket < total) bucket <<= 1;
+    if (!m.tc_supported) return autotune_wide(m, precision, x, cu_seqlens, n_events, total, max_n, cache_path,
+                                              (cudaStream_t)stream, prop, bucket);
     const std::string key = "sm" + std::to_string(prop.major) + std::to_string(prop.minor) + "_" +
                             std::to_string(prop.multiProcessorCount) + "_d" + std::to_string(m.cfg.d) + "_prec" +
                             std::to_string(precision) + "_T" + std::to_string(bucket) + "_v" + std::to_string(MLPF_ATTN_VARIANTS);

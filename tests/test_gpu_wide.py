@@ -151,3 +151,27 @@ def test_fp8_refused(full_model):
     with pytest.raises(MlpfError) as ei:
         run_gpu(model, x, cu, "fp8")
     assert ei.value.status == 7   # MLPF_E_UNSUPPORTED
+
+
+def test_autotune_picks_a_wide_kernel(full_model, tmp_path):
+    """mlpf_autotune on a generic-width model times its two attention kernels, keeps
+    one in MLPF_OPT_WIDE_ATTN_KERNEL, writes a "_wide" cache line and reuses it."""
+    import torch
+    from paper_2601_17554_b300._lib import OPT_WIDE_ATTN_KERNEL
+    model, w = full_model
+    x, cu = synth.gen_events(108, [900, 300, 1200])
+    xt, ct = torch.from_numpy(x).cuda(), torch.from_numpy(cu).cuda()
+    path = str(tmp_path / "tune.txt")
+    try:
+        model.autotune(xt, ct, 1200, precision="bf16", cache_path=path)
+        k = model.get_option(OPT_WIDE_ATTN_KERNEL)
+        assert k in (0, 1)
+        lines = [ln for ln in open(path).read().split("\n") if ln]
+        assert len(lines) == 1 and lines[0].split()[0].endswith("_wide") and int(lines[0].split()[1]) == k
+        model.set_option(OPT_WIDE_ATTN_KERNEL, 1 - k)
+        model.autotune(xt, ct, 1200, precision="bf16", cache_path=path)   # cached: no timing
+        assert model.get_option(OPT_WIDE_ATTN_KERNEL) == k
+        assert len([ln for ln in open(path).read().split("\n") if ln]) == 1
+        check_lowp(run_gpu(model, x, cu, "bf16"), oracle.forward(w, synth.FULL, x, cu))
+    finally:
+        model.set_option(OPT_WIDE_ATTN_KERNEL, 0)
