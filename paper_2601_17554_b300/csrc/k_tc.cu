@@ -143,13 +143,6 @@ MLPF_DEV void issue_gemm(uint32_t d_tmem, const uint8_t* a, const uint8_t* b, in
     }
 }
 
-// 64 consecutive TMEM columns of this thread's row.
-MLPF_DEV void ld_row64(uint32_t taddr, float* v) {
-    tmem_ld32(taddr, v);
-    tmem_ld32(taddr + 32, v + 32);
-    tmem_wait_ld();
-}
-
 MLPF_DEV uint32_t pack_e4m3x4(float a, float b, float c, float d) {
     uint16_t lo, hi;
     asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(lo) : "f"(b), "f"(a));
@@ -192,19 +185,6 @@ MLPF_DEV void st_op(uint8_t* tile, int r, const float* v, int n, int k0, float q
     }
 }
 
-template <bool F16>
-MLPF_DEV void st_global_row64(uint16_t* dst, const float* v) {
-    uint4* d4 = (uint4*)dst;
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        uint4 u;
-        u.x = pack2<F16>(v[8 * c + 0], v[8 * c + 1]);
-        u.y = pack2<F16>(v[8 * c + 2], v[8 * c + 3]);
-        u.z = pack2<F16>(v[8 * c + 4], v[8 * c + 5]);
-        u.w = pack2<F16>(v[8 * c + 6], v[8 * c + 7]);
-        d4[c] = u;
-    }
-}
 
 
 // Record max |v| of valid rows into amax[slot] (calibration of FP8 scales).
@@ -214,38 +194,6 @@ MLPF_DEV void record_amax(unsigned* amax, int slot, const float* v, int n, bool 
     unsigned u = valid ? __float_as_uint(mx) : 0u;
     u = __reduce_max_sync(0xffffffffu, u);
     if ((threadIdx.x & 31) == 0 && u) atomicMax(amax + slot, u);
-}
-
-// In-place LayerNorm of a 64-vector (two-pass FP32 moments, biased variance).
-MLPF_DEV void layernorm64(const float* z, float* out, const float* g, const float* b) {
-    float s = 0.f;
-#pragma unroll
-    for (int i = 0; i < D; ++i) s += z[i];
-    const float mu = s * (1.0f / D);
-    float q = 0.f;
-#pragma unroll
-    for (int i = 0; i < D; ++i) {
-        const float t = z[i] - mu;
-        q = fmaf(t, t, q);
-    }
-    const float rs = rsqrtf(q * (1.0f / D) + LN_EPS);
-#pragma unroll
-    for (int i = 0; i < D; ++i) out[i] = (z[i] - mu) * rs * __ldg(g + i) + __ldg(b + i);
-}
-
-// This row's 42 input features, zero padded to 64.
-MLPF_DEV void load_x_row(float* v, const float* x, bool valid, int prow) {
-#pragma unroll
-    for (int i = 0; i < 64; ++i) v[i] = 0.f;
-    if (valid) {
-        const float2* src = (const float2*)(x + (size_t)prow * 42);
-#pragma unroll
-        for (int i = 0; i < 21; ++i) {
-            const float2 t = __ldg(src + i);
-            v[2 * i] = t.x;
-            v[2 * i + 1] = t.y;
-        }
-    }
 }
 
 struct RowInfo {
@@ -261,28 +209,6 @@ MLPF_DEV RowInfo row_info(const int4* blk, int nblk, int p) {
         ri.prow = e.y + (p & 63);
     }
     return ri;
-}
-
-// Q, K rows and transposed V (zero for padding rows) from the QKV accumulator,
-// acc * ds + bias, stored in the 16-bit attention format.
-template <bool F16>
-MLPF_DEV void store_qkv(uint32_t tacc, const float* bqkv, float ds, int p, bool valid, uint16_t* q,
-                        uint16_t* k, uint16_t* vt, long ldvt) {
-    float v[64];
-    ld_row64(tacc, v);
-#pragma unroll
-    for (int i = 0; i < 64; ++i) v[i] = fmaf(v[i], ds, __ldg(bqkv + i));
-    st_global_row64<F16>(q + (size_t)p * D, v);
-    ld_row64(tacc + 64, v);
-#pragma unroll
-    for (int i = 0; i < 64; ++i) v[i] = fmaf(v[i], ds, __ldg(bqkv + 64 + i));
-    st_global_row64<F16>(k + (size_t)p * D, v);
-    ld_row64(tacc + 128, v);
-#pragma unroll
-    for (int i = 0; i < 64; ++i) {
-        const float t = valid ? fmaf(v[i], ds, __ldg(bqkv + 128 + i)) : 0.f;
-        vt[(size_t)i * ldvt + p] = (uint16_t)(pack2<F16>(t, 0.f) & 0xffffu);
-    }
 }
 
 // ------------------------------------------------------------------ scheduler
