@@ -219,7 +219,9 @@ mlpf_status mlpf_autotune(mlpf_model* m, int32_t precision, const float* x, cons
  * pz = pT sinh(eta), E = pT cosh(eta); the regressed E is not used).  Distances
  * d_ij = min(pT_i^-2, pT_j^-2) dR_ij^2 / R^2 (rapidity and azimuth) and d_iB =
  * pT_i^-2; E-scheme recombination (Cacciari, Salam, Soyez, JHEP 04 (2008) 063).
- * FP32 on the GPU, one CTA per event, O(N^2) per event.
+ * FP32 on the GPU, one CTA per event, O(N^2) per event.  Equal distances: the beam
+ * distance wins, then the lower entry, entries numbered in the order the kernel keeps
+ * them (by rapidity for events of at most 12,288 elements, else input order).
  * reg        device, [total, 5] decoded outputs of mlpf_forward (pT, eta, sin phi,
  *            cos phi, E); cls: device, [total] int32 classes; cu_seqlens: device,
  *            [n_events + 1] (as mlpf_forward).

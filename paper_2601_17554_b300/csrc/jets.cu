@@ -34,7 +34,9 @@ constexpr int JW = JT / 32;
 constexpr int JLIST = 512;      // entries whose neighbour is recomputed in one step
 // k_antikt_sm: events of at most JCAP elements keep the fields every step reads (y, phi,
 // the entry distance dd, the squared distance d2 to the neighbour, the neighbour nn) in
-// shared memory, 18 bytes per particle; larger events run k_antikt on global memory.
+// shared memory, 18 bytes per particle, with the particles sorted by rapidity (a pair at
+// dy^2 >= R^2 is never within R, so the passes skip its azimuth and distance arithmetic);
+// larger events run k_antikt on global memory, in input order.
 constexpr int JCAP = 12288;
 constexpr size_t kJetSmem = (size_t)JCAP * (4 * sizeof(float) + sizeof(int16_t));
 constexpr int JG = 4;           // listed entries whose neighbours one block scan recomputes
@@ -206,6 +208,7 @@ __global__ void __launch_bounds__(JT) k_antikt(const float* __restrict__ reg, co
         for (int k = tid; k < n; k += JT)
             if (L.act[k]) argmin_pair(bv, bi, L.dd[k], k);
         block_argmin(bv, bi, sv, si);
+        if (bi == INT_MAX) break;   // no active entry left (only for non-finite inputs)
         const int i = bi;
         if (tid == 0) {
             const int j = L.nn[i];
@@ -358,48 +361,71 @@ __global__ void __launch_bounds__(NT) k_antikt_sm(const float* __restrict__ reg,
         s_jets = 0;
     }
     __syncthreads();
-    // particles of the event, in input order (block-wide compaction by chunks)
-    for (int c0 = 0; c0 < N; c0 += NT) {
-        const int row = r0 + c0 + tid;
-        bool f = false;
-        float pt = 0.f, eta = 0.f, s = 0.f, c = 0.f;
-        if (c0 + tid < N) {
-            pt = reg[(size_t)row * 5];
-            eta = reg[(size_t)row * 5 + 1];
-            s = reg[(size_t)row * 5 + 2];
-            c = reg[(size_t)row * 5 + 3];
-            f = cls[row] != 0 && pt > 0.f && (s * s + c * c) > 0.f;
+    // the event's particles sorted by rapidity (= eta for massless particles): a warp's
+    // consecutive entries are then close in y, and the per-step passes skip the distance
+    // arithmetic of a whole warp whose entries are all at |dy| >= R.  Bitonic sort of
+    // (key, element) over the next power of two >= N, keys +inf for the elements that are
+    // not particles (they sort last), in the sdd / sd2 area (free until the neighbour pass)
+    constexpr int SORTCAP = 16384;   // >= JCAP
+    static_assert(SORTCAP >= JCAP && SORTCAP * 6 <= JCAP * 8, "sort area");
+    float* skey = sdd;
+    int16_t* sidx = (int16_t*)(sdd + SORTCAP);
+    int M = 1;
+    while (M < N) M <<= 1;
+    for (int p = tid; p < M; p += NT) {
+        float key = INFINITY;
+        if (p < N) {
+            const int row = r0 + p;
+            const float pt = reg[(size_t)row * 5], eta = reg[(size_t)row * 5 + 1];
+            const float s = reg[(size_t)row * 5 + 2], c = reg[(size_t)row * 5 + 3];
+            if (cls[row] != 0 && pt > 0.f && (s * s + c * c) > 0.f) {
+                key = eta == eta ? fminf(fmaxf(eta, -1e30f), 1e30f) : 0.f;
+                atomicAdd(&s_n, 1);
+            }
             if (jet_of) jet_of[row] = -1;
         }
-        const unsigned b = __ballot_sync(0xffffffffu, f);
-        if (lane == 0) si[warp] = __popc(b);
-        __syncthreads();
-        int off = 0, tot = 0;
-#pragma unroll
-        for (int w = 0; w < NW; ++w) {
-            off += w < warp ? si[w] : 0;
-            tot += si[w];
-        }
-        if (f) {
-            const int k = s_n + off + __popc(b & ((1u << lane) - 1u));
-            const float r = sqrtf(s * s + c * c);
-            const float px = pt * (c / r), py = pt * (s / r);
-            L.idx[k] = row;
-            L.px[k] = px;
-            L.py[k] = py;
-            L.ep[k] = pt * expf(eta);    // E + pz
-            L.em[k] = pt * expf(-eta);   // E - pz
-            sy[k] = eta;                 // massless: rapidity = pseudorapidity
-            sphi[k] = atan2f(s, c);
-            L.pinv[k] = 1.f / (px * px + py * py);
-            L.parent[k] = -1;
-            sdd[k] = 0.f;                // active
-        }
-        __syncthreads();
-        if (tid == 0) s_n += tot;
-        __syncthreads();
+        skey[p] = key;
+        sidx[p] = (int16_t)p;
     }
+    __syncthreads();
+    for (int kk = 2; kk <= M; kk <<= 1)
+        for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+            for (int p = tid; p < M; p += NT) {
+                const int q = p ^ jj;
+                if (q > p) {
+                    const float a = skey[p], b = skey[q];
+                    if ((a > b) == ((p & kk) == 0)) {
+                        skey[p] = b;
+                        skey[q] = a;
+                        const int16_t t = sidx[p];
+                        sidx[p] = sidx[q];
+                        sidx[q] = t;
+                    }
+                }
+            }
+            __syncthreads();
+        }
     const int n = s_n;
+    // entry p = the p-th particle in rapidity order
+    for (int p = tid; p < n; p += NT) {
+        const int row = r0 + sidx[p];
+        const float pt = reg[(size_t)row * 5], eta = reg[(size_t)row * 5 + 1];
+        const float s = reg[(size_t)row * 5 + 2], c = reg[(size_t)row * 5 + 3];
+        const float r = sqrtf(s * s + c * c);
+        const float px = pt * (c / r), py = pt * (s / r);
+        L.idx[p] = row;
+        L.px[p] = px;
+        L.py[p] = py;
+        L.ep[p] = pt * expf(eta);    // E + pz
+        L.em[p] = pt * expf(-eta);   // E - pz
+        sy[p] = eta;                 // massless: rapidity = pseudorapidity
+        sphi[p] = atan2f(s, c);
+        L.pinv[p] = 1.f / (px * px + py * py);
+        L.parent[p] = -1;
+    }
+    __syncthreads();
+    for (int p = tid; p < n; p += NT) sdd[p] = 0.f;   // active (over the sort keys)
+    __syncthreads();
     auto active = [&](int m) { const float d = sdd[m]; return d == d; };
     // nearest active neighbour within R of entry a over the entries m0, m0 + dm, ...
     auto scan = [&](int a, int m0, int dm, float& best, int& bj) {
@@ -408,8 +434,11 @@ __global__ void __launch_bounds__(NT) k_antikt_sm(const float* __restrict__ reg,
         bj = INT_MAX;
         for (int m = m0; m < n; m += dm) {
             if (m == a || !active(m)) continue;
-            const float d = dr2(ya, pa, sy[m], sphi[m]);
-            if (d < r2) argmin_pair(best, bj, d, m);
+            const float dy = ya - sy[m];
+            if (dy * dy < r2) {   // else dR^2 >= dy^2 >= R^2
+                const float d = dr2(ya, pa, sy[m], sphi[m]);
+                if (d < r2) argmin_pair(best, bj, d, m);
+            }
         }
     };
     auto set_nn = [&](int a, float best, int bj) {
@@ -434,6 +463,7 @@ __global__ void __launch_bounds__(NT) k_antikt_sm(const float* __restrict__ reg,
     int gbuf = 0;
     for (int step = 0; step < n; ++step) {   // every step removes one entry
         block_argmin_all<NW>(bv, bi, sv, si);
+        if (bi == INT_MAX) break;   // no active entry left (only for non-finite inputs)
         const int i = bi;
         if (tid == 0) {
             const int j = snn[i];
@@ -495,12 +525,15 @@ __global__ void __launch_bounds__(NT) k_antikt_sm(const float* __restrict__ reg,
                     lost = false;
                 }
             } else if (!lost && !beam) {
-                const float d = dr2(sy[m], sphi[m], yk, pk);
-                if (d < r2 && (d < sd2[m] || (d == sd2[m] && k < nm))) {
-                    snn[m] = (int16_t)k;
-                    sd2[m] = d;
-                    dm = entry_dist(L.pinv[m], d, k, inv_r2);
-                    sdd[m] = dm;
+                const float dy = sy[m] - yk;
+                if (dy * dy < r2) {   // else the merged entry is not within R
+                    const float d = dr2(sy[m], sphi[m], yk, pk);
+                    if (d < r2 && (d < sd2[m] || (d == sd2[m] && k < nm))) {
+                        snn[m] = (int16_t)k;
+                        sd2[m] = d;
+                        dm = entry_dist(L.pinv[m], d, k, inv_r2);
+                        sdd[m] = dm;
+                    }
                 }
             }
             if (lost) {
@@ -544,8 +577,11 @@ __global__ void __launch_bounds__(NT) k_antikt_sm(const float* __restrict__ reg,
 #pragma unroll
                     for (int q = 0; q < JG; ++q) {
                         if (aa[q] < 0 || m == aa[q]) continue;
-                        const float d = dr2(ya[q], pa[q], ym, pm);
-                        if (d < r2) argmin_pair(best[q], bj[q], d, m);
+                        const float dy = ya[q] - ym;
+                        if (dy * dy < r2) {
+                            const float d = dr2(ya[q], pa[q], ym, pm);
+                            if (d < r2) argmin_pair(best[q], bj[q], d, m);
+                        }
                     }
                 }
                 const int g = min(JG, cnt - t0);
