@@ -1,7 +1,7 @@
 """Writes tests/golden/antikt_large_r04.json: the FP64 oracle's anti-kt jets (R = 0.4)
-of one large synthetic event, for the GPU parity test of an event of about 5,000
-particles (the oracle's plain O(N^3) clustering takes about 20 minutes on it, too
-long to run inside the test).  Calls only oracle/ and synth/.
+of one large synthetic event, for the GPU parity test of an event of more than 5,000
+particles (7,500 elements, 5,201 particles; the oracle's plain O(N^3) clustering takes
+about 20 minutes on it, too long to run inside the test).  Calls only oracle/ and synth/.
 
     PYTHONPATH=. python tests/golden/make_antikt_large.py
 """
@@ -13,7 +13,7 @@ import numpy as np
 import synth
 from oracle import jets as J
 
-SEED_EVENTS, SEED_TARGETS, SIZE, R = 45, 46, 7200, 0.4
+SEED_EVENTS, SEED_TARGETS, SIZE, R = 45, 46, 7500, 0.4
 OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "antikt_large_r04.json")
 
 
@@ -22,8 +22,8 @@ def main():
     cls, reg = synth.gen_targets(SEED_TARGETS, x, cu)
     jets, jof = J.event_jets(cls, reg, R)
     with open(OUT, "w") as f:
-        json.dump({"what": "FP64 oracle anti-kt jets of synth.gen_events(45, [7200]) with "
-                           "synth.gen_targets(46, ...) classes and regressions",
+        json.dump({"what": f"FP64 oracle anti-kt jets of synth.gen_events({SEED_EVENTS}, [{SIZE}]) "
+                           f"with synth.gen_targets({SEED_TARGETS}, ...) classes and regressions",
                    "seed_events": SEED_EVENTS, "seed_targets": SEED_TARGETS, "size": SIZE, "R": R,
                    "n_particles": int((jof >= 0).sum()),
                    "jet_of": jof.tolist(), "jets": np.round(jets, 9).tolist()}, f)

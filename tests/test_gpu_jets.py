@@ -144,7 +144,7 @@ def test_full_batch_conserves_momentum(model):
 
 
 def test_large_event_matches_oracle_golden(model):
-    """One event of 7,200 elements (4,992 particles) against the FP64 oracle's jets,
+    """One event of 7,500 elements (5,201 particles) against the FP64 oracle's jets,
     stored in tests/golden/antikt_large_r04.json by tests/golden/make_antikt_large.py
     (the oracle's plain O(N^3) clustering takes about 20 minutes on it)."""
     import json
