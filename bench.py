@@ -546,9 +546,10 @@ def run_ours(args):
     roof = None
     if att_ms:
         ach = exps / (att_ms / 1000.0)
-        # the 16-bit attention kernels take their exponentials two at a time
-        # (ex2.bf16x2 / ex2.f16x2): the MUFU bound is the packed rate
-        packed = prec in ("bf16", "fp16", "fp8") and not wide
+        # the 16-bit attention kernels (fused and generic-width) take their
+        # exponentials two at a time (ex2.bf16x2 / ex2.f16x2): the MUFU bound is the
+        # packed rate
+        packed = prec in ("bf16", "fp16", "fp8")
         exp_peak = unit_rates["ex2_bf16x2_per_s"] if packed else unit_rates["ex2_per_s"]
         kname = {3: "k_attention_warp", 4: "k_attention_warp", 5: "k_attention_warp (64-row items)",
                  6: "k_attention_warp (QK^T on tcgen05)",
