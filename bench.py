@@ -223,6 +223,32 @@ def measured_bf16_tflops():
         return None
 
 
+def measured_hbm_gbs():
+    """HBM copy bandwidth measured on this machine's GPUs (read + write bytes), if recorded."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return float(json.load(open(p))["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def gemm_chain_bytes_per_element(d, n_post_qkv):
+    """Algorithmic DRAM bytes per element of the fused GEMM-chain kernels of one forward:
+    what each kernel must read and write once (x: 42 FP32; the residual stream z: d FP32;
+    Q, K, V^T, the attention output O and h_pid: d 16-bit values each; logits 6 and
+    decoded outputs 5 FP32).  embedding + LN1 + QKV: x, z out, Q K V^T out; each block
+    boundary (k_post<0>): O, z in and out, Q K V^T out; end of the PID stack with the class
+    head: O, z, h_pid out, logits out; regression embedding + QKV: x, h_pid, z out, Q K V^T
+    out; end of the regression stack with its heads: O, z, x's log pT and log E, outputs."""
+    x, z, h = 42 * 4, 4 * d, 2 * d
+    embed = x + z + 3 * h
+    post_qkv = h + 2 * z + 3 * h
+    post_cls = h + z + h + 6 * 4
+    reg_embed = x + h + z + 3 * h
+    post_reg = h + z + 2 * 4 + 5 * 4
+    return embed + n_post_qkv * post_qkv + post_cls + reg_embed + post_reg
+
+
 def attention_traffic(variant, precision):
     """Per-launch DRAM bytes of the attention kernel variant from the committed ncu
     summary (keys bytes_per_launch_<precision>_variant_<n>), else None."""
@@ -584,10 +610,17 @@ def run_ours(args):
         pk = measured_bf16_tflops()
         if pk is not None and prec == "fp8":
             pk *= 2.0   # E4M3 dense rate = 2 x BF16 (nominal ratio)
+        n_post = len(kernel_ms.get("post_qkv", [])) / len(kernel_ms["embed_qkv"])
+        g_bytes = gemm_chain_bytes_per_element(cfg.d, n_post) * T
+        hbm = measured_hbm_gbs()
         gemm = {"kernels": list(gemm_names), "flop_per_step": g_flop, "ms_per_step": g_ms,
                 "tflops": g_flop / (g_ms / 1000.0) / 1e12,
                 "peak_tflops": pk, "frac": (g_flop / (g_ms / 1000.0) / 1e12 / pk) if pk else None,
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops (cuBLAS burst)" + (" x 2 for E4M3" if prec == "fp8" else ""),
+                "hbm_bytes_per_step": g_bytes, "hbm_gbs": g_bytes / (g_ms / 1000.0) / 1e9,
+                "hbm_peak_gbs": hbm, "hbm_frac": (g_bytes / (g_ms / 1000.0) / 1e9 / hbm) if hbm else None,
+                "hbm_source": "algorithmic bytes (each kernel's inputs read once, outputs written once) / "
+                              "the chain's CUDA-event time; peak: MEASURED_PEAKS.json hbm_gbs (copy)",
                 "note": "fused per-tile GEMM chains (K = 64..256) with LayerNorm/GELU epilogues: latency-bound, "
                         "not tensor-bound"}
     if prec != "fp32" and "wide_gemm" in kernel_ms:

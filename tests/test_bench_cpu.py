@@ -35,6 +35,16 @@ def test_gemm_flops_per_element_d64_model():
     assert bench.gemm_flops_per_element(deeper) - f == 2 * (4 * 64 * 64 + 2 * 64 * 256)
 
 
+def test_gemm_chain_bytes_per_element_d64_model():
+    """About 2.7 KB of algorithmic DRAM traffic per element for the d=64 1 + 1 model's
+    four chain kernels (808 + 536 + 936 + 412 bytes from the tensors each one reads and
+    writes); a block boundary adds O, the residual stream in and out and Q, K, V^T."""
+    import bench
+    assert bench.gemm_chain_bytes_per_element(64, 0) == 808 + 536 + 936 + 412
+    assert bench.gemm_chain_bytes_per_element(64, 1) - bench.gemm_chain_bytes_per_element(64, 0) == \
+        2 * 64 + 2 * 4 * 64 + 3 * 2 * 64
+
+
 def test_reference_arm_json_line(capsys, monkeypatch):
     """`bench.py --impl reference`: one JSON line with the contract's keys (the oracle
     timed on the host cores, no host-device copies), printed by rank 0 only."""
