@@ -231,8 +231,11 @@ mlpf_status mlpf_autotune(mlpf_model* m, int32_t precision, const float* x, cons
  * n_jets     device out, [n_events] int32.
  * jet_of     device out or NULL, [total] int32: the element's jet index within its
  *            event, -1 for elements that are not particles.
- * Uses a scratch of 53 bytes per element owned by the model (grown on demand, not
- * during graph capture).  Asynchronous on `stream`.  Errors: MLPF_E_INVALID (NULL
+ * The events' CTAs run largest event first (a one-CTA sort of the element counts, for
+ * up to 4,096 events; more keep the input order), so that the largest events do not
+ * end the launch.  Uses a scratch of 53 bytes per element and 4 per event owned by
+ * the model (grown on demand, not during graph capture).  Asynchronous on `stream`.
+ * Errors: MLPF_E_INVALID (NULL
  * pointers, negative sizes, R out of range), MLPF_E_OOM, MLPF_E_CUDA.
  */
 mlpf_status mlpf_cluster_jets(mlpf_model* m, const float* reg, const int32_t* cls,

@@ -307,6 +307,50 @@ __global__ void __launch_bounds__(JT) k_antikt(const float* __restrict__ reg, co
     if (tid == 0) n_jets[ev] = s_jets;
 }
 
+// The order in which the CTAs of a jet launch take the events: by element count,
+// largest first (ties by event index).  One CTA per event and at most one CTA per SM
+// (the shared-memory kernel), so the block scheduler hands the events out in this
+// order as SMs become free: the longest-processing-time-first rule, which keeps the
+// largest events off the end of the launch.  Bitonic sort of (count, event) keys in
+// shared memory; a launch of more than JORDER events keeps the input order.
+constexpr int JORDER = 4096;
+__global__ void __launch_bounds__(1024) k_jet_order(const int32_t* __restrict__ cu, int n_events,
+                                                    int32_t* __restrict__ order) {
+    __shared__ unsigned long long key[JORDER];
+    const int tid = threadIdx.x;
+    if (n_events > JORDER) {
+        for (int e = tid; e < n_events; e += blockDim.x) order[e] = e;
+        return;
+    }
+    int M = 1;
+    while (M < n_events) M <<= 1;
+    for (int p = tid; p < M; p += blockDim.x) {
+        // ascending keys: larger events first, then lower event index; padding last
+        unsigned long long k = ~0ull;
+        if (p < n_events) {
+            const unsigned n = (unsigned)(cu[p + 1] - cu[p]);
+            k = ((unsigned long long)(0x7fffffffu - n) << 32) | (unsigned)p;
+        }
+        key[p] = k;
+    }
+    __syncthreads();
+    for (int kk = 2; kk <= M; kk <<= 1)
+        for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+            for (int p = tid; p < M; p += blockDim.x) {
+                const int q = p ^ jj;
+                if (q > p) {
+                    const unsigned long long a = key[p], b = key[q];
+                    if ((a > b) == ((p & kk) == 0)) {
+                        key[p] = b;
+                        key[q] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    for (int p = tid; p < n_events; p += blockDim.x) order[p] = (int32_t)(key[p] & 0xffffffffu);
+}
+
 // the entry of smallest (value, index) over the block, in every thread, with one
 // barrier: each warp reduces the per-warp minima itself (sv is rewritten only after
 // the caller's next barrier)
@@ -335,7 +379,7 @@ template <int NT>
 __global__ void __launch_bounds__(NT) k_antikt_sm(const float* __restrict__ reg, const int32_t* __restrict__ cls,
                                                  const int32_t* __restrict__ cu, float r2, JetScratch S,
                                                  float* __restrict__ jets, int32_t* __restrict__ n_jets,
-                                                 int32_t* __restrict__ jet_of) {
+                                                 int32_t* __restrict__ jet_of, const int32_t* __restrict__ order) {
     constexpr int NW = NT / 32;
     extern __shared__ float jsm[];
     float* sy = jsm;
@@ -349,7 +393,7 @@ __global__ void __launch_bounds__(NT) k_antikt_sm(const float* __restrict__ reg,
     __shared__ int gi[2][NW * JG];
     __shared__ int s_n, s_jets, s_cnt, s_over, s_j, s_beam;
     __shared__ int s_list[JLIST];
-    const int ev = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int ev = order[blockIdx.x], tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int r0 = cu[ev], N = cu[ev + 1] - r0;
     if (N > JCAP) return;   // k_antikt takes this event
     const float inv_r2 = 1.f / r2;
@@ -642,9 +686,11 @@ extern "C" mlpf_status mlpf_cluster_jets(mlpf_model* mm, const float* reg, const
     if (n_events == 0) return MLPF_OK;
     Model& m = mm->impl;
     if (cudaSetDevice(m.device) != cudaSuccess) { set_error("cudaSetDevice failed"); return MLPF_E_CUDA; }
-    // scratch: 13 words and 1 byte per element, grown on demand
+    // scratch: 13 words and 1 byte per element, then the events' launch order (one
+    // word per event, 16-byte aligned), grown on demand
     const size_t cap = (size_t)(total > 0 ? total : 1);
-    const size_t need = cap * (13 * 4 + 1) + 256;
+    const size_t order_off = (cap * (13 * 4 + 1) + 15) & ~(size_t)15;
+    const size_t need = order_off + (size_t)n_events * 4 + 256;
     if (m.jet_bytes < need) {
         if (m.jet_base) cudaFree(m.jet_base);
         m.jet_base = nullptr;
@@ -670,11 +716,13 @@ extern "C" mlpf_status mlpf_cluster_jets(mlpf_model* mm, const float* reg, const
     S.jid = iw + 2 * cap;
     S.idx = iw + 3 * cap;
     S.act = (unsigned char*)(iw + 4 * cap);
+    int32_t* order = (int32_t*)((unsigned char*)m.jet_base + order_off);
     // events of at most JCAP elements in shared memory; larger ones (possible only when
     // the batch holds more than JCAP elements) on global memory
+    k_jet_order<<<1, 1024, 0, (cudaStream_t)stream>>>(cu_seqlens, n_events, order);
     cudaFuncSetAttribute(k_antikt_sm<JT_SM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kJetSmem);
     k_antikt_sm<JT_SM><<<n_events, JT_SM, kJetSmem, (cudaStream_t)stream>>>(reg, cls, cu_seqlens, R * R, S, jets,
-                                                                             n_jets, jet_of);
+                                                                             n_jets, jet_of, order);
     if (total > JCAP)
         k_antikt<<<n_events, JT, 0, (cudaStream_t)stream>>>(reg, cls, cu_seqlens, R * R, S, jets, n_jets, jet_of);
     const cudaError_t e = cudaPeekAtLastError();

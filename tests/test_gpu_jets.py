@@ -88,6 +88,22 @@ def test_jets_match_oracle(model, R):
     assert mat >= 0.995 * tot, (mat, tot)
 
 
+def test_many_small_events(model):
+    """5,000 events of 0-7 elements: more events than the launch-order sort takes (4,096),
+    so the CTAs run in event order; every event matches the oracle."""
+    rng = np.random.default_rng(49)
+    sizes = rng.integers(0, 8, 5000)
+    x, cu = synth.gen_events(50, sizes)
+    cls, reg = synth.gen_targets(51, x, cu)
+    gj, gnj, gjof = run_jets(model, reg, cls, cu, 0.4)
+    tot = mat = 0
+    for e in range(len(sizes)):
+        sl = slice(cu[e], cu[e + 1])
+        n, m = compare_event(gj[cu[e]:cu[e + 1]], int(gnj[e]), gjof[sl], cls[sl], reg[sl], 0.4)
+        tot, mat = tot + n, mat + m
+    assert tot > 10000 and mat >= 0.995 * tot, (mat, tot)
+
+
 def test_closed_forms(model):
     # event 0: two particles within R -> one jet, their sum; event 1: two beyond R ->
     # two jets, the harder first; event 2: a class-0 element and a pT = 0 element only
