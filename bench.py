@@ -75,6 +75,10 @@ def parse():
     ap.add_argument("--wide-attn-kernel", type=int, default=None, choices=[0, 1],
                     help="generic-width models: 0 = warp-level attention, 1 = PV on tcgen05 "
                          "(default: autotuned on the batch)")
+    ap.add_argument("--blob", default="",
+                    help="weights from this blob file (the library's blob format, e.g. a trained model "
+                         "exported by the trainer) instead of the seeded ones; its architecture must be "
+                         "--model's.  The oracle baselines and errors use the same weights")
     ap.add_argument("--model", default="small", choices=sorted(MODELS),
                     help="architecture run on the batch (small: the workload's d=64 model)")
     return ap.parse_args()
@@ -306,7 +310,8 @@ def _oracle_init(cfg, wseed):
         threadpool_limits(1)
     except Exception:
         pass
-    _W = (cfg, synth.make_weights(cfg, wseed))
+    # wseed: the weight seed, or the path of a weight blob (--blob)
+    _W = synth.unpack_blob(open(wseed, "rb").read()) if isinstance(wseed, str) else (cfg, synth.make_weights(cfg, wseed))
 
 
 def _oracle_event(args):
@@ -460,7 +465,7 @@ def run_ours(args):
     if not args.no_baselines and rank == 0:
         # the oracle's worker pool, started before the first GPU call
         cfg0, wseed0, _ = model_of(args.model)
-        pool = oracle_pool(cfg0, wseed0, os.cpu_count() or 1)
+        pool = oracle_pool(cfg0, args.blob or wseed0, os.cpu_count() or 1)
     import torch
     from paper_2601_17554_b300 import Model, _lib
 
@@ -468,8 +473,15 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     cfg, wseed, x, cu, sizes = workload_inputs(rank, args.events, args.split, ws, args.model)
-    W = synth.make_weights(cfg, wseed)
-    model = Model(synth.pack_blob(cfg, W), device=local)
+    if args.blob:
+        blob = open(args.blob, "rb").read()
+        bcfg, _ = synth.unpack_blob(blob)
+        if bcfg != cfg:
+            raise SystemExit(f"--blob holds {bcfg}, --model {args.model} is {cfg}")
+        wseed = args.blob
+        model = Model(blob, device=local)
+    else:
+        model = Model(synth.pack_blob(cfg, synth.make_weights(cfg, wseed)), device=local)
     T, n_ev, max_n = x.shape[0], len(sizes), int(sizes.max())
     xd = torch.from_numpy(x).to(dev)
     cud = torch.from_numpy(cu).to(dev)
@@ -668,6 +680,8 @@ def run_ours(args):
                         "particles_per_batch": int((cl != 0).sum()),
                         "note": "anti-kt, E scheme, one CTA per event, O(N^2) per event with "
                                 "nearest-neighbour bookkeeping; latency-bound (one merge per step)"}
+    if args.blob:
+        line["config"]["weights"] = f"blob file {os.path.basename(args.blob)} (not the seeded weights)"
     if wide:
         line["config"]["wide_attn_kernel"] = ("PV and row sums on tcgen05" if wide_kernel == 1
                                               else "warp-level MMAs")

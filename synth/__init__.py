@@ -311,6 +311,36 @@ def pack_blob(cfg: ModelConfig, weights) -> bytes:
     return b"".join(out)
 
 
+def unpack_blob(blob: bytes):
+    """The (ModelConfig, {tensor name: float32 array}) of a blob in the layout that
+    pack_blob writes and the library's trainer exports (version 1 or 2)."""
+    if blob[:4] != BLOB_MAGIC:
+        raise ValueError("not a weight blob")
+    (version,) = struct.unpack_from("<i", blob, 4)
+    if version not in (1, 2):
+        raise ValueError(f"blob version {version}")
+    nh = 10 + (1 if version == 2 else 0)
+    hdr = struct.unpack_from(f"<{nh}i", blob, 8)
+    in_dim, d, heads, ffn, l_pid, l_reg, n_cls, n_reg, act = hdr[:9]
+    arch = hdr[9] if version == 2 else ARCH_SEQ
+    n_tensors = hdr[-1]
+    cfg = ModelConfig(d=d, heads=heads, ffn=ffn, l_pid=l_pid, l_reg=l_reg, act=act, in_dim=in_dim,
+                      n_cls=n_cls, n_reg=n_reg, arch=arch)
+    off = 8 + 4 * nh
+    weights = {}
+    for _ in range(n_tensors):
+        name = blob[off:off + NAME_BYTES].split(b"\0", 1)[0].decode()
+        ndim, d0, d1 = struct.unpack_from("<3i", blob, off + NAME_BYTES)
+        off += NAME_BYTES + 12
+        count = d0 * d1
+        a = np.frombuffer(blob, dtype="<f4", count=count, offset=off).astype(np.float32)
+        weights[name] = a.reshape((d0,) if ndim == 1 else (d0, d1))
+        off += 4 * count
+    if off != len(blob):
+        raise ValueError("trailing bytes in the blob")
+    return cfg, weights
+
+
 # --------------------------------------------------------------------------
 # synthetic targets (supervised training without the CMS samples)
 # --------------------------------------------------------------------------
