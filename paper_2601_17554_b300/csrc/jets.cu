@@ -393,6 +393,8 @@ __global__ void __launch_bounds__(NT) k_antikt_sm(const float* __restrict__ reg,
     __shared__ int gi[2][NW * JG];
     __shared__ int s_n, s_jets, s_cnt, s_over, s_j, s_beam;
     __shared__ int s_list[JLIST];
+    __shared__ float bmin[JCAP / 32], bmax[JCAP / 32];   // y range of each block of 32 entries
+    __shared__ int s_wlo[NW], s_whi[NW];                  // per warp: its lowest / highest near block
     const int ev = order[blockIdx.x], tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int r0 = cu[ev], N = cu[ev + 1] - r0;
     if (N > JCAP) return;   // k_antikt takes this event
@@ -469,6 +471,27 @@ __global__ void __launch_bounds__(NT) k_antikt_sm(const float* __restrict__ reg,
     }
     __syncthreads();
     for (int p = tid; p < n; p += NT) sdd[p] = 0.f;   // active (over the sort keys)
+    // Blocks of 32 consecutive entries keep a conservative range of their rapidities
+    // (widened when a merged entry moves, never narrowed; a y that is not finite has no
+    // neighbour and is in no range).  The rescan of a group of listed entries runs over
+    // the index range from the lowest to the highest block whose range comes within R
+    // of one of them: the entries are sorted by rapidity, merged entries move little, so
+    // that range is a small part of the event, and every thread still takes an equal
+    // share of it.  Float rounding: a pair passes the dR^2 < R^2 test only if |dy| < R
+    // (1 + 2^-22), below the widened R, and rounding is monotonic, so the inclusive test
+    // keeps every such pair.
+    const int nblk = (n + 31) >> 5;   // <= JCAP / 32 <= NT
+    const float Rw = sqrtf(r2) * (1.f + 1e-5f) + 1e-6f;
+    auto near1 = [&](int b, float y) { return y >= bmin[b] - Rw && y <= bmax[b] + Rw; };
+    for (int b = tid; b < nblk; b += NT) {
+        float lo = INFINITY, hi = -INFINITY;
+        for (int m = 32 * b; m < min(n, 32 * b + 32); ++m) {
+            lo = fminf(lo, sy[m]);
+            hi = fmaxf(hi, sy[m]);
+        }
+        bmin[b] = lo;
+        bmax[b] = hi;
+    }
     __syncthreads();
     auto active = [&](int m) { const float d = sdd[m]; return d == d; };
     // nearest active neighbour within R of entry a over the entries m0, m0 + dm, ...
@@ -534,8 +557,11 @@ __global__ void __launch_bounds__(NT) k_antikt_sm(const float* __restrict__ reg,
                 L.py[k] = py;
                 L.ep[k] = ep;
                 L.em[k] = em;
-                sy[k] = 0.5f * logf(ep / em);
+                const float yk = 0.5f * logf(ep / em);
+                sy[k] = yk;
                 sphi[k] = atan2f(py, px);
+                bmin[k >> 5] = fminf(bmin[k >> 5], yk);
+                bmax[k >> 5] = fmaxf(bmax[k >> 5], yk);
                 L.pinv[k] = 1.f / (px * px + py * py);
                 sdd[l] = __int_as_float(0x7fc00000);
                 L.parent[l] = k;
@@ -615,7 +641,28 @@ __global__ void __launch_bounds__(NT) k_antikt_sm(const float* __restrict__ reg,
                     best[q] = INFINITY;
                     bj[q] = INT_MAX;
                 }
-                for (int m = tid; m < n; m += NT) {
+                // the index range of the near blocks: per warp by ballot, then over the warps
+                {
+                    bool nb = false;
+                    if (tid < nblk) {
+#pragma unroll
+                        for (int q = 0; q < JG; ++q) nb |= aa[q] >= 0 && near1(tid, ya[q]);
+                    }
+                    const unsigned bal = __ballot_sync(0xffffffffu, nb);
+                    if (lane == 0) {
+                        s_wlo[warp] = bal ? 32 * warp + __ffs(bal) - 1 : INT_MAX;
+                        s_whi[warp] = bal ? 32 * warp + 31 - __clz(bal) : -1;
+                    }
+                }
+                __syncthreads();
+                int blo = lane < NW ? s_wlo[lane] : INT_MAX, bhi = lane < NW ? s_whi[lane] : -1;
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+                    blo = min(blo, __shfl_xor_sync(0xffffffffu, blo, off));
+                    bhi = max(bhi, __shfl_xor_sync(0xffffffffu, bhi, off));
+                }
+                const int m_end = min(n, 32 * (bhi + 1));
+                for (int m = (blo == INT_MAX ? n : 32 * blo) + tid; m < m_end; m += NT) {
                     if (!active(m)) continue;
                     const float ym = sy[m], pm = sphi[m];
 #pragma unroll
