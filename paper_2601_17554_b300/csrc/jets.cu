@@ -534,7 +534,12 @@ __global__ void __launch_bounds__(NT) k_antikt_sm(const float* __restrict__ reg,
         const int i = bi;
         if (tid == 0) {
             const int j = snn[i];
+            // every global field the step may need, in one round of loads (j's are i's
+            // again when i has no neighbour)
+            const int jj = j < 0 ? i : j;
             const float pi = L.pinv[i];
+            const float pxi = L.px[i], pyi = L.py[i], epi = L.ep[i], emi = L.em[i];
+            const float pxj = L.px[jj], pyj = L.py[jj], epj = L.ep[jj], emj = L.em[jj];
             const bool beam = j < 0 || !(pi * sd2[i] * inv_r2 < pi);
             s_j = j;
             s_beam = beam;
@@ -543,16 +548,15 @@ __global__ void __launch_bounds__(NT) k_antikt_sm(const float* __restrict__ reg,
             if (beam) {   // i is a jet: (px, py, pz, E)
                 const int t = s_jets++;
                 float* o = jets + (size_t)(r0 + t) * 4;
-                o[0] = L.px[i];
-                o[1] = L.py[i];
-                o[2] = 0.5f * (L.ep[i] - L.em[i]);
-                o[3] = 0.5f * (L.ep[i] + L.em[i]);
+                o[0] = pxi;
+                o[1] = pyi;
+                o[2] = 0.5f * (epi - emi);
+                o[3] = 0.5f * (epi + emi);
                 L.jid[i] = t;
                 sdd[i] = __int_as_float(0x7fc00000);   // inactive
             } else {      // merge into the lower index (E scheme)
                 const int k = min(i, j), l = max(i, j);
-                const float px = L.px[k] + L.px[l], py = L.py[k] + L.py[l];
-                const float ep = L.ep[k] + L.ep[l], em = L.em[k] + L.em[l];
+                const float px = pxi + pxj, py = pyi + pyj, ep = epi + epj, em = emi + emj;
                 L.px[k] = px;
                 L.py[k] = py;
                 L.ep[k] = ep;
@@ -641,6 +645,11 @@ __global__ void __launch_bounds__(NT) k_antikt_sm(const float* __restrict__ reg,
                     best[q] = INFINITY;
                     bj[q] = INT_MAX;
                 }
+                // the listed entries' pT^-2 (global memory), loaded before the scan by the
+                // thread that sets their neighbours after it
+                float pin[JG];
+#pragma unroll
+                for (int q = 0; q < JG; ++q) pin[q] = tid == 0 && aa[q] >= 0 ? L.pinv[aa[q]] : 0.f;
                 // the index range of the near blocks: per warp by ballot, then over the warps
                 {
                     bool nb = false;
@@ -694,8 +703,12 @@ __global__ void __launch_bounds__(NT) k_antikt_sm(const float* __restrict__ reg,
                         int ix = lane < NW ? gi[gbuf][lane * JG + q] : INT_MAX;
                         warp_argmin(v, ix);
                         if (lane == 0 && aa[q] >= 0) {
-                            set_nn(aa[q], v, ix);
-                            argmin_pair(bv, bi, sdd[aa[q]], aa[q]);
+                            const int a = aa[q], nn = ix == INT_MAX ? -1 : ix;
+                            const float dd = entry_dist(pin[q], v, nn, inv_r2);
+                            snn[a] = (int16_t)nn;
+                            sd2[a] = nn < 0 ? INFINITY : v;
+                            sdd[a] = dd;
+                            argmin_pair(bv, bi, dd, a);
                         }
                     }
                 }
