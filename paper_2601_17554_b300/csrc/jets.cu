@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 
 #include <climits>
+#include <type_traits>
 #include <string>
 
 #include "internal.h"
@@ -583,41 +584,49 @@ __global__ void __launch_bounds__(NT) k_antikt_sm(const float* __restrict__ reg,
         // carry their distance into the next step's minimum
         bv = INFINITY;
         bi = INT_MAX;
-        for (int m = tid; m < n; m += NT) {
-            float dm = sdd[m];
-            if (!(dm == dm) || (!beam && m == k)) continue;
-            const int nm = snn[m];
-            bool lost = beam ? nm == i : (nm == i || nm == j);
-            if (lost && !beam && nm == k) {
-                // the merged entry moved: still the nearest if it did not move away
-                // (no other entry moved, and the entry it absorbed was not the nearest)
-                const float d = dr2(sy[m], sphi[m], yk, pk);
-                if (d < r2 && d <= sd2[m]) {
-                    sd2[m] = d;
-                    dm = entry_dist(L.pinv[m], d, k, inv_r2);
-                    sdd[m] = dm;
-                    lost = false;
-                }
-            } else if (!lost && !beam) {
-                const float dy = sy[m] - yk;
-                if (dy * dy < r2) {   // else the merged entry is not within R
-                    const float d = dr2(sy[m], sphi[m], yk, pk);
-                    if (d < r2 && (d < sd2[m] || (d == sd2[m] && k < nm))) {
-                        snn[m] = (int16_t)k;
-                        sd2[m] = d;
-                        dm = entry_dist(L.pinv[m], d, k, inv_r2);
-                        sdd[m] = dm;
+        // compiled once for a jet step and once for a merge step (uniform over the step)
+        auto update = [&](auto bc) {
+            constexpr bool BEAM = decltype(bc)::value;
+            for (int m = tid; m < n; m += NT) {
+                float dm = sdd[m];
+                if (!(dm == dm) || (!BEAM && m == k)) continue;
+                const int nm = snn[m];
+                bool lost = BEAM ? nm == i : (nm == i || nm == j);
+                if constexpr (!BEAM) {
+                    if (lost && nm == k) {
+                        // the merged entry moved: still the nearest if it did not move away
+                        // (no other entry moved, and the entry it absorbed was not the nearest)
+                        const float d = dr2(sy[m], sphi[m], yk, pk);
+                        if (d < r2 && d <= sd2[m]) {
+                            sd2[m] = d;
+                            dm = entry_dist(L.pinv[m], d, k, inv_r2);
+                            sdd[m] = dm;
+                            lost = false;
+                        }
+                    } else if (!lost) {
+                        const float dy = sy[m] - yk;
+                        if (dy * dy < r2) {   // else the merged entry is not within R
+                            const float d = dr2(sy[m], sphi[m], yk, pk);
+                            if (d < r2 && (d < sd2[m] || (d == sd2[m] && k < nm))) {
+                                snn[m] = (int16_t)k;
+                                sd2[m] = d;
+                                dm = entry_dist(L.pinv[m], d, k, inv_r2);
+                                sdd[m] = dm;
+                            }
+                        }
                     }
                 }
+                if (lost) {
+                    const int slot = atomicAdd(&s_cnt, 1);
+                    if (slot < JLIST) s_list[slot] = m;
+                    else s_over = 1;
+                } else {
+                    argmin_pair(bv, bi, dm, m);
+                }
             }
-            if (lost) {
-                const int slot = atomicAdd(&s_cnt, 1);
-                if (slot < JLIST) s_list[slot] = m;
-                else s_over = 1;
-            } else {
-                argmin_pair(bv, bi, dm, m);
-            }
-        }
+        };
+        if (beam) update(std::true_type{});
+        else update(std::false_type{});
         __syncthreads();
         const int cnt = s_cnt;
         if (s_over) {   // many entries lost their neighbour: recompute all, then the minimum
@@ -671,20 +680,28 @@ __global__ void __launch_bounds__(NT) k_antikt_sm(const float* __restrict__ reg,
                     bhi = max(bhi, __shfl_xor_sync(0xffffffffu, bhi, off));
                 }
                 const int m_end = min(n, 32 * (bhi + 1));
-                for (int m = (blo == INT_MAX ? n : 32 * blo) + tid; m < m_end; m += NT) {
-                    if (!active(m)) continue;
-                    const float ym = sy[m], pm = sphi[m];
+                const int g = min(JG, cnt - t0);
+                // the scan with the group's G slots in use (most groups hold one or two
+                // entries: about 1.7 entries are listed per step)
+                auto scan_group = [&](auto gc) {
+                    constexpr int G = decltype(gc)::value;
+                    for (int m = (blo == INT_MAX ? n : 32 * blo) + tid; m < m_end; m += NT) {
+                        if (!active(m)) continue;
+                        const float ym = sy[m], pm = sphi[m];
 #pragma unroll
-                    for (int q = 0; q < JG; ++q) {
-                        if (aa[q] < 0 || m == aa[q]) continue;
-                        const float dy = ya[q] - ym;
-                        if (dy * dy < r2) {
-                            const float d = dr2(ya[q], pa[q], ym, pm);
-                            if (d < r2) argmin_pair(best[q], bj[q], d, m);
+                        for (int q = 0; q < G; ++q) {
+                            if (aa[q] < 0 || m == aa[q]) continue;
+                            const float dy = ya[q] - ym;
+                            if (dy * dy < r2) {
+                                const float d = dr2(ya[q], pa[q], ym, pm);
+                                if (d < r2) argmin_pair(best[q], bj[q], d, m);
+                            }
                         }
                     }
-                }
-                const int g = min(JG, cnt - t0);
+                };
+                if (g == 1) scan_group(std::integral_constant<int, 1>{});
+                else if (g == 2) scan_group(std::integral_constant<int, 2>{});
+                else scan_group(std::integral_constant<int, JG>{});
 #pragma unroll
                 for (int q = 0; q < JG; ++q) {
                     if (q >= g) break;   // warp-uniform
