@@ -230,7 +230,8 @@ mlpf_status mlpf_autotune(mlpf_model* m, int32_t precision, const float* x, cons
  *            cu[e] .. cu[e] + n_jets[e] - 1, in the order they leave the list.
  * n_jets     device out, [n_events] int32.
  * jet_of     device out or NULL, [total] int32: the element's jet index within its
- *            event, -1 for elements that are not particles.
+ *            event, -1 for elements that are not particles (and for particles whose
+ *            inputs are not finite enough to give a distance, which join no jet).
  * The events' CTAs run largest event first (a one-CTA sort of the element counts, for
  * up to 4,096 events; more keep the input order), so that the largest events do not
  * end the launch.  Uses a scratch of 53 bytes per element and 4 per event owned by

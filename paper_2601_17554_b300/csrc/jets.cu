@@ -193,6 +193,7 @@ __global__ void __launch_bounds__(JT) k_antikt(const float* __restrict__ reg, co
             L.phi[k] = atan2f(s, c);
             L.pinv[k] = 1.f / (px * px + py * py);
             L.parent[k] = -1;
+            L.jid[k] = -1;   // stays -1 only if the entry never clusters (non-finite input)
             L.act[k] = 1;
         }
         __syncthreads();
@@ -469,6 +470,7 @@ __global__ void __launch_bounds__(NT) k_antikt_sm(const float* __restrict__ reg,
         sphi[p] = atan2f(s, c);
         L.pinv[p] = 1.f / (px * px + py * py);
         L.parent[p] = -1;
+        L.jid[p] = -1;   // stays -1 only if the entry never clusters (non-finite input)
     }
     __syncthreads();
     for (int p = tid; p < n; p += NT) sdd[p] = 0.f;   // active (over the sort keys)

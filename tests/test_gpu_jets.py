@@ -104,6 +104,31 @@ def test_many_small_events(model):
     assert tot > 10000 and mat >= 0.995 * tot, (mat, tot)
 
 
+def test_non_finite_values_stay_contained(model):
+    """An event whose regressions hold NaN and infinite values (pT, eta, sin, cos) between
+    two finite events: the call succeeds, its jet indices are -1 or a jet of the event, and
+    the finite events still match the oracle."""
+    sizes = [300, 200, 250]
+    x, cu = synth.gen_events(52, sizes)
+    cls, reg = synth.gen_targets(53, x, cu)
+    reg, cls = reg.copy(), cls.copy()
+    rows = np.arange(cu[1], cu[2])
+    reg[rows[0:10], 1] = np.nan          # eta
+    reg[rows[10:20], 1] = np.inf
+    reg[rows[20:30], 0] = np.inf         # pT
+    reg[rows[30:40], 2] = np.nan         # sin phi
+    reg[rows[40:50], 3] = -np.inf        # cos phi
+    cls[rows[:50]] = 1
+    gj, gnj, gjof = run_jets(model, reg, cls, cu, 0.4)
+    sl = slice(cu[1], cu[2])
+    assert 0 <= gnj[1] <= sizes[1]
+    assert ((gjof[sl] >= -1) & (gjof[sl] < gnj[1])).all()
+    for e in (0, 2):
+        sl = slice(cu[e], cu[e + 1])
+        n, m = compare_event(gj[cu[e]:cu[e + 1]], int(gnj[e]), gjof[sl], cls[sl], reg[sl], 0.4)
+        assert m >= 0.995 * n
+
+
 def test_closed_forms(model):
     # event 0: two particles within R -> one jet, their sum; event 1: two beyond R ->
     # two jets, the harder first; event 2: a class-0 element and a pT = 0 element only
