@@ -23,3 +23,18 @@ def test_unpack_rejects_bad_blobs():
         synth.unpack_blob(b"XXXX" + blob[4:])
     with pytest.raises(ValueError):
         synth.unpack_blob(blob + b"\0\0\0\0")
+
+
+def test_error_budget_tool_reads_blob_weights(tmp_path):
+    """tests/lowp_budget.py --blob: a blob of the seeded precision-workload model gives the
+    seeded weights back."""
+    from tests import lowp_budget
+    cfg, wseed, _, _ = synth.workload("prec64")
+    w = synth.make_weights(cfg, wseed)
+    path = tmp_path / "m.blob"
+    path.write_bytes(synth.pack_blob(cfg, w))
+    c1, w1 = lowp_budget._weights(str(path))
+    c0, w0 = lowp_budget._weights("")
+    assert c1 == c0 == cfg
+    for k in w0:
+        np.testing.assert_array_equal(np.asarray(w0[k], np.float32), w1[k])
