@@ -174,6 +174,20 @@ def test_full_batch_conserves_momentum(model):
     torch.cuda.synchronize()
     print(f"anti-kt R=0.4 on 512 events ({len(x)} elements): {t0.elapsed_time(t1):.2f} ms, "
           f"{int(nj.sum())} jets")
+    # the largest event alone: the floor of the batch time (one CTA per event)
+    big = int(np.argmax(sizes))
+    s0, s1 = int(cu[big]), int(cu[big + 1])
+    ub = torch.tensor([0, s1 - s0], dtype=torch.int32, device="cuda")
+    rb, cb = rg[s0:s1].contiguous(), cl[s0:s1].contiguous()
+    model.cluster_jets(rb, cb, ub, 0.4)
+    torch.cuda.synchronize()
+    t0.record()
+    _, njb, _ = model.cluster_jets(rb, cb, ub, 0.4)
+    t1.record()
+    torch.cuda.synchronize()
+    print(f"anti-kt R=0.4 on its largest event alone ({s1 - s0} elements, "
+          f"{int((cb != 0).sum())} with a class): {t0.elapsed_time(t1):.2f} ms")
+    assert int(njb[0]) == int(nj[big])
     jets, nj = jets.cpu().numpy().astype(np.float64), nj.cpu().numpy()
     reg, cls = rg.cpu().numpy(), cl.cpu().numpy()
     for e in range(0, len(sizes), 37):
