@@ -1403,19 +1403,45 @@ __global__ void __launch_bounds__(aw_threads<QR, HY>(), QR == 128 ? 1 : 2)
                 // range), then one row-sum MMA per tile instead of one per step
                 // (1 % faster with FP16 operands; slower with BF16)
                 uint32_t ps[2][4];
+                // FP16 operands: S - ref accumulated in FP16 (the references are kept
+                // FP16-representable, so every path uses the same values), whose f16x2
+                // pairs are the exponent arguments as they stand
+                uint32_t nr16[2][2];
+                if constexpr (F16 && !HY) {
+#pragma unroll
+                    for (int mt = 0; mt < 2; ++mt) {
+                        nr16[mt][0] = pack_f16x2(nr[mt][0], nr[mt][1]);
+                        nr16[mt][1] = pack_f16x2(nr[mt][2], nr[mt][3]);
+                    }
+                }
+                (void)nr16;
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    float sc[2][2][4];
                     uint32_t vf[4], pa[2][4];
                     ldsm_x4(vbase + (uint32_t)voff[q], vf[0], vf[1], vf[2], vf[3]);
-                    qkb(kbase, t, q, sc);
+                    if constexpr (F16 && !HY) {
+                        uint32_t kf[4];
+                        ldsm_x4(kbase + koff + 2048u * q, kf[0], kf[1], kf[2], kf[3]);
 #pragma unroll
-                    for (int mt = 0; mt < 2; ++mt)
+                        for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-                        for (int hr = 0; hr < 2; ++hr) {
-                            pa[mt][hr] = exp2_pair<F16>(sc[mt][0][2 * hr], sc[mt][0][2 * hr + 1]);
-                            pa[mt][2 + hr] = exp2_pair<F16>(sc[mt][1][2 * hr], sc[mt][1][2 * hr + 1]);
-                        }
+                            for (int nt = 0; nt < 2; ++nt) {
+                                uint32_t h[2];
+                                mma16816_h(h, qa[mt], kf[2 * nt], kf[2 * nt + 1], nr16[mt]);
+                                pa[mt][2 * nt] = ex2_h2(h[0]);
+                                pa[mt][2 * nt + 1] = ex2_h2(h[1]);
+                            }
+                    } else {
+                        float sc[2][2][4];
+                        qkb(kbase, t, q, sc);
+#pragma unroll
+                        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                            for (int hr = 0; hr < 2; ++hr) {
+                                pa[mt][hr] = exp2_pair<F16>(sc[mt][0][2 * hr], sc[mt][0][2 * hr + 1]);
+                                pa[mt][2 + hr] = exp2_pair<F16>(sc[mt][1][2 * hr], sc[mt][1][2 * hr + 1]);
+                            }
+                    }
 #pragma unroll
                     for (int mt = 0; mt < 2; ++mt) {
                         mma16816<F16>(o[mt][0], pa[mt], vf[0], vf[1]);
@@ -1560,10 +1586,19 @@ __global__ void __launch_bounds__(aw_threads<QR, HY>(), QR == 128 ? 1 : 2)
                                     float mx = lm[mt][hr];
                                     mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
                                     mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
-                                    const float dr = first ? mx : fmaxf(mx, 0.f);
+                                    float dr = first ? mx : fmaxf(mx, 0.f);
+                                    if constexpr (F16 && !HY) {
+                                        // the new reference rounded to FP16 (the bound path's
+                                        // FP16 accumulator input) and used as such everywhere
+                                        const float nn = __half2float(__float2half_rn(nr[mt][2 * hr] - dr));
+                                        dr = nr[mt][2 * hr] - nn;
+                                        nr[mt][2 * hr] = nn;
+                                        nr[mt][2 * hr + 1] = nn;
+                                    } else {
+                                        nr[mt][2 * hr] -= dr;
+                                        nr[mt][2 * hr + 1] -= dr;
+                                    }
                                     const float a = first ? 0.f : ex2_approx(-dr);
-                                    nr[mt][2 * hr] -= dr;
-                                    nr[mt][2 * hr + 1] -= dr;
 #pragma unroll
                                     for (int e = 0; e < 2; ++e) {
                                         o[mt][0][2 * hr + e] *= a;

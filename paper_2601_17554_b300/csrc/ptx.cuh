@@ -405,6 +405,20 @@ MLPF_DEV void mma16816_c(float* d, const uint32_t* a, uint32_t b0, uint32_t b1, 
               "f"(c[3]));
 }
 // d[16x8] += a[16x16] * b[16x8], FP32 accumulate; 16-bit operands FP16 or BF16
+// FP16 operands with an FP16 accumulator (C and D are two f16x2 registers: rows g and
+// g + 8 of the 16 x 8 tile, columns 2 tq and 2 tq + 1)
+MLPF_DEV void mma16816_h(uint32_t* d, const uint32_t* a, uint32_t b0, uint32_t b1, const uint32_t* c) {
+    asm("mma.sync.aligned.m16n8k16.row.col.f16.f16.f16.f16 {%0, %1}, {%2, %3, %4, %5}, {%6, %7}, {%8, %9};"
+        : "=r"(d[0]), "=r"(d[1])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1), "r"(c[0]), "r"(c[1]));
+}
+
+MLPF_DEV uint32_t ex2_h2(uint32_t x) {
+    uint32_t p;
+    asm("ex2.approx.f16x2 %0, %1;" : "=r"(p) : "r"(x));
+    return p;
+}
+
 template <bool F16>
 MLPF_DEV void mma16816(float* d, const uint32_t* a, uint32_t b0, uint32_t b1) {
     if constexpr (F16)
